@@ -1,0 +1,286 @@
+"""Krylov bases and f(A)b methods of arXiv 2212.12758, step by step in FP64.
+
+Indices are 0-based in code: column c of V is the paper's v_{c+1}; H has shape
+(m+1) x m and H[j, c-1] is the paper's h_{j+1,c}.
+
+Readings of the paper taken here (where it is garbled or silent):
+* Alg. 2: the window update is w <- w - h_{j,i-1} v_j and the subdiagonal is
+  h_{i,i-1} = ||w_i||_2 (the printed lines index h_{j,i} v_i and ||w||).
+* The window of Alg. 2 is orthogonalised either by one classical pass (all
+  window dots of the unmodified w, then one update; ``orth="cgs"``) or by the
+  modified sequence (``orth="mgs"``). They agree in exact arithmetic; the CUDA
+  library uses the classical pass.
+* gamma_b = ||b||_2 for the Alg. 2 based methods (eq. relationxx).
+* Breakdown (the paper assumes none, §2): when the new norm satisfies
+  h_{c,c-1} <= 64 eps ||w|| (w before orthogonalisation) or is zero, the basis
+  stops with m_used = c columns.
+* Alg. 4 reuses the basis sketch Theta for the Blendenpik preconditioner, and
+  LSQR starts at zero.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg
+import scipy.sparse
+
+from . import matfun
+
+EPS = np.finfo(np.float64).eps
+ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ = 0, 1, 2, 3
+
+
+def as_operator(A):
+    """Accept a scipy sparse matrix, a dense array, or anything with ``@``."""
+    return A
+
+
+@dataclass
+class Basis:
+    V: np.ndarray      # n x (m_used+1) basis
+    H: np.ndarray      # (m_used+1) x m_used Hessenberg
+    beta: float        # ||b||_2
+    m_used: int
+
+
+def nt_basis(A, b, m: int, k: int, orth: str = "cgs") -> Basis:
+    """Alg. 2 (truncated orthogonalization, §2.1.2): w_i = A v_{i-1} is
+    orthogonalised against the last k basis vectors only."""
+    b = np.asarray(b, dtype=np.float64)
+    n = b.shape[0]
+    V = np.zeros((n, m + 1))
+    H = np.zeros((m + 1, m))
+    beta = float(np.linalg.norm(b))
+    if beta == 0.0:
+        return Basis(V[:, :1], H[:1, :0], 0.0, 0)
+    V[:, 0] = b / beta
+    for c in range(1, m + 1):
+        w = A @ V[:, c - 1]
+        wnorm = float(np.linalg.norm(w))
+        win = list(range(max(0, c - k), c))
+        if orth == "cgs":
+            h = V[:, win].T @ w
+            w = w - V[:, win] @ h
+            H[win, c - 1] = h
+        else:
+            for j in win:
+                H[j, c - 1] = V[:, j] @ w
+                w = w - H[j, c - 1] * V[:, j]
+        H[c, c - 1] = float(np.linalg.norm(w))
+        if not H[c, c - 1] > 64 * EPS * wnorm:
+            return _breakdown(V, H, beta, c)
+        V[:, c] = w / H[c, c - 1]
+    return Basis(V, H, beta, m)
+
+
+def _breakdown(V, H, beta, c):
+    """Basis of dimension c: V_c spans an invariant subspace (in exact arithmetic)."""
+    Vb = np.zeros((V.shape[0], c + 1))
+    Vb[:, :c] = V[:, :c]
+    Hb = np.zeros((c + 1, c))
+    Hb[:c, :c] = H[:c, :c]
+    return Basis(Vb, Hb, beta, c)
+
+
+def arnoldi(A, b, m: int, reorth: bool = False) -> Basis:
+    """Arnoldi with modified Gram-Schmidt (eq. arnoldi, §2): an orthonormal
+    basis U_{m+1} and Hessenberg K. ``reorth`` adds a second MGS pass."""
+    b = np.asarray(b, dtype=np.float64)
+    n = b.shape[0]
+    U = np.zeros((n, m + 1))
+    K = np.zeros((m + 1, m))
+    beta = float(np.linalg.norm(b))
+    if beta == 0.0:
+        return Basis(U[:, :1], K[:1, :0], 0.0, 0)
+    U[:, 0] = b / beta
+    for c in range(1, m + 1):
+        w = A @ U[:, c - 1]
+        wnorm = float(np.linalg.norm(w))
+        for _ in range(2 if reorth else 1):
+            for j in range(c):
+                hj = U[:, j] @ w
+                K[j, c - 1] += hj
+                w = w - hj * U[:, j]
+        K[c, c - 1] = float(np.linalg.norm(w))
+        if not K[c, c - 1] > 64 * EPS * wnorm:
+            return _breakdown(U, K, beta, c)
+        U[:, c] = w / K[c, c - 1]
+    return Basis(U, K, beta, m)
+
+
+# ---------------------------------------------------------------------------- LSQR
+@dataclass
+class LSQRResult:
+    x: np.ndarray
+    iters: int
+    converged: bool
+
+
+def lsqr(matvec, rmatvec, rhs: np.ndarray, ncols: int, tol: float, maxit: int) -> LSQRResult:
+    """LSQR (Paige and Saunders 1982) for min ||Op x - rhs||_2 from x = 0.
+
+    Golub-Kahan bidiagonalisation with the QR update of the bidiagonal by plane
+    rotations. Stops when ||Op^T r|| <= tol * ||Op||_F-estimate * ||r|| (the
+    method's least-squares stopping rule) or after maxit iterations.
+    """
+    x = np.zeros(ncols)
+    beta = float(np.linalg.norm(rhs))
+    if beta == 0.0:
+        return LSQRResult(x, 0, True)
+    u = rhs / beta
+    v = rmatvec(u)
+    alpha = float(np.linalg.norm(v))
+    if alpha == 0.0:
+        return LSQRResult(x, 0, True)
+    v = v / alpha
+    w = v.copy()
+    phibar, rhobar = beta, alpha
+    anorm2 = 0.0
+    for it in range(1, maxit + 1):
+        u = matvec(v) - alpha * u
+        beta = float(np.linalg.norm(u))
+        anorm2 += alpha * alpha + beta * beta
+        if beta > 0.0:
+            u = u / beta
+            v = rmatvec(u) - beta * v
+            alpha = float(np.linalg.norm(v))
+            if alpha > 0.0:
+                v = v / alpha
+        rho = math.hypot(rhobar, beta)
+        c = rhobar / rho
+        s = beta / rho
+        theta = s * alpha
+        rhobar = -c * alpha
+        phi = c * phibar
+        phibar = s * phibar
+        x = x + (phi / rho) * w
+        w = v - (theta / rho) * w
+        if phibar * alpha * abs(c) <= tol * math.sqrt(anorm2) * phibar or beta == 0.0 or alpha == 0.0:
+            return LSQRResult(x, it, True)
+    return LSQRResult(x, maxit, False)
+
+
+# ------------------------------------------------------------------------- methods
+@dataclass
+class Result:
+    x: np.ndarray
+    m_used: int
+    coeffs: np.ndarray          # c with x = gamma * V_m c (gamma = ||b||) where applicable
+    Hhat: np.ndarray | None = None
+    y: np.ndarray | None = None
+    SV: np.ndarray | None = None
+    R: np.ndarray | None = None
+    lsqr_iters: int = 0
+    basis: Basis | None = None
+
+
+def fm_arnoldi(A, b, m: int, f: int, t: float = 1.0, coef=None, reorth: bool = False) -> Result:
+    """Standard Krylov approximation f_m = ||b|| U_m f(K_m) e_1 (eq. standardfm)."""
+    B = arnoldi(A, b, m, reorth=reorth)
+    mu = B.m_used
+    if mu == 0:
+        return Result(np.zeros_like(b, dtype=np.float64), 0, np.zeros(0), basis=B)
+    c = matfun.f_e1(B.H[:mu, :mu], f, t, coef)
+    return Result(B.beta * (B.V[:, :mu] @ c), mu, c, Hhat=B.H[:mu, :mu], basis=B)
+
+
+def noproj(A, b, m: int, k: int, f: int, t: float = 1.0, coef=None, orth: str = "cgs") -> Result:
+    """Alg. 5: ||b|| V_m f(H_m) e_1, no least-squares solve (eq. noproj)."""
+    B = nt_basis(A, b, m, k, orth)
+    mu = B.m_used
+    if mu == 0:
+        return Result(np.zeros_like(b, dtype=np.float64), 0, np.zeros(0), basis=B)
+    c = matfun.f_e1(B.H[:mu, :mu], f, t, coef)
+    return Result(B.beta * (B.V[:, :mu] @ c), mu, c, Hhat=B.H[:mu, :mu], basis=B)
+
+
+def _last_column_update(B: Basis, y: np.ndarray) -> np.ndarray:
+    """H_m + h_{m+1,m} y e_m^T (eq. relationxx)."""
+    mu = B.m_used
+    Hhat = B.H[:mu, :mu].copy()
+    Hhat[:, mu - 1] += B.H[mu, mu - 1] * y
+    return Hhat
+
+
+def sketched_ls(A, b, m: int, k: int, f: int, sketch, t: float = 1.0, coef=None,
+                tol: float = 1e-14, maxit: int | None = None, orth: str = "cgs",
+                exact_ls: bool = False) -> Result:
+    """Alg. 4: y = argmin ||V_m z - v_{m+1}|| by Blendenpik (QR of Theta V_m gives
+    the preconditioner R; LSQR on V_m R^{-1}), then ||b|| V_m f(H_m + h y e_m^T) e_1.
+    ``exact_ls`` solves the least-squares problem densely instead (for pins)."""
+    B = nt_basis(A, b, m, k, orth)
+    mu = B.m_used
+    if mu == 0:
+        return Result(np.zeros_like(b, dtype=np.float64), 0, np.zeros(0), basis=B)
+    Vm, vlast = B.V[:, :mu], B.V[:, mu]
+    SV = sketch.apply(Vm)
+    R = np.linalg.qr(SV, mode="r")
+    if exact_ls:
+        y = np.linalg.lstsq(Vm, vlast, rcond=None)[0]
+        iters = 0
+    else:
+        def mv(z):
+            return Vm @ scipy.linalg.solve_triangular(R, z, lower=False)
+
+        def rmv(u):
+            return scipy.linalg.solve_triangular(R, Vm.T @ u, lower=False, trans="T")
+
+        res = lsqr(mv, rmv, vlast, mu, tol, maxit if maxit is not None else 4 * mu)
+        y = scipy.linalg.solve_triangular(R, res.x, lower=False)
+        iters = res.iters
+    Hhat = _last_column_update(B, y)
+    c = matfun.f_e1(Hhat, f, t, coef)
+    return Result(B.beta * (Vm @ c), mu, c, Hhat=Hhat, y=y, SV=SV, R=R, lsqr_iters=iters, basis=B)
+
+
+def sketched_fast(A, b, m: int, k: int, f: int, sketch, t: float = 1.0, coef=None,
+                  orth: str = "cgs", form: str = "sfom", sav: str = "direct") -> Result:
+    """The sketched variant working on Theta V and Theta A V only.
+
+    form="sfom": eq. sFOM, V_m R^{-1} f(S_m^T Theta A V_m R^{-1}) S_m^T Theta b with
+                 Theta V_m = S_m R_m (thin QR).
+    form="sketch_solve": the Remark after eq. sFOM, y = argmin ||Theta(V_m z - v_{m+1})||,
+                 then ||b|| V_m f(H_m + h y e_m^T) e_1.
+    sav="direct" sketches A V_m column by column; sav="relation" uses
+    Theta V_{m+1} H_m (eq. arnoldilike).
+    """
+    B = nt_basis(A, b, m, k, orth)
+    mu = B.m_used
+    if mu == 0:
+        return Result(np.zeros_like(b, dtype=np.float64), 0, np.zeros(0), basis=B)
+    Vm = B.V[:, :mu]
+    SVfull = sketch.apply(B.V[:, : mu + 1])
+    SV = SVfull[:, :mu]
+    S, R = np.linalg.qr(SV)
+    if form == "sketch_solve":
+        y = scipy.linalg.solve_triangular(R, S.T @ SVfull[:, mu], lower=False)
+        Hhat = _last_column_update(B, y)
+        c = matfun.f_e1(Hhat, f, t, coef)
+        return Result(B.beta * (Vm @ c), mu, c, Hhat=Hhat, y=y, SV=SVfull, R=R, basis=B)
+    if sav == "direct":
+        SAV = sketch.apply(np.column_stack([A @ Vm[:, j] for j in range(mu)]))
+    else:
+        SAV = SVfull @ B.H[: mu + 1, :mu]
+    # M = S^T (Theta A V_m) R^{-1}, i.e. M R = S^T Theta A V_m
+    M = scipy.linalg.solve_triangular(R, (S.T @ SAV).T, lower=False, trans="T").T
+    Sb = sketch.apply(np.asarray(b, dtype=np.float64))
+    z = matfun.f_apply(M, S.T @ Sb, f, t, coef)
+    c = scipy.linalg.solve_triangular(R, z, lower=False)
+    return Result(Vm @ c, mu, c / B.beta, SV=SVfull, R=R, basis=B)
+
+
+def run(method: int, A, b, m: int, k: int, f: int, sketch=None, t: float = 1.0, **kw) -> Result:
+    """Dispatch on the library's method enum."""
+    if method == ARNOLDI:
+        return fm_arnoldi(A, b, m, f, t, reorth=kw.get("reorth", False))
+    if method == NOPROJ:
+        return noproj(A, b, m, k, f, t, orth=kw.get("orth", "cgs"))
+    if method == SKETCHED_LS:
+        return sketched_ls(A, b, m, k, f, sketch, t, tol=kw.get("tol", 1e-14), maxit=kw.get("maxit"),
+                           orth=kw.get("orth", "cgs"))
+    if method == SKETCHED_FAST:
+        return sketched_fast(A, b, m, k, f, sketch, t, orth=kw.get("orth", "cgs"),
+                             form=kw.get("form", "sketch_solve"))
+    raise ValueError("unknown method")

@@ -1,0 +1,242 @@
+"""Pins of the oracle's Krylov bases and f(A)b methods against the paper's statements.
+
+Each check is fixed by the mathematics, not by the oracle itself:
+* eq. arnoldilike: A V_m = V_{m+1} H_m for every basis (residual ~ eps);
+* Alg. 2 with k >= m and MGS is Arnoldi (identical operations);
+* symmetric A, k = 2 gives Lanczos (orthonormal basis; Alg. 5 equals Arnoldi);
+* lemma:basis: with the LS solved exactly, Alg. 4 equals Arnoldi;
+* thm:lastcol: every method is exact for polynomials of degree <= m-1;
+* m = n and #distinct eigenvalues <= m give the exact f(A)b;
+* an orthogonal sketch (full SRHT) makes the sketched variant equal to Arnoldi;
+* eq. sFOM equals its sketch-and-solve form (Remark in §3.3);
+* thm:convclassic, lemma:derivative and thm:lastcol bounds on small cases.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.sparse
+import scipy.sparse.linalg
+
+from oracle import krylov, matfun, sketch
+from paper_2212_12758_gb300 import workloads as W
+
+EXP, SQRT, INVSQRT, POLY = matfun.EXP, matfun.SQRT, matfun.INVSQRT, matfun.POLY
+
+
+def _small_cd(N=12):
+    A = W.to_scipy(W.convdiff(2, N))
+    b = W.random_vector(A.shape[0], 0)
+    return A, b
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _sketch(n, kind=sketch.SPARSE_SIGN, s=None, m=10):
+    s = s or 4 * m
+    return sketch.make(kind, n, s, 1, 8)
+
+
+@pytest.mark.parametrize("k,orth", [(2, "cgs"), (2, "mgs"), (4, "cgs"), (30, "mgs")])
+def test_arnoldi_like_relation(k, orth):
+    A, b = _small_cd()
+    B = krylov.nt_basis(A, b, 25, k, orth)
+    res = A @ B.V[:, :25] - B.V @ B.H
+    assert np.linalg.norm(res) / (scipy.sparse.linalg.norm(A) * np.linalg.norm(B.V)) < 1e-14
+    assert np.allclose(np.linalg.norm(B.V, axis=0), 1.0)
+
+
+def test_nt_full_window_mgs_is_arnoldi():
+    A, b = _small_cd()
+    B1 = krylov.nt_basis(A, b, 20, 20, "mgs")
+    B2 = krylov.arnoldi(A, b, 20)
+    assert np.array_equal(B1.V, B2.V) and np.array_equal(B1.H, B2.H)
+
+
+def test_arnoldi_orthonormal():
+    A, b = _small_cd()
+    B = krylov.arnoldi(A, b, 30, reorth=True)
+    assert np.linalg.norm(B.V.T @ B.V - np.eye(31)) < 1e-13
+
+
+def test_symmetric_k2_is_lanczos():
+    A = W.to_scipy(W.laplacian3d(8))
+    b = W.random_vector(A.shape[0], 1)
+    B = krylov.nt_basis(A, b, 12, 2)
+    assert np.linalg.norm(B.V.T @ B.V - np.eye(13)) < 1e-8
+    r1 = krylov.noproj(A, b, 12, 2, INVSQRT)
+    r2 = krylov.fm_arnoldi(A, b, 12, INVSQRT)
+    assert _rel(r1.x, r2.x) < 1e-8
+
+
+def test_m_equals_n_is_exact():
+    rng = np.random.default_rng(4)
+    n = 12
+    M = np.diag(np.linspace(1, 3, n)) + 0.2 * rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+    for f in (EXP, SQRT, INVSQRT):
+        exact = matfun.exact_fAb(M, b, f, -0.7 if f == EXP else 1.0)
+        r = krylov.fm_arnoldi(M, b, n, f, -0.7 if f == EXP else 1.0)
+        assert _rel(r.x, exact) < 1e-10
+
+
+def test_diagonal_few_distinct_eigenvalues_exact():
+    d = np.repeat([0.5, 1.0, 2.0, 3.5, 5.0], 40)
+    A = W.to_scipy(W.diagonal(d))
+    b = W.random_vector(len(d), 2)
+    exact = np.exp(-0.3 * d) * b  # f(A) b = f(a_ii) b_i
+    assert np.allclose(matfun.exact_fAb(np.diag(d), b, EXP, -0.3), exact, atol=1e-14)
+    th = _sketch(len(d), sketch.SRHT, s=16)
+    for meth in (0, 1, 2, 3):
+        r = krylov.run(meth, A, b, 8, 2, EXP, th, -0.3)
+        assert r.m_used == 5  # the Krylov space is invariant after 5 steps
+        assert _rel(r.x, exact) < 1e-9
+
+
+@pytest.mark.parametrize("meth", [0, 1, 2, 3])
+def test_polynomial_exactness(meth):
+    """thm:lastcol and its corollary: all methods reproduce p(A) b for deg p <= m-1."""
+    A, b = _small_cd()
+    m = 8
+    coef = np.random.default_rng(meth).standard_normal(m) / 10.0**np.arange(m)
+    exact = matfun.exact_fAb(A.toarray() / 1000.0, b, POLY, coef=coef)
+    As = A / 1000.0
+    th = _sketch(A.shape[0], sketch.SPARSE_SIGN, s=4 * m, m=m)
+    if meth == 0:
+        r = krylov.fm_arnoldi(As, b, m, POLY, coef=coef)
+    elif meth == 1:
+        r = krylov.sketched_ls(As, b, m, 2, POLY, th, coef=coef)
+    elif meth == 2:
+        r = krylov.sketched_fast(As, b, m, 2, POLY, th, coef=coef, form="sketch_solve")
+    else:
+        r = krylov.noproj(As, b, m, 2, POLY, coef=coef)
+    assert _rel(r.x, exact) < 1e-10
+
+
+def test_lemma_basis_exact_ls_equals_arnoldi():
+    A, b = _small_cd(16)
+    th = _sketch(A.shape[0], m=20)
+    for f, t in ((EXP, -0.01), (INVSQRT, 1.0)):
+        r1 = krylov.sketched_ls(A, b, 20, 2, f, th, t, exact_ls=True)
+        r2 = krylov.fm_arnoldi(A, b, 20, f, t)
+        assert _rel(r1.x, r2.x) < 1e-10
+        r3 = krylov.sketched_ls(A, b, 20, 2, f, th, t, tol=1e-14)
+        assert _rel(r3.x, r2.x) < 1e-10
+
+
+def test_orthogonal_sketch_gives_arnoldi():
+    A = W.to_scipy(W.convdiff(2, 16))  # n = 256 = n'
+    b = W.random_vector(256, 3)
+    th = sketch.SRHT_(256, 256, 4)
+    r1 = krylov.sketched_fast(A, b, 20, 2, EXP, th, -0.01, form="sketch_solve")
+    r2 = krylov.fm_arnoldi(A, b, 20, EXP, -0.01)
+    assert _rel(r1.x, r2.x) < 1e-10
+
+
+def test_sfom_equals_sketch_and_solve():
+    A, b = _small_cd(20)
+    th = _sketch(A.shape[0], sketch.SRHT, s=60, m=25)
+    for f, t in ((EXP, -0.01), (SQRT, 1.0)):
+        r1 = krylov.sketched_fast(A, b, 25, 2, f, th, t, form="sfom", sav="direct")
+        r2 = krylov.sketched_fast(A, b, 25, 2, f, th, t, form="sfom", sav="relation")
+        r3 = krylov.sketched_fast(A, b, 25, 2, f, th, t, form="sketch_solve")
+        assert _rel(r1.x, r3.x) < 1e-11 and _rel(r2.x, r3.x) < 1e-11
+
+
+def test_lsqr_matches_lstsq():
+    rng = np.random.default_rng(8)
+    M = rng.standard_normal((300, 12)) @ np.diag(np.logspace(0, 1, 12))
+    rhs = rng.standard_normal(300)
+    res = krylov.lsqr(lambda z: M @ z, lambda u: M.T @ u, rhs, 12, 1e-14, 200)
+    ref = np.linalg.lstsq(M, rhs, rcond=None)[0]
+    assert res.converged and _rel(res.x, ref) < 1e-10
+
+
+def test_exp_matches_expm_multiply_on_c1_shape():
+    """exp(-0.01 A) b for the 2D convection-diffusion operator: Arnoldi with a large
+    basis agrees with SciPy's expm_multiply (Al-Mohy and Higham 2011)."""
+    A = W.to_scipy(W.convdiff(2, 40))
+    b = W.random_vector(A.shape[0], 0)
+    ref = scipy.sparse.linalg.expm_multiply(-0.01 * A, b)
+    r = krylov.fm_arnoldi(A, b, 120, EXP, -0.01, reorth=True)
+    assert _rel(r.x, ref) < 1e-9
+
+
+def test_convclassic_bound_symmetric():
+    """thm:convclassic on a symmetric case: W(A) = [lmin, lmax]; the minimax error
+    is bounded by the Chebyshev interpolant's error."""
+    A = W.to_scipy(W.laplacian3d(6))
+    lam = np.linalg.eigvalsh(A.toarray())
+    b = W.random_vector(A.shape[0], 5)
+    exact = matfun.exact_fAb(A.toarray(), b, INVSQRT)
+    for m in (3, 5, 8):
+        r = krylov.fm_arnoldi(A, b, m, INVSQRT)
+        lo, hi = lam[0], lam[-1]
+        k = np.arange(m)
+        nodes = (lo + hi) / 2 + (hi - lo) / 2 * np.cos((2 * k + 1) * np.pi / (2 * m))
+        p = np.polynomial.Polynomial.fit(nodes, 1 / np.sqrt(nodes), m - 1)
+        z = np.linspace(lo, hi, 20001)
+        cheb_err = np.max(np.abs(1 / np.sqrt(z) - p(z)))
+        assert np.linalg.norm(exact - r.x) <= 2 * (1 + math.sqrt(2)) * cheb_err * 1.0001
+
+
+def _range_box(*mats):
+    re_lo = min(np.linalg.eigvalsh((M + M.T) / 2)[0] for M in mats)
+    re_hi = max(np.linalg.eigvalsh((M + M.T) / 2)[-1] for M in mats)
+    im = max(np.abs(np.linalg.eigvalsh(((M - M.T) / 2j).astype(complex))).max() for M in mats)
+    return re_lo, re_hi, im
+
+
+def test_lemma_derivative_bound():
+    """lemma:derivative for f = exp(tz): perturbing y changes f(.) by at most
+    (1+sqrt2)^2 ||f'||_D ||h (y - y~)||."""
+    A, b = _small_cd(10)
+    t = -0.002
+    B = krylov.nt_basis(A, b, 12, 2)
+    m = 12
+    Vm = B.V[:, :m]
+    y = np.linalg.lstsq(Vm, B.V[:, m], rcond=None)[0]
+    yt = y + 1e-3 * np.random.default_rng(1).standard_normal(m)
+    C = B.H[:m, :m].copy(); C[:, -1] += B.H[m, m - 1] * y
+    D = B.H[:m, :m].copy(); D[:, -1] += B.H[m, m - 1] * yt
+    re_lo, re_hi, im = _range_box(C, D)
+    fprime = abs(t) * math.exp(t * re_lo)  # sup of |t e^{tz}| on the box (t < 0)
+    lhs = np.linalg.norm(scipy.linalg.expm(t * C) - scipy.linalg.expm(t * D), "fro")
+    rhs = (1 + math.sqrt(2)) ** 2 * fprime * np.linalg.norm(B.H[m, m - 1] * (y - yt))
+    assert lhs <= rhs
+
+
+def test_lastcol_bound_disk():
+    """thm:lastcol with a disk containing both numerical ranges: the minimax error
+    is bounded by the Taylor remainder of exp(tz) about the disk centre."""
+    A, b = _small_cd(10)
+    t = -0.0004
+    for m in (4, 6, 8):
+        B = krylov.nt_basis(A, b, m, 2)
+        Vm = B.V[:, :m]
+        P = np.linalg.pinv(Vm) @ (A @ Vm)
+        Hm = B.H[:m, :m]
+        lhs = np.linalg.norm(scipy.linalg.expm(t * P)[:, 0] - scipy.linalg.expm(t * Hm)[:, 0])
+        c = np.trace(Hm) / m
+        r = max(np.linalg.norm(P - c * np.eye(m), 2), np.linalg.norm(Hm - c * np.eye(m), 2))
+        x = abs(t) * r
+        tail = sum(x**j / math.factorial(j) for j in range(m, m + 60))
+        rhs = (2 + 2 * math.sqrt(2)) * math.exp(t * c) * tail
+        assert lhs <= rhs * 1.0001
+
+
+def test_matfun_against_eigendecomposition():
+    rng = np.random.default_rng(9)
+    n = 15
+    X = rng.standard_normal((n, n))
+    lam = np.linspace(0.5, 4.0, n)
+    M = X @ np.diag(lam) @ np.linalg.inv(X)
+    z = rng.standard_normal(n)
+    for f, t in ((EXP, -0.4), (SQRT, 1.0), (INVSQRT, 1.0)):
+        ref = X @ (matfun.f_scalar(lam, f, t) * np.linalg.solve(X, z))
+        assert _rel(matfun.f_apply(M, z, f, t), ref) < 1e-8
+    S = matfun.sqrtm(M)
+    assert np.linalg.norm(S @ S - M) / np.linalg.norm(M) < 1e-10
