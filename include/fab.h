@@ -1,0 +1,169 @@
+/*
+ * fab.h - C ABI of libfab: randomized Krylov approximations of f(A)b on one
+ * GB300 GPU (sm_103a), after Cortinovis, Kressner and Nakatsukasa,
+ * "Speeding up Krylov subspace methods for computing f(A)b via randomization"
+ * (arXiv 2212.12758).
+ *
+ * Problem (paper §1): given a sparse nonsymmetric A (n x n, CSR) and b, compute
+ * x ~ f(A) b for f in {exp(tz), z^{1/2}, z^{-1/2}} from an m-dimensional Krylov
+ * space K_m(A, b) = span{b, Ab, ..., A^{m-1} b} (eq. krylovspace).
+ *
+ * Methods (enum fab_method):
+ *   FAB_ARNOLDI        eq. standardfm: ||b|| U_m f(K_m) e_1 with an orthonormal
+ *                      Arnoldi basis (classical Gram-Schmidt applied twice).
+ *   FAB_SKETCHED_LS    Alg. 4: Alg. 2 basis, y = argmin ||V_m z - v_{m+1}|| by
+ *                      Blendenpik (QR of Theta V_m as preconditioner, LSQR), then
+ *                      ||b|| V_m f(H_m + h_{m+1,m} y e_m^T) e_1 (eq. relationxx).
+ *   FAB_SKETCHED_FAST  eq. sFOM in its sketch-and-solve form (Remark after eq. sFOM):
+ *                      y = argmin ||Theta (V_m z - v_{m+1})||, then as above.
+ *   FAB_NOPROJ         Alg. 5: ||b|| V_m f(H_m) e_1 (eq. noproj).
+ * The Alg. 2 basis orthogonalizes A v_{i-1} against the last k basis vectors
+ * only (§2.1.2); the sketch Theta (s x n) is applied in the same pass that
+ * produces each basis vector.
+ *
+ * Sketches (enum fab_sketch), all generated on the device from (seed, index)
+ * by SplitMix64 (stream 1 sparse-sign rows, 2 signs, 3 SRHT D, 4 SRHT P):
+ *   FAB_SK_SPARSE_SIGN  zeta nonzeros +-1/sqrt(zeta) per column (paper §2.1.1).
+ *   FAB_SK_SRHT         s^{-1/2} P H D on the input zero-padded to n' = 2^ceil(log2 n)
+ *                       (paper §2.1.1).
+ *   FAB_SK_GAUSSIAN     reserved (dense N(0,1/s)); fab_apply returns FAB_EINVAL.
+ *
+ * Conventions for every entry point:
+ *   - Return FAB_OK (0) or a negative FAB_E* code; nothing throws across the ABI.
+ *   - Pointers flagged "on device" are CUDA device pointers of the current
+ *     device; otherwise host pointers. All arrays are caller-owned and are not
+ *     retained after the call returns, except as stated for handles.
+ *   - Handles are not thread-safe; use one handle per host thread.
+ *   - A fab_params.stream of NULL means the legacy default stream.
+ */
+#ifndef FAB_H
+#define FAB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  FAB_OK = 0,
+  FAB_EINVAL = -1,    /* invalid argument: bad CSR, k < 1, s < m+1, sizes out of range */
+  FAB_ENOMEM = -2,    /* device allocation failed (nothing leaked)                     */
+  FAB_ECUDA = -3,     /* a CUDA call failed                                            */
+  FAB_ENUMERIC = -4,  /* NaN/Inf in the basis, or no principal square root             */
+  FAB_ETIMEOUT = -5,  /* a bounded wait expired                                        */
+  FAB_ENOTCONV = -6   /* LSQR or the square-root iteration hit its iteration limit     */
+};
+
+typedef enum { FAB_F_EXP = 0, FAB_F_SQRT = 1, FAB_F_INVSQRT = 2 } fab_func;
+typedef enum { FAB_ARNOLDI = 0, FAB_SKETCHED_LS = 1, FAB_SKETCHED_FAST = 2, FAB_NOPROJ = 3 } fab_method;
+typedef enum { FAB_SK_SPARSE_SIGN = 0, FAB_SK_SRHT = 1, FAB_SK_GAUSSIAN = 2 } fab_sketch;
+typedef enum { FAB_FP64 = 0, FAB_MIXED = 1 } fab_precision;
+
+/* Parameters of one solve. Fill with fab_params_default() and override. */
+typedef struct fab_params {
+  int f;             /* fab_func                                                   */
+  double t;          /* f(z) = exp(t z) for FAB_F_EXP; ignored otherwise           */
+  int m;             /* Krylov dimension, 1 <= m <= 1024                            */
+  int k;             /* truncation window of Alg. 2, 1 <= k <= 8 (ignored by Arnoldi) */
+  int s;             /* sketch rows, m+1 <= s <= 4096 (sketched methods)            */
+  int zeta;          /* nonzeros per column of the sparse-sign sketch, 1..min(s,64) */
+  int sketch;        /* fab_sketch                                                 */
+  uint64_t seed;     /* sketch seed                                                */
+  int method;        /* fab_method                                                 */
+  int precision;     /* fab_precision; only FAB_FP64 is accepted by this version   */
+  double lsqr_tol;   /* LSQR stopping tolerance (paper §5 uses 1e-6)               */
+  int lsqr_maxit;    /* LSQR iteration limit (0: 4m)                               */
+  void* stream;      /* cudaStream_t to run on, or NULL                            */
+} fab_params;
+
+/* Diagnostics of the last solve (all optional for the caller). */
+typedef struct fab_stats {
+  int m_used;           /* basis dimension actually used (< m after a breakdown) */
+  int lsqr_iters;       /* LSQR iterations (FAB_SKETCHED_LS)                     */
+  int fh_iters;         /* squarings (exp) or Denman-Beavers iterations           */
+  int reserved;
+  double h_last;        /* h_{m+1,m}                                             */
+  double beta;          /* ||b||_2                                               */
+  double ms_basis;      /* device time of the basis (+ fused sketch) loop        */
+  double ms_small;      /* device time of QR / LSQR / f(H)                       */
+  double ms_combine;    /* device time of x = ||b|| V_m c                        */
+  double ms_total;      /* device time of the whole solve                        */
+} fab_stats;
+
+typedef struct fab_handle fab_handle;
+
+/* Default parameters: exp with t = 1, m = 30, k = 2, s = 4m... set explicitly. */
+void fab_params_default(fab_params* p);
+
+/* Message for an error code (static string). */
+const char* fab_strerror(int code);
+
+/*
+ * fab_create - copy A (CSR) into a new handle.
+ *   n       matrix order, 1 <= n < 2^31
+ *   nnz     number of stored entries, 0 <= nnz < 2^31
+ *   rowptr  n+1 row offsets (int64), rowptr[0] = 0, nondecreasing, rowptr[n] = nnz
+ *   colind  nnz column indices (int32), each in [0, n)
+ *   vals    nnz FP64 values
+ *   inputs_on_device  nonzero if the three arrays are device pointers
+ * The handle owns its device copy of A and all solve workspace; the caller keeps
+ * ownership of its arrays. Validation (monotone rowptr, column range) is done on
+ * the host copy; invalid input returns FAB_EINVAL and *out is left NULL.
+ * The matrix is the operator A of the paper's problem statement (§1).
+ */
+int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr,
+               const int32_t* colind, const double* vals, int inputs_on_device);
+
+/*
+ * fab_apply - x ~ f(A) b with the method, basis and sketch given in *p.
+ *   b, x           n-vectors (FP64), device pointers if bx_on_device else host
+ *   st             optional diagnostics (may be NULL)
+ * Runs on p->stream; returns after x is written (the call synchronizes that
+ * stream). Workspace grows on demand and is kept by the handle. A breakdown of
+ * the basis (h_{c,c-1} <= 64 eps ||A v_{c-1}||) is not an error: the space is
+ * invariant and the result uses m_used = c basis vectors. b = 0 gives x = 0.
+ */
+int fab_apply(fab_handle* h, const fab_params* p, const double* b, double* x,
+              int bx_on_device, fab_stats* st);
+
+/* Release a handle and everything it owns. NULL-safe. */
+void fab_destroy(fab_handle* h);
+
+/*
+ * fab_last_state - copy the last solve's small quantities to host arrays.
+ *   H      (m+1) x m Hessenberg, column-major, ld = m+1 (paper's underline H_m)
+ *   SV     s x (m+1) sketch Theta V_{m+1}, column-major (sketched methods; else untouched)
+ *   y      m-vector of eq. leastsquares (sketched methods; zero for the others)
+ *   coeffs m-vector c with x = ||b|| V_m c
+ * Any pointer may be NULL. Sizes are those of the last fab_apply's m and s.
+ * Returns FAB_EINVAL if no solve has run on this handle.
+ */
+int fab_last_state(fab_handle* h, double* H, double* SV, double* y, double* coeffs);
+
+/*
+ * fab_last_basis - copy the last solve's basis V_{m+1} (n x (m+1), column-major,
+ * ld = n) to a host or device array (dst_on_device). The library stores each
+ * column unnormalized with a separate scale; the copy holds the normalized v_j.
+ */
+int fab_last_basis(fab_handle* h, double* V, int dst_on_device);
+
+/*
+ * fab_sketch_apply - out = Theta V for ncols device columns.
+ *   sketch, s, zeta, seed  as in fab_params (Theta is s x n)
+ *   V_dev   device array, column j at V_dev + j*ldv, ldv >= n
+ *   out_dev device array s x ncols, column-major, ld = s
+ *   stream  cudaStream_t or NULL
+ * Uses the same fused kernels as the basis loop (exact int64 block transform
+ * per 4096-row chunk, FP64 cross-chunk sums). Allocates its scratch with
+ * cudaMallocAsync on the stream and synchronizes the stream before returning.
+ */
+int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t seed,
+                     const double* V_dev, int64_t ldv, int ncols, double* out_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FAB_H */

@@ -1,0 +1,595 @@
+// Basis-loop kernels of libfab: CSR SpMV fused with the window dot products of
+// Alg. 2 (truncated orthogonalization, paper §2.1.2), the window update fused
+// with the norm and the sketch of the new vector (paper §2.1.1, §3.3), the
+// cross-chunk sketch reduction, the SRHT row sampling, and the classical
+// Gram-Schmidt passes of the Arnoldi baseline (eq. arnoldi).
+//
+// Storage: the basis is kept as raw columns W_j (column-major, leading
+// dimension ld) with separate scales sigma_j = 1/||W_j||, so v_j = sigma_j W_j.
+// Every consumer folds sigma_j into its coefficients, which saves the pass
+// that would otherwise normalize each new vector.
+#include <float.h>
+#include <limits.h>
+
+#include "fab_internal.cuh"
+
+namespace fab {
+
+int sm_count();
+
+// ------------------------------------------------------------------- state
+__global__ void k_state_reset(DevState* st, int m) {
+  st->m_used = m;
+  st->stop = 0;
+  st->status = FAB_OK;
+  st->flag = 0;
+  st->iters = 0;
+  st->beta = 0.0;
+  for (int i = 0; i < 16; ++i) st->scal[i] = 0.0;
+}
+
+cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s) {
+  k_state_reset<<<1, 1, 0, s>>>(st, m);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------- SpMV + window dot products
+// w = sigma_{c-1} A W_{c-1} is written to W_c; for the window j0..j0+kw-1 the
+// dots <W_j, w> and ||w||^2 are reduced over the grid. The last block writes
+// h_{j,c-1} = sigma_j <W_j, w> into H, the update coefficients
+// coef_q = sigma_j h_{j,c-1} for the raw columns, and ||w||^2 into wn2[c].
+__global__ __launch_bounds__(kThreads) void k_spmv_dots(
+    Csr A, double* __restrict__ W, int64_t ld, int c, int j0, int kw, const double* __restrict__ sigma,
+    double* __restrict__ H, int ldh, double* __restrict__ coef, double* __restrict__ wn2, double* __restrict__ part,
+    unsigned* __restrict__ counter, DevState* st) {
+  constexpr int NV = kMaxWindow + 1;
+  __shared__ double sh[32 * NV];
+  __shared__ double tot[NV];
+  if (st->stop) return;
+  const double* vin = W + (size_t)(c - 1) * ld;
+  double* wout = W + (size_t)c * ld;
+  const double sc = sigma[c - 1];
+  double acc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+  for (int r = blockIdx.x * kThreads + threadIdx.x; r < A.n; r += gridDim.x * kThreads) {
+    const int e0 = A.rowptr[r], e1 = A.rowptr[r + 1];
+    double y = 0.0;
+    for (int e = e0; e < e1; ++e) y = fma(__ldg(A.vals + e), __ldg(vin + __ldg(A.colind + e)), y);
+    const double w = sc * y;
+    wout[r] = w;
+#pragma unroll
+    for (int q = 0; q < kMaxWindow; ++q)
+      if (q < kw) acc[q] = fma(W[(size_t)(j0 + q) * ld + r], w, acc[q]);
+    acc[kMaxWindow] = fma(w, w, acc[kMaxWindow]);
+  }
+  block_sum<NV>(acc, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) part[(size_t)blockIdx.x * NV + q] = acc[q];
+  }
+  if (!last_block(counter)) return;
+  sum_partials(part, gridDim.x, NV, tot, sh);
+  if (threadIdx.x < kw) {
+    const int j = j0 + threadIdx.x;
+    const double h = sigma[j] * tot[threadIdx.x];
+    H[j + (size_t)ldh * (c - 1)] = h;
+    coef[threadIdx.x] = sigma[j] * h;
+  }
+  if (threadIdx.x == 0) {
+    wn2[c] = tot[kMaxWindow];
+    *counter = 0;
+  }
+}
+
+cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0, int kw, const double* sigma,
+                             double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
+                             DevState* st, cudaStream_t s) {
+  static int occ = 0;
+  if (occ == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_dots, kThreads, 0);
+    if (occ < 1) occ = 1;
+  }
+  const int need = (A.n + kThreads - 1) / kThreads;
+  int grid = sm_count() * occ;
+  if (need < grid) grid = need < 1 ? 1 : need;
+  k_spmv_dots<<<grid, kThreads, 0, s>>>(A, W, ld, c, j0, kw, sigma, H, ldh, coef, wn2, part, counter, st);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------- exact int64 chunk sketches
+// A chunk of 4096 consecutive rows is converted to a common block exponent:
+// x = X * 2^(E - 1071) with X an int64 of at most 49 significant bits, E the
+// largest biased exponent in the chunk. Sums of up to 4096 such integers are
+// exact in int64 (|sum| < 2^61), so the chunk's sketch is exact apart from
+// the rounding of x to X (relative 2^-49 of the chunk maximum) and of the
+// final int64 -> FP64 conversion, and it does not depend on summation order.
+
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+__device__ __forceinline__ long long to_fixed(double x, int E) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const int ef = (int)((bits >> 52) & 0x7FF);
+  const unsigned long long mant = bits & ((1ull << 52) - 1);
+  const unsigned long long M = ef ? (mant | (1ull << 52)) : mant;
+  const int eff = ef ? ef : 1;
+  int sh = E - eff + 4;
+  if (sh > 63) sh = 63;
+  if (sh < 1) sh = 1;  // only when E == 0 (all entries zero or subnormal)
+  const long long X = (long long)((M + (1ull << (sh - 1))) >> sh);
+  return (bits >> 63) ? -X : X;
+}
+
+__device__ __forceinline__ int pidx(int j) { return j + (j >> 4); }  // bank-conflict padding
+
+// In-register Walsh-Hadamard butterflies over the 4 index bits held by a thread.
+__device__ __forceinline__ void wht16(long long (&X)[16]) {
+#pragma unroll
+  for (int h = 1; h < 16; h <<= 1) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if ((i & h) == 0) {
+        const long long a = X[i], b = X[i + h];
+        X[i] = a + b;
+        X[i + h] = a - b;
+      }
+    }
+  }
+}
+
+// Block maximum of an int (all threads receive it).
+__device__ __forceinline__ int block_max_int(int v, int* sh) {
+  v = (int)__reduce_max_sync(0xffffffffu, (unsigned)v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int m = 0;
+  for (int w = 0; w < kThreads / 32; ++w) m = max(m, sh[w]);
+  __syncthreads();
+  return m;
+}
+
+// SRHT chunk: y = H_4096 (D x_chunk); writes y at the sampled in-chunk rows.
+// Thread t holds rows i*256 + t (i = 0..15) of the chunk.
+__device__ void sketch_chunk_srht(const double (&v)[kRowsPerThread], int chunk, const SketchDev& sk,
+                                  long long* buf, const int* s_rl, int* s_int) {
+  const int t = threadIdx.x;
+  int e = 0;
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) e = max(e, exp_field(v[i]));
+  const int E = block_max_int(e, s_int);
+  long long X[16];
+  const unsigned long long word0 = (unsigned long long)chunk * (kChunk / 64) + (t >> 6);
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) {
+    long long x = to_fixed(v[i], E);
+    const unsigned long long dw = rng_u(sk.st_D, word0 + (unsigned long long)i * (kThreads / 64));
+    if ((dw >> (t & 63)) & 1ull) x = -x;
+    X[i] = x;
+  }
+  wht16(X);  // index bits 8..11
+#pragma unroll
+  for (int i = 0; i < 16; ++i) buf[pidx(i * kThreads + t)] = X[i];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 16; ++q) X[q] = buf[pidx(t * 16 + q)];
+  wht16(X);  // index bits 0..3
+#pragma unroll
+  for (int q = 0; q < 16; ++q) buf[pidx(t * 16 + q)] = X[q];
+  __syncthreads();
+  const int base3 = (t >> 4) * 256 + (t & 15);
+#pragma unroll
+  for (int q = 0; q < 16; ++q) X[q] = buf[pidx(base3 + q * 16)];
+  wht16(X);  // index bits 4..7
+#pragma unroll
+  for (int q = 0; q < 16; ++q) buf[pidx(base3 + q * 16)] = X[q];
+  __syncthreads();
+  double b;
+  const double a = pow2_split(E - 1071, &b);
+  double* out = sk.part + (size_t)chunk * sk.s;
+  for (int q = t; q < sk.s; q += kThreads) out[q] = ((double)buf[pidx(s_rl[q])] * a) * b;
+  __syncthreads();
+}
+
+// Sparse-sign chunk: every row j scatters +-X_j into its zeta sketch rows.
+__device__ void sketch_chunk_sparse(const double (&v)[kRowsPerThread], int chunk, int n, const SketchDev& sk,
+                                    unsigned long long* acc, int* s_int) {
+  const int t = threadIdx.x;
+  int e = 0;
+#pragma unroll
+  for (int i = 0; i < kRowsPerThread; ++i) e = max(e, exp_field(v[i]));
+  const int E = block_max_int(e, s_int);
+  const unsigned s = (unsigned)sk.s;
+  for (int i = 0; i < kRowsPerThread; ++i) {
+    const long long j = (long long)chunk * kChunk + i * kThreads + t;
+    if (j >= n) break;
+    const long long X = to_fixed(v[i], E);
+    if (X == 0) continue;
+    int rows[kMaxZeta];
+    int have = 0;
+    unsigned long long h = 0;
+    for (int cand = 0; cand < 256 && have < sk.zeta; ++cand) {
+      if ((cand & 1) == 0) h = rng_u(sk.st_rows, (unsigned long long)j * 128ull + (unsigned long long)(cand >> 1));
+      const unsigned half = (cand & 1) ? (unsigned)(h >> 32) : (unsigned)h;
+      const int r = (int)(((unsigned long long)half * s) >> 32);
+      bool dup = false;
+#pragma unroll
+      for (int q = 0; q < kMaxZeta; ++q) dup |= (q < have) && (rows[q] == r);
+      if (!dup) {
+#pragma unroll
+        for (int q = 0; q < kMaxZeta; ++q)
+          if (q == have) rows[q] = r;
+        ++have;
+      }
+    }
+    for (int r = 0; have < sk.zeta; ++r) {  // fallback: smallest unused rows
+      bool dup = false;
+#pragma unroll
+      for (int q = 0; q < kMaxZeta; ++q) dup |= (q < have) && (rows[q] == r);
+      if (!dup) {
+#pragma unroll
+        for (int q = 0; q < kMaxZeta; ++q)
+          if (q == have) rows[q] = r;
+        ++have;
+      }
+    }
+    const unsigned long long sg = rng_u(sk.st_signs, (unsigned long long)j);
+#pragma unroll
+    for (int q = 0; q < kMaxZeta; ++q) {
+      if (q < sk.zeta) {
+        const long long val = ((sg >> q) & 1ull) ? -X : X;
+        atomicAdd(acc + rows[q], (unsigned long long)val);
+      }
+    }
+  }
+  __syncthreads();
+  double b;
+  const double a = pow2_split(E - 1071, &b);
+  double* out = sk.part + (size_t)chunk * sk.s;
+  for (int q = t; q < sk.s; q += kThreads) {
+    out[q] = ((double)(long long)acc[q] * a) * b;
+    acc[q] = 0ull;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------ window update + norm + sketch
+// W_c <- W_c - sum_q coef_q W_{j0+q}; optionally ||W_c||^2 is reduced over the
+// grid (mode & kModeNorm) and the last block writes h_{c,c-1} and sigma_c, or
+// ||b|| and sigma_0 for the start vector (mode & kModeInit); optionally the
+// chunk sketch partials of the updated column are written.
+constexpr int kModeNorm = 1;
+constexpr int kModeInit = 2;
+
+template <int SK>
+__global__ __launch_bounds__(kThreads) void k_update(int n, double* __restrict__ W, int64_t ld, int c, int j0, int nc,
+                                                      const double* __restrict__ coef, double* __restrict__ H, int ldh,
+                                                      double* __restrict__ sigma, const double* __restrict__ wn2,
+                                                      int mode, double* __restrict__ part,
+                                                      unsigned* __restrict__ counter, SketchDev sk, DevState* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double sh[32];
+  __shared__ double tot[1];
+  __shared__ int s_int[32];
+  if (st->stop) return;
+  double* s_coef = reinterpret_cast<double*>(smem_raw);  // nc doubles
+  unsigned char* after = smem_raw + ((size_t)nc * 8 + 15) / 16 * 16;
+  long long* buf = reinterpret_cast<long long*>(after);                     // SRHT: pidx(4096) int64
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(after);   // sparse: s uint64
+  int* s_rl = reinterpret_cast<int*>(after + (size_t)(kChunk + kChunk / 16) * 8);  // SRHT: s ints
+  for (int i = threadIdx.x; i < nc; i += kThreads) s_coef[i] = coef[i];
+  if (SK == SK_SRHT)
+    for (int q = threadIdx.x; q < sk.s; q += kThreads) s_rl[q] = sk.P[q] & (kChunk - 1);
+  if (SK == SK_SPARSE)
+    for (int q = threadIdx.x; q < sk.s; q += kThreads) acc[q] = 0ull;
+  __syncthreads();
+  double* wc = W + (size_t)c * ld;
+  const double* Wb = W + (size_t)j0 * ld;
+  double nrm = 0.0;
+  const int nchunks = (n + kChunk - 1) / kChunk;
+  for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const int base = chunk * kChunk + threadIdx.x;
+    double v[kRowsPerThread];
+    if ((chunk + 1) * kChunk <= n) {
+#pragma unroll
+      for (int i = 0; i < kRowsPerThread; ++i) v[i] = wc[base + i * kThreads];
+      for (int q = 0; q < nc; ++q) {
+        const double cf = s_coef[q];
+        const double* col = Wb + (size_t)q * ld + base;
+#pragma unroll
+        for (int i = 0; i < kRowsPerThread; ++i) v[i] = fma(-cf, col[i * kThreads], v[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < kRowsPerThread; ++i) {
+        if (nc > 0) wc[base + i * kThreads] = v[i];
+        nrm = fma(v[i], v[i], nrm);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kRowsPerThread; ++i) v[i] = (base + i * kThreads < n) ? wc[base + i * kThreads] : 0.0;
+      for (int q = 0; q < nc; ++q) {
+        const double cf = s_coef[q];
+        const double* col = Wb + (size_t)q * ld + base;
+#pragma unroll
+        for (int i = 0; i < kRowsPerThread; ++i)
+          if (base + i * kThreads < n) v[i] = fma(-cf, col[i * kThreads], v[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < kRowsPerThread; ++i) {
+        if (base + i * kThreads < n) {
+          if (nc > 0) wc[base + i * kThreads] = v[i];
+          nrm = fma(v[i], v[i], nrm);
+        }
+      }
+    }
+    if (SK == SK_SRHT) sketch_chunk_srht(v, chunk, sk, buf, s_rl, s_int);
+    if (SK == SK_SPARSE) sketch_chunk_sparse(v, chunk, n, sk, acc, s_int);
+  }
+  if (!(mode & kModeNorm)) return;
+  double nv[1] = {nrm};
+  block_sum<1>(nv, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = nv[0];
+  if (!last_block(counter)) return;
+  sum_partials(part, gridDim.x, 1, tot, sh);
+  if (threadIdx.x == 0) {
+    const double h = sqrt(tot[0]);
+    if (mode & kModeInit) {
+      st->beta = h;
+      if (!isfinite(h)) {
+        st->status = FAB_ENUMERIC;
+        st->stop = 1;
+      } else if (h == 0.0) {
+        st->m_used = 0;
+        st->stop = 1;
+        sigma[0] = 0.0;
+      } else {
+        sigma[0] = 1.0 / h;
+      }
+    } else {
+      H[c + (size_t)ldh * (c - 1)] = h;
+      if (!isfinite(h)) {
+        st->status = FAB_ENUMERIC;
+        st->stop = 1;
+      } else if (!(h > 64.0 * DBL_EPSILON * sqrt(wn2[c]))) {
+        st->m_used = c;  // the basis spans an invariant subspace
+        st->stop = 1;
+        sigma[c] = 0.0;
+      } else {
+        sigma[c] = 1.0 / h;
+      }
+    }
+    *counter = 0;
+  }
+}
+
+size_t update_smem_bytes(int kind, int nc, int s) {
+  size_t b = ((size_t)nc * 8 + 15) / 16 * 16;
+  if (kind == SK_SRHT) b += (size_t)(kChunk + kChunk / 16) * 8 + (size_t)s * 4;
+  if (kind == SK_SPARSE) b += (size_t)s * 8;
+  return b;
+}
+
+cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
+                          int ldh, double* sigma, const double* wn2, int mode, double* part, unsigned* counter,
+                          const SketchDev& sk, DevState* st, cudaStream_t s) {
+  const size_t smem = update_smem_bytes(sk.kind, nc, sk.s);
+  const int nchunks = (n + kChunk - 1) / kChunk;
+  const void* fn = sk.kind == SK_SRHT ? (const void*)k_update<SK_SRHT>
+                   : sk.kind == SK_SPARSE ? (const void*)k_update<SK_SPARSE> : (const void*)k_update<SK_NONE>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
+  if (occ < 1) occ = 1;
+  int grid = sm_count() * occ;
+  if (nchunks < grid) grid = nchunks < 1 ? 1 : nchunks;
+  switch (sk.kind) {
+    case SK_SRHT:
+      k_update<SK_SRHT><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, sigma, wn2, mode, part,
+                                                      counter, sk, st);
+      break;
+    case SK_SPARSE:
+      k_update<SK_SPARSE><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, sigma, wn2, mode, part,
+                                                        counter, sk, st);
+      break;
+    default:
+      k_update<SK_NONE><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, sigma, wn2, mode, part,
+                                                      counter, sk, st);
+  }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------- cross-chunk sketch reduce
+// out[q] = scale * sigma[col] * sum_chunks sign(q, chunk) * part[chunk][q], one
+// warp per sketch row, fixed order. For the SRHT the sign is the cross-chunk
+// Hadamard factor (-1)^popcount(rh_q & chunk), rh_q = P_q >> 12.
+__global__ void k_sketch_reduce(SketchDev sk, const double* __restrict__ sigma, int col, double scale,
+                                double* __restrict__ out, DevState* st) {
+  if (st->stop) return;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= sk.s) return;
+  const int rh = (sk.kind == SK_SRHT) ? (sk.P[q] >> sk.chunk_log2) : 0;
+  double a = 0.0;
+  for (int ch = lane; ch < sk.nchunks; ch += 32) {
+    double v = sk.part[(size_t)ch * sk.s + q];
+    if (__popc(rh & ch) & 1) v = -v;
+    a += v;
+  }
+  a = warp_sum(a);
+  if (lane == 0) out[q] = a * scale * (sigma ? sigma[col] : 1.0);
+}
+
+cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
+                                 DevState* st, cudaStream_t s) {
+  const int warps_per_block = 8;
+  const int grid = (sk.s + warps_per_block - 1) / warps_per_block;
+  k_sketch_reduce<<<grid, warps_per_block * 32, 0, s>>>(sk, sigma, col, scale, out, st);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ SRHT row sampling
+// Floyd's algorithm: for i = 0..s-1, j = n'-s+i, t = floor(u(seed,4,i) (j+1) / 2^64);
+// take t unless already taken, else j. Then the rows are sorted (bitonic).
+__global__ void k_srht_sample(int64_t npad, int s, uint64_t stP, int* __restrict__ P) {
+  __shared__ int S[kMaxS];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int i = 0; i < s; ++i) {
+      const long long j = npad - s + i;
+      const unsigned long long t = __umul64hi(rng_u(stP, (unsigned long long)i), (unsigned long long)(j + 1));
+      bool found = false;
+      for (int q = lane; q < i; q += 32) found |= (S[q] == (int)t);
+      found = __any_sync(0xffffffffu, found);
+      if (lane == 0) S[i] = found ? (int)j : (int)t;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  int L = 1;
+  while (L < s) L <<= 1;
+  for (int i = s + threadIdx.x; i < L; i += blockDim.x) S[i] = INT_MAX;
+  __syncthreads();
+  for (int k = 2; k <= L; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const int a = S[i], b = S[ixj];
+          if ((a > b) == up) {
+            S[i] = b;
+            S[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < s; i += blockDim.x) P[i] = S[i];
+}
+
+cudaError_t launch_srht_sample(int64_t npad, int s, uint64_t stP, int* P, cudaStream_t st) {
+  k_srht_sample<<<1, 1024, 0, st>>>(npad, s, stP, P);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- GEMV-T pass
+// part[tile][q] = sum over the tile's rows of W_{j0+q}[r] x[r]; one warp per column.
+__global__ __launch_bounds__(kThreads) void k_gemv_t(int n, const double* __restrict__ W, int64_t ld, int j0, int nc,
+                                                      const double* __restrict__ x, double* __restrict__ part,
+                                                      DevState* st) {
+  __shared__ double xs[kTileRows];
+  if (st && st->stop) return;
+  const int tile = blockIdx.x;
+  const int r0 = tile * kTileRows;
+  const int rows = min(kTileRows, n - r0);
+  for (int i = threadIdx.x; i < rows; i += kThreads) xs[i] = x[r0 + i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int col = warp; col < nc; col += kThreads / 32) {
+    const double* wcol = W + (size_t)(j0 + col) * ld + r0;
+    double a0 = 0.0, a1 = 0.0;
+    int i = lane;
+    for (; i + 32 < rows; i += 64) {
+      a0 = fma(wcol[i], xs[i], a0);
+      a1 = fma(wcol[i + 32], xs[i + 32], a1);
+    }
+    if (i < rows) a0 = fma(wcol[i], xs[i], a0);
+    const double a = warp_sum(a0 + a1);
+    if (lane == 0) part[(size_t)tile * nc + col] = a;
+  }
+}
+
+cudaError_t launch_gemv_t(int n, const double* W, int64_t ld, int j0, int nc, const double* x, double* part,
+                          int ntiles, DevState* st, cudaStream_t s) {
+  k_gemv_t<<<ntiles, kThreads, 0, s>>>(n, W, ld, j0, nc, x, part, st);
+  return cudaGetLastError();
+}
+
+// d_q = sum over tiles of part[tile][q] (fixed order), then with j = j0+q:
+//   Hcol[j] = sigma_j d_q (or += when h_accumulate), coef[q] = extra * sigma_j * (sigma_j d_q).
+__global__ void k_reduce_cols(const double* __restrict__ part, int ntiles, int nc, const double* __restrict__ sigma,
+                              int j0, double* __restrict__ Hcol, int h_accumulate, double* __restrict__ coef,
+                              double extra, DevState* st) {
+  if (st && st->stop) return;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= nc) return;
+  double a = 0.0;
+  for (int t = lane; t < ntiles; t += 32) a += part[(size_t)t * nc + q];
+  a = warp_sum(a);
+  if (lane == 0) {
+    const int j = j0 + q;
+    const double h = sigma[j] * a;
+    if (Hcol) Hcol[j] = h_accumulate ? Hcol[j] + h : h;
+    if (coef) coef[q] = extra * sigma[j] * h;
+  }
+}
+
+cudaError_t launch_reduce_cols(const double* part, int ntiles, int nc, const double* sigma, int j0, double* Hcol,
+                               int h_accumulate, double* coef, double coef_scale_extra, DevState* st,
+                               cudaStream_t s) {
+  const int grid = (nc + 7) / 8;
+  k_reduce_cols<<<grid, 256, 0, s>>>(part, ntiles, nc, sigma, j0, Hcol, h_accumulate, coef, coef_scale_extra, st);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- combine
+// out[r] = keep * out[r] + sum_q coef[q] W_q[r]   (keep = 0 overwrites out)
+__global__ __launch_bounds__(kThreads) void k_combine(int n, const double* __restrict__ W, int64_t ld, int nc,
+                                                       const double* __restrict__ coef, double* __restrict__ out,
+                                                       double keep) {
+  extern __shared__ double s_cf[];
+  for (int i = threadIdx.x; i < nc; i += kThreads) s_cf[i] = coef[i];
+  __syncthreads();
+  for (int r = blockIdx.x * kThreads + threadIdx.x; r < n; r += gridDim.x * kThreads) {
+    double a = (keep != 0.0) ? keep * out[r] : 0.0;
+    for (int q = 0; q < nc; ++q) a = fma(s_cf[q], W[(size_t)q * ld + r], a);
+    out[r] = a;
+  }
+}
+
+cudaError_t launch_combine(int n, const double* W, int64_t ld, int nc, const double* coef, double* out, double keep,
+                           cudaStream_t s) {
+  k_combine<<<grid_rows(n), kThreads, (size_t)nc * 8, s>>>(n, W, ld, nc, coef, out, keep);
+  return cudaGetLastError();
+}
+
+// dst_j = sigma_j W_j (normalized basis for inspection)
+__global__ void k_scale_columns(int n, const double* __restrict__ W, int64_t ld, int nc,
+                                const double* __restrict__ sigma, double* __restrict__ dst, int64_t ldd) {
+  const int j = blockIdx.y;
+  if (j >= nc) return;
+  const double sg = sigma[j];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    dst[(size_t)j * ldd + r] = sg * W[(size_t)j * ld + r];
+}
+
+cudaError_t launch_scale_columns(int n, const double* W, int64_t ld, int nc, const double* sigma, double* dst,
+                                 int64_t ldd, cudaStream_t s) {
+  dim3 grid((unsigned)min((n + 255) / 256, 1024), (unsigned)nc);
+  k_scale_columns<<<grid, 256, 0, s>>>(n, W, ld, nc, sigma, dst, ldd);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- grid sizes
+static int g_sms = 0;
+int sm_count() {
+  if (g_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
+  }
+  return g_sms;
+}
+
+int grid_rows(int n) {
+  const int need = (n + kThreads - 1) / kThreads;
+  const int cap = sm_count() * 8;
+  return need < 1 ? 1 : (need < cap ? need : cap);
+}
+
+
+}  // namespace fab

@@ -1,0 +1,683 @@
+// C ABI of libfab (include/fab.h): handle lifetime, workspace, and the host
+// orchestration of one f(A)b solve. Every arithmetic step runs in the kernels
+// of basis.cu and small.cu; this file only validates arguments, allocates,
+// and enqueues launches on the caller's stream.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fab_internal.cuh"
+#include "small.cuh"
+
+using namespace fab;
+
+namespace {
+
+// Pade [13/13] approximant of exp (Higham, "The scaling and squaring method for the
+// matrix exponential revisited", SIAM J. Matrix Anal. Appl. 26 (2005)):
+// coefficients c_j = (2m-j)! m! / ((2m)! j! (m-j)!), m = 13, and the backward-error
+// threshold theta_13 of that paper's Table 2.3.
+constexpr double kTheta13 = 5.371920351148152;
+
+struct Pade13 {
+  double b[14];
+  Pade13() {
+    const int m = 13;
+    double c = 1.0;
+    double raw[14];
+    raw[0] = 1.0;
+    for (int j = 0; j < m; ++j) {
+      c = c * (double)(m - j) / ((double)(2 * m - j) * (double)(j + 1));
+      raw[j + 1] = c;
+    }
+    for (int j = 0; j <= m; ++j) b[j] = raw[j] / raw[m];
+  }
+};
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Grow-only device buffer; returns false on allocation failure.
+bool ensure(Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return true;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  b.bytes = bytes;
+  return true;
+}
+
+template <typename T>
+T* ptr(Buf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+int fault_countdown() {
+  // Host-side allocation fault injection for tests: FAB_FAULT=alloc:N makes the
+  // N-th workspace allocation of the process fail.
+  static int remaining = -2;
+  if (remaining == -2) {
+    remaining = -1;
+    const char* e = getenv("FAB_FAULT");
+    if (e && strncmp(e, "alloc:", 6) == 0) remaining = atoi(e + 6);
+  }
+  return remaining;
+}
+
+bool fault_hit() {
+  int r = fault_countdown();
+  if (r < 0) return false;
+  static int count = 0;
+  ++count;
+  return count == r;
+}
+
+}  // namespace
+
+struct fab_handle {
+  int n = 0, nnz = 0;
+  int* d_rowptr = nullptr;
+  int* d_colind = nullptr;
+  double* d_vals = nullptr;
+  int64_t ld = 0;
+  // workspace
+  Buf W, H, sigma, wn2, coef, part, counter, gpart, skpart, SV, P, qr, tau, y, cvec, dense, piv, scal, lsq, u, xbuf,
+      state;
+  // cached SRHT sample
+  int64_t P_npad = -1;
+  int P_s = -1;
+  uint64_t P_seed = 0;
+  // last solve
+  int has_state = 0, last_m = 0, last_s = 0, last_sketched = 0;
+};
+
+extern "C" {
+
+void fab_params_default(fab_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->f = FAB_F_EXP;
+  p->t = 1.0;
+  p->m = 30;
+  p->k = 2;
+  p->s = 120;
+  p->zeta = 8;
+  p->sketch = FAB_SK_SPARSE_SIGN;
+  p->seed = 1;
+  p->method = FAB_SKETCHED_FAST;
+  p->precision = FAB_FP64;
+  p->lsqr_tol = 1e-6;
+  p->lsqr_maxit = 0;
+  p->stream = nullptr;
+}
+
+const char* fab_strerror(int code) {
+  switch (code) {
+    case FAB_OK: return "ok";
+    case FAB_EINVAL: return "invalid argument";
+    case FAB_ENOMEM: return "device allocation failed";
+    case FAB_ECUDA: return "CUDA error";
+    case FAB_ENUMERIC: return "non-finite value or no principal square root";
+    case FAB_ETIMEOUT: return "bounded wait expired";
+    case FAB_ENOTCONV: return "iteration limit reached";
+    default: return "unknown error";
+  }
+}
+
+int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colind,
+               const double* vals, int inputs_on_device) {
+  if (!out) return FAB_EINVAL;
+  *out = nullptr;
+  if (n < 1 || n >= (int64_t)1 << 31 || nnz < 0 || nnz >= (int64_t)1 << 31 || !rowptr || (nnz > 0 && (!colind || !vals)))
+    return FAB_EINVAL;
+  std::vector<int64_t> rp(n + 1);
+  std::vector<int32_t> ci(nnz);
+  std::vector<double> va(nnz);
+  if (inputs_on_device) {
+    if (cudaMemcpy(rp.data(), rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (nnz > 0 && cudaMemcpy(ci.data(), colind, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (nnz > 0 && cudaMemcpy(va.data(), vals, nnz * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)) {
+      cudaGetLastError();
+      return FAB_ECUDA;
+    }
+  } else {
+    memcpy(rp.data(), rowptr, (n + 1) * sizeof(int64_t));
+    if (nnz > 0) {
+      memcpy(ci.data(), colind, nnz * sizeof(int32_t));
+      memcpy(va.data(), vals, nnz * sizeof(double));
+    }
+  }
+  if (rp[0] != 0 || rp[n] != nnz) return FAB_EINVAL;
+  for (int64_t i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i]) return FAB_EINVAL;
+  for (int64_t e = 0; e < nnz; ++e)
+    if (ci[e] < 0 || ci[e] >= n) return FAB_EINVAL;
+  std::vector<int> rp32(n + 1);
+  for (int64_t i = 0; i <= n; ++i) rp32[i] = (int)rp[i];
+  fab_handle* h = new fab_handle();
+  h->n = (int)n;
+  h->nnz = (int)nnz;
+  h->ld = ((n + 31) / 32) * 32;
+  if (fault_hit() || cudaMalloc(&h->d_rowptr, (n + 1) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->d_colind, std::max<int64_t>(nnz, 1) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->d_vals, std::max<int64_t>(nnz, 1) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    fab_destroy(h);
+    return FAB_ENOMEM;
+  }
+  if (cudaMemcpy(h->d_rowptr, rp32.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (nnz > 0 && cudaMemcpy(h->d_colind, ci.data(), nnz * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (nnz > 0 && cudaMemcpy(h->d_vals, va.data(), nnz * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)) {
+    cudaGetLastError();
+    fab_destroy(h);
+    return FAB_ECUDA;
+  }
+  *out = h;
+  return FAB_OK;
+}
+
+void fab_destroy(fab_handle* h) {
+  if (!h) return;
+  cudaFree(h->d_rowptr);
+  cudaFree(h->d_colind);
+  cudaFree(h->d_vals);
+  Buf* bufs[] = {&h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
+                 &h->skpart, &h->SV, &h->P,     &h->qr,  &h->tau,  &h->y,    &h->cvec,    &h->dense,
+                 &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state};
+  for (Buf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  cudaGetLastError();
+  delete h;
+}
+
+}  // extern "C"
+
+namespace {
+
+#define CK(call)                              \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) {                  \
+      cudaGetLastError();                     \
+      return FAB_ECUDA;                       \
+    }                                         \
+  } while (0)
+
+bool sketched(int method) { return method == FAB_SKETCHED_FAST || method == FAB_SKETCHED_LS; }
+
+int64_t next_pow2(int64_t n) {
+  int64_t p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+int validate(const fab_handle* h, const fab_params* p) {
+  if (p->f < 0 || p->f > 2) return FAB_EINVAL;
+  if (p->method < 0 || p->method > 3) return FAB_EINVAL;
+  if (p->m < 1 || p->m > kMaxM) return FAB_EINVAL;
+  if (p->precision != FAB_FP64) return FAB_EINVAL;
+  if (p->method != FAB_ARNOLDI && (p->k < 1 || p->k > kMaxWindow)) return FAB_EINVAL;
+  if (p->f == FAB_F_EXP && !isfinite(p->t)) return FAB_EINVAL;
+  if (sketched(p->method)) {
+    if (p->s < p->m + 1 || p->s > kMaxS) return FAB_EINVAL;
+    if (p->sketch == FAB_SK_SPARSE_SIGN) {
+      if (p->zeta < 1 || p->zeta > kMaxZeta || p->zeta > p->s) return FAB_EINVAL;
+    } else if (p->sketch == FAB_SK_SRHT) {
+      if (p->s > next_pow2(h->n)) return FAB_EINVAL;
+    } else {
+      return FAB_EINVAL;
+    }
+    if (p->method == FAB_SKETCHED_LS && !(p->lsqr_tol > 0.0)) return FAB_EINVAL;
+  }
+  return FAB_OK;
+}
+
+struct Ws {
+  double *W, *H, *sigma, *wn2, *coef, *part, *gpart, *skpart, *SV, *qr, *tau, *y, *cvec, *scal, *u, *xbuf;
+  double* mats[9];
+  double *lv_v, *lv_w, *lv_x, *lv_z, *lv_coef, *lv_q, *unorm2, *one;
+  unsigned* counter;
+  int *P, *piv;
+  DevState* st;
+};
+
+int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
+  const int m = p->m, s = sketched(p->method) ? p->s : 1;
+  const int n = h->n;
+  const size_t ld = (size_t)h->ld;
+  const int ntiles = (n + kTileRows - 1) / kTileRows;
+  const int nchunks = (n + kChunk - 1) / kChunk;
+  const size_t part_blocks = (size_t)sm_count() * kMaxPartBlocks;
+  struct Need {
+    Buf* b;
+    size_t bytes;
+  } need[] = {
+      {&h->W, ld * (m + 1) * 8},
+      {&h->H, (size_t)(m + 1) * m * 8},
+      {&h->sigma, (size_t)(m + 1) * 8},
+      {&h->wn2, (size_t)(m + 1) * 8},
+      {&h->coef, (size_t)(m + 1) * 8},
+      {&h->part, part_blocks * (kMaxWindow + 1) * 8},
+      {&h->counter, 64},
+      {&h->gpart, (size_t)ntiles * (m + 1) * 8},
+      {&h->skpart, (size_t)nchunks * s * 8},
+      {&h->SV, (size_t)s * (m + 1) * 8},
+      {&h->P, (size_t)s * 4},
+      {&h->qr, (size_t)s * (m + 1) * 8},
+      {&h->tau, (size_t)(m + 1) * 8},
+      {&h->y, (size_t)(m + 1) * 8},
+      {&h->cvec, (size_t)(m + 1) * 8},
+      {&h->dense, (size_t)9 * m * m * 8},
+      {&h->piv, (size_t)(m + 1) * 4},
+      {&h->scal, 64 * 8},
+      {&h->lsq, (size_t)6 * (m + 1) * 8},
+      {&h->state, sizeof(DevState)},
+  };
+  for (auto& q : need) {
+    const bool grow = q.b->bytes < (q.bytes ? q.bytes : 16);
+    if (grow && fault_hit()) return FAB_ENOMEM;
+    if (!ensure(*q.b, q.bytes)) return FAB_ENOMEM;
+    if (grow && q.b == &h->counter) CK(cudaMemset(h->counter.p, 0, h->counter.bytes));
+  }
+  if (p->method == FAB_SKETCHED_LS) {
+    if ((h->u.bytes < (size_t)n * 8 && fault_hit()) || !ensure(h->u, (size_t)n * 8)) return FAB_ENOMEM;
+  }
+  ws.W = ptr<double>(h->W);
+  ws.H = ptr<double>(h->H);
+  ws.sigma = ptr<double>(h->sigma);
+  ws.wn2 = ptr<double>(h->wn2);
+  ws.coef = ptr<double>(h->coef);
+  ws.part = ptr<double>(h->part);
+  ws.gpart = ptr<double>(h->gpart);
+  ws.skpart = ptr<double>(h->skpart);
+  ws.SV = ptr<double>(h->SV);
+  ws.qr = ptr<double>(h->qr);
+  ws.tau = ptr<double>(h->tau);
+  ws.y = ptr<double>(h->y);
+  ws.cvec = ptr<double>(h->cvec);
+  ws.scal = ptr<double>(h->scal);
+  ws.u = ptr<double>(h->u);
+  for (int i = 0; i < 9; ++i) ws.mats[i] = ptr<double>(h->dense) + (size_t)i * m * m;
+  double* l = ptr<double>(h->lsq);
+  ws.lv_v = l;
+  ws.lv_w = l + (m + 1);
+  ws.lv_x = l + 2 * (m + 1);
+  ws.lv_z = l + 3 * (m + 1);
+  ws.lv_coef = l + 4 * (m + 1);
+  ws.lv_q = l + 5 * (m + 1);
+  ws.unorm2 = ws.scal + 8;
+  ws.one = ws.scal + 9;
+  ws.counter = ptr<unsigned>(h->counter);
+  ws.P = ptr<int>(h->P);
+  ws.piv = ptr<int>(h->piv);
+  ws.st = ptr<DevState>(h->state);
+  return FAB_OK;
+}
+
+// exp(M) e_1 into c by Pade [13/13] scaling and squaring; M (ld m) is overwritten.
+int expm_e1(Ws& ws, int m, const int* mdev, double* c, int* squarings, cudaStream_t s) {
+  static const Pade13 pd;
+  const double* b = pd.b;
+  double *M = ws.mats[0], *A2 = ws.mats[1], *A4 = ws.mats[2], *A6 = ws.mats[3], *T = ws.mats[4], *U = ws.mats[5],
+         *V = ws.mats[6], *X = ws.mats[7], *X2 = ws.mats[8];
+  CK(launch_norm1(M, m, mdev, ws.scal + 10, s));
+  double nrm = 0.0;
+  CK(cudaMemcpyAsync(&nrm, ws.scal + 10, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!isfinite(nrm)) return FAB_ENUMERIC;
+  int sq = 0;
+  if (nrm > kTheta13) sq = (int)ceil(log2(nrm / kTheta13));
+  if (sq > 0) CK(launch_lincomb(M, M, nullptr, nullptr, nullptr, ldexp(1.0, -sq), 0, 0, 0, 0.0, m, mdev, m, s));
+  CK(launch_gemm(A2, M, M, m, mdev, m, 1.0, 0.0, s));
+  CK(launch_gemm(A4, A2, A2, m, mdev, m, 1.0, 0.0, s));
+  CK(launch_gemm(A6, A4, A2, m, mdev, m, 1.0, 0.0, s));
+  // U = M [A6 (b13 A6 + b11 A4 + b9 A2) + b7 A6 + b5 A4 + b3 A2 + b1 I]
+  CK(launch_lincomb(T, A6, A4, A2, nullptr, b[13], b[11], b[9], 0, 0.0, m, mdev, m, s));
+  CK(launch_gemm(X, A6, T, m, mdev, m, 1.0, 0.0, s));
+  CK(launch_lincomb(X, X, A6, A4, A2, 1.0, b[7], b[5], b[3], b[1], m, mdev, m, s));
+  CK(launch_gemm(U, M, X, m, mdev, m, 1.0, 0.0, s));
+  // V = A6 (b12 A6 + b10 A4 + b8 A2) + b6 A6 + b4 A4 + b2 A2 + b0 I
+  CK(launch_lincomb(T, A6, A4, A2, nullptr, b[12], b[10], b[8], 0, 0.0, m, mdev, m, s));
+  CK(launch_gemm(V, A6, T, m, mdev, m, 1.0, 0.0, s));
+  CK(launch_lincomb(V, V, A6, A4, A2, 1.0, b[6], b[4], b[2], b[0], m, mdev, m, s));
+  // (V - U) X = (V + U)
+  CK(launch_lincomb(T, V, U, nullptr, nullptr, 1.0, -1.0, 0, 0, 0.0, m, mdev, m, s));
+  CK(launch_lincomb(X, V, U, nullptr, nullptr, 1.0, 1.0, 0, 0, 0.0, m, mdev, m, s));
+  CK(launch_lu(T, m, mdev, ws.piv, ws.scal + 11, ws.st, s));
+  CK(launch_lu_solve(T, m, ws.piv, mdev, m, X, m, 0, s));
+  for (int i = 0; i < sq; ++i) {
+    CK(launch_gemm(X2, X, X, m, mdev, m, 1.0, 0.0, s));
+    std::swap(X, X2);
+  }
+  CK(cudaMemcpyAsync(c, X, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (squarings) *squarings = sq;
+  return FAB_OK;
+}
+
+// f(M) e_1 for f = sqrt (want_sqrt) or inverse sqrt by the scaled product-form
+// Denman-Beavers iteration; M (ld m) is overwritten.
+int sqrtm_e1(Ws& ws, int m, const int* mdev, double* c, int want_sqrt, int* iters, cudaStream_t s) {
+  double *M = ws.mats[0], *T = ws.mats[1], *Minv = ws.mats[2];
+  CK(launch_first_column(want_sqrt ? M : nullptr, mdev, c, s));
+  const int maxit = 100;
+  double err = INFINITY;
+  int extra = -1;
+  for (int it = 0; it < maxit; ++it) {
+    CK(cudaMemcpyAsync(T, M, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(launch_lu(T, m, mdev, ws.piv, ws.scal + 11, ws.st, s));
+    CK(launch_lu_solve(T, m, ws.piv, mdev, m, Minv, m, 1, s));
+    CK(launch_db_update(M, Minv, m, mdev, c, ws.scal + 11, err > 1e-2 ? 1 : 0, ws.st, s));
+    DevState hs;
+    CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs.status != FAB_OK) return hs.status;
+    err = hs.scal[1];
+    if (iters) *iters = it + 1;
+    if (extra >= 0) return FAB_OK;
+    if (err <= 1e-13 * sqrt((double)m)) extra = 0;  // one more step after convergence
+  }
+  return FAB_ENOTCONV;
+}
+
+}  // namespace
+
+extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, double* x, int bx_on_device,
+                         fab_stats* stats) {
+  if (!h || !p || !b || !x) return FAB_EINVAL;
+  int rc = validate(h, p);
+  if (rc != FAB_OK) return rc;
+  Ws ws;
+  rc = ensure_ws(h, p, ws);
+  if (rc != FAB_OK) return rc;
+  cudaStream_t s = (cudaStream_t)p->stream;
+  const int n = h->n, m = p->m, k = p->k;
+  const int64_t ld = h->ld;
+  const int ldh = m + 1;
+  const bool sk_on = sketched(p->method);
+  const int* mdev = &ws.st->m_used;
+  Csr A{h->n, h->nnz, h->d_rowptr, h->d_colind, h->d_vals};
+  h->has_state = 0;
+
+  cudaEvent_t ev[4];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+    }
+  } guard{ev};
+
+  CK(cudaEventRecord(ev[0], s));
+  CK(launch_state_reset(ws.st, m, s));
+  CK(cudaMemsetAsync(ws.H, 0, (size_t)ldh * m * sizeof(double), s));
+  CK(cudaMemsetAsync(ws.y, 0, (size_t)(m + 1) * sizeof(double), s));
+  CK(cudaMemcpyAsync(ws.W, b, (size_t)n * sizeof(double), cudaMemcpyDefault, s));
+
+  SketchDev sk;
+  memset(&sk, 0, sizeof(sk));
+  sk.kind = SK_NONE;
+  double sk_scale = 1.0;
+  if (sk_on) {
+    sk.kind = p->sketch == FAB_SK_SRHT ? SK_SRHT : SK_SPARSE;
+    sk.s = p->s;
+    sk.zeta = p->zeta;
+    sk.chunk_log2 = kChunkLog2;
+    sk.nchunks = (n + kChunk - 1) / kChunk;
+    sk.st_rows = rng_state(p->seed, 1);
+    sk.st_signs = rng_state(p->seed, 2);
+    sk.st_D = rng_state(p->seed, 3);
+    sk.P = ws.P;
+    sk.part = ws.skpart;
+    if (sk.kind == SK_SRHT) {
+      const int64_t npad = next_pow2(n);
+      if (h->P_npad != npad || h->P_s != p->s || h->P_seed != p->seed) {
+        CK(launch_srht_sample(npad, p->s, rng_state(p->seed, 4), ws.P, s));
+        h->P_npad = npad;
+        h->P_s = p->s;
+        h->P_seed = p->seed;
+      }
+      sk_scale = 1.0 / sqrt((double)p->s);
+    } else {
+      sk_scale = 1.0 / sqrt((double)p->zeta);
+    }
+  }
+  SketchDev none;
+  memset(&none, 0, sizeof(none));
+  none.kind = SK_NONE;
+
+  // start vector: ||b||, sigma_0, sketch of b
+  CK(launch_update(n, ws.W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, 1 | 2, ws.part, ws.counter,
+                   sk_on ? sk : none, ws.st, s));
+  if (sk_on) CK(launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
+
+  const int ntiles = (n + kTileRows - 1) / kTileRows;
+  for (int c = 1; c <= m; ++c) {
+    if (p->method == FAB_ARNOLDI) {
+      CK(launch_spmv_dots(A, ws.W, ld, c, 0, 0, ws.sigma, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
+      double* Hcol = ws.H + (size_t)ldh * (c - 1);
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        CK(launch_gemv_t(n, ws.W, ld, 0, c, ws.W + (size_t)c * ld, ws.gpart, ntiles, ws.st, s));
+        CK(launch_reduce_cols(ws.gpart, ntiles, c, ws.sigma, 0, Hcol, pass, ws.coef, 1.0, ws.st, s));
+        CK(launch_update(n, ws.W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, pass == 1 ? 1 : 0, ws.part,
+                         ws.counter, none, ws.st, s));
+      }
+    } else {
+      const int j0 = std::max(0, c - k), kw = c - j0;
+      CK(launch_spmv_dots(A, ws.W, ld, c, j0, kw, ws.sigma, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
+                          s));
+      CK(launch_update(n, ws.W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, 1, ws.part, ws.counter,
+                       sk_on ? sk : none, ws.st, s));
+      if (sk_on) CK(launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
+    }
+  }
+  CK(cudaEventRecord(ev[1], s));
+  DevState hs;
+  CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hs.status != FAB_OK) return hs.status;
+  const int mu = hs.m_used;
+  h->last_m = m;
+  h->last_s = sk_on ? p->s : 0;
+  h->last_sketched = sk_on ? 1 : 0;
+  int lsqr_iters = 0, fh_iters = 0;
+  if (mu == 0) {  // b = 0
+    CK(cudaMemsetAsync(ws.cvec, 0, (size_t)m * sizeof(double), s));
+    if (bx_on_device) {
+      CK(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), s));
+    } else {
+      memset(x, 0, (size_t)n * sizeof(double));
+    }
+    CK(cudaStreamSynchronize(s));
+    h->has_state = 1;
+    if (stats) {
+      memset(stats, 0, sizeof(*stats));
+    }
+    return FAB_OK;
+  }
+  const bool breakdown = mu < m;
+  const double* yptr = nullptr;
+  if (!breakdown && p->method == FAB_SKETCHED_FAST) {
+    // y = argmin || Theta V_m z - Theta v_{m+1} || (sketch-and-solve form of eq. sFOM)
+    CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * (mu + 1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(launch_householder_qr(ws.qr, p->s, p->s, mdev, 1, ws.tau, s));
+    CK(launch_trsv(ws.qr, p->s, mdev, ws.qr + (size_t)mu * p->s, ws.y, 0, nullptr, s));
+    yptr = ws.y;
+  } else if (!breakdown && p->method == FAB_SKETCHED_LS) {
+    // Blendenpik: R from the QR of Theta V_m; LSQR on V_m R^{-1} u ~ v_{m+1}; y = R^{-1} u
+    CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * mu * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(launch_householder_qr(ws.qr, p->s, p->s, mdev, 0, ws.tau, s));
+    const double one = 1.0;
+    CK(cudaMemcpyAsync(ws.one, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(launch_lsqr_u(n, ws.W + (size_t)mu * ld, ld, 1, ws.one, ws.u, 1, ws.part, ws.counter, ws.unorm2, ws.st, s));
+    CK(launch_gemv_t(n, ws.W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
+    CK(launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, ws.lv_q, 0, nullptr, 1.0, ws.st, s));
+    LsqrVecs lv{ws.lv_v, ws.lv_w, ws.lv_x, ws.lv_z, ws.lv_coef, ws.lv_q};
+    CK(launch_lsqr_start(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, p->lsqr_tol, ws.st, s));
+    const int maxit = p->lsqr_maxit > 0 ? p->lsqr_maxit : 4 * mu;
+    bool converged = false;
+    for (int it = 0; it < maxit; ++it) {
+      CK(launch_lsqr_u(n, ws.W, ld, mu, ws.lv_coef, ws.u, 0, ws.part, ws.counter, ws.unorm2, ws.st, s));
+      CK(launch_gemv_t(n, ws.W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
+      CK(launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, ws.lv_q, 0, nullptr, 1.0, ws.st, s));
+      CK(launch_lsqr_step(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, ws.st, s));
+      CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (hs.status != FAB_OK) return hs.status;
+      if (hs.flag) {
+        converged = true;
+        break;
+      }
+    }
+    lsqr_iters = hs.iters;
+    if (!converged) return FAB_ENOTCONV;
+    CK(launch_trsv(ws.qr, p->s, mdev, ws.lv_x, ws.y, 0, nullptr, s));
+    yptr = ws.y;
+  }
+  // f(H_m + h y e_m^T) e_1
+  if (p->f == FAB_F_EXP) {
+    CK(launch_build_hhat(ws.H, ldh, mdev, yptr, p->t, ws.mats[0], m, m, s));
+    rc = expm_e1(ws, m, mdev, ws.cvec, &fh_iters, s);
+  } else {
+    CK(launch_build_hhat(ws.H, ldh, mdev, yptr, 1.0, ws.mats[0], m, m, s));
+    rc = sqrtm_e1(ws, m, mdev, ws.cvec, p->f == FAB_F_SQRT, &fh_iters, s);
+  }
+  if (rc != FAB_OK) return rc;
+  CK(cudaEventRecord(ev[2], s));
+  // x = ||b|| V_m c
+  CK(launch_prep_coef(ws.cvec, ws.sigma, mdev, ws.st, ws.coef, s));
+  double* xdst = x;
+  if (!bx_on_device) {
+    if ((h->xbuf.bytes < (size_t)n * 8 && fault_hit()) || !ensure(h->xbuf, (size_t)n * 8)) return FAB_ENOMEM;
+    xdst = ptr<double>(h->xbuf);
+  }
+  CK(launch_combine(n, ws.W, ld, mu, ws.coef, xdst, 0.0, s));
+  CK(cudaEventRecord(ev[3], s));
+  if (!bx_on_device) CK(cudaMemcpyAsync(x, xdst, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hs.status != FAB_OK) return hs.status;
+  h->has_state = 1;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->m_used = mu;
+    stats->lsqr_iters = lsqr_iters;
+    stats->fh_iters = fh_iters;
+    stats->beta = hs.beta;
+    double hl = 0.0;
+    if (mu == m) CK(cudaMemcpy(&hl, ws.H + m + (size_t)ldh * (m - 1), sizeof(double), cudaMemcpyDeviceToHost));
+    stats->h_last = hl;
+    float t01 = 0, t12 = 0, t23 = 0, t03 = 0;
+    cudaEventElapsedTime(&t01, ev[0], ev[1]);
+    cudaEventElapsedTime(&t12, ev[1], ev[2]);
+    cudaEventElapsedTime(&t23, ev[2], ev[3]);
+    cudaEventElapsedTime(&t03, ev[0], ev[3]);
+    stats->ms_basis = t01;
+    stats->ms_small = t12;
+    stats->ms_combine = t23;
+    stats->ms_total = t03;
+  }
+  return FAB_OK;
+}
+
+extern "C" int fab_last_state(fab_handle* h, double* H, double* SV, double* y, double* coeffs) {
+  if (!h || !h->has_state) return FAB_EINVAL;
+  const int m = h->last_m;
+  if (H && cudaMemcpy(H, h->H.p, (size_t)(m + 1) * m * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return FAB_ECUDA;
+  if (SV && h->last_sketched &&
+      cudaMemcpy(SV, h->SV.p, (size_t)h->last_s * (m + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FAB_ECUDA;
+  if (y && cudaMemcpy(y, h->y.p, (size_t)m * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return FAB_ECUDA;
+  if (coeffs && cudaMemcpy(coeffs, h->cvec.p, (size_t)m * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return FAB_ECUDA;
+  return FAB_OK;
+}
+
+extern "C" int fab_last_basis(fab_handle* h, double* V, int dst_on_device) {
+  if (!h || !h->has_state || !V) return FAB_EINVAL;
+  const int m = h->last_m, n = h->n;
+  double* dst = V;
+  void* tmp = nullptr;
+  if (!dst_on_device) {
+    if (cudaMalloc(&tmp, (size_t)n * (m + 1) * 8) != cudaSuccess) {
+      cudaGetLastError();
+      return FAB_ENOMEM;
+    }
+    dst = (double*)tmp;
+  }
+  int rc = FAB_OK;
+  if (launch_scale_columns(n, ptr<double>(h->W), h->ld, m + 1, ptr<double>(h->sigma), dst, n, 0) != cudaSuccess)
+    rc = FAB_ECUDA;
+  if (rc == FAB_OK && !dst_on_device &&
+      cudaMemcpy(V, dst, (size_t)n * (m + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = FAB_ECUDA;
+  if (rc == FAB_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FAB_ECUDA;
+  if (tmp) cudaFree(tmp);
+  cudaGetLastError();
+  return rc;
+}
+
+extern "C" int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t seed, const double* V_dev,
+                                int64_t ldv, int ncols, double* out_dev, void* stream) {
+  if (n < 1 || n >= (int64_t)1 << 31 || s < 1 || s > kMaxS || ncols < 0 || ldv < n || !V_dev || !out_dev)
+    return FAB_EINVAL;
+  if (sketch == FAB_SK_SPARSE_SIGN) {
+    if (zeta < 1 || zeta > kMaxZeta || zeta > s) return FAB_EINVAL;
+  } else if (sketch == FAB_SK_SRHT) {
+    if (s > next_pow2(n)) return FAB_EINVAL;
+  } else {
+    return FAB_EINVAL;
+  }
+  if (ncols == 0) return FAB_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nchunks = (int)((n + kChunk - 1) / kChunk);
+  double* part = nullptr;
+  int* P = nullptr;
+  DevState* ds = nullptr;
+  if (cudaMallocAsync((void**)&part, (size_t)nchunks * s * 8, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&P, (size_t)s * 4, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&ds, sizeof(DevState), st) != cudaSuccess) {
+    cudaGetLastError();
+    if (part) cudaFreeAsync(part, st);
+    if (P) cudaFreeAsync(P, st);
+    cudaStreamSynchronize(st);
+    return FAB_ENOMEM;
+  }
+  int rc = FAB_OK;
+  SketchDev sk;
+  memset(&sk, 0, sizeof(sk));
+  sk.kind = sketch == FAB_SK_SRHT ? SK_SRHT : SK_SPARSE;
+  sk.s = s;
+  sk.zeta = zeta;
+  sk.chunk_log2 = kChunkLog2;
+  sk.nchunks = nchunks;
+  sk.st_rows = rng_state(seed, 1);
+  sk.st_signs = rng_state(seed, 2);
+  sk.st_D = rng_state(seed, 3);
+  sk.P = P;
+  sk.part = part;
+  const double scale = sk.kind == SK_SRHT ? 1.0 / sqrt((double)s) : 1.0 / sqrt((double)zeta);
+  if (launch_state_reset(ds, 0, st) != cudaSuccess) rc = FAB_ECUDA;
+  if (rc == FAB_OK && sk.kind == SK_SRHT && launch_srht_sample(next_pow2(n), s, rng_state(seed, 4), P, st) != cudaSuccess)
+    rc = FAB_ECUDA;
+  for (int j = 0; j < ncols && rc == FAB_OK; ++j) {
+    if (launch_update((int)n, const_cast<double*>(V_dev), ldv, j, 0, 0, nullptr, nullptr, 1, nullptr, nullptr, 0,
+                      nullptr, nullptr, sk, ds, st) != cudaSuccess ||
+        launch_sketch_reduce(sk, nullptr, 0, scale, out_dev + (size_t)j * s, ds, st) != cudaSuccess)
+      rc = FAB_ECUDA;
+  }
+  cudaFreeAsync(part, st);
+  cudaFreeAsync(P, st);
+  cudaFreeAsync(ds, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) rc = FAB_ECUDA;
+  cudaGetLastError();
+  return rc;
+}

@@ -1,0 +1,173 @@
+// Internal declarations shared by the libfab translation units (device helpers,
+// device-side solve state, kernel launchers). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fab.h"
+
+namespace fab {
+
+constexpr int kThreads = 256;        // threads per block of the streaming kernels
+constexpr int kChunkLog2 = 12;       // rows per sketch chunk: 4096 (one int64 transform block)
+constexpr int kChunk = 1 << kChunkLog2;
+constexpr int kRowsPerThread = kChunk / kThreads;  // 16
+constexpr int kMaxWindow = 8;        // k of Alg. 2
+constexpr int kMaxM = 1024;          // Krylov dimension limit
+constexpr int kMaxS = 4096;          // sketch rows limit
+constexpr int kMaxZeta = 16;         // sparse-sign nonzeros per column limit
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+enum SketchKind { SK_NONE = -1, SK_SPARSE = 0, SK_SRHT = 1 };
+
+// Device-side state of one solve. Written only by kernels (reset by k_state_reset).
+struct DevState {
+  int m_used;    // basis dimension (m until a breakdown)
+  int stop;      // set once the basis loop must not continue (breakdown or error)
+  int status;    // FAB_OK or the device-detected error
+  int flag;      // iteration-loop flag (LSQR / square-root iteration converged)
+  int iters;     // iteration count reported by the loops
+  int pad;
+  double beta;   // ||b||_2
+  double scal[16];  // scalars of the small-stage loops (LSQR recurrence, DB scaling)
+};
+
+// Sketch description passed by value to the basis kernels.
+struct SketchDev {
+  int kind;            // SketchKind
+  int s;               // rows of Theta
+  int zeta;            // sparse sign: nonzeros per column
+  int chunk_log2;      // log2 of the rows per transform chunk (<= kChunkLog2)
+  int nchunks;         // ceil(n / chunk)
+  int pad;
+  uint64_t st_rows;    // SplitMix64 stream states (see fab_rng_state)
+  uint64_t st_signs;
+  uint64_t st_D;
+  const int* P;        // SRHT sampled rows (device, s entries, sorted)
+  double* part;        // nchunks x s chunk partials (chunk-major)
+};
+
+// ----------------------------------------------------------------- SplitMix64
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// Initial state of stream `stream` for `seed`: mix64(seed + stream * gamma).
+__host__ __device__ __forceinline__ uint64_t rng_state(uint64_t seed, uint64_t stream) {
+  return mix64(seed + stream * kGamma);
+}
+// idx-th output (0-based) of the generator whose state starts at `state`.
+__host__ __device__ __forceinline__ uint64_t rng_u(uint64_t state, uint64_t idx) {
+  return mix64(state + (idx + 1) * kGamma);
+}
+
+// ------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of NV values per thread; result valid in thread 0 (out[0..NV)).
+// Fixed combination order (deterministic for a given launch shape).
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* >= 32*NV */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[warp * NV + q] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double a = 0.0;
+      for (int w = 0; w < nw; ++w) a += sh[w * NV + q];
+      v[q] = a;
+    }
+  }
+  __syncthreads();
+}
+
+// Last-block-done: returns true in every thread of the block that finished last.
+// Partials written before the call are visible to that block afterwards.
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(counter, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// Sum of `nv` columns of a row-major nblocks x nv partial array, by one block,
+// in a fixed order. out[q] (shared) receives column q. nv <= 32.
+__device__ __forceinline__ void sum_partials(const double* part, int nblocks, int nv, double* out,
+                                             double* sh /* blockDim.x doubles */) {
+  for (int q = 0; q < nv; ++q) {
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) a += __ldcg(part + (size_t)b * nv + q);
+    a = warp_sum(a);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+      out[q] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// 2^e as a double for e in [-1074, 1023], without FP64 arithmetic on the value.
+__device__ __forceinline__ double pow2_split(int e, double* second) {
+  // returns a and sets *second = b with a*b = 2^e and both normal doubles
+  int e1 = e / 2, e2 = e - e1;
+  *second = __longlong_as_double((long long)(e2 + 1023) << 52);
+  return __longlong_as_double((long long)(e1 + 1023) << 52);
+}
+
+// ----------------------------------------------------------------- launchers
+// (defined in basis.cu / small.cu; all take the stream last and return cudaError_t)
+struct Csr {
+  int n;
+  int nnz;
+  const int* rowptr;
+  const int* colind;
+  const double* vals;
+};
+
+cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s);
+cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0, int kw, const double* sigma,
+                             double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
+                             DevState* st, cudaStream_t s);
+cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
+                          int ldh, double* sigma, const double* wn2, int mode, double* part, unsigned* counter,
+                          const SketchDev& sk, DevState* st, cudaStream_t s);
+cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
+                                 DevState* st, cudaStream_t s);
+cudaError_t launch_srht_sample(int64_t npad, int s, uint64_t stP, int* P, cudaStream_t st);
+cudaError_t launch_gemv_t(int n, const double* W, int64_t ld, int j0, int nc, const double* x, double* part,
+                          int ntiles, DevState* st, cudaStream_t s);
+cudaError_t launch_reduce_cols(const double* part, int ntiles, int nc, const double* sigma, int j0,
+                               double* Hcol, int h_accumulate, double* coef, double coef_scale_extra,
+                               DevState* st, cudaStream_t s);
+cudaError_t launch_combine(int n, const double* W, int64_t ld, int nc, const double* coef, double* out,
+                           double keep, cudaStream_t s);
+cudaError_t launch_scale_columns(int n, const double* W, int64_t ld, int nc, const double* sigma, double* dst,
+                                 int64_t ldd, cudaStream_t s);
+
+int sm_count();              // multiprocessors of the current device
+int grid_rows(int n);        // grid for the thread-per-row kernels
+constexpr int kMaxPartBlocks = 64;  // partial buffers hold sm_count() * kMaxPartBlocks blocks
+constexpr int kTileRows = 2048;     // rows per GEMV-T tile
+
+}  // namespace fab

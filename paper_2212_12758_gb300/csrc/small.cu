@@ -1,0 +1,628 @@
+// Small dense FP64 kernels of libfab: the m x m / s x m work after the basis
+// loop. Householder QR of the sketch Theta V_m (the R factor of Blendenpik and
+// of eq. sFOM), triangular solves, the projected matrix H_m + h y e_m^T
+// (eq. relationxx), dense products and LU for f(H) (Pade scaling and squaring
+// for exp, product-form Denman-Beavers for the square root), and the scalar
+// recurrence of LSQR. Matrix sizes are read from the device (m_used), so a
+// breakdown of the basis needs no host round trip.
+#include <float.h>
+#include <math.h>
+
+#include "fab_internal.cuh"
+#include "small.cuh"
+
+namespace fab {
+
+// ------------------------------------------------------------ Householder QR
+// In place on A (rows x (mu + extra), column-major): R in the upper triangle,
+// reflector vectors below it (implicit leading 1), tau[j]. The reflectors are
+// also applied to the `extra` trailing columns (right-hand sides), which then
+// hold Q^T rhs. Reflector j: beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta,
+// v = x / (alpha - beta).
+__global__ __launch_bounds__(1024) void k_householder_qr(double* __restrict__ A, int lda, int rows,
+                                                          const int* __restrict__ mdev, int extra,
+                                                          double* __restrict__ tau) {
+  __shared__ double red[32];
+  __shared__ double s_beta, s_tau, s_vinv;
+  const int mu = *mdev;
+  const int ncols = mu + extra;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < mu && j < rows; ++j) {
+    double* aj = A + (size_t)j * lda;
+    double ss = 0.0;
+    for (int i = j + 1 + tid; i < rows; i += blockDim.x) ss = fma(aj[i], aj[i], ss);
+    ss = warp_sum(ss);
+    if (lane == 0) red[warp] = ss;
+    __syncthreads();
+    if (tid == 0) {
+      double sig = 0.0;
+      for (int w = 0; w < nw; ++w) sig += red[w];
+      const double alpha = aj[j];
+      if (sig == 0.0) {
+        s_tau = 0.0;
+        s_beta = alpha;
+        s_vinv = 0.0;
+      } else {
+        const double nrm = sqrt(fma(alpha, alpha, sig));
+        const double beta = (alpha <= 0.0) ? nrm : -nrm;
+        s_tau = (beta - alpha) / beta;
+        s_vinv = 1.0 / (alpha - beta);
+        s_beta = beta;
+      }
+    }
+    __syncthreads();
+    const double tj = s_tau, vinv = s_vinv;
+    for (int i = j + 1 + tid; i < rows; i += blockDim.x) aj[i] *= vinv;
+    __syncthreads();
+    for (int col = j + 1 + warp; col < ncols; col += nw) {
+      double* ac = A + (size_t)col * lda;
+      double d = (lane == 0) ? ac[j] : 0.0;
+      for (int i = j + 1 + lane; i < rows; i += 32) d = fma(aj[i], ac[i], d);
+      d = warp_sum(d) * tj;
+      if (lane == 0) ac[j] -= d;
+      for (int i = j + 1 + lane; i < rows; i += 32) ac[i] = fma(-d, aj[i], ac[i]);
+    }
+    if (tid == 0) {
+      tau[j] = tj;
+      aj[j] = s_beta;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_householder_qr(double* A, int lda, int rows, const int* mdev, int extra, double* tau,
+                                  cudaStream_t s) {
+  k_householder_qr<<<1, 1024, 0, s>>>(A, lda, rows, mdev, extra, tau);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------- triangular solves
+// x <- R^{-1} x (trans = 0) or R^{-T} x (trans = 1), R = upper triangle of the
+// leading mu x mu block of R (ld ldr). Optional pre-scale of x by *pre (device).
+__global__ __launch_bounds__(1024) void k_trsv(const double* __restrict__ R, int ldr, const int* __restrict__ mdev,
+                                                const double* __restrict__ xin, double* __restrict__ xout, int trans,
+                                                const double* __restrict__ pre) {
+  __shared__ double xs[kMaxM];
+  const int mu = *mdev;
+  const double p = pre ? *pre : 1.0;
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) xs[i] = p * xin[i];
+  __syncthreads();
+  if (!trans) {
+    for (int j = mu - 1; j >= 0; --j) {
+      if (threadIdx.x == 0) xs[j] /= R[j + (size_t)j * ldr];
+      __syncthreads();
+      const double xj = xs[j];
+      for (int i = threadIdx.x; i < j; i += blockDim.x) xs[i] = fma(-R[i + (size_t)j * ldr], xj, xs[i]);
+      __syncthreads();
+    }
+  } else {
+    for (int j = 0; j < mu; ++j) {
+      if (threadIdx.x == 0) xs[j] /= R[j + (size_t)j * ldr];
+      __syncthreads();
+      const double xj = xs[j];
+      for (int i = j + 1 + threadIdx.x; i < mu; i += blockDim.x) xs[i] = fma(-R[j + (size_t)i * ldr], xj, xs[i]);
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) xout[i] = xs[i];
+}
+
+cudaError_t launch_trsv(const double* R, int ldr, const int* mdev, const double* xin, double* xout, int trans,
+                        const double* pre, cudaStream_t s) {
+  k_trsv<<<1, 256, 0, s>>>(R, ldr, mdev, xin, xout, trans, pre);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ projected matrix
+// M = scale * (H_mu + h_{mu+1,mu} y e_mu^T), H column-major with ld ldh. y may be NULL.
+__global__ void k_build_hhat(const double* __restrict__ H, int ldh, const int* __restrict__ mdev,
+                             const double* __restrict__ y, double scale, double* __restrict__ M, int ldm) {
+  const int mu = *mdev;
+  const double hl = (y && mu > 0) ? H[mu + (size_t)ldh * (mu - 1)] : 0.0;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < mu * mu; idx += gridDim.x * blockDim.x) {
+    const int i = idx % mu, j = idx / mu;
+    double v = H[i + (size_t)ldh * j];
+    if (y && j == mu - 1) v = fma(hl, y[i], v);
+    M[i + (size_t)ldm * j] = scale * v;
+  }
+}
+
+cudaError_t launch_build_hhat(const double* H, int ldh, const int* mdev, const double* y, double scale, double* M,
+                              int ldm, int mmax, cudaStream_t s) {
+  const int grid = (mmax * mmax + 255) / 256;
+  k_build_hhat<<<grid < 1 ? 1 : (grid > 1024 ? 1024 : grid), 256, 0, s>>>(H, ldh, mdev, y, scale, M, ldm);
+  return cudaGetLastError();
+}
+
+// ||M||_1 (maximum absolute column sum) into *out.
+__global__ void k_norm1(const double* __restrict__ M, int ldm, const int* __restrict__ mdev, double* out) {
+  __shared__ double red[32];
+  const int mu = *mdev;
+  double best = 0.0;
+  for (int j = threadIdx.x; j < mu; j += blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i < mu; ++i) a += fabs(M[i + (size_t)ldm * j]);
+    best = fmax(best, a);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, red[w]);
+    *out = b;
+  }
+}
+
+cudaError_t launch_norm1(const double* M, int ldm, const int* mdev, double* out, cudaStream_t s) {
+  k_norm1<<<1, 1024, 0, s>>>(M, ldm, mdev, out);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------- dense products
+// C = alpha A B + beta C (mu x mu, common ld); C must not alias A or B.
+__global__ void k_gemm(double* __restrict__ C, const double* __restrict__ A, const double* __restrict__ B, int ld,
+                       const int* __restrict__ mdev, double alpha, double beta) {
+  const int mu = *mdev;
+  const int i = blockIdx.x * 16 + threadIdx.x, j = blockIdx.y * 16 + threadIdx.y;
+  if (i >= mu || j >= mu) return;
+  double a0 = 0.0, a1 = 0.0;
+  int l = 0;
+  for (; l + 1 < mu; l += 2) {
+    a0 = fma(A[i + (size_t)ld * l], B[l + (size_t)ld * j], a0);
+    a1 = fma(A[i + (size_t)ld * (l + 1)], B[l + 1 + (size_t)ld * j], a1);
+  }
+  if (l < mu) a0 = fma(A[i + (size_t)ld * l], B[l + (size_t)ld * j], a0);
+  const double acc = a0 + a1;
+  C[i + (size_t)ld * j] = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * C[i + (size_t)ld * j]);
+}
+
+cudaError_t launch_gemm(double* C, const double* A, const double* B, int ld, const int* mdev, int mmax, double alpha,
+                        double beta, cudaStream_t s) {
+  dim3 grid((mmax + 15) / 16, (mmax + 15) / 16), block(16, 16);
+  k_gemm<<<grid, block, 0, s>>>(C, A, B, ld, mdev, alpha, beta);
+  return cudaGetLastError();
+}
+
+// out = a0 X0 + a1 X1 + a2 X2 + a3 X3 + d I (any X may be NULL; out may alias one X)
+__global__ void k_lincomb(double* out, const double* X0, const double* X1, const double* X2, const double* X3,
+                          double a0, double a1, double a2, double a3, double d, int ld, const int* __restrict__ mdev) {
+  const int mu = *mdev;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < mu * mu; idx += gridDim.x * blockDim.x) {
+    const int i = idx % mu, j = idx / mu;
+    const size_t o = i + (size_t)ld * j;
+    double v = (i == j) ? d : 0.0;
+    if (X0) v = fma(a0, X0[o], v);
+    if (X1) v = fma(a1, X1[o], v);
+    if (X2) v = fma(a2, X2[o], v);
+    if (X3) v = fma(a3, X3[o], v);
+    out[o] = v;
+  }
+}
+
+cudaError_t launch_lincomb(double* out, const double* X0, const double* X1, const double* X2, const double* X3,
+                           double a0, double a1, double a2, double a3, double d, int ld, const int* mdev, int mmax,
+                           cudaStream_t s) {
+  int grid = (mmax * mmax + 255) / 256;
+  grid = grid < 1 ? 1 : (grid > 1024 ? 1024 : grid);
+  k_lincomb<<<grid, 256, 0, s>>>(out, X0, X1, X2, X3, a0, a1, a2, a3, d, ld, mdev);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- LU
+// In-place LU with partial pivoting (rows swapped across the whole matrix,
+// ties to the smallest row index). piv[k] = row swapped with k. Writes
+// log|det| to *logdet and flags a zero pivot in st->status (FAB_ENUMERIC).
+__global__ __launch_bounds__(1024) void k_lu(double* __restrict__ M, int ld, const int* __restrict__ mdev,
+                                              int* __restrict__ piv, double* __restrict__ logdet, DevState* st) {
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  __shared__ int s_p;
+  __shared__ double s_logdet;
+  const int mu = *mdev;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) s_logdet = 0.0;
+  for (int k = 0; k < mu; ++k) {
+    double best = -1.0;
+    int bi = mu;
+    for (int i = k + tid; i < mu; i += blockDim.x) {
+      const double a = fabs(M[i + (size_t)ld * k]);
+      if (a > best) {
+        best = a;
+        bi = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      rv[warp] = best;
+      ri[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double b = -1.0;
+      int p = mu;
+      for (int w = 0; w < nw; ++w)
+        if (rv[w] > b || (rv[w] == b && ri[w] < p)) {
+          b = rv[w];
+          p = ri[w];
+        }
+      s_p = p;
+      piv[k] = p;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != k) {
+      for (int j = tid; j < mu; j += blockDim.x) {
+        const double t = M[k + (size_t)ld * j];
+        M[k + (size_t)ld * j] = M[p + (size_t)ld * j];
+        M[p + (size_t)ld * j] = t;
+      }
+    }
+    __syncthreads();
+    const double pivot = M[k + (size_t)ld * k];
+    if (tid == 0) {
+      if (pivot == 0.0 || !isfinite(pivot)) {
+        st->status = FAB_ENUMERIC;
+      } else {
+        s_logdet += log(fabs(pivot));
+      }
+    }
+    const double pinv = (pivot != 0.0) ? 1.0 / pivot : 0.0;
+    for (int i = k + 1 + tid; i < mu; i += blockDim.x) M[i + (size_t)ld * k] *= pinv;
+    __syncthreads();
+    const int r = mu - k - 1;
+    for (int idx = tid; idx < r * r; idx += blockDim.x) {
+      const int i = k + 1 + idx % r, j = k + 1 + idx / r;
+      M[i + (size_t)ld * j] = fma(-M[i + (size_t)ld * k], M[k + (size_t)ld * j], M[i + (size_t)ld * j]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && logdet) *logdet = s_logdet;
+}
+
+cudaError_t launch_lu(double* M, int ld, const int* mdev, int* piv, double* logdet, DevState* st, cudaStream_t s) {
+  k_lu<<<1, 1024, 0, s>>>(M, ld, mdev, piv, logdet, st);
+  return cudaGetLastError();
+}
+
+// Solve LU X = P B in place for nrhs columns of B (one warp per column,
+// column-oriented substitution). identity_rhs: B is set to I first.
+__global__ void k_lu_solve(const double* __restrict__ LU, int ld, const int* __restrict__ piv,
+                           const int* __restrict__ mdev, double* __restrict__ B, int ldb, int identity_rhs) {
+  extern __shared__ double sb[];
+  const int mu = *mdev;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  const int col = blockIdx.x * wpb + warp;
+  if (col >= mu) return;
+  double* b = sb + (size_t)warp * mu;
+  double* bg = B + (size_t)ldb * col;
+  for (int i = lane; i < mu; i += 32) b[i] = identity_rhs ? (i == col ? 1.0 : 0.0) : bg[i];
+  __syncwarp();
+  if (lane == 0) {
+    for (int k = 0; k < mu; ++k) {
+      const int p = piv[k];
+      if (p != k) {
+        const double t = b[k];
+        b[k] = b[p];
+        b[p] = t;
+      }
+    }
+  }
+  __syncwarp();
+  for (int k = 0; k < mu; ++k) {  // unit lower
+    const double bk = b[k];
+    for (int i = k + 1 + lane; i < mu; i += 32) b[i] = fma(-LU[i + (size_t)ld * k], bk, b[i]);
+    __syncwarp();
+  }
+  for (int k = mu - 1; k >= 0; --k) {  // upper
+    if (lane == 0) b[k] /= LU[k + (size_t)ld * k];
+    __syncwarp();
+    const double bk = b[k];
+    for (int i = lane; i < k; i += 32) b[i] = fma(-LU[i + (size_t)ld * k], bk, b[i]);
+    __syncwarp();
+  }
+  for (int i = lane; i < mu; i += 32) bg[i] = b[i];
+}
+
+cudaError_t launch_lu_solve(const double* LU, int ld, const int* piv, const int* mdev, int mmax, double* B, int ldb,
+                            int identity_rhs, cudaStream_t s) {
+  const int wpb = 4;
+  const int grid = (mmax + wpb - 1) / wpb;
+  k_lu_solve<<<grid, wpb * 32, (size_t)wpb * mmax * sizeof(double), s>>>(LU, ld, piv, mdev, B, ldb, identity_rhs);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------- Denman-Beavers step
+// Product form with determinant scaling (mu_k = |det M_k|^{-1/(2 m)}):
+//   M <- (I + (mu^2 M + mu^-2 Minv) / 2) / 2,   y <- mu (y + mu^-2 Minv y) / 2,
+// with M_0 = Y_0 = H (y_0 = H e_1 for the square root, e_1 for the inverse
+// square root with Z_0 = I). Writes ||M - I||_F to st->scal[1].
+__global__ __launch_bounds__(1024) void k_db_update(double* __restrict__ M, const double* __restrict__ Minv, int ld,
+                                                     const int* __restrict__ mdev, double* __restrict__ y,
+                                                     const double* __restrict__ logdet, int scale_on, DevState* st) {
+  __shared__ double ys[kMaxM];
+  __shared__ double red[32];
+  const int mu = *mdev;
+  const double g = scale_on ? exp(-(*logdet) / (2.0 * mu)) : 1.0;
+  const double g2 = g * g, gi2 = 1.0 / g2;
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) ys[i] = y[i];
+  __syncthreads();
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) {
+    double a = 0.0;
+    for (int j = 0; j < mu; ++j) a = fma(Minv[i + (size_t)ld * j], ys[j], a);
+    y[i] = 0.5 * g * fma(gi2, a, ys[i]);
+  }
+  double err = 0.0;
+  for (int idx = threadIdx.x; idx < mu * mu; idx += blockDim.x) {
+    const int i = idx % mu, j = idx / mu;
+    const size_t o = i + (size_t)ld * j;
+    const double v = 0.5 * ((i == j ? 1.0 : 0.0) + 0.5 * fma(g2, M[o], gi2 * Minv[o]));
+    M[o] = v;
+    const double dv = v - (i == j ? 1.0 : 0.0);
+    err = fma(dv, dv, err);
+  }
+  err = warp_sum(err);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = err;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double e = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) e += red[w];
+    st->scal[1] = sqrt(e);
+    if (!isfinite(e)) st->status = FAB_ENUMERIC;
+  }
+}
+
+cudaError_t launch_db_update(double* M, const double* Minv, int ld, const int* mdev, double* y, const double* logdet,
+                             int scale_on, DevState* st, cudaStream_t s) {
+  k_db_update<<<1, 1024, 0, s>>>(M, Minv, ld, mdev, y, logdet, scale_on, st);
+  return cudaGetLastError();
+}
+
+// Copy column 0 of M (or e_1 when M is NULL) into y.
+__global__ void k_first_column(const double* __restrict__ M, const int* __restrict__ mdev, double* __restrict__ y) {
+  const int mu = *mdev;
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) y[i] = M ? M[i] : (i == 0 ? 1.0 : 0.0);
+}
+
+cudaError_t launch_first_column(const double* M, const int* mdev, double* y, cudaStream_t s) {
+  k_first_column<<<1, 1024, 0, s>>>(M, mdev, y);
+  return cudaGetLastError();
+}
+
+// coef_j = ||b|| c_j sigma_j for the combine x = sum_j coef_j W_j.
+__global__ void k_prep_coef(const double* __restrict__ c, const double* __restrict__ sigma,
+                            const int* __restrict__ mdev, const DevState* st, double* __restrict__ coef) {
+  const int mu = *mdev;
+  for (int j = threadIdx.x; j < mu; j += blockDim.x) coef[j] = st->beta * c[j] * sigma[j];
+}
+
+cudaError_t launch_prep_coef(const double* c, const double* sigma, const int* mdev, const DevState* st, double* coef,
+                             cudaStream_t s) {
+  k_prep_coef<<<1, 1024, 0, s>>>(c, sigma, mdev, st, coef);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ LSQR
+// State in st->scal: 0 alpha, 1 beta, 2 phibar, 3 rhobar, 4 anorm2, 5 tau
+// (u = tau * ustore), 6 keep (= -alpha * tau, the factor of ustore in the next
+// u update), 7 tol. m-vectors in lv: v, w, x, z (= R^{-1} v), coef (= sigma z).
+// Paige-Saunders recurrences, in the order of their published algorithm.
+
+__device__ void lsqr_block_norm(const double* a, int mu, double* red, double* out) {
+  double ss = 0.0;
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) ss = fma(a[i], a[i], ss);
+  ss = warp_sum(ss);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out = sqrt(t);
+  }
+  __syncthreads();
+}
+
+// Back substitution z = R^{-1} v in shared memory (block-wide).
+__device__ void lsqr_trsv(const double* R, int ldr, int mu, double* zs) {
+  for (int j = mu - 1; j >= 0; --j) {
+    if (threadIdx.x == 0) zs[j] /= R[j + (size_t)j * ldr];
+    __syncthreads();
+    const double zj = zs[j];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) zs[i] = fma(-R[i + (size_t)j * ldr], zj, zs[i]);
+    __syncthreads();
+  }
+}
+
+// Start: beta_1 from ||ustore|| (u_1 = v_{m+1} = sigma_mu ustore), then
+// v = R^{-T} V_m^T u_1, alpha, w = v, phibar = beta_1, rhobar = alpha, x = 0.
+__global__ __launch_bounds__(1024) void k_lsqr_start(const double* __restrict__ R, int ldr,
+                                                      const int* __restrict__ mdev, const double* __restrict__ sigma,
+                                                      const double* __restrict__ unorm2, LsqrVecs lv, double tol,
+                                                      DevState* st) {
+  __shared__ double vs[kMaxM];
+  __shared__ double red[32];
+  __shared__ double s_nrm;
+  const int mu = *mdev;
+  const double beta1 = sigma[mu] * sqrt(*unorm2);
+  const double tau = (beta1 > 0.0) ? sigma[mu] / beta1 : 0.0;
+  // v = R^{-T} (tau q)
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) vs[i] = tau * lv.q[i];
+  __syncthreads();
+  for (int j = 0; j < mu; ++j) {
+    if (threadIdx.x == 0) vs[j] /= R[j + (size_t)j * ldr];
+    __syncthreads();
+    const double vj = vs[j];
+    for (int i = j + 1 + threadIdx.x; i < mu; i += blockDim.x) vs[i] = fma(-R[j + (size_t)i * ldr], vj, vs[i]);
+    __syncthreads();
+  }
+  lsqr_block_norm(vs, mu, red, &s_nrm);
+  const double alpha = s_nrm;
+  const double ainv = alpha > 0.0 ? 1.0 / alpha : 0.0;
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) {
+    const double vi = vs[i] * ainv;
+    vs[i] = vi;
+    lv.v[i] = vi;
+    lv.w[i] = vi;
+    lv.x[i] = 0.0;
+  }
+  __syncthreads();
+  lsqr_trsv(R, ldr, mu, vs);  // z = R^{-1} v
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) {
+    lv.z[i] = vs[i];
+    lv.coef[i] = sigma[i] * vs[i];
+  }
+  if (threadIdx.x == 0) {
+    st->scal[0] = alpha;
+    st->scal[1] = beta1;
+    st->scal[2] = beta1;
+    st->scal[3] = alpha;
+    st->scal[4] = 0.0;
+    st->scal[5] = tau;
+    st->scal[6] = -alpha * tau;
+    st->scal[7] = tol;
+    st->iters = 0;
+    st->flag = (beta1 == 0.0 || alpha == 0.0) ? 1 : 0;
+  }
+}
+
+cudaError_t launch_lsqr_start(const double* R, int ldr, const int* mdev, const double* sigma, const double* unorm2,
+                              const LsqrVecs& lv, double tol, DevState* st, cudaStream_t s) {
+  k_lsqr_start<<<1, 1024, 0, s>>>(R, ldr, mdev, sigma, unorm2, lv, tol, st);
+  return cudaGetLastError();
+}
+
+// After ustore <- V_m z - alpha u (unnormalized) with ||ustore||^2 in *unorm2 and
+// q_j = sigma_j <W_j, ustore>:
+//   beta = ||ustore||, anorm2 += alpha^2 + beta^2, u = ustore / beta,
+//   v <- R^{-T} (q / beta) - beta v, alpha = ||v||, v /= alpha,
+//   rotation, x += (phi/rho) w, w = v - (theta/rho) w, stopping test,
+//   z = R^{-1} v, coef = sigma z, keep = -alpha / beta.
+__global__ __launch_bounds__(1024) void k_lsqr_step(const double* __restrict__ R, int ldr,
+                                                     const int* __restrict__ mdev, const double* __restrict__ sigma,
+                                                     const double* __restrict__ unorm2, LsqrVecs lv, DevState* st) {
+  __shared__ double vs[kMaxM];
+  __shared__ double red[32];
+  __shared__ double s_nrm;
+  if (st->flag) return;
+  const int mu = *mdev;
+  double alpha = st->scal[0];
+  const double beta = sqrt(*unorm2);
+  const double anorm2 = st->scal[4] + alpha * alpha + beta * beta;
+  double alpha_new = alpha;
+  if (beta > 0.0) {
+    const double binv = 1.0 / beta;
+    for (int i = threadIdx.x; i < mu; i += blockDim.x) vs[i] = lv.q[i] * binv;
+    __syncthreads();
+    for (int j = 0; j < mu; ++j) {
+      if (threadIdx.x == 0) vs[j] /= R[j + (size_t)j * ldr];
+      __syncthreads();
+      const double vj = vs[j];
+      for (int i = j + 1 + threadIdx.x; i < mu; i += blockDim.x) vs[i] = fma(-R[j + (size_t)i * ldr], vj, vs[i]);
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < mu; i += blockDim.x) vs[i] = fma(-beta, lv.v[i], vs[i]);
+    __syncthreads();
+    lsqr_block_norm(vs, mu, red, &s_nrm);
+    alpha_new = s_nrm;
+    if (alpha_new > 0.0) {
+      const double ainv = 1.0 / alpha_new;
+      for (int i = threadIdx.x; i < mu; i += blockDim.x) vs[i] *= ainv;
+    }
+    __syncthreads();
+  } else {
+    for (int i = threadIdx.x; i < mu; i += blockDim.x) vs[i] = lv.v[i];
+    __syncthreads();
+  }
+  const double rhobar = st->scal[3], phibar = st->scal[2];
+  const double rho = hypot(rhobar, beta);
+  const double c = rhobar / rho, sn = beta / rho;
+  const double theta = sn * alpha_new;
+  const double rhobar_new = -c * alpha_new;
+  const double phi = c * phibar;
+  const double phibar_new = sn * phibar;
+  const double f1 = phi / rho, f2 = theta / rho;
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) {
+    const double wi = lv.w[i];
+    lv.x[i] = fma(f1, wi, lv.x[i]);
+    lv.w[i] = fma(-f2, wi, vs[i]);
+    lv.v[i] = vs[i];
+  }
+  __syncthreads();
+  lsqr_trsv(R, ldr, mu, vs);
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) {
+    lv.z[i] = vs[i];
+    lv.coef[i] = sigma[i] * vs[i];
+  }
+  if (threadIdx.x == 0) {
+    const double tol = st->scal[7];
+    st->scal[0] = alpha_new;
+    st->scal[1] = beta;
+    st->scal[2] = phibar_new;
+    st->scal[3] = rhobar_new;
+    st->scal[4] = anorm2;
+    st->scal[5] = beta > 0.0 ? 1.0 / beta : 0.0;
+    st->scal[6] = beta > 0.0 ? -alpha_new / beta : 0.0;
+    st->iters += 1;
+    const bool done = (phibar_new * alpha_new * fabs(c) <= tol * sqrt(anorm2) * phibar_new) || beta == 0.0 ||
+                      alpha_new == 0.0;
+    if (done) st->flag = 1;
+    if (!isfinite(anorm2) || !isfinite(phibar_new)) {
+      st->status = FAB_ENUMERIC;
+      st->flag = 1;
+    }
+  }
+}
+
+cudaError_t launch_lsqr_step(const double* R, int ldr, const int* mdev, const double* sigma, const double* unorm2,
+                             const LsqrVecs& lv, DevState* st, cudaStream_t s) {
+  k_lsqr_step<<<1, 1024, 0, s>>>(R, ldr, mdev, sigma, unorm2, lv, st);
+  return cudaGetLastError();
+}
+
+// ustore[r] <- sum_q coef_q W_q[r] + keep * ustore[r] with keep = st->scal[6]
+// (keep_zero: ustore is overwritten); ||ustore||^2 reduced over the grid into *unorm2.
+__global__ __launch_bounds__(kThreads) void k_lsqr_u(int n, const double* __restrict__ W, int64_t ld, int nc,
+                                                      const double* __restrict__ coef, double* __restrict__ u,
+                                                      int keep_zero, double* __restrict__ part,
+                                                      unsigned* __restrict__ counter, double* __restrict__ unorm2,
+                                                      const DevState* st) {
+  extern __shared__ double s_cf[];
+  __shared__ double sh[32];
+  __shared__ double tot[1];
+  if (st->flag) return;
+  const double keep = keep_zero ? 0.0 : st->scal[6];
+  for (int i = threadIdx.x; i < nc; i += kThreads) s_cf[i] = coef[i];
+  __syncthreads();
+  double nrm = 0.0;
+  for (int r = blockIdx.x * kThreads + threadIdx.x; r < n; r += gridDim.x * kThreads) {
+    double a = keep_zero ? 0.0 : keep * u[r];
+    for (int q = 0; q < nc; ++q) a = fma(s_cf[q], W[(size_t)q * ld + r], a);
+    u[r] = a;
+    nrm = fma(a, a, nrm);
+  }
+  double nv[1] = {nrm};
+  block_sum<1>(nv, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = nv[0];
+  if (!last_block(counter)) return;
+  sum_partials(part, gridDim.x, 1, tot, sh);
+  if (threadIdx.x == 0) {
+    *unorm2 = tot[0];
+    *counter = 0;
+  }
+}
+
+cudaError_t launch_lsqr_u(int n, const double* W, int64_t ld, int nc, const double* coef, double* u, int keep_zero,
+                          double* part, unsigned* counter, double* unorm2, const DevState* st, cudaStream_t s) {
+  k_lsqr_u<<<grid_rows(n), kThreads, (size_t)(nc > 0 ? nc : 1) * 8, s>>>(n, W, ld, nc, coef, u, keep_zero, part,
+                                                                          counter, unorm2, st);
+  return cudaGetLastError();
+}
+
+}  // namespace fab

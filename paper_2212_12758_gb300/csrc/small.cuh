@@ -1,0 +1,44 @@
+// Launchers of the small dense FP64 kernels (small.cu). Internal.
+#pragma once
+
+#include "fab_internal.cuh"
+
+namespace fab {
+
+struct LsqrVecs {
+  double* v;
+  double* w;
+  double* x;
+  double* z;
+  double* coef;
+  double* q;  // sigma_j <W_j, ustore> from the GEMV-T reduction
+};
+
+cudaError_t launch_householder_qr(double* A, int lda, int rows, const int* mdev, int extra, double* tau,
+                                  cudaStream_t s);
+cudaError_t launch_trsv(const double* R, int ldr, const int* mdev, const double* xin, double* xout, int trans,
+                        const double* pre, cudaStream_t s);
+cudaError_t launch_build_hhat(const double* H, int ldh, const int* mdev, const double* y, double scale, double* M,
+                              int ldm, int mmax, cudaStream_t s);
+cudaError_t launch_norm1(const double* M, int ldm, const int* mdev, double* out, cudaStream_t s);
+cudaError_t launch_gemm(double* C, const double* A, const double* B, int ld, const int* mdev, int mmax, double alpha,
+                        double beta, cudaStream_t s);
+cudaError_t launch_lincomb(double* out, const double* X0, const double* X1, const double* X2, const double* X3,
+                           double a0, double a1, double a2, double a3, double d, int ld, const int* mdev, int mmax,
+                           cudaStream_t s);
+cudaError_t launch_lu(double* M, int ld, const int* mdev, int* piv, double* logdet, DevState* st, cudaStream_t s);
+cudaError_t launch_lu_solve(const double* LU, int ld, const int* piv, const int* mdev, int mmax, double* B, int ldb,
+                            int identity_rhs, cudaStream_t s);
+cudaError_t launch_db_update(double* M, const double* Minv, int ld, const int* mdev, double* y, const double* logdet,
+                             int scale_on, DevState* st, cudaStream_t s);
+cudaError_t launch_first_column(const double* M, const int* mdev, double* y, cudaStream_t s);
+cudaError_t launch_prep_coef(const double* c, const double* sigma, const int* mdev, const DevState* st, double* coef,
+                             cudaStream_t s);
+cudaError_t launch_lsqr_start(const double* R, int ldr, const int* mdev, const double* sigma, const double* unorm2,
+                              const LsqrVecs& lv, double tol, DevState* st, cudaStream_t s);
+cudaError_t launch_lsqr_step(const double* R, int ldr, const int* mdev, const double* sigma, const double* unorm2,
+                             const LsqrVecs& lv, DevState* st, cudaStream_t s);
+cudaError_t launch_lsqr_u(int n, const double* W, int64_t ld, int nc, const double* coef, double* u, int keep_zero,
+                          double* part, unsigned* counter, double* unorm2, const DevState* st, cudaStream_t s);
+
+}  // namespace fab

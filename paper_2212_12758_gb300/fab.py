@@ -1,0 +1,189 @@
+"""ctypes binding of libfab (include/fab.h): argument marshalling only.
+
+Every step of a solve runs in the CUDA kernels of libfab.so. Device arrays are
+passed as torch CUDA tensors (data_ptr), host arrays as numpy arrays. There is
+no fallback: importing this module raises if the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libfab.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libfab.so is not built ({_LIB_PATH}); run __graft_entry__.build() first")
+lib = ctypes.CDLL(_LIB_PATH)
+
+FAB_OK, FAB_EINVAL, FAB_ENOMEM, FAB_ECUDA, FAB_ENUMERIC, FAB_ETIMEOUT, FAB_ENOTCONV = 0, -1, -2, -3, -4, -5, -6
+EXP, SQRT, INVSQRT = 0, 1, 2
+ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ = 0, 1, 2, 3
+SPARSE_SIGN, SRHT, GAUSSIAN = 0, 1, 2
+FP64, MIXED = 0, 1
+
+# Every symbol the header declares (checked against include/fab.h by the tests).
+SYMBOLS = ("fab_params_default", "fab_strerror", "fab_create", "fab_apply", "fab_destroy", "fab_last_state",
+           "fab_last_basis", "fab_sketch_apply")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("f", ctypes.c_int), ("t", ctypes.c_double), ("m", ctypes.c_int), ("k", ctypes.c_int),
+                ("s", ctypes.c_int), ("zeta", ctypes.c_int), ("sketch", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("method", ctypes.c_int), ("precision", ctypes.c_int), ("lsqr_tol", ctypes.c_double),
+                ("lsqr_maxit", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("m_used", ctypes.c_int), ("lsqr_iters", ctypes.c_int), ("fh_iters", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("h_last", ctypes.c_double), ("beta", ctypes.c_double),
+                ("ms_basis", ctypes.c_double), ("ms_small", ctypes.c_double), ("ms_combine", ctypes.c_double),
+                ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_vp, _i64, _i32, _u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
+lib.fab_params_default.argtypes = [ctypes.POINTER(Params)]
+lib.fab_params_default.restype = None
+lib.fab_strerror.argtypes = [_i32]
+lib.fab_strerror.restype = ctypes.c_char_p
+lib.fab_create.argtypes = [ctypes.POINTER(_vp), _i64, _i64, _vp, _vp, _vp, _i32]
+lib.fab_create.restype = _i32
+lib.fab_apply.argtypes = [_vp, ctypes.POINTER(Params), _vp, _vp, _i32, ctypes.POINTER(Stats)]
+lib.fab_apply.restype = _i32
+lib.fab_destroy.argtypes = [_vp]
+lib.fab_destroy.restype = None
+lib.fab_last_state.argtypes = [_vp, _vp, _vp, _vp, _vp]
+lib.fab_last_state.restype = _i32
+lib.fab_last_basis.argtypes = [_vp, _vp, _i32]
+lib.fab_last_basis.restype = _i32
+lib.fab_sketch_apply.argtypes = [_i32, _i64, _i32, _i32, _u64, _vp, _i64, _i32, _vp, _vp]
+lib.fab_sketch_apply.restype = _i32
+
+
+class FabError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {lib.fab_strerror(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(code: int, where: str):
+    if code != FAB_OK:
+        raise FabError(code, where)
+
+
+def _addr(a):
+    """Pointer of a numpy array (host) or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _on_device(a) -> int:
+    return 0 if isinstance(a, np.ndarray) else int(getattr(a, "is_cuda", False))
+
+
+def params(f=EXP, t=1.0, m=30, k=2, s=None, zeta=8, sketch=SPARSE_SIGN, seed=1, method=SKETCHED_FAST,
+           precision=FP64, lsqr_tol=1e-6, lsqr_maxit=0, stream=None) -> Params:
+    p = Params()
+    lib.fab_params_default(ctypes.byref(p))
+    p.f, p.t, p.m, p.k = int(f), float(t), int(m), int(k)
+    p.s = int(s if s is not None else 4 * m)
+    p.zeta, p.sketch, p.seed, p.method = int(zeta), int(sketch), int(seed), int(method)
+    p.precision, p.lsqr_tol, p.lsqr_maxit = int(precision), float(lsqr_tol), int(lsqr_maxit)
+    p.stream = stream
+    return p
+
+
+@dataclass
+class LastState:
+    H: np.ndarray
+    SV: np.ndarray | None
+    y: np.ndarray
+    coeffs: np.ndarray
+
+
+class Matrix:
+    """A handle owning a device copy of A (fab_create / fab_destroy)."""
+
+    def __init__(self, rowptr, colind, vals, n: int | None = None):
+        n = int(n if n is not None else len(rowptr) - 1)
+        on_dev = _on_device(rowptr)
+        if not on_dev:
+            rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+            colind = np.ascontiguousarray(colind, dtype=np.int32)
+            vals = np.ascontiguousarray(vals, dtype=np.float64)
+        nnz = int(rowptr[-1])
+        h = ctypes.c_void_p()
+        _check(lib.fab_create(ctypes.byref(h), n, nnz, _addr(rowptr), _addr(colind), _addr(vals), on_dev),
+               "fab_create")
+        self._h = h
+        self.n = n
+        self.nnz = nnz
+        self._last = None
+
+    @classmethod
+    def from_csr(cls, A):
+        return cls(A.rowptr, A.colind, A.vals, A.n)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.fab_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def apply(self, b, p: Params, x=None, stats: bool = False):
+        """x ~ f(A) b. b and x are both numpy (host) or both torch CUDA tensors."""
+        on_dev = _on_device(b)
+        if x is None:
+            if on_dev:
+                import torch
+
+                x = torch.empty_like(b)
+            else:
+                x = np.empty(self.n, dtype=np.float64)
+        if not on_dev:
+            b = np.ascontiguousarray(b, dtype=np.float64)
+        st = Stats()
+        _check(lib.fab_apply(self._h, ctypes.byref(p), _addr(b), _addr(x), on_dev, ctypes.byref(st)), "fab_apply")
+        self._last = (p.m, p.s, p.method in (SKETCHED_FAST, SKETCHED_LS))
+        return (x, st) if stats else x
+
+    def last_state(self) -> LastState:
+        m, s, sk = self._last
+        H = np.zeros((m, m + 1))  # column-major (m+1) x m read as row-major transpose
+        SV = np.zeros((m + 1, s)) if sk else None
+        y = np.zeros(m)
+        c = np.zeros(m)
+        _check(lib.fab_last_state(self._h, _addr(H), _addr(SV), _addr(y), _addr(c)), "fab_last_state")
+        return LastState(H=H.T.copy(), SV=None if SV is None else SV.T.copy(), y=y, coeffs=c)
+
+    def last_basis(self) -> np.ndarray:
+        m = self._last[0]
+        V = np.zeros((m + 1, self.n))
+        _check(lib.fab_last_basis(self._h, _addr(V), 0), "fab_last_basis")
+        return V.T.copy()
+
+
+def sketch_apply(V, s: int, sketch: int = SPARSE_SIGN, zeta: int = 8, seed: int = 1, out=None, stream=None):
+    """Theta V for a torch CUDA tensor V of shape (ncols, n) (each row one column
+    vector, contiguous); returns a (ncols, s) tensor."""
+    import torch
+
+    if not (V.is_cuda and V.dtype == torch.float64 and V.is_contiguous()):
+        raise ValueError("V must be a contiguous float64 CUDA tensor")
+    ncols, n = V.shape
+    if out is None:
+        out = torch.empty((ncols, s), dtype=torch.float64, device=V.device)
+    _check(lib.fab_sketch_apply(int(sketch), int(n), int(s), int(zeta), int(seed), V.data_ptr(), int(n), int(ncols),
+                                out.data_ptr(), stream), "fab_sketch_apply")
+    return out
