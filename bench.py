@@ -1,0 +1,367 @@
+"""Benchmark: randomized Krylov f(A)b solves on one GB300 (or N replicas).
+
+Workload (one "step" = one whole solve of the hot path): 3D convection-diffusion,
+7-point upwind finite differences on a 200^3 grid (n = 8,000,000, nnz = 55,760,000,
+CSR FP64), x = exp(-1e-3 A) b with b ~ N(0,1) (seed 0, normalized), Krylov dimension
+m = 100, truncation window k = 4, SRHT sketch with s = 400 rows, method sketched_fast
+(eq. sFOM, sketch-and-solve form), all arithmetic FP64. sketched_ls (Alg. 4) and full
+Arnoldi on the same inputs are timed beside it. Inputs are synthetic.
+
+Timed region: K solves on the device with A, b and x resident in HBM (CUDA events on
+the solving stream, synchronize + barrier on both sides, max over ranks). The inputs
+(A 0.7 GB, basis 6.5 GB per solve) are far larger than L2. e2e repeats the measurement
+through the C ABI with pinned host buffers (b copied in, x copied out inside the call).
+
+N > 1 (torchrun): every rank runs its own replica of the workload (no collective);
+value = all ranks' solves / the slowest rank's time ("scaling": "weak").
+
+--impl reference times the plain FP64 CPU oracle (oracle/) on this host's cores on a
+bounded sample of the same workload and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "f(A)b solves/s + HBM GB/s at rel err ≤1e-6, sketched vs Arnoldi; p99 latency"
+N_GRID, M, K_WIN, S_ROWS, T_EXP, SEED_B, SEED_SK = 200, 100, 4, 400, -1e-3, 0, 1
+WORKLOAD = ("3D convection-diffusion 200^3 upwind FD (n=8,000,000, nnz=55,760,000), x=exp(-1e-3 A) b, "
+            "m=100, k=4, SRHT s=400, sketched_fast, FP64")
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# FP64 FMA peak: the recipe's nominal GB300 FP64 rate (no measured FP64 figure is
+# provided by the pool's peak file).
+FP64_PEAK_GFLOPS_NOMINAL = 1250.0
+
+
+def algorithmic_cost(n: int, nnz: int, m: int, k: int, s: int):
+    """Algorithmic bytes and FP64 flops per launch of the basis kernels (FP64 path).
+
+    spmv_dots (step c, window kw <= k): A values + column indices (12 nnz), row
+      pointers (4 (n+1)), the gathered column v_{c-1} (8 n, counted once), the other
+      kw-1 window columns (8 n each), the write of w (8 n). Flops: 2 nnz (SpMV)
+      + 2 n kw (dots) + 2 n (||w||^2) + n (scale).
+    update (step c): read w and kw window columns, write the new column: 8 n (kw + 2);
+      flops 2 n kw + 2 n; the sketch partials add 8 s per 4096-row chunk.
+    """
+    kw = k
+    sp_bytes = 12 * nnz + 4 * (n + 1) + 8 * n * kw + 8 * n
+    sp_flops = 2 * nnz + 2 * n * kw + 3 * n
+    nch = (n + 4095) // 4096
+    up_bytes = 8 * n * (kw + 2) + 8 * s * nch
+    up_flops = 2 * n * kw + 2 * n
+    return {"spmv_dots": (sp_bytes, sp_flops), "update": (up_bytes, up_flops)}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fab_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group("nccl")
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def cpu_oracle_sample(A, b, budget_s: float = 15.0):
+    """Time the FP64 CPU oracle on a bounded sample of one solve of the workload:
+    the first steps of Alg. 2 (SpMV + window orthogonalization), the SRHT sketch of
+    those columns and the combine of those columns, extrapolated linearly to the
+    m = 100 steps of one solve (the small m x m terms are negligible at this n)."""
+    import oracle
+    from paper_2212_12758_gb300 import workloads as W
+
+    As = W.to_scipy(A)
+    th = oracle.sketch.SRHT_(A.n, S_ROWS, SEED_SK)
+    steps = 2
+    while True:
+        t0 = time.perf_counter()
+        B = oracle.krylov.nt_basis(As, b, steps, K_WIN)
+        _ = th.apply(B.V)
+        _ = B.V[:, :steps] @ np.ones(steps)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 2 or steps >= 16:
+            break
+        steps *= 2
+    per_step = dt / (steps + 1)
+    solve_s = per_step * (M + 1)
+    cores = len(os.sched_getaffinity(0))
+    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {steps} of {M} basis steps (Alg. 2 window k={K_WIN}, SRHT sketch, combine) of one "
+                      f"solve on the full n={A.n} matrix, {dt:.1f} s, extrapolated to {M} steps"}
+
+
+def run_reference(args):
+    dist, rank, ws = _dist()
+    if rank != 0:
+        return 0
+    from paper_2212_12758_gb300 import workloads as W
+
+    A = W.convdiff(3, N_GRID)
+    b = W.random_vector(A.n, SEED_B)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(A, b, budget_s=4.0)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample(A, b, budget_s=4.0))
+    wall = time.perf_counter() - t0
+    v = float(np.median([x["value"] for x in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "m": M, "k": K_WIN, "s": S_ROWS,
+                       "sketch": "srht", "method": "sketched_fast"},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fab", choices=["fab", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the sketched_ls / Arnoldi side measurements")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    dist, rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_2212_12758_gb300 import fab
+    from paper_2212_12758_gb300 import workloads as W
+
+    A = W.convdiff(3, N_GRID)
+    b = W.random_vector(A.n, SEED_B)
+    n, nnz = A.n, A.nnz
+    Mx = fab.Matrix.from_csr(A)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def P(method, m=M):
+        return fab.params(f=fab.EXP, t=T_EXP, m=m, k=K_WIN, s=S_ROWS, sketch=fab.SRHT, seed=SEED_SK, method=method,
+                          lsqr_tol=1e-6, stream=sp)
+
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.empty_like(bd)
+    p_fast = P(fab.SKETCHED_FAST)
+    for _ in range(args.warmup):
+        _, st = Mx.apply(bd, p_fast, x=xd, stats=True)
+    torch.cuda.synchronize()
+    launches_per_solve = st.launches
+
+    # ---------------------------------------------------------------- timed
+    clocks = ClockSampler(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fab.profile_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    for i in range(args.steps):
+        evs[i][0].record(stream)
+        Mx.apply(bd, p_fast, x=xd)
+        evs[i][1].record(stream)
+    t_all1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = fab.profile_query()
+    fab.profile_enable(False)
+    total_ms = t_all0.elapsed_time(t_all1)
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    lat = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
+    solves_per_s = ws * args.steps / (total_ms / 1000.0)
+    ms_per_step = total_ms / args.steps
+
+    # ------------------------------------------------------------ roofline
+    cost = algorithmic_cost(n, nnz, M, K_WIN, S_ROWS)
+    dom = max(("spmv_dots", "update"), key=lambda k_: prof[k_][0])
+    tot_ms, cnt = prof[dom]
+    avg_s = tot_ms / max(cnt, 1) / 1000.0
+    bytes_l, flops_l = cost[dom]
+    peaks = _peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_frac = bytes_l / avg_s / 1e9 / hbm_peak
+    alu_frac = flops_l / avg_s / 1e9 / FP64_PEAK_GFLOPS_NOMINAL
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": flops_l / avg_s / 1e9, "peak": FP64_PEAK_GFLOPS_NOMINAL,
+                "unit": "GFLOP/s (FP64)", "frac": alu_frac}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_l / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_frac}
+    roof.update({"kernel": dom, "traffic": None, "ms_per_launch": avg_s * 1000.0,
+                 "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
+                 "hbm_gbs_algorithmic": bytes_l / avg_s / 1e9, "hbm_frac_of_measured": hbm_frac,
+                 "fp64_gflops": flops_l / avg_s / 1e9, "fp64_frac_of_nominal": alu_frac})
+    kernel_share = {k_: {"ms": v[0], "launches": v[1], "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-9)}
+                    for k_, v in prof.items()}
+    # whole-solve algorithmic traffic (basis steps + combine)
+    solve_bytes = M * (cost["spmv_dots"][0] + cost["update"][0]) + 8 * n * M
+    hbm_gbs_solve = solve_bytes / (ms_per_step / 1000.0) / 1e9
+
+    # ------------------------------------------------------- accuracy (untimed)
+    x_fast = xd.clone()
+    extras = {}
+    ref_x = None
+    if not args.no_extras:
+        xr = torch.empty_like(bd)
+        Mx.apply(bd, P(fab.ARNOLDI, m=150), x=xr)
+        xr2 = torch.empty_like(bd)
+        Mx.apply(bd, P(fab.ARNOLDI, m=140), x=xr2)
+        ref_x = xr
+        ref_conv = float(torch.linalg.norm(xr - xr2) / torch.linalg.norm(xr))
+        extras["reference_solution"] = {"method": "arnoldi m=150 (FP64, this library)",
+                                        "rel_change_vs_m140": ref_conv}
+        for name, meth in (("arnoldi", fab.ARNOLDI), ("sketched_ls", fab.SKETCHED_LS), ("noproj", fab.NOPROJ)):
+            reps = 2 if meth == fab.ARNOLDI else 3
+            xo = torch.empty_like(bd)
+            Mx.apply(bd, P(meth), x=xo)  # warm
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                _, sto = Mx.apply(bd, P(meth), x=xo, stats=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            extras[name] = {"solves_per_s": 1000.0 / ms, "ms_per_solve": ms,
+                            "rel_err": float(torch.linalg.norm(xo - ref_x) / torch.linalg.norm(ref_x)),
+                            "lsqr_iters": sto.lsqr_iters}
+    rel_err = float(torch.linalg.norm(x_fast - ref_x) / torch.linalg.norm(ref_x)) if ref_x is not None else None
+
+    # ----------------------------------------------------------------- e2e
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        fab.lib.fab_apply(Mx._h, p_fast, bh.data_ptr(), xh.data_ptr(), 0, None)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc = fab.lib.fab_apply(Mx._h, p_fast, bh.data_ptr(), xh.data_ptr(), 0, None)
+        assert rc == 0, rc
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": ws / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(A, b)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "m": M, "k": K_WIN, "s": S_ROWS,
+                           "sketch": "srht", "method": "sketched_fast", "f": "exp(tA), t=-1e-3",
+                           "l2": "inputs larger than L2 (A 0.7 GB, basis 6.5 GB per solve)",
+                           "parallelism": f"replicas x{ws}"},
+                "hbm_gbs": hbm_gbs_solve, "rel_err": rel_err,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                "roofline": roof, "kernels": kernel_share, "gpu_launches": launches_per_solve * args.steps,
+                "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, **extras}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

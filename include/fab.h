@@ -83,7 +83,7 @@ typedef struct fab_stats {
   int m_used;           /* basis dimension actually used (< m after a breakdown) */
   int lsqr_iters;       /* LSQR iterations (FAB_SKETCHED_LS)                     */
   int fh_iters;         /* squarings (exp) or Denman-Beavers iterations           */
-  int reserved;
+  int launches;         /* kernel launches issued by this solve                  */
   double h_last;        /* h_{m+1,m}                                             */
   double beta;          /* ||b||_2                                               */
   double ms_basis;      /* device time of the basis (+ fused sketch) loop        */
@@ -161,6 +161,24 @@ int fab_last_basis(fab_handle* h, double* V, int dst_on_device);
  */
 int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t seed,
                      const double* V_dev, int64_t ldv, int ncols, double* out_dev, void* stream);
+
+/*
+ * Kernel-level device timing (measurement support, not needed for solving).
+ * fab_profile_enable(1) resets the accumulators and makes every later
+ * fab_apply record CUDA events, on the solve's stream, around each launch of
+ * the kernel classes below; fab_profile_enable(0) stops recording.
+ * fab_profile_query returns the accumulated device time (ms) and the number of
+ * launches of one class:
+ *   "spmv_dots"      SpMV fused with the window dot products (Alg. 2 lines 3-5)
+ *   "update"         window update + norm + fused sketch of the new vector
+ *   "sketch_reduce"  cross-chunk reduction of the sketch
+ *   "gemv_t"         V^T w passes (Arnoldi, LSQR)
+ *   "small"          QR / LSQR scalar steps / f(H) kernels
+ *   "combine"        x = ||b|| V_m c and the LSQR vector update
+ * Unknown names return FAB_EINVAL. Process-wide; not thread-safe.
+ */
+int fab_profile_enable(int on);
+int fab_profile_query(const char* name, double* total_ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

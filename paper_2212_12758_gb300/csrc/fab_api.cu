@@ -82,6 +82,45 @@ bool fault_hit() {
   return count == r;
 }
 
+// ------------------------------------------------------------ profiling
+enum ProfKind { PK_SPMV = 0, PK_UPDATE, PK_SKRED, PK_GEMVT, PK_SMALL, PK_COMBINE, PK_COUNT };
+const char* kProfNames[PK_COUNT] = {"spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine"};
+
+struct Profiler {
+  bool on = false;
+  double total_ms[PK_COUNT] = {0};
+  long long launches[PK_COUNT] = {0};
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> kinds;  // kind of each recorded (start, end) pair
+  size_t used = 0;         // events taken from the pool in the current solve
+  cudaEvent_t take() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin_solve() {
+    used = 0;
+    kinds.clear();
+  }
+  // Called after the solve's stream has been synchronized.
+  void end_solve() {
+    for (size_t i = 0; i + 1 < used && i / 2 < kinds.size(); i += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pool[i], pool[i + 1]) == cudaSuccess) {
+        total_ms[kinds[i / 2]] += ms;
+        launches[kinds[i / 2]] += 1;
+      }
+    }
+    cudaGetLastError();
+    used = 0;
+    kinds.clear();
+  }
+};
+Profiler g_prof;
+
 }  // namespace
 
 struct fab_handle {
@@ -213,6 +252,30 @@ namespace {
     }                                         \
   } while (0)
 
+// Enqueue one kernel launch of class `kind`: counted, and bracketed by profiling
+// events when profiling is on.
+#define LK(kind, call)                                            \
+  do {                                                            \
+    cudaEvent_t e0_ = nullptr, e1_ = nullptr;                     \
+    if (g_prof.on) {                                              \
+      e0_ = g_prof.take();                                        \
+      e1_ = g_prof.take();                                        \
+      if (e0_ && e1_) cudaEventRecord(e0_, s);                    \
+    }                                                             \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) {                                      \
+      cudaGetLastError();                                         \
+      return FAB_ECUDA;                                           \
+    }                                                             \
+    if (e0_ && e1_) {                                             \
+      cudaEventRecord(e1_, s);                                    \
+      g_prof.kinds.push_back(kind);                               \
+    }                                                             \
+    ++g_launches;                                                 \
+  } while (0)
+
+thread_local int g_launches = 0;
+
 bool sketched(int method) { return method == FAB_SKETCHED_FAST || method == FAB_SKETCHED_LS; }
 
 int64_t next_pow2(int64_t n) {
@@ -330,33 +393,33 @@ int expm_e1(Ws& ws, int m, const int* mdev, double* c, int* squarings, cudaStrea
   const double* b = pd.b;
   double *M = ws.mats[0], *A2 = ws.mats[1], *A4 = ws.mats[2], *A6 = ws.mats[3], *T = ws.mats[4], *U = ws.mats[5],
          *V = ws.mats[6], *X = ws.mats[7], *X2 = ws.mats[8];
-  CK(launch_norm1(M, m, mdev, ws.scal + 10, s));
+  LK(PK_SMALL, launch_norm1(M, m, mdev, ws.scal + 10, s));
   double nrm = 0.0;
   CK(cudaMemcpyAsync(&nrm, ws.scal + 10, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (!isfinite(nrm)) return FAB_ENUMERIC;
   int sq = 0;
   if (nrm > kTheta13) sq = (int)ceil(log2(nrm / kTheta13));
-  if (sq > 0) CK(launch_lincomb(M, M, nullptr, nullptr, nullptr, ldexp(1.0, -sq), 0, 0, 0, 0.0, m, mdev, m, s));
-  CK(launch_gemm(A2, M, M, m, mdev, m, 1.0, 0.0, s));
-  CK(launch_gemm(A4, A2, A2, m, mdev, m, 1.0, 0.0, s));
-  CK(launch_gemm(A6, A4, A2, m, mdev, m, 1.0, 0.0, s));
+  if (sq > 0) LK(PK_SMALL, launch_lincomb(M, M, nullptr, nullptr, nullptr, ldexp(1.0, -sq), 0, 0, 0, 0.0, m, mdev, m, s));
+  LK(PK_SMALL, launch_gemm(A2, M, M, m, mdev, m, 1.0, 0.0, s));
+  LK(PK_SMALL, launch_gemm(A4, A2, A2, m, mdev, m, 1.0, 0.0, s));
+  LK(PK_SMALL, launch_gemm(A6, A4, A2, m, mdev, m, 1.0, 0.0, s));
   // U = M [A6 (b13 A6 + b11 A4 + b9 A2) + b7 A6 + b5 A4 + b3 A2 + b1 I]
-  CK(launch_lincomb(T, A6, A4, A2, nullptr, b[13], b[11], b[9], 0, 0.0, m, mdev, m, s));
-  CK(launch_gemm(X, A6, T, m, mdev, m, 1.0, 0.0, s));
-  CK(launch_lincomb(X, X, A6, A4, A2, 1.0, b[7], b[5], b[3], b[1], m, mdev, m, s));
-  CK(launch_gemm(U, M, X, m, mdev, m, 1.0, 0.0, s));
+  LK(PK_SMALL, launch_lincomb(T, A6, A4, A2, nullptr, b[13], b[11], b[9], 0, 0.0, m, mdev, m, s));
+  LK(PK_SMALL, launch_gemm(X, A6, T, m, mdev, m, 1.0, 0.0, s));
+  LK(PK_SMALL, launch_lincomb(X, X, A6, A4, A2, 1.0, b[7], b[5], b[3], b[1], m, mdev, m, s));
+  LK(PK_SMALL, launch_gemm(U, M, X, m, mdev, m, 1.0, 0.0, s));
   // V = A6 (b12 A6 + b10 A4 + b8 A2) + b6 A6 + b4 A4 + b2 A2 + b0 I
-  CK(launch_lincomb(T, A6, A4, A2, nullptr, b[12], b[10], b[8], 0, 0.0, m, mdev, m, s));
-  CK(launch_gemm(V, A6, T, m, mdev, m, 1.0, 0.0, s));
-  CK(launch_lincomb(V, V, A6, A4, A2, 1.0, b[6], b[4], b[2], b[0], m, mdev, m, s));
+  LK(PK_SMALL, launch_lincomb(T, A6, A4, A2, nullptr, b[12], b[10], b[8], 0, 0.0, m, mdev, m, s));
+  LK(PK_SMALL, launch_gemm(V, A6, T, m, mdev, m, 1.0, 0.0, s));
+  LK(PK_SMALL, launch_lincomb(V, V, A6, A4, A2, 1.0, b[6], b[4], b[2], b[0], m, mdev, m, s));
   // (V - U) X = (V + U)
-  CK(launch_lincomb(T, V, U, nullptr, nullptr, 1.0, -1.0, 0, 0, 0.0, m, mdev, m, s));
-  CK(launch_lincomb(X, V, U, nullptr, nullptr, 1.0, 1.0, 0, 0, 0.0, m, mdev, m, s));
-  CK(launch_lu(T, m, mdev, ws.piv, ws.scal + 11, ws.st, s));
-  CK(launch_lu_solve(T, m, ws.piv, mdev, m, X, m, 0, s));
+  LK(PK_SMALL, launch_lincomb(T, V, U, nullptr, nullptr, 1.0, -1.0, 0, 0, 0.0, m, mdev, m, s));
+  LK(PK_SMALL, launch_lincomb(X, V, U, nullptr, nullptr, 1.0, 1.0, 0, 0, 0.0, m, mdev, m, s));
+  LK(PK_SMALL, launch_lu(T, m, mdev, ws.piv, ws.scal + 11, ws.st, s));
+  LK(PK_SMALL, launch_lu_solve(T, m, ws.piv, mdev, m, X, m, 0, s));
   for (int i = 0; i < sq; ++i) {
-    CK(launch_gemm(X2, X, X, m, mdev, m, 1.0, 0.0, s));
+    LK(PK_SMALL, launch_gemm(X2, X, X, m, mdev, m, 1.0, 0.0, s));
     std::swap(X, X2);
   }
   CK(cudaMemcpyAsync(c, X, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -368,15 +431,15 @@ int expm_e1(Ws& ws, int m, const int* mdev, double* c, int* squarings, cudaStrea
 // Denman-Beavers iteration; M (ld m) is overwritten.
 int sqrtm_e1(Ws& ws, int m, const int* mdev, double* c, int want_sqrt, int* iters, cudaStream_t s) {
   double *M = ws.mats[0], *T = ws.mats[1], *Minv = ws.mats[2];
-  CK(launch_first_column(want_sqrt ? M : nullptr, mdev, c, s));
+  LK(PK_SMALL, launch_first_column(want_sqrt ? M : nullptr, mdev, c, s));
   const int maxit = 100;
   double err = INFINITY;
   int extra = -1;
   for (int it = 0; it < maxit; ++it) {
     CK(cudaMemcpyAsync(T, M, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(launch_lu(T, m, mdev, ws.piv, ws.scal + 11, ws.st, s));
-    CK(launch_lu_solve(T, m, ws.piv, mdev, m, Minv, m, 1, s));
-    CK(launch_db_update(M, Minv, m, mdev, c, ws.scal + 11, err > 1e-2 ? 1 : 0, ws.st, s));
+    LK(PK_SMALL, launch_lu(T, m, mdev, ws.piv, ws.scal + 11, ws.st, s));
+    LK(PK_SMALL, launch_lu_solve(T, m, ws.piv, mdev, m, Minv, m, 1, s));
+    LK(PK_SMALL, launch_db_update(M, Minv, m, mdev, c, ws.scal + 11, err > 1e-2 ? 1 : 0, ws.st, s));
     DevState hs;
     CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -407,6 +470,8 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   const int* mdev = &ws.st->m_used;
   Csr A{h->n, h->nnz, h->d_rowptr, h->d_colind, h->d_vals};
   h->has_state = 0;
+  g_launches = 0;
+  g_prof.begin_solve();
 
   cudaEvent_t ev[4];
   for (auto& e : ev) CK(cudaEventCreate(&e));
@@ -418,7 +483,7 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   } guard{ev};
 
   CK(cudaEventRecord(ev[0], s));
-  CK(launch_state_reset(ws.st, m, s));
+  LK(PK_SMALL, launch_state_reset(ws.st, m, s));
   CK(cudaMemsetAsync(ws.H, 0, (size_t)ldh * m * sizeof(double), s));
   CK(cudaMemsetAsync(ws.y, 0, (size_t)(m + 1) * sizeof(double), s));
   CK(cudaMemcpyAsync(ws.W, b, (size_t)n * sizeof(double), cudaMemcpyDefault, s));
@@ -441,7 +506,7 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
     if (sk.kind == SK_SRHT) {
       const int64_t npad = next_pow2(n);
       if (h->P_npad != npad || h->P_s != p->s || h->P_seed != p->seed) {
-        CK(launch_srht_sample(npad, p->s, rng_state(p->seed, 4), ws.P, s));
+        LK(PK_SMALL, launch_srht_sample(npad, p->s, rng_state(p->seed, 4), ws.P, s));
         h->P_npad = npad;
         h->P_s = p->s;
         h->P_seed = p->seed;
@@ -456,28 +521,28 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   none.kind = SK_NONE;
 
   // start vector: ||b||, sigma_0, sketch of b
-  CK(launch_update(n, ws.W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, 1 | 2, ws.part, ws.counter,
+  LK(PK_UPDATE, launch_update(n, ws.W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, 1 | 2, ws.part, ws.counter,
                    sk_on ? sk : none, ws.st, s));
-  if (sk_on) CK(launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
+  if (sk_on) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
 
   const int ntiles = (n + kTileRows - 1) / kTileRows;
   for (int c = 1; c <= m; ++c) {
     if (p->method == FAB_ARNOLDI) {
-      CK(launch_spmv_dots(A, ws.W, ld, c, 0, 0, ws.sigma, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
+      LK(PK_SPMV, launch_spmv_dots(A, ws.W, ld, c, 0, 0, ws.sigma, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
       double* Hcol = ws.H + (size_t)ldh * (c - 1);
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-        CK(launch_gemv_t(n, ws.W, ld, 0, c, ws.W + (size_t)c * ld, ws.gpart, ntiles, ws.st, s));
-        CK(launch_reduce_cols(ws.gpart, ntiles, c, ws.sigma, 0, Hcol, pass, ws.coef, 1.0, ws.st, s));
-        CK(launch_update(n, ws.W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, pass == 1 ? 1 : 0, ws.part,
+        LK(PK_GEMVT, launch_gemv_t(n, ws.W, ld, 0, c, ws.W + (size_t)c * ld, ws.gpart, ntiles, ws.st, s));
+        LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, c, ws.sigma, 0, Hcol, pass, ws.coef, 1.0, ws.st, s));
+        LK(PK_UPDATE, launch_update(n, ws.W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, pass == 1 ? 1 : 0, ws.part,
                          ws.counter, none, ws.st, s));
       }
     } else {
       const int j0 = std::max(0, c - k), kw = c - j0;
-      CK(launch_spmv_dots(A, ws.W, ld, c, j0, kw, ws.sigma, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
+      LK(PK_SPMV, launch_spmv_dots(A, ws.W, ld, c, j0, kw, ws.sigma, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
                           s));
-      CK(launch_update(n, ws.W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, 1, ws.part, ws.counter,
+      LK(PK_UPDATE, launch_update(n, ws.W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, 1, ws.part, ws.counter,
                        sk_on ? sk : none, ws.st, s));
-      if (sk_on) CK(launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
+      if (sk_on) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
     }
   }
   CK(cudaEventRecord(ev[1], s));
@@ -509,27 +574,27 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   if (!breakdown && p->method == FAB_SKETCHED_FAST) {
     // y = argmin || Theta V_m z - Theta v_{m+1} || (sketch-and-solve form of eq. sFOM)
     CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * (mu + 1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(launch_householder_qr(ws.qr, p->s, p->s, mdev, 1, ws.tau, s));
-    CK(launch_trsv(ws.qr, p->s, mdev, ws.qr + (size_t)mu * p->s, ws.y, 0, nullptr, s));
+    LK(PK_SMALL, launch_householder_qr(ws.qr, p->s, p->s, mdev, 1, ws.tau, s));
+    LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.qr + (size_t)mu * p->s, ws.y, 0, nullptr, s));
     yptr = ws.y;
   } else if (!breakdown && p->method == FAB_SKETCHED_LS) {
     // Blendenpik: R from the QR of Theta V_m; LSQR on V_m R^{-1} u ~ v_{m+1}; y = R^{-1} u
     CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * mu * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(launch_householder_qr(ws.qr, p->s, p->s, mdev, 0, ws.tau, s));
+    LK(PK_SMALL, launch_householder_qr(ws.qr, p->s, p->s, mdev, 0, ws.tau, s));
     const double one = 1.0;
     CK(cudaMemcpyAsync(ws.one, &one, sizeof(double), cudaMemcpyHostToDevice, s));
-    CK(launch_lsqr_u(n, ws.W + (size_t)mu * ld, ld, 1, ws.one, ws.u, 1, ws.part, ws.counter, ws.unorm2, ws.st, s));
-    CK(launch_gemv_t(n, ws.W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
-    CK(launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, ws.lv_q, 0, nullptr, 1.0, ws.st, s));
+    LK(PK_COMBINE, launch_lsqr_u(n, ws.W + (size_t)mu * ld, ld, 1, ws.one, ws.u, 1, ws.part, ws.counter, ws.unorm2, ws.st, s));
+    LK(PK_GEMVT, launch_gemv_t(n, ws.W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
+    LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, ws.lv_q, 0, nullptr, 1.0, ws.st, s));
     LsqrVecs lv{ws.lv_v, ws.lv_w, ws.lv_x, ws.lv_z, ws.lv_coef, ws.lv_q};
-    CK(launch_lsqr_start(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, p->lsqr_tol, ws.st, s));
+    LK(PK_SMALL, launch_lsqr_start(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, p->lsqr_tol, ws.st, s));
     const int maxit = p->lsqr_maxit > 0 ? p->lsqr_maxit : 4 * mu;
     bool converged = false;
     for (int it = 0; it < maxit; ++it) {
-      CK(launch_lsqr_u(n, ws.W, ld, mu, ws.lv_coef, ws.u, 0, ws.part, ws.counter, ws.unorm2, ws.st, s));
-      CK(launch_gemv_t(n, ws.W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
-      CK(launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, ws.lv_q, 0, nullptr, 1.0, ws.st, s));
-      CK(launch_lsqr_step(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, ws.st, s));
+      LK(PK_COMBINE, launch_lsqr_u(n, ws.W, ld, mu, ws.lv_coef, ws.u, 0, ws.part, ws.counter, ws.unorm2, ws.st, s));
+      LK(PK_GEMVT, launch_gemv_t(n, ws.W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
+      LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, ws.lv_q, 0, nullptr, 1.0, ws.st, s));
+      LK(PK_SMALL, launch_lsqr_step(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, ws.st, s));
       CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (hs.status != FAB_OK) return hs.status;
@@ -540,31 +605,32 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
     }
     lsqr_iters = hs.iters;
     if (!converged) return FAB_ENOTCONV;
-    CK(launch_trsv(ws.qr, p->s, mdev, ws.lv_x, ws.y, 0, nullptr, s));
+    LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.lv_x, ws.y, 0, nullptr, s));
     yptr = ws.y;
   }
   // f(H_m + h y e_m^T) e_1
   if (p->f == FAB_F_EXP) {
-    CK(launch_build_hhat(ws.H, ldh, mdev, yptr, p->t, ws.mats[0], m, m, s));
+    LK(PK_SMALL, launch_build_hhat(ws.H, ldh, mdev, yptr, p->t, ws.mats[0], m, m, s));
     rc = expm_e1(ws, m, mdev, ws.cvec, &fh_iters, s);
   } else {
-    CK(launch_build_hhat(ws.H, ldh, mdev, yptr, 1.0, ws.mats[0], m, m, s));
+    LK(PK_SMALL, launch_build_hhat(ws.H, ldh, mdev, yptr, 1.0, ws.mats[0], m, m, s));
     rc = sqrtm_e1(ws, m, mdev, ws.cvec, p->f == FAB_F_SQRT, &fh_iters, s);
   }
   if (rc != FAB_OK) return rc;
   CK(cudaEventRecord(ev[2], s));
   // x = ||b|| V_m c
-  CK(launch_prep_coef(ws.cvec, ws.sigma, mdev, ws.st, ws.coef, s));
+  LK(PK_COMBINE, launch_prep_coef(ws.cvec, ws.sigma, mdev, ws.st, ws.coef, s));
   double* xdst = x;
   if (!bx_on_device) {
     if ((h->xbuf.bytes < (size_t)n * 8 && fault_hit()) || !ensure(h->xbuf, (size_t)n * 8)) return FAB_ENOMEM;
     xdst = ptr<double>(h->xbuf);
   }
-  CK(launch_combine(n, ws.W, ld, mu, ws.coef, xdst, 0.0, s));
+  LK(PK_COMBINE, launch_combine(n, ws.W, ld, mu, ws.coef, xdst, 0.0, s));
   CK(cudaEventRecord(ev[3], s));
   if (!bx_on_device) CK(cudaMemcpyAsync(x, xdst, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (g_prof.on) g_prof.end_solve();
   if (hs.status != FAB_OK) return hs.status;
   h->has_state = 1;
   if (stats) {
@@ -572,6 +638,7 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
     stats->m_used = mu;
     stats->lsqr_iters = lsqr_iters;
     stats->fh_iters = fh_iters;
+    stats->launches = g_launches;
     stats->beta = hs.beta;
     double hl = 0.0;
     if (mu == m) CK(cudaMemcpy(&hl, ws.H + m + (size_t)ldh * (m - 1), sizeof(double), cudaMemcpyDeviceToHost));
@@ -680,4 +747,26 @@ extern "C" int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t
   if (cudaStreamSynchronize(st) != cudaSuccess) rc = FAB_ECUDA;
   cudaGetLastError();
   return rc;
+}
+
+extern "C" int fab_profile_enable(int on) {
+  g_prof.on = on != 0;
+  for (int i = 0; i < PK_COUNT; ++i) {
+    g_prof.total_ms[i] = 0.0;
+    g_prof.launches[i] = 0;
+  }
+  g_prof.begin_solve();
+  return FAB_OK;
+}
+
+extern "C" int fab_profile_query(const char* name, double* total_ms, int64_t* launches) {
+  if (!name) return FAB_EINVAL;
+  for (int i = 0; i < PK_COUNT; ++i) {
+    if (strcmp(name, kProfNames[i]) == 0) {
+      if (total_ms) *total_ms = g_prof.total_ms[i];
+      if (launches) *launches = g_prof.launches[i];
+      return FAB_OK;
+    }
+  }
+  return FAB_EINVAL;
 }

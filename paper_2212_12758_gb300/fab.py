@@ -25,7 +25,8 @@ FP64, MIXED = 0, 1
 
 # Every symbol the header declares (checked against include/fab.h by the tests).
 SYMBOLS = ("fab_params_default", "fab_strerror", "fab_create", "fab_apply", "fab_destroy", "fab_last_state",
-           "fab_last_basis", "fab_sketch_apply")
+           "fab_last_basis", "fab_sketch_apply", "fab_profile_enable", "fab_profile_query")
+PROFILE_KINDS = ("spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine")
 
 
 class Params(ctypes.Structure):
@@ -37,7 +38,7 @@ class Params(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("m_used", ctypes.c_int), ("lsqr_iters", ctypes.c_int), ("fh_iters", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("h_last", ctypes.c_double), ("beta", ctypes.c_double),
+                ("launches", ctypes.c_int), ("h_last", ctypes.c_double), ("beta", ctypes.c_double),
                 ("ms_basis", ctypes.c_double), ("ms_small", ctypes.c_double), ("ms_combine", ctypes.c_double),
                 ("ms_total", ctypes.c_double)]
 
@@ -62,6 +63,10 @@ lib.fab_last_basis.argtypes = [_vp, _vp, _i32]
 lib.fab_last_basis.restype = _i32
 lib.fab_sketch_apply.argtypes = [_i32, _i64, _i32, _i32, _u64, _vp, _i64, _i32, _vp, _vp]
 lib.fab_sketch_apply.restype = _i32
+lib.fab_profile_enable.argtypes = [_i32]
+lib.fab_profile_enable.restype = _i32
+lib.fab_profile_query.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+lib.fab_profile_query.restype = _i32
 
 
 class FabError(RuntimeError):
@@ -186,4 +191,19 @@ def sketch_apply(V, s: int, sketch: int = SPARSE_SIGN, zeta: int = 8, seed: int 
         out = torch.empty((ncols, s), dtype=torch.float64, device=V.device)
     _check(lib.fab_sketch_apply(int(sketch), int(n), int(s), int(zeta), int(seed), V.data_ptr(), int(n), int(ncols),
                                 out.data_ptr(), stream), "fab_sketch_apply")
+    return out
+
+
+def profile_enable(on: bool = True):
+    _check(lib.fab_profile_enable(1 if on else 0), "fab_profile_enable")
+
+
+def profile_query():
+    """{kernel class: (total device ms, launches)} accumulated since profile_enable."""
+    out = {}
+    for name in PROFILE_KINDS:
+        ms = ctypes.c_double()
+        cnt = ctypes.c_int64()
+        _check(lib.fab_profile_query(name.encode(), ctypes.byref(ms), ctypes.byref(cnt)), "fab_profile_query")
+        out[name] = (ms.value, cnt.value)
     return out
