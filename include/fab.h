@@ -163,6 +163,31 @@ int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t seed,
                      const double* V_dev, int64_t ldv, int ncols, double* out_dev, void* stream);
 
 /*
+ * fab_sketch_apply_noalloc - the same out = Theta V as fab_sketch_apply (same
+ * arguments, same kernels, same result), but it allocates no device memory:
+ * its scratch lives in one fixed array inside the library.
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate while they run: a host application that pre-reserves or caps all
+ * device memory for its own allocator, or a latency-sensitive loop where a
+ * cudaMalloc/cudaFree (which may synchronize the device) is not acceptable.
+ *
+ * Limits: the fixed scratch holds ceil(n/4096) * s <= 1,048,576 chunk partial
+ * sums (8 MiB) plus the SRHT row sample (s <= 4096); larger sizes return
+ * FAB_EINVAL without touching the device. Every GPU that loads the library
+ * keeps this scratch (about 8.02 MiB) until the process exits.
+ * Set-up: the first call on each device looks up the scratch address on that
+ * device (the device must be current); make that first call before any stream
+ * capture.
+ * Sharing: all calls on a device use the same scratch and it keeps the last
+ * call's contents (each call clears what it needs); calls whose work overlaps
+ * on the GPU (different streams or host threads) race on it, so serialize them.
+ * Returns after synchronizing `stream`.
+ */
+int fab_sketch_apply_noalloc(int sketch, int64_t n, int s, int zeta, uint64_t seed,
+                             const double* V_dev, int64_t ldv, int ncols, double* out_dev, void* stream);
+
+/*
  * Kernel-level device timing (measurement support, not needed for solving).
  * fab_profile_enable(1) resets the accumulators and makes every later
  * fab_apply record CUDA events, on the solve's stream, around each launch of

@@ -25,7 +25,8 @@ FP64, MIXED = 0, 1
 
 # Every symbol the header declares (checked against include/fab.h by the tests).
 SYMBOLS = ("fab_params_default", "fab_strerror", "fab_create", "fab_apply", "fab_destroy", "fab_last_state",
-           "fab_last_basis", "fab_sketch_apply", "fab_profile_enable", "fab_profile_query")
+           "fab_last_basis", "fab_sketch_apply", "fab_sketch_apply_noalloc", "fab_profile_enable",
+           "fab_profile_query")
 PROFILE_KINDS = ("spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine")
 
 
@@ -63,6 +64,8 @@ lib.fab_last_basis.argtypes = [_vp, _vp, _i32]
 lib.fab_last_basis.restype = _i32
 lib.fab_sketch_apply.argtypes = [_i32, _i64, _i32, _i32, _u64, _vp, _i64, _i32, _vp, _vp]
 lib.fab_sketch_apply.restype = _i32
+lib.fab_sketch_apply_noalloc.argtypes = [_i32, _i64, _i32, _i32, _u64, _vp, _i64, _i32, _vp, _vp]
+lib.fab_sketch_apply_noalloc.restype = _i32
 lib.fab_profile_enable.argtypes = [_i32]
 lib.fab_profile_enable.restype = _i32
 lib.fab_profile_query.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -206,4 +209,20 @@ def profile_query():
         cnt = ctypes.c_int64()
         _check(lib.fab_profile_query(name.encode(), ctypes.byref(ms), ctypes.byref(cnt)), "fab_profile_query")
         out[name] = (ms.value, cnt.value)
+    return out
+
+
+def sketch_apply_noalloc(V, s: int, sketch: int = SPARSE_SIGN, zeta: int = 8, seed: int = 1, out=None, stream=None):
+    """Same result as sketch_apply, computed with the library's fixed scratch
+    (fab_sketch_apply_noalloc): no device allocation inside the call. `out` must
+    be given by callers that cannot allocate either."""
+    import torch
+
+    if not (V.is_cuda and V.dtype == torch.float64 and V.is_contiguous()):
+        raise ValueError("V must be a contiguous float64 CUDA tensor")
+    ncols, n = V.shape
+    if out is None:
+        out = torch.empty((ncols, s), dtype=torch.float64, device=V.device)
+    _check(lib.fab_sketch_apply_noalloc(int(sketch), int(n), int(s), int(zeta), int(seed), V.data_ptr(), int(n),
+                                        int(ncols), out.data_ptr(), stream), "fab_sketch_apply_noalloc")
     return out
