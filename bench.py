@@ -195,6 +195,9 @@ def main():
     ap.add_argument("--impl", default="fab", choices=["fab", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the sketched_ls / Arnoldi side measurements")
+    ap.add_argument("--grid", type=int, default=N_GRID,
+                    help="grid side N of the 3D operator (default 200, the benchmark workload; smaller N only "
+                         "for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -215,7 +218,7 @@ def main():
     from paper_2212_12758_gb300 import fab
     from paper_2212_12758_gb300 import workloads as W
 
-    A = W.convdiff(3, N_GRID)
+    A = W.convdiff(3, args.grid)
     b = W.random_vector(A.n, SEED_B)
     n, nnz = A.n, A.nnz
     Mx = fab.Matrix.from_csr(A)
@@ -348,7 +351,8 @@ def main():
         line = {"metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": n, "nnz": nnz, "m": M, "k": K_WIN, "s": S_ROWS,
+                "config": {"workload": WORKLOAD if args.grid == N_GRID else WORKLOAD.replace("200^3", f"{args.grid}^3"),
+                           "n": n, "nnz": nnz, "m": M, "k": K_WIN, "s": S_ROWS,
                            "sketch": "srht", "method": "sketched_fast", "f": "exp(tA), t=-1e-3",
                            "l2": "inputs larger than L2 (A 0.7 GB, basis 6.5 GB per solve)",
                            "parallelism": f"replicas x{ws}"},

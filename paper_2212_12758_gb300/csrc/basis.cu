@@ -34,50 +34,135 @@ cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s) {
 }
 
 // --------------------------------------------- SpMV + window dot products
-// w = sigma_{c-1} A W_{c-1} is written to W_c; for the window j0..j0+kw-1 the
-// dots <W_j, w> and ||w||^2 are reduced over the grid. The last block writes
-// h_{j,c-1} = sigma_j <W_j, w> into H, the update coefficients
-// coef_q = sigma_j h_{j,c-1} for the raw columns, and ||w||^2 into wn2[c].
+// W_c = A W_{c-1} (the raw, unscaled product) is written to column c; for the
+// window j0..j0+kw-1 the dots d_j = <W_j, W_c> and ||W_c||^2 are reduced over
+// the grid. With v_j = sigma_j W_j the last block writes
+//   h_{j,c-1} = sigma_j sigma_{c-1} d_j   (into H),
+//   coef_q    = sigma_j^2 d_j             (update coefficient of the raw column),
+//   wn2[c]    = sigma_{c-1}^2 ||W_c||^2   (= ||A v_{c-1}||^2, for the breakdown test).
+// CSR tiles of 256 rows are staged in shared memory by bulk copies (double
+// buffered, one tile ahead); a tile whose nonzeros exceed the stage capacity is
+// read from global memory directly.
+constexpr int kSpmvTile = kThreads;  // rows per tile, one per thread
+constexpr int kSpmvCap = 2048;       // nonzeros per stage (vals 16 KB + colind 8 KB)
+
+size_t spmv_smem_bytes() { return (size_t)2 * kSpmvCap * (sizeof(double) + sizeof(int)); }
+
 __global__ __launch_bounds__(kThreads) void k_spmv_dots(
     Csr A, double* __restrict__ W, int64_t ld, int c, int j0, int kw, const double* __restrict__ sigma,
     double* __restrict__ H, int ldh, double* __restrict__ coef, double* __restrict__ wn2, double* __restrict__ part,
     unsigned* __restrict__ counter, DevState* st) {
   constexpr int NV = kMaxWindow + 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  double* s_vals = reinterpret_cast<double*>(smem_raw);                        // [2][kSpmvCap]
+  int* s_col = reinterpret_cast<int*>(smem_raw + 2 * kSpmvCap * sizeof(double));  // [2][kSpmvCap]
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ int s_e0[2];
+  __shared__ int s_staged[2];
   __shared__ double sh[32 * NV];
   __shared__ double tot[NV];
   if (st->stop) return;
+  const int tid = threadIdx.x;
+  const int ntiles = (A.n + kSpmvTile - 1) / kSpmvTile;
   const double* vin = W + (size_t)(c - 1) * ld;
   double* wout = W + (size_t)c * ld;
-  const double sc = sigma[c - 1];
   double acc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-  for (int r = blockIdx.x * kThreads + threadIdx.x; r < A.n; r += gridDim.x * kThreads) {
-    const int e0 = A.rowptr[r], e1 = A.rowptr[r + 1];
-    double y = 0.0;
-    for (int e = e0; e < e1; ++e) y = fma(__ldg(A.vals + e), __ldg(vin + __ldg(A.colind + e)), y);
-    const double w = sc * y;
-    wout[r] = w;
+  if (tid == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // thread 0: stage the nonzeros of `tile` into buffer `stg` (aligned to 4 entries
+  // so that both copies start and end on 16-byte boundaries; the CSR arrays are
+  // allocated with 4 spare entries).
+  auto issue = [&](int tile, int stg) {
+    const int r0 = tile * kSpmvTile;
+    const int r1 = min(r0 + kSpmvTile, A.n);
+    const int e0 = A.rowptr[r0], e1 = A.rowptr[r1];
+    const int e0a = e0 & ~3, e1a = (e1 + 3) & ~3;
+    const int cnt = e1a - e0a;
+    if (cnt > 0 && cnt <= kSpmvCap) {
+      s_e0[stg] = e0a;
+      s_staged[stg] = 1;
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&s_bar[stg], (uint32_t)cnt * 12u);
+      bulk_copy_g2s(s_vals + stg * kSpmvCap, A.vals + e0a, (uint32_t)cnt * 8u, &s_bar[stg]);
+      bulk_copy_g2s(s_col + stg * kSpmvCap, A.colind + e0a, (uint32_t)cnt * 4u, &s_bar[stg]);
+    } else {
+      s_staged[stg] = 0;
+    }
+  };
+  uint32_t par0 = 0, par1 = 0;
+  int it = 0;
+  int tile = blockIdx.x;
+  if (tid == 0 && tile < ntiles) issue(tile, 0);
+  __syncthreads();
+  bool failed = false;
+  for (; tile < ntiles; tile += gridDim.x, ++it) {
+    const int stg = it & 1;
+    const int next = tile + gridDim.x;
+    if (tid == 0 && next < ntiles) issue(next, stg ^ 1);
+    const bool staged = s_staged[stg] != 0;
+    if (staged) {
+      const uint32_t par = stg ? par1 : par0;
+      const bool ok = mbar_wait_bounded(&s_bar[stg], par);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      if (stg) par1 ^= 1u; else par0 ^= 1u;
+    }
+    const int r = tile * kSpmvTile + tid;
+    if (r < A.n) {
+      const int e0 = A.rowptr[r], e1 = A.rowptr[r + 1];
+      double y = 0.0;
+      if (staged) {
+        const int base = s_e0[stg];
+        const double* sv = s_vals + stg * kSpmvCap - base;
+        const int* sc = s_col + stg * kSpmvCap - base;
+        for (int e = e0; e < e1; ++e) y = fma(sv[e], __ldg(vin + sc[e]), y);
+      } else {
+        for (int e = e0; e < e1; ++e) y = fma(__ldg(A.vals + e), __ldg(vin + __ldg(A.colind + e)), y);
+      }
+      wout[r] = y;
 #pragma unroll
-    for (int q = 0; q < kMaxWindow; ++q)
-      if (q < kw) acc[q] = fma(W[(size_t)(j0 + q) * ld + r], w, acc[q]);
-    acc[kMaxWindow] = fma(w, w, acc[kMaxWindow]);
+      for (int q = 0; q < kMaxWindow; ++q)
+        if (q < kw) acc[q] = fma(W[(size_t)(j0 + q) * ld + r], y, acc[q]);
+      acc[kMaxWindow] = fma(y, y, acc[kMaxWindow]);
+    }
+    __syncthreads();  // every thread is done with buffer stg before it is refilled
+  }
+  if (failed) {
+    // A staged tile never arrived: record it, give the copies in flight a second
+    // bounded wait so that none lands in shared memory after the block exits.
+    if (tid == 0) {
+      st->status = FAB_ETIMEOUT;
+      st->stop = 1;
+      for (int b = 0; b < 2; ++b)
+        if (s_staged[b]) mbar_wait_bounded(&s_bar[b], b ? par1 : par0);
+    }
+    __syncthreads();
+    return;
   }
   block_sum<NV>(acc, sh);
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) part[(size_t)blockIdx.x * NV + q] = acc[q];
   }
   if (!last_block(counter)) return;
   sum_partials(part, gridDim.x, NV, tot, sh);
-  if (threadIdx.x < kw) {
-    const int j = j0 + threadIdx.x;
-    const double h = sigma[j] * tot[threadIdx.x];
-    H[j + (size_t)ldh * (c - 1)] = h;
-    coef[threadIdx.x] = sigma[j] * h;
+  const double sp = sigma[c - 1];
+  if (tid < kw) {
+    const int j = j0 + tid;
+    const double d = tot[tid];
+    H[j + (size_t)ldh * (c - 1)] = sigma[j] * sp * d;
+    coef[tid] = sigma[j] * sigma[j] * d;
   }
-  if (threadIdx.x == 0) {
-    wn2[c] = tot[kMaxWindow];
+  if (tid == 0) {
+    wn2[c] = sp * sp * tot[kMaxWindow];
     *counter = 0;
   }
 }
@@ -86,14 +171,16 @@ cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0,
                              double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
                              DevState* st, cudaStream_t s) {
   static int occ = 0;
+  const size_t smem = spmv_smem_bytes();
   if (occ == 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_dots, kThreads, 0);
+    cudaFuncSetAttribute(k_spmv_dots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_dots, kThreads, smem);
     if (occ < 1) occ = 1;
   }
-  const int need = (A.n + kThreads - 1) / kThreads;
+  const int need = (A.n + kSpmvTile - 1) / kSpmvTile;
   int grid = sm_count() * occ;
   if (need < grid) grid = need < 1 ? 1 : need;
-  k_spmv_dots<<<grid, kThreads, 0, s>>>(A, W, ld, c, j0, kw, sigma, H, ldh, coef, wn2, part, counter, st);
+  k_spmv_dots<<<grid, kThreads, smem, s>>>(A, W, ld, c, j0, kw, sigma, H, ldh, coef, wn2, part, counter, st);
   return cudaGetLastError();
 }
 
@@ -153,7 +240,7 @@ __device__ __forceinline__ int block_max_int(int v, int* sh) {
 // SRHT chunk: y = H_4096 (D x_chunk); writes y at the sampled in-chunk rows.
 // Thread t holds rows i*256 + t (i = 0..15) of the chunk.
 __device__ void sketch_chunk_srht(const double (&v)[kRowsPerThread], int chunk, const SketchDev& sk,
-                                  long long* buf, const int* s_rl, int* s_int) {
+                                  long long* buf, const int* s_P, double* s_acc, int* s_int) {
   const int t = threadIdx.x;
   int e = 0;
 #pragma unroll
@@ -187,14 +274,18 @@ __device__ void sketch_chunk_srht(const double (&v)[kRowsPerThread], int chunk, 
   __syncthreads();
   double b;
   const double a = pow2_split(E - 1071, &b);
-  double* out = sk.part + (size_t)chunk * sk.s;
-  for (int q = t; q < sk.s; q += kThreads) out[q] = ((double)buf[pidx(s_rl[q])] * a) * b;
+  // cross-chunk Hadamard factor (-1)^popcount(rh_q & chunk), rh_q = P_q >> 12
+  for (int q = t; q < sk.s; q += kThreads) {
+    const int p = s_P[q];
+    const double yq = ((double)buf[pidx(p & (kChunk - 1))] * a) * b;
+    s_acc[q] += (__popc((p >> kChunkLog2) & chunk) & 1) ? -yq : yq;
+  }
   __syncthreads();
 }
 
 // Sparse-sign chunk: every row j scatters +-X_j into its zeta sketch rows.
 __device__ void sketch_chunk_sparse(const double (&v)[kRowsPerThread], int chunk, int n, const SketchDev& sk,
-                                    unsigned long long* acc, int* s_int) {
+                                    unsigned long long* acc, double* s_acc, int* s_int) {
   const int t = threadIdx.x;
   int e = 0;
 #pragma unroll
@@ -246,9 +337,8 @@ __device__ void sketch_chunk_sparse(const double (&v)[kRowsPerThread], int chunk
   __syncthreads();
   double b;
   const double a = pow2_split(E - 1071, &b);
-  double* out = sk.part + (size_t)chunk * sk.s;
   for (int q = t; q < sk.s; q += kThreads) {
-    out[q] = ((double)(long long)acc[q] * a) * b;
+    s_acc[q] += ((double)(long long)acc[q] * a) * b;
     acc[q] = 0ull;
   }
   __syncthreads();
@@ -274,13 +364,16 @@ __global__ __launch_bounds__(kThreads) void k_update(int n, double* __restrict__
   __shared__ int s_int[32];
   if (st->stop) return;
   double* s_coef = reinterpret_cast<double*>(smem_raw);  // nc doubles
-  unsigned char* after = smem_raw + ((size_t)nc * 8 + 15) / 16 * 16;
+  double* s_acc = reinterpret_cast<double*>(smem_raw + ((size_t)nc * 8 + 15) / 16 * 16);  // s doubles
+  unsigned char* after = reinterpret_cast<unsigned char*>(s_acc) + ((size_t)(SK == SK_NONE ? 0 : sk.s) * 8 + 15) / 16 * 16;
   long long* buf = reinterpret_cast<long long*>(after);                     // SRHT: pidx(4096) int64
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(after);   // sparse: s uint64
-  int* s_rl = reinterpret_cast<int*>(after + (size_t)(kChunk + kChunk / 16) * 8);  // SRHT: s ints
+  int* s_P = reinterpret_cast<int*>(after + (size_t)(kChunk + kChunk / 16) * 8);  // SRHT: s ints
   for (int i = threadIdx.x; i < nc; i += kThreads) s_coef[i] = coef[i];
+  if (SK != SK_NONE)
+    for (int q = threadIdx.x; q < sk.s; q += kThreads) s_acc[q] = 0.0;
   if (SK == SK_SRHT)
-    for (int q = threadIdx.x; q < sk.s; q += kThreads) s_rl[q] = sk.P[q] & (kChunk - 1);
+    for (int q = threadIdx.x; q < sk.s; q += kThreads) s_P[q] = sk.P[q];
   if (SK == SK_SPARSE)
     for (int q = threadIdx.x; q < sk.s; q += kThreads) acc[q] = 0ull;
   __syncthreads();
@@ -323,8 +416,12 @@ __global__ __launch_bounds__(kThreads) void k_update(int n, double* __restrict__
         }
       }
     }
-    if (SK == SK_SRHT) sketch_chunk_srht(v, chunk, sk, buf, s_rl, s_int);
-    if (SK == SK_SPARSE) sketch_chunk_sparse(v, chunk, n, sk, acc, s_int);
+    if (SK == SK_SRHT) sketch_chunk_srht(v, chunk, sk, buf, s_P, s_acc, s_int);
+    if (SK == SK_SPARSE) sketch_chunk_sparse(v, chunk, n, sk, acc, s_acc, s_int);
+  }
+  if (SK != SK_NONE) {  // this block's share of the sketch (its chunks, fixed order)
+    double* out = sk.part + (size_t)blockIdx.x * sk.s;
+    for (int q = threadIdx.x; q < sk.s; q += kThreads) out[q] = s_acc[q];
   }
   if (!(mode & kModeNorm)) return;
   double nv[1] = {nrm};
@@ -347,11 +444,13 @@ __global__ __launch_bounds__(kThreads) void k_update(int n, double* __restrict__
         sigma[0] = 1.0 / h;
       }
     } else {
-      H[c + (size_t)ldh * (c - 1)] = h;
-      if (!isfinite(h)) {
+      // the stored column is W_c = w' / sigma_{c-1}: h_{c,c-1} = ||w'|| = sigma_{c-1} ||W_c||
+      const double hc = sigma[c - 1] * h;
+      H[c + (size_t)ldh * (c - 1)] = hc;
+      if (!isfinite(hc)) {
         st->status = FAB_ENUMERIC;
         st->stop = 1;
-      } else if (!(h > 64.0 * DBL_EPSILON * sqrt(wn2[c]))) {
+      } else if (!(hc > 64.0 * DBL_EPSILON * sqrt(wn2[c]))) {
         st->m_used = c;  // the basis spans an invariant subspace
         st->stop = 1;
         sigma[c] = 0.0;
@@ -365,6 +464,7 @@ __global__ __launch_bounds__(kThreads) void k_update(int n, double* __restrict__
 
 size_t update_smem_bytes(int kind, int nc, int s) {
   size_t b = ((size_t)nc * 8 + 15) / 16 * 16;
+  if (kind != SK_NONE) b += ((size_t)s * 8 + 15) / 16 * 16;
   if (kind == SK_SRHT) b += (size_t)(kChunk + kChunk / 16) * 8 + (size_t)s * 4;
   if (kind == SK_SPARSE) b += (size_t)s * 8;
   return b;
@@ -372,7 +472,7 @@ size_t update_smem_bytes(int kind, int nc, int s) {
 
 cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
                           int ldh, double* sigma, const double* wn2, int mode, double* part, unsigned* counter,
-                          const SketchDev& sk, DevState* st, cudaStream_t s) {
+                          SketchDev& sk, DevState* st, cudaStream_t s) {
   const size_t smem = update_smem_bytes(sk.kind, nc, sk.s);
   const int nchunks = (n + kChunk - 1) / kChunk;
   const void* fn = sk.kind == SK_SRHT ? (const void*)k_update<SK_SRHT>
@@ -383,6 +483,7 @@ cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, c
   if (occ < 1) occ = 1;
   int grid = sm_count() * occ;
   if (nchunks < grid) grid = nchunks < 1 ? 1 : nchunks;
+  sk.nparts = grid;  // one sketch partial per block
   switch (sk.kind) {
     case SK_SRHT:
       k_update<SK_SRHT><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, sigma, wn2, mode, part,
@@ -399,23 +500,18 @@ cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, c
   return cudaGetLastError();
 }
 
-// ----------------------------------------------- cross-chunk sketch reduce
-// out[q] = scale * sigma[col] * sum_chunks sign(q, chunk) * part[chunk][q], one
-// warp per sketch row, fixed order. For the SRHT the sign is the cross-chunk
-// Hadamard factor (-1)^popcount(rh_q & chunk), rh_q = P_q >> 12.
+// ---------------------------------------------- cross-block sketch reduce
+// out[q] = scale * sigma[col] * sum_blocks part[block][q] (the per-block partials
+// of k_update already carry the cross-chunk Hadamard signs); one warp per
+// sketch row, fixed order.
 __global__ void k_sketch_reduce(SketchDev sk, const double* __restrict__ sigma, int col, double scale,
                                 double* __restrict__ out, DevState* st) {
   if (st->stop) return;
   const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (q >= sk.s) return;
-  const int rh = (sk.kind == SK_SRHT) ? (sk.P[q] >> sk.chunk_log2) : 0;
   double a = 0.0;
-  for (int ch = lane; ch < sk.nchunks; ch += 32) {
-    double v = sk.part[(size_t)ch * sk.s + q];
-    if (__popc(rh & ch) & 1) v = -v;
-    a += v;
-  }
+  for (int b = lane; b < sk.nparts; b += 32) a += sk.part[(size_t)b * sk.s + q];
   a = warp_sum(a);
   if (lane == 0) out[q] = a * scale * (sigma ? sigma[col] : 1.0);
 }
@@ -508,10 +604,11 @@ cudaError_t launch_gemv_t(int n, const double* W, int64_t ld, int j0, int nc, co
 }
 
 // d_q = sum over tiles of part[tile][q] (fixed order), then with j = j0+q:
-//   Hcol[j] = sigma_j d_q (or += when h_accumulate), coef[q] = extra * sigma_j * (sigma_j d_q).
+//   Hcol[j] = sigma_j sig_col d_q (or += when h_accumulate; sig_col = 1 when NULL),
+//   coef[q] = sigma_j^2 d_q (update coefficient of a raw column).
 __global__ void k_reduce_cols(const double* __restrict__ part, int ntiles, int nc, const double* __restrict__ sigma,
-                              int j0, double* __restrict__ Hcol, int h_accumulate, double* __restrict__ coef,
-                              double extra, DevState* st) {
+                              int j0, const double* __restrict__ sig_col, double* __restrict__ Hcol, int h_accumulate,
+                              double* __restrict__ coef, DevState* st) {
   if (st && st->stop) return;
   const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -521,17 +618,17 @@ __global__ void k_reduce_cols(const double* __restrict__ part, int ntiles, int n
   a = warp_sum(a);
   if (lane == 0) {
     const int j = j0 + q;
-    const double h = sigma[j] * a;
+    const double h = sigma[j] * (sig_col ? *sig_col : 1.0) * a;
     if (Hcol) Hcol[j] = h_accumulate ? Hcol[j] + h : h;
-    if (coef) coef[q] = extra * sigma[j] * h;
+    if (coef) coef[q] = sigma[j] * sigma[j] * a;
   }
 }
 
-cudaError_t launch_reduce_cols(const double* part, int ntiles, int nc, const double* sigma, int j0, double* Hcol,
-                               int h_accumulate, double* coef, double coef_scale_extra, DevState* st,
+cudaError_t launch_reduce_cols(const double* part, int ntiles, int nc, const double* sigma, int j0,
+                               const double* sig_col, double* Hcol, int h_accumulate, double* coef, DevState* st,
                                cudaStream_t s) {
   const int grid = (nc + 7) / 8;
-  k_reduce_cols<<<grid, 256, 0, s>>>(part, ntiles, nc, sigma, j0, Hcol, h_accumulate, coef, coef_scale_extra, st);
+  k_reduce_cols<<<grid, 256, 0, s>>>(part, ntiles, nc, sigma, j0, sig_col, Hcol, h_accumulate, coef, st);
   return cudaGetLastError();
 }
 

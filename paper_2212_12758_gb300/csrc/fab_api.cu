@@ -21,6 +21,7 @@ namespace {
 // coefficients c_j = (2m-j)! m! / ((2m)! j! (m-j)!), m = 13, and the backward-error
 // threshold theta_13 of that paper's Table 2.3.
 constexpr double kTheta13 = 5.371920351148152;
+constexpr int64_t kCsrPad = 4;  // spare CSR entries for the aligned tile copies
 
 struct Pade13 {
   double b[14];
@@ -208,13 +209,16 @@ int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr, 
   h->nnz = (int)nnz;
   h->ld = ((n + 31) / 32) * 32;
   if (fault_hit() || cudaMalloc(&h->d_rowptr, (n + 1) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&h->d_colind, std::max<int64_t>(nnz, 1) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&h->d_vals, std::max<int64_t>(nnz, 1) * sizeof(double)) != cudaSuccess) {
+      cudaMalloc(&h->d_colind, (nnz + kCsrPad) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->d_vals, (nnz + kCsrPad) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     fab_destroy(h);
     return FAB_ENOMEM;
   }
-  if (cudaMemcpy(h->d_rowptr, rp32.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+  // the spare entries past nnz are read (never used) by the 16-byte aligned tile copies
+  if (cudaMemset(h->d_colind + nnz, 0, kCsrPad * sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->d_vals + nnz, 0, kCsrPad * sizeof(double)) != cudaSuccess ||
+      cudaMemcpy(h->d_rowptr, rp32.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
       (nnz > 0 && cudaMemcpy(h->d_colind, ci.data(), nnz * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) ||
       (nnz > 0 && cudaMemcpy(h->d_vals, va.data(), nnz * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)) {
     cudaGetLastError();
@@ -416,7 +420,7 @@ int expm_e1(Ws& ws, int m, const int* mdev, double* c, int* squarings, cudaStrea
   // (V - U) X = (V + U)
   LK(PK_SMALL, launch_lincomb(T, V, U, nullptr, nullptr, 1.0, -1.0, 0, 0, 0.0, m, mdev, m, s));
   LK(PK_SMALL, launch_lincomb(X, V, U, nullptr, nullptr, 1.0, 1.0, 0, 0, 0.0, m, mdev, m, s));
-  LK(PK_SMALL, launch_lu(T, m, mdev, ws.piv, ws.scal + 11, ws.st, s));
+  LK(PK_SMALL, launch_lu_fast(T, m, mdev, m, ws.piv, ws.scal + 11, ws.st, s));
   LK(PK_SMALL, launch_lu_solve(T, m, ws.piv, mdev, m, X, m, 0, s));
   for (int i = 0; i < sq; ++i) {
     LK(PK_SMALL, launch_gemm(X2, X, X, m, mdev, m, 1.0, 0.0, s));
@@ -437,7 +441,7 @@ int sqrtm_e1(Ws& ws, int m, const int* mdev, double* c, int want_sqrt, int* iter
   int extra = -1;
   for (int it = 0; it < maxit; ++it) {
     CK(cudaMemcpyAsync(T, M, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    LK(PK_SMALL, launch_lu(T, m, mdev, ws.piv, ws.scal + 11, ws.st, s));
+    LK(PK_SMALL, launch_lu_fast(T, m, mdev, m, ws.piv, ws.scal + 11, ws.st, s));
     LK(PK_SMALL, launch_lu_solve(T, m, ws.piv, mdev, m, Minv, m, 1, s));
     LK(PK_SMALL, launch_db_update(M, Minv, m, mdev, c, ws.scal + 11, err > 1e-2 ? 1 : 0, ws.st, s));
     DevState hs;
@@ -484,6 +488,7 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
 
   CK(cudaEventRecord(ev[0], s));
   LK(PK_SMALL, launch_state_reset(ws.st, m, s));
+  CK(cudaMemsetAsync(ws.counter, 0, 64, s));
   CK(cudaMemsetAsync(ws.H, 0, (size_t)ldh * m * sizeof(double), s));
   CK(cudaMemsetAsync(ws.y, 0, (size_t)(m + 1) * sizeof(double), s));
   CK(cudaMemcpyAsync(ws.W, b, (size_t)n * sizeof(double), cudaMemcpyDefault, s));
@@ -532,7 +537,8 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
       double* Hcol = ws.H + (size_t)ldh * (c - 1);
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
         LK(PK_GEMVT, launch_gemv_t(n, ws.W, ld, 0, c, ws.W + (size_t)c * ld, ws.gpart, ntiles, ws.st, s));
-        LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, c, ws.sigma, 0, Hcol, pass, ws.coef, 1.0, ws.st, s));
+        LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, c, ws.sigma, 0, ws.sigma + (c - 1), Hcol, pass, ws.coef,
+                                        ws.st, s));
         LK(PK_UPDATE, launch_update(n, ws.W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, pass == 1 ? 1 : 0, ws.part,
                          ws.counter, none, ws.st, s));
       }
@@ -574,18 +580,18 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   if (!breakdown && p->method == FAB_SKETCHED_FAST) {
     // y = argmin || Theta V_m z - Theta v_{m+1} || (sketch-and-solve form of eq. sFOM)
     CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * (mu + 1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    LK(PK_SMALL, launch_householder_qr(ws.qr, p->s, p->s, mdev, 1, ws.tau, s));
+    LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 1, ws.tau, s));
     LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.qr + (size_t)mu * p->s, ws.y, 0, nullptr, s));
     yptr = ws.y;
   } else if (!breakdown && p->method == FAB_SKETCHED_LS) {
     // Blendenpik: R from the QR of Theta V_m; LSQR on V_m R^{-1} u ~ v_{m+1}; y = R^{-1} u
     CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * mu * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    LK(PK_SMALL, launch_householder_qr(ws.qr, p->s, p->s, mdev, 0, ws.tau, s));
+    LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 0, ws.tau, s));
     const double one = 1.0;
     CK(cudaMemcpyAsync(ws.one, &one, sizeof(double), cudaMemcpyHostToDevice, s));
     LK(PK_COMBINE, launch_lsqr_u(n, ws.W + (size_t)mu * ld, ld, 1, ws.one, ws.u, 1, ws.part, ws.counter, ws.unorm2, ws.st, s));
     LK(PK_GEMVT, launch_gemv_t(n, ws.W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
-    LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, ws.lv_q, 0, nullptr, 1.0, ws.st, s));
+    LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, nullptr, ws.lv_q, 0, nullptr, ws.st, s));
     LsqrVecs lv{ws.lv_v, ws.lv_w, ws.lv_x, ws.lv_z, ws.lv_coef, ws.lv_q};
     LK(PK_SMALL, launch_lsqr_start(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, p->lsqr_tol, ws.st, s));
     const int maxit = p->lsqr_maxit > 0 ? p->lsqr_maxit : 4 * mu;
@@ -593,7 +599,7 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
     for (int it = 0; it < maxit; ++it) {
       LK(PK_COMBINE, launch_lsqr_u(n, ws.W, ld, mu, ws.lv_coef, ws.u, 0, ws.part, ws.counter, ws.unorm2, ws.st, s));
       LK(PK_GEMVT, launch_gemv_t(n, ws.W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
-      LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, ws.lv_q, 0, nullptr, 1.0, ws.st, s));
+      LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, nullptr, ws.lv_q, 0, nullptr, ws.st, s));
       LK(PK_SMALL, launch_lsqr_step(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, ws.st, s));
       CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));

@@ -40,12 +40,12 @@ struct SketchDev {
   int zeta;            // sparse sign: nonzeros per column
   int chunk_log2;      // log2 of the rows per transform chunk (<= kChunkLog2)
   int nchunks;         // ceil(n / chunk)
-  int pad;
+  int nparts;          // block partials written by the last k_update (its grid)
   uint64_t st_rows;    // SplitMix64 stream states (see fab_rng_state)
   uint64_t st_signs;
   uint64_t st_D;
   const int* P;        // SRHT sampled rows (device, s entries, sorted)
-  double* part;        // nchunks x s chunk partials (chunk-major)
+  double* part;        // nparts x s block partials (block-major), nparts <= nchunks
 };
 
 // ----------------------------------------------------------------- SplitMix64
@@ -135,6 +135,51 @@ __device__ __forceinline__ double pow2_split(int e, double* second) {
   return __longlong_as_double((long long)(e1 + 1023) << 52);
 }
 
+// ------------------------------------------------ TMA bulk copy + mbarrier
+// One-dimensional bulk copies global -> shared (cp.async.bulk) completing on an
+// mbarrier with a transaction count. Source and destination must be 16-byte
+// aligned and the size a multiple of 16 bytes.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of `bar`: false if the limit expired.
+constexpr int kWaitLimit = 1 << 20;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 // ----------------------------------------------------------------- launchers
 // (defined in basis.cu / small.cu; all take the stream last and return cudaError_t)
 struct Csr {
@@ -151,15 +196,15 @@ cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0,
                              DevState* st, cudaStream_t s);
 cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
                           int ldh, double* sigma, const double* wn2, int mode, double* part, unsigned* counter,
-                          const SketchDev& sk, DevState* st, cudaStream_t s);
+                          SketchDev& sk, DevState* st, cudaStream_t s);
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
                                  DevState* st, cudaStream_t s);
 cudaError_t launch_srht_sample(int64_t npad, int s, uint64_t stP, int* P, cudaStream_t st);
 cudaError_t launch_gemv_t(int n, const double* W, int64_t ld, int j0, int nc, const double* x, double* part,
                           int ntiles, DevState* st, cudaStream_t s);
 cudaError_t launch_reduce_cols(const double* part, int ntiles, int nc, const double* sigma, int j0,
-                               double* Hcol, int h_accumulate, double* coef, double coef_scale_extra,
-                               DevState* st, cudaStream_t s);
+                               const double* sig_col, double* Hcol, int h_accumulate, double* coef, DevState* st,
+                               cudaStream_t s);
 cudaError_t launch_combine(int n, const double* W, int64_t ld, int nc, const double* coef, double* out,
                            double keep, cudaStream_t s);
 cudaError_t launch_scale_columns(int n, const double* W, int64_t ld, int nc, const double* sigma, double* dst,

@@ -8,6 +8,8 @@
 #include <float.h>
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "fab_internal.cuh"
 #include "small.cuh"
 
@@ -623,6 +625,253 @@ cudaError_t launch_lsqr_u(int n, const double* W, int64_t ld, int nc, const doub
   k_lsqr_u<<<grid_rows(n), kThreads, (size_t)(nc > 0 ? nc : 1) * 8, s>>>(n, W, ld, nc, coef, u, keep_zero, part,
                                                                           counter, unorm2, st);
   return cudaGetLastError();
+}
+
+
+// ------------------------------------------------ cluster QR / LU (DSMEM)
+// The s x (mu+extra) matrix of the QR (or the mu x mu matrix of the LU) is
+// distributed by columns over the CTAs of one thread-block cluster: global
+// column g lives in shared memory of CTA g % CL. At step j the owner of column j
+// forms the reflector (QR) or the pivot and multipliers (LU); after one cluster
+// barrier every CTA reads that vector from the owner's shared memory and updates
+// its own columns. One cluster barrier per step; the FP64 work of a step is
+// spread over CL SMs instead of one.
+namespace cg = cooperative_groups;
+
+template <int CL>
+__global__ void __launch_bounds__(256) k_qr_cluster(double* __restrict__ A, int lda, int rows,
+                                                    const int* __restrict__ mdev, int extra,
+                                                    double* __restrict__ tau_out) {
+  extern __shared__ __align__(16) double smem_d[];
+  __shared__ double red[32];
+  __shared__ double s_tau[kMaxM];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int r = (int)cluster.block_rank();
+  const int mu = *mdev;
+  const int ncols = mu + extra;
+  const int nloc = (ncols - r + CL - 1) / CL;  // my columns: g = r, r + CL, ...
+  double* loc = smem_d;                             // nloc x rows
+  double* vbuf = smem_d + (size_t)((ncols + CL - 1) / CL) * rows;  // rows
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int lc = 0; lc < nloc; ++lc) {
+    const double* src = A + (size_t)(lc * CL + r) * lda;
+    for (int i = tid; i < rows; i += blockDim.x) loc[(size_t)lc * rows + i] = src[i];
+  }
+  __syncthreads();
+  const int steps = mu < rows ? mu : rows;
+  for (int j = 0; j < steps; ++j) {
+    const int owner = j % CL;
+    if (r == owner) {
+      double* cj = loc + (size_t)(j / CL) * rows;
+      double ss = 0.0;
+      for (int i = j + 1 + tid; i < rows; i += blockDim.x) ss = fma(cj[i], cj[i], ss);
+      ss = warp_sum(ss);
+      if (lane == 0) red[warp] = ss;
+      __syncthreads();
+      double sig = 0.0;
+      for (int w = 0; w < nw; ++w) sig += red[w];
+      const double alpha = cj[j];
+      double t = 0.0, beta = alpha, vinv = 0.0;
+      if (sig != 0.0) {
+        const double nrm = sqrt(fma(alpha, alpha, sig));
+        beta = (alpha <= 0.0) ? nrm : -nrm;
+        t = (beta - alpha) / beta;
+        vinv = 1.0 / (alpha - beta);
+      }
+      __syncthreads();
+      for (int i = j + 1 + tid; i < rows; i += blockDim.x) cj[i] *= vinv;
+      if (tid == 0) {
+        cj[j] = beta;
+        s_tau[j] = t;
+      }
+    }
+    cluster.sync();  // reflector j is published in the owner's shared memory
+    const double* rcol = cluster.map_shared_rank(loc + (size_t)(j / CL) * rows, owner);
+    const double* rtau = cluster.map_shared_rank(s_tau, owner);
+    for (int i = j + 1 + tid; i < rows; i += blockDim.x) vbuf[i] = rcol[i];
+    const double tj = rtau[j];
+    if (r != owner && tid == 0) s_tau[j] = tj;
+    __syncthreads();
+    // apply H_j = I - tau v v^T (v_j = 1) to my columns g > j, one warp per column
+    int first = (j + 1 - r + CL - 1) / CL;  // first local column with g > j
+    if (first < 0) first = 0;
+    for (int lc = first + warp; lc < nloc; lc += nw) {
+      double* col = loc + (size_t)lc * rows;
+      double d = (lane == 0) ? col[j] : 0.0;
+      for (int i = j + 1 + lane; i < rows; i += 32) d = fma(vbuf[i], col[i], d);
+      d = warp_sum(d) * tj;
+      if (lane == 0) col[j] -= d;
+      for (int i = j + 1 + lane; i < rows; i += 32) col[i] = fma(-d, vbuf[i], col[i]);
+    }
+    __syncthreads();
+  }
+  cluster.sync();  // no CTA exits while others may still read its shared memory
+  for (int lc = 0; lc < nloc; ++lc) {
+    double* dst = A + (size_t)(lc * CL + r) * lda;
+    for (int i = tid; i < rows; i += blockDim.x) dst[i] = loc[(size_t)lc * rows + i];
+  }
+  if (r == 0)
+    for (int j = tid; j < steps; j += blockDim.x) tau_out[j] = s_tau[j];
+}
+
+// LU with partial pivoting (ties to the smallest row), rows swapped across the
+// whole matrix; piv[k] = row swapped with k; log|det| to *logdet.
+template <int CL>
+__global__ void __launch_bounds__(256) k_lu_cluster(double* __restrict__ M, int ld, const int* __restrict__ mdev,
+                                                    int* __restrict__ piv, double* __restrict__ logdet,
+                                                    DevState* st) {
+  extern __shared__ __align__(16) double smem_d[];
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  __shared__ int s_piv[kMaxM];
+  __shared__ double s_logdet;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int r = (int)cluster.block_rank();
+  const int mu = *mdev;
+  const int nloc = (mu - r + CL - 1) / CL;
+  double* loc = smem_d;
+  double* lbuf = smem_d + (size_t)((mu + CL - 1) / CL) * mu;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int lc = 0; lc < nloc; ++lc) {
+    const double* src = M + (size_t)(lc * CL + r) * ld;
+    for (int i = tid; i < mu; i += blockDim.x) loc[(size_t)lc * mu + i] = src[i];
+  }
+  if (tid == 0) s_logdet = 0.0;
+  __syncthreads();
+  for (int k = 0; k < mu; ++k) {
+    const int owner = k % CL;
+    if (r == owner) {
+      double* ck = loc + (size_t)(k / CL) * mu;
+      double best = -1.0;
+      int bi = mu;
+      for (int i = k + tid; i < mu; i += blockDim.x) {
+        const double a = fabs(ck[i]);
+        if (a > best) {
+          best = a;
+          bi = i;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        rv[warp] = best;
+        ri[warp] = bi;
+      }
+      __syncthreads();
+      double b = -1.0;
+      int p = mu;
+      for (int w = 0; w < nw; ++w)
+        if (rv[w] > b || (rv[w] == b && ri[w] < p)) {
+          b = rv[w];
+          p = ri[w];
+        }
+      if (tid == 0) {
+        const double t = ck[k];
+        ck[k] = ck[p];
+        ck[p] = t;
+        s_piv[k] = p;
+        const double pv = ck[k];
+        if (pv == 0.0 || !isfinite(pv)) st->status = FAB_ENUMERIC;
+      }
+      __syncthreads();
+      const double pv = ck[k];
+      const double pinv = pv != 0.0 ? 1.0 / pv : 0.0;
+      for (int i = k + 1 + tid; i < mu; i += blockDim.x) ck[i] *= pinv;
+    }
+    cluster.sync();  // pivot and multipliers of column k are published
+    const int p = *cluster.map_shared_rank(s_piv + k, owner);
+    const double* rcol = cluster.map_shared_rank(loc + (size_t)(k / CL) * mu, owner);
+    for (int i = k + 1 + tid; i < mu; i += blockDim.x) lbuf[i] = rcol[i];
+    if (tid == 0) {
+      if (r != owner) s_piv[k] = p;
+      const double pv = rcol[k];  // U_kk (after the owner's swap)
+      if (pv != 0.0 && isfinite(pv)) s_logdet += log(fabs(pv));
+    }
+    __syncthreads();
+    for (int lc = warp; lc < nloc; lc += nw) {
+      const int g = lc * CL + r;
+      if (g == k) continue;
+      double* col = loc + (size_t)lc * mu;
+      if (lane == 0 && p != k) {
+        const double t = col[k];
+        col[k] = col[p];
+        col[p] = t;
+      }
+      __syncwarp();
+      if (g > k) {
+        const double ukj = col[k];
+        for (int i = k + 1 + lane; i < mu; i += 32) col[i] = fma(-lbuf[i], ukj, col[i]);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  cluster.sync();
+  for (int lc = 0; lc < nloc; ++lc) {
+    double* dst = M + (size_t)(lc * CL + r) * ld;
+    for (int i = tid; i < mu; i += blockDim.x) dst[i] = loc[(size_t)lc * mu + i];
+  }
+  if (r == 0) {
+    for (int k = tid; k < mu; k += blockDim.x) piv[k] = s_piv[k];
+    if (tid == 0 && logdet) *logdet = s_logdet;
+  }
+}
+
+namespace {
+template <typename K>
+cudaError_t launch_cluster(K kernel, int cl, size_t smem, cudaStream_t s, void** args) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cl > 8) cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, (const void*)kernel, args);
+}
+}  // namespace
+
+// Cluster QR when the matrix fits the cluster's shared memory, else the one-block kernel.
+cudaError_t launch_qr(double* A, int lda, int rows, const int* mdev, int max_cols, int extra, double* tau,
+                      cudaStream_t s) {
+  const int ncols = max_cols + extra;
+  for (int cl : {16, 8}) {
+    const size_t smem = ((size_t)((ncols + cl - 1) / cl) + 1) * rows * sizeof(double);
+    if (smem > 200 * 1024) continue;
+    void* args[] = {&A, &lda, &rows, (void*)&mdev, &extra, &tau};
+    cudaError_t e = cl == 16 ? launch_cluster(k_qr_cluster<16>, 16, smem, s, args)
+                             : launch_cluster(k_qr_cluster<8>, 8, smem, s, args);
+    if (e == cudaSuccess) return e;
+    cudaGetLastError();
+  }
+  return launch_householder_qr(A, lda, rows, mdev, extra, tau, s);
+}
+
+cudaError_t launch_lu_fast(double* M, int ld, const int* mdev, int max_m, int* piv, double* logdet, DevState* st,
+                           cudaStream_t s) {
+  for (int cl : {16, 8}) {
+    const size_t smem = ((size_t)((max_m + cl - 1) / cl) + 1) * max_m * sizeof(double);
+    if (smem > 200 * 1024) continue;
+    void* args[] = {&M, &ld, (void*)&mdev, &piv, &logdet, &st};
+    cudaError_t e = cl == 16 ? launch_cluster(k_lu_cluster<16>, 16, smem, s, args)
+                             : launch_cluster(k_lu_cluster<8>, 8, smem, s, args);
+    if (e == cudaSuccess) return e;
+    cudaGetLastError();
+  }
+  return launch_lu(M, ld, mdev, piv, logdet, st, s);
 }
 
 }  // namespace fab

@@ -16,6 +16,11 @@ struct LsqrVecs {
 
 cudaError_t launch_householder_qr(double* A, int lda, int rows, const int* mdev, int extra, double* tau,
                                   cudaStream_t s);
+// Cluster (DSMEM) versions when the matrix fits a cluster's shared memory.
+cudaError_t launch_qr(double* A, int lda, int rows, const int* mdev, int max_cols, int extra, double* tau,
+                      cudaStream_t s);
+cudaError_t launch_lu_fast(double* M, int ld, const int* mdev, int max_m, int* piv, double* logdet, DevState* st,
+                           cudaStream_t s);
 cudaError_t launch_trsv(const double* R, int ldr, const int* mdev, const double* xin, double* xout, int trans,
                         const double* pre, cudaStream_t s);
 cudaError_t launch_build_hhat(const double* H, int ldh, const int* mdev, const double* y, double scale, double* M,
