@@ -34,12 +34,15 @@ cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s) {
 }
 
 // --------------------------------------------- SpMV + window dot products
-// W_c = A W_{c-1} (the raw, unscaled product) is written to column c; for the
-// window j0..j0+kw-1 the dots d_j = <W_j, W_c> and ||W_c||^2 are reduced over
-// the grid. With v_j = sigma_j W_j the last block writes
-//   h_{j,c-1} = sigma_j sigma_{c-1} d_j   (into H),
-//   coef_q    = sigma_j^2 d_j             (update coefficient of the raw column),
-//   wn2[c]    = sigma_{c-1}^2 ||W_c||^2   (= ||A v_{c-1}||^2, for the breakdown test).
+// W_c = 2^shf[c-1] A W_{c-1} is written to column c (an exact power-of-two rescale
+// done on the exponent bits keeps the raw columns near unit norm without FP64
+// work); for the window j0..j0+kw-1 the dots d_j = <W_j, W_c> and ||W_c||^2 are
+// reduced over the grid. With v_j = sigma_j W_j and tau = sigma_{c-1} 2^-shf[c-1]
+// (so that A v_{c-1} = tau W_c) the last block writes
+//   h_{j,c-1} = sigma_j tau d_j     (into H),
+//   coef_q    = sigma_j^2 d_j       (update coefficient of the raw column),
+//   wn2[c]    = tau^2 ||W_c||^2     (= ||A v_{c-1}||^2, for the breakdown test),
+//   scl[c]    = tau.
 // CSR tiles of 256 rows are staged in shared memory by bulk copies (double
 // buffered, one tile ahead); a tile whose nonzeros exceed the stage capacity is
 // read from global memory directly.
@@ -49,8 +52,8 @@ constexpr int kSpmvCap = 2048;       // nonzeros per stage (vals 16 KB + colind 
 size_t spmv_smem_bytes() { return (size_t)2 * kSpmvCap * (sizeof(double) + sizeof(int)); }
 
 __global__ __launch_bounds__(kThreads) void k_spmv_dots(
-    Csr A, double* __restrict__ W, int64_t ld, int c, int j0, int kw, const double* __restrict__ sigma,
-    double* __restrict__ H, int ldh, double* __restrict__ coef, double* __restrict__ wn2, double* __restrict__ part,
+    Csr A, double* __restrict__ W, int64_t ld, int c, int j0, int kw, ColScale cs, double* __restrict__ H,
+    int ldh, double* __restrict__ coef, double* __restrict__ wn2, double* __restrict__ part,
     unsigned* __restrict__ counter, DevState* st) {
   constexpr int NV = kMaxWindow + 1;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -66,6 +69,10 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
   const int ntiles = (A.n + kSpmvTile - 1) / kSpmvTile;
   const double* vin = W + (size_t)(c - 1) * ld;
   double* wout = W + (size_t)c * ld;
+  const int ksh = cs.shf[c - 1];
+  double p2k;
+  const double p2k_hi = pow2_split(ksh, &p2k);
+  p2k *= p2k_hi;  // 2^ksh (only used for zeros / subnormals)
   double acc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) acc[q] = 0.0;
@@ -121,12 +128,13 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
       double y = 0.0;
       if (staged) {
         const int base = s_e0[stg];
-        const double* sv = s_vals + stg * kSpmvCap - base;
-        const int* sc = s_col + stg * kSpmvCap - base;
-        for (int e = e0; e < e1; ++e) y = fma(sv[e], __ldg(vin + sc[e]), y);
+        const double* sv = s_vals + stg * kSpmvCap;
+        const int* sc = s_col + stg * kSpmvCap;
+        for (int e = e0 - base; e < e1 - base; ++e) y = fma(sv[e], __ldg(vin + sc[e]), y);
       } else {
         for (int e = e0; e < e1; ++e) y = fma(__ldg(A.vals + e), __ldg(vin + __ldg(A.colind + e)), y);
       }
+      y = scale_pow2(y, ksh, p2k);
       wout[r] = y;
 #pragma unroll
       for (int q = 0; q < kMaxWindow; ++q)
@@ -154,20 +162,23 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
   }
   if (!last_block(counter)) return;
   sum_partials(part, gridDim.x, NV, tot, sh);
-  const double sp = sigma[c - 1];
+  double pinv;
+  const double pinv_hi = pow2_split(-ksh, &pinv);
+  const double tau = (cs.sigma[c - 1] * pinv_hi) * pinv;  // exact: power-of-two factors
   if (tid < kw) {
     const int j = j0 + tid;
     const double d = tot[tid];
-    H[j + (size_t)ldh * (c - 1)] = sigma[j] * sp * d;
-    coef[tid] = sigma[j] * sigma[j] * d;
+    H[j + (size_t)ldh * (c - 1)] = cs.sigma[j] * tau * d;
+    coef[tid] = cs.sigma[j] * cs.sigma[j] * d;
   }
   if (tid == 0) {
-    wn2[c] = sp * sp * tot[kMaxWindow];
+    wn2[c] = tau * tau * tot[kMaxWindow];
+    cs.scl[c] = tau;
     *counter = 0;
   }
 }
 
-cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0, int kw, const double* sigma,
+cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0, int kw, ColScale cs,
                              double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
                              DevState* st, cudaStream_t s) {
   static int occ = 0;
@@ -180,7 +191,7 @@ cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0,
   const int need = (A.n + kSpmvTile - 1) / kSpmvTile;
   int grid = sm_count() * occ;
   if (need < grid) grid = need < 1 ? 1 : need;
-  k_spmv_dots<<<grid, kThreads, smem, s>>>(A, W, ld, c, j0, kw, sigma, H, ldh, coef, wn2, part, counter, st);
+  k_spmv_dots<<<grid, kThreads, smem, s>>>(A, W, ld, c, j0, kw, cs, H, ldh, coef, wn2, part, counter, st);
   return cudaGetLastError();
 }
 
@@ -355,7 +366,7 @@ constexpr int kModeInit = 2;
 template <int SK>
 __global__ __launch_bounds__(kThreads) void k_update(int n, double* __restrict__ W, int64_t ld, int c, int j0, int nc,
                                                       const double* __restrict__ coef, double* __restrict__ H, int ldh,
-                                                      double* __restrict__ sigma, const double* __restrict__ wn2,
+                                                      ColScale cs, const double* __restrict__ wn2,
                                                       int mode, double* __restrict__ part,
                                                       unsigned* __restrict__ counter, SketchDev sk, DevState* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -439,13 +450,15 @@ __global__ __launch_bounds__(kThreads) void k_update(int n, double* __restrict__
       } else if (h == 0.0) {
         st->m_used = 0;
         st->stop = 1;
-        sigma[0] = 0.0;
+        cs.sigma[0] = 0.0;
+        cs.shf[0] = 0;
       } else {
-        sigma[0] = 1.0 / h;
+        cs.sigma[0] = 1.0 / h;
+        cs.shf[0] = exponent_of(cs.sigma[0]);
       }
     } else {
-      // the stored column is W_c = w' / sigma_{c-1}: h_{c,c-1} = ||w'|| = sigma_{c-1} ||W_c||
-      const double hc = sigma[c - 1] * h;
+      // the stored column is W_c = w' / scl[c]: h_{c,c-1} = ||w'|| = scl[c] ||W_c||
+      const double hc = cs.scl[c] * h;
       H[c + (size_t)ldh * (c - 1)] = hc;
       if (!isfinite(hc)) {
         st->status = FAB_ENUMERIC;
@@ -453,9 +466,11 @@ __global__ __launch_bounds__(kThreads) void k_update(int n, double* __restrict__
       } else if (!(hc > 64.0 * DBL_EPSILON * sqrt(wn2[c]))) {
         st->m_used = c;  // the basis spans an invariant subspace
         st->stop = 1;
-        sigma[c] = 0.0;
+        cs.sigma[c] = 0.0;
+        cs.shf[c] = 0;
       } else {
-        sigma[c] = 1.0 / h;
+        cs.sigma[c] = 1.0 / h;
+        cs.shf[c] = exponent_of(cs.sigma[c]);
       }
     }
     *counter = 0;
@@ -471,7 +486,7 @@ size_t update_smem_bytes(int kind, int nc, int s) {
 }
 
 cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
-                          int ldh, double* sigma, const double* wn2, int mode, double* part, unsigned* counter,
+                          int ldh, ColScale cs, const double* wn2, int mode, double* part, unsigned* counter,
                           SketchDev& sk, DevState* st, cudaStream_t s) {
   const size_t smem = update_smem_bytes(sk.kind, nc, sk.s);
   const int nchunks = (n + kChunk - 1) / kChunk;
@@ -486,15 +501,15 @@ cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, c
   sk.nparts = grid;  // one sketch partial per block
   switch (sk.kind) {
     case SK_SRHT:
-      k_update<SK_SRHT><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, sigma, wn2, mode, part,
+      k_update<SK_SRHT><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, cs, wn2, mode, part,
                                                       counter, sk, st);
       break;
     case SK_SPARSE:
-      k_update<SK_SPARSE><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, sigma, wn2, mode, part,
+      k_update<SK_SPARSE><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, cs, wn2, mode, part,
                                                         counter, sk, st);
       break;
     default:
-      k_update<SK_NONE><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, sigma, wn2, mode, part,
+      k_update<SK_NONE><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, cs, wn2, mode, part,
                                                       counter, sk, st);
   }
   return cudaGetLastError();

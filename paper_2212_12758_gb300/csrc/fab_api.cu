@@ -131,7 +131,7 @@ struct fab_handle {
   double* d_vals = nullptr;
   int64_t ld = 0;
   // workspace
-  Buf W, H, sigma, wn2, coef, part, counter, gpart, skpart, SV, P, qr, tau, y, cvec, dense, piv, scal, lsq, u, xbuf,
+  Buf W, H, sigma, shf, scl, wn2, coef, part, counter, gpart, skpart, SV, P, qr, tau, y, cvec, dense, piv, scal, lsq, u, xbuf,
       state;
   // cached SRHT sample
   int64_t P_npad = -1;
@@ -234,7 +234,7 @@ void fab_destroy(fab_handle* h) {
   cudaFree(h->d_rowptr);
   cudaFree(h->d_colind);
   cudaFree(h->d_vals);
-  Buf* bufs[] = {&h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
+  Buf* bufs[] = {&h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
                  &h->skpart, &h->SV, &h->P,     &h->qr,  &h->tau,  &h->y,    &h->cvec,    &h->dense,
                  &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state};
   for (Buf* b : bufs)
@@ -310,6 +310,7 @@ int validate(const fab_handle* h, const fab_params* p) {
 }
 
 struct Ws {
+  ColScale cs;
   double *W, *H, *sigma, *wn2, *coef, *part, *gpart, *skpart, *SV, *qr, *tau, *y, *cvec, *scal, *u, *xbuf;
   double* mats[9];
   double *lv_v, *lv_w, *lv_x, *lv_z, *lv_coef, *lv_q, *unorm2, *one;
@@ -332,6 +333,8 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
       {&h->W, ld * (m + 1) * 8},
       {&h->H, (size_t)(m + 1) * m * 8},
       {&h->sigma, (size_t)(m + 1) * 8},
+      {&h->shf, (size_t)(m + 1) * 4},
+      {&h->scl, (size_t)(m + 1) * 8},
       {&h->wn2, (size_t)(m + 1) * 8},
       {&h->coef, (size_t)(m + 1) * 8},
       {&h->part, part_blocks * (kMaxWindow + 1) * 8},
@@ -362,6 +365,7 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
   ws.W = ptr<double>(h->W);
   ws.H = ptr<double>(h->H);
   ws.sigma = ptr<double>(h->sigma);
+  ws.cs = ColScale{ptr<double>(h->sigma), ptr<int>(h->shf), ptr<double>(h->scl)};
   ws.wn2 = ptr<double>(h->wn2);
   ws.coef = ptr<double>(h->coef);
   ws.part = ptr<double>(h->part);
@@ -526,27 +530,27 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   none.kind = SK_NONE;
 
   // start vector: ||b||, sigma_0, sketch of b
-  LK(PK_UPDATE, launch_update(n, ws.W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, 1 | 2, ws.part, ws.counter,
+  LK(PK_UPDATE, launch_update(n, ws.W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1 | 2, ws.part, ws.counter,
                    sk_on ? sk : none, ws.st, s));
   if (sk_on) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
 
   const int ntiles = (n + kTileRows - 1) / kTileRows;
   for (int c = 1; c <= m; ++c) {
     if (p->method == FAB_ARNOLDI) {
-      LK(PK_SPMV, launch_spmv_dots(A, ws.W, ld, c, 0, 0, ws.sigma, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
+      LK(PK_SPMV, launch_spmv_dots(A, ws.W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
       double* Hcol = ws.H + (size_t)ldh * (c - 1);
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
         LK(PK_GEMVT, launch_gemv_t(n, ws.W, ld, 0, c, ws.W + (size_t)c * ld, ws.gpart, ntiles, ws.st, s));
-        LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, c, ws.sigma, 0, ws.sigma + (c - 1), Hcol, pass, ws.coef,
+        LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, c, ws.sigma, 0, ws.cs.scl + c, Hcol, pass, ws.coef,
                                         ws.st, s));
-        LK(PK_UPDATE, launch_update(n, ws.W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, pass == 1 ? 1 : 0, ws.part,
+        LK(PK_UPDATE, launch_update(n, ws.W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, ws.wn2, pass == 1 ? 1 : 0, ws.part,
                          ws.counter, none, ws.st, s));
       }
     } else {
       const int j0 = std::max(0, c - k), kw = c - j0;
-      LK(PK_SPMV, launch_spmv_dots(A, ws.W, ld, c, j0, kw, ws.sigma, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
+      LK(PK_SPMV, launch_spmv_dots(A, ws.W, ld, c, j0, kw, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
                           s));
-      LK(PK_UPDATE, launch_update(n, ws.W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.sigma, ws.wn2, 1, ws.part, ws.counter,
+      LK(PK_UPDATE, launch_update(n, ws.W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part, ws.counter,
                        sk_on ? sk : none, ws.st, s));
       if (sk_on) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
     }
@@ -560,6 +564,7 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   h->last_m = m;
   h->last_s = sk_on ? p->s : 0;
   h->last_sketched = sk_on ? 1 : 0;
+  h->has_state = 1;  // the basis, H and the sketch can be inspected from here on
   int lsqr_iters = 0, fh_iters = 0;
   if (mu == 0) {  // b = 0
     CK(cudaMemsetAsync(ws.cvec, 0, (size_t)m * sizeof(double), s));
@@ -742,7 +747,7 @@ extern "C" int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t
   if (rc == FAB_OK && sk.kind == SK_SRHT && launch_srht_sample(next_pow2(n), s, rng_state(seed, 4), P, st) != cudaSuccess)
     rc = FAB_ECUDA;
   for (int j = 0; j < ncols && rc == FAB_OK; ++j) {
-    if (launch_update((int)n, const_cast<double*>(V_dev), ldv, j, 0, 0, nullptr, nullptr, 1, nullptr, nullptr, 0,
+    if (launch_update((int)n, const_cast<double*>(V_dev), ldv, j, 0, 0, nullptr, nullptr, 1, ColScale{}, nullptr, 0,
                       nullptr, nullptr, sk, ds, st) != cudaSuccess ||
         launch_sketch_reduce(sk, nullptr, 0, scale, out_dev + (size_t)j * s, ds, st) != cudaSuccess)
       rc = FAB_ECUDA;

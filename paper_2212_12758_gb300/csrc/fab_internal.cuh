@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/fab.h"
 
@@ -127,6 +128,25 @@ __device__ __forceinline__ void sum_partials(const double* part, int nblocks, in
   }
 }
 
+// y * 2^k, exact: integer addition to the exponent field for normal results;
+// zeros, subnormals and out-of-range exponents take the FP64 multiply.
+__device__ __forceinline__ double scale_pow2(double y, int k, double p2k) {
+  const long long b = __double_as_longlong(y);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0 || e + k <= 0 || e + k >= 2047) return y * p2k;
+  return __longlong_as_double(b + ((long long)k << 52));
+}
+// Unbiased exponent of a positive normal double (floor(log2 x)).
+__host__ __device__ __forceinline__ int exponent_of(double x) {
+#ifdef __CUDA_ARCH__
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF) - 1023;
+#else
+  long long b;
+  memcpy(&b, &x, 8);
+  return (int)((b >> 52) & 0x7FF) - 1023;
+#endif
+}
+
 // 2^e as a double for e in [-1074, 1023], without FP64 arithmetic on the value.
 __device__ __forceinline__ double pow2_split(int e, double* second) {
   // returns a and sets *second = b with a*b = 2^e and both normal doubles
@@ -191,11 +211,19 @@ struct Csr {
 };
 
 cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s);
-cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0, int kw, const double* sigma,
+// Column bookkeeping of the raw basis (see basis.cu): sigma[j] = 1/||W_j||,
+// shf[j] = floor(log2 sigma[j]) (the exact power of two applied when W_j is the
+// SpMV input), scl[c] = sigma[c-1] 2^-shf[c-1] in [1, 2) (A v_{c-1} = scl[c] W_c).
+struct ColScale {
+  double* sigma;
+  int* shf;
+  double* scl;
+};
+cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0, int kw, ColScale cs,
                              double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
                              DevState* st, cudaStream_t s);
 cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
-                          int ldh, double* sigma, const double* wn2, int mode, double* part, unsigned* counter,
+                          int ldh, ColScale cs, const double* wn2, int mode, double* part, unsigned* counter,
                           SketchDev& sk, DevState* st, cudaStream_t s);
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
                                  DevState* st, cudaStream_t s);
