@@ -51,6 +51,7 @@ constexpr int kSpmvCap = 2048;       // nonzeros per stage (vals 16 KB + colind 
 
 size_t spmv_smem_bytes() { return (size_t)2 * kSpmvCap * (sizeof(double) + sizeof(int)); }
 
+template <int KW>
 __global__ __launch_bounds__(kThreads) void k_spmv_dots(
     Csr A, double* __restrict__ W, int64_t ld, int c, int j0, int kw, ColScale cs, double* __restrict__ H,
     int ldh, double* __restrict__ coef, double* __restrict__ wn2, double* __restrict__ part,
@@ -125,20 +126,36 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
     const int r = tile * kSpmvTile + tid;
     if (r < A.n) {
       const int e0 = A.rowptr[r], e1 = A.rowptr[r + 1];
+      double wv[KW > 0 ? KW : 1];
+#pragma unroll
+      for (int q = 0; q < KW; ++q) wv[q] = W[(size_t)(j0 + q) * ld + r];  // window entries, issued early
       double y = 0.0;
       if (staged) {
         const int base = s_e0[stg];
-        const double* sv = s_vals + stg * kSpmvCap;
-        const int* sc = s_col + stg * kSpmvCap;
-        for (int e = e0 - base; e < e1 - base; ++e) y = fma(sv[e], __ldg(vin + sc[e]), y);
+        const double* sv = s_vals + stg * kSpmvCap - base;
+        const int* sc = s_col + stg * kSpmvCap - base;
+        int e = e0;
+        for (; e + 8 <= e1; e += 8) {  // eight gathers in flight per thread
+          double g[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) g[u] = __ldg(vin + sc[e + u]);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) y = fma(sv[e + u], g[u], y);
+        }
+        const int rem = e1 - e;
+        double g[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) g[u] = (u < rem) ? __ldg(vin + sc[e + u]) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (u < rem) y = fma(sv[e + u], g[u], y);
       } else {
         for (int e = e0; e < e1; ++e) y = fma(__ldg(A.vals + e), __ldg(vin + __ldg(A.colind + e)), y);
       }
       y = scale_pow2(y, ksh, p2k);
       wout[r] = y;
 #pragma unroll
-      for (int q = 0; q < kMaxWindow; ++q)
-        if (q < kw) acc[q] = fma(W[(size_t)(j0 + q) * ld + r], y, acc[q]);
+      for (int q = 0; q < KW; ++q) acc[q] = fma(wv[q], y, acc[q]);
       acc[kMaxWindow] = fma(y, y, acc[kMaxWindow]);
     }
     __syncthreads();  // every thread is done with buffer stg before it is refilled
@@ -181,18 +198,23 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
 cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0, int kw, ColScale cs,
                              double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
                              DevState* st, cudaStream_t s) {
-  static int occ = 0;
+  static const void* fns[kMaxWindow + 1] = {
+      (const void*)k_spmv_dots<0>, (const void*)k_spmv_dots<1>, (const void*)k_spmv_dots<2>,
+      (const void*)k_spmv_dots<3>, (const void*)k_spmv_dots<4>, (const void*)k_spmv_dots<5>,
+      (const void*)k_spmv_dots<6>, (const void*)k_spmv_dots<7>, (const void*)k_spmv_dots<8>};
+  static int occ[kMaxWindow + 1] = {0};
+  if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
   const size_t smem = spmv_smem_bytes();
-  if (occ == 0) {
-    cudaFuncSetAttribute(k_spmv_dots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv_dots, kThreads, smem);
-    if (occ < 1) occ = 1;
+  if (occ[kw] == 0) {
+    cudaFuncSetAttribute(fns[kw], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kw], fns[kw], kThreads, smem);
+    if (occ[kw] < 1) occ[kw] = 1;
   }
   const int need = (A.n + kSpmvTile - 1) / kSpmvTile;
-  int grid = sm_count() * occ;
+  int grid = sm_count() * occ[kw];
   if (need < grid) grid = need < 1 ? 1 : need;
-  k_spmv_dots<<<grid, kThreads, smem, s>>>(A, W, ld, c, j0, kw, cs, H, ldh, coef, wn2, part, counter, st);
-  return cudaGetLastError();
+  void* args[] = {(void*)&A, &W, &ld, &c, &j0, &kw, &cs, &H, &ldh, &coef, &wn2, &part, &counter, &st};
+  return cudaLaunchKernel(fns[kw], dim3(grid), dim3(kThreads), args, smem, s);
 }
 
 // ---------------------------------------------- exact int64 chunk sketches
@@ -364,7 +386,7 @@ constexpr int kModeNorm = 1;
 constexpr int kModeInit = 2;
 
 template <int SK>
-__global__ __launch_bounds__(kThreads) void k_update(int n, double* __restrict__ W, int64_t ld, int c, int j0, int nc,
+__global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(int n, double* __restrict__ W, int64_t ld, int c, int j0, int nc,
                                                       const double* __restrict__ coef, double* __restrict__ H, int ldh,
                                                       ColScale cs, const double* __restrict__ wn2,
                                                       int mode, double* __restrict__ part,

@@ -130,11 +130,12 @@ __device__ __forceinline__ void sum_partials(const double* part, int nblocks, in
 
 // y * 2^k, exact: integer addition to the exponent field for normal results;
 // zeros, subnormals and out-of-range exponents take the FP64 multiply.
+static __device__ __noinline__ double scale_pow2_slow(double y, double p2k) { return y * p2k; }
 __device__ __forceinline__ double scale_pow2(double y, int k, double p2k) {
   const long long b = __double_as_longlong(y);
   const int e = (int)((b >> 52) & 0x7FF);
-  if (e == 0 || e + k <= 0 || e + k >= 2047) return y * p2k;
-  return __longlong_as_double(b + ((long long)k << 52));
+  if (e != 0 && e + k > 0 && e + k < 2047) return __longlong_as_double(b + ((long long)k << 52));
+  return scale_pow2_slow(y, p2k);  // out of line: keeps the common path free of FP64 work
 }
 // Unbiased exponent of a positive normal double (floor(log2 x)).
 __host__ __device__ __forceinline__ int exponent_of(double x) {
