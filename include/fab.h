@@ -26,7 +26,9 @@
  *   FAB_SK_SPARSE_SIGN  zeta nonzeros +-1/sqrt(zeta) per column (paper §2.1.1).
  *   FAB_SK_SRHT         s^{-1/2} P H D on the input zero-padded to n' = 2^ceil(log2 n)
  *                       (paper §2.1.1).
- *   FAB_SK_GAUSSIAN     reserved (dense N(0,1/s)); fab_apply returns FAB_EINVAL.
+ *   FAB_SK_GAUSSIAN     dense N(0, 1/s) entries, rounded to BF16 (stream 5, Box-Muller);
+ *                       applied to a BF16 copy of the basis on the tensor cores with FP32
+ *                       accumulation. fab_apply accepts it with FAB_MIXED and m+1 <= 256.
  *
  * Conventions for every entry point:
  *   - Return FAB_OK (0) or a negative FAB_E* code; nothing throws across the ABI.
@@ -72,7 +74,8 @@ typedef struct fab_params {
   int sketch;        /* fab_sketch                                                 */
   uint64_t seed;     /* sketch seed                                                */
   int method;        /* fab_method                                                 */
-  int precision;     /* fab_precision; only FAB_FP64 is accepted by this version   */
+  int precision;     /* fab_precision: FAB_FP64, or FAB_MIXED (FP32 A and basis, BF16 */
+                     /* Gaussian sketch, FP64 small stage)                          */
   double lsqr_tol;   /* LSQR stopping tolerance (paper §5 uses 1e-6)               */
   int lsqr_maxit;    /* LSQR iteration limit (0: 4m)                               */
   void* stream;      /* cudaStream_t to run on, or NULL                            */
@@ -155,9 +158,11 @@ int fab_last_basis(fab_handle* h, double* V, int dst_on_device);
  *   V_dev   device array, column j at V_dev + j*ldv, ldv >= n
  *   out_dev device array s x ncols, column-major, ld = s
  *   stream  cudaStream_t or NULL
- * Uses the same fused kernels as the basis loop (exact int64 block transform
- * per 4096-row chunk, FP64 cross-chunk sums). Allocates its scratch with
- * cudaMallocAsync on the stream and synchronizes the stream before returning.
+ * Sign sketches use the same fused kernels as the basis loop (exact int64 block
+ * transform per 4096-row chunk, FP64 cross-chunk sums); the Gaussian sketch
+ * rounds the columns to BF16 and multiplies on the tensor cores (ncols <= 256).
+ * Allocates its scratch with cudaMallocAsync on the stream and synchronizes the
+ * stream before returning.
  */
 int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t seed,
                      const double* V_dev, int64_t ldv, int ncols, double* out_dev, void* stream);

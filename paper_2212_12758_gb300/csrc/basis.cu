@@ -11,11 +11,36 @@
 #include <float.h>
 #include <limits.h>
 
+#include <cuda_bf16.h>
+
 #include "fab_internal.cuh"
 
 namespace fab {
 
 int sm_count();
+
+// Floating-point layout of the basis element type (FP64 path / FP32 mixed path).
+template <typename T>
+struct Fp;
+template <>
+struct Fp<double> {
+  static constexpr int kMant = 52, kExpMax = 0x7FF;
+  static constexpr int kFixOff = 1071;  // chunk fixed point: x = X * 2^(E - kFixOff)
+  __device__ static unsigned long long bits(double x) { return (unsigned long long)__double_as_longlong(x); }
+};
+template <>
+struct Fp<float> {
+  static constexpr int kMant = 23, kExpMax = 0xFF;
+  static constexpr int kFixOff = 175;
+  __device__ static unsigned long long bits(float x) { return (unsigned long long)(unsigned)__float_as_uint(x); }
+};
+
+__device__ __forceinline__ float scale_pow2(float y, int k, float p2k) {
+  const unsigned b = __float_as_uint(y);
+  const int e = (int)((b >> 23) & 0xFF);
+  if (e != 0 && e + k > 0 && e + k < 255) return __uint_as_float(b + ((unsigned)k << 23));
+  return y * p2k;
+}
 
 // ------------------------------------------------------------------- state
 __global__ void k_state_reset(DevState* st, int m) {
@@ -49,17 +74,16 @@ cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s) {
 constexpr int kSpmvTile = kThreads;  // rows per tile, one per thread
 constexpr int kSpmvCap = 2048;       // nonzeros per stage (vals 16 KB + colind 8 KB)
 
-size_t spmv_smem_bytes() { return (size_t)2 * kSpmvCap * (sizeof(double) + sizeof(int)); }
-
-template <int KW>
+template <typename TV, int KW>
 __global__ __launch_bounds__(kThreads) void k_spmv_dots(
-    Csr A, double* __restrict__ W, int64_t ld, int c, int j0, int kw, ColScale cs, double* __restrict__ H,
+    Csr A, TV* __restrict__ W, int64_t ld, int c, int j0, int kw, ColScale cs, double* __restrict__ H,
     int ldh, double* __restrict__ coef, double* __restrict__ wn2, double* __restrict__ part,
     unsigned* __restrict__ counter, DevState* st) {
   constexpr int NV = kMaxWindow + 1;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  double* s_vals = reinterpret_cast<double*>(smem_raw);                        // [2][kSpmvCap]
-  int* s_col = reinterpret_cast<int*>(smem_raw + 2 * kSpmvCap * sizeof(double));  // [2][kSpmvCap]
+  TV* s_vals = reinterpret_cast<TV*>(smem_raw);                                // [2][kSpmvCap]
+  int* s_col = reinterpret_cast<int*>(smem_raw + 2 * kSpmvCap * sizeof(TV));   // [2][kSpmvCap]
+  const TV* Avals = reinterpret_cast<const TV*>(A.vals);
   __shared__ __align__(8) uint64_t s_bar[2];
   __shared__ int s_e0[2];
   __shared__ int s_staged[2];
@@ -68,15 +92,15 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
   if (st->stop) return;
   const int tid = threadIdx.x;
   const int ntiles = (A.n + kSpmvTile - 1) / kSpmvTile;
-  const double* vin = W + (size_t)(c - 1) * ld;
-  double* wout = W + (size_t)c * ld;
+  const TV* vin = W + (size_t)(c - 1) * ld;
+  TV* wout = W + (size_t)c * ld;
   const int ksh = cs.shf[c - 1];
-  double p2k;
-  const double p2k_hi = pow2_split(ksh, &p2k);
-  p2k *= p2k_hi;  // 2^ksh (only used for zeros / subnormals)
-  double acc[NV];
+  double p2k_lo;
+  const double p2k_hi = pow2_split(ksh, &p2k_lo);
+  const TV p2k = (TV)(p2k_hi * p2k_lo);  // 2^ksh (only used for zeros / subnormals)
+  TV acc[NV];  // per-thread partial sums (FP32 rows for the mixed path, FP64 across threads)
 #pragma unroll
-  for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+  for (int q = 0; q < NV; ++q) acc[q] = (TV)0;
   if (tid == 0) {
     mbar_init(&s_bar[0], 1);
     mbar_init(&s_bar[1], 1);
@@ -96,8 +120,8 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
       s_e0[stg] = e0a;
       s_staged[stg] = 1;
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&s_bar[stg], (uint32_t)cnt * 12u);
-      bulk_copy_g2s(s_vals + stg * kSpmvCap, A.vals + e0a, (uint32_t)cnt * 8u, &s_bar[stg]);
+      mbar_arrive_expect_tx(&s_bar[stg], (uint32_t)cnt * (uint32_t)(sizeof(TV) + 4));
+      bulk_copy_g2s(s_vals + stg * kSpmvCap, Avals + e0a, (uint32_t)cnt * (uint32_t)sizeof(TV), &s_bar[stg]);
       bulk_copy_g2s(s_col + stg * kSpmvCap, A.colind + e0a, (uint32_t)cnt * 4u, &s_bar[stg]);
     } else {
       s_staged[stg] = 0;
@@ -126,31 +150,31 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
     const int r = tile * kSpmvTile + tid;
     if (r < A.n) {
       const int e0 = A.rowptr[r], e1 = A.rowptr[r + 1];
-      double wv[KW > 0 ? KW : 1];
+      TV wv[KW > 0 ? KW : 1];
 #pragma unroll
       for (int q = 0; q < KW; ++q) wv[q] = W[(size_t)(j0 + q) * ld + r];  // window entries, issued early
-      double y = 0.0;
+      TV y = (TV)0;
       if (staged) {
         const int base = s_e0[stg];
-        const double* sv = s_vals + stg * kSpmvCap - base;
+        const TV* sv = s_vals + stg * kSpmvCap - base;
         const int* sc = s_col + stg * kSpmvCap - base;
         int e = e0;
         for (; e + 8 <= e1; e += 8) {  // eight gathers in flight per thread
-          double g[8];
+          TV g[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) g[u] = __ldg(vin + sc[e + u]);
 #pragma unroll
           for (int u = 0; u < 8; ++u) y = fma(sv[e + u], g[u], y);
         }
         const int rem = e1 - e;
-        double g[8];
+        TV g[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) g[u] = (u < rem) ? __ldg(vin + sc[e + u]) : 0.0;
+        for (int u = 0; u < 8; ++u) g[u] = (u < rem) ? __ldg(vin + sc[e + u]) : (TV)0;
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           if (u < rem) y = fma(sv[e + u], g[u], y);
       } else {
-        for (int e = e0; e < e1; ++e) y = fma(__ldg(A.vals + e), __ldg(vin + __ldg(A.colind + e)), y);
+        for (int e = e0; e < e1; ++e) y = fma(__ldg(Avals + e), __ldg(vin + __ldg(A.colind + e)), y);
       }
       y = scale_pow2(y, ksh, p2k);
       wout[r] = y;
@@ -172,10 +196,13 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
     __syncthreads();
     return;
   }
-  block_sum<NV>(acc, sh);
+  double accd[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) accd[q] = (double)acc[q];
+  block_sum<NV>(accd, sh);
   if (tid == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) part[(size_t)blockIdx.x * NV + q] = acc[q];
+    for (int q = 0; q < NV; ++q) part[(size_t)blockIdx.x * NV + q] = accd[q];
   }
   if (!last_block(counter)) return;
   sum_partials(part, gridDim.x, NV, tot, sh);
@@ -195,16 +222,17 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
   }
 }
 
-cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0, int kw, ColScale cs,
+template <typename TV>
+cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int kw, ColScale cs,
                              double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
                              DevState* st, cudaStream_t s) {
   static const void* fns[kMaxWindow + 1] = {
-      (const void*)k_spmv_dots<0>, (const void*)k_spmv_dots<1>, (const void*)k_spmv_dots<2>,
-      (const void*)k_spmv_dots<3>, (const void*)k_spmv_dots<4>, (const void*)k_spmv_dots<5>,
-      (const void*)k_spmv_dots<6>, (const void*)k_spmv_dots<7>, (const void*)k_spmv_dots<8>};
+      (const void*)k_spmv_dots<TV, 0>, (const void*)k_spmv_dots<TV, 1>, (const void*)k_spmv_dots<TV, 2>,
+      (const void*)k_spmv_dots<TV, 3>, (const void*)k_spmv_dots<TV, 4>, (const void*)k_spmv_dots<TV, 5>,
+      (const void*)k_spmv_dots<TV, 6>, (const void*)k_spmv_dots<TV, 7>, (const void*)k_spmv_dots<TV, 8>};
   static int occ[kMaxWindow + 1] = {0};
   if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
-  const size_t smem = spmv_smem_bytes();
+  const size_t smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
   if (occ[kw] == 0) {
     cudaFuncSetAttribute(fns[kw], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kw], fns[kw], kThreads, smem);
@@ -216,6 +244,10 @@ cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0,
   void* args[] = {(void*)&A, &W, &ld, &c, &j0, &kw, &cs, &H, &ldh, &coef, &wn2, &part, &counter, &st};
   return cudaLaunchKernel(fns[kw], dim3(grid), dim3(kThreads), args, smem, s);
 }
+template cudaError_t launch_spmv_dots<double>(const Csr&, double*, int64_t, int, int, int, ColScale, double*, int,
+                                              double*, double*, double*, unsigned*, DevState*, cudaStream_t);
+template cudaError_t launch_spmv_dots<float>(const Csr&, float*, int64_t, int, int, int, ColScale, double*, int,
+                                             double*, double*, double*, unsigned*, DevState*, cudaStream_t);
 
 // ---------------------------------------------- exact int64 chunk sketches
 // A chunk of 4096 consecutive rows is converted to a common block exponent:
@@ -225,21 +257,30 @@ cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0,
 // the rounding of x to X (relative 2^-49 of the chunk maximum) and of the
 // final int64 -> FP64 conversion, and it does not depend on summation order.
 
-__device__ __forceinline__ int exp_field(double x) {
-  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+template <typename T>
+__device__ __forceinline__ int exp_field(T x) {
+  return (int)((Fp<T>::bits(x) >> Fp<T>::kMant) & Fp<T>::kExpMax);
 }
 
-__device__ __forceinline__ long long to_fixed(double x, int E) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-  const int ef = (int)((bits >> 52) & 0x7FF);
-  const unsigned long long mant = bits & ((1ull << 52) - 1);
-  const unsigned long long M = ef ? (mant | (1ull << 52)) : mant;
+// x (FP64 or FP32) as X with x = X 2^(E - kFixOff), |X| < 2^49, rounded to nearest.
+template <typename T>
+__device__ __forceinline__ long long to_fixed(T x, int E) {
+  constexpr int P = Fp<T>::kMant;  // stored mantissa bits
+  const unsigned long long bits = Fp<T>::bits(x);
+  const int ef = (int)((bits >> P) & Fp<T>::kExpMax);
+  const unsigned long long M = ef ? ((bits & ((1ull << P) - 1)) | (1ull << P)) : (bits & ((1ull << P) - 1));
   const int eff = ef ? ef : 1;
-  int sh = E - eff + 4;
-  if (sh > 63) sh = 63;
-  if (sh < 1) sh = 1;  // only when E == 0 (all entries zero or subnormal)
-  const long long X = (long long)((M + (1ull << (sh - 1))) >> sh);
-  return (bits >> 63) ? -X : X;
+  // X = M 2^(eff - E - (P - 48)): a left shift for FP32 (exact), a right shift for FP64
+  const int L = eff - E + 48 - P;
+  long long X;
+  if (L >= 0) {
+    X = (long long)(M << L);
+  } else {
+    int sh = -L;
+    if (sh > 63) sh = 63;
+    X = (long long)((M + (1ull << (sh - 1))) >> sh);
+  }
+  return ((bits >> (sizeof(T) * 8 - 1)) & 1ull) ? -X : X;
 }
 
 __device__ __forceinline__ int pidx(int j) { return j + (j >> 4); }  // bank-conflict padding
@@ -272,7 +313,8 @@ __device__ __forceinline__ int block_max_int(int v, int* sh) {
 
 // SRHT chunk: y = H_4096 (D x_chunk); writes y at the sampled in-chunk rows.
 // Thread t holds rows i*256 + t (i = 0..15) of the chunk.
-__device__ void sketch_chunk_srht(const double (&v)[kRowsPerThread], int chunk, const SketchDev& sk,
+template <typename TV>
+__device__ void sketch_chunk_srht(const TV (&v)[kRowsPerThread], int chunk, const SketchDev& sk,
                                   long long* buf, const int* s_P, double* s_acc, int* s_int) {
   const int t = threadIdx.x;
   int e = 0;
@@ -306,7 +348,7 @@ __device__ void sketch_chunk_srht(const double (&v)[kRowsPerThread], int chunk, 
   for (int q = 0; q < 16; ++q) buf[pidx(base3 + q * 16)] = X[q];
   __syncthreads();
   double b;
-  const double a = pow2_split(E - 1071, &b);
+  const double a = pow2_split(E - Fp<TV>::kFixOff, &b);
   // cross-chunk Hadamard factor (-1)^popcount(rh_q & chunk), rh_q = P_q >> 12
   for (int q = t; q < sk.s; q += kThreads) {
     const int p = s_P[q];
@@ -317,7 +359,8 @@ __device__ void sketch_chunk_srht(const double (&v)[kRowsPerThread], int chunk, 
 }
 
 // Sparse-sign chunk: every row j scatters +-X_j into its zeta sketch rows.
-__device__ void sketch_chunk_sparse(const double (&v)[kRowsPerThread], int chunk, int n, const SketchDev& sk,
+template <typename TV>
+__device__ void sketch_chunk_sparse(const TV (&v)[kRowsPerThread], int chunk, int n, const SketchDev& sk,
                                     unsigned long long* acc, double* s_acc, int* s_int) {
   const int t = threadIdx.x;
   int e = 0;
@@ -369,7 +412,7 @@ __device__ void sketch_chunk_sparse(const double (&v)[kRowsPerThread], int chunk
   }
   __syncthreads();
   double b;
-  const double a = pow2_split(E - 1071, &b);
+  const double a = pow2_split(E - Fp<TV>::kFixOff, &b);
   for (int q = t; q < sk.s; q += kThreads) {
     s_acc[q] += ((double)(long long)acc[q] * a) * b;
     acc[q] = 0ull;
@@ -385,8 +428,8 @@ __device__ void sketch_chunk_sparse(const double (&v)[kRowsPerThread], int chunk
 constexpr int kModeNorm = 1;
 constexpr int kModeInit = 2;
 
-template <int SK>
-__global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(int n, double* __restrict__ W, int64_t ld, int c, int j0, int nc,
+template <int SK, typename TV>
+__global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(int n, TV* __restrict__ W, int64_t ld, int c, int j0, int nc,
                                                       const double* __restrict__ coef, double* __restrict__ H, int ldh,
                                                       ColScale cs, const double* __restrict__ wn2,
                                                       int mode, double* __restrict__ part,
@@ -396,47 +439,49 @@ __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(in
   __shared__ double tot[1];
   __shared__ int s_int[32];
   if (st->stop) return;
-  double* s_coef = reinterpret_cast<double*>(smem_raw);  // nc doubles
+  TV* s_coef = reinterpret_cast<TV*>(smem_raw);  // nc coefficients
   double* s_acc = reinterpret_cast<double*>(smem_raw + ((size_t)nc * 8 + 15) / 16 * 16);  // s doubles
-  unsigned char* after = reinterpret_cast<unsigned char*>(s_acc) + ((size_t)(SK == SK_NONE ? 0 : sk.s) * 8 + 15) / 16 * 16;
+  const bool sk_acc = (SK == SK_SRHT || SK == SK_SPARSE);
+  unsigned char* after = reinterpret_cast<unsigned char*>(s_acc) + ((size_t)(sk_acc ? sk.s : 0) * 8 + 15) / 16 * 16;
   long long* buf = reinterpret_cast<long long*>(after);                     // SRHT: pidx(4096) int64
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(after);   // sparse: s uint64
   int* s_P = reinterpret_cast<int*>(after + (size_t)(kChunk + kChunk / 16) * 8);  // SRHT: s ints
-  for (int i = threadIdx.x; i < nc; i += kThreads) s_coef[i] = coef[i];
-  if (SK != SK_NONE)
+  for (int i = threadIdx.x; i < nc; i += kThreads) s_coef[i] = (TV)coef[i];
+  if (sk_acc)
     for (int q = threadIdx.x; q < sk.s; q += kThreads) s_acc[q] = 0.0;
   if (SK == SK_SRHT)
     for (int q = threadIdx.x; q < sk.s; q += kThreads) s_P[q] = sk.P[q];
   if (SK == SK_SPARSE)
     for (int q = threadIdx.x; q < sk.s; q += kThreads) acc[q] = 0ull;
   __syncthreads();
-  double* wc = W + (size_t)c * ld;
-  const double* Wb = W + (size_t)j0 * ld;
+  TV* wc = W + (size_t)c * ld;
+  const TV* Wb = W + (size_t)j0 * ld;
   double nrm = 0.0;
   const int nchunks = (n + kChunk - 1) / kChunk;
   for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const int base = chunk * kChunk + threadIdx.x;
-    double v[kRowsPerThread];
+    TV v[kRowsPerThread];
+    TV nrm_c = (TV)0;  // this chunk's share in the element type, added to nrm in FP64
     if ((chunk + 1) * kChunk <= n) {
 #pragma unroll
       for (int i = 0; i < kRowsPerThread; ++i) v[i] = wc[base + i * kThreads];
       for (int q = 0; q < nc; ++q) {
-        const double cf = s_coef[q];
-        const double* col = Wb + (size_t)q * ld + base;
+        const TV cf = s_coef[q];
+        const TV* col = Wb + (size_t)q * ld + base;
 #pragma unroll
         for (int i = 0; i < kRowsPerThread; ++i) v[i] = fma(-cf, col[i * kThreads], v[i]);
       }
 #pragma unroll
       for (int i = 0; i < kRowsPerThread; ++i) {
         if (nc > 0) wc[base + i * kThreads] = v[i];
-        nrm = fma(v[i], v[i], nrm);
+        nrm_c = fma(v[i], v[i], nrm_c);
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < kRowsPerThread; ++i) v[i] = (base + i * kThreads < n) ? wc[base + i * kThreads] : 0.0;
+      for (int i = 0; i < kRowsPerThread; ++i) v[i] = (base + i * kThreads < n) ? wc[base + i * kThreads] : (TV)0;
       for (int q = 0; q < nc; ++q) {
-        const double cf = s_coef[q];
-        const double* col = Wb + (size_t)q * ld + base;
+        const TV cf = s_coef[q];
+        const TV* col = Wb + (size_t)q * ld + base;
 #pragma unroll
         for (int i = 0; i < kRowsPerThread; ++i)
           if (base + i * kThreads < n) v[i] = fma(-cf, col[i * kThreads], v[i]);
@@ -445,14 +490,21 @@ __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(in
       for (int i = 0; i < kRowsPerThread; ++i) {
         if (base + i * kThreads < n) {
           if (nc > 0) wc[base + i * kThreads] = v[i];
-          nrm = fma(v[i], v[i], nrm);
+          nrm_c = fma(v[i], v[i], nrm_c);
         }
       }
     }
+    nrm += (double)nrm_c;
     if (SK == SK_SRHT) sketch_chunk_srht(v, chunk, sk, buf, s_P, s_acc, s_int);
     if (SK == SK_SPARSE) sketch_chunk_sparse(v, chunk, n, sk, acc, s_acc, s_int);
+    if (SK == SK_GAUSS) {  // BF16 copy of the column for the tensor-core Gaussian sketch
+      __nv_bfloat16* bc = sk.Wbf + (size_t)c * sk.ldbf;
+#pragma unroll
+      for (int i = 0; i < kRowsPerThread; ++i)
+        if (base + i * kThreads < n) bc[base + i * kThreads] = __float2bfloat16_rn((float)v[i]);
+    }
   }
-  if (SK != SK_NONE) {  // this block's share of the sketch (its chunks, fixed order)
+  if (sk_acc) {  // this block's share of the sketch (its chunks, fixed order)
     double* out = sk.part + (size_t)blockIdx.x * sk.s;
     for (int q = threadIdx.x; q < sk.s; q += kThreads) out[q] = s_acc[q];
   }
@@ -501,19 +553,25 @@ __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(in
 
 size_t update_smem_bytes(int kind, int nc, int s) {
   size_t b = ((size_t)nc * 8 + 15) / 16 * 16;
-  if (kind != SK_NONE) b += ((size_t)s * 8 + 15) / 16 * 16;
+  if (kind == SK_SRHT || kind == SK_SPARSE) b += ((size_t)s * 8 + 15) / 16 * 16;
   if (kind == SK_SRHT) b += (size_t)(kChunk + kChunk / 16) * 8 + (size_t)s * 4;
   if (kind == SK_SPARSE) b += (size_t)s * 8;
   return b;
 }
 
-cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
-                          int ldh, ColScale cs, const double* wn2, int mode, double* part, unsigned* counter,
-                          SketchDev& sk, DevState* st, cudaStream_t s) {
+template <typename TV>
+cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H, int ldh,
+                          ColScale cs, const double* wn2, int mode, double* part, unsigned* counter, SketchDev& sk,
+                          DevState* st, cudaStream_t s) {
   const size_t smem = update_smem_bytes(sk.kind, nc, sk.s);
   const int nchunks = (n + kChunk - 1) / kChunk;
-  const void* fn = sk.kind == SK_SRHT ? (const void*)k_update<SK_SRHT>
-                   : sk.kind == SK_SPARSE ? (const void*)k_update<SK_SPARSE> : (const void*)k_update<SK_NONE>;
+  const void* fn = nullptr;
+  switch (sk.kind) {
+    case SK_SRHT: fn = (const void*)k_update<SK_SRHT, TV>; break;
+    case SK_SPARSE: fn = (const void*)k_update<SK_SPARSE, TV>; break;
+    case SK_GAUSS: fn = (const void*)k_update<SK_GAUSS, TV>; break;
+    default: fn = (const void*)k_update<SK_NONE, TV>;
+  }
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
@@ -521,21 +579,16 @@ cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, c
   int grid = sm_count() * occ;
   if (nchunks < grid) grid = nchunks < 1 ? 1 : nchunks;
   sk.nparts = grid;  // one sketch partial per block
-  switch (sk.kind) {
-    case SK_SRHT:
-      k_update<SK_SRHT><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, cs, wn2, mode, part,
-                                                      counter, sk, st);
-      break;
-    case SK_SPARSE:
-      k_update<SK_SPARSE><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, cs, wn2, mode, part,
-                                                        counter, sk, st);
-      break;
-    default:
-      k_update<SK_NONE><<<grid, kThreads, smem, s>>>(n, W, ld, c, j0, nc, coef, H, ldh, cs, wn2, mode, part,
-                                                      counter, sk, st);
-  }
-  return cudaGetLastError();
+  void* args[] = {&n, &W, &ld, &c, &j0, &nc, (void*)&coef, &H, &ldh, &cs, (void*)&wn2, &mode, &part, &counter,
+                  &sk, &st};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, s);
 }
+template cudaError_t launch_update<double>(int, double*, int64_t, int, int, int, const double*, double*, int,
+                                           ColScale, const double*, int, double*, unsigned*, SketchDev&, DevState*,
+                                           cudaStream_t);
+template cudaError_t launch_update<float>(int, float*, int64_t, int, int, int, const double*, double*, int, ColScale,
+                                          const double*, int, double*, unsigned*, SketchDev&, DevState*,
+                                          cudaStream_t);
 
 // ---------------------------------------------- cross-block sketch reduce
 // out[q] = scale * sigma[col] * sum_blocks part[block][q] (the per-block partials
@@ -609,36 +662,44 @@ cudaError_t launch_srht_sample(int64_t npad, int s, uint64_t stP, int* P, cudaSt
 
 // ------------------------------------------------------------- GEMV-T pass
 // part[tile][q] = sum over the tile's rows of W_{j0+q}[r] x[r]; one warp per column.
-__global__ __launch_bounds__(kThreads) void k_gemv_t(int n, const double* __restrict__ W, int64_t ld, int j0, int nc,
-                                                      const double* __restrict__ x, double* __restrict__ part,
+template <typename TV, typename TX>
+__global__ __launch_bounds__(kThreads) void k_gemv_t(int n, const TV* __restrict__ W, int64_t ld, int j0, int nc,
+                                                      const TX* __restrict__ x, double* __restrict__ part,
                                                       DevState* st) {
-  __shared__ double xs[kTileRows];
+  __shared__ TV xs[kTileRows];
   if (st && st->stop) return;
   const int tile = blockIdx.x;
   const int r0 = tile * kTileRows;
   const int rows = min(kTileRows, n - r0);
-  for (int i = threadIdx.x; i < rows; i += kThreads) xs[i] = x[r0 + i];
+  for (int i = threadIdx.x; i < rows; i += kThreads) xs[i] = (TV)x[r0 + i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int col = warp; col < nc; col += kThreads / 32) {
-    const double* wcol = W + (size_t)(j0 + col) * ld + r0;
-    double a0 = 0.0, a1 = 0.0;
+    const TV* wcol = W + (size_t)(j0 + col) * ld + r0;
+    TV a0 = (TV)0, a1 = (TV)0;
     int i = lane;
     for (; i + 32 < rows; i += 64) {
       a0 = fma(wcol[i], xs[i], a0);
       a1 = fma(wcol[i + 32], xs[i + 32], a1);
     }
     if (i < rows) a0 = fma(wcol[i], xs[i], a0);
-    const double a = warp_sum(a0 + a1);
+    const double a = warp_sum((double)a0 + (double)a1);
     if (lane == 0) part[(size_t)tile * nc + col] = a;
   }
 }
 
-cudaError_t launch_gemv_t(int n, const double* W, int64_t ld, int j0, int nc, const double* x, double* part,
-                          int ntiles, DevState* st, cudaStream_t s) {
-  k_gemv_t<<<ntiles, kThreads, 0, s>>>(n, W, ld, j0, nc, x, part, st);
+template <typename TV, typename TX>
+cudaError_t launch_gemv_t(int n, const TV* W, int64_t ld, int j0, int nc, const TX* x, double* part, int ntiles,
+                          DevState* st, cudaStream_t s) {
+  k_gemv_t<TV, TX><<<ntiles, kThreads, 0, s>>>(n, W, ld, j0, nc, x, part, st);
   return cudaGetLastError();
 }
+template cudaError_t launch_gemv_t<double, double>(int, const double*, int64_t, int, int, const double*, double*, int,
+                                                   DevState*, cudaStream_t);
+template cudaError_t launch_gemv_t<float, float>(int, const float*, int64_t, int, int, const float*, double*, int,
+                                                 DevState*, cudaStream_t);
+template cudaError_t launch_gemv_t<float, double>(int, const float*, int64_t, int, int, const double*, double*, int,
+                                                  DevState*, cudaStream_t);
 
 // d_q = sum over tiles of part[tile][q] (fixed order), then with j = j0+q:
 //   Hcol[j] = sigma_j sig_col d_q (or += when h_accumulate; sig_col = 1 when NULL),
@@ -671,7 +732,8 @@ cudaError_t launch_reduce_cols(const double* part, int ntiles, int nc, const dou
 
 // -------------------------------------------------------------- combine
 // out[r] = keep * out[r] + sum_q coef[q] W_q[r]   (keep = 0 overwrites out)
-__global__ __launch_bounds__(kThreads) void k_combine(int n, const double* __restrict__ W, int64_t ld, int nc,
+template <typename TV>
+__global__ __launch_bounds__(kThreads) void k_combine(int n, const TV* __restrict__ W, int64_t ld, int nc,
                                                        const double* __restrict__ coef, double* __restrict__ out,
                                                        double keep) {
   extern __shared__ double s_cf[];
@@ -679,31 +741,52 @@ __global__ __launch_bounds__(kThreads) void k_combine(int n, const double* __res
   __syncthreads();
   for (int r = blockIdx.x * kThreads + threadIdx.x; r < n; r += gridDim.x * kThreads) {
     double a = (keep != 0.0) ? keep * out[r] : 0.0;
-    for (int q = 0; q < nc; ++q) a = fma(s_cf[q], W[(size_t)q * ld + r], a);
+    for (int q = 0; q < nc; ++q) a = fma(s_cf[q], (double)W[(size_t)q * ld + r], a);
     out[r] = a;
   }
 }
 
-cudaError_t launch_combine(int n, const double* W, int64_t ld, int nc, const double* coef, double* out, double keep,
+template <typename TV>
+cudaError_t launch_combine(int n, const TV* W, int64_t ld, int nc, const double* coef, double* out, double keep,
                            cudaStream_t s) {
-  k_combine<<<grid_rows(n), kThreads, (size_t)nc * 8, s>>>(n, W, ld, nc, coef, out, keep);
+  k_combine<TV><<<grid_rows(n), kThreads, (size_t)(nc > 0 ? nc : 1) * 8, s>>>(n, W, ld, nc, coef, out, keep);
   return cudaGetLastError();
 }
+template cudaError_t launch_combine<double>(int, const double*, int64_t, int, const double*, double*, double,
+                                            cudaStream_t);
+template cudaError_t launch_combine<float>(int, const float*, int64_t, int, const double*, double*, double,
+                                           cudaStream_t);
 
 // dst_j = sigma_j W_j (normalized basis for inspection)
-__global__ void k_scale_columns(int n, const double* __restrict__ W, int64_t ld, int nc,
-                                const double* __restrict__ sigma, double* __restrict__ dst, int64_t ldd) {
+template <typename TV>
+__global__ void k_scale_columns(int n, const TV* __restrict__ W, int64_t ld, int nc, const double* __restrict__ sigma,
+                                double* __restrict__ dst, int64_t ldd) {
   const int j = blockIdx.y;
   if (j >= nc) return;
   const double sg = sigma[j];
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
-    dst[(size_t)j * ldd + r] = sg * W[(size_t)j * ld + r];
+    dst[(size_t)j * ldd + r] = sg * (double)W[(size_t)j * ld + r];
 }
 
-cudaError_t launch_scale_columns(int n, const double* W, int64_t ld, int nc, const double* sigma, double* dst,
+template <typename TV>
+cudaError_t launch_scale_columns(int n, const TV* W, int64_t ld, int nc, const double* sigma, double* dst,
                                  int64_t ldd, cudaStream_t s) {
   dim3 grid((unsigned)min((n + 255) / 256, 1024), (unsigned)nc);
-  k_scale_columns<<<grid, 256, 0, s>>>(n, W, ld, nc, sigma, dst, ldd);
+  k_scale_columns<TV><<<grid, 256, 0, s>>>(n, W, ld, nc, sigma, dst, ldd);
+  return cudaGetLastError();
+}
+template cudaError_t launch_scale_columns<double>(int, const double*, int64_t, int, const double*, double*, int64_t,
+                                                  cudaStream_t);
+template cudaError_t launch_scale_columns<float>(int, const float*, int64_t, int, const double*, double*, int64_t,
+                                                 cudaStream_t);
+
+// FP64 -> FP32 copy (start vector of the mixed-precision path)
+__global__ void k_to_f32(int n, const double* __restrict__ x, float* __restrict__ y) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) y[r] = (float)x[r];
+}
+
+cudaError_t launch_to_f32(int n, const double* x, float* y, cudaStream_t s) {
+  k_to_f32<<<grid_rows(n), kThreads, 0, s>>>(n, x, y);
   return cudaGetLastError();
 }
 

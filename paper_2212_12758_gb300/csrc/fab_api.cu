@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "fab_internal.cuh"
+#include "gauss.cuh"
 #include "small.cuh"
 
 using namespace fab;
@@ -129,16 +130,20 @@ struct fab_handle {
   int* d_rowptr = nullptr;
   int* d_colind = nullptr;
   double* d_vals = nullptr;
+  float* d_vals32 = nullptr;  // FP32 copy for the mixed-precision path (made on first use)
   int64_t ld = 0;
   // workspace
   Buf W, H, sigma, shf, scl, wn2, coef, part, counter, gpart, skpart, SV, P, qr, tau, y, cvec, dense, piv, scal, lsq, u, xbuf,
       state;
+  Buf W32, Wbf, G;  // mixed path: FP32 basis, its BF16 copy, Gaussian sketch (BF16, s x ld)
+  int G_n = -1, G_s = -1;
+  uint64_t G_seed = 0;
   // cached SRHT sample
   int64_t P_npad = -1;
   int P_s = -1;
   uint64_t P_seed = 0;
   // last solve
-  int has_state = 0, last_m = 0, last_s = 0, last_sketched = 0;
+  int has_state = 0, last_m = 0, last_s = 0, last_sketched = 0, last_mixed = 0;
 };
 
 extern "C" {
@@ -234,7 +239,8 @@ void fab_destroy(fab_handle* h) {
   cudaFree(h->d_rowptr);
   cudaFree(h->d_colind);
   cudaFree(h->d_vals);
-  Buf* bufs[] = {&h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
+  cudaFree(h->d_vals32);
+  Buf* bufs[] = {&h->W32, &h->Wbf, &h->G, &h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
                  &h->skpart, &h->SV, &h->P,     &h->qr,  &h->tau,  &h->y,    &h->cvec,    &h->dense,
                  &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state};
   for (Buf* b : bufs)
@@ -292,7 +298,7 @@ int validate(const fab_handle* h, const fab_params* p) {
   if (p->f < 0 || p->f > 2) return FAB_EINVAL;
   if (p->method < 0 || p->method > 3) return FAB_EINVAL;
   if (p->m < 1 || p->m > kMaxM) return FAB_EINVAL;
-  if (p->precision != FAB_FP64) return FAB_EINVAL;
+  if (p->precision != FAB_FP64 && p->precision != FAB_MIXED) return FAB_EINVAL;
   if (p->method != FAB_ARNOLDI && (p->k < 1 || p->k > kMaxWindow)) return FAB_EINVAL;
   if (p->f == FAB_F_EXP && !isfinite(p->t)) return FAB_EINVAL;
   if (sketched(p->method)) {
@@ -301,6 +307,8 @@ int validate(const fab_handle* h, const fab_params* p) {
       if (p->zeta < 1 || p->zeta > kMaxZeta || p->zeta > p->s) return FAB_EINVAL;
     } else if (p->sketch == FAB_SK_SRHT) {
       if (p->s > next_pow2(h->n)) return FAB_EINVAL;
+    } else if (p->sketch == FAB_SK_GAUSSIAN) {
+      if (p->precision != FAB_MIXED || p->m + 1 > kGaussMaxCols) return FAB_EINVAL;  // BF16 tensor-core sketch
     } else {
       return FAB_EINVAL;
     }
@@ -311,6 +319,8 @@ int validate(const fab_handle* h, const fab_params* p) {
 
 struct Ws {
   ColScale cs;
+  float* W32;
+  __nv_bfloat16 *Wbf, *G;
   double *W, *H, *sigma, *wn2, *coef, *part, *gpart, *skpart, *SV, *qr, *tau, *y, *cvec, *scal, *u, *xbuf;
   double* mats[9];
   double *lv_v, *lv_w, *lv_x, *lv_z, *lv_coef, *lv_q, *unorm2, *one;
@@ -339,7 +349,7 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
       {&h->coef, (size_t)(m + 1) * 8},
       {&h->part, part_blocks * (kMaxWindow + 1) * 8},
       {&h->counter, 64},
-      {&h->gpart, (size_t)ntiles * (m + 1) * 8},
+      {&h->gpart, std::max((size_t)ntiles * (m + 1) * 8, gauss_partial_bytes(n, s, m + 1))},
       {&h->skpart, (size_t)nchunks * s * 8},
       {&h->SV, (size_t)s * (m + 1) * 8},
       {&h->P, (size_t)s * 4},
@@ -363,6 +373,9 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
     if ((h->u.bytes < (size_t)n * 8 && fault_hit()) || !ensure(h->u, (size_t)n * 8)) return FAB_ENOMEM;
   }
   ws.W = ptr<double>(h->W);
+  ws.W32 = ptr<float>(h->W32);
+  ws.Wbf = ptr<__nv_bfloat16>(h->Wbf);
+  ws.G = ptr<__nv_bfloat16>(h->G);
   ws.H = ptr<double>(h->H);
   ws.sigma = ptr<double>(h->sigma);
   ws.cs = ColScale{ptr<double>(h->sigma), ptr<int>(h->shf), ptr<double>(h->scl)};
@@ -462,21 +475,19 @@ int sqrtm_e1(Ws& ws, int m, const int* mdev, double* c, int want_sqrt, int* iter
 
 }  // namespace
 
-extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, double* x, int bx_on_device,
-                         fab_stats* stats) {
-  if (!h || !p || !b || !x) return FAB_EINVAL;
-  int rc = validate(h, p);
-  if (rc != FAB_OK) return rc;
-  Ws ws;
-  rc = ensure_ws(h, p, ws);
-  if (rc != FAB_OK) return rc;
+// One solve with the basis stored as TV (double: FP64 path; float: mixed path).
+template <typename TV>
+int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, int bx_on_device, fab_stats* stats,
+               Ws& ws, TV* W, const void* vals) {
+  int rc = FAB_OK;
   cudaStream_t s = (cudaStream_t)p->stream;
+  constexpr bool kMixed = sizeof(TV) == 4;
   const int n = h->n, m = p->m, k = p->k;
   const int64_t ld = h->ld;
   const int ldh = m + 1;
   const bool sk_on = sketched(p->method);
   const int* mdev = &ws.st->m_used;
-  Csr A{h->n, h->nnz, h->d_rowptr, h->d_colind, h->d_vals};
+  Csr A{h->n, h->nnz, h->d_rowptr, h->d_colind, vals};
   h->has_state = 0;
   g_launches = 0;
   g_prof.begin_solve();
@@ -495,14 +506,20 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   CK(cudaMemsetAsync(ws.counter, 0, 64, s));
   CK(cudaMemsetAsync(ws.H, 0, (size_t)ldh * m * sizeof(double), s));
   CK(cudaMemsetAsync(ws.y, 0, (size_t)(m + 1) * sizeof(double), s));
-  CK(cudaMemcpyAsync(ws.W, b, (size_t)n * sizeof(double), cudaMemcpyDefault, s));
+  if (kMixed) {  // b is FP64 (host or device): stage it, then round to FP32 in column 0
+    if ((h->xbuf.bytes < (size_t)n * 8 && fault_hit()) || !ensure(h->xbuf, (size_t)n * 8)) return FAB_ENOMEM;
+    CK(cudaMemcpyAsync(h->xbuf.p, b, (size_t)n * sizeof(double), cudaMemcpyDefault, s));
+    LK(PK_SMALL, launch_to_f32(n, ptr<double>(h->xbuf), reinterpret_cast<float*>(W), s));
+  } else {
+    CK(cudaMemcpyAsync(W, b, (size_t)n * sizeof(double), cudaMemcpyDefault, s));
+  }
 
   SketchDev sk;
   memset(&sk, 0, sizeof(sk));
   sk.kind = SK_NONE;
   double sk_scale = 1.0;
   if (sk_on) {
-    sk.kind = p->sketch == FAB_SK_SRHT ? SK_SRHT : SK_SPARSE;
+    sk.kind = p->sketch == FAB_SK_SRHT ? SK_SRHT : (p->sketch == FAB_SK_GAUSSIAN ? SK_GAUSS : SK_SPARSE);
     sk.s = p->s;
     sk.zeta = p->zeta;
     sk.chunk_log2 = kChunkLog2;
@@ -521,6 +538,15 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
         h->P_seed = p->seed;
       }
       sk_scale = 1.0 / sqrt((double)p->s);
+    } else if (sk.kind == SK_GAUSS) {
+      sk.Wbf = ws.Wbf;
+      sk.ldbf = ld;
+      if (h->G_n != n || h->G_s != p->s || h->G_seed != p->seed) {  // G (BF16, s x n) cached per handle
+        LK(PK_SMALL, launch_gauss_generate(p->s, n, ld, rng_state(p->seed, 5), ws.G, s));
+        h->G_n = n;
+        h->G_s = p->s;
+        h->G_seed = p->seed;
+      }
     } else {
       sk_scale = 1.0 / sqrt((double)p->zeta);
     }
@@ -529,32 +555,35 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   memset(&none, 0, sizeof(none));
   none.kind = SK_NONE;
 
-  // start vector: ||b||, sigma_0, sketch of b
-  LK(PK_UPDATE, launch_update(n, ws.W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1 | 2, ws.part, ws.counter,
+  // start vector: ||b||, sigma_0, sketch of b (Gaussian: its BF16 copy)
+  LK(PK_UPDATE, launch_update(n, W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1 | 2, ws.part, ws.counter,
                    sk_on ? sk : none, ws.st, s));
-  if (sk_on) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
+  if (sk_on && sk.kind != SK_GAUSS) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
 
   const int ntiles = (n + kTileRows - 1) / kTileRows;
   for (int c = 1; c <= m; ++c) {
     if (p->method == FAB_ARNOLDI) {
-      LK(PK_SPMV, launch_spmv_dots(A, ws.W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
+      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
       double* Hcol = ws.H + (size_t)ldh * (c - 1);
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-        LK(PK_GEMVT, launch_gemv_t(n, ws.W, ld, 0, c, ws.W + (size_t)c * ld, ws.gpart, ntiles, ws.st, s));
+        LK(PK_GEMVT, launch_gemv_t(n, (const TV*)W, ld, 0, c, (const TV*)W + (size_t)c * ld, ws.gpart, ntiles, ws.st, s));
         LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, c, ws.sigma, 0, ws.cs.scl + c, Hcol, pass, ws.coef,
                                         ws.st, s));
-        LK(PK_UPDATE, launch_update(n, ws.W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, ws.wn2, pass == 1 ? 1 : 0, ws.part,
+        LK(PK_UPDATE, launch_update(n, W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, ws.wn2, pass == 1 ? 1 : 0, ws.part,
                          ws.counter, none, ws.st, s));
       }
     } else {
       const int j0 = std::max(0, c - k), kw = c - j0;
-      LK(PK_SPMV, launch_spmv_dots(A, ws.W, ld, c, j0, kw, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
+      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, j0, kw, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
                           s));
-      LK(PK_UPDATE, launch_update(n, ws.W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part, ws.counter,
+      LK(PK_UPDATE, launch_update(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part, ws.counter,
                        sk_on ? sk : none, ws.st, s));
-      if (sk_on) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
+      if (sk_on && sk.kind != SK_GAUSS)
+        LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
     }
   }
+  if (sk_on && sk.kind == SK_GAUSS)  // Theta V_{m+1} = G (BF16 basis) on the tensor cores, FP64 finish
+    LK(PK_SKRED, launch_gauss_sketch(ws.G, ws.Wbf, ld, n, p->s, m + 1, ws.sigma, ws.gpart, ws.SV, ws.st, s));
   CK(cudaEventRecord(ev[1], s));
   DevState hs;
   CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -564,6 +593,7 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   h->last_m = m;
   h->last_s = sk_on ? p->s : 0;
   h->last_sketched = sk_on ? 1 : 0;
+  h->last_mixed = kMixed ? 1 : 0;
   h->has_state = 1;  // the basis, H and the sketch can be inspected from here on
   int lsqr_iters = 0, fh_iters = 0;
   if (mu == 0) {  // b = 0
@@ -594,16 +624,16 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
     LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 0, ws.tau, s));
     const double one = 1.0;
     CK(cudaMemcpyAsync(ws.one, &one, sizeof(double), cudaMemcpyHostToDevice, s));
-    LK(PK_COMBINE, launch_lsqr_u(n, ws.W + (size_t)mu * ld, ld, 1, ws.one, ws.u, 1, ws.part, ws.counter, ws.unorm2, ws.st, s));
-    LK(PK_GEMVT, launch_gemv_t(n, ws.W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
+    LK(PK_COMBINE, launch_lsqr_u(n, (const TV*)W + (size_t)mu * ld, ld, 1, ws.one, ws.u, 1, ws.part, ws.counter, ws.unorm2, ws.st, s));
+    LK(PK_GEMVT, launch_gemv_t(n, (const TV*)W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
     LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, nullptr, ws.lv_q, 0, nullptr, ws.st, s));
     LsqrVecs lv{ws.lv_v, ws.lv_w, ws.lv_x, ws.lv_z, ws.lv_coef, ws.lv_q};
     LK(PK_SMALL, launch_lsqr_start(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, p->lsqr_tol, ws.st, s));
     const int maxit = p->lsqr_maxit > 0 ? p->lsqr_maxit : 4 * mu;
     bool converged = false;
     for (int it = 0; it < maxit; ++it) {
-      LK(PK_COMBINE, launch_lsqr_u(n, ws.W, ld, mu, ws.lv_coef, ws.u, 0, ws.part, ws.counter, ws.unorm2, ws.st, s));
-      LK(PK_GEMVT, launch_gemv_t(n, ws.W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
+      LK(PK_COMBINE, launch_lsqr_u(n, (const TV*)W, ld, mu, ws.lv_coef, ws.u, 0, ws.part, ws.counter, ws.unorm2, ws.st, s));
+      LK(PK_GEMVT, launch_gemv_t(n, (const TV*)W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
       LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, nullptr, ws.lv_q, 0, nullptr, ws.st, s));
       LK(PK_SMALL, launch_lsqr_step(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, ws.st, s));
       CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -636,7 +666,7 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
     if ((h->xbuf.bytes < (size_t)n * 8 && fault_hit()) || !ensure(h->xbuf, (size_t)n * 8)) return FAB_ENOMEM;
     xdst = ptr<double>(h->xbuf);
   }
-  LK(PK_COMBINE, launch_combine(n, ws.W, ld, mu, ws.coef, xdst, 0.0, s));
+  LK(PK_COMBINE, launch_combine(n, (const TV*)W, ld, mu, ws.coef, xdst, 0.0, s));
   CK(cudaEventRecord(ev[3], s));
   if (!bx_on_device) CK(cudaMemcpyAsync(x, xdst, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -667,6 +697,32 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   return FAB_OK;
 }
 
+extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, double* x, int bx_on_device,
+                         fab_stats* stats) {
+  if (!h || !p || !b || !x) return FAB_EINVAL;
+  int rc = validate(h, p);
+  if (rc != FAB_OK) return rc;
+  Ws ws;
+  rc = ensure_ws(h, p, ws);
+  if (rc != FAB_OK) return rc;
+  if (p->precision == FAB_MIXED) {
+    if (!h->d_vals32) {  // FP32 copy of A's values, made once per handle
+      if (fault_hit() || cudaMalloc(&h->d_vals32, (size_t)(h->nnz + kCsrPad) * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        h->d_vals32 = nullptr;
+        return FAB_ENOMEM;
+      }
+      if (launch_to_f32(h->nnz + (int)kCsrPad, h->d_vals, h->d_vals32, (cudaStream_t)p->stream) != cudaSuccess ||
+          cudaStreamSynchronize((cudaStream_t)p->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return FAB_ECUDA;
+      }
+    }
+    return apply_impl<float>(h, p, b, x, bx_on_device, stats, ws, ws.W32, h->d_vals32);
+  }
+  return apply_impl<double>(h, p, b, x, bx_on_device, stats, ws, ws.W, h->d_vals);
+}
+
 extern "C" int fab_last_state(fab_handle* h, double* H, double* SV, double* y, double* coeffs) {
   if (!h || !h->has_state) return FAB_EINVAL;
   const int m = h->last_m;
@@ -692,8 +748,12 @@ extern "C" int fab_last_basis(fab_handle* h, double* V, int dst_on_device) {
     dst = (double*)tmp;
   }
   int rc = FAB_OK;
-  if (launch_scale_columns(n, ptr<double>(h->W), h->ld, m + 1, ptr<double>(h->sigma), dst, n, 0) != cudaSuccess)
-    rc = FAB_ECUDA;
+  const cudaError_t e = h->last_mixed
+                            ? launch_scale_columns(n, (const float*)ptr<float>(h->W32), h->ld, m + 1,
+                                                   ptr<double>(h->sigma), dst, n, 0)
+                            : launch_scale_columns(n, (const double*)ptr<double>(h->W), h->ld, m + 1,
+                                                   ptr<double>(h->sigma), dst, n, 0);
+  if (e != cudaSuccess) rc = FAB_ECUDA;
   if (rc == FAB_OK && !dst_on_device &&
       cudaMemcpy(V, dst, (size_t)n * (m + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
     rc = FAB_ECUDA;
@@ -711,11 +771,42 @@ extern "C" int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t
     if (zeta < 1 || zeta > kMaxZeta || zeta > s) return FAB_EINVAL;
   } else if (sketch == FAB_SK_SRHT) {
     if (s > next_pow2(n)) return FAB_EINVAL;
+  } else if (sketch == FAB_SK_GAUSSIAN) {
+    if (ncols > kGaussMaxCols) return FAB_EINVAL;
   } else {
     return FAB_EINVAL;
   }
   if (ncols == 0) return FAB_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  if (sketch == FAB_SK_GAUSSIAN) {  // G and the BF16 columns in scratch, GEMM on the tensor cores
+    const int64_t ld = ((n + 31) / 32) * 32;
+    __nv_bfloat16 *G = nullptr, *B = nullptr;
+    double *part = nullptr, *ones = nullptr;
+    DevState* ds = nullptr;
+    int rc = FAB_OK;
+    if (cudaMallocAsync((void**)&G, (size_t)ld * s * 2, st) != cudaSuccess ||
+        cudaMallocAsync((void**)&B, (size_t)ld * ncols * 2, st) != cudaSuccess ||
+        cudaMallocAsync((void**)&part, gauss_partial_bytes((int)n, s, ncols) + 16, st) != cudaSuccess ||
+        cudaMallocAsync((void**)&ones, (size_t)ncols * 8, st) != cudaSuccess ||
+        cudaMallocAsync((void**)&ds, sizeof(DevState), st) != cudaSuccess)
+      rc = FAB_ENOMEM;
+    std::vector<double> h1((size_t)ncols, 1.0);
+    if (rc == FAB_OK && (cudaMemcpyAsync(ones, h1.data(), (size_t)ncols * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                         launch_state_reset(ds, 0, st) != cudaSuccess ||
+                         launch_gauss_generate(s, (int)n, ld, rng_state(seed, 5), G, st) != cudaSuccess ||
+                         launch_to_bf16((int)n, ncols, V_dev, ldv, B, ld, st) != cudaSuccess ||
+                         launch_gauss_sketch(G, B, ld, (int)n, s, ncols, ones, part, out_dev, ds, st) != cudaSuccess))
+      rc = FAB_ECUDA;
+    DevState hs;
+    if (rc == FAB_OK && cudaMemcpyAsync(&hs, ds, sizeof(DevState), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      rc = FAB_ECUDA;
+    for (void* q : {(void*)G, (void*)B, (void*)part, (void*)ones, (void*)ds})
+      if (q) cudaFreeAsync(q, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = FAB_ECUDA;
+    if (rc == FAB_OK && hs.status != FAB_OK) rc = hs.status;
+    cudaGetLastError();
+    return rc;
+  }
   const int nchunks = (int)((n + kChunk - 1) / kChunk);
   double* part = nullptr;
   int* P = nullptr;

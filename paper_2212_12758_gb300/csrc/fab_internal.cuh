@@ -2,6 +2,7 @@
 // device-side solve state, kernel launchers). Not part of the public ABI.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -20,7 +21,7 @@ constexpr int kMaxS = 4096;          // sketch rows limit
 constexpr int kMaxZeta = 16;         // sparse-sign nonzeros per column limit
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 
-enum SketchKind { SK_NONE = -1, SK_SPARSE = 0, SK_SRHT = 1 };
+enum SketchKind { SK_NONE = -1, SK_SPARSE = 0, SK_SRHT = 1, SK_GAUSS = 2 };
 
 // Device-side state of one solve. Written only by kernels (reset by k_state_reset).
 struct DevState {
@@ -46,6 +47,8 @@ struct SketchDev {
   uint64_t st_signs;
   uint64_t st_D;
   const int* P;        // SRHT sampled rows (device, s entries, sorted)
+  __nv_bfloat16* Wbf;  // Gaussian: BF16 copy of the basis (column c at Wbf + c * ldbf)
+  int64_t ldbf;
   double* part;        // nparts x s block partials (block-major), nparts <= nchunks
 };
 
@@ -208,7 +211,7 @@ struct Csr {
   int nnz;
   const int* rowptr;
   const int* colind;
-  const double* vals;
+  const void* vals;  // FP64 values (FP64 path) or FP32 values (mixed path)
 };
 
 cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s);
@@ -220,24 +223,30 @@ struct ColScale {
   int* shf;
   double* scl;
 };
-cudaError_t launch_spmv_dots(const Csr& A, double* W, int64_t ld, int c, int j0, int kw, ColScale cs,
+template <typename TV>
+cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int kw, ColScale cs,
                              double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
                              DevState* st, cudaStream_t s);
-cudaError_t launch_update(int n, double* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
+template <typename TV>
+cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
                           int ldh, ColScale cs, const double* wn2, int mode, double* part, unsigned* counter,
                           SketchDev& sk, DevState* st, cudaStream_t s);
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
                                  DevState* st, cudaStream_t s);
 cudaError_t launch_srht_sample(int64_t npad, int s, uint64_t stP, int* P, cudaStream_t st);
-cudaError_t launch_gemv_t(int n, const double* W, int64_t ld, int j0, int nc, const double* x, double* part,
+template <typename TV, typename TX>
+cudaError_t launch_gemv_t(int n, const TV* W, int64_t ld, int j0, int nc, const TX* x, double* part,
                           int ntiles, DevState* st, cudaStream_t s);
 cudaError_t launch_reduce_cols(const double* part, int ntiles, int nc, const double* sigma, int j0,
                                const double* sig_col, double* Hcol, int h_accumulate, double* coef, DevState* st,
                                cudaStream_t s);
-cudaError_t launch_combine(int n, const double* W, int64_t ld, int nc, const double* coef, double* out,
+template <typename TV>
+cudaError_t launch_combine(int n, const TV* W, int64_t ld, int nc, const double* coef, double* out,
                            double keep, cudaStream_t s);
-cudaError_t launch_scale_columns(int n, const double* W, int64_t ld, int nc, const double* sigma, double* dst,
+template <typename TV>
+cudaError_t launch_scale_columns(int n, const TV* W, int64_t ld, int nc, const double* sigma, double* dst,
                                  int64_t ldd, cudaStream_t s);
+cudaError_t launch_to_f32(int n, const double* x, float* y, cudaStream_t s);
 
 int sm_count();              // multiprocessors of the current device
 int grid_rows(int n);        // grid for the thread-per-row kernels

@@ -590,7 +590,8 @@ cudaError_t launch_lsqr_step(const double* R, int ldr, const int* mdev, const do
 
 // ustore[r] <- sum_q coef_q W_q[r] + keep * ustore[r] with keep = st->scal[6]
 // (keep_zero: ustore is overwritten); ||ustore||^2 reduced over the grid into *unorm2.
-__global__ __launch_bounds__(kThreads) void k_lsqr_u(int n, const double* __restrict__ W, int64_t ld, int nc,
+template <typename TV>
+__global__ __launch_bounds__(kThreads) void k_lsqr_u(int n, const TV* __restrict__ W, int64_t ld, int nc,
                                                       const double* __restrict__ coef, double* __restrict__ u,
                                                       int keep_zero, double* __restrict__ part,
                                                       unsigned* __restrict__ counter, double* __restrict__ unorm2,
@@ -605,7 +606,7 @@ __global__ __launch_bounds__(kThreads) void k_lsqr_u(int n, const double* __rest
   double nrm = 0.0;
   for (int r = blockIdx.x * kThreads + threadIdx.x; r < n; r += gridDim.x * kThreads) {
     double a = keep_zero ? 0.0 : keep * u[r];
-    for (int q = 0; q < nc; ++q) a = fma(s_cf[q], W[(size_t)q * ld + r], a);
+    for (int q = 0; q < nc; ++q) a = fma(s_cf[q], (double)W[(size_t)q * ld + r], a);
     u[r] = a;
     nrm = fma(a, a, nrm);
   }
@@ -620,12 +621,17 @@ __global__ __launch_bounds__(kThreads) void k_lsqr_u(int n, const double* __rest
   }
 }
 
-cudaError_t launch_lsqr_u(int n, const double* W, int64_t ld, int nc, const double* coef, double* u, int keep_zero,
+template <typename TV>
+cudaError_t launch_lsqr_u(int n, const TV* W, int64_t ld, int nc, const double* coef, double* u, int keep_zero,
                           double* part, unsigned* counter, double* unorm2, const DevState* st, cudaStream_t s) {
-  k_lsqr_u<<<grid_rows(n), kThreads, (size_t)(nc > 0 ? nc : 1) * 8, s>>>(n, W, ld, nc, coef, u, keep_zero, part,
+  k_lsqr_u<TV><<<grid_rows(n), kThreads, (size_t)(nc > 0 ? nc : 1) * 8, s>>>(n, W, ld, nc, coef, u, keep_zero, part,
                                                                           counter, unorm2, st);
   return cudaGetLastError();
 }
+template cudaError_t launch_lsqr_u<double>(int, const double*, int64_t, int, const double*, double*, int, double*,
+                                           unsigned*, double*, const DevState*, cudaStream_t);
+template cudaError_t launch_lsqr_u<float>(int, const float*, int64_t, int, const double*, double*, int, double*,
+                                          unsigned*, double*, const DevState*, cudaStream_t);
 
 
 // ------------------------------------------------ cluster QR / LU (DSMEM)

@@ -43,7 +43,8 @@ cudaError_t launch_lsqr_start(const double* R, int ldr, const int* mdev, const d
                               const LsqrVecs& lv, double tol, DevState* st, cudaStream_t s);
 cudaError_t launch_lsqr_step(const double* R, int ldr, const int* mdev, const double* sigma, const double* unorm2,
                              const LsqrVecs& lv, DevState* st, cudaStream_t s);
-cudaError_t launch_lsqr_u(int n, const double* W, int64_t ld, int nc, const double* coef, double* u, int keep_zero,
+template <typename TV>
+cudaError_t launch_lsqr_u(int n, const TV* W, int64_t ld, int nc, const double* coef, double* u, int keep_zero,
                           double* part, unsigned* counter, double* unorm2, const DevState* st, cudaStream_t s);
 
 }  // namespace fab

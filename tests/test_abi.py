@@ -66,4 +66,5 @@ def test_sketch_apply_rejects_bad_sizes(fab):
     out = ctypes.c_void_p(1)
     assert fab.lib.fab_sketch_apply(fab.SRHT, 10, 32, 8, 1, out, 10, 1, out, None) == fab.FAB_EINVAL  # s > n'
     assert fab.lib.fab_sketch_apply(fab.SPARSE_SIGN, 10, 4, 8, 1, out, 10, 1, out, None) == fab.FAB_EINVAL  # zeta > s
-    assert fab.lib.fab_sketch_apply(fab.GAUSSIAN, 10, 4, 2, 1, out, 10, 1, out, None) == fab.FAB_EINVAL
+    assert fab.lib.fab_sketch_apply(fab.GAUSSIAN, 10, 4, 2, 1, out, 10, 257, out, None) == fab.FAB_EINVAL  # ncols
+    assert fab.lib.fab_sketch_apply(7, 10, 4, 2, 1, out, 10, 1, out, None) == fab.FAB_EINVAL  # unknown sketch

@@ -1,0 +1,89 @@
+"""GPU: the Gaussian sketch on the tensor cores and the mixed-precision path.
+
+Gaussian entries are defined in FP64 (Box-Muller of SplitMix64 stream 5) and
+rounded to BF16; sketching one-hot columns reveals G column by column, which
+must equal the oracle's entries exactly. For general columns the device rounds
+V to BF16 (exactly as the oracle's round_bf16) and accumulates the exact BF16
+products in FP32 within a split of the reduction, then in FP64 across splits;
+the bound used is the classical accumulation bound gamma_K sum |g v| with
+K = n (no assumption on the order), u = 2^-24.
+
+Mixed precision (FP32 matrix and basis, FP64 small stage) is compared with the
+FP64 oracle's f_m at the same m and sketch; the tolerance per case is stated
+with the test.
+"""
+import numpy as np
+import pytest
+
+from oracle import krylov, matfun
+from oracle import sketch as osk
+from paper_2212_12758_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fab():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2212_12758_gb300 import fab as f
+
+    return f
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,s", [(5000, 300), (777, 128), (70000, 64)])
+def test_gaussian_entries_bit_exact(fab, n, s):
+    import torch
+
+    rng = np.random.default_rng(n)
+    cols = np.unique(np.r_[np.arange(min(60, n)), np.arange(n - 60, n), rng.integers(0, n, 100)])[:256]
+    V = torch.zeros((len(cols), n), dtype=torch.float64, device="cuda")
+    V[torch.arange(len(cols)), torch.from_numpy(cols).cuda()] = 1.0
+    out = fab.sketch_apply(V, s, sketch=fab.GAUSSIAN, seed=9).cpu().numpy().T  # s x ncols
+    G = osk.gaussian_entries(s, n, 9, bf16=True)
+    mism = int(np.count_nonzero(out != G[:, cols]))
+    assert mism == 0, f"{mism} Gaussian entries differ"
+
+
+@pytest.mark.parametrize("n,s", [(70000, 300), (4096 * 3 + 5, 128)])
+def test_gaussian_sketch_random_columns(fab, n, s):
+    import torch
+
+    rng = np.random.default_rng(1)
+    Vh = rng.standard_normal((5, n)) * np.array([[1.0], [1e-5], [3e3], [1.0], [1.0]])
+    out = fab.sketch_apply(torch.from_numpy(Vh).cuda(), s, sketch=fab.GAUSSIAN, seed=4).cpu().numpy()
+    G = osk.gaussian_entries(s, n, 4, bf16=True)
+    Vb = osk.round_bf16(Vh)
+    ref = Vb @ G.T  # exact products of BF16 values, FP64 sums
+    bound = n * 2.0**-24 * (np.abs(Vb) @ np.abs(G).T)
+    assert np.all(np.abs(out - ref) <= bound)
+
+
+CASES = [
+    # name, matrix builder, f, t, m, k, sketch, s
+    ("convdiff2d_exp_srht", lambda: W.convdiff(2, 100), matfun.EXP, -0.002, 30, 2, osk.SRHT, 120),
+    ("graph_invsqrt_gauss", lambda: W.chung_lu_laplacian(20000, seed=2), matfun.INVSQRT, 1.0, 30, 2, osk.GAUSSIAN, 120),
+    ("graph_sqrt_gauss", lambda: W.chung_lu_laplacian(20000, seed=2), matfun.SQRT, 1.0, 30, 2, osk.GAUSSIAN, 120),
+]
+
+
+@pytest.mark.parametrize("name,build,f,t,m,k,sk,s", CASES)
+@pytest.mark.parametrize("method", [krylov.NOPROJ, krylov.SKETCHED_FAST, krylov.SKETCHED_LS, krylov.ARNOLDI])
+def test_mixed_precision_vs_fp64_oracle(fab, name, build, f, t, m, k, sk, s, method):
+    import torch
+
+    A = build()
+    b = W.random_vector(A.n, 0)
+    th = osk.make(sk, A.n, s, 3, 8)
+    ref = krylov.run(method, W.to_scipy(A), b, m, k, f, th, t, tol=1e-10)
+    M = fab.Matrix.from_csr(A)
+    p = fab.params(f=f, t=t, m=m, k=k, s=s, sketch=sk, seed=3, method=method, precision=fab.MIXED, lsqr_tol=1e-10)
+    x = M.apply(torch.from_numpy(b).cuda(), p).cpu().numpy()
+    err = _rel(x, ref.x)
+    print(f"\nMIXED {name} method={method}: rel err vs FP64 oracle f_m = {err:.3e}")
+    assert err <= 1e-3
