@@ -103,6 +103,11 @@ void fab_params_default(fab_params* p);
 /* Message for an error code (static string). */
 const char* fab_strerror(int code);
 
+/* Detail of the last FAB_ECUDA returned on this host thread: the kernel class
+ * whose launch (or, with FAB_SYNC_CHECK=1 in the environment, whose execution)
+ * failed and the CUDA error string. Empty if none. */
+const char* fab_last_error(void);
+
 /*
  * fab_create - copy A (CSR) into a new handle.
  *   n       matrix order, 1 <= n < 2^31

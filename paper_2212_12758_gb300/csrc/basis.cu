@@ -152,7 +152,7 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
       const int e0 = A.rowptr[r], e1 = A.rowptr[r + 1];
       TV wv[KW > 0 ? KW : 1];
 #pragma unroll
-      for (int q = 0; q < KW; ++q) wv[q] = W[(size_t)(j0 + q) * ld + r];  // window entries, issued early
+      for (int q = 0; q < KW; ++q) wv[q] = W[(size_t)(j0 + q) * ld + r];  // window entries, issued early (r < n)
       TV y = (TV)0;
       if (staged) {
         const int base = s_e0[stg];
@@ -167,12 +167,14 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
           for (int u = 0; u < 8; ++u) y = fma(sv[e + u], g[u], y);
         }
         const int rem = e1 - e;
-        TV g[8];
+        if (rem > 0) {  // tail: every index is clamped into the row, so no load can leave it
+          TV g[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) g[u] = (u < rem) ? __ldg(vin + sc[e + u]) : (TV)0;
+          for (int u = 0; u < 8; ++u) g[u] = __ldg(vin + sc[min(e + u, e1 - 1)]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (u < rem) y = fma(sv[e + u], g[u], y);
+          for (int u = 0; u < 8; ++u)
+            if (u < rem) y = fma(sv[e + u], g[u], y);
+        }
       } else {
         for (int e = e0; e < e1; ++e) y = fma(__ldg(Avals + e), __ldg(vin + __ldg(A.colind + e)), y);
       }
@@ -476,15 +478,20 @@ __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(in
         if (nc > 0) wc[base + i * kThreads] = v[i];
         nrm_c = fma(v[i], v[i], nrm_c);
       }
-    } else {
+    } else {  // last, partial chunk: every load index is clamped to a valid row
 #pragma unroll
-      for (int i = 0; i < kRowsPerThread; ++i) v[i] = (base + i * kThreads < n) ? wc[base + i * kThreads] : (TV)0;
+      for (int i = 0; i < kRowsPerThread; ++i) {
+        const TV t = wc[min(base + i * kThreads, n - 1)];
+        v[i] = (base + i * kThreads < n) ? t : (TV)0;
+      }
       for (int q = 0; q < nc; ++q) {
         const TV cf = s_coef[q];
-        const TV* col = Wb + (size_t)q * ld + base;
+        const TV* col = Wb + (size_t)q * ld;
 #pragma unroll
-        for (int i = 0; i < kRowsPerThread; ++i)
-          if (base + i * kThreads < n) v[i] = fma(-cf, col[i * kThreads], v[i]);
+        for (int i = 0; i < kRowsPerThread; ++i) {
+          const TV t = col[min(base + i * kThreads, n - 1)];
+          if (base + i * kThreads < n) v[i] = fma(-cf, t, v[i]);
+        }
       }
 #pragma unroll
       for (int i = 0; i < kRowsPerThread; ++i) {
@@ -682,7 +689,7 @@ __global__ __launch_bounds__(kThreads) void k_gemv_t(int n, const TV* __restrict
       a0 = fma(wcol[i], xs[i], a0);
       a1 = fma(wcol[i + 32], xs[i + 32], a1);
     }
-    if (i < rows) a0 = fma(wcol[i], xs[i], a0);
+    if (i < rows) a0 = fma(wcol[min(i, rows - 1)], xs[min(i, rows - 1)], a0);
     const double a = warp_sum((double)a0 + (double)a1);
     if (lane == 0) part[(size_t)tile * nc + col] = a;
   }

@@ -3,6 +3,7 @@
 // of basis.cu and small.cu; this file only validates arguments, allocates,
 // and enqueues launches on the caller's stream.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -273,7 +274,9 @@ namespace {
       if (e0_ && e1_) cudaEventRecord(e0_, s);                    \
     }                                                             \
     cudaError_t e_ = (call);                                      \
+    if (e_ == cudaSuccess && sync_check()) e_ = cudaStreamSynchronize(s); \
     if (e_ != cudaSuccess) {                                      \
+      note_error(kind, e_, __LINE__);                             \
       cudaGetLastError();                                         \
       return FAB_ECUDA;                                           \
     }                                                             \
@@ -283,6 +286,21 @@ namespace {
     }                                                             \
     ++g_launches;                                                 \
   } while (0)
+
+// Debug aid: FAB_SYNC_CHECK=1 synchronizes after every launch so that a failing
+// kernel is named by fab_last_error() instead of surfacing at a later call.
+bool sync_check() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("FAB_SYNC_CHECK");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+thread_local char g_errmsg[256] = "";
+void note_error(int kind, cudaError_t e, int line) {
+  snprintf(g_errmsg, sizeof(g_errmsg), "%s launch (fab_api.cu:%d): %s", kProfNames[kind], line, cudaGetErrorString(e));
+}
 
 thread_local int g_launches = 0;
 
@@ -872,3 +890,5 @@ extern "C" int fab_profile_query(const char* name, double* total_ms, int64_t* la
   }
   return FAB_EINVAL;
 }
+
+extern "C" const char* fab_last_error(void) { return g_errmsg; }

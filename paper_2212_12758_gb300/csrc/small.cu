@@ -255,6 +255,10 @@ __global__ __launch_bounds__(1024) void k_lu(double* __restrict__ M, int ld, con
           b = rv[w];
           p = ri[w];
         }
+      if (p < k || p >= mu) {  // only with non-finite entries: keep the row, flag the matrix
+        p = k;
+        st->status = FAB_ENUMERIC;
+      }
       s_p = p;
       piv[k] = p;
     }
@@ -310,7 +314,7 @@ __global__ void k_lu_solve(const double* __restrict__ LU, int ld, const int* __r
   if (lane == 0) {
     for (int k = 0; k < mu; ++k) {
       const int p = piv[k];
-      if (p != k) {
+      if (p != k && p > k && p < mu) {
         const double t = b[k];
         b[k] = b[p];
         b[p] = t;
@@ -777,6 +781,10 @@ __global__ void __launch_bounds__(256) k_lu_cluster(double* __restrict__ M, int 
           b = rv[w];
           p = ri[w];
         }
+      if (p < k || p >= mu) {  // only with non-finite entries
+        p = k;
+        if (tid == 0) st->status = FAB_ENUMERIC;
+      }
       if (tid == 0) {
         const double t = ck[k];
         ck[k] = ck[p];
@@ -791,7 +799,8 @@ __global__ void __launch_bounds__(256) k_lu_cluster(double* __restrict__ M, int 
       for (int i = k + 1 + tid; i < mu; i += blockDim.x) ck[i] *= pinv;
     }
     cluster.sync();  // pivot and multipliers of column k are published
-    const int p = *cluster.map_shared_rank(s_piv + k, owner);
+    int p = *cluster.map_shared_rank(s_piv + k, owner);
+    if (p < k || p >= mu) p = k;
     const double* rcol = cluster.map_shared_rank(loc + (size_t)(k / CL) * mu, owner);
     for (int i = k + 1 + tid; i < mu; i += blockDim.x) lbuf[i] = rcol[i];
     if (tid == 0) {

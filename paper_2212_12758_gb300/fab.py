@@ -24,7 +24,7 @@ SPARSE_SIGN, SRHT, GAUSSIAN = 0, 1, 2
 FP64, MIXED = 0, 1
 
 # Every symbol the header declares (checked against include/fab.h by the tests).
-SYMBOLS = ("fab_params_default", "fab_strerror", "fab_create", "fab_apply", "fab_destroy", "fab_last_state",
+SYMBOLS = ("fab_params_default", "fab_strerror", "fab_last_error", "fab_create", "fab_apply", "fab_destroy", "fab_last_state",
            "fab_last_basis", "fab_sketch_apply", "fab_sketch_apply_noalloc", "fab_profile_enable",
            "fab_profile_query")
 PROFILE_KINDS = ("spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine")
@@ -52,6 +52,8 @@ lib.fab_params_default.argtypes = [ctypes.POINTER(Params)]
 lib.fab_params_default.restype = None
 lib.fab_strerror.argtypes = [_i32]
 lib.fab_strerror.restype = ctypes.c_char_p
+lib.fab_last_error.argtypes = []
+lib.fab_last_error.restype = ctypes.c_char_p
 lib.fab_create.argtypes = [ctypes.POINTER(_vp), _i64, _i64, _vp, _vp, _vp, _i32]
 lib.fab_create.restype = _i32
 lib.fab_apply.argtypes = [_vp, ctypes.POINTER(Params), _vp, _vp, _i32, ctypes.POINTER(Stats)]
@@ -74,7 +76,8 @@ lib.fab_profile_query.restype = _i32
 
 class FabError(RuntimeError):
     def __init__(self, code: int, where: str):
-        super().__init__(f"{where}: {lib.fab_strerror(code).decode()} ({code})")
+        detail = lib.fab_last_error().decode() if code == FAB_ECUDA else ""
+        super().__init__(f"{where}: {lib.fab_strerror(code).decode()} ({code}){' - ' + detail if detail else ''}")
         self.code = code
 
 
