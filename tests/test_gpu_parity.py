@@ -159,7 +159,9 @@ def test_zero_rhs_and_invalid_params(fab, torch):
     with pytest.raises(fab.FabError):
         M.apply(np.ones(A.n), fab.params(m=10, k=0))
     with pytest.raises(fab.FabError):
-        M.apply(np.ones(A.n), fab.params(m=10, precision=fab.MIXED))
+        M.apply(np.ones(A.n), fab.params(m=10, precision=7))
+    with pytest.raises(fab.FabError):  # the Gaussian sketch needs the mixed-precision path
+        M.apply(np.ones(A.n), fab.params(m=10, sketch=fab.GAUSSIAN))
     bad = np.ones(A.n)
     bad[7] = np.nan
     with pytest.raises(fab.FabError) as e:
