@@ -354,11 +354,14 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
   const int ntiles = (n + kTileRows - 1) / kTileRows;
   const int nchunks = (n + kChunk - 1) / kChunk;
   const size_t part_blocks = (size_t)sm_count() * kMaxPartBlocks;
+  const bool gauss = p->precision == FAB_MIXED && p->sketch == FAB_SK_GAUSSIAN && sketched(p->method);
   struct Need {
     Buf* b;
     size_t bytes;
   } need[] = {
-      {&h->W, ld * (m + 1) * 8},
+      {p->precision == FAB_MIXED ? &h->W32 : &h->W, ld * (m + 1) * (p->precision == FAB_MIXED ? 4 : 8)},
+      {&h->Wbf, gauss ? ld * (m + 1) * 2 : 0},
+      {&h->G, gauss ? ld * (size_t)p->s * 2 : 0},
       {&h->H, (size_t)(m + 1) * m * 8},
       {&h->sigma, (size_t)(m + 1) * 8},
       {&h->shf, (size_t)(m + 1) * 4},
@@ -500,6 +503,11 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   int rc = FAB_OK;
   cudaStream_t s = (cudaStream_t)p->stream;
   constexpr bool kMixed = sizeof(TV) == 4;
+  // every device buffer this solve touches must exist before the first launch
+  if (!W || !vals || !ws.H || !ws.st || !ws.SV || !ws.part || !ws.gpart ||
+      (p->sketch == FAB_SK_GAUSSIAN && sketched(p->method) && (!ws.Wbf || !ws.G)) ||
+      (p->method == FAB_SKETCHED_LS && !ws.u))
+    return FAB_ENOMEM;
   const int n = h->n, m = p->m, k = p->k;
   const int64_t ld = h->ld;
   const int ldh = m + 1;
