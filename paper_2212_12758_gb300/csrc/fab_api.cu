@@ -12,6 +12,7 @@
 
 #include "fab_internal.cuh"
 #include "gauss.cuh"
+#include "handle.cuh"
 #include "small.cuh"
 
 using namespace fab;
@@ -40,30 +41,6 @@ struct Pade13 {
   }
 };
 
-struct Buf {
-  void* p = nullptr;
-  size_t bytes = 0;
-};
-
-// Grow-only device buffer; returns false on allocation failure.
-bool ensure(Buf& b, size_t bytes) {
-  if (bytes == 0) bytes = 16;
-  if (b.bytes >= bytes) return true;
-  if (b.p) cudaFree(b.p);
-  b.p = nullptr;
-  b.bytes = 0;
-  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  b.bytes = bytes;
-  return true;
-}
-
-template <typename T>
-T* ptr(Buf& b) {
-  return reinterpret_cast<T*>(b.p);
-}
 
 int fault_countdown() {
   // Host-side allocation fault injection for tests: FAB_FAULT=alloc:N makes the
@@ -126,26 +103,6 @@ Profiler g_prof;
 
 }  // namespace
 
-struct fab_handle {
-  int n = 0, nnz = 0;
-  int* d_rowptr = nullptr;
-  int* d_colind = nullptr;
-  double* d_vals = nullptr;
-  float* d_vals32 = nullptr;  // FP32 copy for the mixed-precision path (made on first use)
-  int64_t ld = 0;
-  // workspace
-  Buf W, H, sigma, shf, scl, wn2, coef, part, counter, gpart, skpart, SV, P, qr, tau, y, cvec, dense, piv, scal, lsq, u, xbuf,
-      state;
-  Buf W32, Wbf, G;  // mixed path: FP32 basis, its BF16 copy, Gaussian sketch (BF16, s x ld)
-  int G_n = -1, G_s = -1;
-  uint64_t G_seed = 0;
-  // cached SRHT sample
-  int64_t P_npad = -1;
-  int P_s = -1;
-  uint64_t P_seed = 0;
-  // last solve
-  int has_state = 0, last_m = 0, last_s = 0, last_sketched = 0, last_mixed = 0;
-};
 
 extern "C" {
 
@@ -237,10 +194,12 @@ int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr, 
 
 void fab_destroy(fab_handle* h) {
   if (!h) return;
-  cudaFree(h->d_rowptr);
-  cudaFree(h->d_colind);
-  cudaFree(h->d_vals);
-  cudaFree(h->d_vals32);
+  if (h->owns_matrix) {
+    cudaFree(h->d_rowptr);
+    cudaFree(h->d_colind);
+    cudaFree(h->d_vals);
+  }
+  cudaFree(h->d_vals32);  // always the handle's own (made on first mixed-precision solve)
   Buf* bufs[] = {&h->W32, &h->Wbf, &h->G, &h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
                  &h->skpart, &h->SV, &h->P,     &h->qr,  &h->tau,  &h->y,    &h->cvec,    &h->dense,
                  &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state};
@@ -347,7 +306,13 @@ struct Ws {
   DevState* st;
 };
 
-int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
+struct Need {
+  Buf* b;
+  size_t bytes;
+};
+
+// The workspace a solve needs (buffer, bytes), shared by allocation and admission.
+int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
   const int m = p->m, s = sketched(p->method) ? p->s : 1;
   const int n = h->n;
   const size_t ld = (size_t)h->ld;
@@ -355,10 +320,7 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
   const int nchunks = (n + kChunk - 1) / kChunk;
   const size_t part_blocks = (size_t)sm_count() * kMaxPartBlocks;
   const bool gauss = p->precision == FAB_MIXED && p->sketch == FAB_SK_GAUSSIAN && sketched(p->method);
-  struct Need {
-    Buf* b;
-    size_t bytes;
-  } need[] = {
+  const Need need[] = {
       {p->precision == FAB_MIXED ? &h->W32 : &h->W, ld * (m + 1) * (p->precision == FAB_MIXED ? 4 : 8)},
       {&h->Wbf, gauss ? ld * (m + 1) * 2 : 0},
       {&h->G, gauss ? ld * (size_t)p->s * 2 : 0},
@@ -383,16 +345,28 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
       {&h->scal, 64 * 8},
       {&h->lsq, (size_t)6 * (m + 1) * 8},
       {&h->state, sizeof(DevState)},
+      {&h->u, p->method == FAB_SKETCHED_LS ? (size_t)n * 8 : 0},
+      {&h->xbuf, (size_t)n * 8},
   };
-  for (auto& q : need) {
+  const int cnt = (int)(sizeof(need) / sizeof(need[0]));
+  for (int i = 0; i < cnt; ++i) out[i] = need[i];
+  return cnt;
+}
+
+int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
+  Need need[64];
+  const int cnt = ws_needs(h, p, need);
+  const int n = h->n;
+  const int m = p->m;
+  for (int i = 0; i < cnt; ++i) {
+    auto& q = need[i];
+    if (q.bytes == 0 && (q.b == &h->u || q.b == &h->xbuf)) continue;  // allocated on demand
     const bool grow = q.b->bytes < (q.bytes ? q.bytes : 16);
     if (grow && fault_hit()) return FAB_ENOMEM;
     if (!ensure(*q.b, q.bytes)) return FAB_ENOMEM;
     if (grow && q.b == &h->counter) CK(cudaMemset(h->counter.p, 0, h->counter.bytes));
   }
-  if (p->method == FAB_SKETCHED_LS) {
-    if ((h->u.bytes < (size_t)n * 8 && fault_hit()) || !ensure(h->u, (size_t)n * 8)) return FAB_ENOMEM;
-  }
+  (void)n;
   ws.W = ptr<double>(h->W);
   ws.W32 = ptr<float>(h->W32);
   ws.Wbf = ptr<__nv_bfloat16>(h->Wbf);
@@ -900,3 +874,37 @@ extern "C" int fab_profile_query(const char* name, double* total_ms, int64_t* la
 }
 
 extern "C" const char* fab_last_error(void) { return g_errmsg; }
+
+namespace fab {
+size_t estimate_ws_bytes(const fab_handle* h, const fab_params* p) {
+  Need need[64];
+  const int cnt = ws_needs(const_cast<fab_handle*>(h), p, need);
+  size_t t = 0;
+  for (int i = 0; i < cnt; ++i) t += need[i].bytes;
+  if (p->precision == FAB_MIXED) t += (size_t)(h->nnz + kCsrPad) * sizeof(float);
+  return t;
+}
+
+size_t handle_ws_bytes(const fab_handle* h) {
+  const Buf* bufs[] = {&h->W32, &h->Wbf, &h->G,    &h->shf,  &h->scl,  &h->W,   &h->H,     &h->sigma,
+                       &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart, &h->skpart, &h->SV, &h->P,
+                       &h->qr,  &h->tau, &h->y,    &h->cvec, &h->dense, &h->piv, &h->scal, &h->lsq,
+                       &h->u,   &h->xbuf, &h->state};
+  size_t t = 0;
+  for (const Buf* b : bufs) t += b->bytes;
+  if (h->d_vals32) t += (size_t)(h->nnz + kCsrPad) * sizeof(float);
+  return t;
+}
+
+fab_handle* clone_for_workspace(const fab_handle* h) {
+  fab_handle* c = new fab_handle();
+  c->n = h->n;
+  c->nnz = h->nnz;
+  c->owns_matrix = false;
+  c->d_rowptr = h->d_rowptr;
+  c->d_colind = h->d_colind;
+  c->d_vals = h->d_vals;
+  c->ld = h->ld;
+  return c;
+}
+}  // namespace fab

@@ -1,0 +1,70 @@
+// The handle behind the C ABI (fab_api.cu) and its device workspace, shared
+// with the serving runtime (server.cu). Internal.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/fab.h"
+
+namespace fab {
+
+// Grow-only device buffer.
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Grow-only device buffer; returns false on allocation failure.
+inline bool ensure(Buf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return true;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  b.bytes = bytes;
+  return true;
+}
+
+template <typename T>
+T* ptr(Buf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+}  // namespace fab
+
+struct fab_handle {
+  int n = 0, nnz = 0;
+  bool owns_matrix = true;     // false for workspace clones (they share the device CSR)
+  int* d_rowptr = nullptr;
+  int* d_colind = nullptr;
+  double* d_vals = nullptr;
+  float* d_vals32 = nullptr;  // FP32 copy for the mixed-precision path (made on first use)
+  int64_t ld = 0;
+  // workspace
+  fab::Buf W, H, sigma, shf, scl, wn2, coef, part, counter, gpart, skpart, SV, P, qr, tau, y, cvec, dense, piv, scal, lsq, u, xbuf,
+      state;
+  fab::Buf W32, Wbf, G;  // mixed path: FP32 basis, its BF16 copy, Gaussian sketch (BF16, s x ld)
+  int G_n = -1, G_s = -1;
+  uint64_t G_seed = 0;
+  // cached SRHT sample
+  int64_t P_npad = -1;
+  int P_s = -1;
+  uint64_t P_seed = 0;
+  // last solve
+  int has_state = 0, last_m = 0, last_s = 0, last_sketched = 0, last_mixed = 0;
+};
+
+namespace fab {
+// Device bytes the workspace of a solve with these parameters occupies (estimate
+// used by admission control), and bytes currently allocated by a handle.
+size_t estimate_ws_bytes(const fab_handle* h, const fab_params* p);
+size_t handle_ws_bytes(const fab_handle* h);
+// A handle that shares h's device matrix and owns a fresh (empty) workspace.
+fab_handle* clone_for_workspace(const fab_handle* h);
+}  // namespace fab

@@ -86,4 +86,10 @@ def test_mixed_precision_vs_fp64_oracle(fab, name, build, f, t, m, k, sk, s, met
     x = M.apply(torch.from_numpy(b).cuda(), p).cpu().numpy()
     err = _rel(x, ref.x)
     print(f"\nMIXED {name} method={method}: rel err vs FP64 oracle f_m = {err:.3e}")
-    assert err <= 1e-3
+    # FP32 matrix and basis (u = 2^-24): m steps of the recurrence move the basis by
+    # about m u times the basis conditioning; Arnoldi and the LSQR variant project
+    # with FP64 reductions (<= 1e-5 observed <= 1.2e-6); the sketch-only variants
+    # also see the BF16 rounding of the sketched basis and the truncated basis's
+    # conditioning directly (<= 2e-4; observed <= 6e-5 on the power-law graph).
+    tol = 1e-5 if method in (krylov.ARNOLDI, krylov.SKETCHED_LS) else 2e-4
+    assert err <= tol
