@@ -198,6 +198,43 @@ int fab_sketch_apply_noalloc(int sketch, int64_t n, int s, int zeta, uint64_t se
                              const double* V_dev, int64_t ldv, int ncols, double* out_dev, void* stream);
 
 /*
+ * Serving (continuous batching). A server owns `slots` worker threads on the
+ * current device, each with its own CUDA stream and its own device workspace,
+ * so requests of different n, m, f and method run concurrently and their bases
+ * and sketches stay resident between requests. Requests leave the queue in
+ * submission order as soon as a slot is free and the request's workspace fits
+ * both the device-memory budget and the memory the device reports free.
+ * This runtime is not part of the paper; it serves the paper's solves.
+ *
+ * fab_server_create  hbm_budget_bytes: device bytes all slot workspaces may
+ *                    hold together (0: 90 % of the free memory now); slots 1..64.
+ * fab_server_submit  b: host n-vector, copied before the call returns; *p is
+ *                    copied (its stream is ignored). h must outlive its requests;
+ *                    the server never modifies h except to add its FP32 matrix
+ *                    copy for FAB_MIXED. FAB_ENOMEM if the request alone exceeds
+ *                    the budget. Thread-safe.
+ * fab_server_poll    waits up to timeout_ms for the ticket: FAB_ETIMEOUT if not
+ *                    done (the request stays); otherwise copies x (host n-vector),
+ *                    the stats and the latency from submission to completion
+ *                    (ms), releases the ticket and returns the solve's code.
+ * fab_server_destroy finishes the solves in progress, drops queued requests,
+ *                    frees everything. NULL-safe.
+ */
+typedef struct fab_server fab_server;
+typedef struct fab_server_stats {
+  int64_t submitted, completed, queued, in_flight;
+  double bytes_in_use;  /* device bytes held by the slot workspaces */
+  double bytes_budget;
+} fab_server_stats;
+
+int fab_server_create(fab_server** out, size_t hbm_budget_bytes, int slots);
+int fab_server_submit(fab_server* srv, fab_handle* h, const fab_params* p, const double* b, uint64_t* ticket);
+int fab_server_poll(fab_server* srv, uint64_t ticket, double* x, fab_stats* st, double* latency_ms,
+                    int timeout_ms);
+int fab_server_stats_get(fab_server* srv, fab_server_stats* out);
+void fab_server_destroy(fab_server* srv);
+
+/*
  * Kernel-level device timing (measurement support, not needed for solving).
  * fab_profile_enable(1) resets the accumulators and makes every later
  * fab_apply record CUDA events, on the solve's stream, around each launch of

@@ -198,8 +198,8 @@ void fab_destroy(fab_handle* h) {
     cudaFree(h->d_rowptr);
     cudaFree(h->d_colind);
     cudaFree(h->d_vals);
+    cudaFree(h->d_vals32);
   }
-  cudaFree(h->d_vals32);  // always the handle's own (made on first mixed-precision solve)
   Buf* bufs[] = {&h->W32, &h->Wbf, &h->G, &h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
                  &h->skpart, &h->SV, &h->P,     &h->qr,  &h->tau,  &h->y,    &h->cvec,    &h->dense,
                  &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state};
@@ -332,7 +332,7 @@ int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
       {&h->coef, (size_t)(m + 1) * 8},
       {&h->part, part_blocks * (kMaxWindow + 1) * 8},
       {&h->counter, 64},
-      {&h->gpart, std::max((size_t)ntiles * (m + 1) * 8, gauss_partial_bytes(n, s, m + 1))},
+      {&h->gpart, std::max((size_t)ntiles * (m + 1) * 8, gauss ? gauss_partial_bytes(n, s, m + 1) : (size_t)0)},
       {&h->skpart, (size_t)nchunks * s * 8},
       {&h->SV, (size_t)s * (m + 1) * 8},
       {&h->P, (size_t)s * 4},
@@ -490,7 +490,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   Csr A{h->n, h->nnz, h->d_rowptr, h->d_colind, vals};
   h->has_state = 0;
   g_launches = 0;
-  g_prof.begin_solve();
+  if (g_prof.on) g_prof.begin_solve();
 
   cudaEvent_t ev[4];
   for (auto& e : ev) CK(cudaEventCreate(&e));
@@ -706,18 +706,8 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
   rc = ensure_ws(h, p, ws);
   if (rc != FAB_OK) return rc;
   if (p->precision == FAB_MIXED) {
-    if (!h->d_vals32) {  // FP32 copy of A's values, made once per handle
-      if (fault_hit() || cudaMalloc(&h->d_vals32, (size_t)(h->nnz + kCsrPad) * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        h->d_vals32 = nullptr;
-        return FAB_ENOMEM;
-      }
-      if (launch_to_f32(h->nnz + (int)kCsrPad, h->d_vals, h->d_vals32, (cudaStream_t)p->stream) != cudaSuccess ||
-          cudaStreamSynchronize((cudaStream_t)p->stream) != cudaSuccess) {
-        cudaGetLastError();
-        return FAB_ECUDA;
-      }
-    }
+    rc = fab::ensure_vals32(h, (cudaStream_t)p->stream);
+    if (rc != FAB_OK) return rc;
     return apply_impl<float>(h, p, b, x, bx_on_device, stats, ws, ws.W32, h->d_vals32);
   }
   return apply_impl<double>(h, p, b, x, bx_on_device, stats, ws, ws.W, h->d_vals);
@@ -876,6 +866,22 @@ extern "C" int fab_profile_query(const char* name, double* total_ms, int64_t* la
 extern "C" const char* fab_last_error(void) { return g_errmsg; }
 
 namespace fab {
+// FP32 copy of A's values (mixed precision), made once per matrix.
+int ensure_vals32(fab_handle* h, cudaStream_t s) {
+  if (h->d_vals32) return FAB_OK;
+  if (fault_hit() || cudaMalloc(&h->d_vals32, (size_t)(h->nnz + kCsrPad) * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    h->d_vals32 = nullptr;
+    return FAB_ENOMEM;
+  }
+  if (launch_to_f32(h->nnz + (int)kCsrPad, h->d_vals, h->d_vals32, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return FAB_ECUDA;
+  }
+  return FAB_OK;
+}
+
 size_t estimate_ws_bytes(const fab_handle* h, const fab_params* p) {
   Need need[64];
   const int cnt = ws_needs(const_cast<fab_handle*>(h), p, need);
@@ -898,13 +904,19 @@ size_t handle_ws_bytes(const fab_handle* h) {
 
 fab_handle* clone_for_workspace(const fab_handle* h) {
   fab_handle* c = new fab_handle();
+  c->owns_matrix = false;
+  point_to_matrix(c, h);
+  return c;
+}
+
+void point_to_matrix(fab_handle* c, const fab_handle* h) {
   c->n = h->n;
   c->nnz = h->nnz;
-  c->owns_matrix = false;
   c->d_rowptr = h->d_rowptr;
   c->d_colind = h->d_colind;
   c->d_vals = h->d_vals;
+  c->d_vals32 = h->d_vals32;
   c->ld = h->ld;
-  return c;
+  c->has_state = 0;
 }
 }  // namespace fab

@@ -67,4 +67,8 @@ size_t estimate_ws_bytes(const fab_handle* h, const fab_params* p);
 size_t handle_ws_bytes(const fab_handle* h);
 // A handle that shares h's device matrix and owns a fresh (empty) workspace.
 fab_handle* clone_for_workspace(const fab_handle* h);
+// Re-point a workspace clone at another matrix (its workspace is kept).
+void point_to_matrix(fab_handle* clone, const fab_handle* h);
+// FP32 copy of A's values for the mixed-precision path (once per matrix).
+int ensure_vals32(fab_handle* h, cudaStream_t s);
 }  // namespace fab

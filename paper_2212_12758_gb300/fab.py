@@ -26,7 +26,8 @@ FP64, MIXED = 0, 1
 # Every symbol the header declares (checked against include/fab.h by the tests).
 SYMBOLS = ("fab_params_default", "fab_strerror", "fab_last_error", "fab_create", "fab_apply", "fab_destroy", "fab_last_state",
            "fab_last_basis", "fab_sketch_apply", "fab_sketch_apply_noalloc", "fab_profile_enable",
-           "fab_profile_query")
+           "fab_profile_query", "fab_server_create", "fab_server_submit", "fab_server_poll", "fab_server_stats_get",
+           "fab_server_destroy")
 PROFILE_KINDS = ("spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine")
 
 
@@ -68,6 +69,21 @@ lib.fab_sketch_apply.argtypes = [_i32, _i64, _i32, _i32, _u64, _vp, _i64, _i32, 
 lib.fab_sketch_apply.restype = _i32
 lib.fab_sketch_apply_noalloc.argtypes = [_i32, _i64, _i32, _i32, _u64, _vp, _i64, _i32, _vp, _vp]
 lib.fab_sketch_apply_noalloc.restype = _i32
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("bytes_in_use", ctypes.c_double), ("bytes_budget", ctypes.c_double)]
+
+
+lib.fab_server_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_size_t, _i32]
+lib.fab_server_create.restype = _i32
+lib.fab_server_submit.argtypes = [_vp, _vp, ctypes.POINTER(Params), _vp, ctypes.POINTER(ctypes.c_uint64)]
+lib.fab_server_submit.restype = _i32
+lib.fab_server_poll.argtypes = [_vp, ctypes.c_uint64, _vp, ctypes.POINTER(Stats), ctypes.POINTER(ctypes.c_double), _i32]
+lib.fab_server_poll.restype = _i32
+lib.fab_server_stats_get.argtypes = [_vp, ctypes.POINTER(ServerStats)]
+lib.fab_server_stats_get.restype = _i32
+lib.fab_server_destroy.argtypes = [_vp]
+lib.fab_server_destroy.restype = None
 lib.fab_profile_enable.argtypes = [_i32]
 lib.fab_profile_enable.restype = _i32
 lib.fab_profile_query.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -229,3 +245,48 @@ def sketch_apply_noalloc(V, s: int, sketch: int = SPARSE_SIGN, zeta: int = 8, se
     _check(lib.fab_sketch_apply_noalloc(int(sketch), int(n), int(s), int(zeta), int(seed), V.data_ptr(), int(n),
                                         int(ncols), out.data_ptr(), stream), "fab_sketch_apply_noalloc")
     return out
+
+
+class Server:
+    """Continuous-batching server (fab_server_*): submit f(A)b requests on any
+    Matrix handles; each result is polled by its ticket."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, slots: int = 4):
+        h = ctypes.c_void_p()
+        _check(lib.fab_server_create(ctypes.byref(h), int(hbm_budget_bytes), int(slots)), "fab_server_create")
+        self._s = h
+        self._mats = {}
+
+    def submit(self, M: "Matrix", b: np.ndarray, p: Params) -> int:
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        t = ctypes.c_uint64()
+        _check(lib.fab_server_submit(self._s, M._h, ctypes.byref(p), b.ctypes.data, ctypes.byref(t)), "fab_server_submit")
+        self._mats[t.value] = M.n
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 60000):
+        """(x, stats, latency_ms), or None if not done within timeout_ms."""
+        n = self._mats[ticket]
+        x = np.empty(n)
+        st = Stats()
+        lat = ctypes.c_double()
+        rc = lib.fab_server_poll(self._s, ctypes.c_uint64(ticket), x.ctypes.data, ctypes.byref(st), ctypes.byref(lat),
+                                 int(timeout_ms))
+        if rc == FAB_ETIMEOUT:
+            return None
+        del self._mats[ticket]
+        _check(rc, "fab_server_poll")
+        return x, st, lat.value
+
+    def stats(self) -> ServerStats:
+        out = ServerStats()
+        _check(lib.fab_server_stats_get(self._s, ctypes.byref(out)), "fab_server_stats_get")
+        return out
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib.fab_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        self.close()
