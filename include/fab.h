@@ -105,7 +105,8 @@ const char* fab_strerror(int code);
 
 /* Detail of the last FAB_ECUDA returned on this host thread: the kernel class
  * whose launch (or, with FAB_SYNC_CHECK=1 in the environment, whose execution)
- * failed and the CUDA error string. Empty if none. */
+ * failed and the CUDA error string. Empty if none. fab_server_poll returning
+ * FAB_ECUDA sets it to the detail of the slot thread that ran the solve. */
 const char* fab_last_error(void);
 
 /*
@@ -241,7 +242,7 @@ void fab_server_destroy(fab_server* srv);
  * the kernel classes below; fab_profile_enable(0) stops recording.
  * fab_profile_query returns the accumulated device time (ms) and the number of
  * launches of one class:
- *   "spmv_dots"      SpMV fused with the window dot products (Alg. 2 lines 3-5)
+ *   "spmv_dots"      SpMV fused with the window dot products (Alg. 2)
  *   "update"         window update + norm + fused sketch of the new vector
  *   "sketch_reduce"  cross-chunk reduction of the sketch
  *   "gemv_t"         V^T w passes (Arnoldi, LSQR)

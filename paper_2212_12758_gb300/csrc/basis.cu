@@ -13,6 +13,9 @@
 
 #include <cuda_bf16.h>
 
+#include <map>
+#include <mutex>
+
 #include "fab_internal.cuh"
 
 namespace fab {
@@ -236,9 +239,10 @@ cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int
   if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
   const size_t smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
   if (occ[kw] == 0) {
-    cudaFuncSetAttribute(fns[kw], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kw], fns[kw], kThreads, smem);
-    if (occ[kw] < 1) occ[kw] = 1;
+    ensure_smem_limit(fns[kw], smem);
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[kw], kThreads, smem);
+    occ[kw] = o < 1 ? 1 : o;
   }
   const int need = (A.n + kSpmvTile - 1) / kSpmvTile;
   int grid = sm_count() * occ[kw];
@@ -579,7 +583,8 @@ cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const
     case SK_GAUSS: fn = (const void*)k_update<SK_GAUSS, TV>; break;
     default: fn = (const void*)k_update<SK_NONE, TV>;
   }
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_limit(fn, smem);
+  if (e != cudaSuccess) return e;
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
   if (occ < 1) occ = 1;
@@ -807,6 +812,24 @@ int sm_count() {
     if (g_sms <= 0) g_sms = 1;
   }
   return g_sms;
+}
+
+// The dynamic shared-memory limit is a process-wide attribute of a kernel, and
+// several host threads (the serving slots) launch the same kernels with different
+// sizes. Setting it to each launch's own size would let one thread lower it between
+// another thread's set and launch, so it only ever grows, under a lock.
+cudaError_t ensure_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = limit[{dev, fn}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 int grid_rows(int n) {

@@ -866,6 +866,10 @@ extern "C" int fab_profile_query(const char* name, double* total_ms, int64_t* la
 extern "C" const char* fab_last_error(void) { return g_errmsg; }
 
 namespace fab {
+void set_last_error(const char* msg) { snprintf(g_errmsg, sizeof(g_errmsg), "%s", msg ? msg : ""); }
+}  // namespace fab
+
+namespace fab {
 // FP32 copy of A's values (mixed precision), made once per matrix.
 int ensure_vals32(fab_handle* h, cudaStream_t s) {
   if (h->d_vals32) return FAB_OK;

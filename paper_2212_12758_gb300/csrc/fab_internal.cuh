@@ -250,6 +250,8 @@ cudaError_t launch_to_f32(int n, const double* x, float* y, cudaStream_t s);
 
 int sm_count();              // multiprocessors of the current device
 int grid_rows(int n);        // grid for the thread-per-row kernels
+// Raises (never lowers) kernel fn's dynamic shared-memory limit to at least `bytes`; thread-safe.
+cudaError_t ensure_smem_limit(const void* fn, size_t bytes);
 constexpr int kMaxPartBlocks = 64;  // partial buffers hold sm_count() * kMaxPartBlocks blocks
 constexpr int kTileRows = 2048;     // rows per GEMV-T tile
 

@@ -318,11 +318,12 @@ cudaError_t launch_gauss_sketch(const __nv_bfloat16* G, const __nv_bfloat16* Wbf
   CUtensorMap tmA, tmB;
   if (!make_map(&tmA, G, n, s, ld, kBM) || !make_map(&tmB, Wbf, n, ncols, ld, p.npad)) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kStages * (kBM * kBK * 2 + (size_t)p.npad * kBK * 2) + 1024;
-  cudaFuncSetAttribute(k_gauss_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_limit((const void*)k_gauss_mma, smem);
+  if (e != cudaSuccess) return e;
   float* fpart = reinterpret_cast<float*>(part);
   k_gauss_mma<<<dim3(p.mtiles, p.splits), kGThreads, smem, stream>>>(tmA, tmB, p.nkb, p.kb_per_split, p.npad, p.mpad,
                                                                       fpart, st);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_gauss_reduce<<<dim3((ncols + 127) / 128, s), 128, 0, stream>>>(fpart, p.splits, p.mpad, p.npad, s, ncols, sigma,
                                                                    SV);

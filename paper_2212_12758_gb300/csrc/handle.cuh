@@ -71,4 +71,7 @@ fab_handle* clone_for_workspace(const fab_handle* h);
 void point_to_matrix(fab_handle* clone, const fab_handle* h);
 // FP32 copy of A's values for the mixed-precision path (once per matrix).
 int ensure_vals32(fab_handle* h, cudaStream_t s);
+// Sets this host thread's fab_last_error() text (carries a serving slot's detail to the poller).
+void set_last_error(const char* msg);
+
 }  // namespace fab

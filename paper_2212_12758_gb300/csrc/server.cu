@@ -7,6 +7,7 @@
 // both the server's device-memory budget and the memory the device reports free;
 // a blocked slot first releases its own cached workspace. Latency is measured
 // from submission to completion.
+#include <stdio.h>
 #include <string.h>
 
 #include <chrono>
@@ -30,6 +31,7 @@ struct Request {
   std::vector<double> b, x;
   size_t need = 0;  // estimated workspace bytes
   int rc = FAB_OK;
+  char err[256] = "";  // fab_last_error() of the slot thread when rc == FAB_ECUDA
   fab_stats st{};
   Clock::time_point t_submit, t_done;
   bool done = false;
@@ -117,6 +119,7 @@ void worker(fab_server* s, int self) {
     p.stream = sl.stream;
     r->x.assign(r->b.size(), 0.0);
     r->rc = fab_apply(sl.ws, &p, r->b.data(), r->x.data(), 0, &r->st);
+    if (r->rc == FAB_ECUDA) snprintf(r->err, sizeof(r->err), "%s", fab_last_error());
     {
       std::lock_guard<std::mutex> lk(s->mu);
       sl.held = fab::handle_ws_bytes(sl.ws);
@@ -210,6 +213,7 @@ extern "C" int fab_server_poll(fab_server* s, uint64_t ticket, double* x, fab_st
   if (st) *st = r->st;
   if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
   const int rc = r->rc;
+  if (rc == FAB_ECUDA) fab::set_last_error(r->err);
   s->reqs.erase(it);
   delete r;
   return rc;

@@ -841,7 +841,8 @@ __global__ void __launch_bounds__(256) k_lu_cluster(double* __restrict__ M, int 
 namespace {
 template <typename K>
 cudaError_t launch_cluster(K kernel, int cl, size_t smem, cudaStream_t s, void** args) {
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_limit((const void*)kernel, smem);
+  if (e != cudaSuccess) return e;
   if (cl > 8) cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cl, 1, 1);
