@@ -236,6 +236,51 @@ int fab_server_stats_get(fab_server* srv, fab_server_stats* out);
 void fab_server_destroy(fab_server* srv);
 
 /*
+ * Batched solves: many f(A)b of uneven size (different matrices, n, m, k, s, f)
+ * as one CUDA graph. Work items are (solve, basis step, tile): for each basis
+ * step c the graph holds one launch per (window k, sketch kind) group covering
+ * every solve still building its basis (SpMV + window dots, window update +
+ * norm + fused sketch, sketch reduce: Alg. 2 with the sketch of §2.1.1). A
+ * solve's blocks in such a launch are the blocks of its own launch, so its
+ * basis and sketch are bit for bit those fab_apply computes. When a solve's
+ * basis is complete, its small stage (Householder QR of the sketch, the
+ * sketch-and-solve projection of eq. sFOM, or none for Alg. 5; f(H)e_1 by
+ * Pade scaling and squaring or Denman-Beavers) runs as one CTA on a second
+ * branch of the graph, then its combine x = ||b|| V_m c.
+ *
+ * fab_batch_create  plans `count` solves (hs[i], ps[i]) and allocates every
+ *                   workspace at once (one device allocation; FAB_ENOMEM if it
+ *                   does not fit), then captures and instantiates the graph.
+ *                   Supported: method FAB_SKETCHED_FAST (sketch SRHT or sparse
+ *                   sign) or FAB_NOPROJ; precision the same for all solves
+ *                   (FAB_FP64 or FAB_MIXED); anything else FAB_EINVAL. A
+ *                   handle may appear several times; handles must outlive the
+ *                   batch and must not be destroyed or used concurrently while
+ *                   it runs. ps[0].stream is used for set-up.
+ * fab_batch_exec    one run: copies bs[i] (n_i FP64, host or device; NULL bs =
+ *                   inputs already written to fab_batch_input(bt, i)), launches
+ *                   the graph on `stream` (cudaStream_t or NULL), copies each
+ *                   result to xs[i] (NULL xs or xs[i] = leave it at
+ *                   fab_batch_output(bt, i)), waits, and fills sts[i]
+ *                   (nullable). Returns the first non-FAB_OK solve status
+ *                   (the other solves' results are valid) or FAB_OK.
+ * fab_batch_input / fab_batch_output  device addresses (n_i FP64) of solve i's
+ *                   start vector and result; NULL for a bad index.
+ * fab_batch_kernels number of kernel launches in the graph.
+ * fab_batch_destroy NULL-safe.
+ * fab_batch_run     create + exec + destroy in one call (bs, xs required).
+ */
+typedef struct fab_batch fab_batch;
+int fab_batch_create(fab_batch** out, fab_handle* const* hs, const fab_params* ps, int count);
+int fab_batch_exec(fab_batch* bt, const double* const* bs, double* const* xs, fab_stats* sts, void* stream);
+double* fab_batch_input(fab_batch* bt, int i);
+double* fab_batch_output(fab_batch* bt, int i);
+int fab_batch_kernels(const fab_batch* bt);
+void fab_batch_destroy(fab_batch* bt);
+int fab_batch_run(fab_handle* const* hs, const fab_params* ps, const double* const* bs, double* const* xs, int count,
+                  fab_stats* sts);
+
+/*
  * Kernel-level device timing (measurement support, not needed for solving).
  * fab_profile_enable(1) resets the accumulators and makes every later
  * fab_apply record CUDA events, on the solve's stream, around each launch of

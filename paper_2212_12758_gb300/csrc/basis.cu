@@ -77,13 +77,15 @@ cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s) {
 constexpr int kSpmvTile = kThreads;  // rows per tile, one per thread
 constexpr int kSpmvCap = 2048;       // nonzeros per stage (vals 16 KB + colind 8 KB)
 
+// The work of block `bid` of `nblk` (a launch of its own, or one solve's share
+// of a batched wave) is a function of (bid, nblk) only, so a solve gives the
+// same bits whichever way its blocks are launched.
 template <typename TV, int KW>
-__global__ __launch_bounds__(kThreads) void k_spmv_dots(
-    Csr A, TV* __restrict__ W, int64_t ld, int c, int j0, int kw, ColScale cs, double* __restrict__ H,
+__device__ __forceinline__ void spmv_dots_body(
+    const Csr& A, TV* __restrict__ W, int64_t ld, int c, int j0, int kw, const ColScale& cs, double* __restrict__ H,
     int ldh, double* __restrict__ coef, double* __restrict__ wn2, double* __restrict__ part,
-    unsigned* __restrict__ counter, DevState* st) {
+    unsigned* __restrict__ counter, DevState* st, int bid, int nblk, unsigned char* smem_raw) {
   constexpr int NV = kMaxWindow + 1;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   TV* s_vals = reinterpret_cast<TV*>(smem_raw);                                // [2][kSpmvCap]
   int* s_col = reinterpret_cast<int*>(smem_raw + 2 * kSpmvCap * sizeof(TV));   // [2][kSpmvCap]
   const TV* Avals = reinterpret_cast<const TV*>(A.vals);
@@ -132,13 +134,13 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
   };
   uint32_t par0 = 0, par1 = 0;
   int it = 0;
-  int tile = blockIdx.x;
+  int tile = bid;
   if (tid == 0 && tile < ntiles) issue(tile, 0);
   __syncthreads();
   bool failed = false;
-  for (; tile < ntiles; tile += gridDim.x, ++it) {
+  for (; tile < ntiles; tile += nblk, ++it) {
     const int stg = it & 1;
-    const int next = tile + gridDim.x;
+    const int next = tile + nblk;
     if (tid == 0 && next < ntiles) issue(next, stg ^ 1);
     const bool staged = s_staged[stg] != 0;
     if (staged) {
@@ -207,10 +209,10 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
   block_sum<NV>(accd, sh);
   if (tid == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) part[(size_t)blockIdx.x * NV + q] = accd[q];
+    for (int q = 0; q < NV; ++q) part[(size_t)bid * NV + q] = accd[q];
   }
-  if (!last_block(counter)) return;
-  sum_partials(part, gridDim.x, NV, tot, sh);
+  if (!last_block(counter, (unsigned)nblk)) return;
+  sum_partials(part, nblk, NV, tot, sh);
   double pinv;
   const double pinv_hi = pow2_split(-ksh, &pinv);
   const double tau = (cs.sigma[c - 1] * pinv_hi) * pinv;  // exact: power-of-two factors
@@ -227,28 +229,52 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(
   }
 }
 
+template <typename TV, int KW>
+__global__ __launch_bounds__(kThreads) void k_spmv_dots(Csr A, TV* __restrict__ W, int64_t ld, int c, int j0, int kw,
+                                                         ColScale cs, double* __restrict__ H, int ldh,
+                                                         double* __restrict__ coef, double* __restrict__ wn2,
+                                                         double* __restrict__ part, unsigned* __restrict__ counter,
+                                                         DevState* st) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  spmv_dots_body<TV, KW>(A, W, ld, c, j0, kw, cs, H, ldh, coef, wn2, part, counter, st, blockIdx.x, gridDim.x,
+                         smem_raw);
+}
+
 template <typename TV>
-cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int kw, ColScale cs,
-                             double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
-                             DevState* st, cudaStream_t s) {
+const void* spmv_fn(int kw) {
   static const void* fns[kMaxWindow + 1] = {
       (const void*)k_spmv_dots<TV, 0>, (const void*)k_spmv_dots<TV, 1>, (const void*)k_spmv_dots<TV, 2>,
       (const void*)k_spmv_dots<TV, 3>, (const void*)k_spmv_dots<TV, 4>, (const void*)k_spmv_dots<TV, 5>,
       (const void*)k_spmv_dots<TV, 6>, (const void*)k_spmv_dots<TV, 7>, (const void*)k_spmv_dots<TV, 8>};
+  return fns[kw];
+}
+
+template <typename TV>
+int spmv_grid(int n, int kw) {
   static int occ[kMaxWindow + 1] = {0};
-  if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
   if (occ[kw] == 0) {
-    ensure_smem_limit(fns[kw], smem);
+    const size_t smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
+    ensure_smem_limit(spmv_fn<TV>(kw), smem);
     int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fns[kw], kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmv_fn<TV>(kw), kThreads, smem);
     occ[kw] = o < 1 ? 1 : o;
   }
-  const int need = (A.n + kSpmvTile - 1) / kSpmvTile;
-  int grid = sm_count() * occ[kw];
-  if (need < grid) grid = need < 1 ? 1 : need;
+  const int need = (n + kSpmvTile - 1) / kSpmvTile;
+  const int grid = sm_count() * occ[kw];
+  return need < grid ? (need < 1 ? 1 : need) : grid;
+}
+template int spmv_grid<double>(int, int);
+template int spmv_grid<float>(int, int);
+
+template <typename TV>
+cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int kw, ColScale cs,
+                             double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
+                             DevState* st, cudaStream_t s) {
+  if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
+  const int grid = spmv_grid<TV>(A.n, kw);
   void* args[] = {(void*)&A, &W, &ld, &c, &j0, &kw, &cs, &H, &ldh, &coef, &wn2, &part, &counter, &st};
-  return cudaLaunchKernel(fns[kw], dim3(grid), dim3(kThreads), args, smem, s);
+  return cudaLaunchKernel(spmv_fn<TV>(kw), dim3(grid), dim3(kThreads), args, smem, s);
 }
 template cudaError_t launch_spmv_dots<double>(const Csr&, double*, int64_t, int, int, int, ColScale, double*, int,
                                               double*, double*, double*, unsigned*, DevState*, cudaStream_t);
@@ -435,12 +461,12 @@ constexpr int kModeNorm = 1;
 constexpr int kModeInit = 2;
 
 template <int SK, typename TV>
-__global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(int n, TV* __restrict__ W, int64_t ld, int c, int j0, int nc,
-                                                      const double* __restrict__ coef, double* __restrict__ H, int ldh,
-                                                      ColScale cs, const double* __restrict__ wn2,
-                                                      int mode, double* __restrict__ part,
-                                                      unsigned* __restrict__ counter, SketchDev sk, DevState* st) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void update_body(int n, TV* __restrict__ W, int64_t ld, int c, int j0, int nc,
+                                            const double* __restrict__ coef, double* __restrict__ H, int ldh,
+                                            const ColScale& cs, const double* __restrict__ wn2, int mode,
+                                            double* __restrict__ part, unsigned* __restrict__ counter,
+                                            const SketchDev& sk, DevState* st, int bid, int nblk,
+                                            unsigned char* smem_raw) {
   __shared__ double sh[32];
   __shared__ double tot[1];
   __shared__ int s_int[32];
@@ -464,7 +490,7 @@ __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(in
   const TV* Wb = W + (size_t)j0 * ld;
   double nrm = 0.0;
   const int nchunks = (n + kChunk - 1) / kChunk;
-  for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+  for (int chunk = bid; chunk < nchunks; chunk += nblk) {
     const int base = chunk * kChunk + threadIdx.x;
     TV v[kRowsPerThread];
     TV nrm_c = (TV)0;  // this chunk's share in the element type, added to nrm in FP64
@@ -516,15 +542,15 @@ __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(in
     }
   }
   if (sk_acc) {  // this block's share of the sketch (its chunks, fixed order)
-    double* out = sk.part + (size_t)blockIdx.x * sk.s;
+    double* out = sk.part + (size_t)bid * sk.s;
     for (int q = threadIdx.x; q < sk.s; q += kThreads) out[q] = s_acc[q];
   }
   if (!(mode & kModeNorm)) return;
   double nv[1] = {nrm};
   block_sum<1>(nv, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = nv[0];
-  if (!last_block(counter)) return;
-  sum_partials(part, gridDim.x, 1, tot, sh);
+  if (threadIdx.x == 0) part[bid] = nv[0];
+  if (!last_block(counter, (unsigned)nblk)) return;
+  sum_partials(part, nblk, 1, tot, sh);
   if (threadIdx.x == 0) {
     const double h = sqrt(tot[0]);
     if (mode & kModeInit) {
@@ -562,6 +588,16 @@ __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(in
   }
 }
 
+template <int SK, typename TV>
+__global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(
+    int n, TV* __restrict__ W, int64_t ld, int c, int j0, int nc, const double* __restrict__ coef,
+    double* __restrict__ H, int ldh, ColScale cs, const double* __restrict__ wn2, int mode, double* __restrict__ part,
+    unsigned* __restrict__ counter, SketchDev sk, DevState* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  update_body<SK, TV>(n, W, ld, c, j0, nc, coef, H, ldh, cs, wn2, mode, part, counter, sk, st, blockIdx.x, gridDim.x,
+                      smem_raw);
+}
+
 size_t update_smem_bytes(int kind, int nc, int s) {
   size_t b = ((size_t)nc * 8 + 15) / 16 * 16;
   if (kind == SK_SRHT || kind == SK_SPARSE) b += ((size_t)s * 8 + 15) / 16 * 16;
@@ -571,25 +607,39 @@ size_t update_smem_bytes(int kind, int nc, int s) {
 }
 
 template <typename TV>
-cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H, int ldh,
-                          ColScale cs, const double* wn2, int mode, double* part, unsigned* counter, SketchDev& sk,
-                          DevState* st, cudaStream_t s) {
-  const size_t smem = update_smem_bytes(sk.kind, nc, sk.s);
-  const int nchunks = (n + kChunk - 1) / kChunk;
-  const void* fn = nullptr;
-  switch (sk.kind) {
-    case SK_SRHT: fn = (const void*)k_update<SK_SRHT, TV>; break;
-    case SK_SPARSE: fn = (const void*)k_update<SK_SPARSE, TV>; break;
-    case SK_GAUSS: fn = (const void*)k_update<SK_GAUSS, TV>; break;
-    default: fn = (const void*)k_update<SK_NONE, TV>;
+const void* update_fn(int kind) {
+  switch (kind) {
+    case SK_SRHT: return (const void*)k_update<SK_SRHT, TV>;
+    case SK_SPARSE: return (const void*)k_update<SK_SPARSE, TV>;
+    case SK_GAUSS: return (const void*)k_update<SK_GAUSS, TV>;
+    default: return (const void*)k_update<SK_NONE, TV>;
   }
-  cudaError_t e = ensure_smem_limit(fn, smem);
-  if (e != cudaSuccess) return e;
+}
+
+template <typename TV>
+int update_grid(int kind, int n, int nc, int s, size_t* smem_out) {
+  const size_t smem = update_smem_bytes(kind, nc, s);
+  if (smem_out) *smem_out = smem;
+  const void* fn = update_fn<TV>(kind);
+  if (ensure_smem_limit(fn, smem) != cudaSuccess) return -1;
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
   if (occ < 1) occ = 1;
-  int grid = sm_count() * occ;
-  if (nchunks < grid) grid = nchunks < 1 ? 1 : nchunks;
+  const int nchunks = (n + kChunk - 1) / kChunk;
+  const int grid = sm_count() * occ;
+  return nchunks < grid ? (nchunks < 1 ? 1 : nchunks) : grid;
+}
+template int update_grid<double>(int, int, int, int, size_t*);
+template int update_grid<float>(int, int, int, int, size_t*);
+
+template <typename TV>
+cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H, int ldh,
+                          ColScale cs, const double* wn2, int mode, double* part, unsigned* counter, SketchDev& sk,
+                          DevState* st, cudaStream_t s) {
+  size_t smem = 0;
+  const int grid = update_grid<TV>(sk.kind, n, nc, sk.s, &smem);
+  if (grid < 1) return cudaErrorInvalidValue;
+  const void* fn = update_fn<TV>(sk.kind);
   sk.nparts = grid;  // one sketch partial per block
   void* args[] = {&n, &W, &ld, &c, &j0, &nc, (void*)&coef, &H, &ldh, &cs, (void*)&wn2, &mode, &part, &counter,
                   &sk, &st};
@@ -606,16 +656,22 @@ template cudaError_t launch_update<float>(int, float*, int64_t, int, int, int, c
 // out[q] = scale * sigma[col] * sum_blocks part[block][q] (the per-block partials
 // of k_update already carry the cross-chunk Hadamard signs); one warp per
 // sketch row, fixed order.
-__global__ void k_sketch_reduce(SketchDev sk, const double* __restrict__ sigma, int col, double scale,
-                                double* __restrict__ out, DevState* st) {
+__device__ __forceinline__ void sketch_reduce_body(const SketchDev& sk, int nparts, const double* __restrict__ sigma,
+                                                   int col, double scale, double* __restrict__ out, DevState* st,
+                                                   int bid) {
   if (st->stop) return;
-  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int q = (bid * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (q >= sk.s) return;
   double a = 0.0;
-  for (int b = lane; b < sk.nparts; b += 32) a += sk.part[(size_t)b * sk.s + q];
+  for (int b = lane; b < nparts; b += 32) a += sk.part[(size_t)b * sk.s + q];
   a = warp_sum(a);
   if (lane == 0) out[q] = a * scale * (sigma ? sigma[col] : 1.0);
+}
+
+__global__ void k_sketch_reduce(SketchDev sk, const double* __restrict__ sigma, int col, double scale,
+                                double* __restrict__ out, DevState* st) {
+  sketch_reduce_body(sk, sk.nparts, sigma, col, scale, out, st, blockIdx.x);
 }
 
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
@@ -802,6 +858,188 @@ cudaError_t launch_to_f32(int n, const double* x, float* y, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------- batched waves
+// Each wave kernel finds its solve by a binary search of the wave's block
+// prefix and runs that solve's body with the solve's own (bid, nblk), so every
+// solve of a batch computes exactly what its own launches would.
+__device__ __forceinline__ int wave_slot(const Wave& w, int b) {
+  int lo = 0, hi = w.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(w.pre + mid) <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// state reset, counters, H = 0, W_0 = b (FP64 -> TV)
+template <typename TV>
+__global__ void k_init_wave(const BasisJob<TV>* __restrict__ jobs, Wave w) {
+  const int i = wave_slot(w, blockIdx.x);
+  const BasisJob<TV>* J = jobs + w.ids[i];
+  const int bid = blockIdx.x - w.pre[i], nblk = w.pre[i + 1] - w.pre[i];
+  const int n = J->A.n, m = J->m;
+  if (bid == 0 && threadIdx.x == 0) {
+    DevState* st = J->st;
+    st->m_used = m;
+    st->stop = 0;
+    st->status = FAB_OK;
+    st->flag = 0;
+    st->iters = 0;
+    st->beta = 0.0;
+    for (int q = 0; q < 16; ++q) st->scal[q] = 0.0;
+  }
+  if (bid == 0 && threadIdx.x < 16) J->counter[threadIdx.x] = 0u;
+  const int nh = J->ldh * m;
+  for (int q = bid * blockDim.x + threadIdx.x; q < nh; q += nblk * blockDim.x) J->H[q] = 0.0;
+  for (int r = bid * blockDim.x + threadIdx.x; r < n; r += nblk * blockDim.x) J->W[r] = (TV)J->b[r];
+}
+
+template <typename TV, int KW>
+__global__ __launch_bounds__(kThreads) void k_spmv_wave(const BasisJob<TV>* __restrict__ jobs, Wave w, int c) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int i = wave_slot(w, blockIdx.x);
+  const BasisJob<TV>* J = jobs + w.ids[i];
+  const Csr A = J->A;
+  const ColScale cs = J->cs;
+  spmv_dots_body<TV, KW>(A, J->W, J->ld, c, c - KW, KW, cs, J->H, J->ldh, J->coef, J->wn2, J->part, J->counter,
+                         J->st, blockIdx.x - w.pre[i], w.pre[i + 1] - w.pre[i], smem_raw);
+}
+
+template <int SK, typename TV>
+__global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update_wave(
+    const BasisJob<TV>* __restrict__ jobs, Wave w, int c, int nc, int mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int i = wave_slot(w, blockIdx.x);
+  const BasisJob<TV>* J = jobs + w.ids[i];
+  const ColScale cs = J->cs;
+  const SketchDev sk = J->sk;
+  update_body<SK, TV>(J->A.n, J->W, J->ld, c, c - nc, nc, J->coef, J->H, J->ldh, cs, J->wn2, mode, J->part,
+                      J->counter, sk, J->st, blockIdx.x - w.pre[i], w.pre[i + 1] - w.pre[i], smem_raw);
+}
+
+template <typename TV>
+__global__ void k_sketch_reduce_wave(const BasisJob<TV>* __restrict__ jobs, Wave w, int c) {
+  const int i = wave_slot(w, blockIdx.x);
+  const BasisJob<TV>* J = jobs + w.ids[i];
+  const SketchDev sk = J->sk;
+  sketch_reduce_body(sk, w.aux[i], J->cs.sigma, c, J->sk_scale, J->SV + (size_t)c * sk.s, J->st,
+                     blockIdx.x - w.pre[i]);
+}
+
+// x = sum_{q < m_used} coef_q W_q, the arithmetic of k_combine with keep = 0
+template <typename TV>
+__global__ __launch_bounds__(kThreads) void k_combine_wave(const BasisJob<TV>* __restrict__ jobs, Wave w) {
+  extern __shared__ double s_cf[];
+  const int i = wave_slot(w, blockIdx.x);
+  const BasisJob<TV>* J = jobs + w.ids[i];
+  const int bid = blockIdx.x - w.pre[i], nblk = w.pre[i + 1] - w.pre[i];
+  if (J->st->status != FAB_OK) return;
+  const int nc = J->st->m_used, n = J->A.n;
+  const TV* W = J->W;
+  const int64_t ld = J->ld;
+  for (int q = threadIdx.x; q < nc; q += kThreads) s_cf[q] = J->coef[q];
+  __syncthreads();
+  double* out = J->x;
+  for (int r = bid * kThreads + threadIdx.x; r < n; r += nblk * kThreads) {
+    double a = 0.0;
+    for (int q = 0; q < nc; ++q) a = fma(s_cf[q], (double)W[(size_t)q * ld + r], a);
+    out[r] = a;
+  }
+}
+
+template <typename TV>
+cudaError_t launch_init_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, cudaStream_t s) {
+  if (nblocks <= 0) return cudaSuccess;
+  k_init_wave<TV><<<nblocks, kThreads, 0, s>>>(jobs, w);
+  return cudaGetLastError();
+}
+
+template <typename TV>
+cudaError_t launch_spmv_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, int kw, cudaStream_t s) {
+  static const void* fns[kMaxWindow + 1] = {
+      (const void*)k_spmv_wave<TV, 0>, (const void*)k_spmv_wave<TV, 1>, (const void*)k_spmv_wave<TV, 2>,
+      (const void*)k_spmv_wave<TV, 3>, (const void*)k_spmv_wave<TV, 4>, (const void*)k_spmv_wave<TV, 5>,
+      (const void*)k_spmv_wave<TV, 6>, (const void*)k_spmv_wave<TV, 7>, (const void*)k_spmv_wave<TV, 8>};
+  if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
+  if (nblocks <= 0) return cudaSuccess;
+  const size_t smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
+  cudaError_t e = ensure_smem_limit(fns[kw], smem);
+  if (e != cudaSuccess) return e;
+  Wave wv = w;
+  void* args[] = {(void*)&jobs, &wv, &c};
+  return cudaLaunchKernel(fns[kw], dim3(nblocks), dim3(kThreads), args, smem, s);
+}
+
+template <typename TV>
+cudaError_t launch_update_wave(int kind, const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, int nc, int mode,
+                               size_t smem, cudaStream_t s) {
+  if (nblocks <= 0) return cudaSuccess;
+  const void* fn = nullptr;
+  switch (kind) {
+    case SK_SRHT: fn = (const void*)k_update_wave<SK_SRHT, TV>; break;
+    case SK_SPARSE: fn = (const void*)k_update_wave<SK_SPARSE, TV>; break;
+    case SK_NONE: fn = (const void*)k_update_wave<SK_NONE, TV>; break;
+    default: return cudaErrorInvalidValue;  // the Gaussian sketch is not batched
+  }
+  cudaError_t e = ensure_smem_limit(fn, smem);
+  if (e != cudaSuccess) return e;
+  Wave wv = w;
+  void* args[] = {(void*)&jobs, &wv, &c, &nc, &mode};
+  return cudaLaunchKernel(fn, dim3(nblocks), dim3(kThreads), args, smem, s);
+}
+
+template <typename TV>
+cudaError_t launch_sketch_reduce_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, cudaStream_t s) {
+  if (nblocks <= 0) return cudaSuccess;
+  k_sketch_reduce_wave<TV><<<nblocks, 256, 0, s>>>(jobs, w, c);
+  return cudaGetLastError();
+}
+
+template <typename TV>
+cudaError_t launch_combine_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int mmax, cudaStream_t s) {
+  if (nblocks <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(mmax + 1) * sizeof(double);
+  cudaError_t e = ensure_smem_limit((const void*)k_combine_wave<TV>, smem);
+  if (e != cudaSuccess) return e;
+  k_combine_wave<TV><<<nblocks, kThreads, smem, s>>>(jobs, w);
+  return cudaGetLastError();
+}
+
+// Shared-memory limits of every wave kernel, set before a graph capture so the
+// capture itself issues no attribute calls. upd_smem: largest update-wave size.
+template <typename TV>
+cudaError_t wave_prepare(size_t upd_smem, int mmax) {
+  const size_t spmv_smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
+  const void* spmv[] = {(const void*)k_spmv_wave<TV, 0>, (const void*)k_spmv_wave<TV, 1>,
+                        (const void*)k_spmv_wave<TV, 2>, (const void*)k_spmv_wave<TV, 3>,
+                        (const void*)k_spmv_wave<TV, 4>, (const void*)k_spmv_wave<TV, 5>,
+                        (const void*)k_spmv_wave<TV, 6>, (const void*)k_spmv_wave<TV, 7>,
+                        (const void*)k_spmv_wave<TV, 8>};
+  for (const void* f : spmv) {
+    cudaError_t e = ensure_smem_limit(f, spmv_smem);
+    if (e != cudaSuccess) return e;
+  }
+  const void* upd[] = {(const void*)k_update_wave<SK_SRHT, TV>, (const void*)k_update_wave<SK_SPARSE, TV>,
+                       (const void*)k_update_wave<SK_NONE, TV>};
+  for (const void* f : upd) {
+    cudaError_t e = ensure_smem_limit(f, upd_smem);
+    if (e != cudaSuccess) return e;
+  }
+  return ensure_smem_limit((const void*)k_combine_wave<TV>, (size_t)(mmax + 1) * sizeof(double));
+}
+
+#define FAB_WAVES(TV)                                                                                              \
+  template cudaError_t launch_init_wave<TV>(const BasisJob<TV>*, const Wave&, int, cudaStream_t);                  \
+  template cudaError_t launch_spmv_wave<TV>(const BasisJob<TV>*, const Wave&, int, int, int, cudaStream_t);         \
+  template cudaError_t launch_update_wave<TV>(int, const BasisJob<TV>*, const Wave&, int, int, int, int, size_t,    \
+                                              cudaStream_t);                                                       \
+  template cudaError_t launch_sketch_reduce_wave<TV>(const BasisJob<TV>*, const Wave&, int, int, cudaStream_t);     \
+  template cudaError_t launch_combine_wave<TV>(const BasisJob<TV>*, const Wave&, int, int, cudaStream_t);        \
+  template cudaError_t wave_prepare<TV>(size_t, int);
+FAB_WAVES(double)
+FAB_WAVES(float)
+#undef FAB_WAVES
+
 // ------------------------------------------------------------- grid sizes
 static int g_sms = 0;
 int sm_count() {
@@ -831,6 +1069,8 @@ cudaError_t ensure_smem_limit(const void* fn, size_t bytes) {
   if (e == cudaSuccess) cur = bytes;
   return e;
 }
+
+int combine_grid(int n) { return grid_rows(n); }
 
 int grid_rows(int n) {
   const int need = (n + kThreads - 1) / kThreads;

@@ -1,0 +1,509 @@
+// Batched solves of libfab: many f(A)b solves of uneven size (different
+// matrices, n, m, window k, sketch and f) captured into one CUDA graph.
+//
+// Work items are (solve, basis step, tile): for every basis step c the graph
+// holds one launch per (window, sketch kind) group that covers the tiles of
+// every solve still building its basis (SpMV + window dots, then the window
+// update + norm + fused sketch, then the sketch reduce; Alg. 2 with the sketch
+// of §2.1.1). A solve's blocks inside such a wave are exactly the blocks of its
+// own launch, so every solve's basis and sketch are bit for bit those of
+// fab_apply. As soon as a solve's basis is complete its small stage (QR of the
+// sketch, the sketch-and-solve projection of eq. sFOM or none for Alg. 5,
+// f(H)e_1) runs as one CTA on a second branch of the graph, followed by its
+// combine x = ||b|| V_m c, so the FP64-bound small stages of early finishers
+// overlap the HBM-bound basis steps of the others.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <tuple>
+#include <vector>
+
+#include "handle.cuh"
+#include "small.cuh"
+
+namespace {
+
+using namespace fab;
+
+constexpr int kSkReduceWarps = 8;  // warps per block of the sketch reduce (one sketch row per warp)
+
+// Bump allocator over one device allocation (sizing pass when base is NULL).
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+enum WaveType { W_INIT, W_SPMV, W_UPDATE, W_REDUCE, W_SMALL, W_COMBINE };
+
+struct HostWave {
+  int type;
+  int c = 0, arg = 0, mode = 0, kind = SK_NONE;  // arg: window / update column count
+  size_t smem = 0;
+  int nblocks = 0;
+  size_t pre = 0, ids = 0, aux = 0;  // offsets into the table
+  int count = 0;
+  int mmax = 0;
+};
+
+int sk_kind_of(const fab_params& p) {
+  if (p.method != FAB_SKETCHED_FAST) return SK_NONE;
+  return p.sketch == FAB_SK_SRHT ? SK_SRHT : SK_SPARSE;
+}
+
+}  // namespace
+
+struct fab_batch {
+  int count = 0;
+  bool mixed = false;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  std::vector<int> n;
+  std::vector<double*> bdev, xdev;
+  DevState* states = nullptr;
+  std::vector<DevState> hst;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  int kernels = 0;
+};
+
+namespace {
+
+template <typename TV>
+int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream_t user) {
+  const int count = bt->count;
+  // ------------------------------------------------------------ plan
+  std::vector<int> kind(count);
+  int mmax = 1;
+  for (int j = 0; j < count; ++j) {
+    kind[j] = sk_kind_of(ps[j]);
+    mmax = std::max(mmax, ps[j].m);
+  }
+  // groups: distinct (k, sketch kind); waves of a group share the kernel template
+  std::vector<std::pair<int, int>> groups;
+  std::vector<int> group_of(count);
+  for (int j = 0; j < count; ++j) {
+    const std::pair<int, int> g{ps[j].k, kind[j]};
+    auto it = std::find(groups.begin(), groups.end(), g);
+    if (it == groups.end()) {
+      groups.push_back(g);
+      it = groups.end() - 1;
+    }
+    group_of[j] = (int)(it - groups.begin());
+  }
+  std::vector<int> tab;  // wave tables (prefix, ids, aux), uploaded once
+  std::vector<HostWave> waves;
+  auto add_wave = [&](HostWave w, const std::vector<int>& ids, const std::vector<int>& nblk,
+                      const std::vector<int>& aux) {
+    w.count = (int)ids.size();
+    if (w.count == 0) return;
+    w.pre = tab.size();
+    int acc = 0;
+    tab.push_back(0);
+    for (int b : nblk) tab.push_back(acc += b);
+    w.nblocks = acc;
+    w.ids = tab.size();
+    tab.insert(tab.end(), ids.begin(), ids.end());
+    w.aux = tab.size();
+    if (aux.empty()) tab.insert(tab.end(), ids.size(), 0);
+    else tab.insert(tab.end(), aux.begin(), aux.end());
+    waves.push_back(w);
+  };
+  {  // start: state, counters, H = 0, W_0 = b
+    std::vector<int> ids, nb;
+    for (int j = 0; j < count; ++j) {
+      ids.push_back(j);
+      nb.push_back(std::max(1, std::min((bt->n[j] + 2047) / 2048, 128)));
+    }
+    add_wave(HostWave{W_INIT}, ids, nb, {});
+  }
+  std::vector<size_t> skpart_need(count, 1), part_need(count, 1);  // per-solve partial buffer sizes
+  for (int c = 0; c <= mmax; ++c) {
+    for (int g = 0; g < (int)groups.size(); ++g) {
+      const int k = groups[g].first, kd = groups[g].second;
+      std::vector<int> ids;
+      for (int j = 0; j < count; ++j)
+        if (group_of[j] == g && ps[j].m >= c) ids.push_back(j);
+      if (ids.empty()) continue;
+      const int kw = c == 0 ? 0 : std::min(c, k);
+      if (c > 0) {
+        std::vector<int> nb;
+        for (int j : ids) {
+          nb.push_back(spmv_grid<TV>(bt->n[j], kw));
+          part_need[j] = std::max(part_need[j], (size_t)nb.back() * (kMaxWindow + 1));
+        }
+        HostWave w{W_SPMV};
+        w.c = c;
+        w.arg = kw;
+        add_wave(w, ids, nb, {});
+      }
+      std::vector<int> nb;
+      size_t smem = 0;
+      for (int j : ids) {
+        size_t sm = 0;
+        const int s = kd == SK_NONE ? 0 : ps[j].s;
+        const int grid = update_grid<TV>(kd, bt->n[j], kw, s, &sm);
+        if (grid < 1) return FAB_ECUDA;
+        nb.push_back(grid);
+        smem = std::max(smem, sm);
+        part_need[j] = std::max(part_need[j], (size_t)grid);
+        skpart_need[j] = std::max(skpart_need[j], (size_t)grid * (size_t)std::max(s, 1));
+      }
+      HostWave w{W_UPDATE};
+      w.c = c;
+      w.arg = kw;
+      w.mode = c == 0 ? 3 : 1;
+      w.kind = kd;
+      w.smem = smem;
+      add_wave(w, ids, nb, {});
+      if (kd != SK_NONE) {
+        std::vector<int> nr;
+        for (int j : ids) nr.push_back((ps[j].s + kSkReduceWarps - 1) / kSkReduceWarps);
+        HostWave r{W_REDUCE};
+        r.c = c;
+        add_wave(r, ids, nr, nb);  // aux: the update's block count = partials to sum
+      }
+    }
+    if (c >= 1) {  // solves whose basis is complete: small stage, then combine (second branch)
+      std::vector<int> ids, nb;
+      int mm = 1;
+      for (int j = 0; j < count; ++j)
+        if (ps[j].m == c) {
+          ids.push_back(j);
+          nb.push_back(1);
+          mm = std::max(mm, ps[j].m);
+        }
+      if (!ids.empty()) {
+        HostWave w{W_SMALL};
+        w.c = c;
+        w.mmax = mm;
+        add_wave(w, ids, nb, {});
+        std::vector<int> nc;
+        for (int j : ids) nc.push_back(combine_grid(bt->n[j]));
+        HostWave cw{W_COMBINE};
+        cw.c = c;
+        cw.mmax = mm;
+        add_wave(cw, ids, nc, {});
+      }
+    }
+  }
+
+  // ------------------------------------------------------------ layout
+  std::vector<BasisJob<TV>> jobs(count);
+  std::vector<SmallJob> small(count);
+  auto layout = [&](Arena& ar) {
+    BasisJob<TV>* jobs_dev = ar.take<BasisJob<TV>>(count);
+    SmallJob* small_dev = ar.take<SmallJob>(count);
+    int* tab_dev = ar.take<int>(tab.size());
+    DevState* states = ar.take<DevState>(count);
+    for (int j = 0; j < count; ++j) {
+      fab_handle* h = hs[j];
+      const fab_params& p = ps[j];
+      const int n = h->n, m = p.m, s = kind[j] == SK_NONE ? 1 : p.s;
+      BasisJob<TV>& J = jobs[j];
+      memset(&J, 0, sizeof(J));
+      J.A = Csr{h->n, h->nnz, h->d_rowptr, h->d_colind,
+                bt->mixed ? (const void*)h->d_vals32 : (const void*)h->d_vals};
+      J.ld = h->ld;
+      J.W = ar.take<TV>((size_t)h->ld * (m + 1));
+      J.cs.sigma = ar.take<double>(m + 1);
+      J.cs.shf = ar.take<int>(m + 1);
+      J.cs.scl = ar.take<double>(m + 1);
+      J.H = ar.take<double>((size_t)(m + 1) * m);
+      J.ldh = m + 1;
+      J.m = m;
+      J.k = p.k;
+      J.coef = ar.take<double>(m + 1);
+      J.wn2 = ar.take<double>(m + 1);
+      J.part = ar.take<double>(part_need[j]);
+      J.counter = ar.take<unsigned>(16);
+      J.st = states ? states + j : nullptr;
+      J.SV = ar.take<double>((size_t)s * (m + 1));
+      SketchDev& sk = J.sk;
+      sk.kind = kind[j];
+      sk.s = kind[j] == SK_NONE ? 0 : p.s;
+      sk.zeta = p.zeta;
+      sk.chunk_log2 = kChunkLog2;
+      sk.nchunks = (n + kChunk - 1) / kChunk;
+      sk.st_rows = rng_state(p.seed, 1);
+      sk.st_signs = rng_state(p.seed, 2);
+      sk.st_D = rng_state(p.seed, 3);
+      sk.P = ar.take<int>(s);
+      sk.part = ar.take<double>(skpart_need[j]);
+      J.sk_scale = kind[j] == SK_SRHT ? 1.0 / sqrt((double)p.s) : (kind[j] == SK_SPARSE ? 1.0 / sqrt((double)p.zeta) : 1.0);
+      double* bst = ar.take<double>(n);
+      double* xst = ar.take<double>(n);
+      J.b = bst;
+      J.x = xst;
+      if (ar.base) {
+        bt->bdev[j] = bst;
+        bt->xdev[j] = xst;
+      }
+      SmallJob& S = small[j];
+      memset(&S, 0, sizeof(S));
+      S.method = p.method;
+      S.f = p.f;
+      S.m = m;
+      S.s = s;
+      S.t = p.t;
+      S.H = J.H;
+      S.ldh = J.ldh;
+      S.SV = J.SV;
+      S.sigma = J.cs.sigma;
+      S.st = J.st;
+      S.qr = ar.take<double>((size_t)s * (m + 1));
+      S.tau = ar.take<double>(m + 1);
+      S.y = ar.take<double>(m + 1);
+      S.mats = ar.take<double>((size_t)9 * m * m);
+      S.piv = ar.take<int>(m + 1);
+      S.cvec = ar.take<double>(m + 1);
+      S.scal = ar.take<double>(16);
+      S.coef = J.coef;
+    }
+    return std::make_tuple(jobs_dev, small_dev, tab_dev, states);
+  };
+  Arena sizing;
+  layout(sizing);
+  const size_t bytes = sizing.off + 256;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return FAB_ECUDA;
+  }
+  if (bytes > free_b || alloc_fault()) return FAB_ENOMEM;
+  if (cudaMalloc(&bt->mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    bt->mem = nullptr;
+    return FAB_ENOMEM;
+  }
+  bt->bytes = bytes;
+  Arena ar;
+  ar.base = reinterpret_cast<char*>(bt->mem);
+  BasisJob<TV>* jobs_dev;
+  SmallJob* small_dev;
+  int* tab_dev;
+  std::tie(jobs_dev, small_dev, tab_dev, bt->states) = layout(ar);
+
+  cudaStream_t cap = nullptr, side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  auto cleanup = [&]() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
+    if (cap) cudaStreamDestroy(cap);
+  };
+#define BK(call)              \
+  do {                        \
+    if ((call) != cudaSuccess) { \
+      cudaGetLastError();     \
+      cleanup();              \
+      return FAB_ECUDA;       \
+    }                         \
+  } while (0)
+  BK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  BK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+  BK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  BK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+  BK(cudaMemcpyAsync(jobs_dev, jobs.data(), sizeof(BasisJob<TV>) * count, cudaMemcpyHostToDevice, cap));
+  BK(cudaMemcpyAsync(small_dev, small.data(), sizeof(SmallJob) * count, cudaMemcpyHostToDevice, cap));
+  BK(cudaMemcpyAsync(tab_dev, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, cap));
+  for (int j = 0; j < count; ++j)  // SRHT row samples are fixed by (n', s, seed): drawn once here
+    if (kind[j] == SK_SRHT) {
+      int64_t npad = 1;
+      while (npad < bt->n[j]) npad <<= 1;
+      BK(launch_srht_sample(npad, ps[j].s, rng_state(ps[j].seed, 4), const_cast<int*>(jobs[j].sk.P), cap));
+    }
+  BK(cudaStreamSynchronize(cap));
+  PadeCoef pd;
+  memcpy(pd.b, pade13_b(), sizeof(pd.b));
+  pd.theta = pade13_theta();
+  // every wave kernel gets its shared-memory limit before the capture
+  BK(small_fused_prepare(mmax));
+  {
+    size_t upd = 0;
+    for (const HostWave& w : waves)
+      if (w.type == W_UPDATE) upd = std::max(upd, w.smem);
+    BK(wave_prepare<TV>(upd, mmax));
+  }
+
+  // ------------------------------------------------------------ capture
+  BK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  int kernels = 0;
+  bool side_used = false;
+  cudaError_t e = cudaSuccess;
+  for (const HostWave& w : waves) {
+    const Wave wv{tab_dev + w.pre, tab_dev + w.ids, tab_dev + w.aux, w.count};
+    switch (w.type) {
+      case W_INIT: e = launch_init_wave<TV>(jobs_dev, wv, w.nblocks, cap); break;
+      case W_SPMV: e = launch_spmv_wave<TV>(jobs_dev, wv, w.nblocks, w.c, w.arg, cap); break;
+      case W_UPDATE:
+        e = launch_update_wave<TV>(w.kind, jobs_dev, wv, w.nblocks, w.c, w.arg, w.mode, w.smem, cap);
+        break;
+      case W_REDUCE: e = launch_sketch_reduce_wave<TV>(jobs_dev, wv, w.nblocks, w.c, cap); break;
+      case W_SMALL:
+        if ((e = cudaEventRecord(fork, cap)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) break;
+        side_used = true;
+        e = launch_small_fused(small_dev, tab_dev + w.ids, w.count, w.mmax, pd, side);
+        break;
+      case W_COMBINE: e = launch_combine_wave<TV>(jobs_dev, wv, w.nblocks, w.mmax, side); break;
+    }
+    if (e != cudaSuccess) break;
+    ++kernels;
+  }
+  if (e == cudaSuccess && side_used) {
+    e = cudaEventRecord(join, side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join, 0);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    cleanup();
+    return FAB_ECUDA;
+  }
+  e = cudaGraphInstantiate(&bt->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e == cudaSuccess) e = cudaGraphUpload(bt->exec, user);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(user);
+  cleanup();
+#undef BK
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FAB_ECUDA;
+  }
+  bt->kernels = kernels;
+  return FAB_OK;
+}
+
+}  // namespace
+
+extern "C" int fab_batch_create(fab_batch** out, fab_handle* const* hs, const fab_params* ps, int count) {
+  if (!out) return FAB_EINVAL;
+  *out = nullptr;
+  if (!hs || !ps || count < 1) return FAB_EINVAL;
+  const int prec = ps[0].precision;
+  for (int j = 0; j < count; ++j) {
+    const fab_params& p = ps[j];
+    if (!hs[j] || validate_params(hs[j], &p) != FAB_OK) return FAB_EINVAL;
+    if (p.precision != prec) return FAB_EINVAL;
+    if (p.method != FAB_SKETCHED_FAST && p.method != FAB_NOPROJ) return FAB_EINVAL;
+    if (p.method == FAB_SKETCHED_FAST && p.sketch != FAB_SK_SRHT && p.sketch != FAB_SK_SPARSE_SIGN)
+      return FAB_EINVAL;
+  }
+  cudaStream_t user = (cudaStream_t)ps[0].stream;
+  if (prec == FAB_MIXED)
+    for (int j = 0; j < count; ++j) {
+      const int rc = ensure_vals32(hs[j], user);
+      if (rc != FAB_OK) return rc;
+    }
+  fab_batch* bt = new fab_batch();
+  bt->count = count;
+  bt->mixed = prec == FAB_MIXED;
+  bt->n.resize(count);
+  bt->bdev.resize(count);
+  bt->xdev.resize(count);
+  bt->hst.resize(count);
+  for (int j = 0; j < count; ++j) bt->n[j] = hs[j]->n;
+  int rc = bt->mixed ? build<float>(bt, hs, ps, user) : build<double>(bt, hs, ps, user);
+  if (rc == FAB_OK && (cudaEventCreate(&bt->t0) != cudaSuccess || cudaEventCreate(&bt->t1) != cudaSuccess)) {
+    cudaGetLastError();
+    rc = FAB_ECUDA;
+  }
+  if (rc != FAB_OK) {
+    fab_batch_destroy(bt);
+    return rc;
+  }
+  *out = bt;
+  return FAB_OK;
+}
+
+extern "C" int fab_batch_exec(fab_batch* bt, const double* const* bs, double* const* xs, fab_stats* sts,
+                              void* stream) {
+  if (!bt || !bt->exec) return FAB_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int count = bt->count;
+  if (bs)
+    for (int j = 0; j < count; ++j) {
+      if (!bs[j]) return FAB_EINVAL;
+      if (cudaMemcpyAsync(bt->bdev[j], bs[j], (size_t)bt->n[j] * sizeof(double), cudaMemcpyDefault, s) !=
+          cudaSuccess)
+        goto cuda_fail;
+    }
+  if (cudaEventRecord(bt->t0, s) != cudaSuccess || cudaGraphLaunch(bt->exec, s) != cudaSuccess ||
+      cudaEventRecord(bt->t1, s) != cudaSuccess)
+    goto cuda_fail;
+  if (cudaMemcpyAsync(bt->hst.data(), bt->states, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    goto cuda_fail;
+  if (xs)
+    for (int j = 0; j < count; ++j) {
+      if (!xs[j]) continue;
+      if (cudaMemcpyAsync(xs[j], bt->xdev[j], (size_t)bt->n[j] * sizeof(double), cudaMemcpyDefault, s) !=
+          cudaSuccess)
+        goto cuda_fail;
+    }
+  if (cudaStreamSynchronize(s) != cudaSuccess) goto cuda_fail;
+  {
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, bt->t0, bt->t1);
+    int rc = FAB_OK;
+    for (int j = 0; j < count; ++j) {
+      const DevState& d = bt->hst[j];
+      if (d.status != FAB_OK && rc == FAB_OK) rc = d.status;
+      if (sts) {
+        fab_stats& st = sts[j];
+        memset(&st, 0, sizeof(st));
+        st.m_used = d.m_used;
+        st.fh_iters = d.iters;
+        st.launches = bt->kernels;
+        st.beta = d.beta;
+        st.h_last = d.scal[15];
+        st.ms_total = ms;
+      }
+    }
+    return rc;
+  }
+cuda_fail:
+  cudaGetLastError();
+  return FAB_ECUDA;
+}
+
+extern "C" double* fab_batch_input(fab_batch* bt, int i) {
+  return (bt && i >= 0 && i < bt->count) ? bt->bdev[i] : nullptr;
+}
+
+extern "C" double* fab_batch_output(fab_batch* bt, int i) {
+  return (bt && i >= 0 && i < bt->count) ? bt->xdev[i] : nullptr;
+}
+
+extern "C" int fab_batch_kernels(const fab_batch* bt) { return bt ? bt->kernels : 0; }
+
+extern "C" void fab_batch_destroy(fab_batch* bt) {
+  if (!bt) return;
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  if (bt->t0) cudaEventDestroy(bt->t0);
+  if (bt->t1) cudaEventDestroy(bt->t1);
+  if (bt->mem) cudaFree(bt->mem);
+  cudaGetLastError();
+  delete bt;
+}
+
+extern "C" int fab_batch_run(fab_handle* const* hs, const fab_params* ps, const double* const* bs, double* const* xs,
+                             int count, fab_stats* sts) {
+  if (!bs || !xs) return FAB_EINVAL;
+  fab_batch* bt = nullptr;
+  int rc = fab_batch_create(&bt, hs, ps, count);
+  if (rc != FAB_OK) return rc;
+  rc = fab_batch_exec(bt, bs, xs, sts, ps[0].stream);
+  fab_batch_destroy(bt);
+  return rc;
+}

@@ -867,6 +867,13 @@ extern "C" const char* fab_last_error(void) { return g_errmsg; }
 
 namespace fab {
 void set_last_error(const char* msg) { snprintf(g_errmsg, sizeof(g_errmsg), "%s", msg ? msg : ""); }
+int validate_params(const fab_handle* h, const fab_params* p) { return validate(h, p); }
+const double* pade13_b() {
+  static const Pade13 pd;
+  return pd.b;
+}
+double pade13_theta() { return kTheta13; }
+bool alloc_fault() { return fault_hit(); }
 }  // namespace fab
 
 namespace fab {

@@ -99,18 +99,19 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* >= 32*N
 
 // Last-block-done: returns true in every thread of the block that finished last.
 // Partials written before the call are visible to that block afterwards.
-__device__ __forceinline__ bool last_block(unsigned* counter) {
+__device__ __forceinline__ bool last_block(unsigned* counter, unsigned nblk) {
   __shared__ int s_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned prev = atomicAdd(counter, 1u);
-    s_last = (prev == gridDim.x - 1);
+    s_last = (prev == nblk - 1);
   }
   __syncthreads();
   if (s_last) __threadfence();
   return s_last != 0;
 }
+__device__ __forceinline__ bool last_block(unsigned* counter) { return last_block(counter, gridDim.x); }
 
 // Sum of `nv` columns of a row-major nblocks x nv partial array, by one block,
 // in a fixed order. out[q] (shared) receives column q. nv <= 32.
@@ -233,6 +234,55 @@ cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const
                           SketchDev& sk, DevState* st, cudaStream_t s);
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
                                  DevState* st, cudaStream_t s);
+
+// ------------------------------------------------------------ batched waves
+// One solve of a batch as the basis kernels see it (a device-resident table).
+template <typename TV>
+struct BasisJob {
+  Csr A;
+  TV* W;  // raw basis, n x (m+1), ld
+  int64_t ld;
+  ColScale cs;
+  double* H;  // (m+1) x m
+  int ldh;
+  int m, k;
+  double *coef, *wn2, *part;
+  unsigned* counter;
+  DevState* st;
+  SketchDev sk;  // sk.kind SK_NONE for Alg. 5 without a sketch
+  double sk_scale;
+  double* SV;       // s x (m+1)
+  const double* b;  // start vector (FP64, device)
+  double* x;        // result (FP64, device)
+};
+// A wave is one launch over several solves: job ids[i] owns blocks pre[i] ..
+// pre[i+1]-1 (its own launch's grid); aux[i] is a per-job extra (the sketch
+// partial count of the update wave before a reduce wave).
+struct Wave {
+  const int* pre;
+  const int* ids;
+  const int* aux;
+  int count;
+};
+// Grid of the single-solve launch of each basis kernel (a batched solve uses the same).
+template <typename TV>
+int spmv_grid(int n, int kw);
+template <typename TV>
+int update_grid(int kind, int n, int nc, int s, size_t* smem);
+int combine_grid(int n);
+template <typename TV>
+cudaError_t launch_init_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, cudaStream_t s);
+template <typename TV>
+cudaError_t launch_spmv_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, int kw, cudaStream_t s);
+template <typename TV>
+cudaError_t launch_update_wave(int kind, const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, int nc, int mode,
+                               size_t smem, cudaStream_t s);
+template <typename TV>
+cudaError_t launch_sketch_reduce_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, cudaStream_t s);
+template <typename TV>
+cudaError_t launch_combine_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int mmax, cudaStream_t s);
+template <typename TV>
+cudaError_t wave_prepare(size_t upd_smem, int mmax);
 cudaError_t launch_srht_sample(int64_t npad, int s, uint64_t stP, int* P, cudaStream_t st);
 template <typename TV, typename TX>
 cudaError_t launch_gemv_t(int n, const TV* W, int64_t ld, int j0, int nc, const TX* x, double* part,

@@ -73,5 +73,12 @@ void point_to_matrix(fab_handle* clone, const fab_handle* h);
 int ensure_vals32(fab_handle* h, cudaStream_t s);
 // Sets this host thread's fab_last_error() text (carries a serving slot's detail to the poller).
 void set_last_error(const char* msg);
+// Parameter checks of fab_apply (FAB_OK or FAB_EINVAL).
+int validate_params(const fab_handle* h, const fab_params* p);
+// Pade [13/13] numerator coefficients b_0..b_13 and the threshold theta_13.
+const double* pade13_b();
+double pade13_theta();
+// Host-side allocation fault injection (FAB_FAULT=alloc:N): true for the N-th call.
+bool alloc_fault();
 
 }  // namespace fab

@@ -21,12 +21,10 @@ namespace fab {
 // also applied to the `extra` trailing columns (right-hand sides), which then
 // hold Q^T rhs. Reflector j: beta = -sign(alpha) ||x||, tau = (beta - alpha)/beta,
 // v = x / (alpha - beta).
-__global__ __launch_bounds__(1024) void k_householder_qr(double* __restrict__ A, int lda, int rows,
-                                                          const int* __restrict__ mdev, int extra,
-                                                          double* __restrict__ tau) {
+__device__ __forceinline__ void householder_qr_body(double* __restrict__ A, int lda, int rows, int mu, int extra,
+                                                    double* __restrict__ tau) {
   __shared__ double red[32];
   __shared__ double s_beta, s_tau, s_vinv;
-  const int mu = *mdev;
   const int ncols = mu + extra;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j < mu && j < rows; ++j) {
@@ -72,6 +70,12 @@ __global__ __launch_bounds__(1024) void k_householder_qr(double* __restrict__ A,
   }
 }
 
+__global__ __launch_bounds__(1024) void k_householder_qr(double* __restrict__ A, int lda, int rows,
+                                                          const int* __restrict__ mdev, int extra,
+                                                          double* __restrict__ tau) {
+  householder_qr_body(A, lda, rows, *mdev, extra, tau);
+}
+
 cudaError_t launch_householder_qr(double* A, int lda, int rows, const int* mdev, int extra, double* tau,
                                   cudaStream_t s) {
   k_householder_qr<<<1, 1024, 0, s>>>(A, lda, rows, mdev, extra, tau);
@@ -81,11 +85,9 @@ cudaError_t launch_householder_qr(double* A, int lda, int rows, const int* mdev,
 // ------------------------------------------------------- triangular solves
 // x <- R^{-1} x (trans = 0) or R^{-T} x (trans = 1), R = upper triangle of the
 // leading mu x mu block of R (ld ldr). Optional pre-scale of x by *pre (device).
-__global__ __launch_bounds__(1024) void k_trsv(const double* __restrict__ R, int ldr, const int* __restrict__ mdev,
-                                                const double* __restrict__ xin, double* __restrict__ xout, int trans,
-                                                const double* __restrict__ pre) {
+__device__ __forceinline__ void trsv_body(const double* __restrict__ R, int ldr, int mu, const double* __restrict__ xin,
+                                          double* __restrict__ xout, int trans, const double* __restrict__ pre) {
   __shared__ double xs[kMaxM];
-  const int mu = *mdev;
   const double p = pre ? *pre : 1.0;
   for (int i = threadIdx.x; i < mu; i += blockDim.x) xs[i] = p * xin[i];
   __syncthreads();
@@ -107,6 +109,12 @@ __global__ __launch_bounds__(1024) void k_trsv(const double* __restrict__ R, int
     }
   }
   for (int i = threadIdx.x; i < mu; i += blockDim.x) xout[i] = xs[i];
+}
+
+__global__ __launch_bounds__(1024) void k_trsv(const double* __restrict__ R, int ldr, const int* __restrict__ mdev,
+                                                const double* __restrict__ xin, double* __restrict__ xout, int trans,
+                                                const double* __restrict__ pre) {
+  trsv_body(R, ldr, *mdev, xin, xout, trans, pre);
 }
 
 cudaError_t launch_trsv(const double* R, int ldr, const int* mdev, const double* xin, double* xout, int trans,
@@ -137,9 +145,9 @@ cudaError_t launch_build_hhat(const double* H, int ldh, const int* mdev, const d
 }
 
 // ||M||_1 (maximum absolute column sum) into *out.
-__global__ void k_norm1(const double* __restrict__ M, int ldm, const int* __restrict__ mdev, double* out) {
+__device__ __forceinline__ double norm1_body(const double* __restrict__ M, int ldm, int mu, double* out) {
   __shared__ double red[32];
-  const int mu = *mdev;
+  __shared__ double s_out;
   double best = 0.0;
   for (int j = threadIdx.x; j < mu; j += blockDim.x) {
     double a = 0.0;
@@ -152,8 +160,15 @@ __global__ void k_norm1(const double* __restrict__ M, int ldm, const int* __rest
   if (threadIdx.x == 0) {
     double b = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, red[w]);
-    *out = b;
+    if (out) *out = b;
+    s_out = b;
   }
+  __syncthreads();
+  return s_out;
+}
+
+__global__ void k_norm1(const double* __restrict__ M, int ldm, const int* __restrict__ mdev, double* out) {
+  norm1_body(M, ldm, *mdev, out);
 }
 
 cudaError_t launch_norm1(const double* M, int ldm, const int* mdev, double* out, cudaStream_t s) {
@@ -215,13 +230,12 @@ cudaError_t launch_lincomb(double* out, const double* X0, const double* X1, cons
 // In-place LU with partial pivoting (rows swapped across the whole matrix,
 // ties to the smallest row index). piv[k] = row swapped with k. Writes
 // log|det| to *logdet and flags a zero pivot in st->status (FAB_ENUMERIC).
-__global__ __launch_bounds__(1024) void k_lu(double* __restrict__ M, int ld, const int* __restrict__ mdev,
-                                              int* __restrict__ piv, double* __restrict__ logdet, DevState* st) {
+__device__ __forceinline__ void lu_body(double* __restrict__ M, int ld, int mu, int* __restrict__ piv,
+                                        double* __restrict__ logdet, DevState* st) {
   __shared__ double rv[32];
   __shared__ int ri[32];
   __shared__ int s_p;
   __shared__ double s_logdet;
-  const int mu = *mdev;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   if (tid == 0) s_logdet = 0.0;
   for (int k = 0; k < mu; ++k) {
@@ -291,6 +305,12 @@ __global__ __launch_bounds__(1024) void k_lu(double* __restrict__ M, int ld, con
     __syncthreads();
   }
   if (tid == 0 && logdet) *logdet = s_logdet;
+  __syncthreads();
+}
+
+__global__ __launch_bounds__(1024) void k_lu(double* __restrict__ M, int ld, const int* __restrict__ mdev,
+                                              int* __restrict__ piv, double* __restrict__ logdet, DevState* st) {
+  lu_body(M, ld, *mdev, piv, logdet, st);
 }
 
 cudaError_t launch_lu(double* M, int ld, const int* mdev, int* piv, double* logdet, DevState* st, cudaStream_t s) {
@@ -350,12 +370,11 @@ cudaError_t launch_lu_solve(const double* LU, int ld, const int* piv, const int*
 //   M <- (I + (mu^2 M + mu^-2 Minv) / 2) / 2,   y <- mu (y + mu^-2 Minv y) / 2,
 // with M_0 = Y_0 = H (y_0 = H e_1 for the square root, e_1 for the inverse
 // square root with Z_0 = I). Writes ||M - I||_F to st->scal[1].
-__global__ __launch_bounds__(1024) void k_db_update(double* __restrict__ M, const double* __restrict__ Minv, int ld,
-                                                     const int* __restrict__ mdev, double* __restrict__ y,
-                                                     const double* __restrict__ logdet, int scale_on, DevState* st) {
+__device__ __forceinline__ void db_update_body(double* __restrict__ M, const double* __restrict__ Minv, int ld, int mu,
+                                               double* __restrict__ y, const double* __restrict__ logdet,
+                                               int scale_on, DevState* st) {
   __shared__ double ys[kMaxM];
   __shared__ double red[32];
-  const int mu = *mdev;
   const double g = scale_on ? exp(-(*logdet) / (2.0 * mu)) : 1.0;
   const double g2 = g * g, gi2 = 1.0 / g2;
   for (int i = threadIdx.x; i < mu; i += blockDim.x) ys[i] = y[i];
@@ -383,6 +402,13 @@ __global__ __launch_bounds__(1024) void k_db_update(double* __restrict__ M, cons
     st->scal[1] = sqrt(e);
     if (!isfinite(e)) st->status = FAB_ENUMERIC;
   }
+  __syncthreads();
+}
+
+__global__ __launch_bounds__(1024) void k_db_update(double* __restrict__ M, const double* __restrict__ Minv, int ld,
+                                                     const int* __restrict__ mdev, double* __restrict__ y,
+                                                     const double* __restrict__ logdet, int scale_on, DevState* st) {
+  db_update_body(M, Minv, ld, *mdev, y, logdet, scale_on, st);
 }
 
 cudaError_t launch_db_update(double* M, const double* Minv, int ld, const int* mdev, double* y, const double* logdet,
@@ -836,6 +862,203 @@ __global__ void __launch_bounds__(256) k_lu_cluster(double* __restrict__ M, int 
     for (int k = tid; k < mu; k += blockDim.x) piv[k] = s_piv[k];
     if (tid == 0 && logdet) *logdet = s_logdet;
   }
+}
+
+// ------------------------------------------------- fused small stage (batch)
+// The steps of the small stage, each done by the whole CTA, with the same
+// per-element arithmetic as the multi-kernel path: products and linear
+// combinations of m x m matrices, LU solves one warp per right-hand side.
+__device__ void blk_gemm(double* __restrict__ C, const double* __restrict__ A, const double* __restrict__ B, int ld,
+                         int mu) {
+  for (int idx = threadIdx.x; idx < mu * mu; idx += blockDim.x) {
+    const int i = idx % mu, j = idx / mu;
+    double a0 = 0.0, a1 = 0.0;
+    int l = 0;
+    for (; l + 1 < mu; l += 2) {
+      a0 = fma(A[i + (size_t)ld * l], B[l + (size_t)ld * j], a0);
+      a1 = fma(A[i + (size_t)ld * (l + 1)], B[l + 1 + (size_t)ld * j], a1);
+    }
+    if (l < mu) a0 = fma(A[i + (size_t)ld * l], B[l + (size_t)ld * j], a0);
+    C[i + (size_t)ld * j] = a0 + a1;
+  }
+  __syncthreads();
+}
+
+__device__ void blk_lincomb(double* out, const double* X0, const double* X1, const double* X2, const double* X3,
+                            double a0, double a1, double a2, double a3, double d, int ld, int mu) {
+  for (int idx = threadIdx.x; idx < mu * mu; idx += blockDim.x) {
+    const int i = idx % mu, j = idx / mu;
+    const size_t o = i + (size_t)ld * j;
+    double v = (i == j) ? d : 0.0;
+    if (X0) v = fma(a0, X0[o], v);
+    if (X1) v = fma(a1, X1[o], v);
+    if (X2) v = fma(a2, X2[o], v);
+    if (X3) v = fma(a3, X3[o], v);
+    out[o] = v;
+  }
+  __syncthreads();
+}
+
+// LU X = P B for all mu columns of B (identity_rhs: B = I); sb holds one mu-vector per warp.
+__device__ void blk_lu_solve(const double* __restrict__ LU, int ld, const int* __restrict__ piv, int mu,
+                             double* __restrict__ B, int ldb, int identity_rhs, double* sb) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* b = sb + (size_t)warp * mu;
+  for (int col = warp; col < mu; col += nw) {
+    double* bg = B + (size_t)ldb * col;
+    for (int i = lane; i < mu; i += 32) b[i] = identity_rhs ? (i == col ? 1.0 : 0.0) : bg[i];
+    __syncwarp();
+    if (lane == 0) {
+      for (int k = 0; k < mu; ++k) {
+        const int p = piv[k];
+        if (p != k && p > k && p < mu) {
+          const double t = b[k];
+          b[k] = b[p];
+          b[p] = t;
+        }
+      }
+    }
+    __syncwarp();
+    for (int k = 0; k < mu; ++k) {
+      const double bk = b[k];
+      for (int i = k + 1 + lane; i < mu; i += 32) b[i] = fma(-LU[i + (size_t)ld * k], bk, b[i]);
+      __syncwarp();
+    }
+    for (int k = mu - 1; k >= 0; --k) {
+      if (lane == 0) b[k] /= LU[k + (size_t)ld * k];
+      __syncwarp();
+      const double bk = b[k];
+      for (int i = lane; i < k; i += 32) b[i] = fma(-LU[i + (size_t)ld * k], bk, b[i]);
+      __syncwarp();
+    }
+    for (int i = lane; i < mu; i += 32) bg[i] = b[i];
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
+// exp(M) e_1 by Pade [13/13] scaling and squaring (Higham 2005); M (ld m) is overwritten.
+__device__ void blk_expm_e1(double* mats, int m, int mu, const PadeCoef& pd, double* c, int* piv, double* logdet,
+                            double* sb, DevState* st) {
+  const size_t mm = (size_t)m * m;
+  double *M = mats, *A2 = mats + mm, *A4 = mats + 2 * mm, *A6 = mats + 3 * mm, *T = mats + 4 * mm,
+         *U = mats + 5 * mm, *V = mats + 6 * mm, *X = mats + 7 * mm, *X2 = mats + 8 * mm;
+  const double* b = pd.b;
+  const double nrm = norm1_body(M, m, mu, nullptr);
+  if (!isfinite(nrm)) {
+    if (threadIdx.x == 0) st->status = FAB_ENUMERIC;
+    return;
+  }
+  int sq = 0;
+  if (nrm > pd.theta) sq = (int)ceil(log2(nrm / pd.theta));
+  if (sq > 0) blk_lincomb(M, M, nullptr, nullptr, nullptr, ldexp(1.0, -sq), 0, 0, 0, 0.0, m, mu);
+  blk_gemm(A2, M, M, m, mu);
+  blk_gemm(A4, A2, A2, m, mu);
+  blk_gemm(A6, A4, A2, m, mu);
+  blk_lincomb(T, A6, A4, A2, nullptr, b[13], b[11], b[9], 0, 0.0, m, mu);
+  blk_gemm(X, A6, T, m, mu);
+  blk_lincomb(X, X, A6, A4, A2, 1.0, b[7], b[5], b[3], b[1], m, mu);
+  blk_gemm(U, M, X, m, mu);
+  blk_lincomb(T, A6, A4, A2, nullptr, b[12], b[10], b[8], 0, 0.0, m, mu);
+  blk_gemm(V, A6, T, m, mu);
+  blk_lincomb(V, V, A6, A4, A2, 1.0, b[6], b[4], b[2], b[0], m, mu);
+  blk_lincomb(T, V, U, nullptr, nullptr, 1.0, -1.0, 0, 0, 0.0, m, mu);
+  blk_lincomb(X, V, U, nullptr, nullptr, 1.0, 1.0, 0, 0, 0.0, m, mu);
+  lu_body(T, m, mu, piv, logdet, st);
+  blk_lu_solve(T, m, piv, mu, X, m, 0, sb);
+  for (int i = 0; i < sq; ++i) {
+    blk_gemm(X2, X, X, m, mu);
+    double* t = X;
+    X = X2;
+    X2 = t;
+  }
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) c[i] = X[i];
+  if (threadIdx.x == 0) st->iters = sq;
+  __syncthreads();
+}
+
+// f(M) e_1 for f = sqrt or inverse sqrt by the scaled product-form Denman-Beavers
+// iteration with the stopping rule of the multi-kernel path.
+__device__ void blk_sqrtm_e1(double* mats, int m, int mu, int want_sqrt, double* c, int* piv, double* logdet,
+                             double* sb, DevState* st) {
+  const size_t mm = (size_t)m * m;
+  double *M = mats, *T = mats + mm, *Minv = mats + 2 * mm;
+  for (int i = threadIdx.x; i < mu; i += blockDim.x) c[i] = want_sqrt ? M[i] : (i == 0 ? 1.0 : 0.0);
+  __syncthreads();
+  double err = INFINITY;
+  int extra = -1;
+  for (int it = 0; it < 100; ++it) {
+    for (int idx = threadIdx.x; idx < (int)mm; idx += blockDim.x) T[idx] = M[idx];
+    __syncthreads();
+    lu_body(T, m, mu, piv, logdet, st);
+    blk_lu_solve(T, m, piv, mu, Minv, m, 1, sb);
+    db_update_body(M, Minv, m, mu, c, logdet, err > 1e-2 ? 1 : 0, st);
+    if (st->status != FAB_OK) return;
+    err = st->scal[1];
+    if (threadIdx.x == 0) st->iters = it + 1;
+    if (extra >= 0) return;
+    if (err <= 1e-13 * sqrt((double)m)) extra = 0;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st->status = FAB_ENOTCONV;
+}
+
+__global__ __launch_bounds__(256) void k_small_fused(const SmallJob* __restrict__ jobs, const int* __restrict__ ids,
+                                                     PadeCoef pd) {
+  extern __shared__ double s_lu[];  // one mu-vector per warp
+  const SmallJob J = jobs[ids ? ids[blockIdx.x] : blockIdx.x];
+  DevState* st = J.st;
+  if (st->status != FAB_OK) return;
+  const int mu = st->m_used, m = J.m;
+  if (threadIdx.x == 0) st->scal[15] = (mu == m) ? J.H[m + (size_t)J.ldh * (m - 1)] : 0.0;  // h_{m+1,m}
+  if (mu == 0) {  // b = 0
+    for (int j = threadIdx.x; j <= m; j += blockDim.x) J.coef[j] = 0.0;
+    return;
+  }
+  const double* yptr = nullptr;
+  if (mu == m && J.method == FAB_SKETCHED_FAST) {
+    // y = argmin || Theta V_m z - Theta v_{m+1} || (sketch-and-solve form of eq. sFOM)
+    const size_t cnt = (size_t)J.s * (mu + 1);
+    for (size_t i = threadIdx.x; i < cnt; i += blockDim.x) J.qr[i] = J.SV[i];
+    __syncthreads();
+    householder_qr_body(J.qr, J.s, J.s, mu, 1, J.tau);
+    __syncthreads();
+    trsv_body(J.qr, J.s, mu, J.qr + (size_t)mu * J.s, J.y, 0, nullptr);
+    __syncthreads();
+    yptr = J.y;
+  }
+  // M = scale (H_mu + h_{mu+1,mu} y e_mu^T)
+  const double scale = (J.f == FAB_F_EXP) ? J.t : 1.0;
+  const double hl = yptr ? J.H[mu + (size_t)J.ldh * (mu - 1)] : 0.0;
+  for (int idx = threadIdx.x; idx < mu * mu; idx += blockDim.x) {
+    const int i = idx % mu, j = idx / mu;
+    double v = J.H[i + (size_t)J.ldh * j];
+    if (yptr && j == mu - 1) v = fma(hl, yptr[i], v);
+    J.mats[i + (size_t)m * j] = scale * v;
+  }
+  __syncthreads();
+  if (J.f == FAB_F_EXP)
+    blk_expm_e1(J.mats, m, mu, pd, J.cvec, J.piv, J.scal + 11, s_lu, st);
+  else
+    blk_sqrtm_e1(J.mats, m, mu, J.f == FAB_F_SQRT, J.cvec, J.piv, J.scal + 11, s_lu, st);
+  __syncthreads();
+  if (st->status != FAB_OK) return;
+  const double beta = st->beta;
+  for (int j = threadIdx.x; j < mu; j += blockDim.x) J.coef[j] = beta * J.cvec[j] * J.sigma[j];
+}
+
+cudaError_t small_fused_prepare(int mmax) {
+  return ensure_smem_limit((const void*)k_small_fused, (size_t)(256 / 32) * (mmax > 0 ? mmax : 1) * sizeof(double));
+}
+
+cudaError_t launch_small_fused(const SmallJob* jobs, const int* ids, int count, int mmax, const PadeCoef& pd,
+                               cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = (size_t)(256 / 32) * (mmax > 0 ? mmax : 1) * sizeof(double);
+  cudaError_t e = ensure_smem_limit((const void*)k_small_fused, smem);
+  if (e != cudaSuccess) return e;
+  k_small_fused<<<count, 256, smem, s>>>(jobs, ids, pd);
+  return cudaGetLastError();
 }
 
 namespace {

@@ -47,4 +47,34 @@ template <typename TV>
 cudaError_t launch_lsqr_u(int n, const TV* W, int64_t ld, int nc, const double* coef, double* u, int keep_zero,
                           double* part, unsigned* counter, double* unorm2, const DevState* st, cudaStream_t s);
 
+// One solve's small stage for the batched path: everything between the basis
+// and the combine, done by one CTA (k_small_fused).
+struct SmallJob {
+  int method, f, m, s;
+  double t;
+  const double* H;  // (m+1) x m, ld ldh
+  int ldh;
+  const double* SV;     // s x (m+1) sketch of the basis (sketched_fast)
+  const double* sigma;  // column scales of the raw basis
+  DevState* st;
+  double* qr;    // s x (m+1)
+  double* tau;   // m+1
+  double* y;     // m+1
+  double* mats;  // 9 m x m, ld m
+  int* piv;      // m+1
+  double* cvec;  // m+1: f(H) e_1
+  double* scal;  // 16 scalars
+  double* coef;  // m+1: output, ||b|| sigma_j c_j (zero when b = 0)
+};
+struct PadeCoef {
+  double b[14];  // [13/13] numerator coefficients (denominator: alternating signs)
+  double theta;  // largest 1-norm for which the unscaled approximant is used
+};
+
+// One CTA of 256 threads per listed job (ids[i] indexes jobs; ids NULL = 0..count-1).
+cudaError_t launch_small_fused(const SmallJob* jobs, const int* ids, int count, int mmax, const PadeCoef& pd,
+                               cudaStream_t s);
+// Sets the kernel's shared-memory limit for m <= mmax (before a graph capture).
+cudaError_t small_fused_prepare(int mmax);
+
 }  // namespace fab

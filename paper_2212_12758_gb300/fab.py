@@ -27,7 +27,8 @@ FP64, MIXED = 0, 1
 SYMBOLS = ("fab_params_default", "fab_strerror", "fab_last_error", "fab_create", "fab_apply", "fab_destroy", "fab_last_state",
            "fab_last_basis", "fab_sketch_apply", "fab_sketch_apply_noalloc", "fab_profile_enable",
            "fab_profile_query", "fab_server_create", "fab_server_submit", "fab_server_poll", "fab_server_stats_get",
-           "fab_server_destroy")
+           "fab_server_destroy", "fab_batch_create", "fab_batch_exec", "fab_batch_input", "fab_batch_output",
+           "fab_batch_kernels", "fab_batch_destroy", "fab_batch_run")
 PROFILE_KINDS = ("spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine")
 
 
@@ -84,6 +85,20 @@ lib.fab_server_stats_get.argtypes = [_vp, ctypes.POINTER(ServerStats)]
 lib.fab_server_stats_get.restype = _i32
 lib.fab_server_destroy.argtypes = [_vp]
 lib.fab_server_destroy.restype = None
+lib.fab_batch_create.argtypes = [ctypes.POINTER(_vp), _vp, _vp, _i32]
+lib.fab_batch_create.restype = _i32
+lib.fab_batch_exec.argtypes = [_vp, _vp, _vp, _vp, _vp]
+lib.fab_batch_exec.restype = _i32
+lib.fab_batch_input.argtypes = [_vp, _i32]
+lib.fab_batch_input.restype = _vp
+lib.fab_batch_output.argtypes = [_vp, _i32]
+lib.fab_batch_output.restype = _vp
+lib.fab_batch_kernels.argtypes = [_vp]
+lib.fab_batch_kernels.restype = _i32
+lib.fab_batch_destroy.argtypes = [_vp]
+lib.fab_batch_destroy.restype = None
+lib.fab_batch_run.argtypes = [_vp, _vp, _vp, _vp, _i32, _vp]
+lib.fab_batch_run.restype = _i32
 lib.fab_profile_enable.argtypes = [_i32]
 lib.fab_profile_enable.restype = _i32
 lib.fab_profile_query.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -287,6 +302,56 @@ class Server:
         if getattr(self, "_s", None):
             lib.fab_server_destroy(self._s)
             self._s = None
+
+    def __del__(self):
+        self.close()
+
+
+class Batch:
+    """Many solves of uneven size as one CUDA graph (fab_batch_*). The Matrix
+    handles must outlive the batch."""
+
+    def __init__(self, mats, ps):
+        self._mats = list(mats)
+        self.count = len(self._mats)
+        hs = (ctypes.c_void_p * self.count)(*[M._h.value for M in self._mats])
+        self._ps = (Params * self.count)(*ps)
+        h = ctypes.c_void_p()
+        _check(lib.fab_batch_create(ctypes.byref(h), ctypes.cast(hs, _vp), ctypes.cast(self._ps, _vp), self.count),
+               "fab_batch_create")
+        self._b = h
+        self.kernels = lib.fab_batch_kernels(self._b)
+
+    def run(self, bs=None, xs=None, stream=None, stats: bool = False):
+        """One run. bs: list of numpy (host) or torch CUDA arrays, or None when
+        the inputs were written to input(i). Returns the list of results as
+        numpy arrays (xs None), or fills xs."""
+        keep = []
+        bp = None
+        if bs is not None:
+            bs = [np.ascontiguousarray(b, dtype=np.float64) if isinstance(b, np.ndarray) else b for b in bs]
+            keep.append(bs)
+            bp = (ctypes.c_void_p * self.count)(*[_addr(b) for b in bs])
+        out = xs
+        if xs is None and bs is not None:
+            out = [np.empty(M.n) for M in self._mats]
+        xp = None if out is None else (ctypes.c_void_p * self.count)(*[_addr(x) for x in out])
+        sts = (Stats * self.count)()
+        _check(lib.fab_batch_exec(self._b, None if bp is None else ctypes.cast(bp, _vp),
+                                  None if xp is None else ctypes.cast(xp, _vp), ctypes.cast(sts, _vp), stream),
+               "fab_batch_exec")
+        return (out, list(sts)) if stats else out
+
+    def input(self, i: int) -> int:
+        return lib.fab_batch_input(self._b, int(i))
+
+    def output(self, i: int) -> int:
+        return lib.fab_batch_output(self._b, int(i))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib.fab_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         self.close()

@@ -1,0 +1,139 @@
+"""GPU: batched solves (fab_batch_*), many uneven solves as one CUDA graph.
+
+A solve's blocks in a batched wave are the blocks of its own launch, so its
+basis and sketch are bit for bit those of fab_apply; its small stage runs in
+one CTA (same operations, one-block reductions), so the batched result agrees
+with the solve alone to rounding of the m x m stage (1e-11 relative, FP64) and
+with the oracle to the library's FP64 target (1e-10).
+"""
+import numpy as np
+import pytest
+
+from oracle import krylov, matfun
+from oracle import sketch as osk
+from paper_2212_12758_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def fab():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2212_12758_gb300 import fab as f
+
+    return f
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+MATS = {
+    "cd2a": lambda: W.convdiff(2, 40),
+    "cd2b": lambda: W.convdiff(2, 71),
+    "cd3": lambda: W.convdiff(3, 19),
+    "graph": lambda: W.chung_lu_laplacian(6000, seed=2),
+}
+
+# (matrix, f, t, m, k, s, zeta, sketch, method, seed)
+SPECS = [
+    ("cd2a", matfun.EXP, -0.01, 30, 2, 120, 8, osk.SPARSE_SIGN, krylov.SKETCHED_FAST, 1),
+    ("cd2b", matfun.EXP, -0.004, 41, 2, 164, 4, osk.SPARSE_SIGN, krylov.SKETCHED_FAST, 2),
+    ("cd3", matfun.EXP, -0.001, 25, 4, 100, 8, osk.SRHT, krylov.SKETCHED_FAST, 3),
+    ("cd2a", matfun.EXP, -0.02, 18, 2, 0, 8, osk.SRHT, krylov.NOPROJ, 1),
+    ("graph", matfun.SQRT, 1.0, 22, 2, 88, 8, osk.SRHT, krylov.SKETCHED_FAST, 4),
+    ("graph", matfun.INVSQRT, 1.0, 30, 2, 120, 8, osk.SPARSE_SIGN, krylov.SKETCHED_FAST, 5),
+    ("cd3", matfun.EXP, -0.002, 35, 3, 0, 8, osk.SRHT, krylov.NOPROJ, 1),
+    ("graph", matfun.INVSQRT, 1.0, 12, 2, 0, 8, osk.SRHT, krylov.NOPROJ, 1),
+    ("cd2b", matfun.EXP, -0.001, 41, 2, 123, 8, osk.SRHT, krylov.SKETCHED_FAST, 6),
+]
+
+
+def _setup(fab, precision):
+    A = {k: v() for k, v in MATS.items()}
+    M = {k: fab.Matrix.from_csr(v) for k, v in A.items()}
+    mats, ps, bs, refs = [], [], [], []
+    for i, (name, f, t, m, k, s, zeta, sk, method, seed) in enumerate(SPECS):
+        kw = dict(f=f, t=t, m=m, k=k, zeta=zeta, sketch=sk, method=method, seed=seed, precision=precision)
+        kw["s"] = s if s else 4 * m
+        mats.append(M[name])
+        ps.append(fab.params(**kw))
+        bs.append(W.random_vector(A[name].n, 10 + i))
+        refs.append((name, kw))
+    return A, M, mats, ps, bs, refs
+
+
+def _oracle(A, name, kw, b):
+    As = W.to_scipy(A[name])
+    th = osk.make(kw["sketch"], A[name].n, kw["s"], kw["seed"], kw["zeta"]) if kw["method"] == krylov.SKETCHED_FAST else None
+    return krylov.run(kw["method"], As, b, kw["m"], kw["k"], kw["f"], th, kw["t"]).x
+
+
+def test_batch_fp64_matches_oracle_and_alone(fab):
+    A, M, mats, ps, bs, refs = _setup(fab, fab.FP64)
+    bt = fab.Batch(mats, ps)
+    xs, sts = bt.run(bs, stats=True)
+    assert bt.kernels > 0
+    for i, ((name, kw), b, x, st) in enumerate(zip(refs, bs, xs, sts)):
+        assert st.m_used == kw["m"], i
+        alone = mats[i].apply(b, ps[i])
+        assert _rel(x, alone) <= 1e-11, i
+        assert _rel(x, _oracle(A, name, kw, b)) <= TOL, i
+    bt.close()
+
+
+def test_batch_mixed_matches_alone(fab):
+    """FP32 basis: the batched basis is the solve's own, bit for bit; the FP64 small stage agrees to rounding."""
+    A, M, mats, ps, bs, refs = _setup(fab, fab.MIXED)
+    bt = fab.Batch(mats, ps)
+    xs = bt.run(bs)
+    for i, ((name, kw), b, x) in enumerate(zip(refs, bs, xs)):
+        alone = mats[i].apply(b, ps[i])
+        assert _rel(x, alone) <= 1e-10, i
+        assert _rel(x, _oracle(A, name, kw, b)) <= 2e-4, i  # FP32 basis against the FP64 oracle
+    bt.close()
+
+
+def test_batch_replay_device_inputs_deterministic(fab):
+    import torch
+
+    A, M, mats, ps, bs, refs = _setup(fab, fab.FP64)
+    bt = fab.Batch(mats, ps)
+    bd = [torch.from_numpy(b).cuda() for b in bs]
+    x1 = [torch.empty_like(b) for b in bd]
+    x2 = [torch.empty_like(b) for b in bd]
+    bt.run(bd, x1)
+    bt.run(None, x2)  # inputs left in the batch's staging vectors by the first run
+    for a, c in zip(x1, x2):
+        assert torch.equal(a, c)
+    bt.close()
+
+
+def test_batch_breakdown_zero_rhs_and_rejects(fab):
+    d = np.repeat([0.5, 1.0, 2.0, 3.5, 5.0], 40)
+    D = fab.Matrix.from_csr(W.diagonal(d))
+    C = fab.Matrix.from_csr(W.convdiff(2, 30))
+    b1 = W.random_vector(len(d), 2)
+    ps = [fab.params(f=fab.EXP, t=-0.3, m=8, k=2, s=16, sketch=fab.SRHT, seed=1),
+          fab.params(f=fab.EXP, t=-0.3, m=8, k=2, method=fab.NOPROJ),
+          fab.params(f=fab.EXP, t=-0.01, m=20, k=2, s=80)]
+    bt = fab.Batch([D, D, C], ps)
+    xs, sts = bt.run([b1, b1, np.zeros(C.n)], stats=True)
+    for i in (0, 1):
+        assert sts[i].m_used == 5
+        assert _rel(xs[i], np.exp(-0.3 * d) * b1) <= 1e-9
+    assert sts[2].m_used == 0 and not np.any(xs[2])
+    bt.close()
+    for bad in (fab.params(m=10, s=40, method=fab.ARNOLDI), fab.params(m=10, s=40, method=fab.SKETCHED_LS),
+                fab.params(m=10, s=40, sketch=fab.GAUSSIAN, precision=fab.MIXED)):
+        with pytest.raises(fab.FabError) as e:
+            fab.Batch([C], [bad])
+        assert e.value.code == fab.FAB_EINVAL
+    with pytest.raises(fab.FabError) as e:  # one precision per batch
+        fab.Batch([C, C], [fab.params(m=10, s=40), fab.params(m=10, s=40, precision=fab.MIXED)])
+    assert e.value.code == fab.FAB_EINVAL
