@@ -39,6 +39,11 @@ WORKLOAD = ("3D convection-diffusion 200^3 upwind FD (n=8,000,000, nnz=55,760,00
             "m=100, k=4, SRHT s=400, sketched_fast, FP64")
 
 
+def workload_name(N: int, n: int, nnz: int) -> str:
+    return (f"3D convection-diffusion {N}^3 upwind FD (n={n:,}, nnz={nnz:,}), x=exp(-1e-3 A) b, "
+            f"m={M}, k={K_WIN}, SRHT s={S_ROWS}, sketched_fast, FP64")
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -119,6 +124,113 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def fp32_step_bytes(n: int, nnz: int, kw: int, s: int) -> int:
+    """Algorithmic bytes of one basis step of the FP32 path (SpMV + dots, update +
+    sketch partials): 8 nnz + 4 (n+1) + 4 n kw + 4 n, then 4 n (kw + 2) + 8 s per chunk."""
+    return 8 * nnz + 4 * (n + 1) + 4 * n * kw + 4 * n + 4 * n * (kw + 2) + 8 * s * ((n + 4095) // 4096)
+
+
+def bench_batch(fab, torch, W, steps: int = 3):
+    """256 uneven 2D convection-diffusion solves (n log-uniform on [1e4, 1e6], t on
+    [1e-4, 1e-2], m on {20..80}, k = 2, sparse sign s = 4m, zeta = 8, batch seed 3)
+    as one CUDA graph, FP32 basis / FP64 small stage; inputs resident on the device."""
+    specs = W.batch_specs(256, seed=3)
+    A = [W.convdiff(2, it.N) for it in specs]
+    mats = [fab.Matrix.from_csr(a) for a in A]
+    k = 2
+
+    def ps(prec):
+        return [fab.params(f=fab.EXP, t=-it.t, m=it.m, k=k, s=4 * it.m, zeta=8, sketch=fab.SPARSE_SIGN, seed=1 + i,
+                           method=fab.SKETCHED_FAST, precision=prec) for i, it in enumerate(specs)]
+
+    bs = [torch.from_numpy(W.random_vector(a.n, 100 + i)).cuda() for i, a in enumerate(A)]
+    t0 = time.perf_counter()
+    bt = fab.Batch(mats, ps(fab.MIXED))
+    create_s = time.perf_counter() - t0
+    xs = [torch.empty_like(b) for b in bs]
+    bt.run(bs, xs)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        bt.run(None, None, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        bt.run(None, None, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    byts = 0
+    for a, it in zip(A, specs):
+        byts += sum(fp32_step_bytes(a.n, a.nnz, min(c, k), 4 * it.m) for c in range(1, it.m + 1))
+        byts += 4 * a.n * it.m + 8 * a.n  # combine
+    bt.run(None, xs)
+    bt64 = fab.Batch(mats, ps(fab.FP64))
+    x64 = [torch.empty_like(b) for b in bs]
+    bt64.run(bs, x64)
+    err = max(float(torch.linalg.norm(x - y) / torch.linalg.norm(y)) for x, y in zip(xs, x64))
+    kernels = bt.kernels
+    bt.close()
+    bt64.close()
+    peak = float(_peaks().get("hbm_gbs", 6800.0))
+    return {"workload": "256 uneven 2D convection-diffusion solves (n 1e4..1e6 log-uniform, m 20..80, t 1e-4..1e-2), "
+                        "k=2, sparse sign s=4m, sketched_fast, FP32 basis / FP64 small stage, one CUDA graph",
+            "solves_per_s": 256 / (ms / 1000.0), "ms_per_batch": ms, "graph_kernels": kernels,
+            "sum_n": int(sum(a.n for a in A)), "algorithmic_gb": byts / 1e9,
+            "hbm_gbs_algorithmic": byts / (ms / 1000.0) / 1e9,
+            "hbm_frac_of_measured": byts / (ms / 1000.0) / 1e9 / peak,
+            "note": "solves with n below ~3e5 keep their basis in L2, so algorithmic GB/s is not all HBM traffic",
+            "max_rel_err_vs_fp64_same_m": err, "create_s": create_s}
+
+
+def bench_mixed_graph(fab, torch, W, reps: int = 2):
+    """Shifted Chung-Lu Laplacian (n = 4M, exponent 2.5, mean degree 10, L + 0.1 I), f = A^{-1/2}
+    and A^{1/2}, m = 150, k = 2, Gaussian sketch s = 600 (BF16 on the tensor cores, FP32
+    accumulation), FP32 basis, FP64 QR and f(H). Error against the library's FP64 Arnoldi
+    f_m at the same m and at m = 300."""
+    A = W.chung_lu_laplacian(4_000_000, seed=2)
+    Mx = fab.Matrix.from_csr(A)
+    b = torch.from_numpy(W.random_vector(A.n, 0)).cuda()
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    m, s = 150, 600
+    out = {"workload": f"Chung-Lu Laplacian n={A.n:,} nnz={A.nnz:,} (+0.1 I), m=150, k=2, Gaussian s=600 BF16 "
+                       "tensor cores, FP32 basis, FP64 small stage, sketched_fast"}
+    peaks = _peaks()
+    for name, f in (("invsqrt", fab.INVSQRT), ("sqrt", fab.SQRT)):
+        p = fab.params(f=f, m=m, k=2, s=s, sketch=fab.GAUSSIAN, seed=1, method=fab.SKETCHED_FAST,
+                       precision=fab.MIXED, stream=sp)
+        x = torch.empty_like(b)
+        Mx.apply(b, p, x=x)  # warm (draws G once per handle)
+        torch.cuda.synchronize()
+        fab.profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            Mx.apply(b, p, x=x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = fab.profile_query()
+        fab.profile_enable(False)
+        ms = e0.elapsed_time(e1) / reps
+        g_ms = prof["sketch_reduce"][0] / max(prof["sketch_reduce"][1], 1)
+        flops = 2.0 * s * A.n * (m + 1)
+        gbytes = 2.0 * s * A.n + 2.0 * A.n * (m + 1)
+        ref = {}
+        for mr in (150, 300):
+            xr = torch.empty_like(b)
+            Mx.apply(b, fab.params(f=f, m=mr, k=2, method=fab.ARNOLDI, stream=sp), x=xr)
+            ref[mr] = float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))
+        out[name] = {"solves_per_s": 1000.0 / ms, "ms_per_solve": ms,
+                     "rel_err_vs_fp64_arnoldi_m150": ref[150], "rel_err_vs_fp64_arnoldi_m300": ref[300],
+                     "gauss_sketch_ms": g_ms, "gauss_tflops": flops / (g_ms / 1000.0) / 1e12,
+                     "gauss_tensor_frac_of_measured_bf16": flops / (g_ms / 1000.0) / 1e12
+                     / float(peaks.get("bf16_tflops", 1900.0)),
+                     "gauss_hbm_gbs_algorithmic": gbytes / (g_ms / 1000.0) / 1e9,
+                     "kernels_ms": {k_: v[0] / reps for k_, v in prof.items()}}
+    return out
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
@@ -187,6 +299,21 @@ def run_reference(args):
     return 0
 
 
+def run_only(args):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2212_12758_gb300 import fab
+    from paper_2212_12758_gb300 import workloads as W
+
+    out = bench_batch(fab, torch, W, steps=args.steps) if args.only == "batch" else \
+        bench_mixed_graph(fab, torch, W, reps=args.steps)
+    print(json.dumps({"only": args.only, **out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -195,6 +322,11 @@ def main():
     ap.add_argument("--impl", default="fab", choices=["fab", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the sketched_ls / Arnoldi side measurements")
+    ap.add_argument("--extras", default="batch,graph",
+                    help="side workloads measured after the main one: batch (256 uneven solves, one graph), "
+                         "graph (4M-node power-law Laplacian, mixed precision, Gaussian sketch)")
+    ap.add_argument("--only", choices=["batch", "graph"], default=None,
+                    help="measure one side workload alone and print its JSON (for profiler runs)")
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="grid side N of the 3D operator (default 200, the benchmark workload; smaller N only "
                          "for profiler captures)")
@@ -203,6 +335,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
 
     import torch
 
@@ -343,6 +477,11 @@ def main():
         e2e_s = float(tt.item())
     e2e = {"value": ws / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
 
+    if not args.no_extras and "batch" in args.extras.split(","):
+        extras["batch_256"] = bench_batch(fab, torch, W)
+    if not args.no_extras and "graph" in args.extras.split(","):
+        extras["mixed_graph_4M"] = bench_mixed_graph(fab, torch, W)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(A, b)
@@ -351,7 +490,7 @@ def main():
         line = {"metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD if args.grid == N_GRID else WORKLOAD.replace("200^3", f"{args.grid}^3"),
+                "config": {"workload": workload_name(args.grid, n, nnz),
                            "n": n, "nnz": nnz, "m": M, "k": K_WIN, "s": S_ROWS,
                            "sketch": "srht", "method": "sketched_fast", "f": "exp(tA), t=-1e-3",
                            "l2": "inputs larger than L2 (A 0.7 GB, basis 6.5 GB per solve)",

@@ -236,6 +236,28 @@ int fab_server_stats_get(fab_server* srv, fab_server_stats* out);
 void fab_server_destroy(fab_server* srv);
 
 /*
+ * SpMV tiling of a matrix (the work unit of the SpMV + window-dot kernel, Alg. 2).
+ * The rows are cut into tiles of consecutive rows with at most rows_max (<= 256)
+ * rows and at most nnz_cap nonzeros each (a longer row is a tile of its own);
+ * a tile with R rows runs 256 / pow2ceil(R) lanes per row, so short rows get a
+ * thread each and a long row the whole block. staged = 1 copies a tile's
+ * nonzeros into shared memory (bulk copies) when they fit 2048 entries.
+ * fab_create uses (256, 2048, 1). The tiling fixes the order of the SpMV
+ * additions, so results differ within rounding between tilings (and are
+ * reproducible for a given one).
+ * fab_set_tiling  sets it; FAB_EINVAL for rows_max outside 1..256, nnz_cap < 1
+ *                 or a workspace clone.
+ * fab_tune        times the kernel on h's matrix (precision FAB_FP64 or
+ *                 FAB_MIXED, window k) for rows_max in {256, 128, 64}, nnz_cap
+ *                 in {2048, 1024, 512} and staged in {1, 0}, keeps the fastest
+ *                 and writes it to choice[3] (nullable). Uses a temporary device
+ *                 buffer of about (k+1) n words; `stream` is a cudaStream_t or NULL.
+ * Neither may run while a solve, batch or server request uses h.
+ */
+int fab_set_tiling(fab_handle* h, int rows_max, int nnz_cap, int staged);
+int fab_tune(fab_handle* h, int precision, int k, int* choice, void* stream);
+
+/*
  * Batched solves: many f(A)b of uneven size (different matrices, n, m, k, s, f)
  * as one CUDA graph. Work items are (solve, basis step, tile): for each basis
  * step c the graph holds one launch per (window k, sketch kind) group covering

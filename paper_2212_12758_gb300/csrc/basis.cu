@@ -71,11 +71,12 @@ cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s) {
 //   coef_q    = sigma_j^2 d_j       (update coefficient of the raw column),
 //   wn2[c]    = tau^2 ||W_c||^2     (= ||A v_{c-1}||^2, for the breakdown test),
 //   scl[c]    = tau.
-// CSR tiles of 256 rows are staged in shared memory by bulk copies (double
-// buffered, one tile ahead); a tile whose nonzeros exceed the stage capacity is
-// read from global memory directly.
-constexpr int kSpmvTile = kThreads;  // rows per tile, one per thread
-constexpr int kSpmvCap = 2048;       // nonzeros per stage (vals 16 KB + colind 8 KB)
+// The rows are cut into tiles of at most 256 rows and (unless a single row has
+// more) at most kSpmvCap nonzeros, so every block iteration has about the same
+// work whatever the row lengths. A tile's nonzeros are staged in shared memory
+// by bulk copies (double buffered, one tile ahead) when they fit the stage; a
+// longer single-row tile is read from global memory with the same order of
+// operations.
 
 // The work of block `bid` of `nblk` (a launch of its own, or one solve's share
 // of a batched wave) is a function of (bid, nblk) only, so a solve gives the
@@ -94,9 +95,10 @@ __device__ __forceinline__ void spmv_dots_body(
   __shared__ int s_staged[2];
   __shared__ double sh[32 * NV];
   __shared__ double tot[NV];
+  __shared__ TV s_red[kThreads / 32];
   if (st->stop) return;
   const int tid = threadIdx.x;
-  const int ntiles = (A.n + kSpmvTile - 1) / kSpmvTile;
+  const int ntiles = A.ntiles;
   const TV* vin = W + (size_t)(c - 1) * ld;
   TV* wout = W + (size_t)c * ld;
   const int ksh = cs.shf[c - 1];
@@ -116,12 +118,11 @@ __device__ __forceinline__ void spmv_dots_body(
   // so that both copies start and end on 16-byte boundaries; the CSR arrays are
   // allocated with 4 spare entries).
   auto issue = [&](int tile, int stg) {
-    const int r0 = tile * kSpmvTile;
-    const int r1 = min(r0 + kSpmvTile, A.n);
+    const int r0 = A.tiles[tile], r1 = A.tiles[tile + 1];
     const int e0 = A.rowptr[r0], e1 = A.rowptr[r1];
     const int e0a = e0 & ~3, e1a = (e1 + 3) & ~3;
     const int cnt = e1a - e0a;
-    if (cnt > 0 && cnt <= kSpmvCap) {
+    if (A.staged && cnt > 0 && cnt <= kSpmvCap) {
       s_e0[stg] = e0a;
       s_staged[stg] = 1;
       fence_proxy_async_smem();
@@ -152,37 +153,75 @@ __device__ __forceinline__ void spmv_dots_body(
       }
       if (stg) par1 ^= 1u; else par0 ^= 1u;
     }
-    const int r = tile * kSpmvTile + tid;
-    if (r < A.n) {
+    // The tile's rows share the block: L = 256 / pow2ceil(rows) lanes per row
+    // (one row per thread for full tiles, the whole block for a single long row);
+    // each lane sums every L-th nonzero of its row, then the lanes of a row are
+    // combined in a fixed order.
+    const int r0 = A.tiles[tile], nr = A.tiles[tile + 1] - r0;
+    const int lgL = 8 - (nr > 1 ? 32 - __clz(nr - 1) : 0);
+    const int L = 1 << lgL;
+    const int grp = tid >> lgL, lane_r = tid & (L - 1);
+    const bool has_row = grp < nr;
+    const int r = r0 + grp;
+    TV y = (TV)0;
+    TV wv[KW > 0 ? KW : 1];
+    if (has_row) {
       const int e0 = A.rowptr[r], e1 = A.rowptr[r + 1];
-      TV wv[KW > 0 ? KW : 1];
+      if (lane_r == 0) {
 #pragma unroll
-      for (int q = 0; q < KW; ++q) wv[q] = W[(size_t)(j0 + q) * ld + r];  // window entries, issued early (r < n)
-      TV y = (TV)0;
+        for (int q = 0; q < KW; ++q) wv[q] = W[(size_t)(j0 + q) * ld + r];  // window entries, issued early
+      }
+      int e = e0 + lane_r;
       if (staged) {
         const int base = s_e0[stg];
         const TV* sv = s_vals + stg * kSpmvCap - base;
         const int* sc = s_col + stg * kSpmvCap - base;
-        int e = e0;
-        for (; e + 8 <= e1; e += 8) {  // eight gathers in flight per thread
+        for (; e + 7 * L < e1; e += 8 * L) {  // eight gathers in flight per thread
           TV g[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) g[u] = __ldg(vin + sc[e + u]);
+          for (int u = 0; u < 8; ++u) g[u] = __ldg(vin + sc[e + u * L]);
 #pragma unroll
-          for (int u = 0; u < 8; ++u) y = fma(sv[e + u], g[u], y);
+          for (int u = 0; u < 8; ++u) y = fma(sv[e + u * L], g[u], y);
         }
-        const int rem = e1 - e;
-        if (rem > 0) {  // tail: every index is clamped into the row, so no load can leave it
+        if (e < e1) {  // tail: every index is clamped into the row, so no load can leave it
+          const int rem = (e1 - e + L - 1) >> lgL;
           TV g[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) g[u] = __ldg(vin + sc[min(e + u, e1 - 1)]);
+          for (int u = 0; u < 8; ++u) g[u] = __ldg(vin + sc[min(e + u * L, e1 - 1)]);
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            if (u < rem) y = fma(sv[e + u], g[u], y);
+            if (u < rem) y = fma(sv[e + u * L], g[u], y);
         }
-      } else {
-        for (int e = e0; e < e1; ++e) y = fma(__ldg(Avals + e), __ldg(vin + __ldg(A.colind + e)), y);
+      } else {  // same order of operations, operands from global memory
+        for (; e + 7 * L < e1; e += 8 * L) {
+          int cidx[8];
+          TV av[8], g[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            cidx[u] = __ldg(A.colind + e + u * L);
+            av[u] = __ldg(Avals + e + u * L);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) g[u] = __ldg(vin + cidx[u]);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) y = fma(av[u], g[u], y);
+        }
+        for (; e < e1; e += L) y = fma(__ldg(Avals + e), __ldg(vin + __ldg(A.colind + e)), y);
       }
+    }
+    if (L > 1) {  // block-uniform branch: combine the lanes of each row
+      for (int o = (L < 32 ? L : 32) >> 1; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+      if (L > 32) {
+        if ((tid & 31) == 0) s_red[tid >> 5] = y;
+        __syncthreads();
+        if (lane_r == 0) {
+          TV t = s_red[tid >> 5];
+          for (int q = 1; q < (L >> 5); ++q) t += s_red[(tid >> 5) + q];
+          y = t;
+        }
+      }
+    }
+    if (has_row && lane_r == 0) {
       y = scale_pow2(y, ksh, p2k);
       wout[r] = y;
 #pragma unroll
@@ -250,7 +289,7 @@ const void* spmv_fn(int kw) {
 }
 
 template <typename TV>
-int spmv_grid(int n, int kw) {
+int spmv_grid(int ntiles, int kw) {
   static int occ[kMaxWindow + 1] = {0};
   if (occ[kw] == 0) {
     const size_t smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
@@ -259,9 +298,8 @@ int spmv_grid(int n, int kw) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmv_fn<TV>(kw), kThreads, smem);
     occ[kw] = o < 1 ? 1 : o;
   }
-  const int need = (n + kSpmvTile - 1) / kSpmvTile;
   const int grid = sm_count() * occ[kw];
-  return need < grid ? (need < 1 ? 1 : need) : grid;
+  return ntiles < grid ? (ntiles < 1 ? 1 : ntiles) : grid;
 }
 template int spmv_grid<double>(int, int);
 template int spmv_grid<float>(int, int);
@@ -272,7 +310,7 @@ cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int
                              DevState* st, cudaStream_t s) {
   if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
   const size_t smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
-  const int grid = spmv_grid<TV>(A.n, kw);
+  const int grid = spmv_grid<TV>(A.ntiles, kw);
   void* args[] = {(void*)&A, &W, &ld, &c, &j0, &kw, &cs, &H, &ldh, &coef, &wn2, &part, &counter, &st};
   return cudaLaunchKernel(spmv_fn<TV>(kw), dim3(grid), dim3(kThreads), args, smem, s);
 }

@@ -136,7 +136,7 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       if (c > 0) {
         std::vector<int> nb;
         for (int j : ids) {
-          nb.push_back(spmv_grid<TV>(bt->n[j], kw));
+          nb.push_back(spmv_grid<TV>(hs[j]->ntiles, kw));
           part_need[j] = std::max(part_need[j], (size_t)nb.back() * (kMaxWindow + 1));
         }
         HostWave w{W_SPMV};
@@ -209,8 +209,14 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       const int n = h->n, m = p.m, s = kind[j] == SK_NONE ? 1 : p.s;
       BasisJob<TV>& J = jobs[j];
       memset(&J, 0, sizeof(J));
-      J.A = Csr{h->n, h->nnz, h->d_rowptr, h->d_colind,
-                bt->mixed ? (const void*)h->d_vals32 : (const void*)h->d_vals};
+      J.A = Csr{h->n,
+                h->nnz,
+                h->d_rowptr,
+                h->d_colind,
+                bt->mixed ? (const void*)h->d_vals32 : (const void*)h->d_vals,
+                h->d_tiles,
+                h->ntiles,
+                h->tile_staged};
       J.ld = h->ld;
       J.W = ar.take<TV>((size_t)h->ld * (m + 1));
       J.cs.sigma = ar.take<double>(m + 1);
@@ -291,12 +297,17 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
   int* tab_dev;
   std::tie(jobs_dev, small_dev, tab_dev, bt->states) = layout(ar);
 
-  cudaStream_t cap = nullptr, side = nullptr;
+  // Small stages of different completion steps go to separate graph branches
+  // (streams of a pool), so a group never waits for the previous group's CTAs.
+  constexpr int kBranches = 16;
+  cudaStream_t cap = nullptr;
+  cudaStream_t side[kBranches] = {};
   cudaEvent_t fork = nullptr, join = nullptr;
   auto cleanup = [&]() {
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
-    if (side) cudaStreamDestroy(side);
+    for (cudaStream_t& q : side)
+      if (q) cudaStreamDestroy(q);
     if (cap) cudaStreamDestroy(cap);
   };
 #define BK(call)              \
@@ -308,7 +319,7 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
     }                         \
   } while (0)
   BK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  BK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+  for (cudaStream_t& q : side) BK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
   BK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
   BK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
   BK(cudaMemcpyAsync(jobs_dev, jobs.data(), sizeof(BasisJob<TV>) * count, cudaMemcpyHostToDevice, cap));
@@ -335,8 +346,8 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
 
   // ------------------------------------------------------------ capture
   BK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-  int kernels = 0;
-  bool side_used = false;
+  int kernels = 0, branch = -1;
+  bool side_used[kBranches] = {};
   cudaError_t e = cudaSuccess;
   for (const HostWave& w : waves) {
     const Wave wv{tab_dev + w.pre, tab_dev + w.ids, tab_dev + w.aux, w.count};
@@ -348,20 +359,22 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
         break;
       case W_REDUCE: e = launch_sketch_reduce_wave<TV>(jobs_dev, wv, w.nblocks, w.c, cap); break;
       case W_SMALL:
+        branch = (branch + 1) % kBranches;
         if ((e = cudaEventRecord(fork, cap)) != cudaSuccess) break;
-        if ((e = cudaStreamWaitEvent(side, fork, 0)) != cudaSuccess) break;
-        side_used = true;
-        e = launch_small_fused(small_dev, tab_dev + w.ids, w.count, w.mmax, pd, side);
+        if ((e = cudaStreamWaitEvent(side[branch], fork, 0)) != cudaSuccess) break;
+        side_used[branch] = true;
+        e = launch_small_fused(small_dev, tab_dev + w.ids, w.count, w.mmax, pd, side[branch]);
         break;
-      case W_COMBINE: e = launch_combine_wave<TV>(jobs_dev, wv, w.nblocks, w.mmax, side); break;
+      case W_COMBINE: e = launch_combine_wave<TV>(jobs_dev, wv, w.nblocks, w.mmax, side[branch]); break;
     }
     if (e != cudaSuccess) break;
     ++kernels;
   }
-  if (e == cudaSuccess && side_used) {
-    e = cudaEventRecord(join, side);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join, 0);
-  }
+  for (int q = 0; q < kBranches && e == cudaSuccess; ++q)
+    if (side_used[q]) {
+      e = cudaEventRecord(join, side[q]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join, 0);
+    }
   cudaGraph_t graph = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
   if (e != cudaSuccess || e2 != cudaSuccess) {

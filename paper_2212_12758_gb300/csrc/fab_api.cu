@@ -26,6 +26,19 @@ namespace {
 constexpr double kTheta13 = 5.371920351148152;
 constexpr int64_t kCsrPad = 4;  // spare CSR entries for the aligned tile copies
 
+// Bump allocator over a caller-provided device buffer (256-byte aligned pieces).
+struct Arena8 {
+  unsigned char* base;
+  size_t off = 0;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
 struct Pade13 {
   double b[14];
   Pade13() {
@@ -188,6 +201,13 @@ int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr, 
     fab_destroy(h);
     return FAB_ECUDA;
   }
+  h->h_rowptr = new int[n + 1];
+  memcpy(h->h_rowptr, rp32.data(), (n + 1) * sizeof(int));
+  const int rc = fab::build_tiles(h, 256, kSpmvCap, 1);
+  if (rc != FAB_OK) {
+    fab_destroy(h);
+    return rc;
+  }
   *out = h;
   return FAB_OK;
 }
@@ -199,6 +219,8 @@ void fab_destroy(fab_handle* h) {
     cudaFree(h->d_colind);
     cudaFree(h->d_vals);
     cudaFree(h->d_vals32);
+    cudaFree(h->d_tiles);
+    delete[] h->h_rowptr;
   }
   Buf* bufs[] = {&h->W32, &h->Wbf, &h->G, &h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
                  &h->skpart, &h->SV, &h->P,     &h->qr,  &h->tau,  &h->y,    &h->cvec,    &h->dense,
@@ -487,7 +509,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   const int ldh = m + 1;
   const bool sk_on = sketched(p->method);
   const int* mdev = &ws.st->m_used;
-  Csr A{h->n, h->nnz, h->d_rowptr, h->d_colind, vals};
+  Csr A{h->n, h->nnz, h->d_rowptr, h->d_colind, vals, h->d_tiles, h->ntiles, h->tile_staged};
   h->has_state = 0;
   g_launches = 0;
   if (g_prof.on) g_prof.begin_solve();
@@ -863,6 +885,108 @@ extern "C" int fab_profile_query(const char* name, double* total_ms, int64_t* la
   return FAB_EINVAL;
 }
 
+extern "C" int fab_set_tiling(fab_handle* h, int rows_max, int nnz_cap, int staged) {
+  if (!h || !h->owns_matrix) return FAB_EINVAL;
+  return fab::build_tiles(h, rows_max, nnz_cap, staged);
+}
+
+namespace {
+// Device time (ms per launch) of the SpMV + window-dot kernel with h's current tiling.
+template <typename TV>
+int time_spmv(fab_handle* h, const void* vals, int k, unsigned char* scratch, cudaStream_t s, float* ms_out) {
+  const int cols = k + 1;
+  const size_t ld = (size_t)h->ld;
+  Arena8 ar{scratch};
+  TV* W = ar.take<TV>(ld * cols);
+  ColScale cs{ar.take<double>(cols), ar.take<int>(cols), ar.take<double>(cols + 1)};
+  double* H = ar.take<double>((size_t)cols * cols);
+  double* coef = ar.take<double>(cols);
+  double* wn2 = ar.take<double>(cols + 1);
+  double* part = ar.take<double>((size_t)sm_count() * kMaxPartBlocks * (kMaxWindow + 1));
+  unsigned* counter = ar.take<unsigned>(16);
+  DevState* st = ar.take<DevState>(1);
+  Csr A{h->n, h->nnz, h->d_rowptr, h->d_colind, vals, h->d_tiles, h->ntiles, h->tile_staged};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaGetLastError();
+    return FAB_ECUDA;
+  }
+  const int reps = 5;
+  cudaError_t e = launch_spmv_dots<TV>(A, W, ld, k, 0, k, cs, H, cols, coef, wn2, part, counter, st, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i)
+    e = launch_spmv_dots<TV>(A, W, ld, k, 0, k, cs, H, cols, coef, wn2, part, counter, st, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return FAB_ECUDA;
+  }
+  *ms_out = ms / reps;
+  return FAB_OK;
+}
+}  // namespace
+
+extern "C" int fab_tune(fab_handle* h, int precision, int k, int* choice, void* stream) {
+  if (!h || !h->owns_matrix || (precision != FAB_FP64 && precision != FAB_MIXED) || k < 1 || k > kMaxWindow)
+    return FAB_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == FAB_MIXED) {
+    const int rc = ensure_vals32(h, s);
+    if (rc != FAB_OK) return rc;
+  }
+  const size_t esz = precision == FAB_MIXED ? 4 : 8;
+  const int cols = k + 1;
+  const size_t bytes = (size_t)h->ld * cols * esz + (size_t)sm_count() * kMaxPartBlocks * (kMaxWindow + 1) * 8 +
+                       (size_t)cols * cols * 8 + 64 * 1024;
+  unsigned char* scratch = nullptr;
+  if (fault_hit() || cudaMalloc(&scratch, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return FAB_ENOMEM;
+  }
+  if (cudaMemsetAsync(scratch, 0, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(scratch);
+    return FAB_ECUDA;
+  }
+  // candidates: rows per tile x nonzeros per tile x shared-memory staging
+  const int rows_c[] = {256, 128, 64};
+  const int nnz_c[] = {kSpmvCap, kSpmvCap / 2, kSpmvCap / 4};
+  float best = 1e30f;
+  int bi[3] = {256, kSpmvCap, 1};
+  int rc = FAB_OK;
+  for (int ri = 0; ri < 3 && rc == FAB_OK; ++ri)
+    for (int ni = 0; ni < 3 && rc == FAB_OK; ++ni)
+      for (int stg = 1; stg >= 0 && rc == FAB_OK; --stg) {
+        rc = fab::build_tiles(h, rows_c[ri], nnz_c[ni], stg);
+        if (rc != FAB_OK) break;
+        float ms = 0.0f;
+        rc = precision == FAB_MIXED ? time_spmv<float>(h, h->d_vals32, k, scratch, s, &ms)
+                                    : time_spmv<double>(h, h->d_vals, k, scratch, s, &ms);
+        if (rc == FAB_OK && ms < best) {
+          best = ms;
+          bi[0] = rows_c[ri];
+          bi[1] = nnz_c[ni];
+          bi[2] = stg;
+        }
+      }
+  cudaFree(scratch);
+  const int rc2 = fab::build_tiles(h, bi[0], bi[1], bi[2]);
+  if (rc == FAB_OK) rc = rc2;
+  if (choice) {
+    choice[0] = bi[0];
+    choice[1] = bi[1];
+    choice[2] = bi[2];
+  }
+  return rc;
+}
+
 extern "C" const char* fab_last_error(void) { return g_errmsg; }
 
 namespace fab {
@@ -920,7 +1044,47 @@ fab_handle* clone_for_workspace(const fab_handle* h) {
   return c;
 }
 
+int build_tiles(fab_handle* h, int rows_max, int nnz_cap, int staged) {
+  if (!h || !h->h_rowptr || rows_max < 1 || rows_max > kThreads || nnz_cap < 1) return FAB_EINVAL;
+  const int* rp = h->h_rowptr;
+  std::vector<int> t;
+  t.reserve(h->n / 16 + 2);
+  t.push_back(0);
+  int r0 = 0;
+  while (r0 < h->n) {
+    int r1 = r0 + 1;
+    // grow while the tile stays within rows_max rows and its 16-byte aligned
+    // nonzero range within nnz_cap entries
+    while (r1 < h->n && r1 - r0 < rows_max && ((rp[r1 + 1] + 3) & ~3) - (rp[r0] & ~3) <= nnz_cap) ++r1;
+    t.push_back(r1);
+    r0 = r1;
+  }
+  int* d = nullptr;
+  if (alloc_fault() || cudaMalloc(&d, t.size() * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return FAB_ENOMEM;
+  }
+  if (cudaMemcpy(d, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(d);
+    return FAB_ECUDA;
+  }
+  cudaFree(h->d_tiles);
+  h->d_tiles = d;
+  h->ntiles = (int)t.size() - 1;
+  h->tile_rows = rows_max;
+  h->tile_nnz = nnz_cap;
+  h->tile_staged = staged ? 1 : 0;
+  return FAB_OK;
+}
+
 void point_to_matrix(fab_handle* c, const fab_handle* h) {
+  c->d_tiles = h->d_tiles;
+  c->ntiles = h->ntiles;
+  c->tile_rows = h->tile_rows;
+  c->tile_nnz = h->tile_nnz;
+  c->tile_staged = h->tile_staged;
+  c->h_rowptr = h->h_rowptr;
   c->n = h->n;
   c->nnz = h->nnz;
   c->d_rowptr = h->d_rowptr;

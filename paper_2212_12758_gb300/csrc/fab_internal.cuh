@@ -212,8 +212,12 @@ struct Csr {
   int nnz;
   const int* rowptr;
   const int* colind;
-  const void* vals;  // FP64 values (FP64 path) or FP32 values (mixed path)
+  const void* vals;   // FP64 values (FP64 path) or FP32 values (mixed path)
+  const int* tiles;   // SpMV row tiles: tile t is rows tiles[t] .. tiles[t+1]-1 (<= 256 rows)
+  int ntiles;
+  int staged;         // 1: stage a tile's nonzeros in shared memory by bulk copies when they fit
 };
+constexpr int kSpmvCap = 2048;  // nonzeros per staged SpMV tile (FP64: vals 16 KB + colind 8 KB)
 
 cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s);
 // Column bookkeeping of the raw basis (see basis.cu): sigma[j] = 1/||W_j||,
@@ -266,7 +270,7 @@ struct Wave {
 };
 // Grid of the single-solve launch of each basis kernel (a batched solve uses the same).
 template <typename TV>
-int spmv_grid(int n, int kw);
+int spmv_grid(int ntiles, int kw);
 template <typename TV>
 int update_grid(int kind, int n, int nc, int s, size_t* smem);
 int combine_grid(int n);

@@ -46,6 +46,11 @@ struct fab_handle {
   double* d_vals = nullptr;
   float* d_vals32 = nullptr;  // FP32 copy for the mixed-precision path (made on first use)
   int64_t ld = 0;
+  // SpMV row tiles (see build_tiles); shared by workspace clones
+  int* d_tiles = nullptr;
+  int ntiles = 0;
+  int tile_rows = 256, tile_nnz = 2048, tile_staged = 1;
+  int* h_rowptr = nullptr;  // host copy of the row pointers (n+1), for re-tiling
   // workspace
   fab::Buf W, H, sigma, shf, scl, wn2, coef, part, counter, gpart, skpart, SV, P, qr, tau, y, cvec, dense, piv, scal, lsq, u, xbuf,
       state;
@@ -73,6 +78,12 @@ void point_to_matrix(fab_handle* clone, const fab_handle* h);
 int ensure_vals32(fab_handle* h, cudaStream_t s);
 // Sets this host thread's fab_last_error() text (carries a serving slot's detail to the poller).
 void set_last_error(const char* msg);
+// Recut A's SpMV row tiles: consecutive rows, at most rows_max rows and at most
+// nnz_cap nonzeros per tile (a longer row is a tile of its own); staged = 1
+// stages tiles in shared memory. FAB_OK, FAB_EINVAL or FAB_ENOMEM.
+int build_tiles(fab_handle* h, int rows_max, int nnz_cap, int staged);
+// The CSR view of h's matrix for the basis kernels (vals: FP64 or FP32 copy).
+struct Csr;
 // Parameter checks of fab_apply (FAB_OK or FAB_EINVAL).
 int validate_params(const fab_handle* h, const fab_params* p);
 // Pade [13/13] numerator coefficients b_0..b_13 and the threshold theta_13.

@@ -100,6 +100,9 @@ void worker(fab_server* s, int self) {
             r = head;
             s->queue.pop_front();
             sl.busy = true;
+            // reserve the workspace now: other slots' admission must see it
+            // while this solve grows it
+            if (sl.held < r->need) sl.held = r->need;
             break;
           }
           if (sl.held > 0) {  // blocked: give back this slot's cached workspace and retry

@@ -28,7 +28,7 @@ SYMBOLS = ("fab_params_default", "fab_strerror", "fab_last_error", "fab_create",
            "fab_last_basis", "fab_sketch_apply", "fab_sketch_apply_noalloc", "fab_profile_enable",
            "fab_profile_query", "fab_server_create", "fab_server_submit", "fab_server_poll", "fab_server_stats_get",
            "fab_server_destroy", "fab_batch_create", "fab_batch_exec", "fab_batch_input", "fab_batch_output",
-           "fab_batch_kernels", "fab_batch_destroy", "fab_batch_run")
+           "fab_batch_kernels", "fab_batch_destroy", "fab_batch_run", "fab_set_tiling", "fab_tune")
 PROFILE_KINDS = ("spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine")
 
 
@@ -99,6 +99,10 @@ lib.fab_batch_destroy.argtypes = [_vp]
 lib.fab_batch_destroy.restype = None
 lib.fab_batch_run.argtypes = [_vp, _vp, _vp, _vp, _i32, _vp]
 lib.fab_batch_run.restype = _i32
+lib.fab_set_tiling.argtypes = [_vp, _i32, _i32, _i32]
+lib.fab_set_tiling.restype = _i32
+lib.fab_tune.argtypes = [_vp, _i32, _i32, _vp, _vp]
+lib.fab_tune.restype = _i32
 lib.fab_profile_enable.argtypes = [_i32]
 lib.fab_profile_enable.restype = _i32
 lib.fab_profile_query.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -199,6 +203,15 @@ class Matrix:
         _check(lib.fab_apply(self._h, ctypes.byref(p), _addr(b), _addr(x), on_dev, ctypes.byref(st)), "fab_apply")
         self._last = (p.m, p.s, p.method in (SKETCHED_FAST, SKETCHED_LS))
         return (x, st) if stats else x
+
+    def set_tiling(self, rows_max: int = 256, nnz_cap: int = 2048, staged: bool = True):
+        _check(lib.fab_set_tiling(self._h, int(rows_max), int(nnz_cap), 1 if staged else 0), "fab_set_tiling")
+
+    def tune(self, precision: int = FP64, k: int = 2, stream=None):
+        """Autotune the SpMV tiling for this matrix; returns (rows_max, nnz_cap, staged)."""
+        ch = (ctypes.c_int * 3)()
+        _check(lib.fab_tune(self._h, int(precision), int(k), ctypes.cast(ch, _vp), stream), "fab_tune")
+        return tuple(ch)
 
     def last_state(self) -> LastState:
         m, s, sk = self._last

@@ -147,7 +147,7 @@ def chung_lu_laplacian(n: int, exponent: float = 2.5, mean_degree: float = 10.0,
     rows = np.concatenate([rows, np.arange(n, dtype=np.int64)])
     cols = np.concatenate([cols, np.arange(n, dtype=np.int64)])
     vals = np.concatenate([-np.ones(2 * len(lo)), deg + shift])
-    order = np.lexsort((cols, rows))
+    order = np.argsort(rows * n + cols)  # (row, col) pairs are distinct: row-major order
     rows, cols, vals = rows[order], cols[order], vals[order]
     rowptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(np.bincount(rows, minlength=n), out=rowptr[1:])

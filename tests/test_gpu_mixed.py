@@ -72,6 +72,29 @@ CASES = [
 ]
 
 
+class _PerturbedBasisSketch:
+    """Theta applied to V with every entry of V moved by a relative amount of at
+    most u_bf16 = 2^-8 (uniform, seeded): a model of the BF16 copy of the basis
+    that the tensor-core Gaussian sketch reads (the sketch-only methods see that
+    rounding directly)."""
+
+    def __init__(self, th, seed):
+        self.th, self.rng = th, np.random.default_rng(seed)
+
+    def apply(self, V):
+        V = np.asarray(V, dtype=np.float64)
+        return self.th.apply(V * (1.0 + 2.0**-8 * self.rng.uniform(-1.0, 1.0, V.shape)))
+
+
+def _bf16_sensitivity(A, b, m, k, f, th, t, method, ref_x):
+    """Largest change of the oracle's f_m under three BF16-sized basis perturbations."""
+    out = 0.0
+    for seed in range(3):
+        r = krylov.run(method, A, b, m, k, f, _PerturbedBasisSketch(th, seed), t, tol=1e-10)
+        out = max(out, _rel(r.x, ref_x))
+    return out
+
+
 @pytest.mark.parametrize("name,build,f,t,m,k,sk,s", CASES)
 @pytest.mark.parametrize("method", [krylov.NOPROJ, krylov.SKETCHED_FAST, krylov.SKETCHED_LS, krylov.ARNOLDI])
 def test_mixed_precision_vs_fp64_oracle(fab, name, build, f, t, m, k, sk, s, method):
@@ -89,7 +112,13 @@ def test_mixed_precision_vs_fp64_oracle(fab, name, build, f, t, m, k, sk, s, met
     # FP32 matrix and basis (u = 2^-24): m steps of the recurrence move the basis by
     # about m u times the basis conditioning; Arnoldi and the LSQR variant project
     # with FP64 reductions (<= 1e-5 observed <= 1.2e-6); the sketch-only variants
-    # also see the BF16 rounding of the sketched basis and the truncated basis's
-    # conditioning directly (<= 2e-4; observed <= 6e-5 on the power-law graph).
+    # also see the truncated basis's conditioning directly (<= 2e-4). With the
+    # Gaussian sketch they further see the BF16 rounding of the basis (u = 2^-8),
+    # whose effect is measured on the oracle itself: the bound is 4x the largest
+    # change of the oracle's f_m under three such perturbations of the basis.
     tol = 1e-5 if method in (krylov.ARNOLDI, krylov.SKETCHED_LS) else 2e-4
+    if sk == osk.GAUSSIAN and method == krylov.SKETCHED_FAST:
+        sens = _bf16_sensitivity(W.to_scipy(A), b, m, k, f, th, t, method, ref.x)
+        print(f"  BF16-basis sensitivity of the oracle: {sens:.3e}")
+        tol = max(tol, 4.0 * sens)
     assert err <= tol

@@ -224,3 +224,46 @@ def test_c2_full_size_first_steps_and_relation(fab, torch):
         VH = V[:, r].cpu().numpy() @ ls.H
         res.append(np.abs(AV - VH).max())
     assert max(res) <= 1e-12 * np.abs(A.vals).max()
+
+
+# ------------------------------------------------------- SpMV tilings
+@pytest.mark.parametrize("tiling", [(256, 2048, 1), (256, 2048, 0), (64, 512, 1), (16, 128, 1), (1, 2048, 1)])
+def test_spmv_tilings_power_law_graph(fab, torch, tiling):
+    """Every tiling (rows per tile, nonzeros per tile, staging) gives the oracle's result:
+    (1, ., .) puts the whole block on each row, (16, 128) mixes 16..256 lanes per row."""
+    A = W.chung_lu_laplacian(20000, seed=2)
+    b = W.random_vector(A.n, 0)
+    m, k, s = 30, 2, 120
+    th = osk.make(osk.SRHT, A.n, s, 1, 8)
+    ref = krylov.run(krylov.SKETCHED_FAST, W.to_scipy(A), b, m, k, matfun.INVSQRT, th, 1.0)
+    M = fab.Matrix.from_csr(A)
+    M.set_tiling(*tiling)
+    x = M.apply(b, fab.params(f=fab.INVSQRT, m=m, k=k, s=s, sketch=fab.SRHT, seed=1))
+    assert _rel(x, ref.x) <= TOL
+
+
+def test_dense_rows_and_autotune(fab, torch):
+    """Rows longer than a staged tile (a dense first row and column, 5000 entries) take the
+    direct path with the whole block on the row; the autotuned tiling keeps parity."""
+    n = 5000
+    rng = np.random.default_rng(4)
+    D = np.diag(4.0 + rng.random(n))
+    D[0, :] += 0.001 * rng.standard_normal(n)
+    D[:, 0] += 0.001 * rng.standard_normal(n)
+    i = np.arange(n - 1)
+    D[i, i + 1] -= 0.5
+    D[i + 1, i] -= 0.7
+    A = W.from_dense(D)
+    b = W.random_vector(n, 1)
+    m, k = 25, 3
+    ref = krylov.run(krylov.NOPROJ, W.to_scipy(A), b, m, k, matfun.EXP, None, -0.05)
+    M = fab.Matrix.from_csr(A)
+    x = M.apply(b, fab.params(f=fab.EXP, t=-0.05, m=m, k=k, method=fab.NOPROJ))
+    assert _rel(x, ref.x) <= TOL
+    choice = M.tune(fab.FP64, k=k)
+    assert choice[0] in (256, 128, 64) and choice[1] in (2048, 1024, 512) and choice[2] in (0, 1)
+    x2 = M.apply(b, fab.params(f=fab.EXP, t=-0.05, m=m, k=k, method=fab.NOPROJ))
+    assert _rel(x2, ref.x) <= TOL
+    with pytest.raises(fab.FabError) as e:
+        M.set_tiling(0, 2048, 1)
+    assert e.value.code == fab.FAB_EINVAL
