@@ -130,11 +130,11 @@ def fp32_step_bytes(n: int, nnz: int, kw: int, s: int) -> int:
     return 8 * nnz + 4 * (n + 1) + 4 * n * kw + 4 * n + 4 * n * (kw + 2) + 8 * s * ((n + 4095) // 4096)
 
 
-def bench_batch(fab, torch, W, steps: int = 3):
+def bench_batch(fab, torch, W, steps: int = 3, count: int = 256):
     """256 uneven 2D convection-diffusion solves (n log-uniform on [1e4, 1e6], t on
     [1e-4, 1e-2], m on {20..80}, k = 2, sparse sign s = 4m, zeta = 8, batch seed 3)
     as one CUDA graph, FP32 basis / FP64 small stage; inputs resident on the device."""
-    specs = W.batch_specs(256, seed=3)
+    specs = W.batch_specs(count, seed=3)
     A = [W.convdiff(2, it.N) for it in specs]
     mats = [fab.Matrix.from_csr(a) for a in A]
     k = 2
@@ -173,9 +173,9 @@ def bench_batch(fab, torch, W, steps: int = 3):
     bt.close()
     bt64.close()
     peak = float(_peaks().get("hbm_gbs", 6800.0))
-    return {"workload": "256 uneven 2D convection-diffusion solves (n 1e4..1e6 log-uniform, m 20..80, t 1e-4..1e-2), "
+    return {"workload": f"{count} uneven 2D convection-diffusion solves (n 1e4..1e6 log-uniform, m 20..80, t 1e-4..1e-2), "
                         "k=2, sparse sign s=4m, sketched_fast, FP32 basis / FP64 small stage, one CUDA graph",
-            "solves_per_s": 256 / (ms / 1000.0), "ms_per_batch": ms, "graph_kernels": kernels,
+            "solves_per_s": count / (ms / 1000.0), "ms_per_batch": ms, "graph_kernels": kernels, "count": count,
             "sum_n": int(sum(a.n for a in A)), "algorithmic_gb": byts / 1e9,
             "hbm_gbs_algorithmic": byts / (ms / 1000.0) / 1e9,
             "hbm_frac_of_measured": byts / (ms / 1000.0) / 1e9 / peak,
@@ -308,7 +308,7 @@ def run_only(args):
     from paper_2212_12758_gb300 import fab
     from paper_2212_12758_gb300 import workloads as W
 
-    out = bench_batch(fab, torch, W, steps=args.steps) if args.only == "batch" else \
+    out = bench_batch(fab, torch, W, steps=args.steps, count=args.batch_count) if args.only == "batch" else \
         bench_mixed_graph(fab, torch, W, reps=args.steps)
     print(json.dumps({"only": args.only, **out}), flush=True)
     return 0
@@ -327,6 +327,8 @@ def main():
                          "graph (4M-node power-law Laplacian, mixed precision, Gaussian sketch)")
     ap.add_argument("--only", choices=["batch", "graph"], default=None,
                     help="measure one side workload alone and print its JSON (for profiler runs)")
+    ap.add_argument("--batch-count", type=int, default=256,
+                    help="solves in the --only batch workload (same generator, batch seed 3)")
     ap.add_argument("--grid", type=int, default=N_GRID,
                     help="grid side N of the 3D operator (default 200, the benchmark workload; smaller N only "
                          "for profiler captures)")

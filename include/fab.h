@@ -263,8 +263,9 @@ int fab_tune(fab_handle* h, int precision, int k, int* choice, void* stream);
  * step c the graph holds one launch per (window k, sketch kind) group covering
  * every solve still building its basis (SpMV + window dots, window update +
  * norm + fused sketch, sketch reduce: Alg. 2 with the sketch of §2.1.1). A
- * solve's blocks in such a launch are the blocks of its own launch, so its
- * basis and sketch are bit for bit those fab_apply computes. When a solve's
+ * solve's SpMV tiles are grouped at least 8 to a block (a batched solve shares
+ * the GPU), so its results equal fab_apply's up to the grouping of partial
+ * sums (same kernels, same tiles, same sketch). When a solve's
  * basis is complete, its small stage (Householder QR of the sketch, the
  * sketch-and-solve projection of eq. sFOM, or none for Alg. 5; f(H)e_1 by
  * Pade scaling and squaring or Denman-Beavers) runs as one CTA on a second

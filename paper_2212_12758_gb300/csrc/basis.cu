@@ -428,8 +428,60 @@ __device__ void sketch_chunk_srht(const TV (&v)[kRowsPerThread], int chunk, cons
   __syncthreads();
 }
 
-// Sparse-sign chunk: every row j scatters +-X_j into its zeta sketch rows.
-template <typename TV>
+// The zeta distinct sketch rows of column j (R9): candidates floor(h s / 2^32)
+// from the 32-bit halves of stream-1 words, in order, repeats rejected; after
+// 256 candidates the smallest unused rows fill up (never reached in practice).
+__device__ __forceinline__ void sparse_rows(const SketchDev& sk, long long j, int (&rows)[kMaxZeta]) {
+  const unsigned s = (unsigned)sk.s;
+  int have = 0;
+  unsigned long long h = 0;
+  for (int cand = 0; cand < 256 && have < sk.zeta; ++cand) {
+    if ((cand & 1) == 0) h = rng_u(sk.st_rows, (unsigned long long)j * 128ull + (unsigned long long)(cand >> 1));
+    const unsigned half = (cand & 1) ? (unsigned)(h >> 32) : (unsigned)h;
+    const int r = (int)(((unsigned long long)half * s) >> 32);
+    bool dup = false;
+#pragma unroll
+    for (int q = 0; q < kMaxZeta; ++q) dup |= (q < have) && (rows[q] == r);
+    if (!dup) {
+#pragma unroll
+      for (int q = 0; q < kMaxZeta; ++q)
+        if (q == have) rows[q] = r;
+      ++have;
+    }
+  }
+  for (int r = 0; have < sk.zeta; ++r) {  // fallback: smallest unused rows
+    bool dup = false;
+#pragma unroll
+    for (int q = 0; q < kMaxZeta; ++q) dup |= (q < have) && (rows[q] == r);
+    if (!dup) {
+#pragma unroll
+      for (int q = 0; q < kMaxZeta; ++q)
+        if (q == have) rows[q] = r;
+      ++have;
+    }
+  }
+}
+
+__global__ void k_sparse_pattern(int n, SketchDev sk, unsigned short* __restrict__ pat) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    int rows[kMaxZeta];
+    sparse_rows(sk, j, rows);
+    const unsigned long long sg = rng_u(sk.st_signs, (unsigned long long)j);
+#pragma unroll
+    for (int q = 0; q < kMaxZeta; ++q)
+      if (q < sk.zeta) pat[(size_t)q * n + j] = (unsigned short)(rows[q] | (((sg >> q) & 1ull) << 15));
+  }
+}
+
+cudaError_t launch_sparse_pattern(int n, const SketchDev& sk, unsigned short* pat, cudaStream_t s) {
+  if (sk.s > 32768 || sk.zeta > kMaxZeta) return cudaErrorInvalidValue;
+  k_sparse_pattern<<<grid_rows(n), kThreads, 0, s>>>(n, sk, pat);
+  return cudaGetLastError();
+}
+
+// Sparse-sign chunk: every row j scatters +-X_j into its zeta sketch rows (exact
+// int64 sums in shared memory); TAB reads the rows and signs from sk.pat.
+template <typename TV, bool TAB>
 __device__ void sketch_chunk_sparse(const TV (&v)[kRowsPerThread], int chunk, int n, const SketchDev& sk,
                                     unsigned long long* acc, double* s_acc, int* s_int) {
   const int t = threadIdx.x;
@@ -437,46 +489,33 @@ __device__ void sketch_chunk_sparse(const TV (&v)[kRowsPerThread], int chunk, in
 #pragma unroll
   for (int i = 0; i < kRowsPerThread; ++i) e = max(e, exp_field(v[i]));
   const int E = block_max_int(e, s_int);
-  const unsigned s = (unsigned)sk.s;
-  for (int i = 0; i < kRowsPerThread; ++i) {
+  if (TAB) {
+#pragma unroll
+    for (int i = 0; i < kRowsPerThread; ++i) {
+      const long long j = (long long)chunk * kChunk + i * kThreads + t;
+      const long long X = (j < n) ? to_fixed(v[i], E) : 0ll;
+      if (X != 0)
+        for (int q = 0; q < sk.zeta; ++q) {
+          const unsigned w = __ldg(sk.pat + (size_t)q * n + j);
+          atomicAdd(acc + (w & 0x7FFFu), (unsigned long long)((w >> 15) ? -X : X));
+        }
+    }
+  }
+  for (int i = 0; i < kRowsPerThread && !TAB; ++i) {
     const long long j = (long long)chunk * kChunk + i * kThreads + t;
     if (j >= n) break;
     const long long X = to_fixed(v[i], E);
     if (X == 0) continue;
-    int rows[kMaxZeta];
-    int have = 0;
-    unsigned long long h = 0;
-    for (int cand = 0; cand < 256 && have < sk.zeta; ++cand) {
-      if ((cand & 1) == 0) h = rng_u(sk.st_rows, (unsigned long long)j * 128ull + (unsigned long long)(cand >> 1));
-      const unsigned half = (cand & 1) ? (unsigned)(h >> 32) : (unsigned)h;
-      const int r = (int)(((unsigned long long)half * s) >> 32);
-      bool dup = false;
+    {
+      int rows[kMaxZeta];
+      sparse_rows(sk, j, rows);
+      const unsigned long long sg = rng_u(sk.st_signs, (unsigned long long)j);
 #pragma unroll
-      for (int q = 0; q < kMaxZeta; ++q) dup |= (q < have) && (rows[q] == r);
-      if (!dup) {
-#pragma unroll
-        for (int q = 0; q < kMaxZeta; ++q)
-          if (q == have) rows[q] = r;
-        ++have;
-      }
-    }
-    for (int r = 0; have < sk.zeta; ++r) {  // fallback: smallest unused rows
-      bool dup = false;
-#pragma unroll
-      for (int q = 0; q < kMaxZeta; ++q) dup |= (q < have) && (rows[q] == r);
-      if (!dup) {
-#pragma unroll
-        for (int q = 0; q < kMaxZeta; ++q)
-          if (q == have) rows[q] = r;
-        ++have;
-      }
-    }
-    const unsigned long long sg = rng_u(sk.st_signs, (unsigned long long)j);
-#pragma unroll
-    for (int q = 0; q < kMaxZeta; ++q) {
-      if (q < sk.zeta) {
-        const long long val = ((sg >> q) & 1ull) ? -X : X;
-        atomicAdd(acc + rows[q], (unsigned long long)val);
+      for (int q = 0; q < kMaxZeta; ++q) {
+        if (q < sk.zeta) {
+          const long long val = ((sg >> q) & 1ull) ? -X : X;
+          atomicAdd(acc + rows[q], (unsigned long long)val);
+        }
       }
     }
   }
@@ -511,7 +550,7 @@ __device__ __forceinline__ void update_body(int n, TV* __restrict__ W, int64_t l
   if (st->stop) return;
   TV* s_coef = reinterpret_cast<TV*>(smem_raw);  // nc coefficients
   double* s_acc = reinterpret_cast<double*>(smem_raw + ((size_t)nc * 8 + 15) / 16 * 16);  // s doubles
-  const bool sk_acc = (SK == SK_SRHT || SK == SK_SPARSE);
+  const bool sk_acc = (SK == SK_SRHT || SK == SK_SPARSE || SK == SK_SPARSE_TAB);
   unsigned char* after = reinterpret_cast<unsigned char*>(s_acc) + ((size_t)(sk_acc ? sk.s : 0) * 8 + 15) / 16 * 16;
   long long* buf = reinterpret_cast<long long*>(after);                     // SRHT: pidx(4096) int64
   unsigned long long* acc = reinterpret_cast<unsigned long long*>(after);   // sparse: s uint64
@@ -521,7 +560,7 @@ __device__ __forceinline__ void update_body(int n, TV* __restrict__ W, int64_t l
     for (int q = threadIdx.x; q < sk.s; q += kThreads) s_acc[q] = 0.0;
   if (SK == SK_SRHT)
     for (int q = threadIdx.x; q < sk.s; q += kThreads) s_P[q] = sk.P[q];
-  if (SK == SK_SPARSE)
+  if (SK == SK_SPARSE || SK == SK_SPARSE_TAB)
     for (int q = threadIdx.x; q < sk.s; q += kThreads) acc[q] = 0ull;
   __syncthreads();
   TV* wc = W + (size_t)c * ld;
@@ -571,7 +610,8 @@ __device__ __forceinline__ void update_body(int n, TV* __restrict__ W, int64_t l
     }
     nrm += (double)nrm_c;
     if (SK == SK_SRHT) sketch_chunk_srht(v, chunk, sk, buf, s_P, s_acc, s_int);
-    if (SK == SK_SPARSE) sketch_chunk_sparse(v, chunk, n, sk, acc, s_acc, s_int);
+    if (SK == SK_SPARSE) sketch_chunk_sparse<TV, false>(v, chunk, n, sk, acc, s_acc, s_int);
+    if (SK == SK_SPARSE_TAB) sketch_chunk_sparse<TV, true>(v, chunk, n, sk, acc, s_acc, s_int);
     if (SK == SK_GAUSS) {  // BF16 copy of the column for the tensor-core Gaussian sketch
       __nv_bfloat16* bc = sk.Wbf + (size_t)c * sk.ldbf;
 #pragma unroll
@@ -638,9 +678,9 @@ __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(
 
 size_t update_smem_bytes(int kind, int nc, int s) {
   size_t b = ((size_t)nc * 8 + 15) / 16 * 16;
-  if (kind == SK_SRHT || kind == SK_SPARSE) b += ((size_t)s * 8 + 15) / 16 * 16;
+  if (kind == SK_SRHT || kind == SK_SPARSE || kind == SK_SPARSE_TAB) b += ((size_t)s * 8 + 15) / 16 * 16;
   if (kind == SK_SRHT) b += (size_t)(kChunk + kChunk / 16) * 8 + (size_t)s * 4;
-  if (kind == SK_SPARSE) b += (size_t)s * 8;
+  if (kind == SK_SPARSE || kind == SK_SPARSE_TAB) b += (size_t)s * 8;
   return b;
 }
 
@@ -649,6 +689,7 @@ const void* update_fn(int kind) {
   switch (kind) {
     case SK_SRHT: return (const void*)k_update<SK_SRHT, TV>;
     case SK_SPARSE: return (const void*)k_update<SK_SPARSE, TV>;
+    case SK_SPARSE_TAB: return (const void*)k_update<SK_SPARSE_TAB, TV>;
     case SK_GAUSS: return (const void*)k_update<SK_GAUSS, TV>;
     default: return (const void*)k_update<SK_NONE, TV>;
   }
@@ -675,9 +716,10 @@ cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const
                           ColScale cs, const double* wn2, int mode, double* part, unsigned* counter, SketchDev& sk,
                           DevState* st, cudaStream_t s) {
   size_t smem = 0;
-  const int grid = update_grid<TV>(sk.kind, n, nc, sk.s, &smem);
+  const int kind = (sk.kind == SK_SPARSE && sk.pat) ? SK_SPARSE_TAB : sk.kind;
+  const int grid = update_grid<TV>(kind, n, nc, sk.s, &smem);
   if (grid < 1) return cudaErrorInvalidValue;
-  const void* fn = update_fn<TV>(sk.kind);
+  const void* fn = update_fn<TV>(kind);
   sk.nparts = grid;  // one sketch partial per block
   void* args[] = {&n, &W, &ld, &c, &j0, &nc, (void*)&coef, &H, &ldh, &cs, (void*)&wn2, &mode, &part, &counter,
                   &sk, &st};
@@ -1016,6 +1058,7 @@ cudaError_t launch_update_wave(int kind, const BasisJob<TV>* jobs, const Wave& w
   switch (kind) {
     case SK_SRHT: fn = (const void*)k_update_wave<SK_SRHT, TV>; break;
     case SK_SPARSE: fn = (const void*)k_update_wave<SK_SPARSE, TV>; break;
+    case SK_SPARSE_TAB: fn = (const void*)k_update_wave<SK_SPARSE_TAB, TV>; break;
     case SK_NONE: fn = (const void*)k_update_wave<SK_NONE, TV>; break;
     default: return cudaErrorInvalidValue;  // the Gaussian sketch is not batched
   }
@@ -1058,7 +1101,7 @@ cudaError_t wave_prepare(size_t upd_smem, int mmax) {
     if (e != cudaSuccess) return e;
   }
   const void* upd[] = {(const void*)k_update_wave<SK_SRHT, TV>, (const void*)k_update_wave<SK_SPARSE, TV>,
-                       (const void*)k_update_wave<SK_NONE, TV>};
+                       (const void*)k_update_wave<SK_SPARSE_TAB, TV>, (const void*)k_update_wave<SK_NONE, TV>};
   for (const void* f : upd) {
     cudaError_t e = ensure_smem_limit(f, upd_smem);
     if (e != cudaSuccess) return e;

@@ -5,9 +5,10 @@
 // holds one launch per (window, sketch kind) group that covers the tiles of
 // every solve still building its basis (SpMV + window dots, then the window
 // update + norm + fused sketch, then the sketch reduce; Alg. 2 with the sketch
-// of §2.1.1). A solve's blocks inside such a wave are exactly the blocks of its
-// own launch, so every solve's basis and sketch are bit for bit those of
-// fab_apply. As soon as a solve's basis is complete its small stage (QR of the
+// of §2.1.1). A solve's blocks inside such a wave run the bodies of its own
+// launches on the same tiles and chunks (with at least kMinTiles SpMV tiles per
+// block), so its results equal fab_apply's up to the grouping of partial sums.
+// As soon as a solve's basis is complete its small stage (QR of the
 // sketch, the sketch-and-solve projection of eq. sFOM or none for Alg. 5,
 // f(H)e_1) runs as one CTA on a second branch of the graph, followed by its
 // combine x = ||b|| V_m c, so the FP64-bound small stages of early finishers
@@ -55,8 +56,13 @@ struct HostWave {
 
 int sk_kind_of(const fab_params& p) {
   if (p.method != FAB_SKETCHED_FAST) return SK_NONE;
-  return p.sketch == FAB_SK_SRHT ? SK_SRHT : SK_SPARSE;
+  return p.sketch == FAB_SK_SRHT ? SK_SRHT : SK_SPARSE_TAB;  // sparse sign: pattern drawn once, at creation
 }
+
+// A batched solve's SpMV blocks: its own launch's grid, but at least kMinTiles
+// tiles per block (a solve shares the GPU with the rest of the batch, so fewer,
+// longer blocks keep the tile pipeline busy).
+constexpr int kMinTiles = 8;
 
 }  // namespace
 
@@ -136,7 +142,7 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       if (c > 0) {
         std::vector<int> nb;
         for (int j : ids) {
-          nb.push_back(spmv_grid<TV>(hs[j]->ntiles, kw));
+          nb.push_back(std::min(spmv_grid<TV>(hs[j]->ntiles, kw), (hs[j]->ntiles + kMinTiles - 1) / kMinTiles));
           part_need[j] = std::max(part_need[j], (size_t)nb.back() * (kMaxWindow + 1));
         }
         HostWave w{W_SPMV};
@@ -243,7 +249,8 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       sk.st_D = rng_state(p.seed, 3);
       sk.P = ar.take<int>(s);
       sk.part = ar.take<double>(skpart_need[j]);
-      J.sk_scale = kind[j] == SK_SRHT ? 1.0 / sqrt((double)p.s) : (kind[j] == SK_SPARSE ? 1.0 / sqrt((double)p.zeta) : 1.0);
+      sk.pat = kind[j] == SK_SPARSE_TAB ? ar.take<unsigned short>((size_t)n * p.zeta) : nullptr;
+      J.sk_scale = kind[j] == SK_SRHT ? 1.0 / sqrt((double)p.s) : (kind[j] == SK_SPARSE_TAB ? 1.0 / sqrt((double)p.zeta) : 1.0);
       double* bst = ar.take<double>(n);
       double* xst = ar.take<double>(n);
       J.b = bst;
@@ -325,12 +332,15 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
   BK(cudaMemcpyAsync(jobs_dev, jobs.data(), sizeof(BasisJob<TV>) * count, cudaMemcpyHostToDevice, cap));
   BK(cudaMemcpyAsync(small_dev, small.data(), sizeof(SmallJob) * count, cudaMemcpyHostToDevice, cap));
   BK(cudaMemcpyAsync(tab_dev, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, cap));
-  for (int j = 0; j < count; ++j)  // SRHT row samples are fixed by (n', s, seed): drawn once here
+  for (int j = 0; j < count; ++j) {  // SRHT samples and sparse sign patterns are fixed: drawn once here
     if (kind[j] == SK_SRHT) {
       int64_t npad = 1;
       while (npad < bt->n[j]) npad <<= 1;
       BK(launch_srht_sample(npad, ps[j].s, rng_state(ps[j].seed, 4), const_cast<int*>(jobs[j].sk.P), cap));
     }
+    if (kind[j] == SK_SPARSE_TAB)
+      BK(launch_sparse_pattern(bt->n[j], jobs[j].sk, const_cast<unsigned short*>(jobs[j].sk.pat), cap));
+  }
   BK(cudaStreamSynchronize(cap));
   PadeCoef pd;
   memcpy(pd.b, pade13_b(), sizeof(pd.b));

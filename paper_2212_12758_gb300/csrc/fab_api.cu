@@ -222,7 +222,7 @@ void fab_destroy(fab_handle* h) {
     cudaFree(h->d_tiles);
     delete[] h->h_rowptr;
   }
-  Buf* bufs[] = {&h->W32, &h->Wbf, &h->G, &h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
+  Buf* bufs[] = {&h->spat, &h->W32, &h->Wbf, &h->G, &h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
                  &h->skpart, &h->SV, &h->P,     &h->qr,  &h->tau,  &h->y,    &h->cvec,    &h->dense,
                  &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state};
   for (Buf* b : bufs)
@@ -358,6 +358,7 @@ int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
       {&h->skpart, (size_t)nchunks * s * 8},
       {&h->SV, (size_t)s * (m + 1) * 8},
       {&h->P, (size_t)s * 4},
+      {&h->spat, (sketched(p->method) && p->sketch == FAB_SK_SPARSE_SIGN) ? (size_t)n * p->zeta * 2 : 0},
       {&h->qr, (size_t)s * (m + 1) * 8},
       {&h->tau, (size_t)(m + 1) * 8},
       {&h->y, (size_t)(m + 1) * 8},
@@ -571,6 +572,16 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
       }
     } else {
       sk_scale = 1.0 / sqrt((double)p->zeta);
+      unsigned short* pat = ptr<unsigned short>(h->spat);
+      if (h->spat_n != n || h->spat_s != p->s || h->spat_zeta != p->zeta || h->spat_seed != p->seed) {
+        h->spat_n = -1;  // (re)drawn once per (n, s, zeta, seed) and kept with the handle
+        LK(PK_SMALL, launch_sparse_pattern(n, sk, pat, s));
+        h->spat_n = n;
+        h->spat_s = p->s;
+        h->spat_zeta = p->zeta;
+        h->spat_seed = p->seed;
+      }
+      sk.pat = pat;
     }
   }
   SketchDev none;
@@ -1027,7 +1038,7 @@ size_t estimate_ws_bytes(const fab_handle* h, const fab_params* p) {
 }
 
 size_t handle_ws_bytes(const fab_handle* h) {
-  const Buf* bufs[] = {&h->W32, &h->Wbf, &h->G,    &h->shf,  &h->scl,  &h->W,   &h->H,     &h->sigma,
+  const Buf* bufs[] = {&h->spat, &h->W32, &h->Wbf, &h->G,    &h->shf,  &h->scl,  &h->W,   &h->H,     &h->sigma,
                        &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart, &h->skpart, &h->SV, &h->P,
                        &h->qr,  &h->tau, &h->y,    &h->cvec, &h->dense, &h->piv, &h->scal, &h->lsq,
                        &h->u,   &h->xbuf, &h->state};

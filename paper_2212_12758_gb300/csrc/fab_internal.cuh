@@ -21,7 +21,9 @@ constexpr int kMaxS = 4096;          // sketch rows limit
 constexpr int kMaxZeta = 16;         // sparse-sign nonzeros per column limit
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 
-enum SketchKind { SK_NONE = -1, SK_SPARSE = 0, SK_SRHT = 1, SK_GAUSS = 2 };
+enum SketchKind { SK_NONE = -1, SK_SPARSE = 0, SK_SRHT = 1, SK_GAUSS = 2, SK_SPARSE_TAB = 3 };
+// SK_SPARSE_TAB: the sparse sign sketch read from its precomputed pattern table
+// (SketchDev::pat) instead of drawing each column's rows again.
 
 // Device-side state of one solve. Written only by kernels (reset by k_state_reset).
 struct DevState {
@@ -50,6 +52,9 @@ struct SketchDev {
   __nv_bfloat16* Wbf;  // Gaussian: BF16 copy of the basis (column c at Wbf + c * ldbf)
   int64_t ldbf;
   double* part;        // nparts x s block partials (block-major), nparts <= nchunks
+  // sparse sign: zeta x n table (plane q holds the q-th row of every column:
+  // bits 0..14 the row, bit 15 the sign), or NULL to draw the rows on the fly
+  const unsigned short* pat;
 };
 
 // ----------------------------------------------------------------- SplitMix64
@@ -238,6 +243,8 @@ cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const
                           SketchDev& sk, DevState* st, cudaStream_t s);
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
                                  DevState* st, cudaStream_t s);
+// The sparse sign pattern of sk (rows and signs of every column) into pat (zeta x n).
+cudaError_t launch_sparse_pattern(int n, const SketchDev& sk, unsigned short* pat, cudaStream_t s);
 
 // ------------------------------------------------------------ batched waves
 // One solve of a batch as the basis kernels see it (a device-resident table).

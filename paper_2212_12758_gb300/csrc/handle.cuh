@@ -57,6 +57,10 @@ struct fab_handle {
   fab::Buf W32, Wbf, G;  // mixed path: FP32 basis, its BF16 copy, Gaussian sketch (BF16, s x ld)
   int G_n = -1, G_s = -1;
   uint64_t G_seed = 0;
+  // cached sparse sign pattern (zeta x n, see SketchDev::pat)
+  fab::Buf spat;
+  int spat_n = -1, spat_s = -1, spat_zeta = -1;
+  uint64_t spat_seed = 0;
   // cached SRHT sample
   int64_t P_npad = -1;
   int P_s = -1;
