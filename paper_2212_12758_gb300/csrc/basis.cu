@@ -463,13 +463,14 @@ __device__ __forceinline__ void sparse_rows(const SketchDev& sk, long long j, in
 }
 
 __global__ void k_sparse_pattern(int n, SketchDev sk, unsigned short* __restrict__ pat) {
+  const int Z = pat_stride(sk.zeta);
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
     int rows[kMaxZeta];
     sparse_rows(sk, j, rows);
     const unsigned long long sg = rng_u(sk.st_signs, (unsigned long long)j);
 #pragma unroll
     for (int q = 0; q < kMaxZeta; ++q)
-      if (q < sk.zeta) pat[(size_t)q * n + j] = (unsigned short)(rows[q] | (((sg >> q) & 1ull) << 15));
+      if (q < Z) pat[(size_t)j * Z + q] = q < sk.zeta ? (unsigned short)(rows[q] | (((sg >> q) & 1ull) << 15)) : 0;
   }
 }
 
@@ -490,15 +491,26 @@ __device__ void sketch_chunk_sparse(const TV (&v)[kRowsPerThread], int chunk, in
   for (int i = 0; i < kRowsPerThread; ++i) e = max(e, exp_field(v[i]));
   const int E = block_max_int(e, s_int);
   if (TAB) {
+    // a column's entries are one (zeta <= 8) or two 16-byte vector loads
 #pragma unroll
     for (int i = 0; i < kRowsPerThread; ++i) {
       const long long j = (long long)chunk * kChunk + i * kThreads + t;
       const long long X = (j < n) ? to_fixed(v[i], E) : 0ll;
-      if (X != 0)
-        for (int q = 0; q < sk.zeta; ++q) {
-          const unsigned w = __ldg(sk.pat + (size_t)q * n + j);
-          atomicAdd(acc + (w & 0x7FFFu), (unsigned long long)((w >> 15) ? -X : X));
+      if (X != 0) {
+        const int Z = pat_stride(sk.zeta);
+        const uint4* src = reinterpret_cast<const uint4*>(sk.pat + (size_t)j * Z);
+        for (int h = 0; h < Z / 8; ++h) {
+          const uint4 a = __ldg(src + h);
+          const unsigned wv[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (h * 8 + q < sk.zeta) {
+              const unsigned w = (wv[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu;
+              atomicAdd(acc + (w & 0x7FFFu), (unsigned long long)((w >> 15) ? -X : X));
+            }
+          }
         }
+      }
     }
   }
   for (int i = 0; i < kRowsPerThread && !TAB; ++i) {

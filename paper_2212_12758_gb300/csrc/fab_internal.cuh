@@ -52,10 +52,12 @@ struct SketchDev {
   __nv_bfloat16* Wbf;  // Gaussian: BF16 copy of the basis (column c at Wbf + c * ldbf)
   int64_t ldbf;
   double* part;        // nparts x s block partials (block-major), nparts <= nchunks
-  // sparse sign: zeta x n table (plane q holds the q-th row of every column:
-  // bits 0..14 the row, bit 15 the sign), or NULL to draw the rows on the fly
+  // sparse sign: column j's entries at pat[j Z .. j Z + zeta - 1], Z = pat_stride(zeta)
+  // (bits 0..14 the row, bit 15 the sign), or NULL to draw the rows on the fly
   const unsigned short* pat;
 };
+// Entries per column of the sparse sign table: 8 (zeta <= 8) or 16 (16-byte aligned rows).
+__host__ __device__ __forceinline__ int pat_stride(int zeta) { return zeta <= 8 ? 8 : 16; }
 
 // ----------------------------------------------------------------- SplitMix64
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -243,7 +245,7 @@ cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const
                           SketchDev& sk, DevState* st, cudaStream_t s);
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
                                  DevState* st, cudaStream_t s);
-// The sparse sign pattern of sk (rows and signs of every column) into pat (zeta x n).
+// The sparse sign pattern of sk (rows and signs of every column) into pat (n x pat_stride(zeta)).
 cudaError_t launch_sparse_pattern(int n, const SketchDev& sk, unsigned short* pat, cudaStream_t s);
 
 // ------------------------------------------------------------ batched waves
