@@ -79,6 +79,15 @@ typedef struct fab_params {
   double lsqr_tol;   /* LSQR stopping tolerance (paper §5 uses 1e-6)               */
   int lsqr_maxit;    /* LSQR iteration limit (0: 4m)                               */
   void* stream;      /* cudaStream_t to run on, or NULL                            */
+  /* Growing m to a target accuracy (0 = off, the fixed m above). The basis is */
+  /* extended by m_step columns at a time, up to m_max, until the sketched    */
+  /* relative change ||Theta V (c_m - c_{m-step})|| / ||Theta V c_m|| of two  */
+  /* successive solutions is at most target_rel_err (the sketch embeds x_m -  */
+  /* x_{m-step}, §2.1.1). Sketched methods only; s >= m_max + 1. If m_max is  */
+  /* reached first the call returns FAB_ENOTCONV with the m_max solution in x. */
+  double target_rel_err;
+  int m_step;
+  int m_max;
 } fab_params;
 
 /* Diagnostics of the last solve (all optional for the caller). */
@@ -93,6 +102,7 @@ typedef struct fab_stats {
   double ms_small;      /* device time of QR / LSQR / f(H)                       */
   double ms_combine;    /* device time of x = ||b|| V_m c                        */
   double ms_total;      /* device time of the whole solve                        */
+  double err_est;       /* last sketched relative change (target mode), else 0   */
 } fab_stats;
 
 typedef struct fab_handle fab_handle;
@@ -276,7 +286,8 @@ int fab_tune(fab_handle* h, int precision, int k, int* choice, void* stream);
  *                   does not fit), then captures and instantiates the graph.
  *                   Supported: method FAB_SKETCHED_FAST (sketch SRHT or sparse
  *                   sign) or FAB_NOPROJ; precision the same for all solves
- *                   (FAB_FP64 or FAB_MIXED); anything else FAB_EINVAL. A
+ *                   (FAB_FP64 or FAB_MIXED); fixed m (target_rel_err = 0);
+ *                   anything else FAB_EINVAL. A
  *                   handle may appear several times; handles must outlive the
  *                   batch and must not be destroyed or used concurrently while
  *                   it runs. ps[0].stream is used for set-up.

@@ -61,6 +61,13 @@ cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+__global__ void k_state_set_m(DevState* st, int m) { st->m_used = m; }
+
+cudaError_t launch_state_set_m(DevState* st, int m, cudaStream_t s) {
+  k_state_set_m<<<1, 1, 0, s>>>(st, m);
+  return cudaGetLastError();
+}
+
 // --------------------------------------------- SpMV + window dot products
 // W_c = 2^shf[c-1] A W_{c-1} is written to column c (an exact power-of-two rescale
 // done on the exponent bits keeps the raw columns near unit norm without FP64

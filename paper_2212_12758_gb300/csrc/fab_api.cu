@@ -313,8 +313,17 @@ int validate(const fab_handle* h, const fab_params* p) {
     }
     if (p->method == FAB_SKETCHED_LS && !(p->lsqr_tol > 0.0)) return FAB_EINVAL;
   }
+  if (p->target_rel_err != 0.0) {  // growing m to a target: sketched methods, s embeds m_max + 1 columns
+    if (!(p->target_rel_err > 0.0) || !sketched(p->method) || p->m_step < 1 || p->m_max < p->m ||
+        p->m_max > kMaxM || p->s < p->m_max + 1)
+      return FAB_EINVAL;
+    if (p->sketch == FAB_SK_GAUSSIAN && p->m_max + 1 > kGaussMaxCols) return FAB_EINVAL;
+  }
   return FAB_OK;
 }
+
+// Largest Krylov dimension a solve may reach (workspace sizing).
+int m_cap(const fab_params* p) { return p->target_rel_err > 0.0 ? p->m_max : p->m; }
 
 struct Ws {
   ColScale cs;
@@ -335,7 +344,7 @@ struct Need {
 
 // The workspace a solve needs (buffer, bytes), shared by allocation and admission.
 int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
-  const int m = p->m, s = sketched(p->method) ? p->s : 1;
+  const int m = m_cap(p), s = sketched(p->method) ? p->s : 1;
   const int n = h->n;
   const size_t ld = (size_t)h->ld;
   const int ntiles = (n + kTileRows - 1) / kTileRows;
@@ -362,7 +371,7 @@ int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
       {&h->qr, (size_t)s * (m + 1) * 8},
       {&h->tau, (size_t)(m + 1) * 8},
       {&h->y, (size_t)(m + 1) * 8},
-      {&h->cvec, (size_t)(m + 1) * 8},
+      {&h->cvec, (size_t)2 * (m + 1) * 8},  // c and, growing m, the previous c
       {&h->dense, (size_t)9 * m * m * 8},
       {&h->piv, (size_t)(m + 1) * 4},
       {&h->scal, 64 * 8},
@@ -380,7 +389,7 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
   Need need[64];
   const int cnt = ws_needs(h, p, need);
   const int n = h->n;
-  const int m = p->m;
+  const int m = m_cap(p);
   for (int i = 0; i < cnt; ++i) {
     auto& q = need[i];
     if (q.bytes == 0 && (q.b == &h->u || q.b == &h->xbuf)) continue;  // allocated on demand
@@ -505,9 +514,12 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
       (p->sketch == FAB_SK_GAUSSIAN && sketched(p->method) && (!ws.Wbf || !ws.G)) ||
       (p->method == FAB_SKETCHED_LS && !ws.u))
     return FAB_ENOMEM;
-  const int n = h->n, m = p->m, k = p->k;
+  const int n = h->n, k = p->k;
+  const int mcap = m_cap(p);   // largest dimension this solve may grow to
+  const bool grow = p->target_rel_err > 0.0;
+  int m = p->m;                // current dimension
   const int64_t ld = h->ld;
-  const int ldh = m + 1;
+  const int ldh = mcap + 1;
   const bool sk_on = sketched(p->method);
   const int* mdev = &ws.st->m_used;
   Csr A{h->n, h->nnz, h->d_rowptr, h->d_colind, vals, h->d_tiles, h->ntiles, h->tile_staged};
@@ -527,8 +539,8 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   CK(cudaEventRecord(ev[0], s));
   LK(PK_SMALL, launch_state_reset(ws.st, m, s));
   CK(cudaMemsetAsync(ws.counter, 0, 64, s));
-  CK(cudaMemsetAsync(ws.H, 0, (size_t)ldh * m * sizeof(double), s));
-  CK(cudaMemsetAsync(ws.y, 0, (size_t)(m + 1) * sizeof(double), s));
+  CK(cudaMemsetAsync(ws.H, 0, (size_t)ldh * mcap * sizeof(double), s));
+  CK(cudaMemsetAsync(ws.y, 0, (size_t)(mcap + 1) * sizeof(double), s));
   if (kMixed) {  // b is FP64 (host or device): stage it, then round to FP32 in column 0
     if ((h->xbuf.bytes < (size_t)n * 8 && fault_hit()) || !ensure(h->xbuf, (size_t)n * 8)) return FAB_ENOMEM;
     CK(cudaMemcpyAsync(h->xbuf.p, b, (size_t)n * sizeof(double), cudaMemcpyDefault, s));
@@ -594,7 +606,15 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   if (sk_on && sk.kind != SK_GAUSS) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
 
   const int ntiles = (n + kTileRows - 1) / kTileRows;
-  for (int c = 1; c <= m; ++c) {
+  int c_done = 0;          // basis columns 1..c_done are built
+  int m_prev = 0;          // dimension of the previous solution (growing m)
+  double err_est = 0.0;
+  int rc_final = FAB_OK;
+  int lsqr_iters = 0, fh_iters = 0;
+  DevState hs;
+  int mu = 0;
+  for (;;) {  // one pass per dimension m (a single pass unless m grows to a target)
+  for (int c = c_done + 1; c <= m; ++c) {
     if (p->method == FAB_ARNOLDI) {
       LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
       double* Hcol = ws.H + (size_t)ldh * (c - 1);
@@ -615,20 +635,20 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
         LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
     }
   }
+  c_done = m;
   if (sk_on && sk.kind == SK_GAUSS)  // Theta V_{m+1} = G (BF16 basis) on the tensor cores, FP64 finish
     LK(PK_SKRED, launch_gauss_sketch(ws.G, ws.Wbf, ld, n, p->s, m + 1, ws.sigma, ws.gpart, ws.SV, ws.st, s));
   CK(cudaEventRecord(ev[1], s));
-  DevState hs;
   CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (hs.status != FAB_OK) return hs.status;
-  const int mu = hs.m_used;
+  mu = hs.m_used;
   h->last_m = m;
+  h->last_ldh = ldh;
   h->last_s = sk_on ? p->s : 0;
   h->last_sketched = sk_on ? 1 : 0;
   h->last_mixed = kMixed ? 1 : 0;
   h->has_state = 1;  // the basis, H and the sketch can be inspected from here on
-  int lsqr_iters = 0, fh_iters = 0;
   if (mu == 0) {  // b = 0
     CK(cudaMemsetAsync(ws.cvec, 0, (size_t)m * sizeof(double), s));
     if (bx_on_device) {
@@ -691,6 +711,24 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     rc = sqrtm_e1(ws, m, mdev, ws.cvec, p->f == FAB_F_SQRT, &fh_iters, s);
   }
   if (rc != FAB_OK) return rc;
+  if (!grow || mu < m) break;  // fixed m, or an invariant subspace: nothing to gain
+  if (m_prev > 0) {  // sketched relative change of the solution since the previous m
+    LK(PK_SMALL, launch_sketch_change(ws.SV, p->s, mdev, ws.cvec, m_prev, ws.cvec + (mcap + 1), ws.scal + 12, s));
+    double e2[2] = {0.0, 0.0};
+    CK(cudaMemcpyAsync(e2, ws.scal + 12, sizeof(e2), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    err_est = e2[1] > 0.0 ? e2[0] / e2[1] : 0.0;
+    if (err_est <= p->target_rel_err) break;
+  }
+  if (m >= mcap) {  // the cap is reached before the target: best solution, flagged
+    rc_final = FAB_ENOTCONV;
+    break;
+  }
+  CK(cudaMemcpyAsync(ws.cvec + (mcap + 1), ws.cvec, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  m_prev = m;
+  m = std::min(m + p->m_step, mcap);
+  LK(PK_SMALL, launch_state_set_m(ws.st, m, s));
+  }  // growing m
   CK(cudaEventRecord(ev[2], s));
   // x = ||b|| V_m c
   LK(PK_COMBINE, launch_prep_coef(ws.cvec, ws.sigma, mdev, ws.st, ws.coef, s));
@@ -709,6 +747,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   h->has_state = 1;
   if (stats) {
     memset(stats, 0, sizeof(*stats));
+    stats->err_est = err_est;
     stats->m_used = mu;
     stats->lsqr_iters = lsqr_iters;
     stats->fh_iters = fh_iters;
@@ -727,7 +766,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     stats->ms_combine = t23;
     stats->ms_total = t03;
   }
-  return FAB_OK;
+  return rc_final;
 }
 
 extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, double* x, int bx_on_device,
@@ -749,7 +788,9 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
 extern "C" int fab_last_state(fab_handle* h, double* H, double* SV, double* y, double* coeffs) {
   if (!h || !h->has_state) return FAB_EINVAL;
   const int m = h->last_m;
-  if (H && cudaMemcpy(H, h->H.p, (size_t)(m + 1) * m * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return FAB_ECUDA;
+  if (H && cudaMemcpy2D(H, (size_t)(m + 1) * 8, h->H.p, (size_t)h->last_ldh * 8, (size_t)(m + 1) * 8, m,
+                        cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FAB_ECUDA;
   if (SV && h->last_sketched &&
       cudaMemcpy(SV, h->SV.p, (size_t)h->last_s * (m + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
     return FAB_ECUDA;

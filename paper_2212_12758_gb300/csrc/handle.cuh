@@ -66,7 +66,7 @@ struct fab_handle {
   int P_s = -1;
   uint64_t P_seed = 0;
   // last solve
-  int has_state = 0, last_m = 0, last_s = 0, last_sketched = 0, last_mixed = 0;
+  int has_state = 0, last_m = 0, last_s = 0, last_sketched = 0, last_mixed = 0, last_ldh = 0;
 };
 
 namespace fab {

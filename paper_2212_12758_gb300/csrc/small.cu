@@ -864,6 +864,49 @@ __global__ void __launch_bounds__(256) k_lu_cluster(double* __restrict__ M, int 
   }
 }
 
+// ------------------------------------------------ sketched solution change
+// With Theta v_j in the columns of SV (s x (m+1), ld lds): out[0] = || SV c_new -
+// SV c_old || (c_old zero past m_old) and out[1] = || SV c_new ||, c_new of length
+// *mdev. The sketch embeds x_new - x_old and x_new (§2.1.1), so out[0] / out[1]
+// estimates their relative distance.
+__global__ void k_sketch_change(const double* __restrict__ SV, int lds, const int* __restrict__ mdev,
+                                const double* __restrict__ c_new, int m_old, const double* __restrict__ c_old,
+                                double* __restrict__ out) {
+  __shared__ double red[2][32];
+  const int mu = *mdev;
+  double dd = 0.0, aa = 0.0;
+  for (int q = threadIdx.x; q < lds; q += blockDim.x) {
+    double a = 0.0, o = 0.0;
+    for (int j = 0; j < mu; ++j) a = fma(SV[q + (size_t)lds * j], c_new[j], a);
+    for (int j = 0; j < m_old && j < mu; ++j) o = fma(SV[q + (size_t)lds * j], c_old[j], o);
+    const double d = a - o;
+    dd = fma(d, d, dd);
+    aa = fma(a, a, aa);
+  }
+  dd = warp_sum(dd);
+  aa = warp_sum(aa);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = dd;
+    red[1][threadIdx.x >> 5] = aa;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      x += red[0][w];
+      y += red[1][w];
+    }
+    out[0] = sqrt(x);
+    out[1] = sqrt(y);
+  }
+}
+
+cudaError_t launch_sketch_change(const double* SV, int lds, const int* mdev, const double* c_new, int m_old,
+                                 const double* c_old, double* out, cudaStream_t s) {
+  k_sketch_change<<<1, 256, 0, s>>>(SV, lds, mdev, c_new, m_old, c_old, out);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------- fused small stage (batch)
 // The steps of the small stage, each done by the whole CTA, with the same
 // per-element arithmetic as the multi-kernel path: products and linear

@@ -36,14 +36,15 @@ class Params(ctypes.Structure):
     _fields_ = [("f", ctypes.c_int), ("t", ctypes.c_double), ("m", ctypes.c_int), ("k", ctypes.c_int),
                 ("s", ctypes.c_int), ("zeta", ctypes.c_int), ("sketch", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("method", ctypes.c_int), ("precision", ctypes.c_int), ("lsqr_tol", ctypes.c_double),
-                ("lsqr_maxit", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("lsqr_maxit", ctypes.c_int), ("stream", ctypes.c_void_p), ("target_rel_err", ctypes.c_double),
+                ("m_step", ctypes.c_int), ("m_max", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("m_used", ctypes.c_int), ("lsqr_iters", ctypes.c_int), ("fh_iters", ctypes.c_int),
                 ("launches", ctypes.c_int), ("h_last", ctypes.c_double), ("beta", ctypes.c_double),
                 ("ms_basis", ctypes.c_double), ("ms_small", ctypes.c_double), ("ms_combine", ctypes.c_double),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("err_est", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -137,7 +138,8 @@ def _on_device(a) -> int:
 
 
 def params(f=EXP, t=1.0, m=30, k=2, s=None, zeta=8, sketch=SPARSE_SIGN, seed=1, method=SKETCHED_FAST,
-           precision=FP64, lsqr_tol=1e-6, lsqr_maxit=0, stream=None) -> Params:
+           precision=FP64, lsqr_tol=1e-6, lsqr_maxit=0, stream=None, target_rel_err=0.0, m_step=0,
+           m_max=0) -> Params:
     p = Params()
     lib.fab_params_default(ctypes.byref(p))
     p.f, p.t, p.m, p.k = int(f), float(t), int(m), int(k)
@@ -145,6 +147,7 @@ def params(f=EXP, t=1.0, m=30, k=2, s=None, zeta=8, sketch=SPARSE_SIGN, seed=1, 
     p.zeta, p.sketch, p.seed, p.method = int(zeta), int(sketch), int(seed), int(method)
     p.precision, p.lsqr_tol, p.lsqr_maxit = int(precision), float(lsqr_tol), int(lsqr_maxit)
     p.stream = stream
+    p.target_rel_err, p.m_step, p.m_max = float(target_rel_err), int(m_step), int(m_max)
     return p
 
 
