@@ -21,6 +21,7 @@ bounded sample of the same workload and reports the same metric.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -231,6 +232,102 @@ def bench_mixed_graph(fab, torch, W, reps: int = 2):
     return out
 
 
+def _serving_run(fab, W, reqs, arr, slots):
+    """Submit reqs at the arrival times arr (seconds), then poll all; returns latencies etc."""
+    srv = fab.Server(slots=slots)
+    for Mx, b, p, _ in reqs[:slots]:  # warm: workspaces and FP32 matrix copies
+        try:
+            srv.poll(srv.submit(Mx, b, p), timeout_ms=600000)
+        except fab.FabError as e:
+            if e.code != fab.FAB_ENOTCONV:  # a target miss still returns its best solution
+                raise
+    t0 = time.perf_counter()
+    tickets = []
+    for (Mx, b, p, cls), ta in zip(reqs, arr):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append((srv.submit(Mx, b, p), cls))
+    lat, miss, ms_used = [], [0, 0, 0], []
+    for tk, cls in tickets:
+        n_ = srv._mats.pop(tk)
+        x = np.empty(n_)
+        st = fab.Stats()
+        lt = ctypes.c_double()
+        rc = fab.lib.fab_server_poll(srv._s, ctypes.c_uint64(tk), x.ctypes.data, ctypes.byref(st), ctypes.byref(lt),
+                                     600000)
+        if rc == fab.FAB_ENOTCONV:
+            miss[cls] += 1
+        elif rc != fab.FAB_OK:
+            raise RuntimeError(f"request failed: {rc}")
+        lat.append(lt.value)
+        ms_used.append(st.m_used)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array(lat)
+    return {"requests": len(reqs), "solves_per_s": len(reqs) / wall, "wall_s": wall,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "target_misses_by_class": {"convdiff2d": miss[0], "convdiff3d": miss[1], "graph": miss[2]},
+            "mean_m_used": float(np.mean(ms_used))}
+
+
+def bench_serving(fab, torch, W, count: int = 600, rate: float = 2000.0, slots: int = 16, pool: int = 12,
+                  m_step: int = 20):
+    """Continuous batching: Poisson arrivals (mean `rate` per s, seed 4) of f(A)b requests
+    over a pool of pre-created handles, a third each 2D and 3D convection-diffusion and
+    power-law graph Laplacians (n log-uniform on [1e4, 4e6], pool seed 5); exp(tA) for
+    convection-diffusion with t ||A|| log-uniform on [50, 400], sqrt / inverse sqrt for
+    the graphs; sketched_fast, SRHT s = 400, FP32 basis, m grown from 30 by m_step up to
+    150 until the sketched relative change is below 1e-6. Two runs: the offered rate
+    (saturating: its throughput is the sustainable rate) and half the sustainable rate
+    (queueing-free latency). Latency = submission to completion."""
+    import math as _m
+
+    rng = np.random.default_rng(5)
+    mats = []
+    for i in range(pool):
+        cls = i % 3
+        n = float(np.exp(rng.uniform(_m.log(1e4), _m.log(4e6))))
+        if cls == 0:
+            N = max(10, int(round(_m.sqrt(n))))
+            A = W.convdiff(2, N)
+            lam = 8.0 * (N + 1) ** 2 + 20.0 * (N + 1)
+        elif cls == 1:
+            N = max(5, int(round(n ** (1.0 / 3.0))))
+            A = W.convdiff(3, N)
+            lam = 12.0 * (N + 1) ** 2 + 30.0 * (N + 1)
+        else:
+            A = W.chung_lu_laplacian(int(n), seed=2 + i)
+            lam = None
+        mats.append((fab.Matrix.from_csr(A), A.n, lam, cls))
+
+    def requests(cnt, seed):
+        r = np.random.default_rng(seed)
+        pick = r.integers(0, pool, cnt)
+        out = []
+        for i in range(cnt):
+            Mx, n, lam, cls = mats[pick[i]]
+            if lam is not None:
+                f, t = fab.EXP, -float(np.exp(r.uniform(_m.log(50.0), _m.log(400.0)))) / lam
+            else:
+                f, t = (fab.SQRT if r.random() < 0.5 else fab.INVSQRT), 1.0
+            p = fab.params(f=f, t=t, m=30, k=2, s=400, sketch=fab.SRHT, seed=1 + i % 7, method=fab.SKETCHED_FAST,
+                           precision=fab.MIXED, target_rel_err=1e-6, m_step=m_step, m_max=150)
+            out.append((Mx, W.random_vector(n, 1000 + i), p, cls))
+        return out
+
+    sat = _serving_run(fab, W, requests(count, 6), W.poisson_arrivals(rate, count, seed=4), slots)
+    low_rate = 0.5 * sat["solves_per_s"]
+    low_cnt = max(50, int(round(low_rate * 8.0)))
+    low = _serving_run(fab, W, requests(low_cnt, 7), W.poisson_arrivals(low_rate, low_cnt, seed=4), slots)
+    return {"workload": f"Poisson arrivals over a pool of {pool} handles (2D/3D convection-diffusion, power-law "
+                        "graphs; n 1e4..4e6), exp / sqrt / inverse sqrt, sketched_fast SRHT s=400, FP32 basis, "
+                        f"m 30..150 (step {m_step}) grown to a 1e-6 sketched relative change",
+            "slots": slots, "offered": {"rate_per_s": rate, **sat}, "half_sustainable": {"rate_per_s": low_rate, **low},
+            "sustainable_solves_per_s": sat["solves_per_s"]}
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
@@ -308,8 +405,12 @@ def run_only(args):
     from paper_2212_12758_gb300 import fab
     from paper_2212_12758_gb300 import workloads as W
 
-    out = bench_batch(fab, torch, W, steps=args.steps, count=args.batch_count) if args.only == "batch" else \
-        bench_mixed_graph(fab, torch, W, reps=args.steps)
+    if args.only == "batch":
+        out = bench_batch(fab, torch, W, steps=args.steps, count=args.batch_count)
+    elif args.only == "graph":
+        out = bench_mixed_graph(fab, torch, W, reps=args.steps)
+    else:
+        out = bench_serving(fab, torch, W)
     print(json.dumps({"only": args.only, **out}), flush=True)
     return 0
 
@@ -322,10 +423,11 @@ def main():
     ap.add_argument("--impl", default="fab", choices=["fab", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the sketched_ls / Arnoldi side measurements")
-    ap.add_argument("--extras", default="batch,graph",
+    ap.add_argument("--extras", default="batch,graph,serving",
                     help="side workloads measured after the main one: batch (256 uneven solves, one graph), "
-                         "graph (4M-node power-law Laplacian, mixed precision, Gaussian sketch)")
-    ap.add_argument("--only", choices=["batch", "graph"], default=None,
+                         "graph (4M-node power-law Laplacian, mixed precision, Gaussian sketch), serving "
+                         "(Poisson arrivals, continuous batching, p50/p99 latency)")
+    ap.add_argument("--only", choices=["batch", "graph", "serving"], default=None,
                     help="measure one side workload alone and print its JSON (for profiler runs)")
     ap.add_argument("--batch-count", type=int, default=256,
                     help="solves in the --only batch workload (same generator, batch seed 3)")
@@ -483,6 +585,8 @@ def main():
         extras["batch_256"] = bench_batch(fab, torch, W)
     if not args.no_extras and "graph" in args.extras.split(","):
         extras["mixed_graph_4M"] = bench_mixed_graph(fab, torch, W)
+    if not args.no_extras and "serving" in args.extras.split(","):
+        extras["serving"] = bench_serving(fab, torch, W)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
