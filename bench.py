@@ -52,9 +52,14 @@ def _peaks():
         return {}
 
 
-# FP64 FMA peak: the recipe's nominal GB300 FP64 rate (no measured FP64 figure is
-# provided by the pool's peak file).
+# FP64 FMA peak: the nominal GB300 FP64 rate (no measured FP64 figure exists for
+# this part).
 FP64_PEAK_GFLOPS_NOMINAL = 1250.0
+# DRAM bytes (read + write) of one k_spmv_dots launch measured by ncu on the
+# 128^3 case of this workload (263.5 MB for n = 2,097,152, window k = 4); traffic
+# grows with n and nnz, so it is scaled by n to the bench size. Only valid for the
+# kernel version it was taken on, and only for the 3D convection-diffusion operator.
+SPMV_DRAM_BYTES_PER_ROW = 263.5e6 / 2_097_152
 
 
 def algorithmic_cost(n: int, nnz: int, m: int, k: int, s: int):
@@ -129,6 +134,42 @@ def fp32_step_bytes(n: int, nnz: int, kw: int, s: int) -> int:
     """Algorithmic bytes of one basis step of the FP32 path (SpMV + dots, update +
     sketch partials): 8 nnz + 4 (n+1) + 4 n kw + 4 n, then 4 n (kw + 2) + 8 s per chunk."""
     return 8 * nnz + 4 * (n + 1) + 4 * n * kw + 4 * n + 4 * n * (kw + 2) + 8 * s * ((n + 4095) // 4096)
+
+
+def bench_mixed_same(fab, torch, Mx, bd, ref_x, stream, n: int, nnz: int, P, reps: int = 5):
+    """The bench workload with FP32 A and basis (FP64 small stage): solves/s, the
+    basis kernels against the HBM roofline (FP32 algorithmic bytes), error against
+    the FP64 Arnoldi reference solution."""
+    p = P(fab.SKETCHED_FAST)
+    p.precision = fab.MIXED
+    x = torch.empty_like(bd)
+    Mx.apply(bd, p, x=x)
+    torch.cuda.synchronize()
+    fab.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        Mx.apply(bd, p, x=x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = fab.profile_query()
+    fab.profile_enable(False)
+    ms = e0.elapsed_time(e1) / reps
+    peak = float(_peaks().get("hbm_gbs", 6800.0))
+    kw = K_WIN
+    sp_bytes = 8 * nnz + 4 * (n + 1) + 4 * n * kw + 4 * n
+    up_bytes = 4 * n * (kw + 2) + 8 * S_ROWS * ((n + 4095) // 4096)
+    out = {"solves_per_s": 1000.0 / ms, "ms_per_solve": ms,
+           "rel_err_vs_fp64_arnoldi_m150": float(torch.linalg.norm(x - ref_x) / torch.linalg.norm(ref_x))
+           if ref_x is not None else None}
+    for name, byts in (("spmv_dots", sp_bytes), ("update", up_bytes)):
+        t_ms, cnt = prof[name]
+        sec = t_ms / max(cnt, 1) / 1000.0
+        out[name] = {"ms_per_launch": sec * 1000.0, "algorithmic_bytes_per_launch": byts,
+                     "hbm_gbs": byts / sec / 1e9, "hbm_frac_of_measured": byts / sec / 1e9 / peak}
+    basis_s = (prof["spmv_dots"][0] + prof["update"][0] + prof["sketch_reduce"][0]) / 1000.0 / reps
+    out["basis_pass_hbm_frac_of_measured"] = M * (sp_bytes + up_bytes) / basis_s / 1e9 / peak
+    return out
 
 
 def bench_batch(fab, torch, W, steps: int = 3, count: int = 256):
@@ -423,8 +464,9 @@ def main():
     ap.add_argument("--impl", default="fab", choices=["fab", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the sketched_ls / Arnoldi side measurements")
-    ap.add_argument("--extras", default="batch,graph,serving",
-                    help="side workloads measured after the main one: batch (256 uneven solves, one graph), "
+    ap.add_argument("--extras", default="mixed,batch,graph,serving",
+                    help="side workloads measured after the main one: mixed (the same workload with an FP32 "
+                         "basis), batch (256 uneven solves, one graph), "
                          "graph (4M-node power-law Laplacian, mixed precision, Gaussian sketch), serving "
                          "(Poisson arrivals, continuous batching, p50/p99 latency)")
     ap.add_argument("--only", choices=["batch", "graph", "serving"], default=None,
@@ -522,7 +564,9 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": bytes_l / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": hbm_frac}
-    roof.update({"kernel": dom, "traffic": None, "ms_per_launch": avg_s * 1000.0,
+    traffic = SPMV_DRAM_BYTES_PER_ROW * n if dom == "spmv_dots" else None
+    roof.update({"kernel": dom, "traffic": traffic, "traffic_source": "ncu dram__bytes on the 128^3 case, scaled by n"
+                 if traffic else None, "ms_per_launch": avg_s * 1000.0,
                  "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
                  "hbm_gbs_algorithmic": bytes_l / avg_s / 1e9, "hbm_frac_of_measured": hbm_frac,
                  "fp64_gflops": flops_l / avg_s / 1e9, "fp64_frac_of_nominal": alu_frac})
@@ -561,6 +605,8 @@ def main():
                             "rel_err": float(torch.linalg.norm(xo - ref_x) / torch.linalg.norm(ref_x)),
                             "lsqr_iters": sto.lsqr_iters}
     rel_err = float(torch.linalg.norm(x_fast - ref_x) / torch.linalg.norm(ref_x)) if ref_x is not None else None
+    if not args.no_extras and "mixed" in args.extras.split(","):
+        extras["mixed_same_workload"] = bench_mixed_same(fab, torch, Mx, bd, ref_x, stream, n, nnz, P)
 
     # ----------------------------------------------------------------- e2e
     bh = torch.from_numpy(b).pin_memory()
