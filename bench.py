@@ -446,7 +446,19 @@ def run_only(args):
     from paper_2212_12758_gb300 import fab
     from paper_2212_12758_gb300 import workloads as W
 
-    if args.only == "batch":
+    if args.only == "mixed":
+        A = W.convdiff(3, args.grid)
+        Mx = fab.Matrix.from_csr(A)
+        stream = torch.cuda.current_stream()
+        bd = torch.from_numpy(W.random_vector(A.n, SEED_B)).cuda()
+
+        def P(method, m=M):
+            return fab.params(f=fab.EXP, t=T_EXP, m=m, k=K_WIN, s=S_ROWS, sketch=fab.SRHT, seed=SEED_SK,
+                              method=method, lsqr_tol=1e-6, stream=stream.cuda_stream)
+
+        out = {"workload": workload_name(args.grid, A.n, A.nnz).replace("FP64", "FP32 basis"),
+               **bench_mixed_same(fab, torch, Mx, bd, None, stream, A.n, A.nnz, P, reps=args.steps)}
+    elif args.only == "batch":
         out = bench_batch(fab, torch, W, steps=args.steps, count=args.batch_count)
     elif args.only == "graph":
         out = bench_mixed_graph(fab, torch, W, reps=args.steps)
@@ -469,7 +481,7 @@ def main():
                          "basis), batch (256 uneven solves, one graph), "
                          "graph (4M-node power-law Laplacian, mixed precision, Gaussian sketch), serving "
                          "(Poisson arrivals, continuous batching, p50/p99 latency)")
-    ap.add_argument("--only", choices=["batch", "graph", "serving"], default=None,
+    ap.add_argument("--only", choices=["mixed", "batch", "graph", "serving"], default=None,
                     help="measure one side workload alone and print its JSON (for profiler runs)")
     ap.add_argument("--batch-count", type=int, default=256,
                     help="solves in the --only batch workload (same generator, batch seed 3)")

@@ -94,17 +94,21 @@ __device__ __forceinline__ void spmv_dots_body(
     int ldh, double* __restrict__ coef, double* __restrict__ wn2, double* __restrict__ part,
     unsigned* __restrict__ counter, DevState* st, int bid, int nblk, unsigned char* smem_raw) {
   constexpr int NV = kMaxWindow + 1;
-  TV* s_vals = reinterpret_cast<TV*>(smem_raw);                                // [2][kSpmvCap]
-  int* s_col = reinterpret_cast<int*>(smem_raw + 2 * kSpmvCap * sizeof(TV));   // [2][kSpmvCap]
+  constexpr int S = kSpmvStages;
+  TV* s_vals = reinterpret_cast<TV*>(smem_raw);                                // [S][kSpmvCap]
+  int* s_col = reinterpret_cast<int*>(smem_raw + S * kSpmvCap * sizeof(TV));   // [S][kSpmvCap]
   const TV* Avals = reinterpret_cast<const TV*>(A.vals);
-  __shared__ __align__(8) uint64_t s_bar[2];
-  __shared__ int s_e0[2];
-  __shared__ int s_staged[2];
+  // full[q]: the tile of stage q is in shared memory (or the stage holds a direct
+  // tile); empty[q]: every warp is done with it, so it may be refilled.
+  __shared__ __align__(8) uint64_t s_full[S], s_empty[S];
+  __shared__ int s_e0[S];
+  __shared__ int s_staged[S];
+  __shared__ volatile int s_fail;
   __shared__ double sh[32 * NV];
   __shared__ double tot[NV];
   __shared__ TV s_red[kThreads / 32];
   if (st->stop) return;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int ntiles = A.ntiles;
   const TV* vin = W + (size_t)(c - 1) * ld;
   TV* wout = W + (size_t)c * ld;
@@ -116,50 +120,53 @@ __device__ __forceinline__ void spmv_dots_body(
 #pragma unroll
   for (int q = 0; q < NV; ++q) acc[q] = (TV)0;
   if (tid == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&s_full[q], 1);
+      mbar_init(&s_empty[q], kThreads / 32);
+    }
     mbar_fence_init();
+    s_fail = 0;
   }
   __syncthreads();
-  // thread 0: stage the nonzeros of `tile` into buffer `stg` (aligned to 4 entries
-  // so that both copies start and end on 16-byte boundaries; the CSR arrays are
-  // allocated with 4 spare entries).
-  auto issue = [&](int tile, int stg) {
+  // thread 0: fill stage i % S with the tile of iteration i, once every warp has
+  // released that stage's previous tile. Staged copies are aligned to 4 entries so
+  // that both start and end on 16-byte boundaries (the CSR arrays have 4 spare
+  // entries); a tile that does not fit is read directly (full[] still completes).
+  int last_it[S];
+  for (int q = 0; q < S; ++q) last_it[q] = -1;
+  auto issue = [&](int i) {
+    const int tile = bid + i * nblk;
+    const int stg = i % S;
+    if (i >= S && !mbar_wait_bounded(&s_empty[stg], (uint32_t)((i / S - 1) & 1))) {
+      s_fail = 1;  // the stage is still in use: leave it; its consumers time out too
+      return;
+    }
     const int r0 = A.tiles[tile], r1 = A.tiles[tile + 1];
     const int e0 = A.rowptr[r0], e1 = A.rowptr[r1];
     const int e0a = e0 & ~3, e1a = (e1 + 3) & ~3;
     const int cnt = e1a - e0a;
+    last_it[stg] = i;
     if (A.staged && cnt > 0 && cnt <= kSpmvCap) {
       s_e0[stg] = e0a;
       s_staged[stg] = 1;
       fence_proxy_async_smem();
-      mbar_arrive_expect_tx(&s_bar[stg], (uint32_t)cnt * (uint32_t)(sizeof(TV) + 4));
-      bulk_copy_g2s(s_vals + stg * kSpmvCap, Avals + e0a, (uint32_t)cnt * (uint32_t)sizeof(TV), &s_bar[stg]);
-      bulk_copy_g2s(s_col + stg * kSpmvCap, A.colind + e0a, (uint32_t)cnt * 4u, &s_bar[stg]);
+      mbar_arrive_expect_tx(&s_full[stg], (uint32_t)cnt * (uint32_t)(sizeof(TV) + 4));
+      bulk_copy_g2s(s_vals + stg * kSpmvCap, Avals + e0a, (uint32_t)cnt * (uint32_t)sizeof(TV), &s_full[stg]);
+      bulk_copy_g2s(s_col + stg * kSpmvCap, A.colind + e0a, (uint32_t)cnt * 4u, &s_full[stg]);
     } else {
       s_staged[stg] = 0;
+      mbar_arrive(&s_full[stg]);
     }
   };
-  uint32_t par0 = 0, par1 = 0;
+  if (tid == 0)
+    for (int i = 0; i < S - 1 && bid + i * nblk < ntiles; ++i) issue(i);
   int it = 0;
-  int tile = bid;
-  if (tid == 0 && tile < ntiles) issue(tile, 0);
-  __syncthreads();
-  bool failed = false;
-  for (; tile < ntiles; tile += nblk, ++it) {
-    const int stg = it & 1;
-    const int next = tile + nblk;
-    if (tid == 0 && next < ntiles) issue(next, stg ^ 1);
-    const bool staged = s_staged[stg] != 0;
-    if (staged) {
-      const uint32_t par = stg ? par1 : par0;
-      const bool ok = mbar_wait_bounded(&s_bar[stg], par);
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
-      if (stg) par1 ^= 1u; else par0 ^= 1u;
-    }
+  for (int tile = bid; tile < ntiles; tile += nblk, ++it) {
+    const int stg = it % S;
+    if (tid == 0 && bid + (it + S - 1) * nblk < ntiles && !s_fail) issue(it + S - 1);
+    bool ok = !s_fail && mbar_wait_bounded(&s_full[stg], (uint32_t)((it / S) & 1));
+    if (!ok) s_fail = 1;
+    const bool staged = ok && s_staged[stg] != 0;
     // The tile's rows share the block: L = 256 / pow2ceil(rows) lanes per row
     // (one row per thread for full tiles, the whole block for a single long row);
     // each lane sums every L-th nonzero of its row, then the lanes of a row are
@@ -168,7 +175,7 @@ __device__ __forceinline__ void spmv_dots_body(
     const int lgL = 8 - (nr > 1 ? 32 - __clz(nr - 1) : 0);
     const int L = 1 << lgL;
     const int grp = tid >> lgL, lane_r = tid & (L - 1);
-    const bool has_row = grp < nr;
+    const bool has_row = ok && grp < nr;
     const int r = r0 + grp;
     TV y = (TV)0;
     TV wv[KW > 0 ? KW : 1];
@@ -226,6 +233,7 @@ __device__ __forceinline__ void spmv_dots_body(
           for (int q = 1; q < (L >> 5); ++q) t += s_red[(tid >> 5) + q];
           y = t;
         }
+        __syncthreads();  // s_red is free for the next such tile
       }
     }
     if (has_row && lane_r == 0) {
@@ -235,16 +243,18 @@ __device__ __forceinline__ void spmv_dots_body(
       for (int q = 0; q < KW; ++q) acc[q] = fma(wv[q], y, acc[q]);
       acc[kMaxWindow] = fma(y, y, acc[kMaxWindow]);
     }
-    __syncthreads();  // every thread is done with buffer stg before it is refilled
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&s_empty[stg]);  // this warp is done with the stage
   }
-  if (failed) {
-    // A staged tile never arrived: record it, give the copies in flight a second
-    // bounded wait so that none lands in shared memory after the block exits.
+  __syncthreads();
+  if (s_fail) {
+    // A tile never arrived or a stage was never released: record it and give every
+    // copy issued a bounded wait so that none lands in shared memory after exit.
     if (tid == 0) {
       st->status = FAB_ETIMEOUT;
       st->stop = 1;
-      for (int b = 0; b < 2; ++b)
-        if (s_staged[b]) mbar_wait_bounded(&s_bar[b], b ? par1 : par0);
+      for (int q = 0; q < S; ++q)
+        if (last_it[q] >= 0) mbar_wait_bounded(&s_full[q], (uint32_t)((last_it[q] / S) & 1));
     }
     __syncthreads();
     return;
@@ -299,7 +309,7 @@ template <typename TV>
 int spmv_grid(int ntiles, int kw) {
   static int occ[kMaxWindow + 1] = {0};
   if (occ[kw] == 0) {
-    const size_t smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
+    const size_t smem = (size_t)kSpmvStages * kSpmvCap * (sizeof(TV) + sizeof(int));
     ensure_smem_limit(spmv_fn<TV>(kw), smem);
     int o = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmv_fn<TV>(kw), kThreads, smem);
@@ -316,7 +326,7 @@ cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int
                              double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
                              DevState* st, cudaStream_t s) {
   if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
+  const size_t smem = (size_t)kSpmvStages * kSpmvCap * (sizeof(TV) + sizeof(int));
   const int grid = spmv_grid<TV>(A.ntiles, kw);
   void* args[] = {(void*)&A, &W, &ld, &c, &j0, &kw, &cs, &H, &ldh, &coef, &wn2, &part, &counter, &st};
   return cudaLaunchKernel(spmv_fn<TV>(kw), dim3(grid), dim3(kThreads), args, smem, s);
@@ -1061,7 +1071,7 @@ cudaError_t launch_spmv_wave(const BasisJob<TV>* jobs, const Wave& w, int nblock
       (const void*)k_spmv_wave<TV, 6>, (const void*)k_spmv_wave<TV, 7>, (const void*)k_spmv_wave<TV, 8>};
   if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
   if (nblocks <= 0) return cudaSuccess;
-  const size_t smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
+  const size_t smem = (size_t)kSpmvStages * kSpmvCap * (sizeof(TV) + sizeof(int));
   cudaError_t e = ensure_smem_limit(fns[kw], smem);
   if (e != cudaSuccess) return e;
   Wave wv = w;
@@ -1109,7 +1119,7 @@ cudaError_t launch_combine_wave(const BasisJob<TV>* jobs, const Wave& w, int nbl
 // capture itself issues no attribute calls. upd_smem: largest update-wave size.
 template <typename TV>
 cudaError_t wave_prepare(size_t upd_smem, int mmax) {
-  const size_t spmv_smem = (size_t)2 * kSpmvCap * (sizeof(TV) + sizeof(int));
+  const size_t spmv_smem = (size_t)kSpmvStages * kSpmvCap * (sizeof(TV) + sizeof(int));
   const void* spmv[] = {(const void*)k_spmv_wave<TV, 0>, (const void*)k_spmv_wave<TV, 1>,
                         (const void*)k_spmv_wave<TV, 2>, (const void*)k_spmv_wave<TV, 3>,
                         (const void*)k_spmv_wave<TV, 4>, (const void*)k_spmv_wave<TV, 5>,

@@ -187,6 +187,9 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_addr(dst)),
@@ -224,7 +227,8 @@ struct Csr {
   int ntiles;
   int staged;         // 1: stage a tile's nonzeros in shared memory by bulk copies when they fit
 };
-constexpr int kSpmvCap = 2048;  // nonzeros per staged SpMV tile (FP64: vals 16 KB + colind 8 KB)
+constexpr int kSpmvCap = 2048;   // nonzeros per staged SpMV tile (FP64: vals 16 KB + colind 8 KB)
+constexpr int kSpmvStages = 2;   // staged tiles in flight per block (ring of shared-memory buffers)
 
 cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s);
 cudaError_t launch_state_set_m(DevState* st, int m, cudaStream_t s);  // basis target dimension
