@@ -225,12 +225,12 @@ def bench_batch(fab, torch, W, steps: int = 3, count: int = 256):
             "max_rel_err_vs_fp64_same_m": err, "create_s": create_s}
 
 
-def bench_mixed_graph(fab, torch, W, reps: int = 2):
+def bench_mixed_graph(fab, torch, W, reps: int = 2, n: int = 4_000_000, references: bool = True):
     """Shifted Chung-Lu Laplacian (n = 4M, exponent 2.5, mean degree 10, L + 0.1 I), f = A^{-1/2}
     and A^{1/2}, m = 150, k = 2, Gaussian sketch s = 600 (BF16 on the tensor cores, FP32
     accumulation), FP32 basis, FP64 QR and f(H). Error against the library's FP64 Arnoldi
     f_m at the same m and at m = 300."""
-    A = W.chung_lu_laplacian(4_000_000, seed=2)
+    A = W.chung_lu_laplacian(n, seed=2)
     Mx = fab.Matrix.from_csr(A)
     b = torch.from_numpy(W.random_vector(A.n, 0)).cuda()
     stream = torch.cuda.current_stream()
@@ -258,8 +258,8 @@ def bench_mixed_graph(fab, torch, W, reps: int = 2):
         g_ms = prof["sketch_reduce"][0] / max(prof["sketch_reduce"][1], 1)
         flops = 2.0 * s * A.n * (m + 1)
         gbytes = 2.0 * s * A.n + 2.0 * A.n * (m + 1)
-        ref = {}
-        for mr in (150, 300):
+        ref = {150: None, 300: None}
+        for mr in ((150, 300) if references else ()):
             xr = torch.empty_like(b)
             Mx.apply(b, fab.params(f=f, m=mr, k=2, method=fab.ARNOLDI, stream=sp), x=xr)
             ref[mr] = float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))
@@ -461,7 +461,7 @@ def run_only(args):
     elif args.only == "batch":
         out = bench_batch(fab, torch, W, steps=args.steps, count=args.batch_count)
     elif args.only == "graph":
-        out = bench_mixed_graph(fab, torch, W, reps=args.steps)
+        out = bench_mixed_graph(fab, torch, W, reps=args.steps, n=args.graph_n, references=not args.no_extras)
     else:
         out = bench_serving(fab, torch, W)
     print(json.dumps({"only": args.only, **out}), flush=True)
@@ -483,6 +483,8 @@ def main():
                          "(Poisson arrivals, continuous batching, p50/p99 latency)")
     ap.add_argument("--only", choices=["mixed", "batch", "graph", "serving"], default=None,
                     help="measure one side workload alone and print its JSON (for profiler runs)")
+    ap.add_argument("--graph-n", type=int, default=4_000_000,
+                    help="nodes of the --only graph workload (smaller only for profiler captures)")
     ap.add_argument("--batch-count", type=int, default=256,
                     help="solves in the --only batch workload (same generator, batch seed 3)")
     ap.add_argument("--grid", type=int, default=N_GRID,
