@@ -1108,6 +1108,13 @@ int build_tiles(fab_handle* h, int rows_max, int nnz_cap, int staged) {
     // grow while the tile stays within rows_max rows and its 16-byte aligned
     // nonzero range within nnz_cap entries
     while (r1 < h->n && r1 - r0 < rows_max && ((rp[r1 + 1] + 3) & ~3) - (rp[r0] & ~3) <= nnz_cap) ++r1;
+    // a tile cut by the nonzero cap keeps a power-of-two row count, so that
+    // 256 / rows lanes per row use every thread of the block
+    if (r1 < h->n && r1 - r0 < rows_max) {
+      int R = 1;
+      while (2 * R <= r1 - r0) R *= 2;
+      r1 = r0 + R;
+    }
     t.push_back(r1);
     r0 = r1;
   }
