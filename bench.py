@@ -187,6 +187,12 @@ def bench_batch(fab, torch, W, steps: int = 3, count: int = 256):
 
     bs = [torch.from_numpy(W.random_vector(a.n, 100 + i)).cuda() for i, a in enumerate(A)]
     t0 = time.perf_counter()
+    choices = {}
+    for Mx in mats:  # the autotuner picks each matrix's SpMV tiling for the FP32 kernel, window k
+        ch = Mx.tune(fab.MIXED, k=k)
+        choices[str(ch)] = choices.get(str(ch), 0) + 1
+    tune_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
     bt = fab.Batch(mats, ps(fab.MIXED))
     create_s = time.perf_counter() - t0
     xs = [torch.empty_like(b) for b in bs]
@@ -222,7 +228,8 @@ def bench_batch(fab, torch, W, steps: int = 3, count: int = 256):
             "hbm_gbs_algorithmic": byts / (ms / 1000.0) / 1e9,
             "hbm_frac_of_measured": byts / (ms / 1000.0) / 1e9 / peak,
             "note": "solves with n below ~3e5 keep their basis in L2, so algorithmic GB/s is not all HBM traffic",
-            "max_rel_err_vs_fp64_same_m": err, "create_s": create_s}
+            "max_rel_err_vs_fp64_same_m": err, "create_s": create_s, "autotune_s": tune_s,
+            "tilings_chosen": choices}
 
 
 def bench_mixed_graph(fab, torch, W, reps: int = 2, n: int = 4_000_000, references: bool = True):
