@@ -59,10 +59,12 @@ int sk_kind_of(const fab_params& p) {
   return p.sketch == FAB_SK_SRHT ? SK_SRHT : SK_SPARSE_TAB;  // sparse sign: pattern drawn once, at creation
 }
 
-// A batched solve's SpMV blocks: its own launch's grid, but at least kMinTiles
-// tiles per block (a solve shares the GPU with the rest of the batch, so fewer,
-// longer blocks keep the tile pipeline busy).
-constexpr int kMinTiles = 8;
+// A batched solve's blocks: its own launch's grid, but at least kMinTiles SpMV
+// tiles and kMinChunks update chunks per block (a solve shares the GPU with the
+// rest of the batch, so fewer, longer blocks amortise each block's start-up and
+// its partial-sum reduction).
+constexpr int kMinTiles = 32;
+constexpr int kMinChunks = 4;
 
 }  // namespace
 
@@ -155,8 +157,9 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       for (int j : ids) {
         size_t sm = 0;
         const int s = kd == SK_NONE ? 0 : ps[j].s;
-        const int grid = update_grid<TV>(kd, bt->n[j], kw, s, &sm);
+        int grid = update_grid<TV>(kd, bt->n[j], kw, s, &sm);
         if (grid < 1) return FAB_ECUDA;
+        grid = std::min(grid, ((bt->n[j] + kChunk - 1) / kChunk + kMinChunks - 1) / kMinChunks);
         nb.push_back(grid);
         smem = std::max(smem, sm);
         part_need[j] = std::max(part_need[j], (size_t)grid);
