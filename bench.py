@@ -470,7 +470,7 @@ def run_only(args):
     elif args.only == "graph":
         out = bench_mixed_graph(fab, torch, W, reps=args.steps, n=args.graph_n, references=not args.no_extras)
     else:
-        out = bench_serving(fab, torch, W)
+        out = bench_serving(fab, torch, W, slots=args.serving_slots)
     print(json.dumps({"only": args.only, **out}), flush=True)
     return 0
 
@@ -490,6 +490,7 @@ def main():
                          "(Poisson arrivals, continuous batching, p50/p99 latency)")
     ap.add_argument("--only", choices=["mixed", "batch", "graph", "serving"], default=None,
                     help="measure one side workload alone and print its JSON (for profiler runs)")
+    ap.add_argument("--serving-slots", type=int, default=16, help="server slots of the --only serving workload")
     ap.add_argument("--graph-n", type=int, default=4_000_000,
                     help="nodes of the --only graph workload (smaller only for profiler captures)")
     ap.add_argument("--batch-count", type=int, default=256,

@@ -227,6 +227,7 @@ void fab_destroy(fab_handle* h) {
                  &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
   cudaGetLastError();
   delete h;
 }
@@ -285,6 +286,15 @@ void note_error(int kind, cudaError_t e, int line) {
 
 thread_local int g_launches = 0;
 
+// Host waits of a solve. A serving slot waits on a blocking-sync event so that
+// its thread sleeps instead of spinning on a core the other slots need.
+thread_local cudaEvent_t g_wait_event = nullptr;
+cudaError_t wait_stream(cudaStream_t s) {
+  if (!g_wait_event) return cudaStreamSynchronize(s);
+  cudaError_t e = cudaEventRecord(g_wait_event, s);
+  return e == cudaSuccess ? cudaEventSynchronize(g_wait_event) : e;
+}
+
 bool sketched(int method) { return method == FAB_SKETCHED_FAST || method == FAB_SKETCHED_LS; }
 
 int64_t next_pow2(int64_t n) {
@@ -335,7 +345,12 @@ struct Ws {
   unsigned* counter;
   int *P, *piv;
   DevState* st;
+  // pinned host copies: the status word and a few scalars (a copy to pageable
+  // memory would go through the driver's shared staging buffer)
+  DevState* hs;
+  double* hd;
 };
+constexpr size_t kPinnedBytes = 512;  // DevState + 16 doubles
 
 struct Need {
   Buf* b;
@@ -432,6 +447,15 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
   ws.P = ptr<int>(h->P);
   ws.piv = ptr<int>(h->piv);
   ws.st = ptr<DevState>(h->state);
+  if (!h->h_pinned) {
+    if (cudaHostAlloc(&h->h_pinned, kPinnedBytes, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      h->h_pinned = nullptr;
+      return FAB_ENOMEM;
+    }
+  }
+  ws.hs = reinterpret_cast<DevState*>(h->h_pinned);
+  ws.hd = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(h->h_pinned) + 256);
   return FAB_OK;
 }
 
@@ -442,9 +466,9 @@ int expm_e1(Ws& ws, int m, const int* mdev, double* c, int* squarings, cudaStrea
   double *M = ws.mats[0], *A2 = ws.mats[1], *A4 = ws.mats[2], *A6 = ws.mats[3], *T = ws.mats[4], *U = ws.mats[5],
          *V = ws.mats[6], *X = ws.mats[7], *X2 = ws.mats[8];
   LK(PK_SMALL, launch_norm1(M, m, mdev, ws.scal + 10, s));
-  double nrm = 0.0;
-  CK(cudaMemcpyAsync(&nrm, ws.scal + 10, sizeof(double), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpyAsync(ws.hd, ws.scal + 10, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(wait_stream(s));
+  const double nrm = ws.hd[0];
   if (!isfinite(nrm)) return FAB_ENUMERIC;
   int sq = 0;
   if (nrm > kTheta13) sq = (int)ceil(log2(nrm / kTheta13));
@@ -488,9 +512,9 @@ int sqrtm_e1(Ws& ws, int m, const int* mdev, double* c, int want_sqrt, int* iter
     LK(PK_SMALL, launch_lu_fast(T, m, mdev, m, ws.piv, ws.scal + 11, ws.st, s));
     LK(PK_SMALL, launch_lu_solve(T, m, ws.piv, mdev, m, Minv, m, 1, s));
     LK(PK_SMALL, launch_db_update(M, Minv, m, mdev, c, ws.scal + 11, err > 1e-2 ? 1 : 0, ws.st, s));
-    DevState hs;
+    DevState& hs = *ws.hs;
     CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(wait_stream(s));
     if (hs.status != FAB_OK) return hs.status;
     err = hs.scal[1];
     if (iters) *iters = it + 1;
@@ -611,7 +635,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   double err_est = 0.0;
   int rc_final = FAB_OK;
   int lsqr_iters = 0, fh_iters = 0;
-  DevState hs;
+  DevState& hs = *ws.hs;
   int mu = 0;
   for (;;) {  // one pass per dimension m (a single pass unless m grows to a target)
   for (int c = c_done + 1; c <= m; ++c) {
@@ -640,7 +664,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     LK(PK_SKRED, launch_gauss_sketch(ws.G, ws.Wbf, ld, n, p->s, m + 1, ws.sigma, ws.gpart, ws.SV, ws.st, s));
   CK(cudaEventRecord(ev[1], s));
   CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(wait_stream(s));
   if (hs.status != FAB_OK) return hs.status;
   mu = hs.m_used;
   h->last_m = m;
@@ -656,7 +680,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     } else {
       memset(x, 0, (size_t)n * sizeof(double));
     }
-    CK(cudaStreamSynchronize(s));
+    CK(wait_stream(s));
     h->has_state = 1;
     if (stats) {
       memset(stats, 0, sizeof(*stats));
@@ -690,7 +714,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
       LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, nullptr, ws.lv_q, 0, nullptr, ws.st, s));
       LK(PK_SMALL, launch_lsqr_step(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, ws.st, s));
       CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
+      CK(wait_stream(s));
       if (hs.status != FAB_OK) return hs.status;
       if (hs.flag) {
         converged = true;
@@ -714,9 +738,9 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   if (!grow || mu < m) break;  // fixed m, or an invariant subspace: nothing to gain
   if (m_prev > 0) {  // sketched relative change of the solution since the previous m
     LK(PK_SMALL, launch_sketch_change(ws.SV, p->s, mdev, ws.cvec, m_prev, ws.cvec + (mcap + 1), ws.scal + 12, s));
-    double e2[2] = {0.0, 0.0};
-    CK(cudaMemcpyAsync(e2, ws.scal + 12, sizeof(e2), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    double* e2 = ws.hd + 2;
+    CK(cudaMemcpyAsync(e2, ws.scal + 12, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(wait_stream(s));
     err_est = e2[1] > 0.0 ? e2[0] / e2[1] : 0.0;
     if (err_est <= p->target_rel_err) break;
   }
@@ -741,7 +765,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   CK(cudaEventRecord(ev[3], s));
   if (!bx_on_device) CK(cudaMemcpyAsync(x, xdst, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(wait_stream(s));
   if (g_prof.on) g_prof.end_solve();
   if (hs.status != FAB_OK) return hs.status;
   h->has_state = 1;
@@ -1043,6 +1067,17 @@ extern "C" const char* fab_last_error(void) { return g_errmsg; }
 
 namespace fab {
 void set_last_error(const char* msg) { snprintf(g_errmsg, sizeof(g_errmsg), "%s", msg ? msg : ""); }
+void use_blocking_waits(bool on) {
+  if (on && !g_wait_event) {
+    if (cudaEventCreateWithFlags(&g_wait_event, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      g_wait_event = nullptr;
+    }
+  } else if (!on && g_wait_event) {
+    cudaEventDestroy(g_wait_event);
+    g_wait_event = nullptr;
+  }
+}
 int validate_params(const fab_handle* h, const fab_params* p) { return validate(h, p); }
 const double* pade13_b() {
   static const Pade13 pd;

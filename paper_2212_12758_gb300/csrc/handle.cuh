@@ -65,6 +65,8 @@ struct fab_handle {
   int64_t P_npad = -1;
   int P_s = -1;
   uint64_t P_seed = 0;
+  // pinned host scratch for the solve's small readbacks (status word, norms)
+  void* h_pinned = nullptr;
   // last solve
   int has_state = 0, last_m = 0, last_s = 0, last_sketched = 0, last_mixed = 0, last_ldh = 0;
 };
@@ -88,6 +90,8 @@ void set_last_error(const char* msg);
 int build_tiles(fab_handle* h, int rows_max, int nnz_cap, int staged);
 // The CSR view of h's matrix for the basis kernels (vals: FP64 or FP32 copy).
 struct Csr;
+// This host thread's solves wait on a blocking-sync event (sleep) instead of spinning.
+void use_blocking_waits(bool on);
 // Parameter checks of fab_apply (FAB_OK or FAB_EINVAL).
 int validate_params(const fab_handle* h, const fab_params* p);
 // Pade [13/13] numerator coefficients b_0..b_13 and the threshold theta_13.

@@ -43,6 +43,8 @@ struct Slot {
   fab_handle* ws = nullptr;  // workspace clone (null until first use)
   size_t held = 0;           // device bytes held by ws
   bool busy = false;
+  double* pin = nullptr;     // pinned staging of b and x (grow-only, 2 pin_n doubles)
+  size_t pin_n = 0;
 };
 
 }  // namespace
@@ -87,6 +89,10 @@ bool admissible(const fab_server* s, int self, const Request* r) {
 
 void worker(fab_server* s, int self) {
   cudaSetDevice(s->device);
+  fab::use_blocking_waits(true);
+  struct Release {
+    ~Release() { fab::use_blocking_waits(false); }
+  } release;
   Slot& sl = s->slots[self];
   for (;;) {
     Request* r = nullptr;
@@ -120,8 +126,22 @@ void worker(fab_server* s, int self) {
     else fab::point_to_matrix(sl.ws, r->h);
     fab_params p = r->p;
     p.stream = sl.stream;
-    r->x.assign(r->b.size(), 0.0);
-    r->rc = fab_apply(sl.ws, &p, r->b.data(), r->x.data(), 0, &r->st);
+    const size_t n = r->b.size();
+    r->x.assign(n, 0.0);
+    if (sl.pin_n < n) {  // pinned staging: the copies run asynchronously on the slot's stream
+      if (sl.pin) cudaFreeHost(sl.pin);
+      sl.pin = nullptr;
+      sl.pin_n = 0;
+      if (cudaHostAlloc(&sl.pin, 2 * n * sizeof(double), cudaHostAllocDefault) == cudaSuccess) sl.pin_n = n;
+      else cudaGetLastError();
+    }
+    if (sl.pin) {
+      memcpy(sl.pin, r->b.data(), n * sizeof(double));
+      r->rc = fab_apply(sl.ws, &p, sl.pin, sl.pin + n, 0, &r->st);
+      memcpy(r->x.data(), sl.pin + n, n * sizeof(double));
+    } else {
+      r->rc = fab_apply(sl.ws, &p, r->b.data(), r->x.data(), 0, &r->st);
+    }
     if (r->rc == FAB_ECUDA) snprintf(r->err, sizeof(r->err), "%s", fab_last_error());
     {
       std::lock_guard<std::mutex> lk(s->mu);
@@ -249,6 +269,7 @@ extern "C" void fab_server_destroy(fab_server* s) {
   for (Slot& sl : s->slots) {
     if (sl.ws) fab_destroy(sl.ws);
     if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.pin) cudaFreeHost(sl.pin);
   }
   for (auto& kv : s->reqs) delete kv.second;
   cudaGetLastError();
