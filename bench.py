@@ -377,14 +377,34 @@ def bench_serving(fab, torch, W, count: int = 600, rate: float = 2000.0, slots: 
 
 
 def _dist():
+    """(torch.distributed or None, rank, world size) from the torchrun environment;
+    NCCL on GPUs, gloo otherwise (replicas exchange only their timings)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
 
         if not dist.is_initialized():
-            dist.init_process_group("nccl")
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         return dist, dist.get_rank(), ws
     return None, 0, 1
+
+
+def max_over_ranks(dist, x: float) -> float:
+    """The largest x over all ranks (the slowest replica's time)."""
+    if dist is None:
+        return x
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Units processed by all replicas per second of the slowest replica."""
+    return units_per_rank * world / max_seconds
 
 
 def cpu_oracle_sample(A, b, budget_s: float = 15.0):
@@ -561,13 +581,9 @@ def main():
     clk = clocks.stop()
     prof = fab.profile_query()
     fab.profile_enable(False)
-    total_ms = t_all0.elapsed_time(t_all1)
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(dist, t_all0.elapsed_time(t_all1))
     lat = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
-    solves_per_s = ws * args.steps / (total_ms / 1000.0)
+    solves_per_s = whole_job_rate(args.steps, ws, total_ms / 1000.0)
     ms_per_step = total_ms / args.steps
 
     # ------------------------------------------------------------ roofline
@@ -642,12 +658,8 @@ def main():
         rc = fab.lib.fab_apply(Mx._h, p_fast, bh.data_ptr(), xh.data_ptr(), 0, None)
         assert rc == 0, rc
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": ws / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
+    e2e_s = max_over_ranks(dist, (time.perf_counter() - t0) / e2e_steps)
+    e2e = {"value": whole_job_rate(1, ws, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
 
     if not args.no_extras and "batch" in args.extras.split(","):
         extras["batch_256"] = bench_batch(fab, torch, W)

@@ -346,7 +346,7 @@ struct Ws {
   int *P, *piv;
   DevState* st;
   // pinned host copies: the status word and a few scalars (a copy to pageable
-  // memory would go through the driver's shared staging buffer)
+  // memory would go through the CUDA runtime's shared staging buffer)
   DevState* hs;
   double* hd;
 };
