@@ -16,6 +16,8 @@ Readings of the paper taken here (where it is garbled or silent):
   stops with m_used = c columns.
 * Alg. 4 reuses the basis sketch Theta for the Blendenpik preconditioner, and
   LSQR starts at zero.
+* Alg. 1: gamma_b = r_11 (eq. relationxx); the breakdown rule of Alg. 2 applied
+  to r_ii against ||Theta w||; Alg. 3 runs LSQR on V_m itself.
 """
 from __future__ import annotations
 
@@ -29,7 +31,7 @@ import scipy.sparse
 from . import matfun
 
 EPS = np.finfo(np.float64).eps
-ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ = 0, 1, 2, 3
+ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ, BG_LS = 0, 1, 2, 3, 4
 
 
 def as_operator(A):
@@ -73,6 +75,51 @@ def nt_basis(A, b, m: int, k: int, orth: str = "cgs") -> Basis:
             return _breakdown(V, H, beta, c)
         V[:, c] = w / H[c, c - 1]
     return Basis(V, H, beta, m)
+
+
+@dataclass
+class BGBasis(Basis):
+    S: np.ndarray = None   # s x (m_used+1): Theta V, orthonormal columns
+    R: np.ndarray = None   # (m_used+1) x (m_used+1) upper triangular coefficients
+
+
+def bg_basis(A, b, m: int, sketch) -> BGBasis:
+    """Alg. 1 (§2.1.1, from Balabanov and Grigori): a basis whose sketch
+    S = Theta V keeps orthonormal columns. Step i forms w = A v_{i-1} and its
+    sketch p = Theta w, does one classical Gram-Schmidt step on the sketches
+    (r = S^T p, s = p - S r, r_ii = ||s||), and applies the same coefficients to
+    the long vectors: v_i = (w - V r) / r_ii. H_m is R without its first column;
+    gamma_b = r_11. Breakdown as for Alg. 2, on the sketched norms."""
+    b = np.asarray(b, dtype=np.float64)
+    n = b.shape[0]
+    p = np.asarray(sketch.apply(b), dtype=np.float64).ravel()
+    s = p.shape[0]
+    V = np.zeros((n, m + 1))
+    S = np.zeros((s, m + 1))
+    R = np.zeros((m + 1, m + 1))
+    r11 = float(np.linalg.norm(p))
+    if r11 == 0.0:
+        return BGBasis(V[:, :1], np.zeros((1, 0)), 0.0, 0, S[:, :1], R[:1, :1])
+    R[0, 0] = r11
+    S[:, 0] = p / r11
+    V[:, 0] = b / r11
+    for c in range(1, m + 1):
+        w = A @ V[:, c - 1]
+        p = np.asarray(sketch.apply(w), dtype=np.float64).ravel()
+        r = S[:, :c].T @ p
+        sv = p - S[:, :c] @ r
+        rcc = float(np.linalg.norm(sv))
+        R[:c, c] = r
+        R[c, c] = rcc
+        if not rcc > 64 * EPS * float(np.linalg.norm(p)):
+            Vb = np.zeros((n, c + 1))
+            Vb[:, :c] = V[:, :c]
+            Hb = np.zeros((c + 1, c))
+            Hb[:c, :c] = R[:c, 1 : c + 1]
+            return BGBasis(Vb, Hb, r11, c, S[:, : c + 1], R[: c + 1, : c + 1])
+        S[:, c] = sv / rcc
+        V[:, c] = (w - V[:, :c] @ r) / rcc
+    return BGBasis(V, R[:, 1:].copy(), r11, m, S, R)
 
 
 def _breakdown(V, H, beta, c):
@@ -271,6 +318,28 @@ def sketched_fast(A, b, m: int, k: int, f: int, sketch, t: float = 1.0, coef=Non
     return Result(Vm @ c, mu, c / B.beta, SV=SVfull, R=R, basis=B)
 
 
+def bg_ls(A, b, m: int, f: int, sketch, t: float = 1.0, coef=None, tol: float = 1e-14, maxit: int | None = None,
+          exact_ls: bool = False) -> Result:
+    """Alg. 3: the basis of Alg. 1, y = argmin ||V_m z - v_{m+1}|| by LSQR without a
+    preconditioner (the basis is well conditioned, §3.2), then
+    r_11 V_m f(H_m + h_{m+1,m} y e_m^T) e_1. ``exact_ls`` solves densely (pins)."""
+    B = bg_basis(A, b, m, sketch)
+    mu = B.m_used
+    if mu == 0:
+        return Result(np.zeros_like(b, dtype=np.float64), 0, np.zeros(0), basis=B)
+    Vm, vlast = B.V[:, :mu], B.V[:, mu]
+    if mu < m:  # invariant subspace: v_{m+1} does not exist, Hhat = H_m
+        y, iters = np.zeros(mu), 0
+    elif exact_ls:
+        y, iters = np.linalg.lstsq(Vm, vlast, rcond=None)[0], 0
+    else:
+        res = lsqr(lambda z: Vm @ z, lambda u: Vm.T @ u, vlast, mu, tol, maxit if maxit is not None else 4 * mu)
+        y, iters = res.x, res.iters
+    Hhat = _last_column_update(B, y)
+    c = matfun.f_e1(Hhat, f, t, coef)
+    return Result(B.beta * (Vm @ c), mu, c, Hhat=Hhat, y=y, SV=B.S, R=B.R, lsqr_iters=iters, basis=B)
+
+
 def run(method: int, A, b, m: int, k: int, f: int, sketch=None, t: float = 1.0, **kw) -> Result:
     """Dispatch on the library's method enum."""
     if method == ARNOLDI:
@@ -283,4 +352,6 @@ def run(method: int, A, b, m: int, k: int, f: int, sketch=None, t: float = 1.0, 
     if method == SKETCHED_FAST:
         return sketched_fast(A, b, m, k, f, sketch, t, orth=kw.get("orth", "cgs"),
                              form=kw.get("form", "sketch_solve"))
+    if method == BG_LS:
+        return bg_ls(A, b, m, f, sketch, t, tol=kw.get("tol", 1e-14), maxit=kw.get("maxit"))
     raise ValueError("unknown method")

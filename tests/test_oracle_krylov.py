@@ -240,3 +240,73 @@ def test_matfun_against_eigendecomposition():
         assert _rel(matfun.f_apply(M, z, f, t), ref) < 1e-8
     S = matfun.sqrtm(M)
     assert np.linalg.norm(S @ S - M) / np.linalg.norm(M) < 1e-10
+
+
+# ------------------------------------------------ Alg. 1 basis and Alg. 3
+def test_bg_basis_sketch_orthonormal_and_arnoldi_like():
+    """Alg. 1 keeps S = Theta V orthonormal (the sketched Gram-Schmidt step) and the
+    basis satisfies eq. arnoldilike with H_m = R(:, 2:m+1)."""
+    A, b = _small_cd(14)
+    th = sketch.make(sketch.SRHT, A.shape[0], 90, 3, 8)
+    B = krylov.bg_basis(A, b, 30, th)
+    assert B.m_used == 30
+    # Theta v_i = s_i by linearity: the same coefficients act on both vectors (to the
+    # rounding of the two recurrences, carried through m = 30 steps)
+    assert np.linalg.norm(th.apply(B.V) - B.S) < 1e-9 * np.linalg.norm(B.S)
+    # orthonormal in exact arithmetic; one classical Gram-Schmidt pass per step
+    # loses orthogonality at O(eps kappa^2) of [S_{i-1}, p_i]
+    assert np.linalg.norm(B.S.T @ B.S - np.eye(31)) < 1e-8
+    res = A @ B.V[:, :30] - B.V @ B.H
+    assert np.linalg.norm(res) / (scipy.sparse.linalg.norm(A) * np.linalg.norm(B.V)) < 1e-13
+    assert B.beta == pytest.approx(np.linalg.norm(th.apply(b)))  # gamma_b = r_11
+    assert np.allclose(B.V[:, 0] * B.beta, b)
+
+
+def test_bg_with_orthogonal_sketch_is_arnoldi():
+    """A full SRHT (s = n = 2^p) is an orthogonal map, so the sketched Gram-Schmidt
+    step is exact Gram-Schmidt: the basis and H are Arnoldi's."""
+    A = W.to_scipy(W.convdiff(2, 16))  # n = 256
+    b = W.random_vector(256, 1)
+    th = sketch.make(sketch.SRHT, 256, 256, 2, 8)
+    B = krylov.bg_basis(A, b, 20, th)
+    U = krylov.arnoldi(A, b, 20, reorth=True)
+    assert np.linalg.norm(B.V - U.V) < 1e-10 * np.linalg.norm(U.V)
+    assert np.linalg.norm(B.H - U.H) < 1e-10 * np.linalg.norm(U.H)
+    assert B.beta == pytest.approx(np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("f,t", [(EXP, -0.01), (SQRT, 1.0), (INVSQRT, 1.0)])
+def test_bg_ls_exact_equals_arnoldi_and_lsqr_converges(f, t):
+    """lemma:basis: the compression onto K_m does not depend on the basis, so Alg. 3
+    with the least-squares problem solved exactly equals Arnoldi; LSQR on the well
+    conditioned basis reaches the exact solution."""
+    A, b = _small_cd(12)
+    if f != EXP:
+        A = (A + A.T) / 2  # SPD: convdiff's symmetric part is -Laplace_h + diag
+    th = sketch.make(sketch.SRHT, A.shape[0], 60, 5, 8)
+    ref = krylov.fm_arnoldi(A, b, 18, f, t, reorth=True).x
+    ex = krylov.bg_ls(A, b, 18, f, th, t, exact_ls=True)
+    assert _rel(ex.x, ref) < 1e-10
+    it = krylov.bg_ls(A, b, 18, f, th, t, tol=1e-14)
+    assert _rel(it.x, ex.x) < 1e-10
+    assert 0 < it.lsqr_iters <= 4 * 18
+    assert krylov.run(krylov.BG_LS, A, b, 18, 0, f, th, t).x.tobytes() == it.x.tobytes()
+
+
+def test_bg_ls_polynomial_exact_and_breakdown():
+    """thm:lastcol-type exactness for a polynomial of degree <= m-1, and a diagonal
+    matrix with 5 distinct eigenvalues stops at m_used = 5 with the exact f(A)b."""
+    A, b = _small_cd(10)
+    th = sketch.make(sketch.SRHT, A.shape[0], 50, 1, 8)
+    coef = np.array([0.3, -1.2, 0.5, 2.0])  # degree 3 <= m - 1
+    x = krylov.bg_ls(A, b, 8, POLY, th, 1.0, coef=coef, exact_ls=True).x
+    Ad = A.toarray()
+    ref = sum(c * np.linalg.matrix_power(Ad, i) @ b for i, c in enumerate(coef))
+    assert _rel(x, ref) < 1e-10
+    d = np.repeat([0.5, 1.0, 2.0, 3.5, 5.0], 40)
+    D = scipy.sparse.diags(d).tocsr()
+    bd = W.random_vector(len(d), 2)
+    thd = sketch.make(sketch.SRHT, len(d), 20, 1, 8)
+    r = krylov.bg_ls(D, bd, 9, EXP, thd, -0.3)
+    assert r.m_used == 5
+    assert _rel(r.x, np.exp(-0.3 * d) * bd) < 1e-9
