@@ -172,6 +172,42 @@ def bench_mixed_same(fab, torch, Mx, bd, ref_x, stream, n: int, nnz: int, P, rep
     return out
 
 
+def bench_bg_laplacian(fab, torch, W, N: int = 80, ms=(40, 80, 160), reps: int = 3):
+    """Alg. 3 (Alg. 1 basis + LSQR) against Arnoldi on the paper's §5.1.4 setting: 3D
+    Laplacian N = 80 (n = 512,000), f = A^{-1/2}, SRHT with s = floor(1.05 m), FP64.
+    Error of both against Arnoldi with m = 320 (FP64, this library)."""
+    A = W.laplacian3d(N)
+    Mx = fab.Matrix.from_csr(A)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    b = torch.from_numpy(W.random_vector(A.n, 0)).cuda()
+    xr = torch.empty_like(b)
+    Mx.apply(b, fab.params(f=fab.INVSQRT, m=320, method=fab.ARNOLDI, stream=sp), x=xr)
+    out = {"workload": f"3D Laplacian {N}^3 (n={A.n:,}), x = A^(-1/2) b, SRHT s = floor(1.05 m), FP64; reference "
+                       "Arnoldi m=320"}
+
+    def timed(p):
+        x = torch.empty_like(b)
+        _, st = Mx.apply(b, p, x=x, stats=True)  # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            Mx.apply(b, p, x=x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr)), st
+
+    for m in ms:
+        s = int(1.05 * m)
+        t_bg, e_bg, st = timed(fab.params(f=fab.INVSQRT, m=m, s=s, sketch=fab.SRHT, seed=1, method=fab.BG_LS,
+                                          lsqr_tol=1e-6, stream=sp))
+        t_ar, e_ar, _ = timed(fab.params(f=fab.INVSQRT, m=m, method=fab.ARNOLDI, stream=sp))
+        out[f"m={m}"] = {"bg_ls_ms": t_bg, "arnoldi_ms": t_ar, "bg_ls_rel_err": e_bg, "arnoldi_rel_err": e_ar,
+                         "lsqr_iters": st.lsqr_iters, "speedup_vs_arnoldi": t_ar / t_bg}
+    return out
+
+
 def bench_batch(fab, torch, W, steps: int = 3, count: int = 256):
     """256 uneven 2D convection-diffusion solves (n log-uniform on [1e4, 1e6], t on
     [1e-4, 1e-2], m on {20..80}, k = 2, sparse sign s = 4m, zeta = 8, batch seed 3)
@@ -487,6 +523,8 @@ def run_only(args):
                **bench_mixed_same(fab, torch, Mx, bd, None, stream, A.n, A.nnz, P, reps=args.steps)}
     elif args.only == "batch":
         out = bench_batch(fab, torch, W, steps=args.steps, count=args.batch_count)
+    elif args.only == "bg":
+        out = bench_bg_laplacian(fab, torch, W)
     elif args.only == "graph":
         out = bench_mixed_graph(fab, torch, W, reps=args.steps, n=args.graph_n, references=not args.no_extras)
     else:
@@ -503,12 +541,13 @@ def main():
     ap.add_argument("--impl", default="fab", choices=["fab", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the sketched_ls / Arnoldi side measurements")
-    ap.add_argument("--extras", default="mixed,batch,graph,serving",
+    ap.add_argument("--extras", default="mixed,batch,graph,bg,serving",
                     help="side workloads measured after the main one: mixed (the same workload with an FP32 "
                          "basis), batch (256 uneven solves, one graph), "
                          "graph (4M-node power-law Laplacian, mixed precision, Gaussian sketch), serving "
-                         "(Poisson arrivals, continuous batching, p50/p99 latency)")
-    ap.add_argument("--only", choices=["mixed", "batch", "graph", "serving"], default=None,
+                         "(Poisson arrivals, continuous batching, p50/p99 latency), bg (Alg. 3 vs Arnoldi on the "
+                         "3D Laplacian)")
+    ap.add_argument("--only", choices=["mixed", "batch", "graph", "bg", "serving"], default=None,
                     help="measure one side workload alone and print its JSON (for profiler runs)")
     ap.add_argument("--serving-slots", type=int, default=16, help="server slots of the --only serving workload")
     ap.add_argument("--graph-n", type=int, default=4_000_000,
@@ -665,6 +704,8 @@ def main():
         extras["batch_256"] = bench_batch(fab, torch, W)
     if not args.no_extras and "graph" in args.extras.split(","):
         extras["mixed_graph_4M"] = bench_mixed_graph(fab, torch, W)
+    if not args.no_extras and "bg" in args.extras.split(","):
+        extras["bg_ls_laplacian3d"] = bench_bg_laplacian(fab, torch, W)
     if not args.no_extras and "serving" in args.extras.split(","):
         extras["serving"] = bench_serving(fab, torch, W)
 

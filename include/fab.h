@@ -17,6 +17,12 @@
  *   FAB_SKETCHED_FAST  eq. sFOM in its sketch-and-solve form (Remark after eq. sFOM):
  *                      y = argmin ||Theta (V_m z - v_{m+1})||, then as above.
  *   FAB_NOPROJ         Alg. 5: ||b|| V_m f(H_m) e_1 (eq. noproj).
+ *   FAB_BG_LS          Alg. 3: Alg. 1 basis (sketched Gram-Schmidt: S = Theta V
+ *                      kept orthonormal, the same coefficients applied to the
+ *                      long vectors), y by LSQR on V_m (no preconditioner), then
+ *                      r_11 V_m f(H_m + h_{m+1,m} y e_m^T) e_1. k is ignored; the
+ *                      sketch is SRHT or sparse sign (it is applied to every new
+ *                      vector before its orthogonalization).
  * The Alg. 2 basis orthogonalizes A v_{i-1} against the last k basis vectors
  * only (§2.1.2); the sketch Theta (s x n) is applied in the same pass that
  * produces each basis vector.
@@ -59,7 +65,7 @@ enum {
 };
 
 typedef enum { FAB_F_EXP = 0, FAB_F_SQRT = 1, FAB_F_INVSQRT = 2 } fab_func;
-typedef enum { FAB_ARNOLDI = 0, FAB_SKETCHED_LS = 1, FAB_SKETCHED_FAST = 2, FAB_NOPROJ = 3 } fab_method;
+typedef enum { FAB_ARNOLDI = 0, FAB_SKETCHED_LS = 1, FAB_SKETCHED_FAST = 2, FAB_NOPROJ = 3, FAB_BG_LS = 4 } fab_method;
 typedef enum { FAB_SK_SPARSE_SIGN = 0, FAB_SK_SRHT = 1, FAB_SK_GAUSSIAN = 2 } fab_sketch;
 typedef enum { FAB_FP64 = 0, FAB_MIXED = 1 } fab_precision;
 

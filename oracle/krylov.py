@@ -16,8 +16,9 @@ Readings of the paper taken here (where it is garbled or silent):
   stops with m_used = c columns.
 * Alg. 4 reuses the basis sketch Theta for the Blendenpik preconditioner, and
   LSQR starts at zero.
-* Alg. 1: gamma_b = r_11 (eq. relationxx); the breakdown rule of Alg. 2 applied
-  to r_ii against ||Theta w||; Alg. 3 runs LSQR on V_m itself.
+* Alg. 1: gamma_b = r_11 (eq. relationxx); breakdown when r_ii <= 1e-12
+  ||Theta w_i|| (the sketch, not the long vector, is orthogonalised); Alg. 3 runs
+  LSQR on V_m itself.
 """
 from __future__ import annotations
 
@@ -32,6 +33,9 @@ from . import matfun
 
 EPS = np.finfo(np.float64).eps
 ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ, BG_LS = 0, 1, 2, 3, 4
+# Alg. 1 breakdown: the sketched residual r_ii below this fraction of ||Theta w_i||
+# (far above the rounding of a sketch, far below a genuinely new direction)
+BG_BREAKDOWN = 1e-12
 
 
 def as_operator(A):
@@ -111,7 +115,7 @@ def bg_basis(A, b, m: int, sketch) -> BGBasis:
         rcc = float(np.linalg.norm(sv))
         R[:c, c] = r
         R[c, c] = rcc
-        if not rcc > 64 * EPS * float(np.linalg.norm(p)):
+        if not rcc > BG_BREAKDOWN * float(np.linalg.norm(p)):
             Vb = np.zeros((n, c + 1))
             Vb[:, :c] = V[:, :c]
             Hb = np.zeros((c + 1, c))

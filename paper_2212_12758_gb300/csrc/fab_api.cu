@@ -295,7 +295,11 @@ cudaError_t wait_stream(cudaStream_t s) {
   return e == cudaSuccess ? cudaEventSynchronize(g_wait_event) : e;
 }
 
-bool sketched(int method) { return method == FAB_SKETCHED_FAST || method == FAB_SKETCHED_LS; }
+bool sketched(int method) {
+  return method == FAB_SKETCHED_FAST || method == FAB_SKETCHED_LS || method == FAB_BG_LS;
+}
+// LSQR-based methods (Alg. 4, Alg. 3)
+bool uses_lsqr(int method) { return method == FAB_SKETCHED_LS || method == FAB_BG_LS; }
 
 int64_t next_pow2(int64_t n) {
   int64_t p = 1;
@@ -305,7 +309,7 @@ int64_t next_pow2(int64_t n) {
 
 int validate(const fab_handle* h, const fab_params* p) {
   if (p->f < 0 || p->f > 2) return FAB_EINVAL;
-  if (p->method < 0 || p->method > 3) return FAB_EINVAL;
+  if (p->method < 0 || p->method > 4) return FAB_EINVAL;
   if (p->m < 1 || p->m > kMaxM) return FAB_EINVAL;
   if (p->precision != FAB_FP64 && p->precision != FAB_MIXED) return FAB_EINVAL;
   if (p->method != FAB_ARNOLDI && (p->k < 1 || p->k > kMaxWindow)) return FAB_EINVAL;
@@ -321,7 +325,8 @@ int validate(const fab_handle* h, const fab_params* p) {
     } else {
       return FAB_EINVAL;
     }
-    if (p->method == FAB_SKETCHED_LS && !(p->lsqr_tol > 0.0)) return FAB_EINVAL;
+    if (uses_lsqr(p->method) && !(p->lsqr_tol > 0.0)) return FAB_EINVAL;
+    if (p->method == FAB_BG_LS && p->sketch == FAB_SK_GAUSSIAN) return FAB_EINVAL;  // needs Theta w per step
   }
   if (p->target_rel_err != 0.0) {  // growing m to a target: sketched methods, s embeds m_max + 1 columns
     if (!(p->target_rel_err > 0.0) || !sketched(p->method) || p->m_step < 1 || p->m_max < p->m ||
@@ -392,7 +397,7 @@ int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
       {&h->scal, 64 * 8},
       {&h->lsq, (size_t)6 * (m + 1) * 8},
       {&h->state, sizeof(DevState)},
-      {&h->u, p->method == FAB_SKETCHED_LS ? (size_t)n * 8 : 0},
+      {&h->u, uses_lsqr(p->method) ? (size_t)n * 8 : 0},
       {&h->xbuf, (size_t)n * 8},
   };
   const int cnt = (int)(sizeof(need) / sizeof(need[0]));
@@ -536,7 +541,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   // every device buffer this solve touches must exist before the first launch
   if (!W || !vals || !ws.H || !ws.st || !ws.SV || !ws.part || !ws.gpart ||
       (p->sketch == FAB_SK_GAUSSIAN && sketched(p->method) && (!ws.Wbf || !ws.G)) ||
-      (p->method == FAB_SKETCHED_LS && !ws.u))
+      (uses_lsqr(p->method) && !ws.u))
     return FAB_ENOMEM;
   const int n = h->n, k = p->k;
   const int mcap = m_cap(p);   // largest dimension this solve may grow to
@@ -624,10 +629,17 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   memset(&none, 0, sizeof(none));
   none.kind = SK_NONE;
 
-  // start vector: ||b||, sigma_0, sketch of b (Gaussian: its BF16 copy)
-  LK(PK_UPDATE, launch_update(n, W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1 | 2, ws.part, ws.counter,
-                   sk_on ? sk : none, ws.st, s));
-  if (sk_on && sk.kind != SK_GAUSS) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
+  if (p->method == FAB_BG_LS) {  // Alg. 1 start: p = Theta b, r_11 = ||p||, sigma_0 = 1 / r_11
+    LK(PK_UPDATE, launch_update(n, W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, sk,
+                                ws.st, s));
+    LK(PK_SKRED, launch_sketch_reduce(sk, nullptr, 0, sk_scale, ws.SV, ws.st, s));
+    LK(PK_SMALL, launch_bg_orth(ws.SV, p->s, 0, ws.H, ldh, ws.coef, ws.cs, ws.st, s));
+  } else {
+    // start vector: ||b||, sigma_0, sketch of b (Gaussian: its BF16 copy)
+    LK(PK_UPDATE, launch_update(n, W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1 | 2, ws.part, ws.counter,
+                                sk_on ? sk : none, ws.st, s));
+    if (sk_on && sk.kind != SK_GAUSS) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
+  }
 
   const int ntiles = (n + kTileRows - 1) / kTileRows;
   int c_done = 0;          // basis columns 1..c_done are built
@@ -639,7 +651,17 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   int mu = 0;
   for (;;) {  // one pass per dimension m (a single pass unless m grows to a target)
   for (int c = c_done + 1; c <= m; ++c) {
-    if (p->method == FAB_ARNOLDI) {
+    if (p->method == FAB_BG_LS) {
+      // Alg. 1: w = A v_{c-1}; p = Theta w; sketched Gram-Schmidt step; the same
+      // coefficients on the long vector: W_c <- W_c - sum_j coef_j W_j
+      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
+      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, sk,
+                                  ws.st, s));
+      LK(PK_SKRED, launch_sketch_reduce(sk, ws.cs.scl, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
+      LK(PK_SMALL, launch_bg_orth(ws.SV, p->s, c, ws.H, ldh, ws.coef, ws.cs, ws.st, s));
+      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, none,
+                                  ws.st, s));
+    } else if (p->method == FAB_ARNOLDI) {
       LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
       double* Hcol = ws.H + (size_t)ldh * (c - 1);
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
@@ -695,12 +717,17 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 1, ws.tau, s));
     LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.qr + (size_t)mu * p->s, ws.y, 0, nullptr, s));
     yptr = ws.y;
-  } else if (!breakdown && p->method == FAB_SKETCHED_LS) {
-    // Blendenpik: R from the QR of Theta V_m; LSQR on V_m R^{-1} u ~ v_{m+1}; y = R^{-1} u
-    CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * mu * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 0, ws.tau, s));
-    const double one = 1.0;
-    CK(cudaMemcpyAsync(ws.one, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  } else if (!breakdown && uses_lsqr(p->method)) {
+    if (p->method == FAB_SKETCHED_LS) {
+      // Blendenpik: R from the QR of Theta V_m; LSQR on V_m R^{-1} u ~ v_{m+1}; y = R^{-1} u
+      CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * mu * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 0, ws.tau, s));
+    } else {
+      // Alg. 3: LSQR on V_m itself (the Alg. 1 basis is well conditioned): R = I
+      LK(PK_SMALL, launch_set_identity(ws.qr, p->s, mdev, m, s));
+    }
+    ws.hd[8] = 1.0;
+    CK(cudaMemcpyAsync(ws.one, ws.hd + 8, sizeof(double), cudaMemcpyHostToDevice, s));
     LK(PK_COMBINE, launch_lsqr_u(n, (const TV*)W + (size_t)mu * ld, ld, 1, ws.one, ws.u, 1, ws.part, ws.counter, ws.unorm2, ws.st, s));
     LK(PK_GEMVT, launch_gemv_t(n, (const TV*)W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
     LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, nullptr, ws.lv_q, 0, nullptr, ws.st, s));

@@ -864,6 +864,124 @@ __global__ void __launch_bounds__(256) k_lu_cluster(double* __restrict__ M, int 
   }
 }
 
+// ------------------------------------------------ Alg. 1: sketched Gram-Schmidt
+// Step c of Alg. 1 on the sketches (one block). SV holds S_0..S_{c-1} (orthonormal
+// columns) and, in column c, p = Theta w_c. Computes r = S^T p, s = p - S r,
+// r_cc = ||s|| (one classical Gram-Schmidt pass), stores s / r_cc as S_c, the
+// column c-1 of H (h_{j,c-1} = r_j, h_{c,c-1} = r_cc), and for the raw basis
+// (v_j = sigma_j W_j, A v_{c-1} = scl[c] W_c) the update coefficients
+// coef_j = r_j sigma_j / scl[c] of W_c <- W_c - sum_j coef_j W_j and
+// sigma_c = scl[c] / r_cc. c = 0 (the start vector, p = Theta b): r_00 = ||p||,
+// sigma_0 = 1 / r_00 and gamma_b = r_00 into st->beta. Breakdown: r_cc <= 1e-12 ||p||
+// (the sketch is exact to 2^-49 of a chunk's largest entry) ends the basis with m_used = c.
+__global__ __launch_bounds__(256) void k_bg_orth(double* __restrict__ SV, int lds, int c, double* __restrict__ H,
+                                                 int ldh, double* __restrict__ coef, ColScale cs, DevState* st) {
+  __shared__ double s_r[kMaxM + 1];
+  __shared__ double red[2][32];
+  if (st->stop) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  double* p = SV + (size_t)lds * c;
+  for (int j = warp; j < c; j += nw) {  // r_j = <S_j, p>
+    const double* sj = SV + (size_t)lds * j;
+    double a = 0.0;
+    for (int q = lane; q < lds; q += 32) a = fma(sj[q], p[q], a);
+    a = warp_sum(a);
+    if (lane == 0) s_r[j] = a;
+  }
+  __syncthreads();
+  double ss = 0.0, pp = 0.0;
+  for (int q = tid; q < lds; q += blockDim.x) {
+    const double pq = p[q];
+    double v = pq;
+    for (int j = 0; j < c; ++j) v = fma(-SV[q + (size_t)lds * j], s_r[j], v);
+    p[q] = v;  // s (normalised below)
+    ss = fma(v, v, ss);
+    pp = fma(pq, pq, pp);
+  }
+  ss = warp_sum(ss);
+  pp = warp_sum(pp);
+  if (lane == 0) {
+    red[0][warp] = ss;
+    red[1][warp] = pp;
+  }
+  __syncthreads();
+  __shared__ double s_rcc, s_ok;
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    const double rcc = sqrt(a), pn = sqrt(b);
+    s_rcc = rcc;
+    s_ok = 1.0;
+    if (!isfinite(rcc)) {
+      st->status = FAB_ENUMERIC;
+      st->stop = 1;
+      s_ok = 0.0;
+    } else if (c == 0) {
+      st->beta = rcc;  // gamma_b = r_11
+      if (rcc == 0.0) {
+        st->m_used = 0;
+        st->stop = 1;
+        cs.sigma[0] = 0.0;
+        cs.shf[0] = 0;
+        s_ok = 0.0;
+      } else {
+        cs.sigma[0] = 1.0 / rcc;
+        cs.shf[0] = exponent_of(cs.sigma[0]);
+      }
+    } else {
+      H[c + (size_t)ldh * (c - 1)] = rcc;
+      if (!(rcc > 1e-12 * pn)) {  // far above the int64 sketch's rounding, far below a new direction
+        st->m_used = c;  // the basis spans an invariant subspace
+        st->stop = 1;
+        cs.sigma[c] = 0.0;
+        cs.shf[c] = 0;
+        s_ok = 0.0;
+      } else {
+        cs.sigma[c] = cs.scl[c] / rcc;
+        cs.shf[c] = exponent_of(cs.sigma[c]);
+      }
+    }
+  }
+  __syncthreads();
+  // column c-1 of H holds A v_{c-1} = sum_j r_j v_j + r_cc v_c, also at a breakdown
+  // (then A V_c = V_c H_c spans an invariant subspace)
+  for (int j = tid; j < c; j += blockDim.x) H[j + (size_t)ldh * (c - 1)] = s_r[j];
+  if (s_ok == 0.0) return;
+  const double inv = 1.0 / s_rcc;
+  for (int q = tid; q < lds; q += blockDim.x) p[q] *= inv;
+  if (c > 0) {
+    const double tau = cs.scl[c];
+    for (int j = tid; j < c; j += blockDim.x) coef[j] = s_r[j] * cs.sigma[j] / tau;
+  }
+}
+
+cudaError_t launch_bg_orth(double* SV, int lds, int c, double* H, int ldh, double* coef, ColScale cs, DevState* st,
+                           cudaStream_t s) {
+  if (c > kMaxM) return cudaErrorInvalidValue;
+  k_bg_orth<<<1, 256, 0, s>>>(SV, lds, c, H, ldh, coef, cs, st);
+  return cudaGetLastError();
+}
+
+// R = I in the leading mu x mu block of a rows x mu column-major matrix (ld rows):
+// LSQR on V_m itself for Alg. 3 (the Alg. 1 basis needs no preconditioner).
+__global__ void k_set_identity(double* __restrict__ R, int rows, const int* __restrict__ mdev) {
+  const int mu = *mdev;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < rows * mu; idx += gridDim.x * blockDim.x) {
+    const int i = idx % rows, j = idx / rows;
+    R[idx] = (i == j) ? 1.0 : 0.0;
+  }
+}
+
+cudaError_t launch_set_identity(double* R, int rows, const int* mdev, int mmax, cudaStream_t s) {
+  int grid = (rows * mmax + 255) / 256;
+  grid = grid < 1 ? 1 : (grid > 1024 ? 1024 : grid);
+  k_set_identity<<<grid, 256, 0, s>>>(R, rows, mdev);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------ sketched solution change
 // With Theta v_j in the columns of SV (s x (m+1), ld lds): out[0] = || SV c_new -
 // SV c_old || (c_old zero past m_old) and out[1] = || SV c_new ||, c_new of length

@@ -47,6 +47,10 @@ template <typename TV>
 cudaError_t launch_lsqr_u(int n, const TV* W, int64_t ld, int nc, const double* coef, double* u, int keep_zero,
                           double* part, unsigned* counter, double* unorm2, const DevState* st, cudaStream_t s);
 
+// Step c of Alg. 1 on the sketches (see k_bg_orth) and R = I for Alg. 3's LSQR.
+cudaError_t launch_bg_orth(double* SV, int lds, int c, double* H, int ldh, double* coef, ColScale cs, DevState* st,
+                           cudaStream_t s);
+cudaError_t launch_set_identity(double* R, int rows, const int* mdev, int mmax, cudaStream_t s);
 // out[0] = ||SV c_new - SV c_old||, out[1] = ||SV c_new|| (growing m to a target).
 cudaError_t launch_sketch_change(const double* SV, int lds, const int* mdev, const double* c_new, int m_old,
                                  const double* c_old, double* out, cudaStream_t s);

@@ -19,7 +19,7 @@ lib = ctypes.CDLL(_LIB_PATH)
 
 FAB_OK, FAB_EINVAL, FAB_ENOMEM, FAB_ECUDA, FAB_ENUMERIC, FAB_ETIMEOUT, FAB_ENOTCONV = 0, -1, -2, -3, -4, -5, -6
 EXP, SQRT, INVSQRT = 0, 1, 2
-ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ = 0, 1, 2, 3
+ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ, BG_LS = 0, 1, 2, 3, 4
 SPARSE_SIGN, SRHT, GAUSSIAN = 0, 1, 2
 FP64, MIXED = 0, 1
 
@@ -204,7 +204,7 @@ class Matrix:
             b = np.ascontiguousarray(b, dtype=np.float64)
         st = Stats()
         _check(lib.fab_apply(self._h, ctypes.byref(p), _addr(b), _addr(x), on_dev, ctypes.byref(st)), "fab_apply")
-        self._last = (p.m, p.s, p.method in (SKETCHED_FAST, SKETCHED_LS))
+        self._last = (p.m, p.s, p.method in (SKETCHED_FAST, SKETCHED_LS, BG_LS))
         return (x, st) if stats else x
 
     def set_tiling(self, rows_max: int = 256, nnz_cap: int = 2048, staged: bool = True):
