@@ -63,6 +63,13 @@ cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s) {
 
 __global__ void k_state_set_m(DevState* st, int m) { st->m_used = m; }
 
+__global__ void k_state_clear_flag(DevState* st) { st->flag = 0; }
+
+cudaError_t launch_state_clear_flag(DevState* st, cudaStream_t s) {
+  k_state_clear_flag<<<1, 1, 0, s>>>(st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_state_set_m(DevState* st, int m, cudaStream_t s) {
   k_state_set_m<<<1, 1, 0, s>>>(st, m);
   return cudaGetLastError();
@@ -844,7 +851,7 @@ __global__ __launch_bounds__(kThreads) void k_gemv_t(int n, const TV* __restrict
                                                       const TX* __restrict__ x, double* __restrict__ part,
                                                       DevState* st) {
   __shared__ TV xs[kTileRows];
-  if (st && st->stop) return;
+  if (st && (st->stop || st->flag)) return;  // flag: an LSQR loop has converged
   const int tile = blockIdx.x;
   const int r0 = tile * kTileRows;
   const int rows = min(kTileRows, n - r0);
@@ -884,7 +891,7 @@ template cudaError_t launch_gemv_t<float, double>(int, const float*, int64_t, in
 __global__ void k_reduce_cols(const double* __restrict__ part, int ntiles, int nc, const double* __restrict__ sigma,
                               int j0, const double* __restrict__ sig_col, double* __restrict__ Hcol, int h_accumulate,
                               double* __restrict__ coef, DevState* st) {
-  if (st && st->stop) return;
+  if (st && (st->stop || st->flag)) return;  // flag: an LSQR loop has converged
   const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (q >= nc) return;

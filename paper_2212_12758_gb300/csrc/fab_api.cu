@@ -25,6 +25,7 @@ namespace {
 // threshold theta_13 of that paper's Table 2.3.
 constexpr double kTheta13 = 5.371920351148152;
 constexpr int64_t kCsrPad = 4;  // spare CSR entries for the aligned tile copies
+constexpr int kLsqrPoll = 8;    // LSQR iterations between host reads of the convergence flag
 
 // Bump allocator over a caller-provided device buffer (256-byte aligned pieces).
 struct Arena8 {
@@ -728,6 +729,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     }
     ws.hd[8] = 1.0;
     CK(cudaMemcpyAsync(ws.one, ws.hd + 8, sizeof(double), cudaMemcpyHostToDevice, s));
+    LK(PK_SMALL, launch_state_clear_flag(ws.st, s));  // a previous pass (growing m) left it set
     LK(PK_COMBINE, launch_lsqr_u(n, (const TV*)W + (size_t)mu * ld, ld, 1, ws.one, ws.u, 1, ws.part, ws.counter, ws.unorm2, ws.st, s));
     LK(PK_GEMVT, launch_gemv_t(n, (const TV*)W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
     LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, nullptr, ws.lv_q, 0, nullptr, ws.st, s));
@@ -740,6 +742,9 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
       LK(PK_GEMVT, launch_gemv_t(n, (const TV*)W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
       LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, nullptr, ws.lv_q, 0, nullptr, ws.st, s));
       LK(PK_SMALL, launch_lsqr_step(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, ws.st, s));
+      // iterations after convergence are no-ops on the device, so the host reads
+      // the flag only every kLsqrPoll iterations
+      if ((it + 1) % kLsqrPoll != 0 && it + 1 != maxit) continue;
       CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
       CK(wait_stream(s));
       if (hs.status != FAB_OK) return hs.status;

@@ -232,6 +232,7 @@ constexpr int kSpmvStages = 2;   // staged tiles in flight per block (ring of sh
 
 cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s);
 cudaError_t launch_state_set_m(DevState* st, int m, cudaStream_t s);  // basis target dimension
+cudaError_t launch_state_clear_flag(DevState* st, cudaStream_t s);   // before an iteration loop
 // Column bookkeeping of the raw basis (see basis.cu): sigma[j] = 1/||W_j||,
 // shf[j] = floor(log2 sigma[j]) (the exact power of two applied when W_j is the
 // SpMV input), scl[c] = sigma[c-1] 2^-shf[c-1] in [1, 2) (A v_{c-1} = scl[c] W_c).

@@ -101,3 +101,19 @@ def test_target_parameter_checks(fab):
         fab.Batch([M], [fab.params(f=fab.EXP, t=-0.005, m=10, s=300, sketch=fab.SRHT, target_rel_err=1e-8, m_step=10,
                                    m_max=200)])
     assert e.value.code == fab.FAB_EINVAL
+
+
+@pytest.mark.parametrize("method", ["SKETCHED_LS", "BG_LS"])
+def test_growing_m_with_lsqr_methods(fab, method):
+    """Every growth pass runs its own LSQR loop; the solution at the dimension reached is
+    the single solve's at that dimension."""
+    A, b = _problem()
+    M = fab.Matrix.from_csr(A)
+    meth = getattr(fab, method)
+    p = fab.params(f=fab.EXP, t=-0.005, m=10, k=2, s=300, sketch=fab.SRHT, seed=1, method=meth, lsqr_tol=1e-12,
+                   target_rel_err=1e-8, m_step=10, m_max=200)
+    x, st = M.apply(b, p, stats=True)
+    assert 10 < st.m_used <= 200 and st.err_est <= 1e-8
+    x1 = M.apply(b, fab.params(f=fab.EXP, t=-0.005, m=st.m_used, k=2, s=300, sketch=fab.SRHT, seed=1, method=meth,
+                               lsqr_tol=1e-12))
+    assert _rel(x, x1) <= 1e-12
