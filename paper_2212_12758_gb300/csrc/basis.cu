@@ -171,9 +171,6 @@ __device__ __forceinline__ void spmv_dots_body(
   for (int tile = bid; tile < ntiles; tile += nblk, ++it) {
     const int stg = it % S;
     if (tid == 0 && bid + (it + S - 1) * nblk < ntiles && !s_fail) issue(it + S - 1);
-    bool ok = !s_fail && mbar_wait_bounded(&s_full[stg], (uint32_t)((it / S) & 1));
-    if (!ok) s_fail = 1;
-    const bool staged = ok && s_staged[stg] != 0;
     // The tile's rows share the block: L = 256 / pow2ceil(rows) lanes per row
     // (one row per thread for full tiles, the whole block for a single long row);
     // each lane sums every L-th nonzero of its row, then the lanes of a row are
@@ -182,16 +179,33 @@ __device__ __forceinline__ void spmv_dots_body(
     const int lgL = 8 - (nr > 1 ? 32 - __clz(nr - 1) : 0);
     const int L = 1 << lgL;
     const int grp = tid >> lgL, lane_r = tid & (L - 1);
-    const bool has_row = ok && grp < nr;
+    const bool in_tile = grp < nr;
     const int r = r0 + grp;
-    TV y = (TV)0;
+    // Row bounds and window entries do not need the staged nonzeros. The FP32
+    // path issues them before waiting for the tile so that their latency overlaps
+    // the copy; the FP64 path (bound by its FP64 pipe) loses more by holding them
+    // across the wait and issues them after it.
+    constexpr bool kEarly = sizeof(TV) == 4;
+    int e0 = 0, e1 = 0;
     TV wv[KW > 0 ? KW : 1];
-    if (has_row) {
-      const int e0 = A.rowptr[r], e1 = A.rowptr[r + 1];
-      if (lane_r == 0) {
+    auto load_row = [&]() {
+      if (in_tile) {
+        e0 = A.rowptr[r];
+        e1 = A.rowptr[r + 1];
+        if (lane_r == 0) {
 #pragma unroll
-        for (int q = 0; q < KW; ++q) wv[q] = W[(size_t)(j0 + q) * ld + r];  // window entries, issued early
+          for (int q = 0; q < KW; ++q) wv[q] = W[(size_t)(j0 + q) * ld + r];
+        }
       }
+    };
+    if (kEarly) load_row();
+    bool ok = !s_fail && mbar_wait_bounded(&s_full[stg], (uint32_t)((it / S) & 1));
+    if (!kEarly) load_row();
+    if (!ok) s_fail = 1;
+    const bool staged = ok && s_staged[stg] != 0;
+    const bool has_row = ok && in_tile;
+    TV y = (TV)0;
+    if (has_row) {
       int e = e0 + lane_r;
       if (staged) {
         const int base = s_e0[stg];
