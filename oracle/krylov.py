@@ -345,7 +345,12 @@ def bg_ls(A, b, m: int, f: int, sketch, t: float = 1.0, coef=None, tol: float = 
 
 
 def run(method: int, A, b, m: int, k: int, f: int, sketch=None, t: float = 1.0, **kw) -> Result:
-    """Dispatch on the library's method enum."""
+    """Dispatch on the library's method enum. f = SIGN runs the method on A^2 with
+    the starting vector A b and f = inverse square root (§5.3)."""
+    if f == matfun.SIGN:
+        b = A @ np.asarray(b, dtype=np.float64)
+        A = A @ A
+        f = matfun.INVSQRT
     if method == ARNOLDI:
         return fm_arnoldi(A, b, m, f, t, reorth=kw.get("reorth", False))
     if method == NOPROJ:

@@ -15,6 +15,9 @@ import numpy as np
 import scipy.linalg
 
 EXP, SQRT, INVSQRT, POLY = 0, 1, 2, 99
+# sign(A) b, computed as (A^2)^{-1/2} (A b) (§5.3, after Higham's Chapter 5): a
+# transformation of the problem (see krylov.run), not a function of the small H.
+SIGN = 3
 
 
 def _real(X: np.ndarray) -> np.ndarray:
@@ -69,5 +72,9 @@ def f_scalar(lam, f: int, t: float = 1.0, coef=None):
 
 
 def exact_fAb(A_dense: np.ndarray, b: np.ndarray, f: int, t: float = 1.0, coef=None) -> np.ndarray:
-    """Dense f(A) b (small n): expm / sqrtm as in the paper's reference values (§5)."""
-    return f_apply(np.asarray(A_dense, dtype=np.float64), np.asarray(b, dtype=np.float64), f, t, coef)
+    """Dense f(A) b (small n): expm / sqrtm as in the paper's reference values (§5);
+    sign by scipy's signm."""
+    A_dense = np.asarray(A_dense, dtype=np.float64)
+    if f == SIGN:
+        return _real(scipy.linalg.signm(A_dense)) @ np.asarray(b, dtype=np.float64)
+    return f_apply(A_dense, np.asarray(b, dtype=np.float64), f, t, coef)

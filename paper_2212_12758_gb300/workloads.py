@@ -53,7 +53,7 @@ def _stencil_csr(n: int, offsets, coeffs, valid_masks) -> CSR:
     mask = np.empty((n, width), dtype=bool)
     for e, (off, coef, valid) in enumerate(zip(offsets, coeffs, valid_masks)):
         cols[:, e] = (idx + off).astype(np.int32, copy=False) if valid is not None else idx.astype(np.int32)
-        vals[:, e] = coef
+        vals[:, e] = coef  # a scalar or one value per row
         mask[:, e] = True if valid is None else valid
     counts = mask.sum(axis=1, dtype=np.int64)
     rowptr = np.zeros(n + 1, dtype=np.int64)
@@ -91,6 +91,58 @@ def convdiff(dim: int, N: int, d: float = 1.0, c=None) -> CSR:
         coeffs = (lower[2], lower[1], lower[0], diag, upper, upper, upper)
         masks = (iz > 0, iy > 0, ix > 0, None, ix < N - 1, iy < N - 1, iz < N - 1)
     return _stencil_csr(n, offsets, coeffs, masks)
+
+
+def convdiff_skew(N: int, Pe: float = 200.0, d_in: float = 1000.0) -> CSR:
+    """The convection-diffusion operator of the paper's first experiment (§5.2.1),
+    on an N x N interior grid of the unit square (h = 1/(N+1), Dirichlet):
+    L[u] = -(D1 u_x)_x - (D2 u_y)_y + Pe (1/2 (v1 u_x + v2 u_y) + 1/2 ((v1 u)_x + (v2 u)_y)),
+    D1 = d_in on [0.25, 0.75]^2 and 1 elsewhere, D2 = D1 / 2, v = (x + y, x - y).
+
+    Discretisation (not given in the paper; this module's choice): diffusion by
+    the conservative 5-point scheme with D evaluated at the cell-face midpoints;
+    convection in the printed skew-symmetric form with central differences, which
+    makes the convection part of the matrix exactly skew-symmetric:
+    A[i, i+1] = Pe (v_i + v_{i+1}) / (4h) = -A[i+1, i] along each axis.
+    Rows in lexicographic order, x fastest, columns sorted."""
+    h = 1.0 / (N + 1)
+    n = N * N
+    idx = np.arange(n, dtype=np.int64)
+    ix = idx % N
+    iy = idx // N
+    x = (ix + 1) * h
+    y = (iy + 1) * h
+
+    def D1(px, py):
+        inside = (px >= 0.25) & (px <= 0.75) & (py >= 0.25) & (py <= 0.75)
+        return np.where(inside, d_in, 1.0)
+
+    dxp = D1(x + h / 2, y)
+    dxm = D1(x - h / 2, y)
+    dyp = D1(x, y + h / 2) / 2
+    dym = D1(x, y - h / 2) / 2
+    v1 = x + y
+    v2 = x - y
+    v1p, v1m = v1 + h, v1 - h  # v1 at the east / west neighbours
+    v2p, v2m = v2 - h, v2 + h  # v2 at the north / south neighbours (v2 = x - y)
+    c = Pe / (4 * h)
+    diag = (dxp + dxm + dyp + dym) / h**2
+    east = -dxp / h**2 + c * (v1 + v1p)
+    west = -dxm / h**2 - c * (v1 + v1m)
+    north = -dyp / h**2 + c * (v2 + v2p)
+    south = -dym / h**2 - c * (v2 + v2m)
+    offsets = (-N, -1, 0, 1, N)
+    coeffs = (south, west, diag, east, north)
+    masks = (iy > 0, ix > 0, None, ix < N - 1, iy < N - 1)
+    return _stencil_csr(n, offsets, coeffs, masks)
+
+
+def sine_vector(N: int) -> np.ndarray:
+    """sin(pi x) sin(pi y) on the N x N interior grid, normalised (§5.2.1)."""
+    h = 1.0 / (N + 1)
+    t = np.sin(np.pi * h * np.arange(1, N + 1))
+    b = np.outer(t, t).ravel()  # row iy, column ix: x fastest
+    return b / np.linalg.norm(b)
 
 
 def convdiff_nnz(dim: int, N: int) -> int:

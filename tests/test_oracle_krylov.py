@@ -310,3 +310,46 @@ def test_bg_ls_polynomial_exact_and_breakdown():
     r = krylov.bg_ls(D, bd, 9, EXP, thd, -0.3)
     assert r.m_used == 5
     assert _rel(r.x, np.exp(-0.3 * d) * bd) < 1e-9
+
+
+# ------------------------------------------------------------- sign(A) b
+def _shifted(N=12, mu=None):
+    """A 2D convection-diffusion matrix shifted so that its spectrum straddles the
+    imaginary axis (eigenvalues on both sides): sign(A) is a nontrivial projector."""
+    A = W.to_scipy(W.convdiff(2, N, c=(2.0, 1.0)))
+    if mu is None:
+        mu = float(np.median(np.linalg.eigvals(A.toarray()).real)) + 0.37
+    return (A - mu * scipy.sparse.identity(A.shape[0])).tocsr()
+
+
+def test_sign_formula_and_krylov_exactness():
+    """sign(A) b = (A^2)^{-1/2} (A b) (Higham Ch. 5) on a dense shifted matrix, and the
+    Krylov method on (A^2, A b) with m = n reproduces it."""
+    A = _shifted(8)  # n = 64
+    Ad = A.toarray()
+    b = W.random_vector(64, 3)
+    ref = matfun.exact_fAb(Ad, b, matfun.SIGN)
+    via = matfun.f_apply(Ad @ Ad, Ad @ b, matfun.INVSQRT)
+    assert _rel(via, ref) < 1e-10
+    S = scipy.linalg.signm(Ad).real
+    assert np.linalg.norm(S @ S - np.eye(64)) < 1e-8  # sign(A)^2 = I
+    x = krylov.run(krylov.ARNOLDI, A, b, 64, 0, matfun.SIGN, None, 1.0, reorth=True).x
+    assert _rel(x, ref) < 1e-8
+    th = sketch.make(sketch.SRHT, 64, 64, 2, 8)
+    # full window (k = m) and an orthogonal sketch: the sketched variant on (A^2, A b)
+    # is Arnoldi on (A^2, A b)
+    x3 = krylov.run(krylov.SKETCHED_FAST, A, b, 30, 30, matfun.SIGN, th, 1.0).x
+    x4 = krylov.run(krylov.ARNOLDI, A @ A, A @ b, 30, 0, matfun.INVSQRT, None, 1.0).x
+    assert _rel(x3, x4) < 1e-8
+
+
+def test_convdiff_skew_structure():
+    """The skew-form convection-diffusion operator: symmetric part = the diffusion
+    operator (Pe = 0), skew part = the convection, spectrum in the right half plane."""
+    S = W.to_scipy(W.convdiff_skew(16))
+    D = W.to_scipy(W.convdiff_skew(16, Pe=0.0))
+    assert abs((S + S.T) / 2 - D).max() < 1e-9 * abs(D).max()
+    assert abs(D - D.T).max() == 0.0
+    assert np.linalg.eigvals(S.toarray()).real.min() > 0
+    b = W.sine_vector(16)
+    assert abs(np.linalg.norm(b) - 1) < 1e-15 and np.all(b > 0)
