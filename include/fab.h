@@ -64,7 +64,11 @@ enum {
   FAB_ENOTCONV = -6   /* LSQR or the square-root iteration hit its iteration limit     */
 };
 
-typedef enum { FAB_F_EXP = 0, FAB_F_SQRT = 1, FAB_F_INVSQRT = 2 } fab_func;
+/* FAB_F_SIGN: sign(A) b computed as (A^2)^{-1/2} (A b) (§5.3): the method runs on A^2
+ * (formed once per handle on the host and kept on the device) from the starting
+ * vector A b with f = inverse square root. Single solves only (FAB_EINVAL in a
+ * batch or a server); fab_last_state / fab_last_basis then describe nothing. */
+typedef enum { FAB_F_EXP = 0, FAB_F_SQRT = 1, FAB_F_INVSQRT = 2, FAB_F_SIGN = 3 } fab_func;
 typedef enum { FAB_ARNOLDI = 0, FAB_SKETCHED_LS = 1, FAB_SKETCHED_FAST = 2, FAB_NOPROJ = 3, FAB_BG_LS = 4 } fab_method;
 typedef enum { FAB_SK_SPARSE_SIGN = 0, FAB_SK_SRHT = 1, FAB_SK_GAUSSIAN = 2 } fab_sketch;
 typedef enum { FAB_FP64 = 0, FAB_MIXED = 1 } fab_precision;

@@ -978,6 +978,22 @@ template cudaError_t launch_scale_columns<double>(int, const double*, int64_t, i
 template cudaError_t launch_scale_columns<float>(int, const float*, int64_t, int, const double*, double*, int64_t,
                                                  cudaStream_t);
 
+// y = A x, one thread per row, FP64 (the starting vector A b of sign(A) b).
+__global__ void k_csr_spmv(int n, const int* __restrict__ rowptr, const int* __restrict__ colind,
+                           const double* __restrict__ vals, const double* __restrict__ x, double* __restrict__ y) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) a = fma(vals[e], x[colind[e]], a);
+    y[r] = a;
+  }
+}
+
+cudaError_t launch_csr_spmv(int n, const int* rowptr, const int* colind, const double* vals, const double* x,
+                            double* y, cudaStream_t s) {
+  k_csr_spmv<<<grid_rows(n), kThreads, 0, s>>>(n, rowptr, colind, vals, x, y);
+  return cudaGetLastError();
+}
+
 // FP64 -> FP32 copy (start vector of the mixed-precision path)
 __global__ void k_to_f32(int n, const double* __restrict__ x, float* __restrict__ y) {
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) y[r] = (float)x[r];

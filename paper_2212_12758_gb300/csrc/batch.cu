@@ -420,7 +420,7 @@ extern "C" int fab_batch_create(fab_batch** out, fab_handle* const* hs, const fa
   for (int j = 0; j < count; ++j) {
     const fab_params& p = ps[j];
     if (!hs[j] || validate_params(hs[j], &p) != FAB_OK) return FAB_EINVAL;
-    if (p.precision != prec || p.target_rel_err != 0.0) return FAB_EINVAL;  // fixed m in a batch
+    if (p.precision != prec || p.target_rel_err != 0.0 || p.f == FAB_F_SIGN) return FAB_EINVAL;
     if (p.method != FAB_SKETCHED_FAST && p.method != FAB_NOPROJ) return FAB_EINVAL;
     if (p.method == FAB_SKETCHED_FAST && p.sketch != FAB_SK_SRHT && p.sketch != FAB_SK_SPARSE_SIGN)
       return FAB_EINVAL;

@@ -229,6 +229,8 @@ void fab_destroy(fab_handle* h) {
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  if (h->sbuf.p) cudaFree(h->sbuf.p);
+  if (h->sq) fab_destroy(h->sq);
   cudaGetLastError();
   delete h;
 }
@@ -309,7 +311,7 @@ int64_t next_pow2(int64_t n) {
 }
 
 int validate(const fab_handle* h, const fab_params* p) {
-  if (p->f < 0 || p->f > 2) return FAB_EINVAL;
+  if (p->f < 0 || p->f > 3) return FAB_EINVAL;
   if (p->method < 0 || p->method > 4) return FAB_EINVAL;
   if (p->m < 1 || p->m > kMaxM) return FAB_EINVAL;
   if (p->precision != FAB_FP64 && p->precision != FAB_MIXED) return FAB_EINVAL;
@@ -825,11 +827,89 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   return rc_final;
 }
 
+namespace {
+// A^2 of h's matrix on the host (row by row, a dense accumulator over the touched
+// columns, columns sorted), as a handle of its own.
+int build_square(fab_handle* h) {
+  const int n = h->n, nnz = h->nnz;
+  std::vector<int> ci(nnz);
+  std::vector<double> va(nnz);
+  if ((nnz > 0 && cudaMemcpy(ci.data(), h->d_colind, (size_t)nnz * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) ||
+      (nnz > 0 && cudaMemcpy(va.data(), h->d_vals, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)) {
+    cudaGetLastError();
+    return FAB_ECUDA;
+  }
+  const int* rp = h->h_rowptr;
+  std::vector<int64_t> rp2(n + 1, 0);
+  std::vector<int32_t> ci2;
+  std::vector<double> va2;
+  std::vector<double> acc(n, 0.0);
+  std::vector<char> seen(n, 0);
+  std::vector<int> cols;
+  for (int i = 0; i < n; ++i) {
+    cols.clear();
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const int k = ci[e];
+      const double a = va[e];
+      for (int f = rp[k]; f < rp[k + 1]; ++f) {
+        const int j = ci[f];
+        if (!seen[j]) {
+          seen[j] = 1;
+          cols.push_back(j);
+        }
+        acc[j] = fma(a, va[f], acc[j]);
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int j : cols) {
+      ci2.push_back(j);
+      va2.push_back(acc[j]);
+      acc[j] = 0.0;
+      seen[j] = 0;
+    }
+    rp2[i + 1] = (int64_t)ci2.size();
+  }
+  if (ci2.size() >= ((size_t)1 << 31)) return FAB_EINVAL;
+  fab_handle* sq = nullptr;
+  const int rc = fab_create(&sq, n, (int64_t)ci2.size(), rp2.data(), ci2.data(), va2.data(), 0);
+  if (rc != FAB_OK) return rc;
+  h->sq = sq;
+  return FAB_OK;
+}
+}  // namespace
+
 extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, double* x, int bx_on_device,
                          fab_stats* stats) {
   if (!h || !p || !b || !x) return FAB_EINVAL;
   int rc = validate(h, p);
   if (rc != FAB_OK) return rc;
+  if (p->f == FAB_F_SIGN) {  // sign(A) b = (A^2)^{-1/2} (A b)
+    if (!h->owns_matrix) return FAB_EINVAL;  // not on workspace clones (serving)
+    if (!h->sq && (rc = build_square(h)) != FAB_OK) return rc;
+    cudaStream_t s = (cudaStream_t)p->stream;
+    const size_t n = (size_t)h->n;
+    if (!ensure(h->sbuf, 2 * n * sizeof(double))) return FAB_ENOMEM;
+    double* db = ptr<double>(h->sbuf);
+    double* dab = db + n;
+    if (cudaMemcpyAsync(db, b, n * sizeof(double), cudaMemcpyDefault, s) != cudaSuccess ||
+        launch_csr_spmv(h->n, h->d_rowptr, h->d_colind, h->d_vals, db, dab, s) != cudaSuccess) {
+      cudaGetLastError();
+      return FAB_ECUDA;
+    }
+    fab_params q = *p;
+    q.f = FAB_F_INVSQRT;
+    double* xd = bx_on_device ? x : db;  // b is no longer needed: its buffer takes x
+    rc = fab_apply(h->sq, &q, dab, xd, 1, stats);
+    h->has_state = 0;
+    if ((rc == FAB_OK || rc == FAB_ENOTCONV) && !bx_on_device) {
+      if (cudaMemcpyAsync(x, xd, n * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return FAB_ECUDA;
+      }
+    }
+    return rc;
+  }
   Ws ws;
   rc = ensure_ws(h, p, ws);
   if (rc != FAB_OK) return rc;

@@ -316,6 +316,8 @@ template <typename TV>
 cudaError_t launch_scale_columns(int n, const TV* W, int64_t ld, int nc, const double* sigma, double* dst,
                                  int64_t ldd, cudaStream_t s);
 cudaError_t launch_to_f32(int n, const double* x, float* y, cudaStream_t s);
+cudaError_t launch_csr_spmv(int n, const int* rowptr, const int* colind, const double* vals, const double* x,
+                            double* y, cudaStream_t s);
 
 int sm_count();              // multiprocessors of the current device
 int grid_rows(int n);        // grid for the thread-per-row kernels

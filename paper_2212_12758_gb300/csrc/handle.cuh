@@ -67,6 +67,9 @@ struct fab_handle {
   uint64_t P_seed = 0;
   // pinned host scratch for the solve's small readbacks (status word, norms)
   void* h_pinned = nullptr;
+  // sign(A) b: the handle of A^2 (built on first use) and device scratch for b, A b
+  fab_handle* sq = nullptr;
+  fab::Buf sbuf;
   // last solve
   int has_state = 0, last_m = 0, last_s = 0, last_sketched = 0, last_mixed = 0, last_ldh = 0;
 };

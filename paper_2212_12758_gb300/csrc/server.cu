@@ -190,7 +190,7 @@ extern "C" int fab_server_create(fab_server** out, size_t hbm_budget_bytes, int 
 
 extern "C" int fab_server_submit(fab_server* s, fab_handle* h, const fab_params* p, const double* b,
                                  uint64_t* ticket) {
-  if (!s || !h || !p || !b || !ticket) return FAB_EINVAL;
+  if (!s || !h || !p || !b || !ticket || p->f == FAB_F_SIGN) return FAB_EINVAL;
   Request* r = new Request();
   r->h = h;
   r->p = *p;

@@ -18,7 +18,7 @@ if not os.path.exists(_LIB_PATH):
 lib = ctypes.CDLL(_LIB_PATH)
 
 FAB_OK, FAB_EINVAL, FAB_ENOMEM, FAB_ECUDA, FAB_ENUMERIC, FAB_ETIMEOUT, FAB_ENOTCONV = 0, -1, -2, -3, -4, -5, -6
-EXP, SQRT, INVSQRT = 0, 1, 2
+EXP, SQRT, INVSQRT, SIGN = 0, 1, 2, 3
 ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ, BG_LS = 0, 1, 2, 3, 4
 SPARSE_SIGN, SRHT, GAUSSIAN = 0, 1, 2
 FP64, MIXED = 0, 1

@@ -326,3 +326,50 @@ def test_bg_ls_graph_sqrt_and_breakdown(fab, torch):
     with pytest.raises(fab.FabError) as e:  # Alg. 1 sketches every new vector: no tensor-core Gaussian sketch
         M.apply(bd, fab.params(m=8, s=16, sketch=fab.GAUSSIAN, method=fab.BG_LS, precision=fab.MIXED))
     assert e.value.code == fab.FAB_EINVAL
+
+
+# ------------------------------------------------------------ sign(A) b, §5.2.1
+def _shifted_convdiff(N=16):
+    A = W.to_scipy(W.convdiff(2, N, c=(2.0, 1.0)))
+    ev = np.linalg.eigvals(A.toarray())
+    mu = float(np.median(ev.real)) + 0.37  # spectrum on both sides of the imaginary axis
+    As = (A - mu * __import__("scipy").sparse.identity(A.shape[0])).tocsr()
+    As.sort_indices()
+    return As
+
+
+@pytest.mark.parametrize("method", [krylov.ARNOLDI, krylov.SKETCHED_FAST, krylov.NOPROJ, krylov.BG_LS])
+def test_sign_via_inverse_sqrt_of_square(fab, torch, method):
+    """sign(A) b = (A^2)^{-1/2} (A b): the library forms A^2 on the host with its own
+    summation order, a relative perturbation of about (nonzeros per row) eps that the
+    inverse square root amplifies by about kappa(A^2)/2, so the bar is that bound or
+    1e-10, whichever is larger."""
+    As = _shifted_convdiff(16)
+    A = W.CSR(n=As.shape[0], rowptr=As.indptr.astype(np.int64), colind=As.indices.astype(np.int32),
+              vals=As.data.astype(np.float64))
+    b = W.random_vector(A.n, 5)
+    m, k, s = 40, 2, 120
+    th = osk.make(osk.SRHT, A.n, s, 3, 8)
+    ref = krylov.run(method, As, b, m, k, matfun.SIGN, th, 1.0, tol=1e-14)
+    A2 = (As @ As).toarray()
+    tol = max(TOL, 5 * np.finfo(float).eps * 13 * np.linalg.cond(A2) / 2)
+    _, x, st = _run_gpu(fab, torch, A, b, f=fab.SIGN, m=m, k=k, s=s, sketch=fab.SRHT, seed=3, method=method,
+                        lsqr_tol=1e-14)
+    err = _rel(x, ref.x)
+    print(f"\nsign method={method}: rel err {err:.2e} (bar {tol:.1e})")
+    assert err <= tol
+
+
+@pytest.mark.parametrize("method", [krylov.ARNOLDI, krylov.SKETCHED_FAST, krylov.SKETCHED_LS, krylov.NOPROJ,
+                                    krylov.BG_LS])
+def test_skew_convdiff_exp_all_methods(fab, torch, method):
+    """The §5.2.1 operator (skew-form convection, discontinuous diffusion, Pe = 200) with
+    the sine start vector, exp(t A), every method against the oracle."""
+    A = W.convdiff_skew(48)
+    b = W.sine_vector(48)
+    m, k, s, t = 40, 2, 160, -1e-5
+    th = osk.make(osk.SRHT, A.n, s, 1, 8)
+    ref = krylov.run(method, W.to_scipy(A), b, m, k, matfun.EXP, th, t, tol=1e-14)
+    _, x, _ = _run_gpu(fab, torch, A, b, f=fab.EXP, t=t, m=m, k=k, s=s, sketch=fab.SRHT, seed=1, method=method,
+                       lsqr_tol=1e-14)
+    assert _rel(x, ref.x) <= TOL
