@@ -208,6 +208,43 @@ def bench_bg_laplacian(fab, torch, W, N: int = 80, ms=(40, 80, 160), reps: int =
     return out
 
 
+def bench_skew_convdiff(fab, torch, W, N: int = 352, t: float = -1e-6, ms=(30, 60, 90), reps: int = 3):
+    """The paper's first experiment re-created (§5.2.1): skew-form convection-diffusion
+    with discontinuous diffusion, Pe = 200, N x N grid, b = sin(pi x) sin(pi y)
+    normalised, x = exp(t A) b (t ||A|| ~ 370; t is not given in the paper). Every method
+    at each m (SRHT s = 4m, k = 2, LSQR tol 1e-6), FP64; error against Arnoldi m = 200."""
+    A = W.convdiff_skew(N)
+    Mx = fab.Matrix.from_csr(A)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    b = torch.from_numpy(W.sine_vector(N)).cuda()
+    xr = torch.empty_like(b)
+    Mx.apply(b, fab.params(f=fab.EXP, t=t, m=200, method=fab.ARNOLDI, stream=sp), x=xr)
+    out = {"workload": f"skew-form convection-diffusion {N}x{N} (n={A.n:,}), Pe=200, D=1000 on [0.25,0.75]^2, "
+                       f"exp({t:g} A) b, b = sin(pi x) sin(pi y); reference Arnoldi m=200"}
+    names = (("noproj", fab.NOPROJ), ("sketched_fast", fab.SKETCHED_FAST), ("sketched_ls", fab.SKETCHED_LS),
+             ("bg_ls", fab.BG_LS), ("arnoldi", fab.ARNOLDI))
+    for m in ms:
+        row = {}
+        for name, meth in names:
+            p = fab.params(f=fab.EXP, t=t, m=m, k=2, s=4 * m, sketch=fab.SRHT, seed=1, method=meth, lsqr_tol=1e-6,
+                           stream=sp)
+            x = torch.empty_like(b)
+            Mx.apply(b, p, x=x)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                Mx.apply(b, p, x=x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[name] = {"ms": e0.elapsed_time(e1) / reps,
+                         "rel_err": float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))}
+        row["fastest"] = min(row, key=lambda k_: row[k_]["ms"])
+        out[f"m={m}"] = row
+    return out
+
+
 def bench_batch(fab, torch, W, steps: int = 3, count: int = 256):
     """256 uneven 2D convection-diffusion solves (n log-uniform on [1e4, 1e6], t on
     [1e-4, 1e-2], m on {20..80}, k = 2, sparse sign s = 4m, zeta = 8, batch seed 3)
@@ -525,6 +562,8 @@ def run_only(args):
         out = bench_batch(fab, torch, W, steps=args.steps, count=args.batch_count)
     elif args.only == "bg":
         out = bench_bg_laplacian(fab, torch, W)
+    elif args.only == "skew":
+        out = bench_skew_convdiff(fab, torch, W)
     elif args.only == "graph":
         out = bench_mixed_graph(fab, torch, W, reps=args.steps, n=args.graph_n, references=not args.no_extras)
     else:
@@ -541,13 +580,13 @@ def main():
     ap.add_argument("--impl", default="fab", choices=["fab", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the sketched_ls / Arnoldi side measurements")
-    ap.add_argument("--extras", default="mixed,batch,graph,bg,serving",
+    ap.add_argument("--extras", default="mixed,batch,graph,bg,skew,serving",
                     help="side workloads measured after the main one: mixed (the same workload with an FP32 "
                          "basis), batch (256 uneven solves, one graph), "
                          "graph (4M-node power-law Laplacian, mixed precision, Gaussian sketch), serving "
                          "(Poisson arrivals, continuous batching, p50/p99 latency), bg (Alg. 3 vs Arnoldi on the "
-                         "3D Laplacian)")
-    ap.add_argument("--only", choices=["mixed", "batch", "graph", "bg", "serving"], default=None,
+                         "3D Laplacian), skew (every method on the skew-form convection-diffusion problem)")
+    ap.add_argument("--only", choices=["mixed", "batch", "graph", "bg", "skew", "serving"], default=None,
                     help="measure one side workload alone and print its JSON (for profiler runs)")
     ap.add_argument("--serving-slots", type=int, default=16, help="server slots of the --only serving workload")
     ap.add_argument("--graph-n", type=int, default=4_000_000,
@@ -704,6 +743,8 @@ def main():
         extras["batch_256"] = bench_batch(fab, torch, W)
     if not args.no_extras and "graph" in args.extras.split(","):
         extras["mixed_graph_4M"] = bench_mixed_graph(fab, torch, W)
+    if not args.no_extras and "skew" in args.extras.split(","):
+        extras["skew_convdiff_352"] = bench_skew_convdiff(fab, torch, W)
     if not args.no_extras and "bg" in args.extras.split(","):
         extras["bg_ls_laplacian3d"] = bench_bg_laplacian(fab, torch, W)
     if not args.no_extras and "serving" in args.extras.split(","):
