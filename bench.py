@@ -209,7 +209,7 @@ def bench_bg_laplacian(fab, torch, W, N: int = 80, ms=(40, 80, 160), reps: int =
 
 
 def bench_skew_convdiff(fab, torch, W, N: int = 352, t: float = -1e-6, ms=(30, 60, 90), reps: int = 3):
-    """The paper's first experiment re-created (§5.2.1): skew-form convection-diffusion
+    """The paper's first experiment re-created (§5.1.1): skew-form convection-diffusion
     with discontinuous diffusion, Pe = 200, N x N grid, b = sin(pi x) sin(pi y)
     normalised, x = exp(t A) b (t ||A|| ~ 370; t is not given in the paper). Every method
     at each m (SRHT s = 4m, k = 2, LSQR tol 1e-6), FP64; error against Arnoldi m = 200."""

@@ -64,7 +64,7 @@ enum {
   FAB_ENOTCONV = -6   /* LSQR or the square-root iteration hit its iteration limit     */
 };
 
-/* FAB_F_SIGN: sign(A) b computed as (A^2)^{-1/2} (A b) (§5.3): the method runs on A^2
+/* FAB_F_SIGN: sign(A) b computed as (A^2)^{-1/2} (A b) (§5.1.3): the method runs on A^2
  * (formed once per handle on the host and kept on the device) from the starting
  * vector A b with f = inverse square root. Single solves only (FAB_EINVAL in a
  * batch or a server); fab_last_state / fab_last_basis then describe nothing. */

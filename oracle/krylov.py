@@ -19,6 +19,14 @@ Readings of the paper taken here (where it is garbled or silent):
 * Alg. 1: gamma_b = r_11 (eq. relationxx); breakdown when r_ii <= 1e-12
   ||Theta w_i|| (the sketch, not the long vector, is orthogonalised); Alg. 3 runs
   LSQR on V_m itself.
+* Whitening (§2.1.2, §5.1.3): the condition number checked after every new column
+  is kappa_1(R_i) = ||R_i||_1 ||R_i^{-1}||_1 of the thin QR Theta V_i = Q_i R_i
+  (diag(R_i) > 0), computed exactly (Matlab's condest estimates this 1-norm
+  condition number and needs a square matrix); the first i with kappa_1 > 1000
+  whitens V_i and H_{i-1}, and Alg. 1 continues with the same Theta. A basis that
+  is never whitened returns Alg. 5's approximation, a whitened one Alg. 3's (the
+  recommendation of §6). A QR column with r_ii <= 1e-12 ||Theta v_i|| is a
+  breakdown (m_used = i - 1 columns), as for Alg. 1.
 """
 from __future__ import annotations
 
@@ -32,7 +40,9 @@ import scipy.sparse
 from . import matfun
 
 EPS = np.finfo(np.float64).eps
-ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ, BG_LS = 0, 1, 2, 3, 4
+ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ, BG_LS, WHITEN = 0, 1, 2, 3, 4, 5
+# whitening threshold on kappa_1(Theta V_i) (§5.1.3)
+WHITEN_KAPPA = 1000.0
 # Alg. 1 breakdown: the sketched residual r_ii below this fraction of ||Theta w_i||
 # (far above the rounding of a sketch, far below a genuinely new direction)
 BG_BREAKDOWN = 1e-12
@@ -124,6 +134,99 @@ def bg_basis(A, b, m: int, sketch) -> BGBasis:
         S[:, c] = sv / rcc
         V[:, c] = (w - V[:, :c] @ r) / rcc
     return BGBasis(V, R[:, 1:].copy(), r11, m, S, R)
+
+
+@dataclass
+class WBasis(BGBasis):
+    wh: int = 0            # columns of V when it was whitened (0: never)
+    kappas: np.ndarray = None   # kappa_1(R_i) for i = 1 .. (checked columns)
+
+
+def _qr_pos(X):
+    """Thin QR with a positive diagonal in R (the Gram-Schmidt convention)."""
+    Q, R = np.linalg.qr(X)
+    d = np.sign(np.diag(R))
+    d[d == 0] = 1.0
+    return Q * d, R * d[:, None]
+
+
+def nt_whiten_basis(A, b, m: int, k: int, sketch, kappa_max: float = WHITEN_KAPPA, orth: str = "cgs") -> WBasis:
+    """Alg. 2 with a sketched basis and whitening (§2.1.2).
+
+    After each new column the sketch Theta V_i (i columns) is factored, Theta V_i =
+    Q_i R_i. While kappa_1(R_i) <= kappa_max the basis grows by Alg. 2. The first
+    time it exceeds kappa_max the basis becomes V_i R_i^{-1}, the Hessenberg matrix
+    R_i H_{i-1} R_{i-1}^{-1} (i x (i-1)), the sketch Theta V_i R_i^{-1} = Q_i, and
+    the remaining columns are built by Alg. 1 with the same Theta. b = ||b|| v_1
+    and v_1 = (V R^{-1}) R e_1 give gamma_b = ||b|| r_11 once whitened.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    n = b.shape[0]
+    V = np.zeros((n, m + 1))
+    H = np.zeros((m + 1, m))
+    beta = float(np.linalg.norm(b))
+    sk0 = np.asarray(sketch.apply(np.zeros(n)), dtype=np.float64).ravel()
+    S = np.zeros((sk0.shape[0], m + 1))
+    if beta == 0.0:
+        return WBasis(V[:, :1], H[:1, :0], 0.0, 0, S[:, :1], np.zeros((1, 1)), 0, np.zeros(0))
+    V[:, 0] = b / beta
+    S[:, 0] = np.asarray(sketch.apply(V[:, 0]), dtype=np.float64).ravel()
+    gamma = beta
+    wh = 0
+    Rw = None
+    kappas = [1.0]
+
+    def truncated(c):
+        Vb = np.zeros((n, c + 1))
+        Vb[:, :c] = V[:, :c]
+        Hb = np.zeros((c + 1, c))
+        Hb[:c, :c] = H[:c, :c]
+        return WBasis(Vb, Hb, gamma, c, S[:, : c + 1], Rw, wh, np.array(kappas))
+
+    for c in range(1, m + 1):
+        w = A @ V[:, c - 1]
+        if wh == 0:  # Alg. 2 step
+            wnorm = float(np.linalg.norm(w))
+            win = list(range(max(0, c - k), c))
+            if orth == "cgs":
+                h = V[:, win].T @ w
+                w = w - V[:, win] @ h
+                H[win, c - 1] = h
+            else:
+                for j in win:
+                    H[j, c - 1] = V[:, j] @ w
+                    w = w - H[j, c - 1] * V[:, j]
+            H[c, c - 1] = float(np.linalg.norm(w))
+            if not H[c, c - 1] > 64 * EPS * wnorm:
+                return truncated(c)
+            V[:, c] = w / H[c, c - 1]
+            S[:, c] = np.asarray(sketch.apply(V[:, c]), dtype=np.float64).ravel()
+            i = c + 1
+            Q, R = _qr_pos(S[:, :i])
+            if not R[c, c] > BG_BREAKDOWN * float(np.linalg.norm(S[:, c])):
+                return truncated(c)
+            kap = float(np.linalg.norm(R, 1) * np.linalg.norm(np.linalg.inv(R), 1))
+            kappas.append(kap)
+            if kap > kappa_max:  # whiten V_i, H_{i-1} and the sketch
+                Rinv = scipy.linalg.solve_triangular(R, np.eye(i), lower=False)
+                V[:, :i] = V[:, :i] @ Rinv
+                H[:i, : i - 1] = R @ H[:i, : i - 1] @ Rinv[: i - 1, : i - 1]
+                S[:, :i] = Q
+                gamma = beta * R[0, 0]
+                wh = i
+                Rw = R
+        else:  # Alg. 1 step on the whitened basis
+            p = np.asarray(sketch.apply(w), dtype=np.float64).ravel()
+            r = S[:, :c].T @ p
+            sv = p - S[:, :c] @ r
+            rcc = float(np.linalg.norm(sv))
+            H[:c, c - 1] = r
+            H[c, c - 1] = rcc
+            if not rcc > BG_BREAKDOWN * float(np.linalg.norm(p)):
+                return truncated(c)
+            S[:, c] = sv / rcc
+            V[:, c] = (w - V[:, :c] @ r) / rcc
+    return WBasis(V, H, gamma, m, S, Rw, wh, np.array(kappas))
 
 
 def _breakdown(V, H, beta, c):
@@ -325,7 +428,7 @@ def sketched_fast(A, b, m: int, k: int, f: int, sketch, t: float = 1.0, coef=Non
 def bg_ls(A, b, m: int, f: int, sketch, t: float = 1.0, coef=None, tol: float = 1e-14, maxit: int | None = None,
           exact_ls: bool = False) -> Result:
     """Alg. 3: the basis of Alg. 1, y = argmin ||V_m z - v_{m+1}|| by LSQR without a
-    preconditioner (the basis is well conditioned, §3.2), then
+    preconditioner (the basis is well conditioned, §3.1.1), then
     r_11 V_m f(H_m + h_{m+1,m} y e_m^T) e_1. ``exact_ls`` solves densely (pins)."""
     B = bg_basis(A, b, m, sketch)
     mu = B.m_used
@@ -344,9 +447,37 @@ def bg_ls(A, b, m: int, f: int, sketch, t: float = 1.0, coef=None, tol: float = 
     return Result(B.beta * (Vm @ c), mu, c, Hhat=Hhat, y=y, SV=B.S, R=B.R, lsqr_iters=iters, basis=B)
 
 
+def whiten(A, b, m: int, k: int, f: int, sketch, t: float = 1.0, coef=None, kappa_max: float = WHITEN_KAPPA,
+           tol: float = 1e-14, maxit: int | None = None, exact_ls: bool = False, final: str = "auto",
+           orth: str = "cgs") -> Result:
+    """Alg. 2 with whitening and a switch to Alg. 1 (§2.1.2), finished as §6
+    recommends: a basis that stayed well conditioned gives Alg. 5's
+    ||b|| V_m f(H_m) e_1; a whitened one Alg. 3's gamma_b V_m f(H_m + h y e_m^T) e_1
+    with y = argmin ||V_m z - v_{m+1}|| by LSQR (no preconditioner: Theta V is
+    orthonormal). ``final="noproj"`` forces Alg. 5 on the whitened basis (which
+    §3.3 shows equals eq. sFOM)."""
+    B = nt_whiten_basis(A, b, m, k, sketch, kappa_max, orth)
+    mu = B.m_used
+    if mu == 0:
+        return Result(np.zeros_like(b, dtype=np.float64), 0, np.zeros(0), basis=B)
+    Vm, iters, y = B.V[:, :mu], 0, None
+    if B.wh == 0 or final == "noproj" or mu < m:
+        Hhat = B.H[:mu, :mu]
+    else:
+        vlast = B.V[:, mu]
+        if exact_ls:
+            y = np.linalg.lstsq(Vm, vlast, rcond=None)[0]
+        else:
+            res = lsqr(lambda z: Vm @ z, lambda u: Vm.T @ u, vlast, mu, tol, maxit if maxit is not None else 4 * mu)
+            y, iters = res.x, res.iters
+        Hhat = _last_column_update(B, y)
+    c = matfun.f_e1(Hhat, f, t, coef)
+    return Result(B.beta * (Vm @ c), mu, c, Hhat=Hhat, y=y, SV=B.S, R=B.R, lsqr_iters=iters, basis=B)
+
+
 def run(method: int, A, b, m: int, k: int, f: int, sketch=None, t: float = 1.0, **kw) -> Result:
     """Dispatch on the library's method enum. f = SIGN runs the method on A^2 with
-    the starting vector A b and f = inverse square root (§5.3)."""
+    the starting vector A b and f = inverse square root (§5.1.3)."""
     if f == matfun.SIGN:
         b = A @ np.asarray(b, dtype=np.float64)
         A = A @ A
@@ -363,4 +494,7 @@ def run(method: int, A, b, m: int, k: int, f: int, sketch=None, t: float = 1.0, 
                              form=kw.get("form", "sketch_solve"))
     if method == BG_LS:
         return bg_ls(A, b, m, f, sketch, t, tol=kw.get("tol", 1e-14), maxit=kw.get("maxit"))
+    if method == WHITEN:
+        return whiten(A, b, m, k, f, sketch, t, kappa_max=kw.get("kappa_max", WHITEN_KAPPA),
+                      tol=kw.get("tol", 1e-14), maxit=kw.get("maxit"), final=kw.get("final", "auto"))
     raise ValueError("unknown method")

@@ -15,7 +15,7 @@ import numpy as np
 import scipy.linalg
 
 EXP, SQRT, INVSQRT, POLY = 0, 1, 2, 99
-# sign(A) b, computed as (A^2)^{-1/2} (A b) (§5.3, after Higham's Chapter 5): a
+# sign(A) b, computed as (A^2)^{-1/2} (A b) (§5.1.3, after Higham's Chapter 5): a
 # transformation of the problem (see krylov.run), not a function of the small H.
 SIGN = 3
 

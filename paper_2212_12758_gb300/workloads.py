@@ -94,7 +94,7 @@ def convdiff(dim: int, N: int, d: float = 1.0, c=None) -> CSR:
 
 
 def convdiff_skew(N: int, Pe: float = 200.0, d_in: float = 1000.0) -> CSR:
-    """The convection-diffusion operator of the paper's first experiment (§5.2.1),
+    """The convection-diffusion operator of the paper's first experiment (§5.1.1),
     on an N x N interior grid of the unit square (h = 1/(N+1), Dirichlet):
     L[u] = -(D1 u_x)_x - (D2 u_y)_y + Pe (1/2 (v1 u_x + v2 u_y) + 1/2 ((v1 u)_x + (v2 u)_y)),
     D1 = d_in on [0.25, 0.75]^2 and 1 elsewhere, D2 = D1 / 2, v = (x + y, x - y).
@@ -138,7 +138,7 @@ def convdiff_skew(N: int, Pe: float = 200.0, d_in: float = 1000.0) -> CSR:
 
 
 def sine_vector(N: int) -> np.ndarray:
-    """sin(pi x) sin(pi y) on the N x N interior grid, normalised (§5.2.1)."""
+    """sin(pi x) sin(pi y) on the N x N interior grid, normalised (§5.1.1)."""
     h = 1.0 / (N + 1)
     t = np.sin(np.pi * h * np.arange(1, N + 1))
     b = np.outer(t, t).ravel()  # row iy, column ix: x fastest

@@ -328,7 +328,7 @@ def test_bg_ls_graph_sqrt_and_breakdown(fab, torch):
     assert e.value.code == fab.FAB_EINVAL
 
 
-# ------------------------------------------------------------ sign(A) b, §5.2.1
+# ------------------------------------------------------------ sign(A) b, §5.1.1
 def _shifted_convdiff(N=16):
     A = W.to_scipy(W.convdiff(2, N, c=(2.0, 1.0)))
     ev = np.linalg.eigvals(A.toarray())
@@ -363,7 +363,7 @@ def test_sign_via_inverse_sqrt_of_square(fab, torch, method):
 @pytest.mark.parametrize("method", [krylov.ARNOLDI, krylov.SKETCHED_FAST, krylov.SKETCHED_LS, krylov.NOPROJ,
                                     krylov.BG_LS])
 def test_skew_convdiff_exp_all_methods(fab, torch, method):
-    """The §5.2.1 operator (skew-form convection, discontinuous diffusion, Pe = 200) with
+    """The §5.1.1 operator (skew-form convection, discontinuous diffusion, Pe = 200) with
     the sine start vector, exp(t A), every method against the oracle."""
     A = W.convdiff_skew(48)
     b = W.sine_vector(48)

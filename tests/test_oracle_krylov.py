@@ -353,3 +353,105 @@ def test_convdiff_skew_structure():
     assert np.linalg.eigvals(S.toarray()).real.min() > 0
     b = W.sine_vector(16)
     assert abs(np.linalg.norm(b) - 1) < 1e-15 and np.all(b > 0)
+
+
+# ------------------------------------------------ whitening (§2.1.2, §5.1.3)
+def test_whiten_never_triggered_is_alg5():
+    """A basis that stays below the threshold is Alg. 2's, and the method returns
+    Alg. 5's approximation bit for bit."""
+    A, b = _small_cd(12)
+    th = sketch.make(sketch.SRHT, A.shape[0], 100, 3, 8)
+    r = krylov.whiten(A, b, 25, 2, EXP, th, -0.01, kappa_max=np.inf)
+    assert r.basis.wh == 0
+    assert r.x.tobytes() == krylov.noproj(A, b, 25, 2, EXP, -0.01).x.tobytes()
+    B = krylov.nt_basis(A, b, 25, 2)
+    assert np.array_equal(r.basis.V, B.V) and np.array_equal(r.basis.H, B.H)
+
+
+@pytest.mark.parametrize("kappa_max", [5.0, 20.0, 100.0])
+def test_whiten_triggers_at_first_exceedance(kappa_max):
+    """Whitening happens after the first column i with kappa_1(R_i) > kappa_max,
+    R_i the triangular factor of the sketch of Alg. 2's basis V_i (recomputed here
+    from the Alg. 2 basis and a library QR)."""
+    A, b = _small_cd(14)
+    th = sketch.make(sketch.SRHT, A.shape[0], 120, 3, 8)
+    wb = krylov.nt_whiten_basis(A, b, 30, 2, th, kappa_max)
+    i = wb.wh
+    assert 2 <= i <= 31
+    V = krylov.nt_basis(A, b, 30, 2).V
+    SV = th.apply(V)
+
+    def kap(j):
+        return np.linalg.cond(np.linalg.qr(SV[:, :j], mode="r"), 1)
+
+    assert kap(i) > kappa_max
+    assert all(kap(j) <= kappa_max for j in range(2, i))
+
+
+@pytest.mark.parametrize("kappa_max", [5.0, 20.0, 100.0])
+def test_whitened_basis_is_alg1_basis(kappa_max):
+    """Remark after Alg. 2: Alg. 1 is Alg. 2 followed by whitening. The whitened
+    basis, its Hessenberg matrix (R H R^{-1}), its sketch (Q) and gamma_b = ||b|| r_11
+    are Alg. 1's with the same Theta, to rounding (kappa <= 150 here)."""
+    A, b = _small_cd(14)
+    th = sketch.make(sketch.SRHT, A.shape[0], 120, 3, 8)
+    wb = krylov.nt_whiten_basis(A, b, 30, 2, th, kappa_max)
+    bg = krylov.bg_basis(A, b, 30, th)
+    assert wb.wh > 0 and wb.m_used == bg.m_used == 30
+    assert _rel(wb.V, bg.V) < 1e-10
+    assert _rel(wb.H, bg.H) < 1e-10
+    assert _rel(wb.S, bg.S) < 1e-10
+    assert wb.beta == pytest.approx(bg.beta, rel=1e-14)
+    # the Arnoldi-like relation holds for the whitened pair (eq. arnoldilike)
+    res = A @ wb.V[:, :30] - wb.V @ wb.H
+    assert np.linalg.norm(res) / (scipy.sparse.linalg.norm(A) * np.linalg.norm(wb.V)) < 1e-13
+    assert np.linalg.norm(th.apply(wb.V) - wb.S) < 1e-9 * np.linalg.norm(wb.S)
+
+
+def test_whitened_alg5_equals_sfom():
+    """§3.3: Alg. 5 on the whitened Alg. 2 basis is eq. sFOM."""
+    A, b = _small_cd(14)
+    th = sketch.make(sketch.SRHT, A.shape[0], 120, 3, 8)
+    r = krylov.whiten(A, b, 30, 2, EXP, th, -0.01, kappa_max=20.0, final="noproj")
+    assert r.basis.wh > 0
+    sf = krylov.sketched_fast(A, b, 30, 2, EXP, th, -0.01, form="sfom").x
+    assert _rel(r.x, sf) < 1e-12
+
+
+def test_whiten_e3_standin_equals_arnoldi():
+    """§5.1.3 setting on a synthetic directed graph Laplacian: Alg. 2's sketch
+    passes kappa_1 = 1000 near column 60 (as the paper reports for its graph),
+    after which the method is Alg. 3 on an Alg. 1 continuation: with the
+    least-squares problem solved exactly it is the Arnoldi approximation
+    (lemma:basis), with LSQR to 1e-10 close to it."""
+    A = W.to_scipy(W.chung_lu_laplacian(3000, seed=2))
+    b = W.random_vector(3000, 7)
+    th = sketch.make(sketch.SRHT, 3000, 400, 1, 8)
+    ex = krylov.whiten(A, b, 80, 2, SQRT, th, 1.0, exact_ls=True)
+    assert 50 <= ex.basis.wh <= 70
+    ar = krylov.fm_arnoldi(A, b, 80, SQRT, 1.0, reorth=True).x
+    assert _rel(ex.x, ar) < 1e-9
+    it = krylov.whiten(A, b, 80, 2, SQRT, th, 1.0, tol=1e-12)
+    assert 0 < it.lsqr_iters <= 4 * 80 and _rel(it.x, ex.x) < 1e-9
+    assert krylov.run(krylov.WHITEN, A, b, 80, 2, SQRT, th, 1.0, tol=1e-12).x.tobytes() == it.x.tobytes()
+
+
+def test_whiten_polynomial_exact_and_breakdown():
+    """Exactness for a polynomial of degree <= m-1 through a whitened basis, and a
+    diagonal matrix with 5 distinct eigenvalues: the Alg. 1 continuation stops at
+    m_used = 5 with the exact f(A)b."""
+    A, b = _small_cd(10)
+    th = sketch.make(sketch.SRHT, A.shape[0], 50, 1, 8)
+    coef = np.array([0.3, -1.2, 0.5, 2.0])
+    r = krylov.whiten(A, b, 8, 2, POLY, th, 1.0, coef=coef, kappa_max=1.5, exact_ls=True)
+    assert r.basis.wh > 0
+    Ad = A.toarray()
+    ref = sum(c * np.linalg.matrix_power(Ad, i) @ b for i, c in enumerate(coef))
+    assert _rel(r.x, ref) < 1e-10
+    d = np.repeat([0.5, 1.0, 2.0, 3.5, 5.0], 40)
+    D = scipy.sparse.diags(d).tocsr()
+    bd = W.random_vector(len(d), 2)
+    thd = sketch.make(sketch.SRHT, len(d), 20, 1, 8)
+    rd = krylov.whiten(D, bd, 9, 2, EXP, thd, -0.3, kappa_max=1.0)
+    assert rd.basis.wh == 2 and rd.m_used == 5
+    assert _rel(rd.x, np.exp(-0.3 * d) * bd) < 1e-9
