@@ -23,6 +23,16 @@
  *                      r_11 V_m f(H_m + h_{m+1,m} y e_m^T) e_1. k is ignored; the
  *                      sketch is SRHT or sparse sign (it is applied to every new
  *                      vector before its orthogonalization).
+ *   FAB_WHITEN         Alg. 2 with whitening and a switch to Alg. 1 (§2.1.2, §5.1.3):
+ *                      after every new column the condition number
+ *                      kappa_1(R_i) = ||R_i||_1 ||R_i^{-1}||_1 of the thin QR
+ *                      Theta V_i = Q_i R_i (diag R_i > 0) is updated exactly. At the
+ *                      first kappa_1 > whiten_kappa the basis becomes V_i R_i^{-1},
+ *                      H_{i-1} becomes R_i H_{i-1} R_{i-1}^{-1}, and Alg. 1 builds
+ *                      the remaining columns with the same Theta; the solve then
+ *                      ends as FAB_BG_LS (Alg. 3, gamma_b = ||b|| r_11). A basis
+ *                      that is never whitened ends as FAB_NOPROJ (Alg. 5), as §6
+ *                      recommends. Sketch SRHT or sparse sign; fixed m only.
  * The Alg. 2 basis orthogonalizes A v_{i-1} against the last k basis vectors
  * only (§2.1.2); the sketch Theta (s x n) is applied in the same pass that
  * produces each basis vector.
@@ -69,7 +79,14 @@ enum {
  * vector A b with f = inverse square root. Single solves only (FAB_EINVAL in a
  * batch or a server); fab_last_state / fab_last_basis then describe nothing. */
 typedef enum { FAB_F_EXP = 0, FAB_F_SQRT = 1, FAB_F_INVSQRT = 2, FAB_F_SIGN = 3 } fab_func;
-typedef enum { FAB_ARNOLDI = 0, FAB_SKETCHED_LS = 1, FAB_SKETCHED_FAST = 2, FAB_NOPROJ = 3, FAB_BG_LS = 4 } fab_method;
+typedef enum {
+  FAB_ARNOLDI = 0,
+  FAB_SKETCHED_LS = 1,
+  FAB_SKETCHED_FAST = 2,
+  FAB_NOPROJ = 3,
+  FAB_BG_LS = 4,
+  FAB_WHITEN = 5
+} fab_method;
 typedef enum { FAB_SK_SPARSE_SIGN = 0, FAB_SK_SRHT = 1, FAB_SK_GAUSSIAN = 2 } fab_sketch;
 typedef enum { FAB_FP64 = 0, FAB_MIXED = 1 } fab_precision;
 
@@ -98,6 +115,9 @@ typedef struct fab_params {
   double target_rel_err;
   int m_step;
   int m_max;
+  /* FAB_WHITEN: whiten when kappa_1 of the sketched basis exceeds this (0: 1000, */
+  /* the threshold of §5.1.3; +Inf: never, i.e. Alg. 5 with the check running)   */
+  double whiten_kappa;
 } fab_params;
 
 /* Diagnostics of the last solve (all optional for the caller). */
@@ -107,12 +127,13 @@ typedef struct fab_stats {
   int fh_iters;         /* squarings (exp) or Denman-Beavers iterations           */
   int launches;         /* kernel launches issued by this solve                  */
   double h_last;        /* h_{m+1,m}                                             */
-  double beta;          /* ||b||_2                                               */
+  double beta;          /* ||b||_2 (gamma_b = ||Theta b|| for Alg. 1 and whitening) */
   double ms_basis;      /* device time of the basis (+ fused sketch) loop        */
   double ms_small;      /* device time of QR / LSQR / f(H)                       */
   double ms_combine;    /* device time of x = ||b|| V_m c                        */
   double ms_total;      /* device time of the whole solve                        */
   double err_est;       /* last sketched relative change (target mode), else 0   */
+  int whiten_at;        /* FAB_WHITEN: basis columns when it was whitened, 0: never */
 } fab_stats;
 
 typedef struct fab_handle fab_handle;

@@ -52,6 +52,7 @@ __global__ void k_state_reset(DevState* st, int m) {
   st->status = FAB_OK;
   st->flag = 0;
   st->iters = 0;
+  st->wh = 0;
   st->beta = 0.0;
   for (int i = 0; i < 16; ++i) st->scal[i] = 0.0;
 }
@@ -311,8 +312,9 @@ __global__ __launch_bounds__(kThreads) void k_spmv_dots(Csr A, TV* __restrict__ 
                                                          ColScale cs, double* __restrict__ H, int ldh,
                                                          double* __restrict__ coef, double* __restrict__ wn2,
                                                          double* __restrict__ part, unsigned* __restrict__ counter,
-                                                         DevState* st) {
+                                                         DevState* st, int gate) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  if (gate_closed(st, c, gate)) return;
   spmv_dots_body<TV, KW>(A, W, ld, c, j0, kw, cs, H, ldh, coef, wn2, part, counter, st, blockIdx.x, gridDim.x,
                          smem_raw);
 }
@@ -345,17 +347,17 @@ template int spmv_grid<float>(int, int);
 template <typename TV>
 cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int kw, ColScale cs,
                              double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
-                             DevState* st, cudaStream_t s) {
+                             DevState* st, cudaStream_t s, int gate) {
   if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kSpmvStages * kSpmvCap * (sizeof(TV) + sizeof(int));
   const int grid = spmv_grid<TV>(A.ntiles, kw);
-  void* args[] = {(void*)&A, &W, &ld, &c, &j0, &kw, &cs, &H, &ldh, &coef, &wn2, &part, &counter, &st};
+  void* args[] = {(void*)&A, &W, &ld, &c, &j0, &kw, &cs, &H, &ldh, &coef, &wn2, &part, &counter, &st, &gate};
   return cudaLaunchKernel(spmv_fn<TV>(kw), dim3(grid), dim3(kThreads), args, smem, s);
 }
 template cudaError_t launch_spmv_dots<double>(const Csr&, double*, int64_t, int, int, int, ColScale, double*, int,
-                                              double*, double*, double*, unsigned*, DevState*, cudaStream_t);
+                                              double*, double*, double*, unsigned*, DevState*, cudaStream_t, int);
 template cudaError_t launch_spmv_dots<float>(const Csr&, float*, int64_t, int, int, int, ColScale, double*, int,
-                                             double*, double*, double*, unsigned*, DevState*, cudaStream_t);
+                                             double*, double*, double*, unsigned*, DevState*, cudaStream_t, int);
 
 // ---------------------------------------------- exact int64 chunk sketches
 // A chunk of 4096 consecutive rows is converted to a common block exponent:
@@ -720,8 +722,9 @@ template <int SK, typename TV>
 __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(
     int n, TV* __restrict__ W, int64_t ld, int c, int j0, int nc, const double* __restrict__ coef,
     double* __restrict__ H, int ldh, ColScale cs, const double* __restrict__ wn2, int mode, double* __restrict__ part,
-    unsigned* __restrict__ counter, SketchDev sk, DevState* st) {
+    unsigned* __restrict__ counter, SketchDev sk, DevState* st, int gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (gate_closed(st, c, gate)) return;
   update_body<SK, TV>(n, W, ld, c, j0, nc, coef, H, ldh, cs, wn2, mode, part, counter, sk, st, blockIdx.x, gridDim.x,
                       smem_raw);
 }
@@ -764,7 +767,7 @@ template int update_grid<float>(int, int, int, int, size_t*);
 template <typename TV>
 cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H, int ldh,
                           ColScale cs, const double* wn2, int mode, double* part, unsigned* counter, SketchDev& sk,
-                          DevState* st, cudaStream_t s) {
+                          DevState* st, cudaStream_t s, int gate) {
   size_t smem = 0;
   const int kind = (sk.kind == SK_SPARSE && sk.pat) ? SK_SPARSE_TAB : sk.kind;
   const int grid = update_grid<TV>(kind, n, nc, sk.s, &smem);
@@ -772,15 +775,15 @@ cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const
   const void* fn = update_fn<TV>(kind);
   sk.nparts = grid;  // one sketch partial per block
   void* args[] = {&n, &W, &ld, &c, &j0, &nc, (void*)&coef, &H, &ldh, &cs, (void*)&wn2, &mode, &part, &counter,
-                  &sk, &st};
+                  &sk, &st, &gate};
   return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, s);
 }
 template cudaError_t launch_update<double>(int, double*, int64_t, int, int, int, const double*, double*, int,
                                            ColScale, const double*, int, double*, unsigned*, SketchDev&, DevState*,
-                                           cudaStream_t);
+                                           cudaStream_t, int);
 template cudaError_t launch_update<float>(int, float*, int64_t, int, int, int, const double*, double*, int, ColScale,
                                           const double*, int, double*, unsigned*, SketchDev&, DevState*,
-                                          cudaStream_t);
+                                          cudaStream_t, int);
 
 // ---------------------------------------------- cross-block sketch reduce
 // out[q] = scale * sigma[col] * sum_blocks part[block][q] (the per-block partials
@@ -800,15 +803,16 @@ __device__ __forceinline__ void sketch_reduce_body(const SketchDev& sk, int npar
 }
 
 __global__ void k_sketch_reduce(SketchDev sk, const double* __restrict__ sigma, int col, double scale,
-                                double* __restrict__ out, DevState* st) {
+                                double* __restrict__ out, DevState* st, int gate) {
+  if (gate_closed(st, col, gate)) return;
   sketch_reduce_body(sk, sk.nparts, sigma, col, scale, out, st, blockIdx.x);
 }
 
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
-                                 DevState* st, cudaStream_t s) {
+                                 DevState* st, cudaStream_t s, int gate) {
   const int warps_per_block = 8;
   const int grid = (sk.s + warps_per_block - 1) / warps_per_block;
-  k_sketch_reduce<<<grid, warps_per_block * 32, 0, s>>>(sk, sigma, col, scale, out, st);
+  k_sketch_reduce<<<grid, warps_per_block * 32, 0, s>>>(sk, sigma, col, scale, out, st, gate);
   return cudaGetLastError();
 }
 
@@ -954,6 +958,33 @@ template cudaError_t launch_combine<double>(int, const double*, int64_t, int, co
                                             cudaStream_t);
 template cudaError_t launch_combine<float>(int, const float*, int64_t, int, const double*, double*, double,
                                            cudaStream_t);
+
+// ------------------------------------------------- explicit whitened column
+// W_c <- sum_{q<=c} coef[q] W_q, row by row: a thread reads all of its row before
+// writing it and no other thread touches that row, so the update is in place.
+template <typename TV>
+__global__ __launch_bounds__(kThreads) void k_whiten_column(int n, TV* __restrict__ W, int64_t ld, int c,
+                                                             const double* __restrict__ coef, DevState* st) {
+  extern __shared__ double s_cf[];
+  if (st->stop || *(volatile const int*)&st->wh != c + 1) return;
+  for (int i = threadIdx.x; i <= c; i += kThreads) s_cf[i] = coef[i];
+  __syncthreads();
+  for (int r = blockIdx.x * kThreads + threadIdx.x; r < n; r += gridDim.x * kThreads) {
+    double a = 0.0;
+    for (int q = 0; q <= c; ++q) a = fma(s_cf[q], (double)W[(size_t)q * ld + r], a);
+    W[(size_t)c * ld + r] = (TV)a;
+  }
+}
+
+template <typename TV>
+cudaError_t launch_whiten_column(int n, TV* W, int64_t ld, int c, const double* coef, DevState* st,
+                                 cudaStream_t s) {
+  if (c < 0 || c > kMaxM) return cudaErrorInvalidValue;
+  k_whiten_column<TV><<<grid_rows(n), kThreads, (size_t)(c + 1) * 8, s>>>(n, W, ld, c, coef, st);
+  return cudaGetLastError();
+}
+template cudaError_t launch_whiten_column<double>(int, double*, int64_t, int, const double*, DevState*, cudaStream_t);
+template cudaError_t launch_whiten_column<float>(int, float*, int64_t, int, const double*, DevState*, cudaStream_t);
 
 // dst_j = sigma_j W_j (normalized basis for inspection)
 template <typename TV>

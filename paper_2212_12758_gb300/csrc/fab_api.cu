@@ -225,7 +225,7 @@ void fab_destroy(fab_handle* h) {
   }
   Buf* bufs[] = {&h->spat, &h->W32, &h->Wbf, &h->G, &h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
                  &h->skpart, &h->SV, &h->P,     &h->qr,  &h->tau,  &h->y,    &h->cvec,    &h->dense,
-                 &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state};
+                 &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state, &h->whm};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -299,10 +299,12 @@ cudaError_t wait_stream(cudaStream_t s) {
 }
 
 bool sketched(int method) {
-  return method == FAB_SKETCHED_FAST || method == FAB_SKETCHED_LS || method == FAB_BG_LS;
+  return method == FAB_SKETCHED_FAST || method == FAB_SKETCHED_LS || method == FAB_BG_LS || method == FAB_WHITEN;
 }
-// LSQR-based methods (Alg. 4, Alg. 3)
-bool uses_lsqr(int method) { return method == FAB_SKETCHED_LS || method == FAB_BG_LS; }
+// LSQR-based methods (Alg. 4, Alg. 3; whitening ends in Alg. 3 once whitened)
+bool uses_lsqr(int method) { return method == FAB_SKETCHED_LS || method == FAB_BG_LS || method == FAB_WHITEN; }
+// Whitening threshold of a FAB_WHITEN solve (0 selects the paper's 1000).
+double whiten_kappa(const fab_params* p) { return p->whiten_kappa > 0.0 ? p->whiten_kappa : 1000.0; }
 
 int64_t next_pow2(int64_t n) {
   int64_t p = 1;
@@ -312,7 +314,7 @@ int64_t next_pow2(int64_t n) {
 
 int validate(const fab_handle* h, const fab_params* p) {
   if (p->f < 0 || p->f > 3) return FAB_EINVAL;
-  if (p->method < 0 || p->method > 4) return FAB_EINVAL;
+  if (p->method < 0 || p->method > 5) return FAB_EINVAL;
   if (p->m < 1 || p->m > kMaxM) return FAB_EINVAL;
   if (p->precision != FAB_FP64 && p->precision != FAB_MIXED) return FAB_EINVAL;
   if (p->method != FAB_ARNOLDI && (p->k < 1 || p->k > kMaxWindow)) return FAB_EINVAL;
@@ -329,8 +331,10 @@ int validate(const fab_handle* h, const fab_params* p) {
       return FAB_EINVAL;
     }
     if (uses_lsqr(p->method) && !(p->lsqr_tol > 0.0)) return FAB_EINVAL;
-    if (p->method == FAB_BG_LS && p->sketch == FAB_SK_GAUSSIAN) return FAB_EINVAL;  // needs Theta w per step
+    // Alg. 1 and whitening need Theta w at every step (the Gaussian sketch is applied once, at the end)
+    if ((p->method == FAB_BG_LS || p->method == FAB_WHITEN) && p->sketch == FAB_SK_GAUSSIAN) return FAB_EINVAL;
   }
+  if (p->method == FAB_WHITEN && (!(p->whiten_kappa >= 0.0) || p->target_rel_err != 0.0)) return FAB_EINVAL;
   if (p->target_rel_err != 0.0) {  // growing m to a target: sketched methods, s embeds m_max + 1 columns
     if (!(p->target_rel_err > 0.0) || !sketched(p->method) || p->m_step < 1 || p->m_max < p->m ||
         p->m_max > kMaxM || p->s < p->m_max + 1)
@@ -350,6 +354,7 @@ struct Ws {
   double *W, *H, *sigma, *wn2, *coef, *part, *gpart, *skpart, *SV, *qr, *tau, *y, *cvec, *scal, *u, *xbuf;
   double* mats[9];
   double *lv_v, *lv_w, *lv_x, *lv_z, *lv_coef, *lv_q, *unorm2, *one;
+  double *wR, *wRi, *wT, *wcoef, *wnrm;  // FAB_WHITEN (ld m+1)
   unsigned* counter;
   int *P, *piv;
   DevState* st;
@@ -402,6 +407,7 @@ int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
       {&h->state, sizeof(DevState)},
       {&h->u, uses_lsqr(p->method) ? (size_t)n * 8 : 0},
       {&h->xbuf, (size_t)n * 8},
+      {&h->whm, p->method == FAB_WHITEN ? (3 * (size_t)(m + 1) * (m + 1) + (m + 1) + 8) * 8 : 0},
   };
   const int cnt = (int)(sizeof(need) / sizeof(need[0]));
   for (int i = 0; i < cnt; ++i) out[i] = need[i];
@@ -415,7 +421,7 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
   const int m = m_cap(p);
   for (int i = 0; i < cnt; ++i) {
     auto& q = need[i];
-    if (q.bytes == 0 && (q.b == &h->u || q.b == &h->xbuf)) continue;  // allocated on demand
+    if (q.bytes == 0 && (q.b == &h->u || q.b == &h->xbuf || q.b == &h->whm)) continue;  // allocated on demand
     const bool grow = q.b->bytes < (q.bytes ? q.bytes : 16);
     if (grow && fault_hit()) return FAB_ENOMEM;
     if (!ensure(*q.b, q.bytes)) return FAB_ENOMEM;
@@ -451,6 +457,15 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
   ws.lv_q = l + 5 * (m + 1);
   ws.unorm2 = ws.scal + 8;
   ws.one = ws.scal + 9;
+  {
+    double* w = ptr<double>(h->whm);
+    const size_t sq = (size_t)(m + 1) * (m + 1);
+    ws.wR = w;
+    ws.wRi = w ? w + sq : nullptr;
+    ws.wT = w ? w + 2 * sq : nullptr;
+    ws.wcoef = w ? w + 3 * sq : nullptr;
+    ws.wnrm = w ? w + 3 * sq + (m + 1) : nullptr;
+  }
   ws.counter = ptr<unsigned>(h->counter);
   ws.P = ptr<int>(h->P);
   ws.piv = ptr<int>(h->piv);
@@ -544,7 +559,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   // every device buffer this solve touches must exist before the first launch
   if (!W || !vals || !ws.H || !ws.st || !ws.SV || !ws.part || !ws.gpart ||
       (p->sketch == FAB_SK_GAUSSIAN && sketched(p->method) && (!ws.Wbf || !ws.G)) ||
-      (uses_lsqr(p->method) && !ws.u))
+      (uses_lsqr(p->method) && !ws.u) || (p->method == FAB_WHITEN && !ws.wR))
     return FAB_ENOMEM;
   const int n = h->n, k = p->k;
   const int mcap = m_cap(p);   // largest dimension this solve may grow to
@@ -553,6 +568,8 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   const int64_t ld = h->ld;
   const int ldh = mcap + 1;
   const bool sk_on = sketched(p->method);
+  const bool whiten = p->method == FAB_WHITEN;
+  const int ldr = mcap + 1;  // whitening: R, R^{-1} and scratch are ldr x ldr
   const int* mdev = &ws.st->m_used;
   Csr A{h->n, h->nnz, h->d_rowptr, h->d_colind, vals, h->d_tiles, h->ntiles, h->tile_staged};
   h->has_state = 0;
@@ -642,6 +659,9 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     LK(PK_UPDATE, launch_update(n, W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1 | 2, ws.part, ws.counter,
                                 sk_on ? sk : none, ws.st, s));
     if (sk_on && sk.kind != SK_GAUSS) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
+    if (whiten)  // R = (||Theta v_1||), Q = Theta v_1 / r_11
+      LK(PK_SMALL, launch_wh_check(ws.SV, p->s, 0, ws.qr, ws.wR, ws.wRi, ws.wT, ldr, ws.H, ldh, whiten_kappa(p),
+                                   ws.wcoef, ws.wnrm, ws.cs, ws.st, s));
   }
 
   const int ntiles = (n + kTileRows - 1) / kTileRows;
@@ -652,6 +672,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   int lsqr_iters = 0, fh_iters = 0;
   DevState& hs = *ws.hs;
   int mu = 0;
+  int wh = 0;  // FAB_WHITEN: > 0 once the basis was whitened at wh columns
   for (;;) {  // one pass per dimension m (a single pass unless m grows to a target)
   for (int c = c_done + 1; c <= m; ++c) {
     if (p->method == FAB_BG_LS) {
@@ -664,6 +685,27 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
       LK(PK_SMALL, launch_bg_orth(ws.SV, p->s, c, ws.H, ldh, ws.coef, ws.cs, ws.st, s));
       LK(PK_UPDATE, launch_update(n, W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, none,
                                   ws.st, s));
+    } else if (whiten) {
+      // Both step sequences are queued; the gates let one of them run (1: Alg. 2
+      // until the basis is whitened, 2: Alg. 1 afterwards), so the switch needs
+      // no host round trip.
+      const int j0 = std::max(0, c - k), kw = c - j0;
+      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, j0, kw, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
+                                   s, 1));
+      LK(PK_UPDATE, launch_update(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part, ws.counter, sk,
+                                  ws.st, s, 1));
+      LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s, 1));
+      LK(PK_SMALL, launch_wh_check(ws.SV, p->s, c, ws.qr, ws.wR, ws.wRi, ws.wT, ldr, ws.H, ldh, whiten_kappa(p),
+                                   ws.wcoef, ws.wnrm, ws.cs, ws.st, s));
+      LK(PK_COMBINE, launch_whiten_column(n, W, ld, c, ws.wcoef, ws.st, s));
+      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
+                                   s, 2));
+      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, sk,
+                                  ws.st, s, 2));
+      LK(PK_SKRED, launch_sketch_reduce(sk, ws.cs.scl, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s, 2));
+      LK(PK_SMALL, launch_bg_orth(ws.SV, p->s, c, ws.H, ldh, ws.coef, ws.cs, ws.st, s, ws.wRi, ldr, 2));
+      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, none,
+                                  ws.st, s, 2));
     } else if (p->method == FAB_ARNOLDI) {
       LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
       double* Hcol = ws.H + (size_t)ldh * (c - 1);
@@ -713,6 +755,8 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     return FAB_OK;
   }
   const bool breakdown = mu < m;
+  wh = whiten ? hs.wh : 0;
+  const bool lsqr = !breakdown && (p->method == FAB_SKETCHED_LS || p->method == FAB_BG_LS || wh > 0);
   const double* yptr = nullptr;
   if (!breakdown && p->method == FAB_SKETCHED_FAST) {
     // y = argmin || Theta V_m z - Theta v_{m+1} || (sketch-and-solve form of eq. sFOM)
@@ -720,11 +764,15 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 1, ws.tau, s));
     LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.qr + (size_t)mu * p->s, ws.y, 0, nullptr, s));
     yptr = ws.y;
-  } else if (!breakdown && uses_lsqr(p->method)) {
+  } else if (lsqr) {
     if (p->method == FAB_SKETCHED_LS) {
       // Blendenpik: R from the QR of Theta V_m; LSQR on V_m R^{-1} u ~ v_{m+1}; y = R^{-1} u
       CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * mu * sizeof(double), cudaMemcpyDeviceToDevice, s));
       LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 0, ws.tau, s));
+    } else if (wh > 0) {
+      // Alg. 3 on the whitened basis: LSQR on the stored columns with the implicit
+      // R_{wh-1}^{-1} as right preconditioner; u is y in whitened coordinates
+      LK(PK_SMALL, launch_wh_precond(ws.wR, ldr, wh, ws.qr, p->s, mdev, m, s));
     } else {
       // Alg. 3: LSQR on V_m itself (the Alg. 1 basis is well conditioned): R = I
       LK(PK_SMALL, launch_set_identity(ws.qr, p->s, mdev, m, s));
@@ -757,8 +805,12 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     }
     lsqr_iters = hs.iters;
     if (!converged) return FAB_ENOTCONV;
-    LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.lv_x, ws.y, 0, nullptr, s));
-    yptr = ws.y;
+    if (wh > 0) {
+      yptr = ws.lv_x;
+    } else {
+      LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.lv_x, ws.y, 0, nullptr, s));
+      yptr = ws.y;
+    }
   }
   // f(H_m + h y e_m^T) e_1
   if (p->f == FAB_F_EXP) {
@@ -788,7 +840,8 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   LK(PK_SMALL, launch_state_set_m(ws.st, m, s));
   }  // growing m
   CK(cudaEventRecord(ev[2], s));
-  // x = ||b|| V_m c
+  if (wh > 0) LK(PK_SMALL, launch_wh_coef(ws.wRi, ldr, wh, mdev, ws.cvec, s));  // to the stored columns
+  // x = ||b|| V_m c  (gamma_b for Alg. 1 and a whitened basis)
   LK(PK_COMBINE, launch_prep_coef(ws.cvec, ws.sigma, mdev, ws.st, ws.coef, s));
   double* xdst = x;
   if (!bx_on_device) {
@@ -809,6 +862,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     stats->m_used = mu;
     stats->lsqr_iters = lsqr_iters;
     stats->fh_iters = fh_iters;
+    stats->whiten_at = wh;
     stats->launches = g_launches;
     stats->beta = hs.beta;
     double hl = 0.0;
@@ -1229,7 +1283,7 @@ size_t handle_ws_bytes(const fab_handle* h) {
   const Buf* bufs[] = {&h->spat, &h->W32, &h->Wbf, &h->G,    &h->shf,  &h->scl,  &h->W,   &h->H,     &h->sigma,
                        &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart, &h->skpart, &h->SV, &h->P,
                        &h->qr,  &h->tau, &h->y,    &h->cvec, &h->dense, &h->piv, &h->scal, &h->lsq,
-                       &h->u,   &h->xbuf, &h->state};
+                       &h->u,   &h->xbuf, &h->state, &h->whm};
   size_t t = 0;
   for (const Buf* b : bufs) t += b->bytes;
   if (h->d_vals32) t += (size_t)(h->nnz + kCsrPad) * sizeof(float);

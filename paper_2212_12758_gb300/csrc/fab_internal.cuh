@@ -32,7 +32,7 @@ struct DevState {
   int status;    // FAB_OK or the device-detected error
   int flag;      // iteration-loop flag (LSQR / square-root iteration converged)
   int iters;     // iteration count reported by the loops
-  int pad;
+  int wh;        // basis columns when it was whitened (FAB_WHITEN), 0: not whitened
   double beta;   // ||b||_2
   double scal[16];  // scalars of the small-stage loops (LSQR recurrence, DB scaling)
 };
@@ -215,6 +215,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Phase gate of a basis-step kernel of FAB_WHITEN (the launch argument `gate`):
+// 0 runs always, 1 only while column c is built by Alg. 2 (not yet whitened),
+// 2 only once it is built by Alg. 1 (the basis was whitened with wh <= c
+// columns). Every block of a gated-off launch returns before touching memory.
+__device__ __forceinline__ bool gate_closed(const DevState* st, int c, int gate) {
+  if (gate == 0) return false;
+  const int wh = *(volatile const int*)&st->wh;
+  const bool bg = wh > 0 && c >= wh;
+  return gate == 1 ? bg : !bg;
+}
+
 // ----------------------------------------------------------------- launchers
 // (defined in basis.cu / small.cu; all take the stream last and return cudaError_t)
 struct Csr {
@@ -244,13 +255,13 @@ struct ColScale {
 template <typename TV>
 cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int kw, ColScale cs,
                              double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
-                             DevState* st, cudaStream_t s);
+                             DevState* st, cudaStream_t s, int gate = 0);
 template <typename TV>
 cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
                           int ldh, ColScale cs, const double* wn2, int mode, double* part, unsigned* counter,
-                          SketchDev& sk, DevState* st, cudaStream_t s);
+                          SketchDev& sk, DevState* st, cudaStream_t s, int gate = 0);
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
-                                 DevState* st, cudaStream_t s);
+                                 DevState* st, cudaStream_t s, int gate = 0);
 // The sparse sign pattern of sk (rows and signs of every column) into pat (n x pat_stride(zeta)).
 cudaError_t launch_sparse_pattern(int n, const SketchDev& sk, unsigned short* pat, cudaStream_t s);
 
@@ -315,6 +326,12 @@ cudaError_t launch_combine(int n, const TV* W, int64_t ld, int nc, const double*
 template <typename TV>
 cudaError_t launch_scale_columns(int n, const TV* W, int64_t ld, int nc, const double* sigma, double* dst,
                                  int64_t ldd, cudaStream_t s);
+// Whitening of FAB_WHITEN: when the basis was whitened at this step (st->wh == c+1),
+// column c becomes sum_{q<=c} coef[q] W_q (the explicit whitened vector, unit
+// scale), in place; otherwise every block returns at once.
+template <typename TV>
+cudaError_t launch_whiten_column(int n, TV* W, int64_t ld, int c, const double* coef, DevState* st,
+                                 cudaStream_t s);
 cudaError_t launch_to_f32(int n, const double* x, float* y, cudaStream_t s);
 cudaError_t launch_csr_spmv(int n, const int* rowptr, const int* colind, const double* vals, const double* x,
                             double* y, cudaStream_t s);

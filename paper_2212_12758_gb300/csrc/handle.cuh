@@ -55,6 +55,7 @@ struct fab_handle {
   fab::Buf W, H, sigma, shf, scl, wn2, coef, part, counter, gpart, skpart, SV, P, qr, tau, y, cvec, dense, piv, scal, lsq, u, xbuf,
       state;
   fab::Buf W32, Wbf, G;  // mixed path: FP32 basis, its BF16 copy, Gaussian sketch (BF16, s x ld)
+  fab::Buf whm;          // FAB_WHITEN: R, R^{-1}, scratch ((m+1)^2 each), coefficients, norms
   int G_n = -1, G_s = -1;
   uint64_t G_seed = 0;
   // cached sparse sign pattern (zeta x n, see SketchDev::pat)

@@ -875,10 +875,11 @@ __global__ void __launch_bounds__(256) k_lu_cluster(double* __restrict__ M, int 
 // sigma_0 = 1 / r_00 and gamma_b = r_00 into st->beta. Breakdown: r_cc <= 1e-12 ||p||
 // (the sketch is exact to 2^-49 of a chunk's largest entry) ends the basis with m_used = c.
 __global__ __launch_bounds__(256) void k_bg_orth(double* __restrict__ SV, int lds, int c, double* __restrict__ H,
-                                                 int ldh, double* __restrict__ coef, ColScale cs, DevState* st) {
+                                                 int ldh, double* __restrict__ coef, ColScale cs, DevState* st,
+                                                 const double* __restrict__ Ri, int ldr, int gate) {
   __shared__ double s_r[kMaxM + 1];
   __shared__ double red[2][32];
-  if (st->stop) return;
+  if (st->stop || gate_closed(st, c, gate)) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   double* p = SV + (size_t)lds * c;
   for (int j = warp; j < c; j += nw) {  // r_j = <S_j, p>
@@ -953,15 +954,225 @@ __global__ __launch_bounds__(256) void k_bg_orth(double* __restrict__ SV, int ld
   const double inv = 1.0 / s_rcc;
   for (int q = tid; q < lds; q += blockDim.x) p[q] *= inv;
   if (c > 0) {
+    // After whitening at wh columns (FAB_WHITEN) the whitened vectors 0..wh-2 are
+    // V R_{wh-1}^{-1} of the stored Alg. 2 columns: the coefficient of stored
+    // column j < wh-1 is (R_{wh-1}^{-1} r)_j.
+    const int wh = Ri ? st->wh : 0;
+    const int nt = wh > 1 ? (wh - 1 < c ? wh - 1 : c) : 0;
     const double tau = cs.scl[c];
-    for (int j = tid; j < c; j += blockDim.x) coef[j] = s_r[j] * cs.sigma[j] / tau;
+    for (int j = tid; j < c; j += blockDim.x) {
+      double r = s_r[j];
+      if (j < nt) {
+        r = 0.0;
+        for (int l = j; l < nt; ++l) r = fma(Ri[j + (size_t)ldr * l], s_r[l], r);
+      }
+      coef[j] = r * cs.sigma[j] / tau;
+    }
   }
 }
 
 cudaError_t launch_bg_orth(double* SV, int lds, int c, double* H, int ldh, double* coef, ColScale cs, DevState* st,
-                           cudaStream_t s) {
+                           cudaStream_t s, const double* Ri, int ldr, int gate) {
   if (c > kMaxM) return cudaErrorInvalidValue;
-  k_bg_orth<<<1, 256, 0, s>>>(SV, lds, c, H, ldh, coef, cs, st);
+  k_bg_orth<<<1, 256, 0, s>>>(SV, lds, c, H, ldh, coef, cs, st, Ri, ldr, gate);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ whitening (FAB_WHITEN)
+// Step c of Alg. 2 with whitening (§2.1.2), on one CTA, after column c and its
+// sketch y = Theta v_c (SV column c) exist. The thin QR Theta V_{c+1} = Q R grows
+// by one column (classical Gram-Schmidt applied twice against Q's columns; R
+// column c = the summed projections and rho = ||y - Q r||), R^{-1} by one column
+// (-R_c^{-1} r / rho and 1 / rho), and ||R||_1, ||R^{-1}||_1 (max column sums;
+// appending a column leaves the others unchanged) are kept in nrm[0..1], so
+// kappa_1(R_{c+1}) is exact. rho <= 1e-12 ||y|| stops the basis at c columns.
+// At the first kappa_1 > kmax the basis is whitened at wh = c+1 columns:
+//   H_{c} (rows 0..c, columns 0..c-1) <- R_{c+1} H_c R_c^{-1},
+//   SV columns 0..c <- Q,  gamma_b <- ||b|| r_00,
+//   wcoef[q] = (R^{-1})_{q,c} sigma_q (the explicit whitened column c, written by
+//   launch_whiten_column), sigma_c <- 1 and shf_c <- 0 (it is stored at unit scale),
+// while columns 0..c-1 stay stored as Alg. 2 vectors with R_c^{-1} applied
+// implicitly (k_bg_orth, k_wh_coef). Scratch T holds (c+1) x c values.
+__global__ __launch_bounds__(256) void k_wh_check(double* __restrict__ SV, int lds, int c, double* __restrict__ Q,
+                                                  double* __restrict__ R, double* __restrict__ Ri,
+                                                  double* __restrict__ T, int ldr, double* __restrict__ H, int ldh,
+                                                  double kmax, double* __restrict__ wcoef, double* __restrict__ nrm,
+                                                  ColScale cs, DevState* st) {
+  __shared__ double s_r[kMaxM + 1];
+  __shared__ double s_t[kMaxM + 1];
+  __shared__ double red[2][32];
+  __shared__ double s_rho;
+  __shared__ int s_go;
+  if (st->stop || *(volatile int*)&st->wh != 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, bd = blockDim.x;
+  const double* y = SV + (size_t)lds * c;
+  double* q = Q + (size_t)lds * c;
+  double yy = 0.0;
+  for (int i = tid; i < lds; i += bd) {
+    q[i] = y[i];
+    yy = fma(y[i], y[i], yy);
+  }
+  for (int j = tid; j < c; j += bd) s_r[j] = 0.0;
+  __syncthreads();
+  for (int pass = 0; pass < 2 && c > 0; ++pass) {
+    for (int j = warp; j < c; j += nw) {
+      const double* qj = Q + (size_t)lds * j;
+      double a = 0.0;
+      for (int i = lane; i < lds; i += 32) a = fma(qj[i], q[i], a);
+      a = warp_sum(a);
+      if (lane == 0) s_t[j] = a;
+    }
+    __syncthreads();
+    for (int i = tid; i < lds; i += bd) {
+      double v = q[i];
+      for (int j = 0; j < c; ++j) v = fma(-Q[i + (size_t)lds * j], s_t[j], v);
+      q[i] = v;
+    }
+    for (int j = tid; j < c; j += bd) s_r[j] += s_t[j];
+    __syncthreads();
+  }
+  double qq = 0.0;
+  for (int i = tid; i < lds; i += bd) qq = fma(q[i], q[i], qq);
+  qq = warp_sum(qq);
+  yy = warp_sum(yy);
+  if (lane == 0) {
+    red[0][warp] = qq;
+    red[1][warp] = yy;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    const double rho = sqrt(a), yn = sqrt(b);
+    s_rho = rho;
+    s_go = 1;
+    if (!isfinite(rho) || (c == 0 && !(rho > 0.0))) {
+      st->status = FAB_ENUMERIC;
+      st->stop = 1;
+      s_go = 0;
+    } else if (!(rho > 1e-12 * yn)) {  // the sketch of v_c lies in the span of the others
+      st->m_used = c;
+      st->stop = 1;
+      s_go = 0;
+    }
+  }
+  __syncthreads();
+  if (!s_go) return;
+  const double rho = s_rho, inv = 1.0 / rho;
+  for (int i = tid; i < lds; i += bd) q[i] *= inv;
+  double cr = 0.0, cz = 0.0;
+  for (int j = tid; j < c; j += bd) {
+    double a = 0.0;
+    for (int l = j; l < c; ++l) a = fma(Ri[j + (size_t)ldr * l], s_r[l], a);
+    const double z = -a * inv;
+    Ri[j + (size_t)ldr * c] = z;
+    R[j + (size_t)ldr * c] = s_r[j];
+    cz += fabs(z);
+    cr += fabs(s_r[j]);
+  }
+  cr = warp_sum(cr);
+  cz = warp_sum(cz);
+  __syncthreads();  // red[] is reused
+  if (lane == 0) {
+    red[0][warp] = cr;
+    red[1][warp] = cz;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    R[c + (size_t)ldr * c] = rho;
+    Ri[c + (size_t)ldr * c] = inv;
+    const double n1 = c == 0 ? rho : fmax(nrm[0], a + rho);
+    const double n2 = c == 0 ? inv : fmax(nrm[1], b + inv);
+    nrm[0] = n1;
+    nrm[1] = n2;
+    nrm[2] = n1 * n2;
+    s_go = (c > 0 && n1 * n2 > kmax) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!s_go) return;
+  // whiten at c+1 columns: T = H_c R_c^{-1}, then H_c <- R_{c+1} T (H upper Hessenberg)
+  const int rows = c + 1;
+  for (int idx = tid; idx < rows * c; idx += bd) {
+    const int j = idx % rows, l = idx / rows;
+    double a = 0.0;
+    for (int k = (j > 0 ? j - 1 : 0); k <= l; ++k) a = fma(H[j + (size_t)ldh * k], Ri[k + (size_t)ldr * l], a);
+    T[j + (size_t)ldr * l] = a;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < rows * c; idx += bd) {
+    const int j = idx % rows, l = idx / rows;
+    double a = 0.0;
+    for (int k = j; k <= c; ++k) a = fma(R[j + (size_t)ldr * k], T[k + (size_t)ldr * l], a);
+    H[j + (size_t)ldh * l] = a;
+  }
+  for (int idx = tid; idx < lds * rows; idx += bd) SV[idx] = Q[idx];
+  for (int k = tid; k <= c; k += bd) wcoef[k] = Ri[k + (size_t)ldr * c] * cs.sigma[k];
+  __syncthreads();
+  if (tid == 0) {
+    st->beta *= R[0];
+    cs.sigma[c] = 1.0;
+    cs.shf[c] = 0;
+    st->wh = c + 1;
+  }
+}
+
+cudaError_t launch_wh_check(double* SV, int lds, int c, double* Q, double* R, double* Ri, double* T, int ldr,
+                            double* H, int ldh, double kmax, double* wcoef, double* nrm, ColScale cs, DevState* st,
+                            cudaStream_t s) {
+  if (c < 0 || c > kMaxM) return cudaErrorInvalidValue;
+  k_wh_check<<<1, 256, 0, s>>>(SV, lds, c, Q, R, Ri, T, ldr, H, ldh, kmax, wcoef, nrm, cs, st);
+  return cudaGetLastError();
+}
+
+// Preconditioner of Alg. 3's LSQR on a basis whitened at wh columns: the stored
+// columns are V' with V_whitened = V' blockdiag(R_{wh-1}^{-1}, I), so LSQR on
+// V' P^{-1} with P = blockdiag(R_{wh-1}, I) (rows x mu, ld rows) works on the
+// whitened basis and returns y in its coordinates.
+__global__ void k_wh_precond(const double* __restrict__ R, int ldr, int wh, double* __restrict__ P, int rows,
+                             const int* __restrict__ mdev) {
+  const int mu = *mdev;
+  const int nt = wh - 1 < mu ? wh - 1 : mu;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < rows * mu; idx += gridDim.x * blockDim.x) {
+    const int i = idx % rows, j = idx / rows;
+    double v = (i == j) ? 1.0 : 0.0;
+    if (j < nt && i <= j) v = R[i + (size_t)ldr * j];
+    P[idx] = v;
+  }
+}
+
+cudaError_t launch_wh_precond(const double* R, int ldr, int wh, double* P, int rows, const int* mdev, int mmax,
+                              cudaStream_t s) {
+  int grid = (rows * mmax + 255) / 256;
+  grid = grid < 1 ? 1 : (grid > 1024 ? 1024 : grid);
+  k_wh_precond<<<grid, 256, 0, s>>>(R, ldr, wh, P, rows, mdev);
+  return cudaGetLastError();
+}
+
+// c <- blockdiag(R_{wh-1}^{-1}, I) c (whitened coordinates to stored columns).
+__global__ __launch_bounds__(256) void k_wh_coef(const double* __restrict__ Ri, int ldr, int wh,
+                                                 const int* __restrict__ mdev, double* __restrict__ cv) {
+  __shared__ double s_c[kMaxM + 1];
+  const int mu = *mdev;
+  const int nt = wh - 1 < mu ? wh - 1 : mu;
+  for (int j = threadIdx.x; j < mu; j += blockDim.x) s_c[j] = cv[j];
+  __syncthreads();
+  for (int j = threadIdx.x; j < nt; j += blockDim.x) {
+    double a = 0.0;
+    for (int l = j; l < nt; ++l) a = fma(Ri[j + (size_t)ldr * l], s_c[l], a);
+    cv[j] = a;
+  }
+}
+
+cudaError_t launch_wh_coef(const double* Ri, int ldr, int wh, const int* mdev, double* cv, cudaStream_t s) {
+  k_wh_coef<<<1, 256, 0, s>>>(Ri, ldr, wh, mdev, cv);
   return cudaGetLastError();
 }
 

@@ -48,8 +48,19 @@ cudaError_t launch_lsqr_u(int n, const TV* W, int64_t ld, int nc, const double* 
                           double* part, unsigned* counter, double* unorm2, const DevState* st, cudaStream_t s);
 
 // Step c of Alg. 1 on the sketches (see k_bg_orth) and R = I for Alg. 3's LSQR.
+// Ri (ld ldr): R^{-1} of a basis whitened at st->wh columns (FAB_WHITEN), else NULL;
+// gate: see gate_closed.
 cudaError_t launch_bg_orth(double* SV, int lds, int c, double* H, int ldh, double* coef, ColScale cs, DevState* st,
-                           cudaStream_t s);
+                           cudaStream_t s, const double* Ri = nullptr, int ldr = 0, int gate = 0);
+// Whitening (FAB_WHITEN, see k_wh_check): the condition check of step c and, at the
+// first kappa_1 > kmax, the whitening of H and the sketch; the LSQR preconditioner
+// of a whitened basis; whitened coordinates to stored columns.
+cudaError_t launch_wh_check(double* SV, int lds, int c, double* Q, double* R, double* Ri, double* T, int ldr,
+                            double* H, int ldh, double kmax, double* wcoef, double* nrm, ColScale cs, DevState* st,
+                            cudaStream_t s);
+cudaError_t launch_wh_precond(const double* R, int ldr, int wh, double* P, int rows, const int* mdev, int mmax,
+                              cudaStream_t s);
+cudaError_t launch_wh_coef(const double* Ri, int ldr, int wh, const int* mdev, double* cv, cudaStream_t s);
 cudaError_t launch_set_identity(double* R, int rows, const int* mdev, int mmax, cudaStream_t s);
 // out[0] = ||SV c_new - SV c_old||, out[1] = ||SV c_new|| (growing m to a target).
 cudaError_t launch_sketch_change(const double* SV, int lds, const int* mdev, const double* c_new, int m_old,

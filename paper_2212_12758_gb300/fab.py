@@ -19,7 +19,7 @@ lib = ctypes.CDLL(_LIB_PATH)
 
 FAB_OK, FAB_EINVAL, FAB_ENOMEM, FAB_ECUDA, FAB_ENUMERIC, FAB_ETIMEOUT, FAB_ENOTCONV = 0, -1, -2, -3, -4, -5, -6
 EXP, SQRT, INVSQRT, SIGN = 0, 1, 2, 3
-ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ, BG_LS = 0, 1, 2, 3, 4
+ARNOLDI, SKETCHED_LS, SKETCHED_FAST, NOPROJ, BG_LS, WHITEN = 0, 1, 2, 3, 4, 5
 SPARSE_SIGN, SRHT, GAUSSIAN = 0, 1, 2
 FP64, MIXED = 0, 1
 
@@ -37,14 +37,14 @@ class Params(ctypes.Structure):
                 ("s", ctypes.c_int), ("zeta", ctypes.c_int), ("sketch", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("method", ctypes.c_int), ("precision", ctypes.c_int), ("lsqr_tol", ctypes.c_double),
                 ("lsqr_maxit", ctypes.c_int), ("stream", ctypes.c_void_p), ("target_rel_err", ctypes.c_double),
-                ("m_step", ctypes.c_int), ("m_max", ctypes.c_int)]
+                ("m_step", ctypes.c_int), ("m_max", ctypes.c_int), ("whiten_kappa", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("m_used", ctypes.c_int), ("lsqr_iters", ctypes.c_int), ("fh_iters", ctypes.c_int),
                 ("launches", ctypes.c_int), ("h_last", ctypes.c_double), ("beta", ctypes.c_double),
                 ("ms_basis", ctypes.c_double), ("ms_small", ctypes.c_double), ("ms_combine", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("err_est", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("err_est", ctypes.c_double), ("whiten_at", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -139,7 +139,7 @@ def _on_device(a) -> int:
 
 def params(f=EXP, t=1.0, m=30, k=2, s=None, zeta=8, sketch=SPARSE_SIGN, seed=1, method=SKETCHED_FAST,
            precision=FP64, lsqr_tol=1e-6, lsqr_maxit=0, stream=None, target_rel_err=0.0, m_step=0,
-           m_max=0) -> Params:
+           m_max=0, whiten_kappa=0.0) -> Params:
     p = Params()
     lib.fab_params_default(ctypes.byref(p))
     p.f, p.t, p.m, p.k = int(f), float(t), int(m), int(k)
@@ -148,6 +148,7 @@ def params(f=EXP, t=1.0, m=30, k=2, s=None, zeta=8, sketch=SPARSE_SIGN, seed=1, 
     p.precision, p.lsqr_tol, p.lsqr_maxit = int(precision), float(lsqr_tol), int(lsqr_maxit)
     p.stream = stream
     p.target_rel_err, p.m_step, p.m_max = float(target_rel_err), int(m_step), int(m_max)
+    p.whiten_kappa = float(whiten_kappa)
     return p
 
 
@@ -204,7 +205,7 @@ class Matrix:
             b = np.ascontiguousarray(b, dtype=np.float64)
         st = Stats()
         _check(lib.fab_apply(self._h, ctypes.byref(p), _addr(b), _addr(x), on_dev, ctypes.byref(st)), "fab_apply")
-        self._last = (p.m, p.s, p.method in (SKETCHED_FAST, SKETCHED_LS, BG_LS))
+        self._last = (p.m, p.s, p.method in (SKETCHED_FAST, SKETCHED_LS, BG_LS, WHITEN))
         return (x, st) if stats else x
 
     def set_tiling(self, rows_max: int = 256, nnz_cap: int = 2048, staged: bool = True):
