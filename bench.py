@@ -245,6 +245,53 @@ def bench_skew_convdiff(fab, torch, W, N: int = 352, t: float = -1e-6, ms=(30, 6
     return out
 
 
+def bench_whiten_graph(fab, torch, W, ns=(6301, 1_000_000), ms=(60, 100, 140, 180), reps: int = 3):
+    """The paper's whitening experiment re-created (§5.1.3): x = A^{1/2} b for the
+    Laplacian of a directed Chung-Lu graph (nonsymmetric, eigenvalues with positive
+    real part; n = 6301 as the paper's graph, and n = 1M), b random unit, k = 2,
+    SRHT s = 4m, LSQR tol 1e-6, FP64. Alg. 2's sketch passes kappa_1 = 1000 near
+    column 60 here: every method at each m, error against Arnoldi m = 240."""
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    out = {"workload": "directed Chung-Lu graph Laplacian (seed 2), x = A^(1/2) b, k=2, SRHT s=4m, FP64; "
+                       "reference Arnoldi m=240"}
+    names = (("whiten", fab.WHITEN), ("noproj", fab.NOPROJ), ("sketched_fast", fab.SKETCHED_FAST),
+             ("bg_ls", fab.BG_LS), ("arnoldi", fab.ARNOLDI))
+    for n in ns:
+        A = W.chung_lu_laplacian(n, seed=2)
+        Mx = fab.Matrix.from_csr(A)
+        b = torch.from_numpy(W.random_vector(n, 7)).cuda()
+        xr = torch.empty_like(b)
+        Mx.apply(b, fab.params(f=fab.SQRT, m=240, method=fab.ARNOLDI, stream=sp), x=xr)
+        res = {"nnz": int(A.nnz)}
+        for m in ms:
+            row = {}
+            for name, meth in names:
+                p = fab.params(f=fab.SQRT, m=m, k=2, s=4 * m, sketch=fab.SRHT, seed=1, method=meth, lsqr_tol=1e-6,
+                               stream=sp)
+                x = torch.empty_like(b)
+                try:
+                    _, st = Mx.apply(b, p, x=x, stats=True)
+                except fab.FabError as e:  # e.g. no real principal square root of a garbled projection
+                    row[name] = {"error": e.code}
+                    continue
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    Mx.apply(b, p, x=x)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                row[name] = {"ms": e0.elapsed_time(e1) / reps,
+                             "rel_err": float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))}
+                if meth == fab.WHITEN:
+                    row[name]["whiten_at"] = st.whiten_at
+                    row[name]["lsqr_iters"] = st.lsqr_iters
+            res[f"m={m}"] = row
+        out[f"n={n}"] = res
+    return out
+
+
 def bench_batch(fab, torch, W, steps: int = 3, count: int = 256):
     """256 uneven 2D convection-diffusion solves (n log-uniform on [1e4, 1e6], t on
     [1e-4, 1e-2], m on {20..80}, k = 2, sparse sign s = 4m, zeta = 8, batch seed 3)
@@ -564,6 +611,8 @@ def run_only(args):
         out = bench_bg_laplacian(fab, torch, W)
     elif args.only == "skew":
         out = bench_skew_convdiff(fab, torch, W)
+    elif args.only == "whiten":
+        out = bench_whiten_graph(fab, torch, W)
     elif args.only == "graph":
         out = bench_mixed_graph(fab, torch, W, reps=args.steps, n=args.graph_n, references=not args.no_extras)
     else:
@@ -580,13 +629,13 @@ def main():
     ap.add_argument("--impl", default="fab", choices=["fab", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the sketched_ls / Arnoldi side measurements")
-    ap.add_argument("--extras", default="mixed,batch,graph,bg,skew,serving",
+    ap.add_argument("--extras", default="mixed,batch,graph,bg,skew,whiten,serving",
                     help="side workloads measured after the main one: mixed (the same workload with an FP32 "
                          "basis), batch (256 uneven solves, one graph), "
                          "graph (4M-node power-law Laplacian, mixed precision, Gaussian sketch), serving "
                          "(Poisson arrivals, continuous batching, p50/p99 latency), bg (Alg. 3 vs Arnoldi on the "
                          "3D Laplacian), skew (every method on the skew-form convection-diffusion problem)")
-    ap.add_argument("--only", choices=["mixed", "batch", "graph", "bg", "skew", "serving"], default=None,
+    ap.add_argument("--only", choices=["mixed", "batch", "graph", "bg", "skew", "whiten", "serving"], default=None,
                     help="measure one side workload alone and print its JSON (for profiler runs)")
     ap.add_argument("--serving-slots", type=int, default=16, help="server slots of the --only serving workload")
     ap.add_argument("--graph-n", type=int, default=4_000_000,
@@ -745,6 +794,8 @@ def main():
         extras["mixed_graph_4M"] = bench_mixed_graph(fab, torch, W)
     if not args.no_extras and "skew" in args.extras.split(","):
         extras["skew_convdiff_352"] = bench_skew_convdiff(fab, torch, W)
+    if not args.no_extras and "whiten" in args.extras.split(","):
+        extras["whiten_graph"] = bench_whiten_graph(fab, torch, W)
     if not args.no_extras and "bg" in args.extras.split(","):
         extras["bg_ls_laplacian3d"] = bench_bg_laplacian(fab, torch, W)
     if not args.no_extras and "serving" in args.extras.split(","):
