@@ -168,10 +168,22 @@ __device__ __forceinline__ void spmv_dots_body(
   };
   if (tid == 0)
     for (int i = 0; i < S - 1 && bid + i * nblk < ntiles; ++i) issue(i);
+  // lanes 1..KW of warp 0: the window rows of the tile S-1 iterations ahead, into
+  // L2 ahead of their loads (start rounded down, end up, to 16 bytes: within ld)
+  auto prefetch_window = [&](int i) {
+    const int q = tid - 1;
+    const int tile = bid + i * nblk;
+    if (q < 0 || q >= KW || tile >= ntiles) return;
+    constexpr int kAl = 16 / (int)sizeof(TV);
+    const int ra = A.tiles[tile] & ~(kAl - 1), rb = (A.tiles[tile + 1] + kAl - 1) & ~(kAl - 1);
+    bulk_prefetch_l2_aligned(W + (size_t)(j0 + q) * ld + ra, (uint32_t)((size_t)(rb - ra) * sizeof(TV)));
+  };
+  for (int i = 0; i < S - 1; ++i) prefetch_window(i);
   int it = 0;
   for (int tile = bid; tile < ntiles; tile += nblk, ++it) {
     const int stg = it % S;
     if (tid == 0 && bid + (it + S - 1) * nblk < ntiles && !s_fail) issue(it + S - 1);
+    prefetch_window(it + S - 1);
     // The tile's rows share the block: L = 256 / pow2ceil(rows) lanes per row
     // (one row per thread for full tiles, the whole block for a single long row);
     // each lane sums every L-th nonzero of its row, then the lanes of a row are

@@ -196,6 +196,18 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+// Bulk prefetch of [src, src + bytes) from global memory into L2 (no destination,
+// no completion to wait for): src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+// The same, skipped unless src and bytes are 16-byte multiples: the library's own
+// bases always are (ld a multiple of 32, 256-byte aligned), but a caller's matrix
+// (fab_sketch_apply) may have any leading dimension.
+__device__ __forceinline__ void bulk_prefetch_l2_aligned(const void* src, uint32_t bytes) {
+  if (((uint32_t)reinterpret_cast<uintptr_t>(src) | bytes) & 15u) return;
+  if (bytes > 0) bulk_prefetch_l2(src, bytes);
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
