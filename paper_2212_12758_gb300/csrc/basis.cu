@@ -951,12 +951,11 @@ __global__ __launch_bounds__(kThreads) void k_combine(int n, const TV* __restric
                                                        const double* __restrict__ coef, double* __restrict__ out,
                                                        double keep) {
   extern __shared__ double s_cf[];
-  for (int i = threadIdx.x; i < nc; i += kThreads) s_cf[i] = coef[i];
+  combine_coef_load<TV>(s_cf, coef, nc);
   __syncthreads();
   for (int r = blockIdx.x * kThreads + threadIdx.x; r < n; r += gridDim.x * kThreads) {
-    double a = (keep != 0.0) ? keep * out[r] : 0.0;
-    for (int q = 0; q < nc; ++q) a = fma(s_cf[q], (double)W[(size_t)q * ld + r], a);
-    out[r] = a;
+    const double a = combine_row<TV>(W, ld, nc, s_cf, r);
+    out[r] = (keep != 0.0) ? fma(keep, out[r], a) : a;
   }
 }
 
@@ -1126,14 +1125,10 @@ __global__ __launch_bounds__(kThreads) void k_combine_wave(const BasisJob<TV>* _
   const int nc = J->st->m_used, n = J->A.n;
   const TV* W = J->W;
   const int64_t ld = J->ld;
-  for (int q = threadIdx.x; q < nc; q += kThreads) s_cf[q] = J->coef[q];
+  combine_coef_load<TV>(s_cf, J->coef, nc);
   __syncthreads();
   double* out = J->x;
-  for (int r = bid * kThreads + threadIdx.x; r < n; r += nblk * kThreads) {
-    double a = 0.0;
-    for (int q = 0; q < nc; ++q) a = fma(s_cf[q], (double)W[(size_t)q * ld + r], a);
-    out[r] = a;
-  }
+  for (int r = bid * kThreads + threadIdx.x; r < n; r += nblk * kThreads) out[r] = combine_row<TV>(W, ld, nc, s_cf, r);
 }
 
 template <typename TV>

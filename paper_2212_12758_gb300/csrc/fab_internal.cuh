@@ -196,6 +196,54 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+// Float-float accumulation for combinations of FP32 basis columns with FP64
+// coefficients, on the FP32 pipe: c = hi + lo (two floats), the product hi*w is
+// split exactly by an FMA (TwoProd) and added by Knuth's TwoSum, the small parts
+// go to lo. The result, hi + lo in FP64, is within about 2^-48 of the sum of
+// |terms| (2^24 times below the FP32 basis rounding). The _rn intrinsics are
+// never contracted into FMAs, which TwoSum needs.
+__device__ __forceinline__ float2 ff_split(double c) {
+  const float hi = __double2float_rn(c);
+  return make_float2(hi, __double2float_rn(c - (double)hi));
+}
+__device__ __forceinline__ void ff_madd(float& s_hi, float& s_lo, float2 c, float w) {
+  const float p = __fmul_rn(c.x, w);
+  const float pe = __fmaf_rn(c.x, w, -p);  // c.x w = p + pe exactly
+  const float t = __fadd_rn(s_hi, p);
+  const float bp = __fsub_rn(t, s_hi);
+  const float e = __fadd_rn(__fsub_rn(s_hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));  // s_hi + p = t + e exactly
+  s_hi = t;
+  s_lo = __fadd_rn(s_lo, __fadd_rn(e, __fmaf_rn(c.y, w, pe)));
+}
+// sum_q coef[q] W_q[r] for one row; FP64 columns: FP64 FMAs; FP32 columns: float-float
+// with the coefficients pre-split (s_cf holds nc doubles, or nc float2 for FP32).
+template <typename TV>
+__device__ __forceinline__ double combine_row(const TV* __restrict__ W, int64_t ld, int nc, const void* s_cf, int r) {
+  if constexpr (sizeof(TV) == 4) {
+    const float2* c = reinterpret_cast<const float2*>(s_cf);
+    float hi = 0.0f, lo = 0.0f;
+#pragma unroll 8
+    for (int q = 0; q < nc; ++q) ff_madd(hi, lo, c[q], (float)W[(size_t)q * ld + r]);
+    return (double)hi + (double)lo;
+  } else {
+    const double* c = reinterpret_cast<const double*>(s_cf);
+    double a = 0.0;
+#pragma unroll 4
+    for (int q = 0; q < nc; ++q) a = fma(c[q], (double)W[(size_t)q * ld + r], a);
+    return a;
+  }
+}
+// Fills the shared coefficient table combine_row reads (8 bytes per coefficient).
+template <typename TV>
+__device__ __forceinline__ void combine_coef_load(void* s_cf, const double* coef, int nc) {
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    if constexpr (sizeof(TV) == 4)
+      reinterpret_cast<float2*>(s_cf)[i] = ff_split(coef[i]);
+    else
+      reinterpret_cast<double*>(s_cf)[i] = coef[i];
+  }
+}
+
 // Bulk prefetch of [src, src + bytes) from global memory into L2 (no destination,
 // no completion to wait for): src 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {

@@ -631,12 +631,12 @@ __global__ __launch_bounds__(kThreads) void k_lsqr_u(int n, const TV* __restrict
   __shared__ double tot[1];
   if (st->flag) return;
   const double keep = keep_zero ? 0.0 : st->scal[6];
-  for (int i = threadIdx.x; i < nc; i += kThreads) s_cf[i] = coef[i];
+  combine_coef_load<TV>(s_cf, coef, nc);
   __syncthreads();
   double nrm = 0.0;
   for (int r = blockIdx.x * kThreads + threadIdx.x; r < n; r += gridDim.x * kThreads) {
-    double a = keep_zero ? 0.0 : keep * u[r];
-    for (int q = 0; q < nc; ++q) a = fma(s_cf[q], (double)W[(size_t)q * ld + r], a);
+    double a = combine_row<TV>(W, ld, nc, s_cf, r);
+    if (!keep_zero) a = fma(keep, u[r], a);
     u[r] = a;
     nrm = fma(a, a, nrm);
   }
