@@ -178,26 +178,47 @@ cudaError_t launch_norm1(const double* M, int ldm, const int* mdev, double* out,
 
 // --------------------------------------------------------- dense products
 // C = alpha A B + beta C (mu x mu, common ld); C must not alias A or B.
-__global__ void k_gemm(double* __restrict__ C, const double* __restrict__ A, const double* __restrict__ B, int ld,
-                       const int* __restrict__ mdev, double alpha, double beta) {
+// C = alpha A B + beta C for the leading mu x mu blocks (ld ld). FP64 runs at about two
+// FMAs per clock per SM on GB300, so the product is spread over many SMs: one 8 x 8
+// output tile per 64-thread block (169 blocks at mu = 100), with A's 8 rows and B's 8
+// columns staged in shared memory 128 inner indices at a time.
+constexpr int kGemmT = 8, kGemmK = 128;
+__global__ __launch_bounds__(kGemmT * kGemmT) void k_gemm(double* __restrict__ C, const double* __restrict__ A,
+                                                          const double* __restrict__ B, int ld,
+                                                          const int* __restrict__ mdev, double alpha, double beta) {
+  __shared__ double sA[kGemmK][kGemmT + 1];  // sA[l][i] = A(i0 + i, k0 + l)
+  __shared__ double sB[kGemmK][kGemmT + 1];  // sB[l][j] = B(k0 + l, j0 + j)
   const int mu = *mdev;
-  const int i = blockIdx.x * 16 + threadIdx.x, j = blockIdx.y * 16 + threadIdx.y;
-  if (i >= mu || j >= mu) return;
+  const int i0 = blockIdx.x * kGemmT, j0 = blockIdx.y * kGemmT;
+  if (i0 >= mu || j0 >= mu) return;
+  const int tid = threadIdx.x, ti = tid % kGemmT, tj = tid / kGemmT;
   double a0 = 0.0, a1 = 0.0;
-  int l = 0;
-  for (; l + 1 < mu; l += 2) {
-    a0 = fma(A[i + (size_t)ld * l], B[l + (size_t)ld * j], a0);
-    a1 = fma(A[i + (size_t)ld * (l + 1)], B[l + 1 + (size_t)ld * j], a1);
+  for (int k0 = 0; k0 < mu; k0 += kGemmK) {
+    const int kn = mu - k0 < kGemmK ? mu - k0 : kGemmK;
+    __syncthreads();  // the previous chunk is consumed
+    for (int idx = tid; idx < kn * kGemmT; idx += kGemmT * kGemmT) {
+      const int r = idx % kGemmT, l = idx / kGemmT;
+      sA[l][r] = (i0 + r < mu) ? A[(i0 + r) + (size_t)ld * (k0 + l)] : 0.0;
+      sB[l][r] = (j0 + r < mu) ? B[(k0 + l) + (size_t)ld * (j0 + r)] : 0.0;
+    }
+    __syncthreads();
+    int l = 0;
+    for (; l + 1 < kn; l += 2) {
+      a0 = fma(sA[l][ti], sB[l][tj], a0);
+      a1 = fma(sA[l + 1][ti], sB[l + 1][tj], a1);
+    }
+    if (l < kn) a0 = fma(sA[l][ti], sB[l][tj], a0);
   }
-  if (l < mu) a0 = fma(A[i + (size_t)ld * l], B[l + (size_t)ld * j], a0);
+  const int i = i0 + ti, j = j0 + tj;
+  if (i >= mu || j >= mu) return;
   const double acc = a0 + a1;
   C[i + (size_t)ld * j] = (beta == 0.0) ? alpha * acc : fma(alpha, acc, beta * C[i + (size_t)ld * j]);
 }
 
 cudaError_t launch_gemm(double* C, const double* A, const double* B, int ld, const int* mdev, int mmax, double alpha,
                         double beta, cudaStream_t s) {
-  dim3 grid((mmax + 15) / 16, (mmax + 15) / 16), block(16, 16);
-  k_gemm<<<grid, block, 0, s>>>(C, A, B, ld, mdev, alpha, beta);
+  dim3 grid((mmax + kGemmT - 1) / kGemmT, (mmax + kGemmT - 1) / kGemmT);
+  k_gemm<<<grid, kGemmT * kGemmT, 0, s>>>(C, A, B, ld, mdev, alpha, beta);
   return cudaGetLastError();
 }
 
