@@ -83,31 +83,59 @@ cudaError_t launch_householder_qr(double* A, int lda, int rows, const int* mdev,
 }
 
 // ------------------------------------------------------- triangular solves
-// x <- R^{-1} x (trans = 0) or R^{-T} x (trans = 1), R = upper triangle of the
-// leading mu x mu block of R (ld ldr). Optional pre-scale of x by *pre (device).
+// Block-wide solve with the upper triangle R of the leading mu x mu block (ld ldr):
+// x = R^{-1} (p xin) (trans = 0) or R^{-T} (p xin) (trans = 1), published in the
+// shared array xpub (xin may be xpub: the solve is then in place). Row i lives in a
+// register of thread i % blockDim (mu <= kR blockDim); step j (mu sequential steps)
+// solves x_j in its owner, publishes it behind one block barrier, and every row still
+// to be solved takes its FMA. The entries of R a step needs are loaded two steps
+// ahead, so their latency hides behind the barriers in between.
+template <int kR>
+__device__ __forceinline__ void trsv_core(const double* __restrict__ R, int ldr, int mu, const double* xin,
+                                          double* xpub, int trans, double p) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  double xv[kR], dv[kR], r0[kR], r1[kR];
+  // entry of row i that step j uses: R(i, j) (trans = 0, rows i < j) or R(j, i) (trans = 1, rows i > j)
+  auto entry = [&](int i, int j) -> double {
+    if (j < 0 || j >= mu) return 0.0;
+    if (!trans) return i < j ? R[i + (size_t)j * ldr] : 0.0;
+    return (i > j && i < mu) ? R[j + (size_t)i * ldr] : 0.0;
+  };
+  const int jfirst = trans ? 0 : mu - 1, dj = trans ? 1 : -1;
+#pragma unroll
+  for (int r = 0; r < kR; ++r) {
+    const int i = tid + r * bd;
+    xv[r] = i < mu ? p * xin[i] : 0.0;
+    dv[r] = i < mu ? R[i + (size_t)i * ldr] : 1.0;
+    r0[r] = entry(i, jfirst);
+    r1[r] = entry(i, jfirst + dj);
+  }
+  __syncthreads();  // xin is read everywhere before xpub (maybe the same array) is written
+  for (int step = 0; step < mu; ++step) {
+    const int j = jfirst + step * dj;
+    if (tid == j % bd) {
+      const int rj = j / bd;
+#pragma unroll
+      for (int r = 0; r < kR; ++r)
+        if (r == rj) xpub[j] = xv[r] / dv[r];
+    }
+    __syncthreads();
+    const double xj = xpub[j];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+      xv[r] = fma(-r0[r], xj, xv[r]);  // zero entry for rows the step does not touch
+      r0[r] = r1[r];
+      r1[r] = entry(tid + r * bd, j + 2 * dj);
+    }
+  }
+  __syncthreads();
+}
+
+// x <- R^{-1} x (trans = 0) or R^{-T} x (trans = 1), with an optional pre-scale *pre.
 __device__ __forceinline__ void trsv_body(const double* __restrict__ R, int ldr, int mu, const double* __restrict__ xin,
                                           double* __restrict__ xout, int trans, const double* __restrict__ pre) {
   __shared__ double xs[kMaxM];
-  const double p = pre ? *pre : 1.0;
-  for (int i = threadIdx.x; i < mu; i += blockDim.x) xs[i] = p * xin[i];
-  __syncthreads();
-  if (!trans) {
-    for (int j = mu - 1; j >= 0; --j) {
-      if (threadIdx.x == 0) xs[j] /= R[j + (size_t)j * ldr];
-      __syncthreads();
-      const double xj = xs[j];
-      for (int i = threadIdx.x; i < j; i += blockDim.x) xs[i] = fma(-R[i + (size_t)j * ldr], xj, xs[i]);
-      __syncthreads();
-    }
-  } else {
-    for (int j = 0; j < mu; ++j) {
-      if (threadIdx.x == 0) xs[j] /= R[j + (size_t)j * ldr];
-      __syncthreads();
-      const double xj = xs[j];
-      for (int i = j + 1 + threadIdx.x; i < mu; i += blockDim.x) xs[i] = fma(-R[j + (size_t)i * ldr], xj, xs[i]);
-      __syncthreads();
-    }
-  }
+  trsv_core<kMaxM / 256>(R, ldr, mu, xin, xs, trans, pre ? *pre : 1.0);  // 256-thread blocks
   for (int i = threadIdx.x; i < mu; i += blockDim.x) xout[i] = xs[i];
 }
 
@@ -482,16 +510,9 @@ __device__ void lsqr_block_norm(const double* a, int mu, double* red, double* ou
   __syncthreads();
 }
 
-// Back substitution z = R^{-1} v in shared memory (block-wide).
-__device__ void lsqr_trsv(const double* R, int ldr, int mu, double* zs) {
-  for (int j = mu - 1; j >= 0; --j) {
-    if (threadIdx.x == 0) zs[j] /= R[j + (size_t)j * ldr];
-    __syncthreads();
-    const double zj = zs[j];
-    for (int i = threadIdx.x; i < j; i += blockDim.x) zs[i] = fma(-R[i + (size_t)j * ldr], zj, zs[i]);
-    __syncthreads();
-  }
-}
+// Back substitution z = R^{-1} v in shared memory, in place (block-wide).
+// (the LSQR kernels run kMaxM threads: one row each)
+__device__ void lsqr_trsv(const double* R, int ldr, int mu, double* zs) { trsv_core<1>(R, ldr, mu, zs, zs, 0, 1.0); }
 
 // Start: beta_1 from ||ustore|| (u_1 = v_{m+1} = sigma_mu ustore), then
 // v = R^{-T} V_m^T u_1, alpha, w = v, phibar = beta_1, rhobar = alpha, x = 0.
@@ -506,15 +527,7 @@ __global__ __launch_bounds__(1024) void k_lsqr_start(const double* __restrict__ 
   const double beta1 = sigma[mu] * sqrt(*unorm2);
   const double tau = (beta1 > 0.0) ? sigma[mu] / beta1 : 0.0;
   // v = R^{-T} (tau q)
-  for (int i = threadIdx.x; i < mu; i += blockDim.x) vs[i] = tau * lv.q[i];
-  __syncthreads();
-  for (int j = 0; j < mu; ++j) {
-    if (threadIdx.x == 0) vs[j] /= R[j + (size_t)j * ldr];
-    __syncthreads();
-    const double vj = vs[j];
-    for (int i = j + 1 + threadIdx.x; i < mu; i += blockDim.x) vs[i] = fma(-R[j + (size_t)i * ldr], vj, vs[i]);
-    __syncthreads();
-  }
+  trsv_core<1>(R, ldr, mu, lv.q, vs, 1, tau);
   lsqr_block_norm(vs, mu, red, &s_nrm);
   const double alpha = s_nrm;
   const double ainv = alpha > 0.0 ? 1.0 / alpha : 0.0;
@@ -571,15 +584,7 @@ __global__ __launch_bounds__(1024) void k_lsqr_step(const double* __restrict__ R
   double alpha_new = alpha;
   if (beta > 0.0) {
     const double binv = 1.0 / beta;
-    for (int i = threadIdx.x; i < mu; i += blockDim.x) vs[i] = lv.q[i] * binv;
-    __syncthreads();
-    for (int j = 0; j < mu; ++j) {
-      if (threadIdx.x == 0) vs[j] /= R[j + (size_t)j * ldr];
-      __syncthreads();
-      const double vj = vs[j];
-      for (int i = j + 1 + threadIdx.x; i < mu; i += blockDim.x) vs[i] = fma(-R[j + (size_t)i * ldr], vj, vs[i]);
-      __syncthreads();
-    }
+    trsv_core<1>(R, ldr, mu, lv.q, vs, 1, binv);
     for (int i = threadIdx.x; i < mu; i += blockDim.x) vs[i] = fma(-beta, lv.v[i], vs[i]);
     __syncthreads();
     lsqr_block_norm(vs, mu, red, &s_nrm);
