@@ -762,7 +762,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     // y = argmin || Theta V_m z - Theta v_{m+1} || (sketch-and-solve form of eq. sFOM)
     CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * (mu + 1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
     LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 1, ws.tau, s));
-    LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.qr + (size_t)mu * p->s, ws.y, 0, nullptr, s));
+    LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.qr + (size_t)mu * p->s, ws.y, 0, nullptr, s, m));
     yptr = ws.y;
   } else if (lsqr) {
     if (p->method == FAB_SKETCHED_LS) {
@@ -784,14 +784,14 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     LK(PK_GEMVT, launch_gemv_t(n, (const TV*)W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
     LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, nullptr, ws.lv_q, 0, nullptr, ws.st, s));
     LsqrVecs lv{ws.lv_v, ws.lv_w, ws.lv_x, ws.lv_z, ws.lv_coef, ws.lv_q};
-    LK(PK_SMALL, launch_lsqr_start(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, p->lsqr_tol, ws.st, s));
+    LK(PK_SMALL, launch_lsqr_start(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, p->lsqr_tol, ws.st, s, m));
     const int maxit = p->lsqr_maxit > 0 ? p->lsqr_maxit : 4 * mu;
     bool converged = false;
     for (int it = 0; it < maxit; ++it) {
       LK(PK_COMBINE, launch_lsqr_u(n, (const TV*)W, ld, mu, ws.lv_coef, ws.u, 0, ws.part, ws.counter, ws.unorm2, ws.st, s));
       LK(PK_GEMVT, launch_gemv_t(n, (const TV*)W, ld, 0, mu, ws.u, ws.gpart, ntiles, ws.st, s));
       LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, mu, ws.sigma, 0, nullptr, ws.lv_q, 0, nullptr, ws.st, s));
-      LK(PK_SMALL, launch_lsqr_step(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, ws.st, s));
+      LK(PK_SMALL, launch_lsqr_step(ws.qr, p->s, mdev, ws.sigma, ws.unorm2, lv, ws.st, s, m));
       // iterations after convergence are no-ops on the device, so the host reads
       // the flag only every kLsqrPoll iterations
       if ((it + 1) % kLsqrPoll != 0 && it + 1 != maxit) continue;
@@ -808,7 +808,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     if (wh > 0) {
       yptr = ws.lv_x;
     } else {
-      LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.lv_x, ws.y, 0, nullptr, s));
+      LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.lv_x, ws.y, 0, nullptr, s, m));
       yptr = ws.y;
     }
   }

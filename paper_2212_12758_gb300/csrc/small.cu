@@ -90,10 +90,21 @@ cudaError_t launch_householder_qr(double* A, int lda, int rows, const int* mdev,
 // solves x_j in its owner, publishes it behind one block barrier, and every row still
 // to be solved takes its FMA. The entries of R a step needs are loaded two steps
 // ahead, so their latency hides behind the barriers in between.
+// sR (optional, mu * mu doubles of shared memory): R's upper triangle is staged there
+// first, so that a step waits on shared memory instead of L2.
 template <int kR>
-__device__ __forceinline__ void trsv_core(const double* __restrict__ R, int ldr, int mu, const double* xin,
-                                          double* xpub, int trans, double p) {
+__device__ __forceinline__ void trsv_core(const double* __restrict__ Rg, int ldg, int mu, const double* xin,
+                                          double* xpub, int trans, double p, double* sR = nullptr) {
   const int tid = threadIdx.x, bd = blockDim.x;
+  if (sR) {
+    for (int idx = tid; idx < mu * mu; idx += bd) {
+      const int i = idx % mu, j = idx / mu;
+      if (i <= j) sR[idx] = Rg[i + (size_t)j * ldg];
+    }
+    __syncthreads();
+  }
+  const double* R = sR ? sR : Rg;
+  const int ldr = sR ? mu : ldg;
   double xv[kR], dv[kR], r0[kR], r1[kR];
   // entry of row i that step j uses: R(i, j) (trans = 0, rows i < j) or R(j, i) (trans = 1, rows i > j)
   auto entry = [&](int i, int j) -> double {
@@ -133,21 +144,31 @@ __device__ __forceinline__ void trsv_core(const double* __restrict__ R, int ldr,
 
 // x <- R^{-1} x (trans = 0) or R^{-T} x (trans = 1), with an optional pre-scale *pre.
 __device__ __forceinline__ void trsv_body(const double* __restrict__ R, int ldr, int mu, const double* __restrict__ xin,
-                                          double* __restrict__ xout, int trans, const double* __restrict__ pre) {
+                                          double* __restrict__ xout, int trans, const double* __restrict__ pre,
+                                          double* sR = nullptr) {
   __shared__ double xs[kMaxM];
-  trsv_core<kMaxM / 256>(R, ldr, mu, xin, xs, trans, pre ? *pre : 1.0);  // 256-thread blocks
+  trsv_core<kMaxM / 256>(R, ldr, mu, xin, xs, trans, pre ? *pre : 1.0, sR);  // 256-thread blocks
   for (int i = threadIdx.x; i < mu; i += blockDim.x) xout[i] = xs[i];
 }
+// Largest triangle staged in shared memory by the one-block solves (180 KB).
+constexpr int kTriSmemMax = 150;
+inline size_t tri_smem_bytes(int mmax) { return mmax <= kTriSmemMax ? (size_t)mmax * mmax * sizeof(double) : 0; }
 
 __global__ __launch_bounds__(1024) void k_trsv(const double* __restrict__ R, int ldr, const int* __restrict__ mdev,
                                                 const double* __restrict__ xin, double* __restrict__ xout, int trans,
-                                                const double* __restrict__ pre) {
-  trsv_body(R, ldr, *mdev, xin, xout, trans, pre);
+                                                const double* __restrict__ pre, int staged) {
+  extern __shared__ double s_tri[];
+  trsv_body(R, ldr, *mdev, xin, xout, trans, pre, staged ? s_tri : nullptr);
 }
 
 cudaError_t launch_trsv(const double* R, int ldr, const int* mdev, const double* xin, double* xout, int trans,
-                        const double* pre, cudaStream_t s) {
-  k_trsv<<<1, 256, 0, s>>>(R, ldr, mdev, xin, xout, trans, pre);
+                        const double* pre, cudaStream_t s, int mmax) {
+  const size_t smem = tri_smem_bytes(mmax);
+  if (smem > 0) {
+    const cudaError_t e = ensure_smem_limit((const void*)k_trsv, smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_trsv<<<1, 256, smem, s>>>(R, ldr, mdev, xin, xout, trans, pre, smem > 0 ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -512,14 +533,18 @@ __device__ void lsqr_block_norm(const double* a, int mu, double* red, double* ou
 
 // Back substitution z = R^{-1} v in shared memory, in place (block-wide).
 // (the LSQR kernels run kMaxM threads: one row each)
-__device__ void lsqr_trsv(const double* R, int ldr, int mu, double* zs) { trsv_core<1>(R, ldr, mu, zs, zs, 0, 1.0); }
+__device__ void lsqr_trsv(const double* R, int ldr, int mu, double* zs, double* sR) {
+  trsv_core<1>(R, ldr, mu, zs, zs, 0, 1.0, sR);
+}
 
 // Start: beta_1 from ||ustore|| (u_1 = v_{m+1} = sigma_mu ustore), then
 // v = R^{-T} V_m^T u_1, alpha, w = v, phibar = beta_1, rhobar = alpha, x = 0.
 __global__ __launch_bounds__(1024) void k_lsqr_start(const double* __restrict__ R, int ldr,
                                                       const int* __restrict__ mdev, const double* __restrict__ sigma,
                                                       const double* __restrict__ unorm2, LsqrVecs lv, double tol,
-                                                      DevState* st) {
+                                                      DevState* st, int staged) {
+  extern __shared__ double s_tri[];  // R's triangle (staged) or unused
+  double* sR = staged ? s_tri : nullptr;
   __shared__ double vs[kMaxM];
   __shared__ double red[32];
   __shared__ double s_nrm;
@@ -527,7 +552,7 @@ __global__ __launch_bounds__(1024) void k_lsqr_start(const double* __restrict__ 
   const double beta1 = sigma[mu] * sqrt(*unorm2);
   const double tau = (beta1 > 0.0) ? sigma[mu] / beta1 : 0.0;
   // v = R^{-T} (tau q)
-  trsv_core<1>(R, ldr, mu, lv.q, vs, 1, tau);
+  trsv_core<1>(R, ldr, mu, lv.q, vs, 1, tau, sR);
   lsqr_block_norm(vs, mu, red, &s_nrm);
   const double alpha = s_nrm;
   const double ainv = alpha > 0.0 ? 1.0 / alpha : 0.0;
@@ -539,7 +564,7 @@ __global__ __launch_bounds__(1024) void k_lsqr_start(const double* __restrict__ 
     lv.x[i] = 0.0;
   }
   __syncthreads();
-  lsqr_trsv(R, ldr, mu, vs);  // z = R^{-1} v
+  lsqr_trsv(sR ? sR : R, sR ? mu : ldr, mu, vs, nullptr);  // z = R^{-1} v (triangle already staged)
   for (int i = threadIdx.x; i < mu; i += blockDim.x) {
     lv.z[i] = vs[i];
     lv.coef[i] = sigma[i] * vs[i];
@@ -559,8 +584,13 @@ __global__ __launch_bounds__(1024) void k_lsqr_start(const double* __restrict__ 
 }
 
 cudaError_t launch_lsqr_start(const double* R, int ldr, const int* mdev, const double* sigma, const double* unorm2,
-                              const LsqrVecs& lv, double tol, DevState* st, cudaStream_t s) {
-  k_lsqr_start<<<1, 1024, 0, s>>>(R, ldr, mdev, sigma, unorm2, lv, tol, st);
+                              const LsqrVecs& lv, double tol, DevState* st, cudaStream_t s, int mmax) {
+  const size_t smem = tri_smem_bytes(mmax);
+  if (smem > 0) {
+    const cudaError_t e = ensure_smem_limit((const void*)k_lsqr_start, smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_lsqr_start<<<1, 1024, smem, s>>>(R, ldr, mdev, sigma, unorm2, lv, tol, st, smem > 0 ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -570,14 +600,25 @@ cudaError_t launch_lsqr_start(const double* R, int ldr, const int* mdev, const d
 //   v <- R^{-T} (q / beta) - beta v, alpha = ||v||, v /= alpha,
 //   rotation, x += (phi/rho) w, w = v - (theta/rho) w, stopping test,
 //   z = R^{-1} v, coef = sigma z, keep = -alpha / beta.
-__global__ __launch_bounds__(1024) void k_lsqr_step(const double* __restrict__ R, int ldr,
+__global__ __launch_bounds__(1024) void k_lsqr_step(const double* __restrict__ Rg, int ldg,
                                                      const int* __restrict__ mdev, const double* __restrict__ sigma,
-                                                     const double* __restrict__ unorm2, LsqrVecs lv, DevState* st) {
+                                                     const double* __restrict__ unorm2, LsqrVecs lv, DevState* st,
+                                                     int staged) {
+  extern __shared__ double s_tri[];  // R's triangle (staged) or unused
   __shared__ double vs[kMaxM];
   __shared__ double red[32];
   __shared__ double s_nrm;
   if (st->flag) return;
   const int mu = *mdev;
+  if (staged) {  // both solves below read the triangle from shared memory
+    for (int idx = threadIdx.x; idx < mu * mu; idx += blockDim.x) {
+      const int i = idx % mu, j = idx / mu;
+      if (i <= j) s_tri[idx] = Rg[i + (size_t)j * ldg];
+    }
+    __syncthreads();
+  }
+  const double* R = staged ? s_tri : Rg;
+  const int ldr = staged ? mu : ldg;
   double alpha = st->scal[0];
   const double beta = sqrt(*unorm2);
   const double anorm2 = st->scal[4] + alpha * alpha + beta * beta;
@@ -613,7 +654,7 @@ __global__ __launch_bounds__(1024) void k_lsqr_step(const double* __restrict__ R
     lv.v[i] = vs[i];
   }
   __syncthreads();
-  lsqr_trsv(R, ldr, mu, vs);
+  lsqr_trsv(R, ldr, mu, vs, nullptr);
   for (int i = threadIdx.x; i < mu; i += blockDim.x) {
     lv.z[i] = vs[i];
     lv.coef[i] = sigma[i] * vs[i];
@@ -639,8 +680,13 @@ __global__ __launch_bounds__(1024) void k_lsqr_step(const double* __restrict__ R
 }
 
 cudaError_t launch_lsqr_step(const double* R, int ldr, const int* mdev, const double* sigma, const double* unorm2,
-                             const LsqrVecs& lv, DevState* st, cudaStream_t s) {
-  k_lsqr_step<<<1, 1024, 0, s>>>(R, ldr, mdev, sigma, unorm2, lv, st);
+                             const LsqrVecs& lv, DevState* st, cudaStream_t s, int mmax) {
+  const size_t smem = tri_smem_bytes(mmax);
+  if (smem > 0) {
+    const cudaError_t e = ensure_smem_limit((const void*)k_lsqr_step, smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_lsqr_step<<<1, 1024, smem, s>>>(R, ldr, mdev, sigma, unorm2, lv, st, smem > 0 ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -21,8 +21,9 @@ cudaError_t launch_qr(double* A, int lda, int rows, const int* mdev, int max_col
                       cudaStream_t s);
 cudaError_t launch_lu_fast(double* M, int ld, const int* mdev, int max_m, int* piv, double* logdet, DevState* st,
                            cudaStream_t s);
+// mmax: largest *mdev (R's triangle is staged in shared memory when mmax <= 150; 0: never)
 cudaError_t launch_trsv(const double* R, int ldr, const int* mdev, const double* xin, double* xout, int trans,
-                        const double* pre, cudaStream_t s);
+                        const double* pre, cudaStream_t s, int mmax = 0);
 cudaError_t launch_build_hhat(const double* H, int ldh, const int* mdev, const double* y, double scale, double* M,
                               int ldm, int mmax, cudaStream_t s);
 cudaError_t launch_norm1(const double* M, int ldm, const int* mdev, double* out, cudaStream_t s);
@@ -40,9 +41,9 @@ cudaError_t launch_first_column(const double* M, const int* mdev, double* y, cud
 cudaError_t launch_prep_coef(const double* c, const double* sigma, const int* mdev, const DevState* st, double* coef,
                              cudaStream_t s);
 cudaError_t launch_lsqr_start(const double* R, int ldr, const int* mdev, const double* sigma, const double* unorm2,
-                              const LsqrVecs& lv, double tol, DevState* st, cudaStream_t s);
+                              const LsqrVecs& lv, double tol, DevState* st, cudaStream_t s, int mmax = 0);
 cudaError_t launch_lsqr_step(const double* R, int ldr, const int* mdev, const double* sigma, const double* unorm2,
-                             const LsqrVecs& lv, DevState* st, cudaStream_t s);
+                             const LsqrVecs& lv, DevState* st, cudaStream_t s, int mmax = 0);
 template <typename TV>
 cudaError_t launch_lsqr_u(int n, const TV* W, int64_t ld, int nc, const double* coef, double* u, int keep_zero,
                           double* part, unsigned* counter, double* unorm2, const DevState* st, cudaStream_t s);
