@@ -534,7 +534,8 @@ int sqrtm_e1(Ws& ws, int m, const int* mdev, double* c, int want_sqrt, int* iter
     CK(cudaMemcpyAsync(T, M, (size_t)m * m * sizeof(double), cudaMemcpyDeviceToDevice, s));
     LK(PK_SMALL, launch_lu_fast(T, m, mdev, m, ws.piv, ws.scal + 11, ws.st, s));
     LK(PK_SMALL, launch_lu_solve(T, m, ws.piv, mdev, m, Minv, m, 1, s));
-    LK(PK_SMALL, launch_db_update(M, Minv, m, mdev, c, ws.scal + 11, err > 1e-2 ? 1 : 0, ws.st, s));
+    LK(PK_SMALL, launch_db_update(M, Minv, m, mdev, c, ws.scal + 11, err > 1e-2 ? 1 : 0, ws.st, s, m, ws.part,
+                                  ws.counter));
     DevState& hs = *ws.hs;
     CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(wait_stream(s));

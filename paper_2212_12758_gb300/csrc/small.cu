@@ -117,7 +117,7 @@ __device__ __forceinline__ void trsv_core(const double* __restrict__ Rg, int ldg
   for (int r = 0; r < kR; ++r) {
     const int i = tid + r * bd;
     xv[r] = i < mu ? p * xin[i] : 0.0;
-    dv[r] = i < mu ? R[i + (size_t)i * ldr] : 1.0;
+    dv[r] = i < mu ? 1.0 / R[i + (size_t)i * ldr] : 1.0;  // reciprocal, off the sequential path
     r0[r] = entry(i, jfirst);
     r1[r] = entry(i, jfirst + dj);
   }
@@ -128,7 +128,7 @@ __device__ __forceinline__ void trsv_core(const double* __restrict__ Rg, int ldg
       const int rj = j / bd;
 #pragma unroll
       for (int r = 0; r < kR; ++r)
-        if (r == rj) xpub[j] = xv[r] / dv[r];
+        if (r == rj) xpub[j] = xv[r] * dv[r];
     }
     __syncthreads();
     const double xj = xpub[j];
@@ -388,50 +388,92 @@ cudaError_t launch_lu(double* M, int ld, const int* mdev, int* piv, double* logd
   return cudaGetLastError();
 }
 
-// Solve LU X = P B in place for nrhs columns of B (one warp per column,
-// column-oriented substitution). identity_rhs: B is set to I first.
-__global__ void k_lu_solve(const double* __restrict__ LU, int ld, const int* __restrict__ piv,
-                           const int* __restrict__ mdev, double* __restrict__ B, int ldb, int identity_rhs) {
-  extern __shared__ double sb[];
+// Solve LU X = P B in place for the mu columns of B (one warp per column at a time,
+// column-oriented substitution). identity_rhs: B is set to I first. staged: every
+// block first copies the mu x mu factors into shared memory, so that the 2 mu
+// dependent substitution steps of a column read shared memory instead of L2.
+__global__ void k_lu_solve(const double* __restrict__ LUg, int ldg, const int* __restrict__ piv,
+                           const int* __restrict__ mdev, double* __restrict__ B, int ldb, int identity_rhs,
+                           int staged, int wpb) {
+  extern __shared__ double sm[];
   const int mu = *mdev;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  const int col = blockIdx.x * wpb + warp;
-  if (col >= mu) return;
-  double* b = sb + (size_t)warp * mu;
-  double* bg = B + (size_t)ldb * col;
-  for (int i = lane; i < mu; i += 32) b[i] = identity_rhs ? (i == col ? 1.0 : 0.0) : bg[i];
-  __syncwarp();
-  if (lane == 0) {
-    for (int k = 0; k < mu; ++k) {
-      const int p = piv[k];
-      if (p != k && p > k && p < mu) {
-        const double t = b[k];
-        b[k] = b[p];
-        b[p] = t;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (staged) {  // every warp of the block stages; only the first wpb_solve warps solve
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < mu * mu; idx += blockDim.x) sm[idx] = LUg[idx % mu + (size_t)ldg * (idx / mu)];
+    __syncthreads();
+  }
+  const double* LU = staged ? sm : LUg;
+  const int ld = staged ? mu : ldg;
+  // staged: reciprocals of U's diagonal after the factors (one division per row, in
+  // parallel, instead of one per step on the sequential path)
+  double* dinv = staged ? sm + (size_t)mu * mu : nullptr;
+  if (staged) {
+    for (int k = threadIdx.x; k < mu; k += blockDim.x) dinv[k] = 1.0 / sm[k + (size_t)mu * k];
+    __syncthreads();
+  }
+  double* b = sm + (staged ? (size_t)mu * mu + mu : 0) + (size_t)warp * mu;
+  for (int col = blockIdx.x * wpb + warp; warp < wpb && col < mu; col += gridDim.x * wpb) {
+    double* bg = B + (size_t)ldb * col;
+    int kstart = 0;
+    if (identity_rhs) {
+      // P e_col is the unit vector at the row the swaps carry col to; every lane follows
+      // it through the swap sequence, and the forward pass starts there (zeros above)
+      int pos = col;
+      for (int k = 0; k < mu; ++k) {
+        const int p = piv[k];
+        if (p != k && p > k && p < mu) pos = (pos == k) ? p : (pos == p ? k : pos);
+      }
+      for (int i = lane; i < mu; i += 32) b[i] = (i == pos) ? 1.0 : 0.0;
+      kstart = pos;
+    } else {
+      for (int i = lane; i < mu; i += 32) b[i] = bg[i];
+      __syncwarp();
+      if (lane == 0) {
+        for (int k = 0; k < mu; ++k) {
+          const int p = piv[k];
+          if (p != k && p > k && p < mu) {
+            const double t = b[k];
+            b[k] = b[p];
+            b[p] = t;
+          }
+        }
       }
     }
-  }
-  __syncwarp();
-  for (int k = 0; k < mu; ++k) {  // unit lower
-    const double bk = b[k];
-    for (int i = k + 1 + lane; i < mu; i += 32) b[i] = fma(-LU[i + (size_t)ld * k], bk, b[i]);
+    __syncwarp();
+    for (int k = kstart; k < mu; ++k) {  // unit lower
+      const double bk = b[k];
+      for (int i = k + 1 + lane; i < mu; i += 32) b[i] = fma(-LU[i + (size_t)ld * k], bk, b[i]);
+      __syncwarp();
+    }
+    for (int k = mu - 1; k >= 0; --k) {  // upper
+      if (lane == 0) b[k] = dinv ? b[k] * dinv[k] : b[k] / LU[k + (size_t)ld * k];
+      __syncwarp();
+      const double bk = b[k];
+      for (int i = lane; i < k; i += 32) b[i] = fma(-LU[i + (size_t)ld * k], bk, b[i]);
+      __syncwarp();
+    }
+    for (int i = lane; i < mu; i += 32) bg[i] = b[i];
     __syncwarp();
   }
-  for (int k = mu - 1; k >= 0; --k) {  // upper
-    if (lane == 0) b[k] /= LU[k + (size_t)ld * k];
-    __syncwarp();
-    const double bk = b[k];
-    for (int i = lane; i < k; i += 32) b[i] = fma(-LU[i + (size_t)ld * k], bk, b[i]);
-    __syncwarp();
-  }
-  for (int i = lane; i < mu; i += 32) bg[i] = b[i];
 }
 
 cudaError_t launch_lu_solve(const double* LU, int ld, const int* piv, const int* mdev, int mmax, double* B, int ldb,
                             int identity_rhs, cudaStream_t s) {
+  const size_t stage = (size_t)mmax * mmax * sizeof(double);
+  if (mmax <= 160) {  // factors staged by 8 warps; 2 of them solve: the FP64 work spreads over mmax / 2 SMs
+    const int wpb = 2;
+    const size_t smem = stage + (size_t)(wpb + 1) * mmax * sizeof(double);
+    const cudaError_t e = ensure_smem_limit((const void*)k_lu_solve, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (mmax + wpb - 1) / wpb;
+    k_lu_solve<<<grid, 256, smem, s>>>(LU, ld, piv, mdev, B, ldb, identity_rhs, 1, wpb);
+    return cudaGetLastError();
+  }
   const int wpb = 4;
   const int grid = (mmax + wpb - 1) / wpb;
-  k_lu_solve<<<grid, wpb * 32, (size_t)wpb * mmax * sizeof(double), s>>>(LU, ld, piv, mdev, B, ldb, identity_rhs);
+  k_lu_solve<<<grid, wpb * 32, (size_t)wpb * mmax * sizeof(double), s>>>(LU, ld, piv, mdev, B, ldb, identity_rhs, 0,
+                                                                         wpb);
   return cudaGetLastError();
 }
 
@@ -450,9 +492,16 @@ __device__ __forceinline__ void db_update_body(double* __restrict__ M, const dou
   for (int i = threadIdx.x; i < mu; i += blockDim.x) ys[i] = y[i];
   __syncthreads();
   for (int i = threadIdx.x; i < mu; i += blockDim.x) {
-    double a = 0.0;
-    for (int j = 0; j < mu; ++j) a = fma(Minv[i + (size_t)ld * j], ys[j], a);
-    y[i] = 0.5 * g * fma(gi2, a, ys[i]);
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;  // four chains: FP64 latency, not throughput, bounds this
+    int j = 0;
+    for (; j + 3 < mu; j += 4) {
+      a0 = fma(Minv[i + (size_t)ld * j], ys[j], a0);
+      a1 = fma(Minv[i + (size_t)ld * (j + 1)], ys[j + 1], a1);
+      a2 = fma(Minv[i + (size_t)ld * (j + 2)], ys[j + 2], a2);
+      a3 = fma(Minv[i + (size_t)ld * (j + 3)], ys[j + 3], a3);
+    }
+    for (; j < mu; ++j) a0 = fma(Minv[i + (size_t)ld * j], ys[j], a0);
+    y[i] = 0.5 * g * fma(gi2, (a0 + a1) + (a2 + a3), ys[i]);
   }
   double err = 0.0;
   for (int idx = threadIdx.x; idx < mu * mu; idx += blockDim.x) {
@@ -475,15 +524,63 @@ __device__ __forceinline__ void db_update_body(double* __restrict__ M, const dou
   __syncthreads();
 }
 
-__global__ __launch_bounds__(1024) void k_db_update(double* __restrict__ M, const double* __restrict__ Minv, int ld,
+// The same step over many blocks (a single SM's FP64 rate made the m^2 elementwise
+// update the bottleneck): block 0 alone forms y from Minv and the old y (no other
+// block touches y); every block updates its slice of M and adds its share of
+// ||M - I||_F^2 to part[]; the last block sums the shares in block order.
+__global__ __launch_bounds__(256) void k_db_update(double* __restrict__ M, const double* __restrict__ Minv, int ld,
                                                      const int* __restrict__ mdev, double* __restrict__ y,
-                                                     const double* __restrict__ logdet, int scale_on, DevState* st) {
-  db_update_body(M, Minv, ld, *mdev, y, logdet, scale_on, st);
+                                                     const double* __restrict__ logdet, int scale_on,
+                                                     double* __restrict__ part, unsigned* __restrict__ counter,
+                                                     DevState* st) {
+  __shared__ double ys[kMaxM];
+  __shared__ double red[32];
+  __shared__ double tot[1];
+  const int mu = *mdev;
+  const double g = scale_on ? exp(-(*logdet) / (2.0 * mu)) : 1.0;
+  const double g2 = g * g, gi2 = 1.0 / g2;
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < mu; i += blockDim.x) ys[i] = y[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < mu; i += blockDim.x) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int j = 0;
+      for (; j + 3 < mu; j += 4) {
+        a0 = fma(Minv[i + (size_t)ld * j], ys[j], a0);
+        a1 = fma(Minv[i + (size_t)ld * (j + 1)], ys[j + 1], a1);
+        a2 = fma(Minv[i + (size_t)ld * (j + 2)], ys[j + 2], a2);
+        a3 = fma(Minv[i + (size_t)ld * (j + 3)], ys[j + 3], a3);
+      }
+      for (; j < mu; ++j) a0 = fma(Minv[i + (size_t)ld * j], ys[j], a0);
+      y[i] = 0.5 * g * fma(gi2, (a0 + a1) + (a2 + a3), ys[i]);
+    }
+  }
+  double err = 0.0;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < mu * mu; idx += gridDim.x * blockDim.x) {
+    const int i = idx % mu, j = idx / mu;
+    const size_t o = i + (size_t)ld * j;
+    const double v = 0.5 * ((i == j ? 1.0 : 0.0) + 0.5 * fma(g2, M[o], gi2 * Minv[o]));
+    M[o] = v;
+    const double dv = v - (i == j ? 1.0 : 0.0);
+    err = fma(dv, dv, err);
+  }
+  double ev[1] = {err};
+  block_sum<1>(ev, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = ev[0];
+  if (!last_block(counter)) return;
+  sum_partials(part, gridDim.x, 1, tot, red);
+  if (threadIdx.x == 0) {
+    st->scal[1] = sqrt(tot[0]);
+    if (!isfinite(tot[0])) st->status = FAB_ENUMERIC;
+    *counter = 0;
+  }
 }
 
 cudaError_t launch_db_update(double* M, const double* Minv, int ld, const int* mdev, double* y, const double* logdet,
-                             int scale_on, DevState* st, cudaStream_t s) {
-  k_db_update<<<1, 1024, 0, s>>>(M, Minv, ld, mdev, y, logdet, scale_on, st);
+                             int scale_on, DevState* st, cudaStream_t s, int mmax, double* part, unsigned* counter) {
+  const int nb = (mmax * mmax + 1023) / 1024;  // about four entries per thread
+  const int grid = nb < 1 ? 1 : (nb > 64 ? 64 : nb);
+  k_db_update<<<grid, 256, 0, s>>>(M, Minv, ld, mdev, y, logdet, scale_on, part, counter, st);
   return cudaGetLastError();
 }
 
@@ -767,32 +864,51 @@ __global__ void __launch_bounds__(256) k_qr_cluster(double* __restrict__ A, int 
   }
   __syncthreads();
   const int steps = mu < rows ? mu : rows;
+  // reflector j from the owner's column j (block-wide): v below the diagonal, beta on it
+  auto reflector = [&](int j) {
+    double* cj = loc + (size_t)(j / CL) * rows;
+    double ss = 0.0;
+    for (int i = j + 1 + tid; i < rows; i += blockDim.x) ss = fma(cj[i], cj[i], ss);
+    ss = warp_sum(ss);
+    if (lane == 0) red[warp] = ss;
+    __syncthreads();
+    double sig = 0.0;
+    for (int w = 0; w < nw; ++w) sig += red[w];
+    const double alpha = cj[j];
+    double t = 0.0, beta = alpha, vinv = 0.0;
+    if (sig != 0.0) {
+      const double nrm = sqrt(fma(alpha, alpha, sig));
+      beta = (alpha <= 0.0) ? nrm : -nrm;
+      t = (beta - alpha) / beta;
+      vinv = 1.0 / (alpha - beta);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < rows; i += blockDim.x) cj[i] *= vinv;
+    if (tid == 0) {
+      cj[j] = beta;
+      s_tau[j] = t;
+    }
+    __syncthreads();
+  };
+  // H_j = I - tau v v^T (v_j = 1, v in vbuf) applied to one local column by one warp;
+  // the dot product runs as four independent chains (FP64 latency bounds it)
+  auto apply_col = [&](double* col, int j, double tj) {
+    double d0 = (lane == 0) ? col[j] : 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+    int i = j + 1 + lane;
+    for (; i + 96 < rows; i += 128) {
+      d0 = fma(vbuf[i], col[i], d0);
+      d1 = fma(vbuf[i + 32], col[i + 32], d1);
+      d2 = fma(vbuf[i + 64], col[i + 64], d2);
+      d3 = fma(vbuf[i + 96], col[i + 96], d3);
+    }
+    for (; i < rows; i += 32) d0 = fma(vbuf[i], col[i], d0);
+    const double d = warp_sum((d0 + d1) + (d2 + d3)) * tj;
+    if (lane == 0) col[j] -= d;
+    for (int q = j + 1 + lane; q < rows; q += 32) col[q] = fma(-d, vbuf[q], col[q]);
+  };
   for (int j = 0; j < steps; ++j) {
     const int owner = j % CL;
-    if (r == owner) {
-      double* cj = loc + (size_t)(j / CL) * rows;
-      double ss = 0.0;
-      for (int i = j + 1 + tid; i < rows; i += blockDim.x) ss = fma(cj[i], cj[i], ss);
-      ss = warp_sum(ss);
-      if (lane == 0) red[warp] = ss;
-      __syncthreads();
-      double sig = 0.0;
-      for (int w = 0; w < nw; ++w) sig += red[w];
-      const double alpha = cj[j];
-      double t = 0.0, beta = alpha, vinv = 0.0;
-      if (sig != 0.0) {
-        const double nrm = sqrt(fma(alpha, alpha, sig));
-        beta = (alpha <= 0.0) ? nrm : -nrm;
-        t = (beta - alpha) / beta;
-        vinv = 1.0 / (alpha - beta);
-      }
-      __syncthreads();
-      for (int i = j + 1 + tid; i < rows; i += blockDim.x) cj[i] *= vinv;
-      if (tid == 0) {
-        cj[j] = beta;
-        s_tau[j] = t;
-      }
-    }
+    if (r == owner) reflector(j);
     cluster.sync();  // reflector j is published in the owner's shared memory
     const double* rcol = cluster.map_shared_rank(loc + (size_t)(j / CL) * rows, owner);
     const double* rtau = cluster.map_shared_rank(s_tau, owner);
@@ -800,17 +916,10 @@ __global__ void __launch_bounds__(256) k_qr_cluster(double* __restrict__ A, int 
     const double tj = rtau[j];
     if (r != owner && tid == 0) s_tau[j] = tj;
     __syncthreads();
-    // apply H_j = I - tau v v^T (v_j = 1) to my columns g > j, one warp per column
+    // apply H_j to my columns g > j, one warp per column
     int first = (j + 1 - r + CL - 1) / CL;  // first local column with g > j
     if (first < 0) first = 0;
-    for (int lc = first + warp; lc < nloc; lc += nw) {
-      double* col = loc + (size_t)lc * rows;
-      double d = (lane == 0) ? col[j] : 0.0;
-      for (int i = j + 1 + lane; i < rows; i += 32) d = fma(vbuf[i], col[i], d);
-      d = warp_sum(d) * tj;
-      if (lane == 0) col[j] -= d;
-      for (int i = j + 1 + lane; i < rows; i += 32) col[i] = fma(-d, vbuf[i], col[i]);
-    }
+    for (int lc = first + warp; lc < nloc; lc += nw) apply_col(loc + (size_t)lc * rows, j, tj);
     __syncthreads();
   }
   cluster.sync();  // no CTA exits while others may still read its shared memory
@@ -1543,8 +1652,231 @@ cudaError_t launch_qr(double* A, int lda, int rows, const int* mdev, int max_col
   return launch_householder_qr(A, lda, rows, mdev, extra, tau, s);
 }
 
+// Blocked LU with partial pivoting over a cluster of CL CTAs (ties to the smallest
+// row; rows swapped across the whole matrix, as k_lu_cluster; piv[k] = row swapped
+// with k; log|det| to *logdet). Panels of kLuB columns are owned cyclically (panel P
+// by CTA P % CL, its columns in that CTA's shared memory). Panel P is factored by its
+// owner alone (CTA barriers only) and copied to the owner's publish buffer; after one
+// cluster barrier every CTA copies it and, on each of its columns, applies the
+// panel's row swaps, then (right of the panel) the unit-lower triangular solve for
+// the U block and the rank-kLuB update of the rows below. A publish buffer is written
+// again only for the owner's next panel, CL panels later, after every CTA has passed
+// the barriers of the panels in between (and so has copied it): one cluster barrier
+// per panel, and the factorization of panel P+1 overlaps the other CTAs' updates.
+constexpr int kLuB = 8;
+template <int CL>
+__global__ void __launch_bounds__(256) k_lu_blocked(double* __restrict__ M, int ld, const int* __restrict__ mdev,
+                                                    int* __restrict__ piv, double* __restrict__ logdet,
+                                                    DevState* st) {
+  extern __shared__ __align__(16) double smem_d[];
+  __shared__ double rv[32];
+  __shared__ unsigned long long rk[32];
+  __shared__ int ri[32];
+  __shared__ int s_pp[kLuB];
+  __shared__ int s_piv[kMaxM];
+  __shared__ double s_ld;  // this CTA's sum of log|U_jj| over its panels (panel order)
+  cg::cluster_group cluster = cg::this_cluster();
+  const int r = (int)cluster.block_rank();
+  const int mu = *mdev;
+  const int np = (mu + kLuB - 1) / kLuB;
+  const int maxp = (np + CL - 1) / CL;
+  const int myp = r < np ? (np - 1 - r) / CL + 1 : 0;  // panels r, r + CL, ...
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  double* loc = smem_d;                                  // my panels: column (lp, jj) at loc + (lp kLuB + jj) mu
+  double* pub = loc + (size_t)maxp * kLuB * mu;          // published panel, kLuB x mu
+  int* pub_piv = reinterpret_cast<int*>(pub + (size_t)kLuB * mu);  // kLuB ints
+  double* cur = pub + (size_t)kLuB * mu + kLuB;          // copy of the panel being applied
+  for (int lp = 0; lp < myp; ++lp)
+    for (int jj = 0; jj < kLuB; ++jj) {
+      const int g = (lp * CL + r) * kLuB + jj;
+      if (g >= mu) break;
+      double* dst = loc + (size_t)(lp * kLuB + jj) * mu;
+      const double* src = M + (size_t)g * ld;
+      for (int i = tid; i < mu; i += blockDim.x) dst[i] = src[i];
+    }
+  if (tid == 0) s_ld = 0.0;
+  __syncthreads();
+  // factors panel Q in this (its owner's) CTA and copies it to the publish buffer
+  auto factor = [&](int Q) {
+    const int lpq = Q / CL, q0 = Q * kLuB;
+    const int wq = mu - q0 < kLuB ? mu - q0 : kLuB;
+    double* pc = loc + (size_t)lpq * kLuB * mu;
+    for (int jj = 0; jj < wq; ++jj) {
+      const int j = q0 + jj;
+      double* cj = pc + (size_t)jj * mu;
+      // largest |a| (ties to the smallest row) compared on the bit patterns: for
+      // non-negative doubles the unsigned order of the bits is the order of the
+      // values, and the integer pipe has none of the FP64 latency; NaNs are skipped
+      unsigned long long best = 0;
+      int bi = mu;
+      for (int i = j + tid; i < mu; i += blockDim.x) {
+        const unsigned long long key = (unsigned long long)__double_as_longlong(cj[i]) & 0x7FFFFFFFFFFFFFFFull;
+        if (key <= 0x7FF0000000000000ull && (key > best || bi == mu)) {
+          best = key;
+          bi = i;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        rk[warp] = best;
+        ri[warp] = bi;
+      }
+      __syncthreads();
+      unsigned long long bb = 0;
+      int p = mu;
+      for (int w = 0; w < nw; ++w)
+        if (rk[w] > bb || (rk[w] == bb && ri[w] < p)) {
+          bb = rk[w];
+          p = ri[w];
+        }
+      if (p < j || p >= mu) {  // only with non-finite entries
+        p = j;
+        if (tid == 0) st->status = FAB_ENUMERIC;
+      }
+      if (tid < wq && p != j) {  // the panel's rows j and p
+        double* c2 = pc + (size_t)tid * mu;
+        const double t = c2[j];
+        c2[j] = c2[p];
+        c2[p] = t;
+      }
+      if (tid == 0) s_piv[j] = p;
+      __syncthreads();
+      const double pv = cj[j];
+      if (tid == 0 && (pv == 0.0 || !isfinite(pv))) st->status = FAB_ENUMERIC;
+      const double pinv = pv != 0.0 ? 1.0 / pv : 0.0;  // log|pv| is summed after the factorization
+      for (int i = j + 1 + tid; i < mu; i += blockDim.x) cj[i] *= pinv;
+      __syncthreads();
+      for (int j2 = jj + 1 + warp; j2 < wq; j2 += nw) {
+        double* c2 = pc + (size_t)j2 * mu;
+        const double u = c2[j];
+        for (int i = j + 1 + lane; i < mu; i += 32) c2[i] = fma(-cj[i], u, c2[i]);
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < wq * mu; idx += blockDim.x) pub[idx] = pc[idx];
+    if (tid < wq) pub_piv[tid] = s_piv[q0 + tid];
+    __syncthreads();
+  };
+  // applies the panel in cur (columns c0.., width wP, pivots s_pp) to my local column lc
+  auto apply = [&](int lc, int c0, int wP) {
+    const int g = ((lc / kLuB) * CL + r) * kLuB + lc % kLuB;
+    double* col = loc + (size_t)lc * mu;
+    if (lane == 0)
+      for (int t = 0; t < wP; ++t) {
+        const int pr = s_pp[t], jr = c0 + t;
+        if (pr != jr && pr > jr && pr < mu) {
+          const double x = col[jr];
+          col[jr] = col[pr];
+          col[pr] = x;
+        }
+      }
+    __syncwarp();
+    if (g >= c0 + wP) {
+      for (int t = 0; t < wP; ++t) {  // U block: unit-lower solve with the panel's top wP x wP, lanes t+1..wP-1
+        const double x = col[c0 + t];
+        __syncwarp();
+        if (lane > t && lane < wP) col[c0 + lane] = fma(-cur[(size_t)t * mu + c0 + lane], x, col[c0 + lane]);
+        __syncwarp();
+      }
+      double u[kLuB];
+#pragma unroll
+      for (int t = 0; t < kLuB; ++t) u[t] = t < wP ? col[c0 + t] : 0.0;
+      for (int i = c0 + wP + lane; i < mu; i += 32) {
+        double a = col[i];
+#pragma unroll
+        for (int t = 0; t < kLuB; ++t)
+          if (t < wP) a = fma(-cur[(size_t)t * mu + i], u[t], a);
+        col[i] = a;
+      }
+    }
+    __syncwarp();
+  };
+  if (r == 0) factor(0);  // panel 0's owner
+  for (int P = 0; P < np; ++P) {
+    const int owner = P % CL, lpo = P / CL, c0 = P * kLuB;
+    const int wP = mu - c0 < kLuB ? mu - c0 : kLuB;
+    cluster.sync();  // panel P is published
+    {
+      const double* rp = cluster.map_shared_rank(pub, owner);
+      const int* rpp = cluster.map_shared_rank(pub_piv, owner);
+      for (int idx = tid; idx < wP * mu; idx += blockDim.x)
+        if (idx % mu >= c0) cur[idx] = rp[idx];
+      if (tid < wP) s_pp[tid] = rpp[tid];
+    }
+    __syncthreads();
+    // the owner of panel P+1 brings that panel up to date and factors and publishes it
+    // before updating its other columns (the cluster barrier still waits for every
+    // CTA's updates: measured, this order costs nothing and gains nothing)
+    const int nxt = P + 1 < np ? (P + 1) % CL : -1, lpn = (P + 1) / CL;
+    if (r == nxt) {
+      for (int jj = warp; jj < kLuB; jj += nw)
+        if ((P + 1) * kLuB + jj < mu) apply(lpn * kLuB + jj, c0, wP);
+      __syncthreads();
+      factor(P + 1);
+    }
+    for (int lc = warp; lc < myp * kLuB; lc += nw) {
+      const int lp = lc / kLuB;
+      const int g = (lp * CL + r) * kLuB + lc % kLuB;
+      if (g >= mu || (r == owner && lp == lpo) || (r == nxt && lp == lpn)) continue;
+      apply(lc, c0, wP);
+    }
+    __syncthreads();  // cur and s_pp are refilled for the next panel
+  }
+  {  // log|U_jj| of my panels' columns, in parallel, summed in a fixed order
+    double a = 0.0;
+    for (int lc = tid; lc < myp * kLuB; lc += blockDim.x) {
+      const int g = ((lc / kLuB) * CL + r) * kLuB + lc % kLuB;
+      if (g < mu) {
+        const double d = loc[(size_t)lc * mu + g];
+        if (d != 0.0 && isfinite(d)) a += log(fabs(d));
+      }
+    }
+    a = warp_sum(a);
+    if (lane == 0) rv[warp] = a;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += rv[w];
+      s_ld = t;
+    }
+  }
+  cluster.sync();
+  for (int lp = 0; lp < myp; ++lp)
+    for (int jj = 0; jj < kLuB; ++jj) {
+      const int g = (lp * CL + r) * kLuB + jj;
+      if (g >= mu) break;
+      const double* srcl = loc + (size_t)(lp * kLuB + jj) * mu;
+      double* dst = M + (size_t)g * ld;
+      for (int i = tid; i < mu; i += blockDim.x) dst[i] = srcl[i];
+      if (tid == 0) piv[g] = s_piv[g];
+    }
+  if (r == 0 && tid == 0 && logdet) {  // partial sums in rank order: deterministic
+    double a = 0.0;
+    for (int q = 0; q < CL; ++q) a += *cluster.map_shared_rank(&s_ld, q);
+    *logdet = a;
+  }
+  cluster.sync();  // no CTA exits while rank 0 may still read its s_ld
+}
+
 cudaError_t launch_lu_fast(double* M, int ld, const int* mdev, int max_m, int* piv, double* logdet, DevState* st,
                            cudaStream_t s) {
+  {  // blocked: my panels, the publish buffer (+ pivots) and the applied copy
+    const int np = (max_m + kLuB - 1) / kLuB;
+    const size_t smem = ((size_t)((np + 15) / 16) * kLuB * max_m + 2 * (size_t)kLuB * max_m + kLuB) * sizeof(double);
+    if (smem <= 200 * 1024) {
+      void* args[] = {&M, &ld, (void*)&mdev, &piv, &logdet, &st};
+      cudaError_t e = launch_cluster(k_lu_blocked<16>, 16, smem, s, args);
+      if (e == cudaSuccess) return e;
+      cudaGetLastError();
+    }
+  }
   for (int cl : {16, 8}) {
     const size_t smem = ((size_t)((max_m + cl - 1) / cl) + 1) * max_m * sizeof(double);
     if (smem > 200 * 1024) continue;

@@ -35,8 +35,10 @@ cudaError_t launch_lincomb(double* out, const double* X0, const double* X1, cons
 cudaError_t launch_lu(double* M, int ld, const int* mdev, int* piv, double* logdet, DevState* st, cudaStream_t s);
 cudaError_t launch_lu_solve(const double* LU, int ld, const int* piv, const int* mdev, int mmax, double* B, int ldb,
                             int identity_rhs, cudaStream_t s);
+// One Denman-Beavers step over several blocks (part: gridDim doubles of partials,
+// counter: a zeroed last-block counter, left zeroed).
 cudaError_t launch_db_update(double* M, const double* Minv, int ld, const int* mdev, double* y, const double* logdet,
-                             int scale_on, DevState* st, cudaStream_t s);
+                             int scale_on, DevState* st, cudaStream_t s, int mmax, double* part, unsigned* counter);
 cudaError_t launch_first_column(const double* M, const int* mdev, double* y, cudaStream_t s);
 cudaError_t launch_prep_coef(const double* c, const double* sigma, const int* mdev, const DevState* st, double* coef,
                              cudaStream_t s);
