@@ -668,6 +668,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   const int ntiles = (n + kTileRows - 1) / kTileRows;
   int c_done = 0;          // basis columns 1..c_done are built
   int m_prev = 0;          // dimension of the previous solution (growing m)
+  int qr_cols = 0;         // columns of ws.qr already factored by this solve's previous pass
   double err_est = 0.0;
   int rc_final = FAB_OK;
   int lsqr_iters = 0, fh_iters = 0;
@@ -760,16 +761,28 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   const bool lsqr = !breakdown && (p->method == FAB_SKETCHED_LS || p->method == FAB_BG_LS || wh > 0);
   const double* yptr = nullptr;
   if (!breakdown && p->method == FAB_SKETCHED_FAST) {
-    // y = argmin || Theta V_m z - Theta v_{m+1} || (sketch-and-solve form of eq. sFOM)
-    CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * (mu + 1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 1, ws.tau, s));
+    // y = argmin || Theta V_m z - Theta v_{m+1} || (sketch-and-solve form of eq. sFOM).
+    // Growing m: the previous pass's columns stay factored and its extra column
+    // (Theta v_{m_prev+1}, already transformed) is the next column to factor, so only
+    // the new sketch columns are copied and the QR continues at column m_prev.
+    const bool inc = qr_cols > 0 && qr_cols <= mu && qr_cluster_fits(p->s, m + 1);
+    const int q0 = inc ? qr_cols : 0, fresh = inc ? qr_cols + 1 : 0;
+    CK(cudaMemcpyAsync(ws.qr + (size_t)fresh * p->s, ws.SV + (size_t)fresh * p->s,
+                       (size_t)p->s * (mu + 1 - fresh) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 1, ws.tau, s, q0, fresh));
+    qr_cols = mu;
     LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.qr + (size_t)mu * p->s, ws.y, 0, nullptr, s, m));
     yptr = ws.y;
   } else if (lsqr) {
     if (p->method == FAB_SKETCHED_LS) {
       // Blendenpik: R from the QR of Theta V_m; LSQR on V_m R^{-1} u ~ v_{m+1}; y = R^{-1} u
-      CK(cudaMemcpyAsync(ws.qr, ws.SV, (size_t)p->s * mu * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 0, ws.tau, s));
+      // (growing m: the previous pass's columns stay factored, as above)
+      const bool inc = qr_cols > 0 && qr_cols <= mu && qr_cluster_fits(p->s, m);
+      const int q0 = inc ? qr_cols : 0;
+      CK(cudaMemcpyAsync(ws.qr + (size_t)q0 * p->s, ws.SV + (size_t)q0 * p->s, (size_t)p->s * (mu - q0) * sizeof(double),
+                         cudaMemcpyDeviceToDevice, s));
+      LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 0, ws.tau, s, q0, q0));
+      qr_cols = mu;
     } else if (wh > 0) {
       // Alg. 3 on the whitened basis: LSQR on the stored columns with the implicit
       // R_{wh-1}^{-1} as right preconditioner; u is y in whitened coordinates

@@ -846,7 +846,7 @@ namespace cg = cooperative_groups;
 template <int CL>
 __global__ void __launch_bounds__(256) k_qr_cluster(double* __restrict__ A, int lda, int rows,
                                                     const int* __restrict__ mdev, int extra,
-                                                    double* __restrict__ tau_out) {
+                                                    double* __restrict__ tau_out, int start, int fresh) {
   extern __shared__ __align__(16) double smem_d[];
   __shared__ double red[32];
   __shared__ double s_tau[kMaxM];
@@ -906,7 +906,26 @@ __global__ void __launch_bounds__(256) k_qr_cluster(double* __restrict__ A, int 
     if (lane == 0) col[j] -= d;
     for (int q = j + 1 + lane; q < rows; q += 32) col[q] = fma(-d, vbuf[q], col[q]);
   };
-  for (int j = 0; j < steps; ++j) {
+  // Columns below `start` were factored by an earlier call (v_j below the diagonal
+  // of column j, tau_j in tau_out); columns start .. fresh-1 carry that call's
+  // transformation already (its extra column). The old reflectors are applied, in
+  // order, to my columns g >= fresh, each column on its own, with no cluster barrier
+  // (the reflectors are fixed); the factorization then continues at column start.
+  if (start > 0) {
+    for (int j = tid; j < start; j += blockDim.x) s_tau[j] = tau_out[j];
+    for (int j = 0; j < start && j < steps; ++j) {
+      __syncthreads();  // vbuf is free
+      const double* vj = A + (size_t)j * lda;
+      for (int i = j + 1 + tid; i < rows; i += blockDim.x) vbuf[i] = vj[i];
+      __syncthreads();
+      const double tj = s_tau[j];
+      int first = (fresh - r + CL - 1) / CL;  // first local column with g >= fresh
+      if (first < 0) first = 0;
+      for (int lc = first + warp; lc < nloc; lc += nw) apply_col(loc + (size_t)lc * rows, j, tj);
+    }
+    __syncthreads();
+  }
+  for (int j = start; j < steps; ++j) {
     const int owner = j % CL;
     if (r == owner) reflector(j);
     cluster.sync();  // reflector j is published in the owner's shared memory
@@ -1637,18 +1656,25 @@ cudaError_t launch_cluster(K kernel, int cl, size_t smem, cudaStream_t s, void**
 }  // namespace
 
 // Cluster QR when the matrix fits the cluster's shared memory, else the one-block kernel.
+bool qr_cluster_fits(int rows, int ncols) {
+  for (int cl : {16, 8})
+    if (((size_t)((ncols + cl - 1) / cl) + 1) * rows * sizeof(double) <= 200 * 1024) return true;
+  return false;
+}
+
 cudaError_t launch_qr(double* A, int lda, int rows, const int* mdev, int max_cols, int extra, double* tau,
-                      cudaStream_t s) {
+                      cudaStream_t s, int start, int fresh) {
   const int ncols = max_cols + extra;
   for (int cl : {16, 8}) {
     const size_t smem = ((size_t)((ncols + cl - 1) / cl) + 1) * rows * sizeof(double);
     if (smem > 200 * 1024) continue;
-    void* args[] = {&A, &lda, &rows, (void*)&mdev, &extra, &tau};
+    void* args[] = {&A, &lda, &rows, (void*)&mdev, &extra, &tau, &start, &fresh};
     cudaError_t e = cl == 16 ? launch_cluster(k_qr_cluster<16>, 16, smem, s, args)
                              : launch_cluster(k_qr_cluster<8>, 8, smem, s, args);
     if (e == cudaSuccess) return e;
     cudaGetLastError();
   }
+  if (start > 0) return cudaErrorNotSupported;  // the one-CTA fallback starts at column 0
   return launch_householder_qr(A, lda, rows, mdev, extra, tau, s);
 }
 

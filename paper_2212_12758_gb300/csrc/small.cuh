@@ -17,8 +17,14 @@ struct LsqrVecs {
 cudaError_t launch_householder_qr(double* A, int lda, int rows, const int* mdev, int extra, double* tau,
                                   cudaStream_t s);
 // Cluster (DSMEM) versions when the matrix fits a cluster's shared memory.
+// Householder QR of the rows x (mu + extra) matrix A (R in the upper triangle, v_j below
+// the diagonal, tau_j in tau). start > 0: columns below start hold an earlier call's
+// factorization, columns start .. fresh-1 already carry its reflectors (its extra
+// column), columns from fresh on are new; only the rest is factored (cluster path
+// only: qr_cluster_fits).
 cudaError_t launch_qr(double* A, int lda, int rows, const int* mdev, int max_cols, int extra, double* tau,
-                      cudaStream_t s);
+                      cudaStream_t s, int start = 0, int fresh = 0);
+bool qr_cluster_fits(int rows, int ncols);
 cudaError_t launch_lu_fast(double* M, int ld, const int* mdev, int max_m, int* piv, double* logdet, DevState* st,
                            cudaStream_t s);
 // mmax: largest *mdev (R's triangle is staged in shared memory when mmax <= 150; 0: never)
