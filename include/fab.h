@@ -97,7 +97,7 @@ typedef struct fab_params {
   int m;             /* Krylov dimension, 1 <= m <= 1024                            */
   int k;             /* truncation window of Alg. 2, 1 <= k <= 8 (ignored by Arnoldi) */
   int s;             /* sketch rows, m+1 <= s <= 4096 (sketched methods)            */
-  int zeta;          /* nonzeros per column of the sparse-sign sketch, 1..min(s,64) */
+  int zeta;          /* nonzeros per column of the sparse-sign sketch, 1..min(s,16) */
   int sketch;        /* fab_sketch                                                 */
   uint64_t seed;     /* sketch seed                                                */
   int method;        /* fab_method                                                 */

@@ -514,26 +514,69 @@ __device__ __forceinline__ void sparse_rows(const SketchDev& sk, long long j, in
   }
 }
 
-__global__ void k_sparse_pattern(int n, SketchDev sk, unsigned short* __restrict__ pat) {
-  const int Z = pat_stride(sk.zeta);
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+// The sparse-sign pattern transposed per chunk (one block per 4096-row chunk): count
+// the rows that hit each sketch row, scan the counts into the offsets, then place each
+// row (and its sign) in its sketch rows' lists. Order inside a list is not fixed; the
+// sums taken over it are exact in int64, so the sketch does not depend on it.
+__global__ void k_sparse_pattern(int n, SketchDev sk, unsigned char* __restrict__ tab) {
+  extern __shared__ int s_cnt[];  // s counts, then s cursors
+  int* s_pos = s_cnt + sk.s;
+  const int chunk = blockIdx.x;
+  unsigned char* rec = tab + (size_t)chunk * sparse_rec_bytes(sk.s, sk.zeta);
+  unsigned* off = reinterpret_cast<unsigned*>(rec);
+  unsigned short* ent = reinterpret_cast<unsigned short*>(rec + sparse_off_bytes(sk.s));
+  for (int q = threadIdx.x; q < sk.s; q += blockDim.x) s_cnt[q] = 0;
+  __syncthreads();
+  for (int rl = threadIdx.x; rl < kChunk; rl += blockDim.x) {
+    const long long j = (long long)chunk * kChunk + rl;
+    if (j >= n) break;
+    int rows[kMaxZeta];
+    sparse_rows(sk, j, rows);
+#pragma unroll
+    for (int q = 0; q < kMaxZeta; ++q)
+      if (q < sk.zeta) atomicAdd(&s_cnt[rows[q]], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned a = 0;
+    for (int q = 0; q < sk.s; ++q) {
+      off[q] = a;
+      s_pos[q] = (int)a;
+      a += (unsigned)s_cnt[q];
+    }
+    off[sk.s] = a;
+  }
+  __syncthreads();
+  for (int rl = threadIdx.x; rl < kChunk; rl += blockDim.x) {
+    const long long j = (long long)chunk * kChunk + rl;
+    if (j >= n) break;
     int rows[kMaxZeta];
     sparse_rows(sk, j, rows);
     const unsigned long long sg = rng_u(sk.st_signs, (unsigned long long)j);
 #pragma unroll
     for (int q = 0; q < kMaxZeta; ++q)
-      if (q < Z) pat[(size_t)j * Z + q] = q < sk.zeta ? (unsigned short)(rows[q] | (((sg >> q) & 1ull) << 15)) : 0;
+      if (q < sk.zeta) {
+        const int p = atomicAdd(&s_pos[rows[q]], 1);
+        ent[p] = (unsigned short)(rl | (((sg >> q) & 1ull) << 15));
+      }
   }
 }
 
 cudaError_t launch_sparse_pattern(int n, const SketchDev& sk, unsigned short* pat, cudaStream_t s) {
-  if (sk.s > 32768 || sk.zeta > kMaxZeta) return cudaErrorInvalidValue;
-  k_sparse_pattern<<<grid_rows(n), kThreads, 0, s>>>(n, sk, pat);
+  if (sk.s < 1 || sk.s > kMaxS || sk.zeta < 1 || sk.zeta > kMaxZeta) return cudaErrorInvalidValue;
+  const int nchunks = (n + kChunk - 1) / kChunk;
+  if (nchunks < 1) return cudaSuccess;
+  const size_t smem = (size_t)2 * sk.s * sizeof(int);
+  if (smem > 48 * 1024) {
+    const cudaError_t e = ensure_smem_limit((const void*)k_sparse_pattern, smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_sparse_pattern<<<nchunks, 256, smem, s>>>(n, sk, reinterpret_cast<unsigned char*>(pat));
   return cudaGetLastError();
 }
 
 // Sparse-sign chunk: every row j scatters +-X_j into its zeta sketch rows (exact
-// int64 sums in shared memory); TAB reads the rows and signs from sk.pat.
+// int64 sums in shared memory); TAB gathers from the chunk lists of sk.pat instead.
 template <typename TV, bool TAB>
 __device__ void sketch_chunk_sparse(const TV (&v)[kRowsPerThread], int chunk, int n, const SketchDev& sk,
                                     unsigned long long* acc, double* s_acc, int* s_int) {
@@ -543,26 +586,30 @@ __device__ void sketch_chunk_sparse(const TV (&v)[kRowsPerThread], int chunk, in
   for (int i = 0; i < kRowsPerThread; ++i) e = max(e, exp_field(v[i]));
   const int E = block_max_int(e, s_int);
   if (TAB) {
-    // a column's entries are one (zeta <= 8) or two 16-byte vector loads
+    // gather instead of scatter: the chunk's X in shared memory, then one warp per
+    // sketch row sums the entries of that row's list (no atomics; exact int64 sums)
+    long long* xb = reinterpret_cast<long long*>(reinterpret_cast<unsigned char*>(acc) + ((size_t)sk.s * 8 + 15) / 16 * 16);
 #pragma unroll
     for (int i = 0; i < kRowsPerThread; ++i) {
       const long long j = (long long)chunk * kChunk + i * kThreads + t;
-      const long long X = (j < n) ? to_fixed(v[i], E) : 0ll;
-      if (X != 0) {
-        const int Z = pat_stride(sk.zeta);
-        const uint4* src = reinterpret_cast<const uint4*>(sk.pat + (size_t)j * Z);
-        for (int h = 0; h < Z / 8; ++h) {
-          const uint4 a = __ldg(src + h);
-          const unsigned wv[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            if (h * 8 + q < sk.zeta) {
-              const unsigned w = (wv[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu;
-              atomicAdd(acc + (w & 0x7FFFu), (unsigned long long)((w >> 15) ? -X : X));
-            }
-          }
-        }
+      xb[i * kThreads + t] = (j < n) ? to_fixed(v[i], E) : 0ll;
+    }
+    __syncthreads();
+    const unsigned char* rec = reinterpret_cast<const unsigned char*>(sk.pat) + (size_t)chunk * sparse_rec_bytes(sk.s, sk.zeta);
+    const unsigned* off = reinterpret_cast<const unsigned*>(rec);
+    const unsigned short* ent = reinterpret_cast<const unsigned short*>(rec + sparse_off_bytes(sk.s));
+    const int lane = t & 31;
+    for (int q = t >> 5; q < sk.s; q += kThreads / 32) {
+      const unsigned lo = __ldg(off + q), hi = __ldg(off + q + 1);
+      long long sum = 0;
+      for (unsigned e = lo + lane; e < hi; e += 32) {
+        const unsigned w = __ldg(ent + e);
+        const long long x = xb[w & 0x0FFFu];
+        sum += (w >> 15) ? -x : x;
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (lane == 0) acc[q] += (unsigned long long)sum;
     }
   }
   for (int i = 0; i < kRowsPerThread && !TAB; ++i) {
@@ -745,7 +792,8 @@ size_t update_smem_bytes(int kind, int nc, int s) {
   size_t b = ((size_t)nc * 8 + 15) / 16 * 16;
   if (kind == SK_SRHT || kind == SK_SPARSE || kind == SK_SPARSE_TAB) b += ((size_t)s * 8 + 15) / 16 * 16;
   if (kind == SK_SRHT) b += (size_t)(kChunk + kChunk / 16) * 8 + (size_t)s * 4;
-  if (kind == SK_SPARSE || kind == SK_SPARSE_TAB) b += (size_t)s * 8;
+  if (kind == SK_SPARSE || kind == SK_SPARSE_TAB) b += ((size_t)s * 8 + 15) / 16 * 16;
+  if (kind == SK_SPARSE_TAB) b += (size_t)kChunk * 8;  // the chunk's X for the gather
   return b;
 }
 

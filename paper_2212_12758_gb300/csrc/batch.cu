@@ -252,7 +252,7 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       sk.st_D = rng_state(p.seed, 3);
       sk.P = ar.take<int>(s);
       sk.part = ar.take<double>(skpart_need[j]);
-      sk.pat = kind[j] == SK_SPARSE_TAB ? ar.take<unsigned short>((size_t)n * pat_stride(p.zeta)) : nullptr;
+      sk.pat = kind[j] == SK_SPARSE_TAB ? ar.take<unsigned short>(sparse_table_bytes(n, p.s, p.zeta) / 2) : nullptr;
       J.sk_scale = kind[j] == SK_SRHT ? 1.0 / sqrt((double)p.s) : (kind[j] == SK_SPARSE_TAB ? 1.0 / sqrt((double)p.zeta) : 1.0);
       double* bst = ar.take<double>(n);
       double* xst = ar.take<double>(n);

@@ -395,7 +395,7 @@ int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
       {&h->skpart, (size_t)nchunks * s * 8},
       {&h->SV, (size_t)s * (m + 1) * 8},
       {&h->P, (size_t)s * 4},
-      {&h->spat, (sketched(p->method) && p->sketch == FAB_SK_SPARSE_SIGN) ? (size_t)n * pat_stride(p->zeta) * 2 : 0},
+      {&h->spat, (sketched(p->method) && p->sketch == FAB_SK_SPARSE_SIGN) ? sparse_table_bytes(n, s, p->zeta) : 0},
       {&h->qr, (size_t)s * (m + 1) * 8},
       {&h->tau, (size_t)(m + 1) * 8},
       {&h->y, (size_t)(m + 1) * 8},

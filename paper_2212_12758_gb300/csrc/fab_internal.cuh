@@ -52,12 +52,21 @@ struct SketchDev {
   __nv_bfloat16* Wbf;  // Gaussian: BF16 copy of the basis (column c at Wbf + c * ldbf)
   int64_t ldbf;
   double* part;        // nparts x s block partials (block-major), nparts <= nchunks
-  // sparse sign: column j's entries at pat[j Z .. j Z + zeta - 1], Z = pat_stride(zeta)
-  // (bits 0..14 the row, bit 15 the sign), or NULL to draw the rows on the fly
+  // sparse sign: the pattern transposed per 4096-row chunk (see sparse_rec_bytes): for
+  // chunk c at pat + c * sparse_rec_bytes(s, zeta) bytes, uint32 offsets off[0..s] and
+  // uint16 entries (bits 0..11 the row in the chunk, bit 15 the sign) with the rows
+  // that hit sketch row q at [off[q], off[q+1]); NULL to draw the rows on the fly
   const unsigned short* pat;
 };
-// Entries per column of the sparse sign table: 8 (zeta <= 8) or 16 (16-byte aligned rows).
-__host__ __device__ __forceinline__ int pat_stride(int zeta) { return zeta <= 8 ? 8 : 16; }
+// Bytes of one chunk's record in the transposed sparse-sign table: the s+1 offsets, then
+// zeta entries per row of the chunk, each part padded to 16 bytes.
+__host__ __device__ __forceinline__ size_t sparse_off_bytes(int s) { return ((size_t)(s + 1) * 4 + 15) / 16 * 16; }
+__host__ __device__ __forceinline__ size_t sparse_rec_bytes(int s, int zeta) {
+  return sparse_off_bytes(s) + ((size_t)zeta * 4096 * 2 + 15) / 16 * 16;
+}
+__host__ __device__ __forceinline__ size_t sparse_table_bytes(int64_t n, int s, int zeta) {
+  return (size_t)((n + 4095) / 4096) * sparse_rec_bytes(s, zeta);
+}
 
 // ----------------------------------------------------------------- SplitMix64
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -322,7 +331,7 @@ cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const
                           SketchDev& sk, DevState* st, cudaStream_t s, int gate = 0);
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
                                  DevState* st, cudaStream_t s, int gate = 0);
-// The sparse sign pattern of sk (rows and signs of every column) into pat (n x pat_stride(zeta)).
+// The sparse sign pattern of sk, transposed per chunk, into pat (sparse_table_bytes(n, s, zeta) bytes).
 cudaError_t launch_sparse_pattern(int n, const SketchDev& sk, unsigned short* pat, cudaStream_t s);
 
 // ------------------------------------------------------------ batched waves
