@@ -59,6 +59,24 @@ def test_sketch_matrix_bit_exact(fab, torch, n, kind, s):
     assert np.allclose(out, ref, rtol=1e-15, atol=0)
 
 
+@pytest.mark.parametrize("zeta,s", [(1, 300), (16, 20), (5, 97)])
+def test_sparse_table_sketch_of_the_basis(fab, torch, zeta, s):
+    """A solve's sparse-sign sketch comes from the transposed per-chunk table (gather):
+    Theta v_j of the library's own basis (n = 4900: a full and a partial chunk) against
+    the oracle's sketch of the same vectors, for short and long lists."""
+    A = W.convdiff(2, 70)
+    b = W.random_vector(A.n, 3)
+    m = 12
+    M = fab.Matrix.from_csr(A)
+    M.apply(torch.from_numpy(b).cuda(), fab.params(f=fab.EXP, t=-0.01, m=m, k=2, s=s, zeta=zeta,
+                                                   sketch=fab.SPARSE_SIGN, seed=9, method=fab.SKETCHED_FAST))
+    V = M.last_basis()  # n x (m+1), v_j = sigma_j W_j
+    SV = M.last_state().SV  # s x (m+1)
+    ref = osk.make(osk.SPARSE_SIGN, A.n, s, 9, zeta).apply(V)
+    for j in range(m + 1):
+        assert np.max(np.abs(SV[:, j] - ref[:, j])) <= 1e-13 * np.linalg.norm(V[:, j]), j
+
+
 @pytest.mark.parametrize("n", [1000, 12345, 70000])
 @pytest.mark.parametrize("kind,s", [(osk.SPARSE_SIGN, 160), (osk.SRHT, 400)])
 def test_sketch_random_vectors(fab, torch, n, kind, s):
