@@ -769,7 +769,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     const int q0 = inc ? qr_cols : 0, fresh = inc ? qr_cols + 1 : 0;
     CK(cudaMemcpyAsync(ws.qr + (size_t)fresh * p->s, ws.SV + (size_t)fresh * p->s,
                        (size_t)p->s * (mu + 1 - fresh) * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 1, ws.tau, s, q0, fresh));
+    LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 1, ws.tau, ws.st, s, q0, fresh));
     qr_cols = mu;
     LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.qr + (size_t)mu * p->s, ws.y, 0, nullptr, s, m));
     yptr = ws.y;
@@ -781,7 +781,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
       const int q0 = inc ? qr_cols : 0;
       CK(cudaMemcpyAsync(ws.qr + (size_t)q0 * p->s, ws.SV + (size_t)q0 * p->s, (size_t)p->s * (mu - q0) * sizeof(double),
                          cudaMemcpyDeviceToDevice, s));
-      LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 0, ws.tau, s, q0, q0));
+      LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 0, ws.tau, ws.st, s, q0, q0));
       qr_cols = mu;
     } else if (wh > 0) {
       // Alg. 3 on the whitened basis: LSQR on the stored columns with the implicit

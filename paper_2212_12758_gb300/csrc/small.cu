@@ -846,10 +846,13 @@ namespace cg = cooperative_groups;
 template <int CL>
 __global__ void __launch_bounds__(256) k_qr_cluster(double* __restrict__ A, int lda, int rows,
                                                     const int* __restrict__ mdev, int extra,
-                                                    double* __restrict__ tau_out, int start, int fresh) {
+                                                    double* __restrict__ tau_out, int start, int fresh,
+                                                    DevState* st) {
   extern __shared__ __align__(16) double smem_d[];
   __shared__ double red[32];
   __shared__ double s_tau[kMaxM];
+  __shared__ int s_flag[kMaxM];  // s_flag[j] = 1 once reflector j is published
+  __shared__ int s_fail;
   cg::cluster_group cluster = cg::this_cluster();
   const int r = (int)cluster.block_rank();
   const int mu = *mdev;
@@ -872,8 +875,9 @@ __global__ void __launch_bounds__(256) k_qr_cluster(double* __restrict__ A, int 
     ss = warp_sum(ss);
     if (lane == 0) red[warp] = ss;
     __syncthreads();
-    double sig = 0.0;
-    for (int w = 0; w < nw; ++w) sig += red[w];
+    double sig = lane < nw ? red[lane] : 0.0;  // the nw = 8 warp partials, by shuffles
+    for (int o = 4; o > 0; o >>= 1) sig += __shfl_xor_sync(0xffffffffu, sig, o);
+    sig = __shfl_sync(0xffffffffu, sig, 0);
     const double alpha = cj[j];
     double t = 0.0, beta = alpha, vinv = 0.0;
     if (sig != 0.0) {
@@ -925,21 +929,80 @@ __global__ void __launch_bounds__(256) k_qr_cluster(double* __restrict__ A, int 
     }
     __syncthreads();
   }
+  // Point-to-point publication instead of an all-CTA barrier per column: the owner
+  // of reflector j sets s_flag[j] in every CTA (release at cluster scope) once column
+  // j and tau_j are final (they are never written again), and each CTA waits for its
+  // own flag (acquire; bounded, FAB_ETIMEOUT on expiry). The owner of column j+1
+  // applies H_j to that column first and publishes reflector j+1 before updating its
+  // other columns, so the next reflector's critical path is one column's update.
+  auto publish = [&](int q) {
+    __syncthreads();  // column q and tau_q are written
+    if (tid == 0) {
+      asm volatile("fence.acq_rel.cluster;" ::: "memory");
+      for (int rk = 0; rk < CL; ++rk) {
+        int* f = cluster.map_shared_rank(s_flag + q, rk);
+        asm volatile("st.release.cluster.u32 [%0], %1;" ::"l"(f), "r"(1) : "memory");
+      }
+    }
+  };
+  for (int j = tid; j < kMaxM; j += blockDim.x) s_flag[j] = 0;
+  if (tid == 0) s_fail = 0;
+  cluster.sync();  // every CTA's flags are cleared before any publication
+  if (start < steps && r == start % CL) {
+    reflector(start);
+    publish(start);
+  }
   for (int j = start; j < steps; ++j) {
     const int owner = j % CL;
-    if (r == owner) reflector(j);
-    cluster.sync();  // reflector j is published in the owner's shared memory
+    if (tid == 0) {
+      int ok = 0;
+      for (int it = 0; it < (1 << 22) && !ok; ++it) {
+        asm volatile("ld.acquire.cluster.u32 %0, [%1];" : "=r"(ok) : "l"(s_flag + j) : "memory");
+        if (!ok) __nanosleep(32);
+      }
+      if (!ok) {
+        s_fail = 1;
+        st->status = FAB_ETIMEOUT;
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    {  // every thread's own acquire of the (set) flag orders its reads after the owner's release
+      int f;
+      asm volatile("ld.acquire.cluster.u32 %0, [%1];" : "=r"(f) : "l"(s_flag + j) : "memory");
+      (void)f;
+    }
     const double* rcol = cluster.map_shared_rank(loc + (size_t)(j / CL) * rows, owner);
     const double* rtau = cluster.map_shared_rank(s_tau, owner);
     for (int i = j + 1 + tid; i < rows; i += blockDim.x) vbuf[i] = rcol[i];
     const double tj = rtau[j];
     if (r != owner && tid == 0) s_tau[j] = tj;
     __syncthreads();
-    // apply H_j to my columns g > j, one warp per column
+    const int nxt = j + 1 < steps ? (j + 1) % CL : -1;
+    if (r == nxt) {  // H_j on column j+1 by the whole CTA (all four FP64 pipes), then reflector j+1
+      double* col = loc + (size_t)((j + 1) / CL) * rows;
+      double d = (tid == 0) ? col[j] : 0.0;
+      for (int i = j + 1 + tid; i < rows; i += blockDim.x) d = fma(vbuf[i], col[i], d);
+      d = warp_sum(d);
+      if (lane == 0) red[warp] = d;
+      __syncthreads();
+      double dd = lane < nw ? red[lane] : 0.0;
+      for (int o = 4; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);  // nw = 8 partials
+      dd = __shfl_sync(0xffffffffu, dd, 0) * tj;
+      if (tid == 0) col[j] -= dd;
+      for (int i = j + 1 + tid; i < rows; i += blockDim.x) col[i] = fma(-dd, vbuf[i], col[i]);
+      __syncthreads();
+      reflector(j + 1);
+      publish(j + 1);
+    }
+    // apply H_j to my other columns g > j, one warp per column
     int first = (j + 1 - r + CL - 1) / CL;  // first local column with g > j
     if (first < 0) first = 0;
-    for (int lc = first + warp; lc < nloc; lc += nw) apply_col(loc + (size_t)lc * rows, j, tj);
-    __syncthreads();
+    for (int lc = first + warp; lc < nloc; lc += nw) {
+      if (r == nxt && lc == (j + 1) / CL) continue;  // done above
+      apply_col(loc + (size_t)lc * rows, j, tj);
+    }
+    __syncthreads();  // vbuf is reused
   }
   cluster.sync();  // no CTA exits while others may still read its shared memory
   for (int lc = 0; lc < nloc; ++lc) {
@@ -1663,12 +1726,12 @@ bool qr_cluster_fits(int rows, int ncols) {
 }
 
 cudaError_t launch_qr(double* A, int lda, int rows, const int* mdev, int max_cols, int extra, double* tau,
-                      cudaStream_t s, int start, int fresh) {
+                      DevState* st, cudaStream_t s, int start, int fresh) {
   const int ncols = max_cols + extra;
   for (int cl : {16, 8}) {
     const size_t smem = ((size_t)((ncols + cl - 1) / cl) + 1) * rows * sizeof(double);
     if (smem > 200 * 1024) continue;
-    void* args[] = {&A, &lda, &rows, (void*)&mdev, &extra, &tau, &start, &fresh};
+    void* args[] = {&A, &lda, &rows, (void*)&mdev, &extra, &tau, &start, &fresh, &st};
     cudaError_t e = cl == 16 ? launch_cluster(k_qr_cluster<16>, 16, smem, s, args)
                              : launch_cluster(k_qr_cluster<8>, 8, smem, s, args);
     if (e == cudaSuccess) return e;

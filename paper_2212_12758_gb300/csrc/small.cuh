@@ -23,7 +23,7 @@ cudaError_t launch_householder_qr(double* A, int lda, int rows, const int* mdev,
 // column), columns from fresh on are new; only the rest is factored (cluster path
 // only: qr_cluster_fits).
 cudaError_t launch_qr(double* A, int lda, int rows, const int* mdev, int max_cols, int extra, double* tau,
-                      cudaStream_t s, int start = 0, int fresh = 0);
+                      DevState* st, cudaStream_t s, int start = 0, int fresh = 0);
 bool qr_cluster_fits(int rows, int ncols);
 cudaError_t launch_lu_fast(double* M, int ld, const int* mdev, int max_m, int* piv, double* logdet, DevState* st,
                            cudaStream_t s);
