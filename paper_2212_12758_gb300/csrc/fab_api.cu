@@ -722,10 +722,15 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
       const int j0 = std::max(0, c - k), kw = c - j0;
       LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, j0, kw, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
                           s));
-      LK(PK_UPDATE, launch_update(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part, ws.counter,
-                       sk_on ? sk : none, ws.st, s));
-      if (sk_on && sk.kind != SK_GAUSS)
-        LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
+      if (sk_on) {  // window update, norm and the sketch of the new column in one pass
+        LK(PK_UPDATE, launch_update(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part, ws.counter, sk,
+                                    ws.st, s));
+        if (sk.kind != SK_GAUSS)
+          LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
+      } else {  // no sketch (Alg. 5): the lean kernel, all of a row group's loads in flight at once
+        LK(PK_UPDATE, launch_update_plain(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part,
+                                          ws.counter, ws.st, s));
+      }
     }
   }
   c_done = m;

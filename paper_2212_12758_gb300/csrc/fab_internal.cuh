@@ -329,6 +329,11 @@ template <typename TV>
 cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
                           int ldh, ColScale cs, const double* wn2, int mode, double* part, unsigned* counter,
                           SketchDev& sk, DevState* st, cudaStream_t s, int gate = 0);
+// The Alg. 2 window update and norm of column c without a sketch (see k_update_plain).
+template <typename TV>
+cudaError_t launch_update_plain(int n, TV* W, int64_t ld, int c, int j0, int kw, const double* coef, double* H,
+                                int ldh, ColScale cs, const double* wn2, int mode, double* part, unsigned* counter,
+                                DevState* st, cudaStream_t s);
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
                                  DevState* st, cudaStream_t s, int gate = 0);
 // The sparse sign pattern of sk, transposed per chunk, into pat (sparse_table_bytes(n, s, zeta) bytes).
