@@ -681,15 +681,24 @@ def main():
     bd = torch.from_numpy(b).cuda()
     xd = torch.empty_like(bd)
     p_fast = P(fab.SKETCHED_FAST)
-    for _ in range(args.warmup):
+    # The last warm-up solve records every kernel class (the per-class shares). Each
+    # recorded launch adds an event pair, so the timed region brackets only the
+    # dominant kernel, whose average launch time the roofline needs.
+    for i in range(args.warmup):
+        if i == args.warmup - 1:
+            fab.profile_enable(True)
         _, st = Mx.apply(bd, p_fast, x=xd, stats=True)
     torch.cuda.synchronize()
+    prof_warm = fab.profile_query()
+    fab.profile_enable(False)
     launches_per_solve = st.launches
+    dom = max(("spmv_dots", "update"), key=lambda k_: prof_warm[k_][0])
 
     # ---------------------------------------------------------------- timed
     clocks = ClockSampler(local)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     fab.profile_enable(True)
+    fab.profile_only(dom)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -708,6 +717,7 @@ def main():
     clk = clocks.stop()
     prof = fab.profile_query()
     fab.profile_enable(False)
+    fab.profile_only(None)
     total_ms = max_over_ranks(dist, t_all0.elapsed_time(t_all1))
     lat = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
     solves_per_s = whole_job_rate(args.steps, ws, total_ms / 1000.0)
@@ -715,7 +725,6 @@ def main():
 
     # ------------------------------------------------------------ roofline
     cost = algorithmic_cost(n, nnz, M, K_WIN, S_ROWS)
-    dom = max(("spmv_dots", "update"), key=lambda k_: prof[k_][0])
     tot_ms, cnt = prof[dom]
     avg_s = tot_ms / max(cnt, 1) / 1000.0
     bytes_l, flops_l = cost[dom]
@@ -735,8 +744,10 @@ def main():
                  "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
                  "hbm_gbs_algorithmic": bytes_l / avg_s / 1e9, "hbm_frac_of_measured": hbm_frac,
                  "fp64_gflops": flops_l / avg_s / 1e9, "fp64_frac_of_nominal": alu_frac})
-    kernel_share = {k_: {"ms": v[0], "launches": v[1], "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-9)}
-                    for k_, v in prof.items()}
+    kernel_share = {k_: {"ms": v[0], "launches": v[1],
+                         "share": v[0] / max(sum(x[0] for x in prof_warm.values()), 1e-9)}
+                    for k_, v in prof_warm.items()}
+    kernel_share["source"] = "CUDA events around every launch of the last warm-up solve"
     # whole-solve algorithmic traffic (basis steps + combine)
     solve_bytes = M * (cost["spmv_dots"][0] + cost["update"][0]) + 8 * n * M
     hbm_gbs_solve = solve_bytes / (ms_per_step / 1000.0) / 1e9

@@ -358,9 +358,13 @@ int fab_batch_run(fab_handle* const* hs, const fab_params* ps, const double* con
  *   "gemv_t"         V^T w passes (Arnoldi, LSQR)
  *   "small"          QR / LSQR scalar steps / f(H) kernels
  *   "combine"        x = ||b|| V_m c and the LSQR vector update
+ * fab_profile_only(name) restricts the recording to that class (NULL or ""
+ * restores every class): each event pair adds a little device time between
+ * launches, so a throughput measurement brackets only the kernel it needs.
  * Unknown names return FAB_EINVAL. Process-wide; not thread-safe.
  */
 int fab_profile_enable(int on);
+int fab_profile_only(const char* name);
 int fab_profile_query(const char* name, double* total_ms, int64_t* launches);
 
 #ifdef __cplusplus

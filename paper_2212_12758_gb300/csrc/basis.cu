@@ -971,6 +971,38 @@ cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int c
   return cudaGetLastError();
 }
 
+// Deferred form: the partials of columns c0..c0+ncols-1 lie colstride doubles apart
+// (nparts blocks each) and one launch reduces them all, one warp per (column,
+// sketch row), with the arithmetic and order of sketch_reduce_body. Only the columns
+// the per-step reduce would have written are written: those below m_used, and
+// m_used itself unless the basis loop stopped there (a breakdown or an error).
+__global__ void k_sketch_reduce_cols(SketchDev sk, size_t colstride, int c0, int ncols, int nparts,
+                                     const double* __restrict__ sigma, double scale, double* __restrict__ SV,
+                                     const DevState* st) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= (long long)ncols * sk.s) return;
+  const int col = c0 + (int)(wid / sk.s), q = (int)(wid % sk.s);
+  const int mu = st->m_used;
+  if (!(col < mu || (col == mu && !st->stop))) return;
+  const double* part = sk.part + (size_t)col * colstride;
+  double a = 0.0;
+  for (int b = lane; b < nparts; b += 32) a += part[(size_t)b * sk.s + q];
+  a = warp_sum(a);
+  if (lane == 0) SV[(size_t)col * sk.s + q] = a * scale * sigma[col];
+}
+
+cudaError_t launch_sketch_reduce_cols(const SketchDev& sk, size_t colstride, int c0, int ncols, int nparts,
+                                      const double* sigma, double scale, double* SV, const DevState* st,
+                                      cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  const int warps_per_block = 8;
+  const long long warps = (long long)ncols * sk.s;
+  const int grid = (int)((warps + warps_per_block - 1) / warps_per_block);
+  k_sketch_reduce_cols<<<grid, warps_per_block * 32, 0, s>>>(sk, colstride, c0, ncols, nparts, sigma, scale, SV, st);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------ SRHT row sampling
 // Floyd's algorithm: for i = 0..s-1, j = n'-s+i, t = floor(u(seed,4,i) (j+1) / 2^64);
 // take t unless already taken, else j. Then the rows are sorted (bitonic).

@@ -82,6 +82,8 @@ const char* kProfNames[PK_COUNT] = {"spmv_dots", "update", "sketch_reduce", "gem
 
 struct Profiler {
   bool on = false;
+  int only = -1;  // record one class only (-1: every class)
+  bool wants(int kind) const { return on && (only < 0 || only == kind); }
   double total_ms[PK_COUNT] = {0};
   long long launches[PK_COUNT] = {0};
   std::vector<cudaEvent_t> pool;
@@ -253,7 +255,7 @@ namespace {
 #define LK(kind, call)                                            \
   do {                                                            \
     cudaEvent_t e0_ = nullptr, e1_ = nullptr;                     \
-    if (g_prof.on) {                                              \
+    if (g_prof.wants(kind)) {                                     \
       e0_ = g_prof.take();                                        \
       e1_ = g_prof.take();                                        \
       if (e0_ && e1_) cudaEventRecord(e0_, s);                    \
@@ -370,6 +372,27 @@ struct Need {
   size_t bytes;
 };
 
+// Doubles of one column's block partials of the sketch: k_update runs at most
+// min(chunks, 8 blocks per SM) blocks of 256 threads.
+size_t skpart_col_doubles(int n, int s) {
+  const int nchunks = (n + kChunk - 1) / kChunk;
+  return (size_t)std::max(1, std::min(nchunks, sm_count() * 8)) * (size_t)s;
+}
+
+// Where nothing reads the sketch before a pass of the basis loop ends (the Alg. 2
+// paths of sketched_fast and sketched_ls with a sparse-sign or SRHT sketch), every
+// column keeps its own block partials and one launch reduces the pass's columns,
+// in place of a small latency-bound launch per step. Used while the partials take
+// at most a quarter of the basis' bytes.
+bool defer_sketch_reduce(const fab_handle* h, const fab_params* p) {
+  if (p->method != FAB_SKETCHED_FAST && p->method != FAB_SKETCHED_LS) return false;
+  if (p->sketch == FAB_SK_GAUSSIAN) return false;
+  const int m = m_cap(p);
+  const size_t bytes = (size_t)(m + 1) * skpart_col_doubles(h->n, p->s) * 8;
+  const size_t basis = (size_t)h->ld * (m + 1) * (p->precision == FAB_MIXED ? 4 : 8);
+  return bytes <= basis / 4;
+}
+
 // The workspace a solve needs (buffer, bytes), shared by allocation and admission.
 int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
   const int m = m_cap(p), s = sketched(p->method) ? p->s : 1;
@@ -392,7 +415,7 @@ int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
       {&h->part, part_blocks * (kMaxWindow + 1) * 8},
       {&h->counter, 64},
       {&h->gpart, std::max((size_t)ntiles * (m + 1) * 8, gauss ? gauss_partial_bytes(n, s, m + 1) : (size_t)0)},
-      {&h->skpart, (size_t)nchunks * s * 8},
+      {&h->skpart, defer_sketch_reduce(h, p) ? (size_t)(m + 1) * skpart_col_doubles(n, s) * 8 : (size_t)nchunks * s * 8},
       {&h->SV, (size_t)s * (m + 1) * 8},
       {&h->P, (size_t)s * 4},
       {&h->spat, (sketched(p->method) && p->sketch == FAB_SK_SPARSE_SIGN) ? sparse_table_bytes(n, s, p->zeta) : 0},
@@ -649,6 +672,12 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   SketchDev none;
   memset(&none, 0, sizeof(none));
   none.kind = SK_NONE;
+  // deferred sketch reduce: column c's partials at ws.skpart + c * colstride, and the
+  // number of blocks that wrote them
+  const bool defer = sk_on && sk.kind != SK_GAUSS && defer_sketch_reduce(h, p);
+  const size_t colstride = defer ? skpart_col_doubles(n, p->s) : 0;
+  std::vector<int> col_parts(defer ? m_cap(p) + 1 : 0, 0);
+  int red_from = 0;  // first column whose deferred reduce is pending
 
   if (p->method == FAB_BG_LS) {  // Alg. 1 start: p = Theta b, r_11 = ||p||, sigma_0 = 1 / r_11
     LK(PK_UPDATE, launch_update(n, W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, sk,
@@ -659,7 +688,10 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     // start vector: ||b||, sigma_0, sketch of b (Gaussian: its BF16 copy)
     LK(PK_UPDATE, launch_update(n, W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1 | 2, ws.part, ws.counter,
                                 sk_on ? sk : none, ws.st, s));
-    if (sk_on && sk.kind != SK_GAUSS) LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
+    if (defer)
+      col_parts[0] = sk.nparts;
+    else if (sk_on && sk.kind != SK_GAUSS)
+      LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, 0, sk_scale, ws.SV, ws.st, s));
     if (whiten)  // R = (||Theta v_1||), Q = Theta v_1 / r_11
       LK(PK_SMALL, launch_wh_check(ws.SV, p->s, 0, ws.qr, ws.wR, ws.wRi, ws.wT, ldr, ws.H, ldh, whiten_kappa(p),
                                    ws.wcoef, ws.wnrm, ws.cs, ws.st, s));
@@ -723,9 +755,12 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
       LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, j0, kw, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
                           s));
       if (sk_on) {  // window update, norm and the sketch of the new column in one pass
+        if (defer) sk.part = ws.skpart + (size_t)c * colstride;
         LK(PK_UPDATE, launch_update(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part, ws.counter, sk,
                                     ws.st, s));
-        if (sk.kind != SK_GAUSS)
+        if (defer)
+          col_parts[c] = sk.nparts;
+        else if (sk.kind != SK_GAUSS)
           LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
       } else {  // no sketch (Alg. 5): the lean kernel, all of a row group's loads in flight at once
         LK(PK_UPDATE, launch_update_plain(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part,
@@ -734,6 +769,17 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     }
   }
   c_done = m;
+  if (defer) {  // the pass's sketch columns, one launch per run of equal block counts
+    sk.part = ws.skpart;
+    for (int c0 = red_from; c0 <= m;) {
+      int c1 = c0;
+      while (c1 < m && col_parts[c1 + 1] == col_parts[c0]) ++c1;
+      LK(PK_SKRED, launch_sketch_reduce_cols(sk, colstride, c0, c1 - c0 + 1, col_parts[c0], ws.sigma, sk_scale, ws.SV,
+                                             ws.st, s));
+      c0 = c1 + 1;
+    }
+    red_from = m + 1;
+  }
   if (sk_on && sk.kind == SK_GAUSS)  // Theta V_{m+1} = G (BF16 basis) on the tensor cores, FP64 finish
     LK(PK_SKRED, launch_gauss_sketch(ws.G, ws.Wbf, ld, n, p->s, m + 1, ws.sigma, ws.gpart, ws.SV, ws.st, s));
   CK(cudaEventRecord(ev[1], s));
@@ -1132,6 +1178,20 @@ extern "C" int fab_profile_enable(int on) {
   }
   g_prof.begin_solve();
   return FAB_OK;
+}
+
+extern "C" int fab_profile_only(const char* name) {
+  if (!name || !*name) {
+    g_prof.only = -1;
+    return FAB_OK;
+  }
+  for (int i = 0; i < PK_COUNT; ++i) {
+    if (strcmp(name, kProfNames[i]) == 0) {
+      g_prof.only = i;
+      return FAB_OK;
+    }
+  }
+  return FAB_EINVAL;
 }
 
 extern "C" int fab_profile_query(const char* name, double* total_ms, int64_t* launches) {

@@ -336,6 +336,12 @@ cudaError_t launch_update_plain(int n, TV* W, int64_t ld, int c, int j0, int kw,
                                 DevState* st, cudaStream_t s);
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
                                  DevState* st, cudaStream_t s, int gate = 0);
+// The same reduce for ncols columns at once (column c's nparts partials at sk.part +
+// c * colstride; Theta v_c to SV + c * s), for a pass whose sketch nothing reads
+// before the pass ends.
+cudaError_t launch_sketch_reduce_cols(const SketchDev& sk, size_t colstride, int c0, int ncols, int nparts,
+                                      const double* sigma, double scale, double* SV, const DevState* st,
+                                      cudaStream_t s);
 // The sparse sign pattern of sk, transposed per chunk, into pat (sparse_table_bytes(n, s, zeta) bytes).
 cudaError_t launch_sparse_pattern(int n, const SketchDev& sk, unsigned short* pat, cudaStream_t s);
 

@@ -26,7 +26,7 @@ FP64, MIXED = 0, 1
 # Every symbol the header declares (checked against include/fab.h by the tests).
 SYMBOLS = ("fab_params_default", "fab_strerror", "fab_last_error", "fab_create", "fab_apply", "fab_destroy", "fab_last_state",
            "fab_last_basis", "fab_sketch_apply", "fab_sketch_apply_noalloc", "fab_profile_enable",
-           "fab_profile_query", "fab_server_create", "fab_server_submit", "fab_server_poll", "fab_server_stats_get",
+           "fab_profile_only", "fab_profile_query", "fab_server_create", "fab_server_submit", "fab_server_poll", "fab_server_stats_get",
            "fab_server_destroy", "fab_batch_create", "fab_batch_exec", "fab_batch_input", "fab_batch_output",
            "fab_batch_kernels", "fab_batch_destroy", "fab_batch_run", "fab_set_tiling", "fab_tune")
 PROFILE_KINDS = ("spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine")
@@ -106,6 +106,8 @@ lib.fab_tune.argtypes = [_vp, _i32, _i32, _vp, _vp]
 lib.fab_tune.restype = _i32
 lib.fab_profile_enable.argtypes = [_i32]
 lib.fab_profile_enable.restype = _i32
+lib.fab_profile_only.argtypes = [ctypes.c_char_p]
+lib.fab_profile_only.restype = _i32
 lib.fab_profile_query.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
 lib.fab_profile_query.restype = _i32
 
@@ -250,6 +252,11 @@ def sketch_apply(V, s: int, sketch: int = SPARSE_SIGN, zeta: int = 8, seed: int 
 
 def profile_enable(on: bool = True):
     _check(lib.fab_profile_enable(1 if on else 0), "fab_profile_enable")
+
+
+def profile_only(name=None):
+    """Record only kernel class `name` (None: every class) while profiling is on."""
+    _check(lib.fab_profile_only(name.encode() if name else None), "fab_profile_only")
 
 
 def profile_query():
