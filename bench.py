@@ -68,13 +68,14 @@ def algorithmic_cost(n: int, nnz: int, m: int, k: int, s: int):
     spmv_dots (step c, window kw <= k): A values + column indices (12 nnz), row
       pointers (4 (n+1)), the gathered column v_{c-1} (8 n, counted once), the other
       kw-1 window columns (8 n each), the write of w (8 n). Flops: 2 nnz (SpMV)
-      + 2 n kw (window dots) + 2 n (||A v||^2).
+      + 2 n kw (window dots); ||A v|| for the breakdown test comes from the
+      coefficients, not the rows.
     update (step c): read w and kw window columns, write the new column: 8 n (kw + 2);
       flops 2 n kw + 2 n; the sketch partials add 8 s per 4096-row chunk.
     """
     kw = k
     sp_bytes = 12 * nnz + 4 * (n + 1) + 8 * n * kw + 8 * n
-    sp_flops = 2 * nnz + 2 * n * kw + 2 * n
+    sp_flops = 2 * nnz + 2 * n * kw
     nch = (n + 4095) // 4096
     up_bytes = 8 * n * (kw + 2) + 8 * s * nch
     up_flops = 2 * n * kw + 2 * n

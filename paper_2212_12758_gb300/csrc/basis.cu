@@ -79,13 +79,15 @@ cudaError_t launch_state_set_m(DevState* st, int m, cudaStream_t s) {
 // --------------------------------------------- SpMV + window dot products
 // W_c = 2^shf[c-1] A W_{c-1} is written to column c (an exact power-of-two rescale
 // done on the exponent bits keeps the raw columns near unit norm without FP64
-// work); for the window j0..j0+kw-1 the dots d_j = <W_j, W_c> and ||W_c||^2 are
-// reduced over the grid. With v_j = sigma_j W_j and tau = sigma_{c-1} 2^-shf[c-1]
+// work); for the window j0..j0+kw-1 the dots d_j = <W_j, W_c> are reduced over the
+// grid (recursive halving within a warp: a few additions for all kw dots, not kw
+// full warp reductions). With v_j = sigma_j W_j and tau = sigma_{c-1} 2^-shf[c-1]
 // (so that A v_{c-1} = tau W_c) the last block writes
 //   h_{j,c-1} = sigma_j tau d_j     (into H),
 //   coef_q    = sigma_j^2 d_j       (update coefficient of the raw column),
-//   wn2[c]    = tau^2 ||W_c||^2     (= ||A v_{c-1}||^2, for the breakdown test),
-//   scl[c]    = tau.
+//   scl[c]    = tau
+// (no window: block 0 writes scl[c] alone). ||A v_{c-1}|| for the breakdown test
+// is formed by the update from h_{j,c-1} and h_{c,c-1} (column_norm_tail).
 // The rows are cut into tiles of at most 256 rows and (unless a single row has
 // more) at most kSpmvCap nonzeros, so every block iteration has about the same
 // work whatever the row lengths. A tile's nonzeros are staged in shared memory
@@ -93,15 +95,22 @@ cudaError_t launch_state_set_m(DevState* st, int m, cudaStream_t s) {
 // longer single-row tile is read from global memory with the same order of
 // operations.
 
+// tau = sigma_{c-1} 2^-shf[c-1], exactly (power-of-two factors).
+__device__ __forceinline__ double column_tau(double sigma_prev, int ksh) {
+  double pinv;
+  const double pinv_hi = pow2_split(-ksh, &pinv);
+  return (sigma_prev * pinv_hi) * pinv;
+}
+
 // The work of block `bid` of `nblk` (a launch of its own, or one solve's share
 // of a batched wave) is a function of (bid, nblk) only, so a solve gives the
 // same bits whichever way its blocks are launched.
 template <typename TV, int KW>
 __device__ __forceinline__ void spmv_dots_body(
     const Csr& A, TV* __restrict__ W, int64_t ld, int c, int j0, int kw, const ColScale& cs, double* __restrict__ H,
-    int ldh, double* __restrict__ coef, double* __restrict__ wn2, double* __restrict__ part,
-    unsigned* __restrict__ counter, DevState* st, int bid, int nblk, unsigned char* smem_raw) {
-  constexpr int NV = kMaxWindow + 1;
+    int ldh, double* __restrict__ coef, double* __restrict__ part, unsigned* __restrict__ counter, DevState* st,
+    int bid, int nblk, unsigned char* smem_raw) {
+  constexpr int NV = KW > 0 ? KW : 1;  // window dot products per thread
   constexpr int S = kSpmvStages;
   TV* s_vals = reinterpret_cast<TV*>(smem_raw);                                // [S][kSpmvCap]
   int* s_col = reinterpret_cast<int*>(smem_raw + S * kSpmvCap * sizeof(TV));   // [S][kSpmvCap]
@@ -275,7 +284,6 @@ __device__ __forceinline__ void spmv_dots_body(
       wout[r] = y;
 #pragma unroll
       for (int q = 0; q < KW; ++q) acc[q] = fma(wv[q], y, acc[q]);
-      acc[kMaxWindow] = fma(y, y, acc[kMaxWindow]);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&s_empty[stg]);  // this warp is done with the stage
@@ -293,19 +301,18 @@ __device__ __forceinline__ void spmv_dots_body(
     __syncthreads();
     return;
   }
+  if (KW == 0) {  // no window (Alg. 1, Arnoldi): only the scale of the new column
+    if (bid == 0 && tid == 0) cs.scl[c] = column_tau(cs.sigma[c - 1], ksh);
+    return;
+  }
   double accd[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) accd[q] = (double)acc[q];
-  block_sum<NV>(accd, sh);
-  if (tid == 0) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) part[(size_t)bid * NV + q] = accd[q];
-  }
+  block_sum_multi<NV>(accd, sh, tot);
+  if (tid < NV) part[(size_t)bid * NV + tid] = tot[tid];
   if (!last_block(counter, (unsigned)nblk)) return;
-  sum_partials(part, nblk, NV, tot, sh);
-  double pinv;
-  const double pinv_hi = pow2_split(-ksh, &pinv);
-  const double tau = (cs.sigma[c - 1] * pinv_hi) * pinv;  // exact: power-of-two factors
+  sum_partials_multi<NV>(part, nblk, tot, sh);
+  const double tau = column_tau(cs.sigma[c - 1], ksh);
   if (tid < kw) {
     const int j = j0 + tid;
     const double d = tot[tid];
@@ -313,7 +320,6 @@ __device__ __forceinline__ void spmv_dots_body(
     coef[tid] = cs.sigma[j] * cs.sigma[j] * d;
   }
   if (tid == 0) {
-    wn2[c] = tau * tau * tot[kMaxWindow];
     cs.scl[c] = tau;
     *counter = 0;
   }
@@ -322,13 +328,11 @@ __device__ __forceinline__ void spmv_dots_body(
 template <typename TV, int KW>
 __global__ __launch_bounds__(kThreads) void k_spmv_dots(Csr A, TV* __restrict__ W, int64_t ld, int c, int j0, int kw,
                                                          ColScale cs, double* __restrict__ H, int ldh,
-                                                         double* __restrict__ coef, double* __restrict__ wn2,
-                                                         double* __restrict__ part, unsigned* __restrict__ counter,
-                                                         DevState* st, int gate) {
+                                                         double* __restrict__ coef, double* __restrict__ part,
+                                                         unsigned* __restrict__ counter, DevState* st, int gate) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (gate_closed(st, c, gate)) return;
-  spmv_dots_body<TV, KW>(A, W, ld, c, j0, kw, cs, H, ldh, coef, wn2, part, counter, st, blockIdx.x, gridDim.x,
-                         smem_raw);
+  spmv_dots_body<TV, KW>(A, W, ld, c, j0, kw, cs, H, ldh, coef, part, counter, st, blockIdx.x, gridDim.x, smem_raw);
 }
 
 template <typename TV>
@@ -358,18 +362,18 @@ template int spmv_grid<float>(int, int);
 
 template <typename TV>
 cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int kw, ColScale cs,
-                             double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
+                             double* H, int ldh, double* coef, double* part, unsigned* counter,
                              DevState* st, cudaStream_t s, int gate) {
   if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kSpmvStages * kSpmvCap * (sizeof(TV) + sizeof(int));
   const int grid = spmv_grid<TV>(A.ntiles, kw);
-  void* args[] = {(void*)&A, &W, &ld, &c, &j0, &kw, &cs, &H, &ldh, &coef, &wn2, &part, &counter, &st, &gate};
+  void* args[] = {(void*)&A, &W, &ld, &c, &j0, &kw, &cs, &H, &ldh, &coef, &part, &counter, &st, &gate};
   return cudaLaunchKernel(spmv_fn<TV>(kw), dim3(grid), dim3(kThreads), args, smem, s);
 }
 template cudaError_t launch_spmv_dots<double>(const Csr&, double*, int64_t, int, int, int, ColScale, double*, int,
-                                              double*, double*, double*, unsigned*, DevState*, cudaStream_t, int);
+                                              double*, double*, unsigned*, DevState*, cudaStream_t, int);
 template cudaError_t launch_spmv_dots<float>(const Csr&, float*, int64_t, int, int, int, ColScale, double*, int,
-                                             double*, double*, double*, unsigned*, DevState*, cudaStream_t, int);
+                                             double*, double*, unsigned*, DevState*, cudaStream_t, int);
 
 // ---------------------------------------------- exact int64 chunk sketches
 // A chunk of 4096 consecutive rows is converted to a common block exponent:
@@ -406,6 +410,7 @@ __device__ __forceinline__ long long to_fixed(T x, int E) {
 }
 
 __device__ __forceinline__ int pidx(int j) { return j + (j >> 4); }  // bank-conflict padding
+
 
 // In-register Walsh-Hadamard butterflies over the 4 index bits held by a thread.
 __device__ __forceinline__ void wht16(long long (&X)[16]) {
@@ -651,8 +656,14 @@ constexpr int kModeInit = 2;
 // ||w'||^2 over the grid (each block's share nrm, the last block to finish sums the
 // shares in block order) and the column's bookkeeping: h_{c,c-1}, the breakdown test,
 // sigma_c and its power-of-two shift (kModeInit: the start vector, ||b|| and sigma_0).
-__device__ __forceinline__ void column_norm_tail(double nrm, int c, double* __restrict__ H, int ldh, const ColScale& cs,
-                                                 const double* __restrict__ wn2, int mode, double* __restrict__ part,
+// The breakdown test compares h_{c,c-1} with 64 eps ||A v_{c-1}||, and ||A v_{c-1}||^2
+// is taken as h_{c,c-1}^2 + sum_{j0 <= j < c} h_{j,c-1}^2, from the column of H that the
+// orthogonalization wrote: A v_{c-1} = sum_j h_{j,c-1} v_j + h_{c,c-1} v_c with
+// v_{j0..c} orthonormal (Alg. 2: every column is orthogonalized against the k before
+// it, and any two columns of a window are fewer than k apart; Arnoldi: all columns).
+// The test needs the norm only to a small factor, so no row of the basis pays for it.
+__device__ __forceinline__ void column_norm_tail(double nrm, int c, int j0, double* __restrict__ H, int ldh,
+                                                 const ColScale& cs, int mode, double* __restrict__ part,
                                                  unsigned* __restrict__ counter, DevState* st, int bid, int nblk,
                                                  double* sh, double* tot) {
   double nv[1] = {nrm};
@@ -680,10 +691,15 @@ __device__ __forceinline__ void column_norm_tail(double nrm, int c, double* __re
       // the stored column is W_c = w' / scl[c]: h_{c,c-1} = ||w'|| = scl[c] ||W_c||
       const double hc = cs.scl[c] * h;
       H[c + (size_t)ldh * (c - 1)] = hc;
+      double av2 = hc * hc;  // ||A v_{c-1}||^2
+      for (int j = j0; j < c; ++j) {
+        const double hj = H[j + (size_t)ldh * (c - 1)];
+        av2 = fma(hj, hj, av2);
+      }
       if (!isfinite(hc)) {
         st->status = FAB_ENUMERIC;
         st->stop = 1;
-      } else if (!(hc > 64.0 * DBL_EPSILON * sqrt(wn2[c]))) {
+      } else if (!(hc > 64.0 * DBL_EPSILON * sqrt(av2))) {
         st->m_used = c;  // the basis spans an invariant subspace
         st->stop = 1;
         cs.sigma[c] = 0.0;
@@ -700,7 +716,7 @@ __device__ __forceinline__ void column_norm_tail(double nrm, int c, double* __re
 template <int SK, typename TV>
 __device__ __forceinline__ void update_body(int n, TV* __restrict__ W, int64_t ld, int c, int j0, int nc,
                                             const double* __restrict__ coef, double* __restrict__ H, int ldh,
-                                            const ColScale& cs, const double* __restrict__ wn2, int mode,
+                                            const ColScale& cs, int mode,
                                             double* __restrict__ part, unsigned* __restrict__ counter,
                                             const SketchDev& sk, DevState* st, int bid, int nblk,
                                             unsigned char* smem_raw) {
@@ -784,17 +800,17 @@ __device__ __forceinline__ void update_body(int n, TV* __restrict__ W, int64_t l
     for (int q = threadIdx.x; q < sk.s; q += kThreads) out[q] = s_acc[q];
   }
   if (!(mode & kModeNorm)) return;
-  column_norm_tail(nrm, c, H, ldh, cs, wn2, mode, part, counter, st, bid, nblk, sh, tot);
+  column_norm_tail(nrm, c, j0, H, ldh, cs, mode, part, counter, st, bid, nblk, sh, tot);
 }
 
 template <int SK, typename TV>
 __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(
     int n, TV* __restrict__ W, int64_t ld, int c, int j0, int nc, const double* __restrict__ coef,
-    double* __restrict__ H, int ldh, ColScale cs, const double* __restrict__ wn2, int mode, double* __restrict__ part,
+    double* __restrict__ H, int ldh, ColScale cs, int mode, double* __restrict__ part,
     unsigned* __restrict__ counter, SketchDev sk, DevState* st, int gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (gate_closed(st, c, gate)) return;
-  update_body<SK, TV>(n, W, ld, c, j0, nc, coef, H, ldh, cs, wn2, mode, part, counter, sk, st, blockIdx.x, gridDim.x,
+  update_body<SK, TV>(n, W, ld, c, j0, nc, coef, H, ldh, cs, mode, part, counter, sk, st, blockIdx.x, gridDim.x,
                       smem_raw);
 }
 
@@ -836,7 +852,7 @@ template int update_grid<float>(int, int, int, int, size_t*);
 
 template <typename TV>
 cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H, int ldh,
-                          ColScale cs, const double* wn2, int mode, double* part, unsigned* counter, SketchDev& sk,
+                          ColScale cs, int mode, double* part, unsigned* counter, SketchDev& sk,
                           DevState* st, cudaStream_t s, int gate) {
   size_t smem = 0;
   const int kind = (sk.kind == SK_SPARSE && sk.pat) ? SK_SPARSE_TAB : sk.kind;
@@ -844,16 +860,14 @@ cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const
   if (grid < 1) return cudaErrorInvalidValue;
   const void* fn = update_fn<TV>(kind);
   sk.nparts = grid;  // one sketch partial per block
-  void* args[] = {&n, &W, &ld, &c, &j0, &nc, (void*)&coef, &H, &ldh, &cs, (void*)&wn2, &mode, &part, &counter,
-                  &sk, &st, &gate};
+  void* args[] = {&n, &W, &ld, &c, &j0, &nc, (void*)&coef, &H, &ldh, &cs, &mode, &part, &counter, &sk, &st, &gate};
   return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, s);
 }
 template cudaError_t launch_update<double>(int, double*, int64_t, int, int, int, const double*, double*, int,
-                                           ColScale, const double*, int, double*, unsigned*, SketchDev&, DevState*,
-                                           cudaStream_t, int);
+                                           ColScale, int, double*, unsigned*, SketchDev&, DevState*, cudaStream_t,
+                                           int);
 template cudaError_t launch_update<float>(int, float*, int64_t, int, int, int, const double*, double*, int, ColScale,
-                                          const double*, int, double*, unsigned*, SketchDev&, DevState*,
-                                          cudaStream_t, int);
+                                          int, double*, unsigned*, SketchDev&, DevState*, cudaStream_t, int);
 
 // ------------------------------------------------- window update without a sketch
 // W_c <- W_c - sum_q coef_q W_{j0+q} (KW window columns, a compile-time count) and
@@ -867,7 +881,7 @@ constexpr int kPlainU = 4;
 template <typename TV, int KW>
 __global__ __launch_bounds__(kThreads) void k_update_plain(int n, TV* __restrict__ W, int64_t ld, int c, int j0,
                                                            const double* __restrict__ coef, double* __restrict__ H,
-                                                           int ldh, ColScale cs, const double* __restrict__ wn2,
+                                                           int ldh, ColScale cs,
                                                            int mode, double* __restrict__ part,
                                                            unsigned* __restrict__ counter, DevState* st) {
   __shared__ double sh[32];
@@ -904,7 +918,7 @@ __global__ __launch_bounds__(kThreads) void k_update_plain(int n, TV* __restrict
     nrm += (double)nrm_g;
   }
   if (!(mode & kModeNorm)) return;
-  column_norm_tail(nrm, c, H, ldh, cs, wn2, mode, part, counter, st, blockIdx.x, gridDim.x, sh, tot);
+  column_norm_tail(nrm, c, j0, H, ldh, cs, mode, part, counter, st, blockIdx.x, gridDim.x, sh, tot);
 }
 
 template <typename TV>
@@ -918,7 +932,7 @@ const void* plain_fn(int kw) {
 
 template <typename TV>
 cudaError_t launch_update_plain(int n, TV* W, int64_t ld, int c, int j0, int kw, const double* coef, double* H,
-                                int ldh, ColScale cs, const double* wn2, int mode, double* part, unsigned* counter,
+                                int ldh, ColScale cs, int mode, double* part, unsigned* counter,
                                 DevState* st, cudaStream_t s) {
   if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
   static int occ[kMaxWindow + 1] = {0};
@@ -930,15 +944,13 @@ cudaError_t launch_update_plain(int n, TV* W, int64_t ld, int c, int j0, int kw,
   const int64_t need = ((int64_t)n + (int64_t)kThreads * kPlainU - 1) / ((int64_t)kThreads * kPlainU);
   const int cap = sm_count() * occ[kw];
   const int grid = (int)(need < 1 ? 1 : (need < cap ? need : cap));
-  void* args[] = {&n, &W, &ld, &c, &j0, (void*)&coef, &H, &ldh, &cs, (void*)&wn2, &mode, &part, &counter, &st};
+  void* args[] = {&n, &W, &ld, &c, &j0, (void*)&coef, &H, &ldh, &cs, &mode, &part, &counter, &st};
   return cudaLaunchKernel(plain_fn<TV>(kw), dim3(grid), dim3(kThreads), args, 0, s);
 }
 template cudaError_t launch_update_plain<double>(int, double*, int64_t, int, int, int, const double*, double*, int,
-                                                 ColScale, const double*, int, double*, unsigned*, DevState*,
-                                                 cudaStream_t);
+                                                 ColScale, int, double*, unsigned*, DevState*, cudaStream_t);
 template cudaError_t launch_update_plain<float>(int, float*, int64_t, int, int, int, const double*, double*, int,
-                                                ColScale, const double*, int, double*, unsigned*, DevState*,
-                                                cudaStream_t);
+                                                ColScale, int, double*, unsigned*, DevState*, cudaStream_t);
 
 // ---------------------------------------------- cross-block sketch reduce
 // out[q] = scale * sigma[col] * sum_blocks part[block][q] (the per-block partials
@@ -1264,7 +1276,7 @@ __global__ __launch_bounds__(kThreads) void k_spmv_wave(const BasisJob<TV>* __re
   const BasisJob<TV>* J = jobs + w.ids[i];
   const Csr A = J->A;
   const ColScale cs = J->cs;
-  spmv_dots_body<TV, KW>(A, J->W, J->ld, c, c - KW, KW, cs, J->H, J->ldh, J->coef, J->wn2, J->part, J->counter,
+  spmv_dots_body<TV, KW>(A, J->W, J->ld, c, c - KW, KW, cs, J->H, J->ldh, J->coef, J->part, J->counter,
                          J->st, blockIdx.x - w.pre[i], w.pre[i + 1] - w.pre[i], smem_raw);
 }
 
@@ -1276,7 +1288,7 @@ __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update_wa
   const BasisJob<TV>* J = jobs + w.ids[i];
   const ColScale cs = J->cs;
   const SketchDev sk = J->sk;
-  update_body<SK, TV>(J->A.n, J->W, J->ld, c, c - nc, nc, J->coef, J->H, J->ldh, cs, J->wn2, mode, J->part,
+  update_body<SK, TV>(J->A.n, J->W, J->ld, c, c - nc, nc, J->coef, J->H, J->ldh, cs, mode, J->part,
                       J->counter, sk, J->st, blockIdx.x - w.pre[i], w.pre[i + 1] - w.pre[i], smem_raw);
 }
 

@@ -236,7 +236,6 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       J.m = m;
       J.k = p.k;
       J.coef = ar.take<double>(m + 1);
-      J.wn2 = ar.take<double>(m + 1);
       J.part = ar.take<double>(part_need[j]);
       J.counter = ar.take<unsigned>(16);
       J.st = states ? states + j : nullptr;

@@ -225,7 +225,7 @@ void fab_destroy(fab_handle* h) {
     cudaFree(h->d_tiles);
     delete[] h->h_rowptr;
   }
-  Buf* bufs[] = {&h->spat, &h->W32, &h->Wbf, &h->G, &h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart,
+  Buf* bufs[] = {&h->spat, &h->W32, &h->Wbf, &h->G, &h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->coef, &h->part, &h->counter, &h->gpart,
                  &h->skpart, &h->SV, &h->P,     &h->qr,  &h->tau,  &h->y,    &h->cvec,    &h->dense,
                  &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state, &h->whm};
   for (Buf* b : bufs)
@@ -353,7 +353,7 @@ struct Ws {
   ColScale cs;
   float* W32;
   __nv_bfloat16 *Wbf, *G;
-  double *W, *H, *sigma, *wn2, *coef, *part, *gpart, *skpart, *SV, *qr, *tau, *y, *cvec, *scal, *u, *xbuf;
+  double *W, *H, *sigma, *coef, *part, *gpart, *skpart, *SV, *qr, *tau, *y, *cvec, *scal, *u, *xbuf;
   double* mats[9];
   double *lv_v, *lv_w, *lv_x, *lv_z, *lv_coef, *lv_q, *unorm2, *one;
   double *wR, *wRi, *wT, *wcoef, *wnrm;  // FAB_WHITEN (ld m+1)
@@ -410,7 +410,6 @@ int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
       {&h->sigma, (size_t)(m + 1) * 8},
       {&h->shf, (size_t)(m + 1) * 4},
       {&h->scl, (size_t)(m + 1) * 8},
-      {&h->wn2, (size_t)(m + 1) * 8},
       {&h->coef, (size_t)(m + 1) * 8},
       {&h->part, part_blocks * (kMaxWindow + 1) * 8},
       {&h->counter, 64},
@@ -458,7 +457,6 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
   ws.H = ptr<double>(h->H);
   ws.sigma = ptr<double>(h->sigma);
   ws.cs = ColScale{ptr<double>(h->sigma), ptr<int>(h->shf), ptr<double>(h->scl)};
-  ws.wn2 = ptr<double>(h->wn2);
   ws.coef = ptr<double>(h->coef);
   ws.part = ptr<double>(h->part);
   ws.gpart = ptr<double>(h->gpart);
@@ -680,13 +678,13 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   int red_from = 0;  // first column whose deferred reduce is pending
 
   if (p->method == FAB_BG_LS) {  // Alg. 1 start: p = Theta b, r_11 = ||p||, sigma_0 = 1 / r_11
-    LK(PK_UPDATE, launch_update(n, W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, sk,
+    LK(PK_UPDATE, launch_update(n, W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, 0, ws.part, ws.counter, sk,
                                 ws.st, s));
     LK(PK_SKRED, launch_sketch_reduce(sk, nullptr, 0, sk_scale, ws.SV, ws.st, s));
     LK(PK_SMALL, launch_bg_orth(ws.SV, p->s, 0, ws.H, ldh, ws.coef, ws.cs, ws.st, s));
   } else {
     // start vector: ||b||, sigma_0, sketch of b (Gaussian: its BF16 copy)
-    LK(PK_UPDATE, launch_update(n, W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1 | 2, ws.part, ws.counter,
+    LK(PK_UPDATE, launch_update(n, W, ld, 0, 0, 0, ws.coef, ws.H, ldh, ws.cs, 1 | 2, ws.part, ws.counter,
                                 sk_on ? sk : none, ws.st, s));
     if (defer)
       col_parts[0] = sk.nparts;
@@ -712,58 +710,58 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     if (p->method == FAB_BG_LS) {
       // Alg. 1: w = A v_{c-1}; p = Theta w; sketched Gram-Schmidt step; the same
       // coefficients on the long vector: W_c <- W_c - sum_j coef_j W_j
-      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
-      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, sk,
+      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.part, ws.counter, ws.st, s));
+      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, 0, ws.coef, ws.H, ldh, ws.cs, 0, ws.part, ws.counter, sk,
                                   ws.st, s));
       LK(PK_SKRED, launch_sketch_reduce(sk, ws.cs.scl, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
       LK(PK_SMALL, launch_bg_orth(ws.SV, p->s, c, ws.H, ldh, ws.coef, ws.cs, ws.st, s));
-      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, none,
+      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, 0, ws.part, ws.counter, none,
                                   ws.st, s));
     } else if (whiten) {
       // Both step sequences are queued; the gates let one of them run (1: Alg. 2
       // until the basis is whitened, 2: Alg. 1 afterwards), so the switch needs
       // no host round trip.
       const int j0 = std::max(0, c - k), kw = c - j0;
-      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, j0, kw, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
+      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, j0, kw, ws.cs, ws.H, ldh, ws.coef, ws.part, ws.counter, ws.st,
                                    s, 1));
-      LK(PK_UPDATE, launch_update(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part, ws.counter, sk,
+      LK(PK_UPDATE, launch_update(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, 1, ws.part, ws.counter, sk,
                                   ws.st, s, 1));
       LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s, 1));
       LK(PK_SMALL, launch_wh_check(ws.SV, p->s, c, ws.qr, ws.wR, ws.wRi, ws.wT, ldr, ws.H, ldh, whiten_kappa(p),
                                    ws.wcoef, ws.wnrm, ws.cs, ws.st, s));
       LK(PK_COMBINE, launch_whiten_column(n, W, ld, c, ws.wcoef, ws.st, s));
-      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
+      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.part, ws.counter, ws.st,
                                    s, 2));
-      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, 0, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, sk,
+      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, 0, ws.coef, ws.H, ldh, ws.cs, 0, ws.part, ws.counter, sk,
                                   ws.st, s, 2));
       LK(PK_SKRED, launch_sketch_reduce(sk, ws.cs.scl, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s, 2));
       LK(PK_SMALL, launch_bg_orth(ws.SV, p->s, c, ws.H, ldh, ws.coef, ws.cs, ws.st, s, ws.wRi, ldr, 2));
-      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 0, ws.part, ws.counter, none,
+      LK(PK_UPDATE, launch_update(n, W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, 0, ws.part, ws.counter, none,
                                   ws.st, s, 2));
     } else if (p->method == FAB_ARNOLDI) {
-      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st, s));
+      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, 0, 0, ws.cs, ws.H, ldh, ws.coef, ws.part, ws.counter, ws.st, s));
       double* Hcol = ws.H + (size_t)ldh * (c - 1);
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
         LK(PK_GEMVT, launch_gemv_t(n, (const TV*)W, ld, 0, c, (const TV*)W + (size_t)c * ld, ws.gpart, ntiles, ws.st, s));
         LK(PK_GEMVT, launch_reduce_cols(ws.gpart, ntiles, c, ws.sigma, 0, ws.cs.scl + c, Hcol, pass, ws.coef,
                                         ws.st, s));
-        LK(PK_UPDATE, launch_update(n, W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, ws.wn2, pass == 1 ? 1 : 0, ws.part,
+        LK(PK_UPDATE, launch_update(n, W, ld, c, 0, c, ws.coef, ws.H, ldh, ws.cs, pass == 1 ? 1 : 0, ws.part,
                          ws.counter, none, ws.st, s));
       }
     } else {
       const int j0 = std::max(0, c - k), kw = c - j0;
-      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, j0, kw, ws.cs, ws.H, ldh, ws.coef, ws.wn2, ws.part, ws.counter, ws.st,
+      LK(PK_SPMV, launch_spmv_dots(A, W, ld, c, j0, kw, ws.cs, ws.H, ldh, ws.coef, ws.part, ws.counter, ws.st,
                           s));
       if (sk_on) {  // window update, norm and the sketch of the new column in one pass
         if (defer) sk.part = ws.skpart + (size_t)c * colstride;
-        LK(PK_UPDATE, launch_update(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part, ws.counter, sk,
+        LK(PK_UPDATE, launch_update(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, 1, ws.part, ws.counter, sk,
                                     ws.st, s));
         if (defer)
           col_parts[c] = sk.nparts;
         else if (sk.kind != SK_GAUSS)
           LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c, sk_scale, ws.SV + (size_t)c * p->s, ws.st, s));
       } else {  // no sketch (Alg. 5): the lean kernel, all of a row group's loads in flight at once
-        LK(PK_UPDATE, launch_update_plain(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, ws.wn2, 1, ws.part,
+        LK(PK_UPDATE, launch_update_plain(n, W, ld, c, j0, kw, ws.coef, ws.H, ldh, ws.cs, 1, ws.part,
                                           ws.counter, ws.st, s));
       }
     }
@@ -1157,7 +1155,7 @@ extern "C" int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t
   if (rc == FAB_OK && sk.kind == SK_SRHT && launch_srht_sample(next_pow2(n), s, rng_state(seed, 4), P, st) != cudaSuccess)
     rc = FAB_ECUDA;
   for (int j = 0; j < ncols && rc == FAB_OK; ++j) {
-    if (launch_update((int)n, const_cast<double*>(V_dev), ldv, j, 0, 0, nullptr, nullptr, 1, ColScale{}, nullptr, 0,
+    if (launch_update((int)n, const_cast<double*>(V_dev), ldv, j, 0, 0, nullptr, nullptr, 1, ColScale{}, 0,
                       nullptr, nullptr, sk, ds, st) != cudaSuccess ||
         launch_sketch_reduce(sk, nullptr, 0, scale, out_dev + (size_t)j * s, ds, st) != cudaSuccess)
       rc = FAB_ECUDA;
@@ -1222,7 +1220,6 @@ int time_spmv(fab_handle* h, const void* vals, int k, unsigned char* scratch, cu
   ColScale cs{ar.take<double>(cols), ar.take<int>(cols), ar.take<double>(cols + 1)};
   double* H = ar.take<double>((size_t)cols * cols);
   double* coef = ar.take<double>(cols);
-  double* wn2 = ar.take<double>(cols + 1);
   double* part = ar.take<double>((size_t)sm_count() * kMaxPartBlocks * (kMaxWindow + 1));
   unsigned* counter = ar.take<unsigned>(16);
   DevState* st = ar.take<DevState>(1);
@@ -1235,10 +1232,10 @@ int time_spmv(fab_handle* h, const void* vals, int k, unsigned char* scratch, cu
     return FAB_ECUDA;
   }
   const int reps = 5;
-  cudaError_t e = launch_spmv_dots<TV>(A, W, ld, k, 0, k, cs, H, cols, coef, wn2, part, counter, st, s);
+  cudaError_t e = launch_spmv_dots<TV>(A, W, ld, k, 0, k, cs, H, cols, coef, part, counter, st, s);
   if (e == cudaSuccess) e = cudaEventRecord(e0, s);
   for (int i = 0; i < reps && e == cudaSuccess; ++i)
-    e = launch_spmv_dots<TV>(A, W, ld, k, 0, k, cs, H, cols, coef, wn2, part, counter, st, s);
+    e = launch_spmv_dots<TV>(A, W, ld, k, 0, k, cs, H, cols, coef, part, counter, st, s);
   if (e == cudaSuccess) e = cudaEventRecord(e1, s);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   float ms = 0.0f;
@@ -1360,7 +1357,7 @@ size_t estimate_ws_bytes(const fab_handle* h, const fab_params* p) {
 
 size_t handle_ws_bytes(const fab_handle* h) {
   const Buf* bufs[] = {&h->spat, &h->W32, &h->Wbf, &h->G,    &h->shf,  &h->scl,  &h->W,   &h->H,     &h->sigma,
-                       &h->wn2, &h->coef, &h->part, &h->counter, &h->gpart, &h->skpart, &h->SV, &h->P,
+                       &h->coef, &h->part, &h->counter, &h->gpart, &h->skpart, &h->SV, &h->P,
                        &h->qr,  &h->tau, &h->y,    &h->cvec, &h->dense, &h->piv, &h->scal, &h->lsq,
                        &h->u,   &h->xbuf, &h->state, &h->whm};
   size_t t = 0;

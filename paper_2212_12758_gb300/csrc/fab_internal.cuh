@@ -113,6 +113,70 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* >= 32*N
   __syncthreads();
 }
 
+// Warp totals of V values per lane by recursive halving: in each of the first
+// log2(P) rounds (P = the power of two >= V, missing values zero) a lane keeps one
+// half of its values and adds its partner's copy of that half, then the last
+// 5 - log2(P) rounds add single values. P - 1 + 5 - log2(P) additions per lane in
+// place of 5 V. Value q's total is returned in lanes [q 32/P, (q+1) 32/P).
+// Fixed combination order.
+template <int V>
+__device__ __forceinline__ double warp_sum_multi(const double (&v)[V]) {
+  constexpr int P = V <= 1 ? 1 : V <= 2 ? 2 : V <= 4 ? 4 : V <= 8 ? 8 : V <= 16 ? 16 : 32;
+  static_assert(V >= 1 && V <= 32, "1..32 values");
+  const int lane = threadIdx.x & 31;
+  double x[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) x[q] = q < V ? v[q] : 0.0;
+  int o = 16;
+#pragma unroll
+  for (int h = P / 2; h >= 1; h /= 2) {
+    const bool up = (lane & o) != 0;  // this lane keeps the upper half
+#pragma unroll
+    for (int q = 0; q < h; ++q) {
+      const double keep = up ? x[q + h] : x[q];
+      const double send = up ? x[q] : x[q + h];
+      x[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    o >>= 1;
+  }
+  for (; o > 0; o >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+  return x[0];
+}
+
+// Block totals of V values per thread into out[0..V) (shared; valid after the call
+// in every thread): warp_sum_multi, then thread q adds the warps' totals of value q
+// in warp order.
+template <int V>
+__device__ __forceinline__ void block_sum_multi(const double (&v)[V], double* sh /* >= 32 V */, double* out) {
+  constexpr int P = V <= 1 ? 1 : V <= 2 ? 2 : V <= 4 ? 4 : V <= 8 ? 8 : V <= 16 ? 16 : 32;
+  constexpr int G = 32 / P;  // lanes that hold each total
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double t = warp_sum_multi<V>(v);
+  if (lane % G == 0 && lane / G < V) sh[warp * V + lane / G] = t;
+  __syncthreads();
+  if (threadIdx.x < V) {
+    double a = 0.0;
+    for (int w = 0; w < nw; ++w) a += sh[w * V + threadIdx.x];
+    out[threadIdx.x] = a;
+  }
+  __syncthreads();
+}
+
+// Totals of the V columns of a row-major nblocks x V partial array, by one block in
+// one pass (every column's loads in flight together), into out[0..V) (shared).
+template <int V>
+__device__ __forceinline__ void sum_partials_multi(const double* part, int nblocks, double* out,
+                                                   double* sh /* >= 32 V */) {
+  double a[V];
+#pragma unroll
+  for (int q = 0; q < V; ++q) a[q] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < V; ++q) a[q] += __ldcg(part + (size_t)b * V + q);
+  }
+  block_sum_multi<V>(a, sh, out);
+}
+
 // Last-block-done: returns true in every thread of the block that finished last.
 // Partials written before the call are visible to that block afterwards.
 __device__ __forceinline__ bool last_block(unsigned* counter, unsigned nblk) {
@@ -323,16 +387,16 @@ struct ColScale {
 };
 template <typename TV>
 cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int kw, ColScale cs,
-                             double* H, int ldh, double* coef, double* wn2, double* part, unsigned* counter,
+                             double* H, int ldh, double* coef, double* part, unsigned* counter,
                              DevState* st, cudaStream_t s, int gate = 0);
 template <typename TV>
 cudaError_t launch_update(int n, TV* W, int64_t ld, int c, int j0, int nc, const double* coef, double* H,
-                          int ldh, ColScale cs, const double* wn2, int mode, double* part, unsigned* counter,
+                          int ldh, ColScale cs, int mode, double* part, unsigned* counter,
                           SketchDev& sk, DevState* st, cudaStream_t s, int gate = 0);
 // The Alg. 2 window update and norm of column c without a sketch (see k_update_plain).
 template <typename TV>
 cudaError_t launch_update_plain(int n, TV* W, int64_t ld, int c, int j0, int kw, const double* coef, double* H,
-                                int ldh, ColScale cs, const double* wn2, int mode, double* part, unsigned* counter,
+                                int ldh, ColScale cs, int mode, double* part, unsigned* counter,
                                 DevState* st, cudaStream_t s);
 cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int col, double scale, double* out,
                                  DevState* st, cudaStream_t s, int gate = 0);
@@ -356,7 +420,7 @@ struct BasisJob {
   double* H;  // (m+1) x m
   int ldh;
   int m, k;
-  double *coef, *wn2, *part;
+  double *coef, *part;
   unsigned* counter;
   DevState* st;
   SketchDev sk;  // sk.kind SK_NONE for Alg. 5 without a sketch

@@ -52,7 +52,7 @@ struct fab_handle {
   int tile_rows = 256, tile_nnz = 2048, tile_staged = 1;
   int* h_rowptr = nullptr;  // host copy of the row pointers (n+1), for re-tiling
   // workspace
-  fab::Buf W, H, sigma, shf, scl, wn2, coef, part, counter, gpart, skpart, SV, P, qr, tau, y, cvec, dense, piv, scal, lsq, u, xbuf,
+  fab::Buf W, H, sigma, shf, scl, coef, part, counter, gpart, skpart, SV, P, qr, tau, y, cvec, dense, piv, scal, lsq, u, xbuf,
       state;
   fab::Buf W32, Wbf, G;  // mixed path: FP32 basis, its BF16 copy, Gaussian sketch (BF16, s x ld)
   fab::Buf whm;          // FAB_WHITEN: R, R^{-1}, scratch ((m+1)^2 each), coefficients, norms

@@ -92,7 +92,7 @@ extern "C" int fab_sketch_apply_noalloc(int sketch, int64_t n, int s, int zeta, 
   if (sk.kind == SK_SRHT && launch_srht_sample(next_pow2(n), s, rng_state(seed, 4), P, st) != cudaSuccess)
     return FAB_ECUDA;
   for (int j = 0; j < ncols; ++j) {
-    if (launch_update((int)n, const_cast<double*>(V_dev), ldv, j, 0, 0, nullptr, nullptr, 1, ColScale{}, nullptr, 0,
+    if (launch_update((int)n, const_cast<double*>(V_dev), ldv, j, 0, 0, nullptr, nullptr, 1, ColScale{}, 0,
                       nullptr, nullptr, sk, ds, st) != cudaSuccess ||
         launch_sketch_reduce(sk, nullptr, 0, scale, out_dev + (size_t)j * s, ds, st) != cudaSuccess)
       return FAB_ECUDA;
