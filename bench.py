@@ -56,10 +56,10 @@ def _peaks():
 # this part).
 FP64_PEAK_GFLOPS_NOMINAL = 1250.0
 # DRAM bytes (read + write) of one k_spmv_dots launch measured by ncu on the
-# 128^3 case of this workload (262.1 MB for n = 2,097,152, window k = 4); traffic
+# 128^3 case of this workload (262.4 MB for n = 2,097,152, window k = 4); traffic
 # grows with n and nnz, so it is scaled by n to the bench size. Only valid for the
 # kernel version it was taken on, and only for the 3D convection-diffusion operator.
-SPMV_DRAM_BYTES_PER_ROW = 262.08e6 / 2_097_152
+SPMV_DRAM_BYTES_PER_ROW = 262_368_512 / 2_097_152
 
 
 def algorithmic_cost(n: int, nnz: int, m: int, k: int, s: int):
