@@ -142,6 +142,27 @@ def test_ragged_3d_srht_k4(fab, torch, method):
     assert _rel(x, ref.x) <= TOL
 
 
+@pytest.mark.parametrize("method", [krylov.SKETCHED_FAST, krylov.NOPROJ])
+def test_wide_window_k8_h_and_sketch(fab, torch, method):
+    """Window k = 8, the largest: the first steps run every window width 1..8, so the
+    SpMV's in-warp reduction of the kw window dots runs both with and without zero
+    padding (kw = 3, 5, 6, 7 are padded). H and the sketch of the basis against the
+    oracle; 3D convection-diffusion 23^3 (ragged last chunk), SRHT."""
+    A = W.convdiff(3, 23)
+    b = W.random_vector(A.n, 5)
+    m, k, s, t = 24, 8, 100, -1e-3
+    th = osk.make(osk.SRHT, A.n, s, 3, 8)
+    ref = krylov.run(method, W.to_scipy(A), b, m, k, matfun.EXP, th, t, tol=1e-14)
+    M, x, st = _run_gpu(fab, torch, A, b, f=fab.EXP, t=t, m=m, k=k, s=s, sketch=fab.SRHT, seed=3, method=method)
+    assert st.m_used == m
+    assert _rel(x, ref.x) <= TOL
+    ls = M.last_state()
+    B = ref.basis
+    assert np.allclose(ls.H, B.H, rtol=0, atol=1e-11 * np.abs(B.H).max())
+    if method == krylov.SKETCHED_FAST:
+        assert np.max(np.abs(ls.SV - th.apply(B.V))) <= 1e-12
+
+
 @pytest.mark.parametrize("f", [matfun.SQRT, matfun.INVSQRT])
 @pytest.mark.parametrize("method", [krylov.SKETCHED_FAST, krylov.ARNOLDI, krylov.NOPROJ])
 def test_graph_laplacian_sqrt(fab, torch, f, method):
