@@ -68,3 +68,18 @@ def test_sketch_apply_rejects_bad_sizes(fab):
     assert fab.lib.fab_sketch_apply(fab.SPARSE_SIGN, 10, 4, 8, 1, out, 10, 1, out, None) == fab.FAB_EINVAL  # zeta > s
     assert fab.lib.fab_sketch_apply(fab.GAUSSIAN, 10, 4, 2, 1, out, 10, 257, out, None) == fab.FAB_EINVAL  # ncols
     assert fab.lib.fab_sketch_apply(7, 10, 4, 2, 1, out, 10, 1, out, None) == fab.FAB_EINVAL  # unknown sketch
+
+
+def test_profile_class_selection_is_host_side(fab):
+    """fab_profile_only takes the kernel class names of fab_profile_query (NULL or ""
+    for every class) and rejects others; no device work is involved."""
+    for name in fab.PROFILE_KINDS:
+        assert fab.lib.fab_profile_only(name.encode()) == fab.FAB_OK
+    assert fab.lib.fab_profile_only(None) == fab.FAB_OK
+    assert fab.lib.fab_profile_only(b"") == fab.FAB_OK
+    assert fab.lib.fab_profile_only(b"spmv") == fab.FAB_EINVAL
+    assert fab.lib.fab_profile_query(b"spmv", None, None) == fab.FAB_EINVAL
+    ms, cnt = ctypes.c_double(-1.0), ctypes.c_int64(-1)
+    assert fab.lib.fab_profile_enable(0) == fab.FAB_OK  # resets the accumulators
+    assert fab.lib.fab_profile_query(b"spmv_dots", ctypes.byref(ms), ctypes.byref(cnt)) == fab.FAB_OK
+    assert ms.value == 0.0 and cnt.value == 0
