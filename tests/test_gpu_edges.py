@@ -1,0 +1,135 @@
+"""GPU: edge cases of the path, against closed forms or the FP64 oracle.
+
+A 1 x 1 matrix (the Krylov space ends after one column), rows without nonzeros
+(at the start, the end and inside a row tile), the largest Krylov dimension
+(m = 1024) and the largest sketch (s = 4096, with the sketch-and-solve QR on
+the cluster path and on the one-block fallback).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import krylov, matfun
+from oracle import sketch as osk
+from paper_2212_12758_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def fab():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2212_12758_gb300 import fab as f
+
+    return f
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    assert t.cuda.is_available()
+    return t
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _run(fab, torch, A, b, **kw):
+    M = fab.Matrix.from_csr(A)
+    x, st = M.apply(torch.from_numpy(b).cuda(), fab.params(**kw), stats=True)
+    return x.cpu().numpy(), st
+
+
+def test_one_by_one_matrix(fab, torch):
+    """A = (2), b = (3): A v_1 = 2 v_1, so h_21 = 0 ends the basis at one column and
+    every method returns exp(2t) 3."""
+    A = W.from_dense(np.array([[2.0]]))
+    b = np.array([3.0])
+    t = -0.7
+    for method, kw in ((fab.ARNOLDI, {}), (fab.NOPROJ, {}),
+                       (fab.SKETCHED_FAST, dict(s=4, zeta=2, sketch=fab.SPARSE_SIGN))):
+        x, st = _run(fab, torch, A, b, f=fab.EXP, t=t, m=3, k=2, method=method, **kw)
+        assert st.m_used == 1, method
+        assert abs(x[0] - 3.0 * math.exp(2.0 * t)) <= 1e-14 * 3.0, method
+
+
+def _without_rows(A, empty):
+    """A with the rows marked in `empty` left without nonzeros."""
+    counts = np.diff(A.rowptr)
+    keep = np.repeat(~empty, counts)
+    rowptr = np.zeros(A.n + 1, dtype=np.int64)
+    np.cumsum(np.where(empty, 0, counts), out=rowptr[1:])
+    return W.CSR(n=A.n, rowptr=rowptr, colind=np.ascontiguousarray(A.colind[keep]),
+                 vals=np.ascontiguousarray(A.vals[keep]))
+
+
+@pytest.mark.parametrize("method", [krylov.SKETCHED_FAST, krylov.SKETCHED_LS, krylov.NOPROJ, krylov.ARNOLDI])
+def test_rows_without_nonzeros(fab, torch, method):
+    """2D convection-diffusion 50^2 with its first row, its last row and rows 100..199
+    (inside one 256-row tile and across the next) emptied: A v is zero there."""
+    A0 = W.convdiff(2, 50)
+    empty = np.zeros(A0.n, dtype=bool)
+    empty[[0, A0.n - 1]] = True
+    empty[100:200] = True
+    A = _without_rows(A0, empty)
+    assert np.all(np.diff(A.rowptr)[empty] == 0)
+    b = W.random_vector(A.n, 4)
+    m, k, s, t = 30, 2, 120, -0.01
+    th = osk.make(osk.SRHT, A.n, s, 5, 8)
+    ref = krylov.run(method, W.to_scipy(A), b, m, k, matfun.EXP, th, t, tol=1e-14)
+    x, st = _run(fab, torch, A, b, f=fab.EXP, t=t, m=m, k=k, s=s, sketch=fab.SRHT, seed=5, method=method,
+                 lsqr_tol=1e-14)
+    assert st.m_used == m
+    assert _rel(x, ref.x) <= TOL
+
+
+@pytest.mark.parametrize("method,N", [(krylov.ARNOLDI, 11), (krylov.NOPROJ, 22)])
+def test_largest_krylov_dimension(fab, torch, method, N):
+    """m = 1024, the largest the library takes, on the symmetric 3D Laplacian N^3,
+    exp(-0.5 A) b: Arnoldi (full orthogonalization; N = 11, n = 1331 keeps the oracle's
+    modified Gram-Schmidt short) and Alg. 5 with k = 2 (N = 22; the window recurrence
+    is then Lanczos', whose Ritz values stay in the spectrum)."""
+    A = W.laplacian3d(N)
+    b = W.random_vector(A.n, 6)
+    m, k, t = 1024, 2, -0.5
+    ref = krylov.run(method, W.to_scipy(A), b, m, k, matfun.EXP, None, t)
+    x, st = _run(fab, torch, A, b, f=fab.EXP, t=t, m=m, k=k, method=method)
+    assert st.m_used == m
+    assert _rel(x, ref.x) <= TOL
+
+
+@pytest.mark.parametrize("kind", [osk.SPARSE_SIGN, osk.SRHT])
+def test_largest_sketch_of_vectors(fab, torch, kind):
+    """s = 4096, the largest sketch, on vectors with a wide dynamic range (n = 12345,
+    padded to 16384 for the SRHT)."""
+    n, s = 12345, 4096
+    rng = np.random.default_rng(9)
+    Vh = rng.standard_normal((3, n)) * np.array([[1.0], [1e-7], [3e5]])
+    Vh[2, ::3] *= 1e-9
+    out = fab.sketch_apply(torch.from_numpy(Vh).cuda(), s, sketch=kind, zeta=8, seed=4).cpu().numpy()
+    ref = osk.make(kind, n, s, 4, 8).apply(Vh.T).T
+    for j in range(3):
+        assert np.max(np.abs(out[j] - ref[j])) <= 1e-13 * np.linalg.norm(Vh[j])
+
+
+@pytest.mark.parametrize("m", [40, 100])
+def test_largest_sketch_in_a_solve(fab, torch, m):
+    """sketched_fast with s = 4096 on the 2D convection-diffusion 100^2: the QR of the
+    4096 x (m+1) sketch runs on the cluster (m = 40) and on the one-block fallback
+    (m = 100, too large for the cluster's shared memory)."""
+    A = W.convdiff(2, 100)
+    b = W.random_vector(A.n, 0)
+    s, k, t = 4096, 2, -0.01
+    th = osk.make(osk.SRHT, A.n, s, 1, 8)
+    ref = krylov.run(krylov.SKETCHED_FAST, W.to_scipy(A), b, m, k, matfun.EXP, th, t)
+    x, st = _run(fab, torch, A, b, f=fab.EXP, t=t, m=m, k=k, s=s, sketch=fab.SRHT, seed=1,
+                 method=fab.SKETCHED_FAST)
+    assert st.m_used == m
+    assert _rel(x, ref.x) <= TOL
