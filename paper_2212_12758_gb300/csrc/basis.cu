@@ -301,27 +301,28 @@ __device__ __forceinline__ void spmv_dots_body(
     __syncthreads();
     return;
   }
-  if (KW == 0) {  // no window (Alg. 1, Arnoldi): only the scale of the new column
+  if constexpr (KW == 0) {  // no window (Alg. 1, Arnoldi): only the scale of the new column
     if (bid == 0 && tid == 0) cs.scl[c] = column_tau(cs.sigma[c - 1], ksh);
     return;
-  }
-  double accd[NV];
+  } else {
+    double accd[NV];
 #pragma unroll
-  for (int q = 0; q < NV; ++q) accd[q] = (double)acc[q];
-  block_sum_multi<NV>(accd, sh, tot);
-  if (tid < NV) part[(size_t)bid * NV + tid] = tot[tid];
-  if (!last_block(counter, (unsigned)nblk)) return;
-  sum_partials_multi<NV>(part, nblk, tot, sh);
-  const double tau = column_tau(cs.sigma[c - 1], ksh);
-  if (tid < kw) {
-    const int j = j0 + tid;
-    const double d = tot[tid];
-    H[j + (size_t)ldh * (c - 1)] = cs.sigma[j] * tau * d;
-    coef[tid] = cs.sigma[j] * cs.sigma[j] * d;
-  }
-  if (tid == 0) {
-    cs.scl[c] = tau;
-    *counter = 0;
+    for (int q = 0; q < NV; ++q) accd[q] = (double)acc[q];
+    block_sum_multi<NV>(accd, sh, tot);
+    if (tid < NV) part[(size_t)bid * NV + tid] = tot[tid];
+    if (!last_block(counter, (unsigned)nblk)) return;
+    sum_partials_multi<NV>(part, nblk, tot, sh);
+    const double tau = column_tau(cs.sigma[c - 1], ksh);
+    if (tid < kw) {
+      const int j = j0 + tid;
+      const double d = tot[tid];
+      H[j + (size_t)ldh * (c - 1)] = cs.sigma[j] * tau * d;
+      coef[tid] = cs.sigma[j] * cs.sigma[j] * d;
+    }
+    if (tid == 0) {
+      cs.scl[c] = tau;
+      *counter = 0;
+    }
   }
 }
 
@@ -808,10 +809,10 @@ __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update(
     int n, TV* __restrict__ W, int64_t ld, int c, int j0, int nc, const double* __restrict__ coef,
     double* __restrict__ H, int ldh, ColScale cs, int mode, double* __restrict__ part,
     unsigned* __restrict__ counter, SketchDev sk, DevState* st, int gate) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_upd[];
   if (gate_closed(st, c, gate)) return;
   update_body<SK, TV>(n, W, ld, c, j0, nc, coef, H, ldh, cs, mode, part, counter, sk, st, blockIdx.x, gridDim.x,
-                      smem_raw);
+                      smem_upd);
 }
 
 size_t update_smem_bytes(int kind, int nc, int s) {
@@ -1283,13 +1284,13 @@ __global__ __launch_bounds__(kThreads) void k_spmv_wave(const BasisJob<TV>* __re
 template <int SK, typename TV>
 __global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update_wave(
     const BasisJob<TV>* __restrict__ jobs, Wave w, int c, int nc, int mode) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_upd[];
   const int i = wave_slot(w, blockIdx.x);
   const BasisJob<TV>* J = jobs + w.ids[i];
   const ColScale cs = J->cs;
   const SketchDev sk = J->sk;
   update_body<SK, TV>(J->A.n, J->W, J->ld, c, c - nc, nc, J->coef, J->H, J->ldh, cs, mode, J->part,
-                      J->counter, sk, J->st, blockIdx.x - w.pre[i], w.pre[i + 1] - w.pre[i], smem_raw);
+                      J->counter, sk, J->st, blockIdx.x - w.pre[i], w.pre[i + 1] - w.pre[i], smem_upd);
 }
 
 template <typename TV>
