@@ -172,8 +172,10 @@ int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr,
  *   st             optional diagnostics (may be NULL)
  * Runs on p->stream; returns after x is written (the call synchronizes that
  * stream). Workspace grows on demand and is kept by the handle. A breakdown of
- * the basis (h_{c,c-1} <= 64 eps ||A v_{c-1}||) is not an error: the space is
- * invariant and the result uses m_used = c basis vectors. b = 0 gives x = 0.
+ * the basis (h_{c,c-1} <= 64 eps ||A v_{c-1}||, the norm taken as
+ * (h_{c,c-1}^2 + sum_j h_{j,c-1}^2)^(1/2) over the orthogonalized columns) is not
+ * an error: the space is invariant and the result uses m_used = c basis vectors.
+ * b = 0 gives x = 0.
  */
 int fab_apply(fab_handle* h, const fab_params* p, const double* b, double* x,
               int bx_on_device, fab_stats* st);
@@ -354,7 +356,8 @@ int fab_batch_run(fab_handle* const* hs, const fab_params* ps, const double* con
  * launches of one class:
  *   "spmv_dots"      SpMV fused with the window dot products (Alg. 2)
  *   "update"         window update + norm + fused sketch of the new vector
- *   "sketch_reduce"  cross-chunk reduction of the sketch
+ *   "sketch_reduce"  cross-block reduction of the sketch (per step, or once per
+ *                    pass where nothing reads the sketch before the pass ends)
  *   "gemv_t"         V^T w passes (Arnoldi, LSQR)
  *   "small"          QR / LSQR scalar steps / f(H) kernels
  *   "combine"        x = ||b|| V_m c and the LSQR vector update
