@@ -528,7 +528,7 @@ def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> flo
     return units_per_rank * world / max_seconds
 
 
-def cpu_oracle_sample(A, b, budget_s: float = 15.0):
+def cpu_oracle_sample(A, b, budget_s: float = 30.0, max_steps: int = 32):
     """Time the FP64 CPU oracle on a bounded sample of one solve of the workload:
     the first steps of Alg. 2 (SpMV + window orthogonalization), the SRHT sketch of
     those columns and the combine of those columns, extrapolated linearly to the
@@ -545,7 +545,7 @@ def cpu_oracle_sample(A, b, budget_s: float = 15.0):
         _ = th.apply(B.V)
         _ = B.V[:, :steps] @ np.ones(steps)
         dt = time.perf_counter() - t0
-        if dt > budget_s / 2 or steps >= 16:
+        if dt > budget_s / 2 or steps >= max_steps:
             break
         steps *= 2
     per_step = dt / (steps + 1)
