@@ -4,6 +4,8 @@ Each check is fixed by the mathematics, not by the oracle itself:
 * eq. arnoldilike: A V_m = V_{m+1} H_m for every basis (residual ~ eps);
 * Alg. 2 with k >= m and MGS is Arnoldi (identical operations);
 * symmetric A, k = 2 gives Lanczos (orthonormal basis; Alg. 5 equals Arnoldi);
+* Alg. 2: any k + 1 consecutive vectors are orthonormal, so ||A v_{c-1}||^2 is the sum
+  of the squares of column c-1's window coefficients and h_{c,c-1};
 * lemma:basis: with the LS solved exactly, Alg. 4 equals Arnoldi;
 * thm:lastcol: every method is exact for polynomials of degree <= m-1;
 * m = n and #distinct eigenvalues <= m give the exact f(A)b;
@@ -70,6 +72,27 @@ def test_symmetric_k2_is_lanczos():
     r1 = krylov.noproj(A, b, 12, 2, INVSQRT)
     r2 = krylov.fm_arnoldi(A, b, 12, INVSQRT)
     assert _rel(r1.x, r2.x) < 1e-8
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+def test_nt_window_orthonormal_pythagoras(k):
+    """Alg. 2 orthogonalizes each new vector against the k before it, so any k + 1
+    consecutive basis vectors are orthonormal (each pair is fewer than k + 1 apart), and
+    A v_{c-1} = sum_{j in window} h_{j,c-1} v_j + h_{c,c-1} v_c gives
+    ||A v_{c-1}||^2 = h_{c,c-1}^2 + sum_{window} h_{j,c-1}^2 (the breakdown test's norm).
+    Checked on a nonsymmetric convection-diffusion matrix and a directed graph
+    Laplacian, whose bases are far from orthonormal overall."""
+    for A, b in ((W.to_scipy(W.convdiff(2, 40)), W.random_vector(1600, 1)),
+                 (W.to_scipy(W.chung_lu_laplacian(3000, seed=2)), W.random_vector(3000, 7))):
+        B = krylov.nt_basis(A, b, 40, k)
+        V, H = B.V, B.H
+        for c in range(1, V.shape[1]):
+            j0 = max(0, c - k)
+            Wn = V[:, j0:c + 1]
+            assert np.linalg.norm(Wn.T @ Wn - np.eye(c + 1 - j0)) < 1e-12
+            av = np.linalg.norm(A @ V[:, c - 1])
+            est = math.sqrt(H[c, c - 1] ** 2 + np.sum(H[j0:c, c - 1] ** 2))
+            assert abs(est - av) <= 1e-12 * av
 
 
 def test_m_equals_n_is_exact():
