@@ -67,7 +67,7 @@ extern "C" {
 enum {
   FAB_OK = 0,
   FAB_EINVAL = -1,    /* invalid argument: bad CSR, k < 1, s < m+1, sizes out of range */
-  FAB_ENOMEM = -2,    /* device allocation failed (nothing leaked)                     */
+  FAB_ENOMEM = -2,    /* device or host allocation failed (nothing leaked)             */
   FAB_ECUDA = -3,     /* a CUDA call failed                                            */
   FAB_ENUMERIC = -4,  /* NaN/Inf in the basis, or no principal square root             */
   FAB_ETIMEOUT = -5,  /* a bounded wait expired                                        */

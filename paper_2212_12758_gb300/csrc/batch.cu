@@ -411,7 +411,7 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
 
 }  // namespace
 
-extern "C" int fab_batch_create(fab_batch** out, fab_handle* const* hs, const fab_params* ps, int count) {
+extern "C" int fab_batch_create(fab_batch** out, fab_handle* const* hs, const fab_params* ps, int count) try {
   if (!out) return FAB_EINVAL;
   *out = nullptr;
   if (!hs || !ps || count < 1) return FAB_EINVAL;
@@ -431,6 +431,13 @@ extern "C" int fab_batch_create(fab_batch** out, fab_handle* const* hs, const fa
       if (rc != FAB_OK) return rc;
     }
   fab_batch* bt = new fab_batch();
+  // Releases a partly built batch on every early return and on an exception.
+  struct Owner {
+    fab_batch* bt;
+    ~Owner() {
+      if (bt) fab_batch_destroy(bt);
+    }
+  } owner{bt};
   bt->count = count;
   bt->mixed = prec == FAB_MIXED;
   bt->n.resize(count);
@@ -443,16 +450,16 @@ extern "C" int fab_batch_create(fab_batch** out, fab_handle* const* hs, const fa
     cudaGetLastError();
     rc = FAB_ECUDA;
   }
-  if (rc != FAB_OK) {
-    fab_batch_destroy(bt);
-    return rc;
-  }
+  if (rc != FAB_OK) return rc;
+  owner.bt = nullptr;
   *out = bt;
   return FAB_OK;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
 extern "C" int fab_batch_exec(fab_batch* bt, const double* const* bs, double* const* xs, fab_stats* sts,
-                              void* stream) {
+                              void* stream) try {
   if (!bt || !bt->exec) return FAB_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int count = bt->count;
@@ -500,6 +507,8 @@ extern "C" int fab_batch_exec(fab_batch* bt, const double* const* bs, double* co
 cuda_fail:
   cudaGetLastError();
   return FAB_ECUDA;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
 extern "C" double* fab_batch_input(fab_batch* bt, int i) {
@@ -512,7 +521,7 @@ extern "C" double* fab_batch_output(fab_batch* bt, int i) {
 
 extern "C" int fab_batch_kernels(const fab_batch* bt) { return bt ? bt->kernels : 0; }
 
-extern "C" void fab_batch_destroy(fab_batch* bt) {
+extern "C" void fab_batch_destroy(fab_batch* bt) try {
   if (!bt) return;
   if (bt->exec) cudaGraphExecDestroy(bt->exec);
   if (bt->t0) cudaEventDestroy(bt->t0);
@@ -520,10 +529,11 @@ extern "C" void fab_batch_destroy(fab_batch* bt) {
   if (bt->mem) cudaFree(bt->mem);
   cudaGetLastError();
   delete bt;
+} catch (...) {
 }
 
 extern "C" int fab_batch_run(fab_handle* const* hs, const fab_params* ps, const double* const* bs, double* const* xs,
-                             int count, fab_stats* sts) {
+                             int count, fab_stats* sts) try {
   if (!bs || !xs) return FAB_EINVAL;
   fab_batch* bt = nullptr;
   int rc = fab_batch_create(&bt, hs, ps, count);
@@ -531,4 +541,6 @@ extern "C" int fab_batch_run(fab_handle* const* hs, const fab_params* ps, const 
   rc = fab_batch_exec(bt, bs, xs, sts, ps[0].stream);
   fab_batch_destroy(bt);
   return rc;
+} catch (...) {
+  return fab::abi_error_code();
 }

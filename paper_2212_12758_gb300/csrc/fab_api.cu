@@ -154,7 +154,7 @@ const char* fab_strerror(int code) {
 }
 
 int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colind,
-               const double* vals, int inputs_on_device) {
+               const double* vals, int inputs_on_device) try {
   if (!out) return FAB_EINVAL;
   *out = nullptr;
   if (n < 1 || n >= (int64_t)1 << 31 || nnz < 0 || nnz >= (int64_t)1 << 31 || !rowptr || (nnz > 0 && (!colind || !vals)))
@@ -184,6 +184,14 @@ int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr, 
   std::vector<int> rp32(n + 1);
   for (int64_t i = 0; i <= n; ++i) rp32[i] = (int)rp[i];
   fab_handle* h = new fab_handle();
+  // Destroys the handle on every early return and on an exception (a host
+  // allocation below), so that a create that fails leaves nothing behind.
+  struct Owner {
+    fab_handle* h;
+    ~Owner() {
+      if (h) fab_destroy(h);
+    }
+  } owner{h};
   h->n = (int)n;
   h->nnz = (int)nnz;
   h->ld = ((n + 31) / 32) * 32;
@@ -191,7 +199,6 @@ int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr, 
       cudaMalloc(&h->d_colind, (nnz + kCsrPad) * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&h->d_vals, (nnz + kCsrPad) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
-    fab_destroy(h);
     return FAB_ENOMEM;
   }
   // the spare entries past nnz are read (never used) by the 16-byte aligned tile copies
@@ -201,18 +208,17 @@ int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr, 
       (nnz > 0 && cudaMemcpy(h->d_colind, ci.data(), nnz * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) ||
       (nnz > 0 && cudaMemcpy(h->d_vals, va.data(), nnz * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)) {
     cudaGetLastError();
-    fab_destroy(h);
     return FAB_ECUDA;
   }
   h->h_rowptr = new int[n + 1];
   memcpy(h->h_rowptr, rp32.data(), (n + 1) * sizeof(int));
   const int rc = fab::build_tiles(h, 256, kSpmvCap, 1);
-  if (rc != FAB_OK) {
-    fab_destroy(h);
-    return rc;
-  }
+  if (rc != FAB_OK) return rc;
+  owner.h = nullptr;
   *out = h;
   return FAB_OK;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
 void fab_destroy(fab_handle* h) {
@@ -996,7 +1002,7 @@ int build_square(fab_handle* h) {
 }  // namespace
 
 extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, double* x, int bx_on_device,
-                         fab_stats* stats) {
+                         fab_stats* stats) try {
   if (!h || !p || !b || !x) return FAB_EINVAL;
   int rc = validate(h, p);
   if (rc != FAB_OK) return rc;
@@ -1036,9 +1042,11 @@ extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, do
     return apply_impl<float>(h, p, b, x, bx_on_device, stats, ws, ws.W32, h->d_vals32);
   }
   return apply_impl<double>(h, p, b, x, bx_on_device, stats, ws, ws.W, h->d_vals);
+} catch (...) {
+  return fab::abi_error_code();
 }
 
-extern "C" int fab_last_state(fab_handle* h, double* H, double* SV, double* y, double* coeffs) {
+extern "C" int fab_last_state(fab_handle* h, double* H, double* SV, double* y, double* coeffs) try {
   if (!h || !h->has_state) return FAB_EINVAL;
   const int m = h->last_m;
   if (H && cudaMemcpy2D(H, (size_t)(m + 1) * 8, h->H.p, (size_t)h->last_ldh * 8, (size_t)(m + 1) * 8, m,
@@ -1050,9 +1058,11 @@ extern "C" int fab_last_state(fab_handle* h, double* H, double* SV, double* y, d
   if (y && cudaMemcpy(y, h->y.p, (size_t)m * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return FAB_ECUDA;
   if (coeffs && cudaMemcpy(coeffs, h->cvec.p, (size_t)m * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return FAB_ECUDA;
   return FAB_OK;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
-extern "C" int fab_last_basis(fab_handle* h, double* V, int dst_on_device) {
+extern "C" int fab_last_basis(fab_handle* h, double* V, int dst_on_device) try {
   if (!h || !h->has_state || !V) return FAB_EINVAL;
   const int m = h->last_m, n = h->n;
   double* dst = V;
@@ -1078,10 +1088,12 @@ extern "C" int fab_last_basis(fab_handle* h, double* V, int dst_on_device) {
   if (tmp) cudaFree(tmp);
   cudaGetLastError();
   return rc;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
 extern "C" int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t seed, const double* V_dev,
-                                int64_t ldv, int ncols, double* out_dev, void* stream) {
+                                int64_t ldv, int ncols, double* out_dev, void* stream) try {
   if (n < 1 || n >= (int64_t)1 << 31 || s < 1 || s > kMaxS || ncols < 0 || ldv < n || !V_dev || !out_dev)
     return FAB_EINVAL;
   if (sketch == FAB_SK_SPARSE_SIGN) {
@@ -1166,6 +1178,8 @@ extern "C" int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t
   if (cudaStreamSynchronize(st) != cudaSuccess) rc = FAB_ECUDA;
   cudaGetLastError();
   return rc;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
 extern "C" int fab_profile_enable(int on) {
@@ -1204,9 +1218,11 @@ extern "C" int fab_profile_query(const char* name, double* total_ms, int64_t* la
   return FAB_EINVAL;
 }
 
-extern "C" int fab_set_tiling(fab_handle* h, int rows_max, int nnz_cap, int staged) {
+extern "C" int fab_set_tiling(fab_handle* h, int rows_max, int nnz_cap, int staged) try {
   if (!h || !h->owns_matrix) return FAB_EINVAL;
   return fab::build_tiles(h, rows_max, nnz_cap, staged);
+} catch (...) {
+  return fab::abi_error_code();
 }
 
 namespace {
@@ -1251,7 +1267,7 @@ int time_spmv(fab_handle* h, const void* vals, int k, unsigned char* scratch, cu
 }
 }  // namespace
 
-extern "C" int fab_tune(fab_handle* h, int precision, int k, int* choice, void* stream) {
+extern "C" int fab_tune(fab_handle* h, int precision, int k, int* choice, void* stream) try {
   if (!h || !h->owns_matrix || (precision != FAB_FP64 && precision != FAB_MIXED) || k < 1 || k > kMaxWindow)
     return FAB_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1303,6 +1319,8 @@ extern "C" int fab_tune(fab_handle* h, int precision, int k, int* choice, void* 
     choice[2] = bi[2];
   }
   return rc;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
 extern "C" const char* fab_last_error(void) { return g_errmsg; }

@@ -6,9 +6,31 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <new>
+#include <stdexcept>
+#include <system_error>
+
 #include "../../include/fab.h"
 
 namespace fab {
+
+// The C ABI returns error codes and lets no C++ exception out. Called inside a
+// catch (...) handler, this maps the exception in flight to a code: a failed host
+// allocation, an impossible size or an exhausted system resource (a thread, a lock)
+// is FAB_ENOMEM, anything else FAB_EINVAL.
+inline int abi_error_code() noexcept {
+  try {
+    throw;
+  } catch (const std::bad_alloc&) {
+    return FAB_ENOMEM;
+  } catch (const std::length_error&) {
+    return FAB_ENOMEM;
+  } catch (const std::system_error&) {
+    return FAB_ENOMEM;
+  } catch (...) {
+    return FAB_EINVAL;
+  }
+}
 
 // Grow-only device buffer.
 struct Buf {

@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "fab_internal.cuh"
+#include "handle.cuh"
 
 namespace {
 
@@ -52,7 +53,7 @@ int64_t next_pow2(int64_t n) {
 }  // namespace
 
 extern "C" int fab_sketch_apply_noalloc(int sketch, int64_t n, int s, int zeta, uint64_t seed, const double* V_dev,
-                                        int64_t ldv, int ncols, double* out_dev, void* stream) {
+                                        int64_t ldv, int ncols, double* out_dev, void* stream) try {
   using namespace fab;
   if (n < 1 || n >= (int64_t)1 << 31 || s < 1 || s > kMaxS || ncols < 0 || ldv < n || !V_dev || !out_dev)
     return FAB_EINVAL;
@@ -102,4 +103,6 @@ extern "C" int fab_sketch_apply_noalloc(int sketch, int64_t n, int s, int zeta, 
     return FAB_ECUDA;
   }
   return FAB_OK;
+} catch (...) {
+  return fab::abi_error_code();
 }

@@ -121,31 +121,37 @@ void worker(fab_server* s, int self) {
         s->cv_work.wait_for(lk, std::chrono::milliseconds(20));
       }
     }
-    // solve outside the lock on this slot's stream and workspace
-    if (!sl.ws) sl.ws = fab::clone_for_workspace(r->h);
-    else fab::point_to_matrix(sl.ws, r->h);
-    fab_params p = r->p;
-    p.stream = sl.stream;
-    const size_t n = r->b.size();
-    r->x.assign(n, 0.0);
-    if (sl.pin_n < n) {  // pinned staging: the copies run asynchronously on the slot's stream
-      if (sl.pin) cudaFreeHost(sl.pin);
-      sl.pin = nullptr;
-      sl.pin_n = 0;
-      if (cudaHostAlloc(&sl.pin, 2 * n * sizeof(double), cudaHostAllocDefault) == cudaSuccess) sl.pin_n = n;
-      else cudaGetLastError();
+    // solve outside the lock on this slot's stream and workspace; a host allocation
+    // that fails here is the request's error, not the worker's end
+    try {
+      if (!sl.ws) sl.ws = fab::clone_for_workspace(r->h);
+      else fab::point_to_matrix(sl.ws, r->h);
+      fab_params p = r->p;
+      p.stream = sl.stream;
+      const size_t n = r->b.size();
+      r->x.assign(n, 0.0);
+      if (sl.pin_n < n) {  // pinned staging: the copies run asynchronously on the slot's stream
+        if (sl.pin) cudaFreeHost(sl.pin);
+        sl.pin = nullptr;
+        sl.pin_n = 0;
+        if (cudaHostAlloc(&sl.pin, 2 * n * sizeof(double), cudaHostAllocDefault) == cudaSuccess) sl.pin_n = n;
+        else cudaGetLastError();
+      }
+      if (sl.pin) {
+        memcpy(sl.pin, r->b.data(), n * sizeof(double));
+        r->rc = fab_apply(sl.ws, &p, sl.pin, sl.pin + n, 0, &r->st);
+        memcpy(r->x.data(), sl.pin + n, n * sizeof(double));
+      } else {
+        r->rc = fab_apply(sl.ws, &p, r->b.data(), r->x.data(), 0, &r->st);
+      }
+      if (r->rc == FAB_ECUDA) snprintf(r->err, sizeof(r->err), "%s", fab_last_error());
+    } catch (...) {
+      r->rc = fab::abi_error_code();
+      r->x.clear();
     }
-    if (sl.pin) {
-      memcpy(sl.pin, r->b.data(), n * sizeof(double));
-      r->rc = fab_apply(sl.ws, &p, sl.pin, sl.pin + n, 0, &r->st);
-      memcpy(r->x.data(), sl.pin + n, n * sizeof(double));
-    } else {
-      r->rc = fab_apply(sl.ws, &p, r->b.data(), r->x.data(), 0, &r->st);
-    }
-    if (r->rc == FAB_ECUDA) snprintf(r->err, sizeof(r->err), "%s", fab_last_error());
     {
       std::lock_guard<std::mutex> lk(s->mu);
-      sl.held = fab::handle_ws_bytes(sl.ws);
+      sl.held = sl.ws ? fab::handle_ws_bytes(sl.ws) : 0;
       sl.busy = false;
       r->t_done = Clock::now();
       r->done = true;
@@ -158,19 +164,25 @@ void worker(fab_server* s, int self) {
 
 }  // namespace
 
-extern "C" int fab_server_create(fab_server** out, size_t hbm_budget_bytes, int slots) {
+extern "C" int fab_server_create(fab_server** out, size_t hbm_budget_bytes, int slots) try {
   if (!out || slots < 1 || slots > 64) return FAB_EINVAL;
   *out = nullptr;
   fab_server* s = new fab_server();
+  // Releases whatever was set up (streams, workers already started) on every early
+  // return and on an exception (a thread that cannot start, a host allocation).
+  struct Owner {
+    fab_server* s;
+    ~Owner() {
+      if (s) fab_server_destroy(s);
+    }
+  } owner{s};
   if (cudaGetDevice(&s->device) != cudaSuccess) {
     cudaGetLastError();
-    delete s;
     return FAB_ECUDA;
   }
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
     cudaGetLastError();
-    delete s;
     return FAB_ECUDA;
   }
   s->budget = hbm_budget_bytes ? hbm_budget_bytes : (free_b / 10) * 9;
@@ -178,18 +190,20 @@ extern "C" int fab_server_create(fab_server** out, size_t hbm_budget_bytes, int 
   for (int i = 0; i < slots; ++i) {
     if (cudaStreamCreateWithFlags(&s->slots[i].stream, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
-      for (int j = 0; j < i; ++j) cudaStreamDestroy(s->slots[j].stream);
-      delete s;
+      s->slots[i].stream = nullptr;
       return FAB_ECUDA;
     }
   }
   for (int i = 0; i < slots; ++i) s->slots[i].th = std::thread(worker, s, i);
+  owner.s = nullptr;
   *out = s;
   return FAB_OK;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
 extern "C" int fab_server_submit(fab_server* s, fab_handle* h, const fab_params* p, const double* b,
-                                 uint64_t* ticket) {
+                                 uint64_t* ticket) try {
   if (!s || !h || !p || !b || !ticket || p->f == FAB_F_SIGN) return FAB_EINVAL;
   Request* r = new Request();
   r->h = h;
@@ -219,10 +233,12 @@ extern "C" int fab_server_submit(fab_server* s, fab_handle* h, const fab_params*
   }
   s->cv_work.notify_all();
   return FAB_OK;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
 extern "C" int fab_server_poll(fab_server* s, uint64_t ticket, double* x, fab_stats* st, double* latency_ms,
-                               int timeout_ms) {
+                               int timeout_ms) try {
   if (!s) return FAB_EINVAL;
   std::unique_lock<std::mutex> lk(s->mu);
   auto it = s->reqs.find(ticket);
@@ -240,9 +256,11 @@ extern "C" int fab_server_poll(fab_server* s, uint64_t ticket, double* x, fab_st
   s->reqs.erase(it);
   delete r;
   return rc;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
-extern "C" int fab_server_stats_get(fab_server* s, fab_server_stats* out) {
+extern "C" int fab_server_stats_get(fab_server* s, fab_server_stats* out) try {
   if (!s || !out) return FAB_EINVAL;
   std::lock_guard<std::mutex> lk(s->mu);
   memset(out, 0, sizeof(*out));
@@ -255,9 +273,11 @@ extern "C" int fab_server_stats_get(fab_server* s, fab_server_stats* out) {
   }
   out->bytes_budget = (double)s->budget;
   return FAB_OK;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
-extern "C" void fab_server_destroy(fab_server* s) {
+extern "C" void fab_server_destroy(fab_server* s) try {
   if (!s) return;
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -274,4 +294,5 @@ extern "C" void fab_server_destroy(fab_server* s) {
   for (auto& kv : s->reqs) delete kv.second;
   cudaGetLastError();
   delete s;
+} catch (...) {
 }
