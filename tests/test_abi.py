@@ -83,3 +83,26 @@ def test_profile_class_selection_is_host_side(fab):
     assert fab.lib.fab_profile_enable(0) == fab.FAB_OK  # resets the accumulators
     assert fab.lib.fab_profile_query(b"spmv_dots", ctypes.byref(ms), ctypes.byref(cnt)) == fab.FAB_OK
     assert ms.value == 0.0 and cnt.value == 0
+
+
+def test_create_allocation_fault_returns_enomem(fab):
+    """Host-side fault injection: FAB_FAULT=alloc:1 fails the first device allocation,
+    which fab_create consults before any CUDA call. It returns FAB_ENOMEM, leaves *out
+    NULL and releases its partial handle through the same cleanup as a real failure.
+    (Without a GPU the allocation would fail with the same code anyway; there the check
+    is that the failing path returns cleanly.) The setting is read once per process,
+    so the check runs in a child process."""
+    import subprocess
+    import sys
+
+    code = (
+        "import ctypes, numpy as np\n"
+        "from paper_2212_12758_gb300 import fab\n"
+        "h = ctypes.c_void_p()\n"
+        "rp = np.array([0, 1, 2], dtype=np.int64); ci = np.array([0, 1], dtype=np.int32); va = np.ones(2)\n"
+        "rc = fab.lib.fab_create(ctypes.byref(h), 2, 2, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0)\n"
+        "assert rc == fab.FAB_ENOMEM and not h.value, (rc, h.value)\n"
+        "print('ok')\n")
+    env = dict(os.environ, FAB_FAULT="alloc:1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
