@@ -44,3 +44,23 @@ def test_batch_specs_and_arrivals_ranges():
     arr = W.poisson_arrivals(2000.0, 20000, seed=4)
     assert np.all(np.diff(arr) > 0)
     assert abs(20000 / arr[-1] - 2000.0) < 60.0
+
+
+def test_bench_algorithmic_cost_of_the_basis_kernels():
+    """The per-launch algorithmic bytes and FP64 flops that bench.py divides by the
+    measured launch time, for the 3D convection-diffusion 200^3 workload (m = 100,
+    k = 4, SRHT s = 400): SpMV + window dots 12 nnz + 4(n+1) + 8 n k + 8 n bytes and
+    2 nnz + 2 n k flops; window update + sketch 8 n (k + 2) + 8 s chunks bytes and
+    2 n k + 2 n flops."""
+    import bench
+
+    n, nnz = 8_000_000, 55_760_000
+    assert W.convdiff_nnz(3, 200) == nnz
+    cost = bench.algorithmic_cost(n, nnz, 100, 4, 400)
+    sp_b, sp_f = cost["spmv_dots"]
+    up_b, up_f = cost["update"]
+    assert sp_b == 12 * nnz + 4 * (n + 1) + 8 * n * 4 + 8 * n == 1_021_120_004
+    assert sp_f == 2 * nnz + 2 * n * 4 == 175_520_000
+    chunks = (n + 4095) // 4096
+    assert up_b == 8 * n * 6 + 8 * 400 * chunks
+    assert up_f == 2 * n * 4 + 2 * n == 80_000_000
