@@ -52,14 +52,25 @@ def _peaks():
         return {}
 
 
-# FP64 FMA peak: the nominal GB300 FP64 rate (no measured FP64 figure exists for
-# this part).
+# FP64 FMA rate used only when the live measurement (fab_fma_peak) fails: the
+# nominal GB300 FP64 rate.
 FP64_PEAK_GFLOPS_NOMINAL = 1250.0
+# Basis steps in each sample of the CPU oracle (the GPU line's cpu_baseline and every
+# step of --impl reference use the same sample).
+CPU_SAMPLE_STEPS = 16
 # DRAM bytes (read + write) of one k_spmv_dots launch measured by ncu on the
 # 128^3 case of this workload (262.4 MB for n = 2,097,152, window k = 4); traffic
 # grows with n and nnz, so it is scaled by n to the bench size. Only valid for the
 # kernel version it was taken on, and only for the 3D convection-diffusion operator.
 SPMV_DRAM_BYTES_PER_ROW = 262_368_512 / 2_097_152
+
+
+def bench_config(grid: int, n: int, nnz: int, world: int) -> dict:
+    """The workload description both arms print (the same dict in both lines)."""
+    return {"workload": workload_name(grid, n, nnz), "n": n, "nnz": nnz, "m": M, "k": K_WIN, "s": S_ROWS,
+            "sketch": "srht", "method": "sketched_fast", "f": "exp(tA), t=-1e-3",
+            "l2": "inputs larger than L2 (A 0.7 GB, basis 6.5 GB per solve)",
+            "parallelism": f"replicas x{world}"}
 
 
 def algorithmic_cost(n: int, nnz: int, m: int, k: int, s: int):
@@ -170,6 +181,13 @@ def bench_mixed_same(fab, torch, Mx, bd, ref_x, stream, n: int, nnz: int, P, rep
                      "hbm_gbs": byts / sec / 1e9, "hbm_frac_of_measured": byts / sec / 1e9 / peak}
     basis_s = (prof["spmv_dots"][0] + prof["update"][0] + prof["sketch_reduce"][0]) / 1000.0 / reps
     out["basis_pass_hbm_frac_of_measured"] = M * (sp_bytes + up_bytes) / basis_s / 1e9 / peak
+    # the same pass against the single-pass floor of one basis step with its fused sign
+    # sketch, 8 nnz + 4 (n+1) + 4 n (k+1) bytes (A, row pointers, the k window columns,
+    # the new column written once)
+    b8d = sum(8 * nnz + 4 * (n + 1) + 4 * n * (min(c, kw) + 1) for c in range(1, M + 1))
+    out["basis_pass_frac_vs_8d"] = b8d / basis_s / 1e9 / peak
+    out["basis_pass_bytes_8d"] = b8d
+    out["basis_pass_ms"] = basis_s * 1000.0
     return out
 
 
@@ -528,32 +546,56 @@ def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> flo
     return units_per_rank * world / max_seconds
 
 
-def cpu_oracle_sample(A, b, budget_s: float = 30.0, max_steps: int = 32):
-    """Time the FP64 CPU oracle on a bounded sample of one solve of the workload:
-    the first steps of Alg. 2 (SpMV + window orthogonalization), the SRHT sketch of
-    those columns and the combine of those columns, extrapolated linearly to the
-    m = 100 steps of one solve (the small m x m terms are negligible at this n)."""
+def _oracle_small_stage_s(m: int, s: int, reps: int = 3) -> float:
+    """Seconds the oracle's small stage of one solve takes at the workload's sizes
+    (s x m QR of the sketched basis, the triangular solve of the sketch-and-solve
+    form, exp of the m x m projected matrix): timed on a synthetic problem of those
+    shapes, since the sampled solve has only a few columns."""
+    import scipy.linalg
+
+    import oracle
+
+    rng = np.random.default_rng(0)
+    SV = rng.standard_normal((s, m + 1))
+    H = np.triu(rng.standard_normal((m, m)), -1) * 0.1
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        Q, R = np.linalg.qr(SV[:, :m])
+        y = scipy.linalg.solve_triangular(R, Q.T @ SV[:, m], lower=False)
+        Hh = H.copy()
+        Hh[:, m - 1] += 0.01 * y
+        _ = oracle.matfun.f_e1(Hh, oracle.matfun.EXP, T_EXP)
+        best = min(best, time.perf_counter() - t0)
+    return best
+
+
+def cpu_oracle_sample(A, b, steps: int = CPU_SAMPLE_STEPS, small_s: float | None = None):
+    """Time the FP64 CPU oracle on a bounded sample of one solve of the workload: the
+    first `steps` steps of Alg. 2 (SpMV + window orthogonalization) on the full
+    matrix, the SRHT sketch of those columns and their combine, measured; the per-step
+    time is extrapolated linearly to the m = 100 steps of one solve, and the small
+    stage (QR, triangular solve, f(H) at m = 100, s = 400) is added as measured on
+    a problem of those shapes."""
     import oracle
     from paper_2212_12758_gb300 import workloads as W
 
     As = W.to_scipy(A)
     th = oracle.sketch.SRHT_(A.n, S_ROWS, SEED_SK)
-    steps = 2
-    while True:
-        t0 = time.perf_counter()
-        B = oracle.krylov.nt_basis(As, b, steps, K_WIN)
-        _ = th.apply(B.V)
-        _ = B.V[:, :steps] @ np.ones(steps)
-        dt = time.perf_counter() - t0
-        if dt > budget_s / 2 or steps >= max_steps:
-            break
-        steps *= 2
+    if small_s is None:
+        small_s = _oracle_small_stage_s(M, S_ROWS)
+    t0 = time.perf_counter()
+    B = oracle.krylov.nt_basis(As, b, steps, K_WIN)
+    _ = th.apply(B.V)
+    _ = B.V[:, :steps] @ np.ones(steps)
+    dt = time.perf_counter() - t0
     per_step = dt / (steps + 1)
-    solve_s = per_step * (M + 1)
+    solve_s = per_step * (M + 1) + small_s
     cores = len(os.sched_getaffinity(0))
-    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle", "extrapolated": True,
             "sample": f"first {steps} of {M} basis steps (Alg. 2 window k={K_WIN}, SRHT sketch, combine) of one "
-                      f"solve on the full n={A.n} matrix, {dt:.1f} s, extrapolated to {M} steps"}
+                      f"solve on the full n={A.n} matrix, measured {dt:.2f} s and extrapolated to {M} steps; plus "
+                      f"the m={M} small stage (QR, triangular solve, exp) measured on its own, {small_s * 1e3:.1f} ms"}
 
 
 def run_reference(args):
@@ -562,21 +604,24 @@ def run_reference(args):
         return 0
     from paper_2212_12758_gb300 import workloads as W
 
-    A = W.convdiff(3, N_GRID)
+    A = W.convdiff(3, args.grid)
     b = W.random_vector(A.n, SEED_B)
+    small_s = _oracle_small_stage_s(M, S_ROWS)
     for _ in range(args.warmup):
-        cpu_oracle_sample(A, b, budget_s=4.0)
+        cpu_oracle_sample(A, b, small_s=small_s)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_oracle_sample(A, b, budget_s=4.0))
+        vals.append(cpu_oracle_sample(A, b, small_s=small_s))
     wall = time.perf_counter() - t0
     v = float(np.median([x["value"] for x in vals]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "m": M, "k": K_WIN, "s": S_ROWS,
-                       "sketch": "srht", "method": "sketched_fast"},
+            "config": bench_config(args.grid, A.n, A.nnz, ws),
+            "extrapolated": True,
+            "step": f"each of the {args.steps} timed steps is one bounded sample of a solve ({CPU_SAMPLE_STEPS} of "
+                    f"{M} basis steps measured, extrapolated to a whole solve; value = median over the steps)",
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -695,6 +740,19 @@ def main():
     launches_per_solve = st.launches
     dom = max(("spmv_dots", "update"), key=lambda k_: prof_warm[k_][0])
 
+    # FP64 FMA rate of this GPU at its current clocks (the arithmetic roof of the FP64
+    # basis kernels), measured live with its own clock samples
+    fma_clk = ClockSampler(local)
+    fma_clk.start()
+    try:
+        fp64_peak, fp64_peak_ms = fab.fma_peak(fab.FP64, stream=sp)
+        fp32_peak, _ = fab.fma_peak(fab.MIXED, stream=sp)
+        fp64_src = "measured (fab_fma_peak: independent FP64 FMA chains on every SM, CUDA events)"
+    except Exception:
+        fp64_peak, fp64_peak_ms, fp32_peak = FP64_PEAK_GFLOPS_NOMINAL, 0.0, None
+        fp64_src = "nominal (measurement failed)"
+    fma_clocks = fma_clk.stop()
+
     # ---------------------------------------------------------------- timed
     clocks = ClockSampler(local)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -732,9 +790,9 @@ def main():
     peaks = _peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_frac = bytes_l / avg_s / 1e9 / hbm_peak
-    alu_frac = flops_l / avg_s / 1e9 / FP64_PEAK_GFLOPS_NOMINAL
+    alu_frac = flops_l / avg_s / 1e9 / fp64_peak
     if alu_frac >= hbm_frac:
-        roof = {"bound": "alu", "achieved": flops_l / avg_s / 1e9, "peak": FP64_PEAK_GFLOPS_NOMINAL,
+        roof = {"bound": "alu", "achieved": flops_l / avg_s / 1e9, "peak": fp64_peak,
                 "unit": "GFLOP/s (FP64)", "frac": alu_frac}
     else:
         roof = {"bound": "hbm", "achieved": bytes_l / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
@@ -744,11 +802,24 @@ def main():
                  if traffic else None, "ms_per_launch": avg_s * 1000.0,
                  "algorithmic_bytes_per_launch": bytes_l, "algorithmic_flops_per_launch": flops_l,
                  "hbm_gbs_algorithmic": bytes_l / avg_s / 1e9, "hbm_frac_of_measured": hbm_frac,
-                 "fp64_gflops": flops_l / avg_s / 1e9, "fp64_frac_of_nominal": alu_frac})
+                 "fp64_gflops": flops_l / avg_s / 1e9, "fp64_frac_of_measured": alu_frac,
+                 "fp64_peak": {"gflops": fp64_peak, "source": fp64_src, "ms": fp64_peak_ms, "clocks": fma_clocks,
+                               "fp32_gflops": fp32_peak}})
     kernel_share = {k_: {"ms": v[0], "launches": v[1],
                          "share": v[0] / max(sum(x[0] for x in prof_warm.values()), 1e-9)}
                     for k_, v in prof_warm.items()}
     kernel_share["source"] = "CUDA events around every launch of the last warm-up solve"
+    # the whole basis pass (SpMV + dots, update + norm + sketch, sketch reduce) of the
+    # last warm-up solve against its floor: the larger of the single-pass bytes of
+    # each step, 12 nnz + 4 (n+1) + 8 n (k+1), at the measured HBM rate and its FP64
+    # operations, 2 nnz + 4 n k + 3 n, at the measured FP64 FMA rate
+    basis_s = sum(prof_warm[k_][0] for k_ in ("spmv_dots", "update", "sketch_reduce")) / 1000.0
+    b64 = sum(12 * nnz + 4 * (n + 1) + 8 * n * (min(c, K_WIN) + 1) for c in range(1, M + 1))
+    f64 = sum(2 * nnz + 4 * n * min(c, K_WIN) + 3 * n for c in range(1, M + 1))
+    floor_s = max(b64 / (hbm_peak * 1e9), f64 / (fp64_peak * 1e9))
+    basis_pass = {"ms": basis_s * 1000.0, "bytes_8d": b64, "fp64_flops_8d": f64,
+                  "floor_ms": floor_s * 1000.0, "floor_bound": "hbm" if b64 / hbm_peak >= f64 / fp64_peak else "fp64",
+                  "frac_of_floor": floor_s / basis_s, "hbm_frac_vs_8d": b64 / basis_s / 1e9 / hbm_peak}
     # whole-solve algorithmic traffic (basis steps + combine)
     solve_bytes = M * (cost["spmv_dots"][0] + cost["update"][0]) + 8 * n * M
     hbm_gbs_solve = solve_bytes / (ms_per_step / 1000.0) / 1e9
@@ -821,14 +892,10 @@ def main():
         line = {"metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload_name(args.grid, n, nnz),
-                           "n": n, "nnz": nnz, "m": M, "k": K_WIN, "s": S_ROWS,
-                           "sketch": "srht", "method": "sketched_fast", "f": "exp(tA), t=-1e-3",
-                           "l2": "inputs larger than L2 (A 0.7 GB, basis 6.5 GB per solve)",
-                           "parallelism": f"replicas x{ws}"},
+                "config": bench_config(args.grid, n, nnz, ws),
                 "hbm_gbs": hbm_gbs_solve, "rel_err": rel_err,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-                "roofline": roof, "kernels": kernel_share, "gpu_launches": launches_per_solve * args.steps,
+                "roofline": roof, "basis_pass": basis_pass, "kernels": kernel_share, "gpu_launches": launches_per_solve * args.steps,
                 "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, **extras}
         print(json.dumps(line), flush=True)
     if dist:

@@ -134,6 +134,11 @@ typedef struct fab_stats {
   double ms_total;      /* device time of the whole solve                        */
   double err_est;       /* last sketched relative change (target mode), else 0   */
   int whiten_at;        /* FAB_WHITEN: basis columns when it was whitened, 0: never */
+  double kappa_est;     /* sketched methods with a sketch QR (FAB_SKETCHED_FAST,      */
+                        /* FAB_SKETCHED_LS): max|r_ii| / min|r_ii| of Theta V_m = Q R, */
+                        /* a lower bound on kappa_2(Theta V_m), which tracks kappa_2 */
+                        /* of the basis within the sketch's distortion (§2.1.2); 0   */
+                        /* for the other methods                                     */
 } fab_stats;
 
 typedef struct fab_handle fab_handle;
@@ -169,7 +174,10 @@ int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr,
 /*
  * fab_apply - x ~ f(A) b with the method, basis and sketch given in *p.
  *   b, x           n-vectors (FP64), device pointers if bx_on_device else host
- *   st             optional diagnostics (may be NULL)
+ *   st             optional diagnostics (may be NULL); also filled when the call
+ *                  returns FAB_ENOTCONV or FAB_ENUMERIC from f(H) (x is then not
+ *                  written; m_used, the iteration counts and kappa_est say how far
+ *                  the solve got)
  * Runs on p->stream; returns after x is written (the call synchronizes that
  * stream). Workspace grows on demand and is kept by the handle. A breakdown of
  * the basis (h_{c,c-1} <= 64 eps ||A v_{c-1}||, the norm taken as
@@ -232,7 +240,8 @@ int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t seed,
  * keeps this scratch (about 8.02 MiB) until the process exits.
  * Set-up: the first call on each device looks up the scratch address on that
  * device (the device must be current); make that first call before any stream
- * capture.
+ * capture. The address is kept for the life of the process: a caller that runs
+ * cudaDeviceReset must not call this entry point on that device afterwards.
  * Sharing: all calls on a device use the same scratch and it keeps the last
  * call's contents (each call clears what it needs); calls whose work overlaps
  * on the GPU (different streams or host threads) race on it, so serialize them.
@@ -366,6 +375,19 @@ int fab_batch_run(fab_handle* const* hs, const fab_params* ps, const double* con
  * launches, so a throughput measurement brackets only the kernel it needs.
  * Unknown names return FAB_EINVAL. Process-wide; not thread-safe.
  */
+/*
+ * fab_fma_peak - measured fused multiply-add throughput of this GPU (measurement
+ * support: the arithmetic bound of the FP64 basis kernels, which do about one FP64
+ * FMA per 4 to 8 bytes they move). Runs independent chains of FMAs on every SM and
+ * times them with CUDA events at the clocks the GPU runs now (it changes no clock).
+ *   precision  FAB_FP64 (FP64 FMAs) or FAB_MIXED (FP32 FMAs)
+ *   gflops     2 x FMAs / second / 1e9 (one FMA counts two flops)
+ *   ms         nullable: duration of the timed launch (at least about 50 ms)
+ *   stream     cudaStream_t or NULL; the call synchronizes it
+ * FAB_EINVAL for another precision or a NULL gflops.
+ */
+int fab_fma_peak(int precision, double* gflops, double* ms, void* stream);
+
 int fab_profile_enable(int on);
 int fab_profile_only(const char* name);
 int fab_profile_query(const char* name, double* total_ms, int64_t* launches);

@@ -352,10 +352,29 @@ def noproj(A, b, m: int, k: int, f: int, t: float = 1.0, coef=None, orth: str = 
 
 def _last_column_update(B: Basis, y: np.ndarray) -> np.ndarray:
     """H_m + h_{m+1,m} y e_m^T (eq. relationxx)."""
-    mu = B.m_used
-    Hhat = B.H[:mu, :mu].copy()
-    Hhat[:, mu - 1] += B.H[mu, mu - 1] * y
+    return last_column_update(B.H[: B.m_used + 1, : B.m_used], y)
+
+
+def last_column_update(H: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """H_m + h_{m+1,m} y e_m^T (eq. relationxx) for the (m+1) x m Hessenberg H."""
+    mu = H.shape[1]
+    Hhat = H[:mu, :mu].copy()
+    Hhat[:, mu - 1] += H[mu, mu - 1] * y
     return Hhat
+
+
+def sketch_solve_stage(H: np.ndarray, SV: np.ndarray, f: int, t: float = 1.0, coef=None):
+    """The small stage of the sketch-and-solve form (Remark after eq. sFOM) from the
+    (m+1) x m Hessenberg H and the sketched basis SV = Theta V_{m+1} (s x (m+1)):
+    Theta V_m = S R (thin QR), y = R^{-1} S^T Theta v_{m+1} (the least-squares
+    solution of min ||Theta (V_m z - v_{m+1})||), then c = f(H_m + h_{m+1,m} y e_m^T) e_1.
+    Returns (y, Hhat, c, R)."""
+    mu = H.shape[1]
+    S, R = np.linalg.qr(SV[:, :mu])
+    y = scipy.linalg.solve_triangular(R, S.T @ SV[:, mu], lower=False)
+    Hhat = last_column_update(H, y)
+    c = matfun.f_e1(Hhat, f, t, coef)
+    return y, Hhat, c, R
 
 
 def sketched_ls(A, b, m: int, k: int, f: int, sketch, t: float = 1.0, coef=None,
@@ -406,13 +425,11 @@ def sketched_fast(A, b, m: int, k: int, f: int, sketch, t: float = 1.0, coef=Non
         return Result(np.zeros_like(b, dtype=np.float64), 0, np.zeros(0), basis=B)
     Vm = B.V[:, :mu]
     SVfull = sketch.apply(B.V[:, : mu + 1])
+    if form == "sketch_solve":
+        y, Hhat, c, R = sketch_solve_stage(B.H[: mu + 1, :mu], SVfull, f, t, coef)
+        return Result(B.beta * (Vm @ c), mu, c, Hhat=Hhat, y=y, SV=SVfull, R=R, basis=B)
     SV = SVfull[:, :mu]
     S, R = np.linalg.qr(SV)
-    if form == "sketch_solve":
-        y = scipy.linalg.solve_triangular(R, S.T @ SVfull[:, mu], lower=False)
-        Hhat = _last_column_update(B, y)
-        c = matfun.f_e1(Hhat, f, t, coef)
-        return Result(B.beta * (Vm @ c), mu, c, Hhat=Hhat, y=y, SV=SVfull, R=R, basis=B)
     if sav == "direct":
         SAV = sketch.apply(np.column_stack([A @ Vm[:, j] for j in range(mu)]))
     else:

@@ -55,6 +55,7 @@ __global__ void k_state_reset(DevState* st, int m) {
   st->wh = 0;
   st->beta = 0.0;
   for (int i = 0; i < 16; ++i) st->scal[i] = 0.0;
+  st->kappa = 0.0;
 }
 
 cudaError_t launch_state_reset(DevState* st, int m, cudaStream_t s) {
@@ -1132,6 +1133,41 @@ cudaError_t launch_reduce_cols(const double* part, int ntiles, int nc, const dou
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------- FMA throughput probe
+// Eight independent chains x = fma(x, a, b) per thread, 16 rounds per loop trip, on
+// every SM: the FP64 (or FP32) pipe's fused multiply-add rate at the clocks the GPU
+// runs now. a and b arrive as arguments, so nothing folds; |a| < 1 keeps every chain
+// bounded (x tends to b / (1 - a)); the sum is stored only if it equals an impossible
+// value, which the compiler cannot prove false.
+__device__ double g_fma_sink;
+template <typename T>
+__global__ __launch_bounds__(kThreads) void k_fma_peak(int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = (T)(threadIdx.x * 8 + q) * (T)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = fma(x[q], a, b);
+    }
+  }
+  T t = (T)0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) t += x[q];
+  if (t == (T)-1.25) g_fma_sink = (double)t;
+}
+
+template <typename T>
+cudaError_t launch_fma_peak(int blocks_per_sm, int iters, cudaStream_t s, double* fmas) {
+  const int grid = sm_count() * blocks_per_sm;
+  k_fma_peak<T><<<grid, kThreads, 0, s>>>(iters, (T)0.999999, (T)1e-7);
+  if (fmas) *fmas = (double)grid * kThreads * (double)iters * 16.0 * 8.0;
+  return cudaGetLastError();
+}
+template cudaError_t launch_fma_peak<double>(int, int, cudaStream_t, double*);
+template cudaError_t launch_fma_peak<float>(int, int, cudaStream_t, double*);
+
 // -------------------------------------------------------------- combine
 // out[r] = keep * out[r] + sum_q coef[q] W_q[r]   (keep = 0 overwrites out)
 template <typename TV>
@@ -1263,6 +1299,7 @@ __global__ void k_init_wave(const BasisJob<TV>* __restrict__ jobs, Wave w) {
     st->iters = 0;
     st->beta = 0.0;
     for (int q = 0; q < 16; ++q) st->scal[q] = 0.0;
+    st->kappa = 0.0;
   }
   if (bid == 0 && threadIdx.x < 16) J->counter[threadIdx.x] = 0u;
   const int nh = J->ldh * m;

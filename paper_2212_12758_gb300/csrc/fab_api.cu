@@ -8,6 +8,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "fab_internal.cuh"
@@ -56,24 +58,24 @@ struct Pade13 {
 };
 
 
-int fault_countdown() {
-  // Host-side allocation fault injection for tests: FAB_FAULT=alloc:N makes the
-  // N-th workspace allocation of the process fail.
-  static int remaining = -2;
-  if (remaining == -2) {
-    remaining = -1;
-    const char* e = getenv("FAB_FAULT");
-    if (e && strncmp(e, "alloc:", 6) == 0) remaining = atoi(e + 6);
-  }
-  return remaining;
-}
-
+// Host-side allocation fault injection for tests: FAB_FAULT=alloc:N makes the N-th
+// workspace allocation counted from the moment the variable took its current value
+// fail (the variable is read at every allocation, so a test can re-arm it between
+// calls). The count is kept under a lock: server slot threads allocate concurrently.
+std::mutex g_fault_mu;
 bool fault_hit() {
-  int r = fault_countdown();
-  if (r < 0) return false;
-  static int count = 0;
-  ++count;
-  return count == r;
+  std::lock_guard<std::mutex> lock(g_fault_mu);
+  static std::string seen;  // the FAB_FAULT value the count belongs to
+  static int target = -1, count = 0;
+  const char* e = getenv("FAB_FAULT");
+  const std::string now = e ? e : "";
+  if (now != seen) {
+    seen = now;
+    count = 0;
+    target = now.compare(0, 6, "alloc:") == 0 ? atoi(now.c_str() + 6) : -1;
+  }
+  if (target < 1) return false;
+  return ++count == target;
 }
 
 // ------------------------------------------------------------ profiling
@@ -451,7 +453,19 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
     auto& q = need[i];
     if (q.bytes == 0 && (q.b == &h->u || q.b == &h->xbuf || q.b == &h->whm)) continue;  // allocated on demand
     const bool grow = q.b->bytes < (q.bytes ? q.bytes : 16);
-    if (grow && fault_hit()) return FAB_ENOMEM;
+    if (grow) {
+      // a regrown buffer starts uninitialized (and a failed growth leaves none):
+      // the contents cached with the handle are drawn again
+      if (q.b == &h->P) h->P_npad = -1;
+      if (q.b == &h->spat) h->spat_n = -1;
+      if (q.b == &h->G) h->G_n = -1;
+      if (fault_hit()) {  // as a cudaMalloc that fails after ensure() freed the old buffer
+        cudaFree(q.b->p);
+        q.b->p = nullptr;
+        q.b->bytes = 0;
+        return FAB_ENOMEM;
+      }
+    }
     if (!ensure(*q.b, q.bytes)) return FAB_ENOMEM;
     if (grow && q.b == &h->counter) CK(cudaMemset(h->counter.p, 0, h->counter.bytes));
   }
@@ -825,6 +839,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     CK(cudaMemcpyAsync(ws.qr + (size_t)fresh * p->s, ws.SV + (size_t)fresh * p->s,
                        (size_t)p->s * (mu + 1 - fresh) * sizeof(double), cudaMemcpyDeviceToDevice, s));
     LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 1, ws.tau, ws.st, s, q0, fresh));
+    LK(PK_SMALL, launch_kappa_diag(ws.qr, p->s, mdev, m, ws.st, s));
     qr_cols = mu;
     LK(PK_SMALL, launch_trsv(ws.qr, p->s, mdev, ws.qr + (size_t)mu * p->s, ws.y, 0, nullptr, s, m));
     yptr = ws.y;
@@ -837,6 +852,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
       CK(cudaMemcpyAsync(ws.qr + (size_t)q0 * p->s, ws.SV + (size_t)q0 * p->s, (size_t)p->s * (mu - q0) * sizeof(double),
                          cudaMemcpyDeviceToDevice, s));
       LK(PK_SMALL, launch_qr(ws.qr, p->s, p->s, mdev, m, 0, ws.tau, ws.st, s, q0, q0));
+      LK(PK_SMALL, launch_kappa_diag(ws.qr, p->s, mdev, m, ws.st, s));
       qr_cols = mu;
     } else if (wh > 0) {
       // Alg. 3 on the whitened basis: LSQR on the stored columns with the implicit
@@ -889,7 +905,21 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     LK(PK_SMALL, launch_build_hhat(ws.H, ldh, mdev, yptr, 1.0, ws.mats[0], m, m, s));
     rc = sqrtm_e1(ws, m, mdev, ws.cvec, p->f == FAB_F_SQRT, &fh_iters, s);
   }
-  if (rc != FAB_OK) return rc;
+  if (rc != FAB_OK) {  // no x; the diagnostics say how far the solve got
+    if (stats) {
+      memset(stats, 0, sizeof(*stats));
+      stats->m_used = mu;
+      stats->lsqr_iters = lsqr_iters;
+      stats->fh_iters = fh_iters;
+      stats->launches = g_launches;
+      stats->beta = hs.beta;
+      if (cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+          wait_stream(s) == cudaSuccess)
+        stats->kappa_est = hs.kappa;
+      cudaGetLastError();
+    }
+    return rc;
+  }
   if (!grow || mu < m) break;  // fixed m, or an invariant subspace: nothing to gain
   if (m_prev > 0) {  // sketched relative change of the solution since the previous m
     LK(PK_SMALL, launch_sketch_change(ws.SV, p->s, mdev, ws.cvec, m_prev, ws.cvec + (mcap + 1), ws.scal + 12, s));
@@ -934,6 +964,7 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     stats->whiten_at = wh;
     stats->launches = g_launches;
     stats->beta = hs.beta;
+    stats->kappa_est = hs.kappa;
     double hl = 0.0;
     if (mu == m) CK(cudaMemcpy(&hl, ws.H + m + (size_t)ldh * (m - 1), sizeof(double), cudaMemcpyDeviceToHost));
     stats->h_last = hl;
@@ -1004,6 +1035,9 @@ int build_square(fab_handle* h) {
 extern "C" int fab_apply(fab_handle* h, const fab_params* p, const double* b, double* x, int bx_on_device,
                          fab_stats* stats) try {
   if (!h || !p || !b || !x) return FAB_EINVAL;
+  // The inspectable state (fab_last_state / fab_last_basis) describes the last
+  // successful solve only: any later call may regrow or overwrite its buffers.
+  h->has_state = 0;
   int rc = validate(h, p);
   if (rc != FAB_OK) return rc;
   if (p->f == FAB_F_SIGN) {  // sign(A) b = (A^2)^{-1/2} (A b)
@@ -1216,6 +1250,49 @@ extern "C" int fab_profile_query(const char* name, double* total_ms, int64_t* la
     }
   }
   return FAB_EINVAL;
+}
+
+extern "C" int fab_fma_peak(int precision, double* gflops, double* ms, void* stream) try {
+  if (!gflops || (precision != FAB_FP64 && precision != FAB_MIXED)) return FAB_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return FAB_ECUDA;
+  }
+  auto run = [&](int iters, double* fmas, float* t) -> bool {
+    if (cudaEventRecord(e0, s) != cudaSuccess) return false;
+    const cudaError_t e = precision == FAB_FP64 ? launch_fma_peak<double>(4, iters, s, fmas)
+                                                : launch_fma_peak<float>(4, iters, s, fmas);
+    return e == cudaSuccess && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(t, e0, e1) == cudaSuccess;
+  };
+  // calibrate on a short launch, then time one of at least 50 ms (after a warm-up of the same length)
+  double fmas = 0.0;
+  float t = 0.f;
+  int iters = 64;
+  bool ok = run(iters, &fmas, &t);
+  while (ok && t < 5.f && iters < (1 << 24)) {
+    iters *= 4;
+    ok = run(iters, &fmas, &t);
+  }
+  if (ok) {
+    const double want = 50.0 / (t > 1e-3f ? t : 1e-3f);
+    iters = (int)std::min<double>((double)(1 << 26), ceil(iters * want));
+    ok = run(iters, &fmas, &t) && run(iters, &fmas, &t);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok || !(t > 0.f)) {
+    cudaGetLastError();
+    return FAB_ECUDA;
+  }
+  *gflops = 2.0 * fmas / ((double)t * 1e6);
+  if (ms) *ms = t;
+  return FAB_OK;
+} catch (...) {
+  return fab::abi_error_code();
 }
 
 extern "C" int fab_set_tiling(fab_handle* h, int rows_max, int nnz_cap, int staged) try {

@@ -35,6 +35,7 @@ struct DevState {
   int wh;        // basis columns when it was whitened (FAB_WHITEN), 0: not whitened
   double beta;   // ||b||_2
   double scal[16];  // scalars of the small-stage loops (LSQR recurrence, DB scaling)
+  double kappa;  // max |r_ii| / min |r_ii| of the sketch QR (0: no sketch QR in this solve)
 };
 
 // Sketch description passed by value to the basis kernels.
@@ -480,6 +481,10 @@ cudaError_t launch_to_f32(int n, const double* x, float* y, cudaStream_t s);
 cudaError_t launch_csr_spmv(int n, const int* rowptr, const int* colind, const double* vals, const double* x,
                             double* y, cudaStream_t s);
 
+// FMA throughput probe (T = double or float): blocks_per_sm x sm_count() blocks of
+// kThreads threads, each thread 128 iters FMAs; *fmas receives the total.
+template <typename T>
+cudaError_t launch_fma_peak(int blocks_per_sm, int iters, cudaStream_t s, double* fmas);
 int sm_count();              // multiprocessors of the current device
 int grid_rows(int n);        // grid for the thread-per-row kernels
 // Raises (never lowers) kernel fn's dynamic shared-memory limit to at least `bytes`; thread-safe.

@@ -16,6 +16,10 @@ constexpr size_t kStateBytes = 256;                         // DevState, padded
 constexpr size_t kPBytes = (size_t)fab::kMaxS * sizeof(int);  // SRHT sampled rows
 constexpr size_t kPartDoubles = (size_t)1 << 20;            // chunk partials: 8 MiB
 constexpr size_t kScratchBytes = kStateBytes + kPBytes + kPartDoubles * sizeof(double);
+// The status word sits in the first kStateBytes; the row sample and the partials
+// follow it and must neither overlap it nor lose the 256-byte alignment.
+static_assert(sizeof(fab::DevState) <= kStateBytes, "DevState outgrew its slot in the fixed scratch");
+static_assert(kStateBytes % 256 == 0 && kPBytes % 256 == 0, "scratch pieces keep 256-byte alignment");
 
 // Shared by every call on a device; kept until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];

@@ -1741,6 +1741,44 @@ cudaError_t launch_qr(double* A, int lda, int rows, const int* mdev, int max_col
   return launch_householder_qr(A, lda, rows, mdev, extra, tau, s);
 }
 
+// Condition estimate of the sketched basis (paper §2.1.2: kappa(Theta V_m) tracks
+// kappa(V_m) within the embedding's distortion): max_i |r_ii| / min_i |r_ii| over the
+// first min(m_used, ncols) columns of R in the upper triangle of the QR buffer. It is
+// a lower bound on kappa_2(R) = kappa_2(Theta V_m) (each |r_ii| lies between the
+// smallest and the largest singular value of R). Infinite if some r_ii is zero.
+__global__ void k_kappa_diag(const double* __restrict__ R, int lda, const int* __restrict__ mdev, int ncols,
+                             DevState* st) {
+  __shared__ double s_mx[32], s_mn[32];
+  const int nc = min(*mdev, ncols);
+  double mx = 0.0, mn = INFINITY;
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    const double d = fabs(R[i + (size_t)i * lda]);
+    mx = fmax(mx, d);
+    mn = fmin(mn, d);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_mx[threadIdx.x >> 5] = mx;
+    s_mn[threadIdx.x >> 5] = mn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      mx = fmax(mx, s_mx[w]);
+      mn = fmin(mn, s_mn[w]);
+    }
+    st->kappa = nc < 1 ? 0.0 : (mn > 0.0 ? mx / mn : INFINITY);
+  }
+}
+
+cudaError_t launch_kappa_diag(const double* R, int lda, const int* mdev, int ncols, DevState* st, cudaStream_t s) {
+  k_kappa_diag<<<1, 256, 0, s>>>(R, lda, mdev, ncols, st);
+  return cudaGetLastError();
+}
+
 // Blocked LU with partial pivoting over a cluster of CL CTAs (ties to the smallest
 // row; rows swapped across the whole matrix, as k_lu_cluster; piv[k] = row swapped
 // with k; log|det| to *logdet). Panels of kLuB columns are owned cyclically (panel P

@@ -25,6 +25,9 @@ cudaError_t launch_householder_qr(double* A, int lda, int rows, const int* mdev,
 cudaError_t launch_qr(double* A, int lda, int rows, const int* mdev, int max_cols, int extra, double* tau,
                       DevState* st, cudaStream_t s, int start = 0, int fresh = 0);
 bool qr_cluster_fits(int rows, int ncols);
+// st->kappa = max |r_ii| / min |r_ii| over the first min(*mdev, ncols) columns of the
+// factored QR buffer (a lower bound on kappa_2 of the factored matrix).
+cudaError_t launch_kappa_diag(const double* R, int lda, const int* mdev, int ncols, DevState* st, cudaStream_t s);
 cudaError_t launch_lu_fast(double* M, int ld, const int* mdev, int max_m, int* piv, double* logdet, DevState* st,
                            cudaStream_t s);
 // mmax: largest *mdev (R's triangle is staged in shared memory when mmax <= 150; 0: never)

@@ -28,7 +28,7 @@ SYMBOLS = ("fab_params_default", "fab_strerror", "fab_last_error", "fab_create",
            "fab_last_basis", "fab_sketch_apply", "fab_sketch_apply_noalloc", "fab_profile_enable",
            "fab_profile_only", "fab_profile_query", "fab_server_create", "fab_server_submit", "fab_server_poll", "fab_server_stats_get",
            "fab_server_destroy", "fab_batch_create", "fab_batch_exec", "fab_batch_input", "fab_batch_output",
-           "fab_batch_kernels", "fab_batch_destroy", "fab_batch_run", "fab_set_tiling", "fab_tune")
+           "fab_batch_kernels", "fab_batch_destroy", "fab_batch_run", "fab_set_tiling", "fab_tune", "fab_fma_peak")
 PROFILE_KINDS = ("spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine")
 
 
@@ -44,7 +44,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("m_used", ctypes.c_int), ("lsqr_iters", ctypes.c_int), ("fh_iters", ctypes.c_int),
                 ("launches", ctypes.c_int), ("h_last", ctypes.c_double), ("beta", ctypes.c_double),
                 ("ms_basis", ctypes.c_double), ("ms_small", ctypes.c_double), ("ms_combine", ctypes.c_double),
-                ("ms_total", ctypes.c_double), ("err_est", ctypes.c_double), ("whiten_at", ctypes.c_int)]
+                ("ms_total", ctypes.c_double), ("err_est", ctypes.c_double), ("whiten_at", ctypes.c_int),
+                ("kappa_est", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -104,6 +105,8 @@ lib.fab_set_tiling.argtypes = [_vp, _i32, _i32, _i32]
 lib.fab_set_tiling.restype = _i32
 lib.fab_tune.argtypes = [_vp, _i32, _i32, _vp, _vp]
 lib.fab_tune.restype = _i32
+lib.fab_fma_peak.argtypes = [_i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp]
+lib.fab_fma_peak.restype = _i32
 lib.fab_profile_enable.argtypes = [_i32]
 lib.fab_profile_enable.restype = _i32
 lib.fab_profile_only.argtypes = [ctypes.c_char_p]
@@ -248,6 +251,14 @@ def sketch_apply(V, s: int, sketch: int = SPARSE_SIGN, zeta: int = 8, seed: int 
     _check(lib.fab_sketch_apply(int(sketch), int(n), int(s), int(zeta), int(seed), V.data_ptr(), int(n), int(ncols),
                                 out.data_ptr(), stream), "fab_sketch_apply")
     return out
+
+
+def fma_peak(precision: int = FP64, stream=None):
+    """Measured FMA throughput (GFLOP/s, ms of the timed launch) of the current GPU:
+    FP64 for FP64, FP32 for MIXED (fab_fma_peak)."""
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib.fab_fma_peak(int(precision), ctypes.byref(g), ctypes.byref(ms), stream), "fab_fma_peak")
+    return g.value, ms.value
 
 
 def profile_enable(on: bool = True):

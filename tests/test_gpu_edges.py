@@ -133,3 +133,68 @@ def test_largest_sketch_in_a_solve(fab, torch, m):
                  method=fab.SKETCHED_FAST)
     assert st.m_used == m
     assert _rel(x, ref.x) <= TOL
+
+
+def test_failed_growth_invalidates_the_last_state():
+    """A solve that fails while its workspace grows (FAB_FAULT=alloc:1 set after a
+    successful solve: the next growing buffer is freed and not reallocated, as when
+    cudaMalloc fails) leaves nothing to inspect: fab_last_state and fab_last_basis
+    return FAB_EINVAL instead of reading freed or stale buffers. With the fault
+    cleared the same solve succeeds and matches the oracle. The variable is re-read
+    at every allocation, so one child process runs all three phases."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import ctypes, os, numpy as np\n"
+        "from oracle import krylov, matfun\n"
+        "from oracle import sketch as osk\n"
+        "from paper_2212_12758_gb300 import fab, workloads as W\n"
+        "A = W.convdiff(2, 30); b = W.random_vector(A.n, 0)\n"
+        "M = fab.Matrix.from_csr(A)\n"
+        "p1 = fab.params(f=fab.EXP, t=-0.01, m=10, k=2, s=40, sketch=fab.SRHT, method=fab.SKETCHED_FAST)\n"
+        "x = M.apply(b, p1)\n"
+        "assert fab.lib.fab_last_state(M._h, None, None, None, None) == fab.FAB_OK\n"
+        "p2 = fab.params(f=fab.EXP, t=-0.01, m=60, k=2, s=240, sketch=fab.SRHT, method=fab.SKETCHED_FAST)\n"
+        "os.environ['FAB_FAULT'] = 'alloc:1'\n"
+        "rc = fab.lib.fab_apply(M._h, ctypes.byref(p2), b.ctypes.data, x.ctypes.data, 0, None)\n"
+        "assert rc == fab.FAB_ENOMEM, rc\n"
+        "V = np.zeros((61, A.n))\n"
+        "assert fab.lib.fab_last_state(M._h, None, None, None, None) == fab.FAB_EINVAL\n"
+        "assert fab.lib.fab_last_basis(M._h, V.ctypes.data, 0) == fab.FAB_EINVAL\n"
+        "os.environ['FAB_FAULT'] = ''\n"
+        "x2 = M.apply(b, p2)\n"
+        "th = osk.make(osk.SRHT, A.n, 240, 1, 8)\n"
+        "ref = krylov.run(krylov.SKETCHED_FAST, W.to_scipy(A), b, 60, 2, matfun.EXP, th, -0.01).x\n"
+        "err = np.linalg.norm(x2 - ref) / np.linalg.norm(ref)\n"
+        "assert err <= 1e-10, err\n"
+        "print('ok')\n")
+    env = dict(os.environ)
+    env.pop("FAB_FAULT", None)
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("method", ["SKETCHED_FAST", "SKETCHED_LS"])
+def test_kappa_estimate_of_the_sketched_basis(fab, torch, method):
+    """fab_stats.kappa_est is max|r_ii| / min|r_ii| of the QR of Theta V_m. The |r_ii|
+    of a Householder QR are unique (|r_ii| = dist(column i, span of the columns
+    before it)), so the oracle's QR of its own sketched basis gives the same value
+    up to the basis's rounding; it lower-bounds the oracle's exact kappa_2."""
+    A = W.convdiff(2, 60)
+    b = W.random_vector(A.n, 0)
+    m, s = 30, 120
+    x, st = _run(fab, torch, A, b, f=fab.EXP, t=-0.005, m=m, k=2, s=s, sketch=fab.SRHT, seed=1,
+                 method=getattr(fab, method), lsqr_tol=1e-12)
+    th = osk.make(osk.SRHT, A.n, s, 1, 8)
+    r = krylov.run(getattr(krylov, method), W.to_scipy(A), b, m, 2, matfun.EXP, th, -0.005, tol=1e-12)
+    d = np.abs(np.diag(np.linalg.qr(r.SV[:, :m], mode="r")))
+    kap = d.max() / d.min()
+    assert kap > 1.0
+    assert abs(st.kappa_est - kap) <= 1e-6 * kap, (st.kappa_est, kap)
+    sv = np.linalg.svd(r.SV[:, :m], compute_uv=False)
+    assert st.kappa_est <= sv[0] / sv[-1] * (1 + 1e-6)
+    _, st0 = _run(fab, torch, A, b, f=fab.EXP, t=-0.005, m=m, k=2, method=fab.NOPROJ)
+    assert st0.kappa_est == 0.0

@@ -155,3 +155,17 @@ def test_gaussian_moments():
     G = sketch.gaussian_entries(40, 2000, 3, bf16=False)
     assert abs(G.mean()) < 0.01 / math.sqrt(40) * 5
     assert abs(G.var() * 40 - 1.0) < 0.03
+
+
+def test_gaussian_subspace_embedding():
+    """Theta = G with N(0, 1/s) entries (BF16-rounded) embeds a d-dimensional subspace:
+    the singular values of G Q (Q orthonormal, n x d) lie in
+    [1 - sqrt(d/s) - t, 1 + sqrt(d/s) + t] with probability >= 1 - 2 exp(-s t^2 / 2)
+    (Davidson and Szarek's bound for Gaussian matrices). A wrong scale (say 1/sqrt(n)
+    for 1/sqrt(s)) or correlated entries (a rank-deficient G) fall outside."""
+    n = 4096
+    for d, s, t in ((25, 100, 0.2), (8, 512, 0.1)):
+        Q = np.linalg.qr(np.random.default_rng(3).standard_normal((n, d)))[0]
+        sv = np.linalg.svd(sketch.Gaussian(n, s, 7).apply(Q), compute_uv=False)
+        r = math.sqrt(d / s)
+        assert sv.min() > 1 - r - t and sv.max() < 1 + r + t, (d, s, sv.min(), sv.max())
