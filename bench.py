@@ -65,6 +65,31 @@ CPU_SAMPLE_STEPS = 16
 SPMV_DRAM_BYTES_PER_ROW = 262_368_512 / 2_097_152
 
 
+def oracle_golden_error(x_dev, coeffs):
+    """The solve against the FP64 oracle's solve of the same workload, stored by
+    tests/golden/make_c2_reference.py: relative 2-norm error on the 1024 stored rows of
+    x and on the coefficient vector c (x = ||b|| V_m c)."""
+    path = os.path.join(ROOT, "tests", "golden", "c2_sketched_fast.txt")
+    if not os.path.exists(path):
+        return None
+    rows, vals, gc = [], [], None
+    for line in open(path):
+        if line.startswith("x "):
+            _, i, v = line.split()
+            rows.append(int(i))
+            vals.append(float(v))
+        elif line.startswith("coeffs "):
+            gc = np.array([float(v) for v in line.split()[1:]])
+    import torch
+
+    xs = x_dev[torch.tensor(rows, device=x_dev.device)].cpu().numpy()
+    vals = np.array(vals)
+    return {"x_sampled_rows": float(np.linalg.norm(xs - vals) / np.linalg.norm(vals)),
+            "coeffs": float(np.linalg.norm(coeffs - gc) / np.linalg.norm(gc)) if gc is not None else None,
+            "reference": "FP64 oracle sketched_fast on the same inputs (tests/golden/c2_sketched_fast.txt: "
+                         f"{len(rows)} sampled rows of x and the m coefficients)"}
+
+
 def bench_config(grid: int, n: int, nnz: int, world: int) -> dict:
     """The workload description both arms print (the same dict in both lines)."""
     return {"workload": workload_name(grid, n, nnz), "n": n, "nnz": nnz, "m": M, "k": K_WIN, "s": S_ROWS,
@@ -169,17 +194,25 @@ def bench_mixed_same(fab, torch, Mx, bd, ref_x, stream, n: int, nnz: int, P, rep
     ms = e0.elapsed_time(e1) / reps
     peak = float(_peaks().get("hbm_gbs", 6800.0))
     kw = K_WIN
+    nch = (n + 4095) // 4096
     sp_bytes = 8 * nnz + 4 * (n + 1) + 4 * n * kw + 4 * n
-    up_bytes = 4 * n * (kw + 2) + 8 * S_ROWS * ((n + 4095) // 4096)
+    up_bytes = 4 * n * (kw + 2) + 8 * S_ROWS * nch
+    # one-pass step (steady state): A, row pointers, the previous SpMV output and the k
+    # update-window columns read once, the updated column and the new SpMV output
+    # written, the sketch partials (at most one s-vector per block, counted per chunk)
+    fu_bytes = 8 * nnz + 4 * (n + 1) + 4 * n * (kw + 1) + 8 * n + 8 * S_ROWS * nch
     out = {"solves_per_s": 1000.0 / ms, "ms_per_solve": ms,
            "rel_err_vs_fp64_arnoldi_m150": float(torch.linalg.norm(x - ref_x) / torch.linalg.norm(ref_x))
            if ref_x is not None else None}
-    for name, byts in (("spmv_dots", sp_bytes), ("update", up_bytes)):
+    for name, byts in (("spmv_dots", sp_bytes), ("update", up_bytes), ("fused_step", fu_bytes)):
         t_ms, cnt = prof[name]
-        sec = t_ms / max(cnt, 1) / 1000.0
-        out[name] = {"ms_per_launch": sec * 1000.0, "algorithmic_bytes_per_launch": byts,
+        if cnt == 0:
+            continue
+        sec = t_ms / cnt / 1000.0
+        out[name] = {"ms_per_launch": sec * 1000.0, "launches_per_solve": cnt / reps,
+                     "algorithmic_bytes_per_launch": byts,
                      "hbm_gbs": byts / sec / 1e9, "hbm_frac_of_measured": byts / sec / 1e9 / peak}
-    basis_s = (prof["spmv_dots"][0] + prof["update"][0] + prof["sketch_reduce"][0]) / 1000.0 / reps
+    basis_s = sum(prof[k_][0] for k_ in ("spmv_dots", "update", "sketch_reduce", "fused_step")) / 1000.0 / reps
     out["basis_pass_hbm_frac_of_measured"] = M * (sp_bytes + up_bytes) / basis_s / 1e9 / peak
     # the same pass against the single-pass floor of one basis step with its fused sign
     # sketch, 8 nnz + 4 (n+1) + 4 n (k+1) bytes (A, row pointers, the k window columns,
@@ -403,7 +436,7 @@ def bench_mixed_graph(fab, torch, W, reps: int = 2, n: int = 4_000_000, referenc
         ms = e0.elapsed_time(e1) / reps
         g_ms = prof["sketch_reduce"][0] / max(prof["sketch_reduce"][1], 1)
         flops = 2.0 * s * A.n * (m + 1)
-        gbytes = 2.0 * s * A.n + 2.0 * A.n * (m + 1)
+        gbytes = 2.0 * s * A.n + 4.0 * A.n * (m + 1)  # G once, both BF16 terms of the basis once
         ref = {150: None, 300: None}
         for mr in ((150, 300) if references else ()):
             xr = torch.empty_like(b)
@@ -415,6 +448,7 @@ def bench_mixed_graph(fab, torch, W, reps: int = 2, n: int = 4_000_000, referenc
                      "gauss_tensor_frac_of_measured_bf16": flops / (g_ms / 1000.0) / 1e12
                      / float(peaks.get("bf16_tflops", 1900.0)),
                      "gauss_hbm_gbs_algorithmic": gbytes / (g_ms / 1000.0) / 1e9,
+                     "gauss_hbm_frac_of_measured": gbytes / (g_ms / 1000.0) / 1e9 / float(peaks.get("hbm_gbs", 6800.0)),
                      "kernels_ms": {k_: v[0] / reps for k_, v in prof.items()}}
     return out
 
@@ -642,6 +676,7 @@ def run_only(args):
     if args.only == "mixed":
         A = W.convdiff(3, args.grid)
         Mx = fab.Matrix.from_csr(A)
+        Mx.set_fusion(args.fusion)
         stream = torch.cuda.current_stream()
         bd = torch.from_numpy(W.random_vector(A.n, SEED_B)).cuda()
 
@@ -684,6 +719,9 @@ def main():
     ap.add_argument("--only", choices=["mixed", "batch", "graph", "bg", "skew", "whiten", "serving"], default=None,
                     help="measure one side workload alone and print its JSON (for profiler runs)")
     ap.add_argument("--serving-slots", type=int, default=16, help="server slots of the --only serving workload")
+    ap.add_argument("--fusion", action="store_true",
+                    help="--only mixed: the one-pass basis steps (fab_set_fusion) in place of the two-pass loop "
+                         "(SpMV + dots, then update + sketch)")
     ap.add_argument("--graph-n", type=int, default=4_000_000,
                     help="nodes of the --only graph workload (smaller only for profiler captures)")
     ap.add_argument("--batch-count", type=int, default=256,
@@ -738,7 +776,7 @@ def main():
     prof_warm = fab.profile_query()
     fab.profile_enable(False)
     launches_per_solve = st.launches
-    dom = max(("spmv_dots", "update"), key=lambda k_: prof_warm[k_][0])
+    dom = max(("spmv_dots", "update", "fused_step"), key=lambda k_: prof_warm[k_][0])
 
     # FP64 FMA rate of this GPU at its current clocks (the arithmetic roof of the FP64
     # basis kernels), measured live with its own clock samples
@@ -826,6 +864,7 @@ def main():
 
     # ------------------------------------------------------- accuracy (untimed)
     x_fast = xd.clone()
+    vs_oracle = oracle_golden_error(x_fast, Mx.last_state().coeffs) if args.grid == N_GRID else None
     extras = {}
     ref_x = None
     if not args.no_extras:
@@ -893,7 +932,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": bench_config(args.grid, n, nnz, ws),
-                "hbm_gbs": hbm_gbs_solve, "rel_err": rel_err,
+                "hbm_gbs": hbm_gbs_solve, "rel_err": rel_err, "rel_err_vs_oracle": vs_oracle,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                 "roofline": roof, "basis_pass": basis_pass, "kernels": kernel_share, "gpu_launches": launches_per_solve * args.steps,
                 "e2e": e2e, "clocks": clk, "cpu_baseline": cpu, **extras}

@@ -307,6 +307,30 @@ void fab_server_destroy(fab_server* srv);
  * Neither may run while a solve, batch or server request uses h.
  */
 int fab_set_tiling(fab_handle* h, int rows_max, int nnz_cap, int staged);
+/*
+ * fab_set_fusion - one-pass basis steps of the FP32 basis (FAB_MIXED; Alg. 2 with a
+ * sign sketch or none: FAB_SKETCHED_FAST, FAB_SKETCHED_LS, FAB_NOPROJ). A pass updates,
+ * normalizes and sketches column c-1 (the window update of Alg. 2) and multiplies it by
+ * A with the window dots of step c, so each basis step reads A and the window once;
+ * values of column c-1 outside a block's 4096-row chunk are recomputed from the
+ * previous SpMV output and the window by the same FMAs their owner runs. Used only
+ * when every row of A has at most 8 nonzeros. on = 1 allows it; 0 (the default) keeps
+ * the two-pass loop (SpMV + dots, then update + norm + sketch), which is faster on
+ * GB300 (the one-pass form moves fewer bytes but hides less latency). The two forms
+ * differ only in the grouping of the FP32 partial sums of the dot products and norms.
+ * FAB_EINVAL for a NULL handle. Not while a solve, batch or server request uses h.
+ */
+int fab_set_fusion(fab_handle* h, int on);
+/*
+ * fab_inject_wait_timeout - failure-detection hook for tests (not part of the paper).
+ * In the next solve on h that runs the one-pass steps (fab_set_fusion), the SpMV tasks
+ * of basis step `pass` (1 <= pass <= m) wait for a chunk flag value that no task sets
+ * and give up after `polls` polls of it (each about a microsecond): the kernel records
+ * FAB_ETIMEOUT and returns, no copy is in flight and nothing faults, and fab_apply
+ * returns FAB_ETIMEOUT. The hook is one-shot; later solves on h run normally.
+ * pass = 0 disarms it. FAB_EINVAL for a NULL handle, pass < 0, or polls < 1.
+ */
+int fab_inject_wait_timeout(fab_handle* h, int pass, int polls);
 int fab_tune(fab_handle* h, int precision, int k, int* choice, void* stream);
 
 /*
@@ -370,6 +394,8 @@ int fab_batch_run(fab_handle* const* hs, const fab_params* ps, const double* con
  *   "gemv_t"         V^T w passes (Arnoldi, LSQR)
  *   "small"          QR / LSQR scalar steps / f(H) kernels
  *   "combine"        x = ||b|| V_m c and the LSQR vector update
+ *   "fused_step"     one-pass basis step of the FP32 basis (window update, norm and
+ *                    sketch of column c-1 with the SpMV and window dots of step c)
  * fab_profile_only(name) restricts the recording to that class (NULL or ""
  * restores every class): each event pair adds a little device time between
  * launches, so a throughput measurement brackets only the kernel it needs.

@@ -180,6 +180,14 @@ def round_bf16(x: np.ndarray) -> np.ndarray:
     return np.where(x == 0, x, out)
 
 
+def split_bf16(x: np.ndarray):
+    """x as a sum of two bfloat16 numbers: hi = round_bf16(x), lo = round_bf16(x - hi)
+    (x - hi is exact in FP64). hi + lo is x to 2^-16 relative, hi alone to 2^-8."""
+    x = np.asarray(x, dtype=np.float64)
+    hi = round_bf16(x)
+    return hi, round_bf16(x - hi)
+
+
 def gaussian_entries(s: int, n: int, seed: int, rows=None, bf16: bool = True) -> np.ndarray:
     """Rows `rows` (default all) of the Gaussian sketch, as FP64 values."""
     rows = np.arange(s) if rows is None else np.asarray(rows)

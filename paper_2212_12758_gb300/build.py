@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libfab.so")
-SOURCES = ["basis.cu", "small.cu", "fab_api.cu", "noalloc.cu", "gauss.cu", "server.cu", "batch.cu"]
+SOURCES = ["basis.cu", "fused.cu", "small.cu", "fab_api.cu", "noalloc.cu", "gauss.cu", "server.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=default",
          "--expt-relaxed-constexpr"]

@@ -79,8 +79,8 @@ bool fault_hit() {
 }
 
 // ------------------------------------------------------------ profiling
-enum ProfKind { PK_SPMV = 0, PK_UPDATE, PK_SKRED, PK_GEMVT, PK_SMALL, PK_COMBINE, PK_COUNT };
-const char* kProfNames[PK_COUNT] = {"spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine"};
+enum ProfKind { PK_SPMV = 0, PK_UPDATE, PK_SKRED, PK_GEMVT, PK_SMALL, PK_COMBINE, PK_FUSED, PK_COUNT };
+const char* kProfNames[PK_COUNT] = {"spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine", "fused_step"};
 
 struct Profiler {
   bool on = false;
@@ -214,6 +214,19 @@ int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr, 
   }
   h->h_rowptr = new int[n + 1];
   memcpy(h->h_rowptr, rp32.data(), (n + 1) * sizeof(int));
+  for (int64_t i = 0; i < n; ++i) h->max_row_nnz = std::max(h->max_row_nnz, rp32[i + 1] - rp32[i]);
+  if (h->max_row_nnz >= 1 && h->max_row_nnz <= 8) {  // the one-pass steps' plan
+    std::vector<int> tasks;
+    std::vector<int2> crange;
+    fab::fused_plan((int)n, rp32.data(), ci.data(), fab::sm_count() * 3 / 2, tasks, crange);
+    if (cudaMalloc(&h->d_ftasks, tasks.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&h->d_fcrange, crange.size() * sizeof(int2)) != cudaSuccess ||
+        cudaMemcpy(h->d_ftasks, tasks.data(), tasks.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_fcrange, crange.data(), crange.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      return FAB_ENOMEM;
+    }
+  }
   const int rc = fab::build_tiles(h, 256, kSpmvCap, 1);
   if (rc != FAB_OK) return rc;
   owner.h = nullptr;
@@ -231,11 +244,15 @@ void fab_destroy(fab_handle* h) {
     cudaFree(h->d_vals);
     cudaFree(h->d_vals32);
     cudaFree(h->d_tiles);
+    cudaFree(h->d_ftasks);
+    cudaFree(h->d_fcrange);
+    cudaFree(h->d_ell_col);
+    cudaFree(h->d_ell_val);
     delete[] h->h_rowptr;
   }
   Buf* bufs[] = {&h->spat, &h->W32, &h->Wbf, &h->G, &h->shf, &h->scl, &h->W,     &h->H,   &h->sigma, &h->coef, &h->part, &h->counter, &h->gpart,
                  &h->skpart, &h->SV, &h->P,     &h->qr,  &h->tau,  &h->y,    &h->cvec,    &h->dense,
-                 &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state, &h->whm};
+                 &h->piv,   &h->scal, &h->lsq,  &h->u,   &h->xbuf, &h->state, &h->whm, &h->wbuf, &h->fflags};
   for (Buf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -359,7 +376,8 @@ int m_cap(const fab_params* p) { return p->target_rel_err > 0.0 ? p->m_max : p->
 
 struct Ws {
   ColScale cs;
-  float* W32;
+  float *W32, *wbuf;
+  int* fflags;
   __nv_bfloat16 *Wbf, *G;
   double *W, *H, *sigma, *coef, *part, *gpart, *skpart, *SV, *qr, *tau, *y, *cvec, *scal, *u, *xbuf;
   double* mats[9];
@@ -401,6 +419,16 @@ bool defer_sketch_reduce(const fab_handle* h, const fab_params* p) {
   return bytes <= basis / 4;
 }
 
+// One-pass basis steps (fused.cu): the FP32 basis of Alg. 2 (sketched_fast, sketched_ls,
+// Alg. 5) with a sign sketch or none, rows of at most 8 nonzeros, and the handle's switch on.
+bool fused_steps(const fab_handle* h, const fab_params* p) {
+  if (p->precision != FAB_MIXED || !h->fuse || h->max_row_nnz > 8 || h->max_row_nnz < 1 || !h->d_ftasks)
+    return false;
+  if (p->method == FAB_NOPROJ) return true;
+  if (p->method != FAB_SKETCHED_FAST && p->method != FAB_SKETCHED_LS) return false;
+  return p->sketch == FAB_SK_SRHT || p->sketch == FAB_SK_SPARSE_SIGN;
+}
+
 // The workspace a solve needs (buffer, bytes), shared by allocation and admission.
 int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
   const int m = m_cap(p), s = sketched(p->method) ? p->s : 1;
@@ -412,8 +440,8 @@ int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
   const bool gauss = p->precision == FAB_MIXED && p->sketch == FAB_SK_GAUSSIAN && sketched(p->method);
   const Need need[] = {
       {p->precision == FAB_MIXED ? &h->W32 : &h->W, ld * (m + 1) * (p->precision == FAB_MIXED ? 4 : 8)},
-      {&h->Wbf, gauss ? ld * (m + 1) * 2 : 0},
-      {&h->G, gauss ? ld * (size_t)p->s * 2 : 0},
+      {&h->Wbf, gauss ? gauss_B_bytes(n, m + 1) : 0},  // hi and lo terms, K-blocked
+      {&h->G, gauss ? gauss_G_bytes(n, s) : 0},
       {&h->H, (size_t)(m + 1) * m * 8},
       {&h->sigma, (size_t)(m + 1) * 8},
       {&h->shf, (size_t)(m + 1) * 4},
@@ -438,6 +466,8 @@ int ws_needs(fab_handle* h, const fab_params* p, Need* out) {
       {&h->u, uses_lsqr(p->method) ? (size_t)n * 8 : 0},
       {&h->xbuf, (size_t)n * 8},
       {&h->whm, p->method == FAB_WHITEN ? (3 * (size_t)(m + 1) * (m + 1) + (m + 1) + 8) * 8 : 0},
+      {&h->wbuf, fused_steps(h, p) ? ld * 2 * 4 : 0},
+      {&h->fflags, fused_steps(h, p) ? (size_t)nchunks * 4 : 0},
   };
   const int cnt = (int)(sizeof(need) / sizeof(need[0]));
   for (int i = 0; i < cnt; ++i) out[i] = need[i];
@@ -451,7 +481,8 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
   const int m = m_cap(p);
   for (int i = 0; i < cnt; ++i) {
     auto& q = need[i];
-    if (q.bytes == 0 && (q.b == &h->u || q.b == &h->xbuf || q.b == &h->whm)) continue;  // allocated on demand
+    if (q.bytes == 0 && (q.b == &h->u || q.b == &h->xbuf || q.b == &h->whm || q.b == &h->wbuf || q.b == &h->fflags))
+      continue;  // allocated on demand
     const bool grow = q.b->bytes < (q.bytes ? q.bytes : 16);
     if (grow) {
       // a regrown buffer starts uninitialized (and a failed growth leaves none):
@@ -472,6 +503,8 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
   (void)n;
   ws.W = ptr<double>(h->W);
   ws.W32 = ptr<float>(h->W32);
+  ws.wbuf = ptr<float>(h->wbuf);
+  ws.fflags = ptr<int>(h->fflags);
   ws.Wbf = ptr<__nv_bfloat16>(h->Wbf);
   ws.G = ptr<__nv_bfloat16>(h->G);
   ws.H = ptr<double>(h->H);
@@ -666,9 +699,12 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
       sk_scale = 1.0 / sqrt((double)p->s);
     } else if (sk.kind == SK_GAUSS) {
       sk.Wbf = ws.Wbf;
-      sk.ldbf = ld;
+      sk.bf_cpad = gauss_cpad(mcap + 1);
+      // the copy's rows past n (the end of the last K block) enter the products: zero them
+      CK(cudaMemsetAsync(ws.Wbf + (size_t)(gauss_nkb(n) - 1) * 2 * sk.bf_cpad * 64, 0,
+                         (size_t)2 * sk.bf_cpad * 64 * sizeof(__nv_bfloat16), s));
       if (h->G_n != n || h->G_s != p->s || h->G_seed != p->seed) {  // G (BF16, s x n) cached per handle
-        LK(PK_SMALL, launch_gauss_generate(p->s, n, ld, rng_state(p->seed, 5), ws.G, s));
+        LK(PK_SMALL, launch_gauss_generate(p->s, n, rng_state(p->seed, 5), ws.G, s));
         h->G_n = n;
         h->G_s = p->s;
         h->G_seed = p->seed;
@@ -725,7 +761,54 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
   DevState& hs = *ws.hs;
   int mu = 0;
   int wh = 0;  // FAB_WHITEN: > 0 once the basis was whitened at wh columns
+  // one-pass basis steps: the FP32 Alg. 2 loop on a matrix with short rows
+  const bool fused = kMixed && fused_steps(h, p) && ws.wbuf && ws.fflags && h->d_ell_col &&
+                     (!sk_on || sk.kind == SK_SRHT || sk.kind == SK_SPARSE);
+  const FusePlan fplan{ws.fflags,   h->d_ftasks, h->d_fcrange,     h->d_ell_col,
+                       h->d_ell_val, h->ld,       h->max_row_nnz,    fused ? h->stall_pass : 0,
+                       h->stall_polls};
+  if (fused) h->stall_pass = 0;  // the hook is one-shot
+  if (fused) CK(cudaMemsetAsync(ws.fflags, 0, (size_t)((n + kChunk - 1) / kChunk) * sizeof(int), s));
   for (;;) {  // one pass per dimension m (a single pass unless m grows to a target)
+  if constexpr (kMixed) {
+    if (fused && c_done < m) {
+      // Pass c updates column c-1 (from the second pass of this run on) and multiplies
+      // it by A; the run's last column gets its update, norm and sketch from k_update.
+      const int c0 = c_done + 1;
+      float* wb[2] = {ws.wbuf, ws.wbuf + ld};
+      SketchDev& skf = sk_on ? sk : none;
+      for (int c = c0; c <= m; ++c) {
+        const bool upd = c > c0;
+        const int j0 = std::max(0, c - k), kw = c - j0;
+        const int j0u = std::max(0, c - 1 - k), kwu = upd ? (c - 1) - j0u : 0;
+        const float* wprev = upd ? wb[(c - 1) & 1] : W + (size_t)(c - 1) * ld;
+        float* wnext = c == m ? W + (size_t)c * ld : wb[c & 1];
+        if (defer) skf.part = ws.skpart + (size_t)(c - 1) * colstride;
+        LK(PK_FUSED, launch_fused_step(A, W, ld, c, upd ? 1 : 0, j0u, kwu, j0, kw, wprev, wnext, ws.cs, ws.H, ldh,
+                                       ws.coef, ws.part, ws.counter, skf, ws.st, fplan, s));
+        if (upd && sk_on) {
+          if (defer)
+            col_parts[c - 1] = skf.nparts;
+          else
+            LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, c - 1, sk_scale, ws.SV + (size_t)(c - 1) * p->s, ws.st, s));
+        }
+      }
+      const int j0 = std::max(0, m - k), kw = m - j0;
+      if (sk_on) {
+        if (defer) sk.part = ws.skpart + (size_t)m * colstride;
+        LK(PK_UPDATE, launch_update(n, W, ld, m, j0, kw, ws.coef, ws.H, ldh, ws.cs, 1, ws.part, ws.counter, sk,
+                                    ws.st, s));
+        if (defer)
+          col_parts[m] = sk.nparts;
+        else
+          LK(PK_SKRED, launch_sketch_reduce(sk, ws.sigma, m, sk_scale, ws.SV + (size_t)m * p->s, ws.st, s));
+      } else {
+        LK(PK_UPDATE, launch_update_plain(n, W, ld, m, j0, kw, ws.coef, ws.H, ldh, ws.cs, 1, ws.part, ws.counter,
+                                          ws.st, s));
+      }
+      c_done = m;
+    }
+  }
   for (int c = c_done + 1; c <= m; ++c) {
     if (p->method == FAB_BG_LS) {
       // Alg. 1: w = A v_{c-1}; p = Theta w; sketched Gram-Schmidt step; the same
@@ -799,7 +882,8 @@ int apply_impl(fab_handle* h, const fab_params* p, const double* b, double* x, i
     red_from = m + 1;
   }
   if (sk_on && sk.kind == SK_GAUSS)  // Theta V_{m+1} = G (BF16 basis) on the tensor cores, FP64 finish
-    LK(PK_SKRED, launch_gauss_sketch(ws.G, ws.Wbf, ld, n, p->s, m + 1, ws.sigma, ws.gpart, ws.SV, ws.st, s));
+    LK(PK_SKRED, launch_gauss_sketch(ws.G, ws.Wbf, gauss_cpad(mcap + 1), n, p->s, m + 1, ws.sigma, ws.gpart, ws.SV,
+                                     ws.st, s));
   CK(cudaEventRecord(ev[1], s));
   CK(cudaMemcpyAsync(&hs, ws.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(wait_stream(s));
@@ -1142,13 +1226,12 @@ extern "C" int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t
   if (ncols == 0) return FAB_OK;
   cudaStream_t st = (cudaStream_t)stream;
   if (sketch == FAB_SK_GAUSSIAN) {  // G and the BF16 columns in scratch, GEMM on the tensor cores
-    const int64_t ld = ((n + 31) / 32) * 32;
     __nv_bfloat16 *G = nullptr, *B = nullptr;
     double *part = nullptr, *ones = nullptr;
     DevState* ds = nullptr;
     int rc = FAB_OK;
-    if (cudaMallocAsync((void**)&G, (size_t)ld * s * 2, st) != cudaSuccess ||
-        cudaMallocAsync((void**)&B, (size_t)ld * ncols * 2, st) != cudaSuccess ||
+    if (cudaMallocAsync((void**)&G, gauss_G_bytes(n, s), st) != cudaSuccess ||
+        cudaMallocAsync((void**)&B, gauss_B_bytes(n, ncols), st) != cudaSuccess ||
         cudaMallocAsync((void**)&part, gauss_partial_bytes((int)n, s, ncols) + 16, st) != cudaSuccess ||
         cudaMallocAsync((void**)&ones, (size_t)ncols * 8, st) != cudaSuccess ||
         cudaMallocAsync((void**)&ds, sizeof(DevState), st) != cudaSuccess)
@@ -1156,9 +1239,10 @@ extern "C" int fab_sketch_apply(int sketch, int64_t n, int s, int zeta, uint64_t
     std::vector<double> h1((size_t)ncols, 1.0);
     if (rc == FAB_OK && (cudaMemcpyAsync(ones, h1.data(), (size_t)ncols * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
                          launch_state_reset(ds, 0, st) != cudaSuccess ||
-                         launch_gauss_generate(s, (int)n, ld, rng_state(seed, 5), G, st) != cudaSuccess ||
-                         launch_to_bf16((int)n, ncols, V_dev, ldv, B, ld, st) != cudaSuccess ||
-                         launch_gauss_sketch(G, B, ld, (int)n, s, ncols, ones, part, out_dev, ds, st) != cudaSuccess))
+                         launch_gauss_generate(s, (int)n, rng_state(seed, 5), G, st) != cudaSuccess ||
+                         launch_to_bf16((int)n, ncols, V_dev, ldv, B, st) != cudaSuccess ||
+                         launch_gauss_sketch(G, B, gauss_cpad(ncols), (int)n, s, ncols, ones, part, out_dev, ds, st) !=
+                             cudaSuccess))
       rc = FAB_ECUDA;
     DevState hs;
     if (rc == FAB_OK && cudaMemcpyAsync(&hs, ds, sizeof(DevState), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -1293,6 +1377,19 @@ extern "C" int fab_fma_peak(int precision, double* gflops, double* ms, void* str
   return FAB_OK;
 } catch (...) {
   return fab::abi_error_code();
+}
+
+extern "C" int fab_inject_wait_timeout(fab_handle* h, int pass, int polls) {
+  if (!h || pass < 0 || (pass > 0 && polls < 1)) return FAB_EINVAL;
+  h->stall_pass = pass;
+  h->stall_polls = polls;
+  return FAB_OK;
+}
+
+extern "C" int fab_set_fusion(fab_handle* h, int on) {
+  if (!h) return FAB_EINVAL;
+  h->fuse = on ? 1 : 0;
+  return FAB_OK;
 }
 
 extern "C" int fab_set_tiling(fab_handle* h, int rows_max, int nnz_cap, int staged) try {
@@ -1438,6 +1535,26 @@ int ensure_vals32(fab_handle* h, cudaStream_t s) {
     cudaGetLastError();
     return FAB_ECUDA;
   }
+  // the ELL form the one-pass steps read (rows of at most 8 nonzeros); without it the
+  // two-pass loop runs
+  if (h->d_ftasks && h->max_row_nnz >= 1 && h->max_row_nnz <= 8 && !h->d_ell_col) {
+    const size_t cnt = (size_t)h->max_row_nnz * (size_t)h->ld;
+    if (cudaMalloc(&h->d_ell_col, cnt * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&h->d_ell_val, cnt * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(h->d_ell_col);
+      cudaFree(h->d_ell_val);
+      h->d_ell_col = nullptr;
+      h->d_ell_val = nullptr;
+      return FAB_OK;
+    }
+    if (launch_build_ell(h->n, h->d_rowptr, h->d_colind, h->d_vals32, h->max_row_nnz, h->ld, h->d_ell_col,
+                         h->d_ell_val, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      return FAB_ECUDA;
+    }
+  }
   return FAB_OK;
 }
 
@@ -1458,6 +1575,7 @@ size_t handle_ws_bytes(const fab_handle* h) {
   size_t t = 0;
   for (const Buf* b : bufs) t += b->bytes;
   if (h->d_vals32) t += (size_t)(h->nnz + kCsrPad) * sizeof(float);
+  if (h->d_ell_col) t += (size_t)h->max_row_nnz * (size_t)h->ld * 8;
   return t;
 }
 
@@ -1515,6 +1633,12 @@ void point_to_matrix(fab_handle* c, const fab_handle* h) {
   c->tile_rows = h->tile_rows;
   c->tile_nnz = h->tile_nnz;
   c->tile_staged = h->tile_staged;
+  c->max_row_nnz = h->max_row_nnz;
+  c->fuse = h->fuse;
+  c->d_ftasks = h->d_ftasks;
+  c->d_fcrange = h->d_fcrange;
+  c->d_ell_col = h->d_ell_col;
+  c->d_ell_val = h->d_ell_val;
   c->h_rowptr = h->h_rowptr;
   c->n = h->n;
   c->nnz = h->nnz;

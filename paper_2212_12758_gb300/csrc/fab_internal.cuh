@@ -50,8 +50,9 @@ struct SketchDev {
   uint64_t st_signs;
   uint64_t st_D;
   const int* P;        // SRHT sampled rows (device, s entries, sorted)
-  __nv_bfloat16* Wbf;  // Gaussian: BF16 copy of the basis (column c at Wbf + c * ldbf)
-  int64_t ldbf;
+  __nv_bfloat16* Wbf;  // Gaussian: two-term BF16 copy of the basis, hi = bf16(v), lo = bf16(v - hi),
+                       // K-blocked (see gauss.cuh: entry ((r/64) 2 cpad + t cpad + c) 64 + r%64)
+  int bf_cpad;
   double* part;        // nparts x s block partials (block-major), nparts <= nchunks
   // sparse sign: the pattern transposed per 4096-row chunk (see sparse_rec_bytes): for
   // chunk c at pat + c * sparse_rec_bytes(s, zeta) bytes, uint32 offsets off[0..s] and
@@ -407,6 +408,35 @@ cudaError_t launch_sketch_reduce(const SketchDev& sk, const double* sigma, int c
 cudaError_t launch_sketch_reduce_cols(const SketchDev& sk, size_t colstride, int c0, int ncols, int nparts,
                                       const double* sigma, double scale, double* SV, const DevState* st,
                                       cudaStream_t s);
+// One-pass basis step of the FP32 path (fused.cu): the update, norm and sketch of column
+// c-1 (when upd; window j0u .. j0u+kwu-1, its coefficients in coef) and the SpMV of step c
+// with its window dots (j0 .. c-1); w_{c-1} is read from wprev, w_c written to wnext; the
+// last block writes H's columns c-2 (norm) and c-1, sigma_{c-1}, scl[c], shf[c] and step
+// c's coefficients into coef. Every row of A has at most 8 nonzeros. sk.kind SK_SRHT,
+// SK_SPARSE (with its table) or SK_NONE; sk.nparts receives the grid.
+// plan: per-chunk flags (zeroed at the start of a solve), the task claim order and the
+// chunk ranges the rows of each chunk reference (fused_plan); counter[1] is the task counter.
+struct FusePlan {
+  int* flags;
+  const int* tasks;
+  const int* crange;  // int2 per chunk
+  const int* ell_col;  // A in ELL form (FP32): slot u of row r at u ell_ld + r
+  const float* ell_val;
+  int64_t ell_ld;
+  int ell_k;           // slots (the longest row, <= 8)
+  int stall_pass;      // > 0: in that pass the SpMV tasks wait for a flag no task sets
+  int stall_polls;     //      (fab_inject_wait_timeout), giving up after stall_polls polls
+};
+// The ELL copy of the FP32 CSR matrix for the one-pass steps (k slots, ld >= n).
+cudaError_t launch_build_ell(int n, const int* rowptr, const int* colind, const float* vals, int k, int64_t ld,
+                             int* ecol, float* eval, cudaStream_t s);
+cudaError_t launch_fused_step(const Csr& A, float* W, int64_t ld, int c, int upd, int j0u, int kwu, int j0, int kw,
+                              const float* wprev, float* wnext, ColScale cs, double* H, int ldh, double* coef,
+                              double* part, unsigned* counter, SketchDev& sk, DevState* st, const FusePlan& plan,
+                              cudaStream_t s);
+// Blocks of the one-pass step for a matrix of n rows and sketch kind / rows (and its
+// dynamic shared memory).
+int fused_grid(int kind, int n, int s, size_t* smem);
 // The sparse sign pattern of sk, transposed per chunk, into pat (sparse_table_bytes(n, s, zeta) bytes).
 cudaError_t launch_sparse_pattern(int n, const SketchDev& sk, unsigned short* pat, cudaStream_t s);
 

@@ -3,11 +3,14 @@
 // With a dense Gaussian Theta (s x n) the sketch of the basis is a GEMM with a
 // short output (s x (m+1)) and a long reduction (n): Theta V = G W with G in
 // BF16 (generated once per handle) and the BF16 copy of the basis that the
-// update kernel writes as each column is produced. The GEMM runs on tcgen05:
+// update kernel writes as each column is produced, as two BF16 terms (hi = bf16(v),
+// lo = bf16(v - hi): hi + lo is v to 2^-16 relative, where hi alone is 2^-8), both
+// multiplied into the same FP32 accumulator. The GEMM runs on tcgen05:
 // the reduction dimension is split over the CTAs, each CTA owns one 128-row tile
-// of G and one K-slice; a TMA producer lane streams 64-wide K tiles of G and of
-// the basis into a 4-stage shared-memory ring (128-byte swizzle), one lane issues
-// the UMMAs (M = 128, N = m+1 rounded to 16, K = 16, FP32 accumulation in tensor
+// of G and one K-slice (one CTA per SM, one wave); a TMA producer lane streams 64-wide
+// K tiles of G and of both basis terms into a 2- or 3-stage shared-memory ring
+// (128-byte swizzle), one lane issues the UMMAs (M = 128, N = m+1 rounded to 16, K = 16,
+// two per K step, FP32 accumulation in tensor
 // memory), and the four warps read the accumulator back (tcgen05.ld) into an FP32
 // split-K partial; a second kernel sums the partials in FP64 in a fixed order and
 // applies the column scales sigma_j. Every mbarrier wait is bounded.
@@ -25,7 +28,7 @@ namespace {
 
 constexpr int kBM = 128;     // UMMA M (rows of G per CTA)
 constexpr int kBK = 64;      // K elements per stage (128 bytes of BF16 = one swizzle row)
-constexpr int kStages = 4;
+constexpr int kMaxStages = 4;  // ring depth: as many stages (4 .. 2) as fit the shared memory
 constexpr int kGThreads = 128;
 constexpr uint32_t kTmemCols = 256;
 
@@ -46,12 +49,13 @@ __device__ __forceinline__ unsigned short bf16_bits_rn(double x) {
   return (unsigned short)(sign | ((unsigned long long)e << 7) | (keep & 0x7Full));
 }
 
-__global__ void k_gauss_generate(int s, int n, int64_t ld, uint64_t stG, unsigned short* __restrict__ G) {
-  const int q = blockIdx.y;
+__global__ void k_gauss_generate(int s, int n, int spad, uint64_t stG, unsigned short* __restrict__ G) {
+  const int q = blockIdx.y;  // 0 .. spad-1
   const double sq = sqrt((double)s);
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < ld; j += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t nk = gauss_nkb(n) * 64;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nk; j += (int64_t)gridDim.x * blockDim.x) {
     unsigned short v = 0;
-    if (j < n) {
+    if (j < n && q < s) {
       const unsigned long long idx = (unsigned long long)q * (unsigned long long)n + (unsigned long long)j;
       const unsigned long long h1 = rng_u(stG, 2ull * idx), h2 = rng_u(stG, 2ull * idx + 1ull);
       const double u1 = ((double)(h1 >> 11) + 1.0) * 0x1p-53;
@@ -59,16 +63,18 @@ __global__ void k_gauss_generate(int s, int n, int64_t ld, uint64_t stG, unsigne
       const double g = sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2) / sq;
       v = bf16_bits_rn(g);
     }
-    G[(size_t)q * ld + j] = v;
+    G[((size_t)(j >> 6) * spad + q) * 64 + (size_t)(j & 63)] = v;
   }
 }
 
 // ---------------------------------------------------------------- PTX pieces
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+// One box of a 3D tensor map (x: the 64 reduction indices of a block, always 0; y: the
+// first row; z: the K block).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int y, int z, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-          smem_addr(dst)),
-      "l"((uint64_t)tm), "r"(smem_addr(bar)), "r"(x), "r"(y)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)tm), "r"(smem_addr(bar)), "r"(0), "r"(y), "r"(z)
       : "memory");
 }
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
@@ -125,10 +131,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 }
 
 __global__ void __launch_bounds__(kGThreads, 1)
-    k_gauss_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int nkb,
-                int kb_per_split, int npad, int mpad, float* __restrict__ part, DevState* st) {
+    k_gauss_mma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int cpad,
+                int two, int kStages, int nkb, int kb_per_split, int npad, int mpad, float* __restrict__ part,
+                DevState* st) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ __align__(8) uint64_t full[kMaxStages], empty[kMaxStages], done;
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
   unsigned char* base =
@@ -136,7 +143,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
   const uint32_t bytesA = kBM * kBK * 2;
   const uint32_t bytesB = (uint32_t)npad * kBK * 2;
   unsigned char* sA = base;                       // kStages tiles of 128 x 64 BF16
-  unsigned char* sB = base + kStages * bytesA;    // kStages tiles of npad x 64 BF16
+  unsigned char* sB = base + kStages * bytesA;    // kStages tiles of npad x 64 BF16 (hi term)
+  unsigned char* sL = sB + kStages * bytesB;      // kStages tiles of npad x 64 BF16 (lo term, when two)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mtile = blockIdx.x, split = blockIdx.y;
   const int kb0 = split * kb_per_split;
@@ -167,10 +175,11 @@ __global__ void __launch_bounds__(kGThreads, 1)
         s_fail = 1;
         break;
       }
-      mbar_arrive_expect_tx(&full[stg], bytesA + bytesB);
-      const int kx = (kb0 + i) * kBK;
-      tma_load_2d(sA + stg * bytesA, &tmA, kx, mtile * kBM, &full[stg]);
-      tma_load_2d(sB + stg * bytesB, &tmB, kx, 0, &full[stg]);
+      mbar_arrive_expect_tx(&full[stg], bytesA + (two ? 2u : 1u) * bytesB);
+      const int kb = kb0 + i;  // every box is one contiguous block of 128 (G) or npad (basis) rows
+      tma_load_3d(sA + stg * bytesA, &tmA, mtile * kBM, kb, &full[stg]);
+      tma_load_3d(sB + stg * bytesB, &tmB, 0, kb, &full[stg]);
+      if (two) tma_load_3d(sL + stg * bytesB, &tmB, cpad, kb, &full[stg]);
     }
   } else if (warp == 1 && lane == 0) {  // UMMA issuer
     const uint32_t idesc = idesc_bf16(kBM, npad);
@@ -183,9 +192,12 @@ __global__ void __launch_bounds__(kGThreads, 1)
       tc_fence_after();
       const uint64_t da = sdesc_sw128(smem_addr(sA + stg * bytesA));
       const uint64_t db = sdesc_sw128(smem_addr(sB + stg * bytesB));
+      const uint64_t dl = sdesc_sw128(smem_addr(sL + stg * bytesB));
 #pragma unroll
-      for (int kk = 0; kk < kBK / 16; ++kk)  // 16 BF16 = 32 bytes per UMMA K step
+      for (int kk = 0; kk < kBK / 16; ++kk) {  // 16 BF16 = 32 bytes per UMMA K step
         umma_bf16(tmem, da + 2 * kk, db + 2 * kk, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        if (two) umma_bf16(tmem, da + 2 * kk, dl + 2 * kk, idesc, 1u);  // G lo into the same accumulator
+      }
       umma_commit(&empty[stg]);  // the stage is free once these UMMAs have read it
     }
     umma_commit(&done);
@@ -242,7 +254,9 @@ Split plan(int n, int s, int ncols) {
   p.npad = ((ncols + 15) / 16) * 16;
   if (p.npad < 16) p.npad = 16;
   p.nkb = (n + kBK - 1) / kBK;
-  int want = (sm_count() + p.mtiles - 1) / p.mtiles;  // about one CTA per SM
+  // one CTA per SM and one wave: mtiles x splits <= SMs (a 156th CTA on 152 SMs would
+  // run alone after the first wave and double the kernel's time)
+  int want = sm_count() / p.mtiles;
   if (want < 1) want = 1;
   if (want > p.nkb) want = p.nkb;
   p.kb_per_split = (p.nkb + want - 1) / want;
@@ -264,36 +278,45 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D BF16 tensor map: inner dimension K (length n, contiguous), outer dimension
-// rows (count rows, stride ld elements), box kBK x box_rows, 128-byte swizzle,
-// out-of-range elements read as zero.
-bool make_map(CUtensorMap* tm, const void* base, int n, int rows, int64_t ld, int box_rows) {
+// 3D BF16 tensor map over a K-blocked operand: x the 64 reduction indices of a block
+// (128 bytes, contiguous), y the rows (rows_total, 128 bytes apart), z the K blocks
+// (rows_total x 128 bytes apart); box 64 x box_rows x 1, 128-byte swizzle.
+bool make_map(CUtensorMap* tm, const void* base, int rows_total, int64_t nkb, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+  cuuint64_t dims[3] = {(cuuint64_t)kBK, (cuuint64_t)rows_total, (cuuint64_t)nkb};
+  cuuint64_t strides[2] = {(cuuint64_t)kBK * 2, (cuuint64_t)rows_total * kBK * 2};
+  cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// BF16 copy (round to nearest even from FP64) of ncols FP64 columns (stride ldv) into
-// columns of stride ld; rows n..ld-1 are not touched.
-__global__ void k_to_bf16(int n, int ncols, const double* __restrict__ V, int64_t ldv, unsigned short* __restrict__ B,
-                          int64_t ld) {
+// The two-term BF16 copy of ncols FP64 columns (stride ldv) in the K-blocked layout
+// (cpad = gauss_cpad(ncols)): hi = bf16(v), lo = bf16(v - hi), both rounded to nearest
+// even from FP64 (v - hi is exact); rows past n (to the end of the last block) zero.
+__device__ __forceinline__ double bf16_bits_to_double(unsigned short h) {
+  return (double)__uint_as_float((unsigned)h << 16);
+}
+__global__ void k_to_bf16(int n, int ncols, const double* __restrict__ V, int64_t ldv, unsigned short* __restrict__ B) {
   const int j = blockIdx.y;
-  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
-    B[(size_t)j * ld + r] = bf16_bits_rn(V[(size_t)j * ldv + r]);
+  const int cpad = gauss_cpad(ncols);
+  const int64_t nk = gauss_nkb(n) * 64;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nk; r += (int64_t)gridDim.x * blockDim.x) {
+    const double v = r < n ? V[(size_t)j * ldv + r] : 0.0;
+    const unsigned short h = bf16_bits_rn(v);
+    B[gauss_bidx(r, j, 0, cpad)] = h;
+    B[gauss_bidx(r, j, 1, cpad)] = bf16_bits_rn(v - bf16_bits_to_double(h));
+  }
 }
 
 }  // namespace
 
-cudaError_t launch_to_bf16(int n, int ncols, const double* V, int64_t ldv, __nv_bfloat16* B, int64_t ld,
-                           cudaStream_t st) {
-  const int gx = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
-  k_to_bf16<<<dim3(gx < 1 ? 1 : gx, ncols), 256, 0, st>>>(n, ncols, V, ldv, reinterpret_cast<unsigned short*>(B), ld);
+cudaError_t launch_to_bf16(int n, int ncols, const double* V, int64_t ldv, __nv_bfloat16* B, cudaStream_t st) {
+  const int64_t nk = gauss_nkb(n) * 64;
+  const int gx = (int)((nk + 255) / 256 < 1024 ? (nk + 255) / 256 : 1024);
+  k_to_bf16<<<dim3(gx < 1 ? 1 : gx, ncols), 256, 0, st>>>(n, ncols, V, ldv, reinterpret_cast<unsigned short*>(B));
   return cudaGetLastError();
 }
 
@@ -303,26 +326,32 @@ size_t gauss_partial_bytes(int n, int s, int ncols) {
   return (size_t)p.splits * p.mpad * p.npad * sizeof(float);
 }
 
-cudaError_t launch_gauss_generate(int s, int n, int64_t ld, uint64_t stG, __nv_bfloat16* G, cudaStream_t st) {
-  const int64_t per = (ld + 255) / 256;
+cudaError_t launch_gauss_generate(int s, int n, uint64_t stG, __nv_bfloat16* G, cudaStream_t st) {
+  const int64_t per = (gauss_nkb(n) * 64 + 255) / 256;
   const int gx = (int)(per < 1024 ? per : 1024);
-  k_gauss_generate<<<dim3(gx, s), 256, 0, st>>>(s, n, ld, stG, reinterpret_cast<unsigned short*>(G));
+  k_gauss_generate<<<dim3(gx, gauss_spad(s)), 256, 0, st>>>(s, n, gauss_spad(s), stG,
+                                                             reinterpret_cast<unsigned short*>(G));
   return cudaGetLastError();
 }
 
-cudaError_t launch_gauss_sketch(const __nv_bfloat16* G, const __nv_bfloat16* Wbf, int64_t ld, int n, int s,
-                                int ncols, const double* sigma, double* part, double* SV, DevState* st,
-                                cudaStream_t stream) {
-  if (ncols < 1 || ncols > kGaussMaxCols || (ld % 8) != 0) return cudaErrorInvalidValue;
+cudaError_t launch_gauss_sketch(const __nv_bfloat16* G, const __nv_bfloat16* B, int cpad, int n, int s, int ncols,
+                                const double* sigma, double* part, double* SV, DevState* st, cudaStream_t stream) {
+  if (ncols < 1 || ncols > kGaussMaxCols || cpad < gauss_cpad(ncols)) return cudaErrorInvalidValue;
   const Split p = plan(n, s, ncols);
+  const int two = 1;
   CUtensorMap tmA, tmB;
-  if (!make_map(&tmA, G, n, s, ld, kBM) || !make_map(&tmB, Wbf, n, ncols, ld, p.npad)) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)kStages * (kBM * kBK * 2 + (size_t)p.npad * kBK * 2) + 1024;
+  if (!make_map(&tmA, G, gauss_spad(s), gauss_nkb(n), kBM) || !make_map(&tmB, B, 2 * cpad, gauss_nkb(n), p.npad))
+    return cudaErrorInvalidValue;
+  const size_t stage = kBM * kBK * 2 + (size_t)(1 + two) * p.npad * kBK * 2;
+  const size_t cap = 227 * 1024 - 2048;  // dynamic shared memory a CTA may take, less the static part
+  int nst = kMaxStages;
+  while (nst > 2 && (size_t)nst * stage + 1024 > cap) --nst;
+  const size_t smem = (size_t)nst * stage + 1024;
   cudaError_t e = ensure_smem_limit((const void*)k_gauss_mma, smem);
   if (e != cudaSuccess) return e;
   float* fpart = reinterpret_cast<float*>(part);
-  k_gauss_mma<<<dim3(p.mtiles, p.splits), kGThreads, smem, stream>>>(tmA, tmB, p.nkb, p.kb_per_split, p.npad, p.mpad,
-                                                                      fpart, st);
+  k_gauss_mma<<<dim3(p.mtiles, p.splits), kGThreads, smem, stream>>>(tmA, tmB, cpad, two, nst, p.nkb,
+                                                                      p.kb_per_split, p.npad, p.mpad, fpart, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_gauss_reduce<<<dim3((ncols + 127) / 128, s), 128, 0, stream>>>(fpart, p.splits, p.mpad, p.npad, s, ncols, sigma,

@@ -9,6 +9,7 @@
 #include <new>
 #include <stdexcept>
 #include <system_error>
+#include <vector>
 
 #include "../../include/fab.h"
 
@@ -72,11 +73,23 @@ struct fab_handle {
   int* d_tiles = nullptr;
   int ntiles = 0;
   int tile_rows = 256, tile_nnz = 2048, tile_staged = 1;
+  // one-pass basis steps for the FP32 basis (fused.cu): allowed when every row has at
+  // most 8 nonzeros (max_row_nnz, set by fab_create) and fuse = 1 (fab_set_fusion; the
+  // default 0 keeps the two-pass loop, measured faster on GB300)
+  int max_row_nnz = 0;
+  int fuse = 0;
+  int* d_ftasks = nullptr;  // the one-pass steps' task claim order (2 chunks ints) and, per
+  int* d_fcrange = nullptr; // chunk, the first and last chunk its rows reference (shared by clones)
+  int* d_ell_col = nullptr;  // the FP32 matrix in ELL form for the one-pass steps (max_row_nnz
+  float* d_ell_val = nullptr;  // slots of ld entries), made with the FP32 copy (shared by clones)
   int* h_rowptr = nullptr;  // host copy of the row pointers (n+1), for re-tiling
   // workspace
   fab::Buf W, H, sigma, shf, scl, coef, part, counter, gpart, skpart, SV, P, qr, tau, y, cvec, dense, piv, scal, lsq, u, xbuf,
       state;
   fab::Buf W32, Wbf, G;  // mixed path: FP32 basis, its BF16 copy, Gaussian sketch (BF16, s x ld)
+  fab::Buf wbuf;         // mixed path, one-pass steps: two raw SpMV outputs (2 ld floats)
+  fab::Buf fflags;       // one-pass steps: per-chunk flags of the updated column
+  int stall_pass = 0, stall_polls = 0;  // fab_inject_wait_timeout (one-shot)
   fab::Buf whm;          // FAB_WHITEN: R, R^{-1}, scratch ((m+1)^2 each), coefficients, norms
   int G_n = -1, G_s = -1;
   uint64_t G_seed = 0;
@@ -125,5 +138,10 @@ const double* pade13_b();
 double pade13_theta();
 // Host-side allocation fault injection (FAB_FAULT=alloc:N): true for the N-th call.
 bool alloc_fault();
+// The one-pass steps' plan of a matrix (fused.cu): per 4096-row chunk the first and
+// last chunk its rows reference, and the claim order of the update and SpMV tasks.
+// lead: extra chunks the updates run ahead of the SpMV tasks.
+void fused_plan(int n, const int* rowptr, const int* colind, int lead, std::vector<int>& tasks,
+                std::vector<int2>& crange);
 
 }  // namespace fab

@@ -28,8 +28,8 @@ SYMBOLS = ("fab_params_default", "fab_strerror", "fab_last_error", "fab_create",
            "fab_last_basis", "fab_sketch_apply", "fab_sketch_apply_noalloc", "fab_profile_enable",
            "fab_profile_only", "fab_profile_query", "fab_server_create", "fab_server_submit", "fab_server_poll", "fab_server_stats_get",
            "fab_server_destroy", "fab_batch_create", "fab_batch_exec", "fab_batch_input", "fab_batch_output",
-           "fab_batch_kernels", "fab_batch_destroy", "fab_batch_run", "fab_set_tiling", "fab_tune", "fab_fma_peak")
-PROFILE_KINDS = ("spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine")
+           "fab_batch_kernels", "fab_batch_destroy", "fab_batch_run", "fab_set_tiling", "fab_set_fusion", "fab_inject_wait_timeout", "fab_tune", "fab_fma_peak")
+PROFILE_KINDS = ("spmv_dots", "update", "sketch_reduce", "gemv_t", "small", "combine", "fused_step")
 
 
 class Params(ctypes.Structure):
@@ -103,6 +103,10 @@ lib.fab_batch_run.argtypes = [_vp, _vp, _vp, _vp, _i32, _vp]
 lib.fab_batch_run.restype = _i32
 lib.fab_set_tiling.argtypes = [_vp, _i32, _i32, _i32]
 lib.fab_set_tiling.restype = _i32
+lib.fab_inject_wait_timeout.argtypes = [_vp, _i32, _i32]
+lib.fab_inject_wait_timeout.restype = _i32
+lib.fab_set_fusion.argtypes = [_vp, _i32]
+lib.fab_set_fusion.restype = _i32
 lib.fab_tune.argtypes = [_vp, _i32, _i32, _vp, _vp]
 lib.fab_tune.restype = _i32
 lib.fab_fma_peak.argtypes = [_i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _vp]
@@ -210,11 +214,17 @@ class Matrix:
             b = np.ascontiguousarray(b, dtype=np.float64)
         st = Stats()
         _check(lib.fab_apply(self._h, ctypes.byref(p), _addr(b), _addr(x), on_dev, ctypes.byref(st)), "fab_apply")
-        self._last = (p.m, p.s, p.method in (SKETCHED_FAST, SKETCHED_LS, BG_LS, WHITEN))
+        # growing m: the final dimension is not known here, so the state is not inspectable
+        self._last = None if p.target_rel_err > 0 else (p.m, p.s, p.method in (SKETCHED_FAST, SKETCHED_LS, BG_LS,
+                                                                                WHITEN))
         return (x, st) if stats else x
 
     def set_tiling(self, rows_max: int = 256, nnz_cap: int = 2048, staged: bool = True):
         _check(lib.fab_set_tiling(self._h, int(rows_max), int(nnz_cap), 1 if staged else 0), "fab_set_tiling")
+
+    def set_fusion(self, on: bool = True):
+        """Allow (default) or forbid the one-pass basis steps of the FP32 basis."""
+        _check(lib.fab_set_fusion(self._h, 1 if on else 0), "fab_set_fusion")
 
     def tune(self, precision: int = FP64, k: int = 2, stream=None):
         """Autotune the SpMV tiling for this matrix; returns (rows_max, nnz_cap, staged)."""
@@ -222,8 +232,13 @@ class Matrix:
         _check(lib.fab_tune(self._h, int(precision), int(k), ctypes.cast(ch, _vp), stream), "fab_tune")
         return tuple(ch)
 
+    def _last_sizes(self):
+        if self._last is None:
+            raise ValueError("no inspectable state: no fixed-m solve has run on this handle")
+        return self._last
+
     def last_state(self) -> LastState:
-        m, s, sk = self._last
+        m, s, sk = self._last_sizes()
         H = np.zeros((m, m + 1))  # column-major (m+1) x m read as row-major transpose
         SV = np.zeros((m + 1, s)) if sk else None
         y = np.zeros(m)
@@ -232,7 +247,7 @@ class Matrix:
         return LastState(H=H.T.copy(), SV=None if SV is None else SV.T.copy(), y=y, coeffs=c)
 
     def last_basis(self) -> np.ndarray:
-        m = self._last[0]
+        m = self._last_sizes()[0]
         V = np.zeros((m + 1, self.n))
         _check(lib.fab_last_basis(self._h, _addr(V), 0), "fab_last_basis")
         return V.T.copy()

@@ -140,3 +140,39 @@ def test_batch_breakdown_zero_rhs_and_rejects(fab):
     with pytest.raises(fab.FabError) as e:  # one precision per batch
         fab.Batch([C, C], [fab.params(m=10, s=40), fab.params(m=10, s=40, precision=fab.MIXED)])
     assert e.value.code == fab.FAB_EINVAL
+
+
+@pytest.mark.slow
+def test_batch_fp64_many_blocks_per_wave(fab):
+    """Solves large enough that a wave gives each of them many blocks (a batched solve
+    takes at least 32 SpMV tiles of 256 rows and 4 update chunks of 4096 rows per
+    block: n = 360,000 gives 44 SpMV and 22 update blocks): the cross-block partial
+    sums, the last-block reductions and the block-prefix search of a wave run with
+    several solves of different sizes, windows and sketches in it. Every result against
+    the FP64 oracle at the library's FP64 target, and against the solve alone."""
+    specs = [  # (grid side, f, t, m, k, sketch, s, zeta, method, seed)
+        (600, matfun.EXP, -1e-4, 40, 2, osk.SPARSE_SIGN, 160, 8, krylov.SKETCHED_FAST, 1),
+        (450, matfun.EXP, -2e-4, 33, 2, osk.SRHT, 132, 8, krylov.SKETCHED_FAST, 2),
+        (520, matfun.EXP, -1e-4, 28, 3, osk.SRHT, 0, 8, krylov.NOPROJ, 1),
+        (300, matfun.EXP, -5e-4, 36, 2, osk.SPARSE_SIGN, 144, 4, krylov.SKETCHED_FAST, 3),
+    ]
+    A = [W.convdiff(2, g) for g, *_ in specs]
+    assert A[0].n == 360000
+    mats = [fab.Matrix.from_csr(a) for a in A]
+    ps, bs, refs = [], [], []
+    for i, (g, f, t, m, k, sk, s, zeta, method, seed) in enumerate(specs):
+        kw = dict(f=f, t=t, m=m, k=k, zeta=zeta, sketch=sk, method=method, seed=seed, precision=fab.FP64,
+                  s=s if s else 4 * m)
+        ps.append(fab.params(**kw))
+        b = W.random_vector(A[i].n, 40 + i)
+        bs.append(b)
+        th = osk.make(sk, A[i].n, kw["s"], seed, zeta) if method == krylov.SKETCHED_FAST else None
+        refs.append(krylov.run(method, W.to_scipy(A[i]), b, m, k, f, th, t).x)
+    bt = fab.Batch(mats, ps)
+    xs = [np.empty(a.n) for a in A]
+    bt.run(bs, xs)
+    bt.close()
+    for i in range(len(specs)):
+        assert _rel(xs[i], refs[i]) <= TOL, i
+        alone = mats[i].apply(bs[i], ps[i])
+        assert _rel(xs[i], alone) <= 1e-11, i

@@ -229,11 +229,33 @@ def test_mgs_vs_cgs_window_reading(fab, torch):
 
 
 # ------------------------------------------------ full-size (bench) workload
+def _golden_c2():
+    """The oracle's C2 solve as stored by tests/golden/make_c2_reference.py."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c2_sketched_fast.txt")
+    out = {"x": {}}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        key, *vals = line.split()
+        if key == "x":
+            out["x"][int(vals[0])] = float(vals[1])
+        elif key == "coeffs":
+            out["coeffs"] = np.array([float(v) for v in vals])
+        else:
+            out[key] = float(vals[0])
+    return out
+
+
 @pytest.mark.slow
-def test_c2_full_size_first_steps_and_relation(fab, torch):
-    """3D convection-diffusion 200^3 (n = 8.0M), m = 100, k = 4, SRHT s = 400, exp(-1e-3 A):
-    the first basis steps against the oracle run at full size, and the Arnoldi-like
-    relation A V_m = V_{m+1} H_m (eq. arnoldilike) on sampled rows of the whole basis."""
+def test_c2_full_size_against_the_oracle(fab, torch):
+    """The bench workload at full size: 3D convection-diffusion 200^3 (n = 8.0M,
+    nnz = 55.76M), exp(-1e-3 A) b, m = 100, k = 4, SRHT s = 400, sketched_fast (Remark
+    after eq. sFOM), FP64. The oracle runs the whole solve on the host: x at 1e-10
+    relative 2-norm, the coefficient vector c and H element by element; the stored
+    oracle solve (coefficients and sampled entries, tests/golden/) agrees too; the
+    Arnoldi-like relation A V_m = V_{m+1} H_m (eq. arnoldilike) holds on sampled rows."""
     A = W.convdiff(3, 200)
     assert A.nnz == W.convdiff_nnz(3, 200)
     b = W.random_vector(A.n, 0)
@@ -243,14 +265,21 @@ def test_c2_full_size_first_steps_and_relation(fab, torch):
     p = fab.params(f=fab.EXP, t=t, m=m, k=k, s=s, sketch=fab.SRHT, seed=1, method=fab.SKETCHED_FAST)
     bd = torch.from_numpy(b).cuda()
     x, st = M.apply(bd, p, stats=True)
+    x = x.cpu().numpy()
     assert st.m_used == m
     ls = M.last_state()
-    # oracle: first 4 steps of Alg. 2 at full size
-    B4 = krylov.nt_basis(As, b, 4, k)
-    assert np.allclose(ls.H[:5, :4], B4.H, rtol=0, atol=1e-12 * np.abs(B4.H).max())
-    th = osk.SRHT_(A.n, s, 1)
-    SV4 = th.apply(B4.V[:, :3])
-    assert np.max(np.abs(ls.SV[:, :3] - SV4)) <= 1e-12
+    gold = _golden_c2()
+    idx = np.array(sorted(gold["x"]))
+    xs = np.array([gold["x"][i] for i in idx])
+    assert _rel(x[idx], xs) <= TOL
+    assert _rel(ls.coeffs, gold["coeffs"]) <= TOL
+    ref = krylov.sketched_fast(As, b, m, k, matfun.EXP, osk.SRHT_(A.n, s, 1), t, form="sketch_solve")
+    print(f"\nC2 full size: rel err vs oracle {_rel(x, ref.x):.3e}, kappa_est {st.kappa_est:.3e}")
+    assert _rel(x, ref.x) <= TOL
+    assert _rel(ls.coeffs, ref.coeffs) <= TOL
+    H_ref = ref.basis.H
+    assert np.max(np.abs(ls.H - H_ref)) <= 1e-11 * np.abs(H_ref).max()
+    del ref
     # Arnoldi-like relation on sampled rows of the GPU basis
     V = torch.empty((m + 1, A.n), dtype=torch.float64, device="cuda")
     assert fab.lib.fab_last_basis(M._h, V.data_ptr(), 1) == 0
