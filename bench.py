@@ -90,6 +90,35 @@ def oracle_golden_error(x_dev, coeffs):
                          f"{len(rows)} sampled rows of x and the m coefficients)"}
 
 
+def oracle_golden_c3(fname: str, x_dev, coeffs):
+    """The graph solve against the FP64 oracle's f_m at the same m and sketch, stored by
+    tests/golden/make_c3_reference.py (1024 sampled rows of x, the coefficients, and the
+    rounding model's RMS at this size)."""
+    path = os.path.join(ROOT, "tests", "golden", "c3_gauss.txt")
+    if not os.path.exists(path):
+        return None
+    rows, vals, gc, rms = [], [], None, None
+    for line in open(path):
+        p = line.split()
+        if not p or p[0] != fname:
+            continue
+        if p[1] == "x":
+            rows.append(int(p[2]))
+            vals.append(float(p[3]))
+        elif p[1] == "coeffs":
+            gc = np.array([float(v) for v in p[2:]])
+        elif p[1] == "model_rms":
+            rms = float(p[2])
+    import torch
+
+    xs = x_dev[torch.tensor(rows, device=x_dev.device)].cpu().numpy()
+    vals = np.array(vals)
+    return {"x_sampled_rows": float(np.linalg.norm(xs - vals) / np.linalg.norm(vals)),
+            "coeffs": float(np.linalg.norm(coeffs - gc) / np.linalg.norm(gc)) if gc is not None else None,
+            "rounding_model_rms": rms,
+            "reference": "FP64 oracle sketched_fast, same m, k and Gaussian sketch (tests/golden/c3_gauss.txt)"}
+
+
 def bench_config(grid: int, n: int, nnz: int, world: int) -> dict:
     """The workload description both arms print (the same dict in both lines)."""
     return {"workload": workload_name(grid, n, nnz), "n": n, "nnz": nnz, "m": M, "k": K_WIN, "s": S_ROWS,
@@ -442,7 +471,8 @@ def bench_mixed_graph(fab, torch, W, reps: int = 2, n: int = 4_000_000, referenc
             xr = torch.empty_like(b)
             Mx.apply(b, fab.params(f=f, m=mr, k=2, method=fab.ARNOLDI, stream=sp), x=xr)
             ref[mr] = float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))
-        out[name] = {"solves_per_s": 1000.0 / ms, "ms_per_solve": ms,
+        fm = oracle_golden_c3(name, x, Mx.last_state().coeffs) if n == 4_000_000 else None
+        out[name] = {"solves_per_s": 1000.0 / ms, "ms_per_solve": ms, "rel_err_vs_oracle_fm": fm,
                      "rel_err_vs_fp64_arnoldi_m150": ref[150], "rel_err_vs_fp64_arnoldi_m300": ref[300],
                      "gauss_sketch_ms": g_ms, "gauss_tflops": flops / (g_ms / 1000.0) / 1e12,
                      "gauss_tensor_frac_of_measured_bf16": flops / (g_ms / 1000.0) / 1e12

@@ -114,11 +114,15 @@ __device__ void sketch_chunk_srht(const TV (&v)[kRowsPerThread], int chunk, cons
   for (int i = 0; i < kRowsPerThread; ++i) e = max(e, exp_field(v[i]));
   const int E = block_max_int(e, s_int);
   long long X[16];
+  // D's signs: row i*256 + t takes bit (t mod 64) of word chunk*64 + t/64 + 4i. The 32
+  // threads of a warp share t/64, so the warp needs 16 words: lane l < 16 draws the word of
+  // i = l and every thread reads word i from lane i (one draw per lane instead of 16).
   const unsigned long long word0 = (unsigned long long)chunk * (kChunk / 64) + (t >> 6);
+  const unsigned long long mine = rng_u(sk.st_D, word0 + (unsigned long long)(t & 15) * (kThreads / 64));
 #pragma unroll
   for (int i = 0; i < kRowsPerThread; ++i) {
     long long x = to_fixed(v[i], E);
-    const unsigned long long dw = rng_u(sk.st_D, word0 + (unsigned long long)i * (kThreads / 64));
+    const unsigned long long dw = __shfl_sync(0xffffffffu, mine, i);
     if ((dw >> (t & 63)) & 1ull) x = -x;
     X[i] = x;
   }
