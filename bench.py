@@ -351,10 +351,11 @@ def bench_whiten_graph(fab, torch, W, ns=(6301, 1_000_000), ms=(60, 100, 140, 18
                 p = fab.params(f=fab.SQRT, m=m, k=2, s=4 * m, sketch=fab.SRHT, seed=1, method=meth, lsqr_tol=1e-6,
                                stream=sp)
                 x = torch.empty_like(b)
-                try:
-                    _, st = Mx.apply(b, p, x=x, stats=True)
-                except fab.FabError as e:  # e.g. no real principal square root of a garbled projection
-                    row[name] = {"error": e.code}
+                st = fab.Stats()
+                rc = fab.lib.fab_apply(Mx._h, ctypes.byref(p), b.data_ptr(), x.data_ptr(), 1, ctypes.byref(st))
+                if rc != fab.FAB_OK:  # e.g. no real principal square root of a garbled projection
+                    row[name] = {"error": rc, "m_used": st.m_used, "kappa_est": st.kappa_est,
+                                 "fh_iters": st.fh_iters}
                     continue
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -365,6 +366,8 @@ def bench_whiten_graph(fab, torch, W, ns=(6301, 1_000_000), ms=(60, 100, 140, 18
                 torch.cuda.synchronize()
                 row[name] = {"ms": e0.elapsed_time(e1) / reps,
                              "rel_err": float(torch.linalg.norm(x - xr) / torch.linalg.norm(xr))}
+                if meth in (fab.SKETCHED_FAST, fab.SKETCHED_LS):
+                    row[name]["kappa_est"] = st.kappa_est
                 if meth == fab.WHITEN:
                     row[name]["whiten_at"] = st.whiten_at
                     row[name]["lsqr_iters"] = st.lsqr_iters
