@@ -294,14 +294,18 @@ void fab_server_destroy(fab_server* srv);
  * a tile with R rows runs 256 / pow2ceil(R) lanes per row, so short rows get a
  * thread each and a long row the whole block. staged = 1 copies a tile's
  * nonzeros into shared memory (bulk copies) when they fit 2048 entries.
- * fab_create uses (256, 2048, 1). The tiling fixes the order of the SpMV
+ * staged = 2 stages the same way and processes a staged tile of at least 32 rows
+ * by nonzeros: each thread takes 8 consecutive entries whatever their rows, and
+ * the row sums are assembled in a fixed order (for short rows of uneven length,
+ * such as a power-law graph's); tiles cut by the nonzero cap then keep any row
+ * count. fab_create uses (256, 2048, 1). The tiling fixes the order of the SpMV
  * additions, so results differ within rounding between tilings (and are
  * reproducible for a given one).
- * fab_set_tiling  sets it; FAB_EINVAL for rows_max outside 1..256, nnz_cap < 1
- *                 or a workspace clone.
+ * fab_set_tiling  sets it; FAB_EINVAL for rows_max outside 1..256, nnz_cap < 1,
+ *                 staged outside 0..2 or a workspace clone.
  * fab_tune        times the kernel on h's matrix (precision FAB_FP64 or
  *                 FAB_MIXED, window k) for rows_max in {256, 128, 64}, nnz_cap
- *                 in {2048, 1024, 512} and staged in {1, 0}, keeps the fastest
+ *                 in {2048, 1024, 512} and staged in {2, 1, 0}, keeps the fastest
  *                 and writes it to choice[3] (nullable). Uses a temporary device
  *                 buffer of about (k+1) n words; `stream` is a cudaStream_t or NULL.
  * Neither may run while a solve, batch or server request uses h.

@@ -75,10 +75,15 @@ cudaError_t launch_state_set_m(DevState* st, int m, cudaStream_t s) {
 // longer single-row tile is read from global memory with the same order of
 // operations.
 
+// With A.staged == 2, staged tiles of at least kSegRows rows are processed by
+// nonzeros instead of by rows (the short, uneven rows of a power-law graph leave
+// most lanes of a row-per-lane warp idle and make their shared loads conflict).
+constexpr int kSegRows = 32;
+
 // The work of block `bid` of `nblk` (a launch of its own, or one solve's share
 // of a batched wave) is a function of (bid, nblk) only, so a solve gives the
 // same bits whichever way its blocks are launched.
-template <typename TV, int KW>
+template <typename TV, int KW, bool SEG = false>
 __device__ __forceinline__ void spmv_dots_body(
     const Csr& A, TV* __restrict__ W, int64_t ld, int c, int j0, int kw, const ColScale& cs, double* __restrict__ H,
     int ldh, double* __restrict__ coef, double* __restrict__ part, unsigned* __restrict__ counter, DevState* st,
@@ -97,6 +102,11 @@ __device__ __forceinline__ void spmv_dots_body(
   __shared__ double sh[32 * NV];
   __shared__ double tot[NV];
   __shared__ TV s_red[kThreads / 32];
+  // nonzero-parallel tiles (A.staged == 2): row starts in stage coordinates, and per
+  // thread the sums of the row it continues (head) and of the row it leaves open (tail)
+  constexpr int kSeg = SEG ? kThreads : 1;
+  __shared__ int s_rp[kSeg + 1];
+  __shared__ TV s_head[kSeg], s_tail[kSeg], s_yrow[kSeg];
   if (st->stop) return;
   const int tid = threadIdx.x, lane = tid & 31;
   const int ntiles = A.ntiles;
@@ -171,7 +181,8 @@ __device__ __forceinline__ void spmv_dots_body(
     // each lane sums every L-th nonzero of its row, then the lanes of a row are
     // combined in a fixed order.
     const int r0 = A.tiles[tile], nr = A.tiles[tile + 1] - r0;
-    const int lgL = 8 - (nr > 1 ? 32 - __clz(nr - 1) : 0);
+    const bool seg = SEG && A.staged == 2 && nr >= kSegRows;  // block-uniform
+    const int lgL = seg ? 0 : 8 - (nr > 1 ? 32 - __clz(nr - 1) : 0);
     const int L = 1 << lgL;
     const int grp = tid >> lgL, lane_r = tid & (L - 1);
     const bool in_tile = grp < nr;
@@ -200,7 +211,87 @@ __device__ __forceinline__ void spmv_dots_body(
     const bool staged = ok && s_staged[stg] != 0;
     const bool has_row = ok && in_tile;
     TV y = (TV)0;
-    if (has_row) {
+    bool done = false;
+    if constexpr (SEG) if (seg) {
+      // Thread t takes the 8 staged entries 8t..8t+7 whatever rows they belong to
+      // (conflict-free 16-byte shared loads, 8 independent gathers, no idle lanes on
+      // short rows), sums them per row in order, and the rows are then assembled in a
+      // fixed order: a row inside one thread from that thread's sum, a row spread over
+      // threads ts..te from tail(ts) + head(ts+1) + ... + head(te).
+      const int base = s_e0[stg];
+      int rs = 0, re = 0;
+      if (in_tile) {
+        rs = e0 - base;
+        re = e1 - base;
+        s_rp[grp] = rs;
+        if (grp == nr - 1) s_rp[nr] = re;
+      }
+      const int bad = __syncthreads_or(!ok);
+      if (!bad && s_staged[stg]) {
+        const int lo = s_rp[0], hi = s_rp[nr];
+        const int a = 8 * tid;
+        if (a < hi && a + 8 > lo) {
+          int ci[8];
+          TV av[8], g[8];
+          const int* sc = s_col + stg * kSpmvCap + a;
+          const TV* sv = s_vals + stg * kSpmvCap + a;
+          *reinterpret_cast<int4*>(ci) = *reinterpret_cast<const int4*>(sc);
+          *reinterpret_cast<int4*>(ci + 4) = *reinterpret_cast<const int4*>(sc + 4);
+          if constexpr (sizeof(TV) == 4) {
+            *reinterpret_cast<float4*>(av) = *reinterpret_cast<const float4*>(sv);
+            *reinterpret_cast<float4*>(av + 4) = *reinterpret_cast<const float4*>(sv + 4);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) *reinterpret_cast<double2*>(av + u) = *reinterpret_cast<const double2*>(sv + u);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) g[u] = (a + u >= lo && a + u < hi) ? __ldg(vin + ci[u]) : (TV)0;
+          // the row of the first entry in the tile: the last row starting at or before it
+          const int first = a > lo ? a : lo;
+          int row = 0, top = nr;
+          while (top - row > 1) {
+            const int mid = (row + top) >> 1;
+            if (s_rp[mid] <= first) row = mid;
+            else top = mid;
+          }
+          int rbeg = s_rp[row], rend = s_rp[row + 1];
+          TV sum = (TV)0;
+          auto flush = [&]() {
+            const bool before = rbeg < a, after = rend > a + 8;
+            if (!before && !after) s_yrow[row] = sum;
+            if (before) s_head[tid] = sum;
+            if (after) s_tail[tid] = sum;
+          };
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int e = a + u;
+            if (e < lo || e >= hi) continue;
+            while (e >= rend) {  // the current row ends before entry e
+              flush();
+              ++row;
+              rbeg = rend;
+              rend = s_rp[row + 1];
+              sum = (TV)0;
+            }
+            sum = fma(av[u], g[u], sum);
+          }
+          flush();
+        }
+        __syncthreads();
+        if (has_row && re > rs) {
+          const int ts = rs >> 3, te = (re - 1) >> 3;
+          if (ts == te) {
+            y = s_yrow[grp];
+          } else {
+            y = s_tail[ts];
+            for (int t = ts + 1; t < te; ++t) y += s_head[t];
+            y += s_head[te];
+          }
+        }
+        done = true;
+      }
+    }
+    if (has_row && !done) {
       int e = e0 + lane_r;
       if (staged) {
         const int base = s_e0[stg];
@@ -299,40 +390,51 @@ __device__ __forceinline__ void spmv_dots_body(
   }
 }
 
-template <typename TV, int KW>
+template <typename TV, int KW, bool SEG>
 __global__ __launch_bounds__(kThreads) void k_spmv_dots(Csr A, TV* __restrict__ W, int64_t ld, int c, int j0, int kw,
                                                          ColScale cs, double* __restrict__ H, int ldh,
                                                          double* __restrict__ coef, double* __restrict__ part,
                                                          unsigned* __restrict__ counter, DevState* st, int gate) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (gate_closed(st, c, gate)) return;
-  spmv_dots_body<TV, KW>(A, W, ld, c, j0, kw, cs, H, ldh, coef, part, counter, st, blockIdx.x, gridDim.x, smem_raw);
+  spmv_dots_body<TV, KW, SEG>(A, W, ld, c, j0, kw, cs, H, ldh, coef, part, counter, st, blockIdx.x, gridDim.x,
+                              smem_raw);
 }
 
 template <typename TV>
-const void* spmv_fn(int kw) {
-  static const void* fns[kMaxWindow + 1] = {
-      (const void*)k_spmv_dots<TV, 0>, (const void*)k_spmv_dots<TV, 1>, (const void*)k_spmv_dots<TV, 2>,
-      (const void*)k_spmv_dots<TV, 3>, (const void*)k_spmv_dots<TV, 4>, (const void*)k_spmv_dots<TV, 5>,
-      (const void*)k_spmv_dots<TV, 6>, (const void*)k_spmv_dots<TV, 7>, (const void*)k_spmv_dots<TV, 8>};
-  return fns[kw];
+const void* spmv_fn(int kw, bool seg) {
+  static const void* fns[2][kMaxWindow + 1] = {
+      {(const void*)k_spmv_dots<TV, 0, false>, (const void*)k_spmv_dots<TV, 1, false>,
+       (const void*)k_spmv_dots<TV, 2, false>, (const void*)k_spmv_dots<TV, 3, false>,
+       (const void*)k_spmv_dots<TV, 4, false>, (const void*)k_spmv_dots<TV, 5, false>,
+       (const void*)k_spmv_dots<TV, 6, false>, (const void*)k_spmv_dots<TV, 7, false>,
+       (const void*)k_spmv_dots<TV, 8, false>},
+      {(const void*)k_spmv_dots<TV, 0, true>, (const void*)k_spmv_dots<TV, 1, true>,
+       (const void*)k_spmv_dots<TV, 2, true>, (const void*)k_spmv_dots<TV, 3, true>,
+       (const void*)k_spmv_dots<TV, 4, true>, (const void*)k_spmv_dots<TV, 5, true>,
+       (const void*)k_spmv_dots<TV, 6, true>, (const void*)k_spmv_dots<TV, 7, true>,
+       (const void*)k_spmv_dots<TV, 8, true>}};
+  return fns[seg ? 1 : 0][kw];
 }
 
+// Blocks of one SpMV launch: every resident slot once (the nonzero-parallel form,
+// seg, is a kernel of its own with its own occupancy).
 template <typename TV>
-int spmv_grid(int ntiles, int kw) {
-  static int occ[kMaxWindow + 1] = {0};
-  if (occ[kw] == 0) {
+int spmv_grid(int ntiles, int kw, bool seg) {
+  static int occ[2][kMaxWindow + 1] = {{0}};
+  int& o_kw = occ[seg ? 1 : 0][kw];
+  if (o_kw == 0) {
     const size_t smem = (size_t)kSpmvStages * kSpmvCap * (sizeof(TV) + sizeof(int));
-    ensure_smem_limit(spmv_fn<TV>(kw), smem);
+    ensure_smem_limit(spmv_fn<TV>(kw, seg), smem);
     int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmv_fn<TV>(kw), kThreads, smem);
-    occ[kw] = o < 1 ? 1 : o;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, spmv_fn<TV>(kw, seg), kThreads, smem);
+    o_kw = o < 1 ? 1 : o;
   }
-  const int grid = sm_count() * occ[kw];
+  const int grid = sm_count() * o_kw;
   return ntiles < grid ? (ntiles < 1 ? 1 : ntiles) : grid;
 }
-template int spmv_grid<double>(int, int);
-template int spmv_grid<float>(int, int);
+template int spmv_grid<double>(int, int, bool);
+template int spmv_grid<float>(int, int, bool);
 
 template <typename TV>
 cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int kw, ColScale cs,
@@ -340,9 +442,10 @@ cudaError_t launch_spmv_dots(const Csr& A, TV* W, int64_t ld, int c, int j0, int
                              DevState* st, cudaStream_t s, int gate) {
   if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
   const size_t smem = (size_t)kSpmvStages * kSpmvCap * (sizeof(TV) + sizeof(int));
-  const int grid = spmv_grid<TV>(A.ntiles, kw);
+  const bool seg = A.staged == 2;
+  const int grid = spmv_grid<TV>(A.ntiles, kw, seg);
   void* args[] = {(void*)&A, &W, &ld, &c, &j0, &kw, &cs, &H, &ldh, &coef, &part, &counter, &st, &gate};
-  return cudaLaunchKernel(spmv_fn<TV>(kw), dim3(grid), dim3(kThreads), args, smem, s);
+  return cudaLaunchKernel(spmv_fn<TV>(kw, seg), dim3(grid), dim3(kThreads), args, smem, s);
 }
 template cudaError_t launch_spmv_dots<double>(const Csr&, double*, int64_t, int, int, int, ColScale, double*, int,
                                               double*, double*, unsigned*, DevState*, cudaStream_t, int);
@@ -1173,8 +1276,15 @@ cudaError_t ensure_smem_limit(const void* fn, size_t bytes) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(mu);
-  size_t& cur = limit[{dev, fn}];
-  if (bytes <= cur) return cudaSuccess;
+  auto it = limit.find({dev, fn});
+  if (it == limit.end()) {  // start from the kernel's own limit (48 KB less its static shared memory)
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    it = limit.emplace(std::make_pair(dev, fn), (size_t)fa.maxDynamicSharedSizeBytes).first;
+  }
+  size_t& cur = it->second;
+  if (bytes <= cur) return cudaSuccess;  // never lower the limit below a size launched before
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess) cur = bytes;
   return e;

@@ -144,7 +144,7 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       if (c > 0) {
         std::vector<int> nb;
         for (int j : ids) {
-          nb.push_back(std::min(spmv_grid<TV>(hs[j]->ntiles, kw), (hs[j]->ntiles + kMinTiles - 1) / kMinTiles));
+          nb.push_back(std::min(spmv_grid<TV>(hs[j]->ntiles, kw, false), (hs[j]->ntiles + kMinTiles - 1) / kMinTiles));
           part_need[j] = std::max(part_need[j], (size_t)nb.back() * (kMaxWindow + 1));
         }
         HostWave w{W_SPMV};

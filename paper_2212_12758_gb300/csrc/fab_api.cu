@@ -556,42 +556,44 @@ int ensure_ws(fab_handle* h, const fab_params* p, Ws& ws) {
   return FAB_OK;
 }
 
-// exp(M) e_1 into c; M (ld m) is overwritten. Scaling and squaring (Moler and Van
-// Loan) with the Taylor polynomial T_18 of degree 18: X = M / 2^sq with ||X||_1 <= 1,
-// exp(M) = (T_18(X))^(2^sq). The truncation is at most e / 19! < 3e-17 in the 1-norm
-// for ||X||_1 <= 1. T_18 is evaluated by Paterson and Stockmeyer's scheme in powers
-// of X^4 (7 matrix products, no linear solve): every step is a many-block GEMM or an
-// elementwise combination, where a Pade approximant needs a pivoted LU solve whose
-// m pivot steps are sequential.
+// exp(M) e_1 into c; M (ld m) is overwritten. Scaling and squaring with the [13/13]
+// Pade approximant r_13 (Higham 2005): X = M / 2^sq with ||X||_1 <= theta_13, exp(M) =
+// (r_13(X))^(2^sq), r_13 = (V - U)^{-1} (V + U), U odd and V even in X, both formed from
+// X^2, X^4, X^6 (6 many-block GEMMs). The solve is the blocked cluster LU of the
+// Denman-Beavers path with an m-column substitution; the squarings are GEMMs.
 int expm_e1(Ws& ws, int m, const int* mdev, double* c, int* squarings, cudaStream_t s) {
-  double cf[19];
-  cf[0] = 1.0;
-  for (int j = 1; j <= 18; ++j) cf[j] = cf[j - 1] / j;  // 1 / j!
-  double *X = ws.mats[0], *X2 = ws.mats[1], *X3 = ws.mats[2], *X4 = ws.mats[3], *P = ws.mats[4], *Q = ws.mats[5];
+  const double* b = pade13_b();
+  double *X = ws.mats[0], *X2 = ws.mats[1], *X4 = ws.mats[2], *X6 = ws.mats[3], *T = ws.mats[4], *U = ws.mats[5],
+         *V = ws.mats[6], *R = ws.mats[7], *R2 = ws.mats[8];
   LK(PK_SMALL, launch_norm1(X, m, mdev, ws.scal + 10, s));
   CK(cudaMemcpyAsync(ws.hd, ws.scal + 10, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(wait_stream(s));
   const double nrm = ws.hd[0];
   if (!isfinite(nrm)) return FAB_ENUMERIC;
-  const int sq = nrm > 1.0 ? (int)ceil(log2(nrm)) : 0;
+  const int sq = nrm > kTheta13 ? (int)ceil(log2(nrm / kTheta13)) : 0;
   if (sq > 0) LK(PK_SMALL, launch_lincomb(X, X, nullptr, nullptr, nullptr, ldexp(1.0, -sq), 0, 0, 0, 0.0, m, mdev, m, s));
   LK(PK_SMALL, launch_gemm(X2, X, X, m, mdev, m, 1.0, 0.0, s));
-  LK(PK_SMALL, launch_gemm(X3, X2, X, m, mdev, m, 1.0, 0.0, s));
   LK(PK_SMALL, launch_gemm(X4, X2, X2, m, mdev, m, 1.0, 0.0, s));
-  // B_4 = c16 I + c17 X + c18 X^2; then Horner in X^4: B <- X^4 B + B_i, i = 3, 2, 1, 0,
-  // with B_i = c_{4i} I + c_{4i+1} X + c_{4i+2} X^2 + c_{4i+3} X^3
-  LK(PK_SMALL, launch_lincomb(P, X, X2, nullptr, nullptr, cf[17], cf[18], 0, 0, cf[16], m, mdev, m, s));
-  for (int i = 3; i >= 0; --i) {
-    LK(PK_SMALL, launch_gemm(Q, X4, P, m, mdev, m, 1.0, 0.0, s));
-    LK(PK_SMALL, launch_lincomb(Q, Q, X, X2, X3, 1.0, cf[4 * i + 1], cf[4 * i + 2], cf[4 * i + 3], cf[4 * i], m, mdev,
-                                m, s));
-    std::swap(P, Q);
-  }
+  LK(PK_SMALL, launch_gemm(X6, X4, X2, m, mdev, m, 1.0, 0.0, s));
+  // U = X (X^6 (b13 X^6 + b11 X^4 + b9 X^2) + b7 X^6 + b5 X^4 + b3 X^2 + b1 I)
+  LK(PK_SMALL, launch_lincomb(T, X6, X4, X2, nullptr, b[13], b[11], b[9], 0, 0.0, m, mdev, m, s));
+  LK(PK_SMALL, launch_gemm(R, X6, T, m, mdev, m, 1.0, 0.0, s));
+  LK(PK_SMALL, launch_lincomb(R, R, X6, X4, X2, 1.0, b[7], b[5], b[3], b[1], m, mdev, m, s));
+  LK(PK_SMALL, launch_gemm(U, X, R, m, mdev, m, 1.0, 0.0, s));
+  // V = X^6 (b12 X^6 + b10 X^4 + b8 X^2) + b6 X^6 + b4 X^4 + b2 X^2 + b0 I
+  LK(PK_SMALL, launch_lincomb(T, X6, X4, X2, nullptr, b[12], b[10], b[8], 0, 0.0, m, mdev, m, s));
+  LK(PK_SMALL, launch_gemm(V, X6, T, m, mdev, m, 1.0, 0.0, s));
+  LK(PK_SMALL, launch_lincomb(V, V, X6, X4, X2, 1.0, b[6], b[4], b[2], b[0], m, mdev, m, s));
+  // (V - U) R = V + U
+  LK(PK_SMALL, launch_lincomb(T, V, U, nullptr, nullptr, 1.0, -1.0, 0, 0, 0.0, m, mdev, m, s));
+  LK(PK_SMALL, launch_lincomb(R, V, U, nullptr, nullptr, 1.0, 1.0, 0, 0, 0.0, m, mdev, m, s));
+  LK(PK_SMALL, launch_lu_fast(T, m, mdev, m, ws.piv, ws.scal + 11, ws.st, s));
+  LK(PK_SMALL, launch_lu_solve(T, m, ws.piv, mdev, m, R, m, 0, s));
   for (int i = 0; i < sq; ++i) {
-    LK(PK_SMALL, launch_gemm(Q, P, P, m, mdev, m, 1.0, 0.0, s));
-    std::swap(P, Q);
+    LK(PK_SMALL, launch_gemm(R2, R, R, m, mdev, m, 1.0, 0.0, s));
+    std::swap(R, R2);
   }
-  CK(cudaMemcpyAsync(c, P, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(c, R, (size_t)m * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (squarings) *squarings = sq;
   return FAB_OK;
 }
@@ -1471,7 +1473,7 @@ extern "C" int fab_tune(fab_handle* h, int precision, int k, int* choice, void* 
   int rc = FAB_OK;
   for (int ri = 0; ri < 3 && rc == FAB_OK; ++ri)
     for (int ni = 0; ni < 3 && rc == FAB_OK; ++ni)
-      for (int stg = 1; stg >= 0 && rc == FAB_OK; --stg) {
+      for (int stg = 2; stg >= 0 && rc == FAB_OK; --stg) {
         rc = fab::build_tiles(h, rows_c[ri], nnz_c[ni], stg);
         if (rc != FAB_OK) break;
         float ms = 0.0f;
@@ -1587,7 +1589,8 @@ fab_handle* clone_for_workspace(const fab_handle* h) {
 }
 
 int build_tiles(fab_handle* h, int rows_max, int nnz_cap, int staged) {
-  if (!h || !h->h_rowptr || rows_max < 1 || rows_max > kThreads || nnz_cap < 1) return FAB_EINVAL;
+  if (!h || !h->h_rowptr || rows_max < 1 || rows_max > kThreads || nnz_cap < 1 || staged < 0 || staged > 2)
+    return FAB_EINVAL;
   const int* rp = h->h_rowptr;
   std::vector<int> t;
   t.reserve(h->n / 16 + 2);
@@ -1599,8 +1602,9 @@ int build_tiles(fab_handle* h, int rows_max, int nnz_cap, int staged) {
     // nonzero range within nnz_cap entries
     while (r1 < h->n && r1 - r0 < rows_max && ((rp[r1 + 1] + 3) & ~3) - (rp[r0] & ~3) <= nnz_cap) ++r1;
     // a tile cut by the nonzero cap keeps a power-of-two row count, so that
-    // 256 / rows lanes per row use every thread of the block
-    if (r1 < h->n && r1 - r0 < rows_max) {
+    // 256 / rows lanes per row use every thread of the block (not needed when
+    // the tile is processed by nonzeros)
+    if (staged != 2 && r1 < h->n && r1 - r0 < rows_max) {
       int R = 1;
       while (2 * R <= r1 - r0) R *= 2;
       r1 = r0 + R;
@@ -1623,7 +1627,7 @@ int build_tiles(fab_handle* h, int rows_max, int nnz_cap, int staged) {
   h->ntiles = (int)t.size() - 1;
   h->tile_rows = rows_max;
   h->tile_nnz = nnz_cap;
-  h->tile_staged = staged ? 1 : 0;
+  h->tile_staged = staged;
   return FAB_OK;
 }
 

@@ -371,7 +371,8 @@ struct Csr {
   const void* vals;   // FP64 values (FP64 path) or FP32 values (mixed path)
   const int* tiles;   // SpMV row tiles: tile t is rows tiles[t] .. tiles[t+1]-1 (<= 256 rows)
   int ntiles;
-  int staged;         // 1: stage a tile's nonzeros in shared memory by bulk copies when they fit
+  int staged;         // 1: stage a tile's nonzeros in shared memory by bulk copies when they fit;
+                      // 2: the same, and process tiles of many rows by nonzeros
 };
 constexpr int kSpmvCap = 2048;   // nonzeros per staged SpMV tile (FP64: vals 16 KB + colind 8 KB)
 constexpr int kSpmvStages = 2;   // staged tiles in flight per block (ring of shared-memory buffers)
@@ -471,7 +472,7 @@ struct Wave {
 };
 // Grid of the single-solve launch of each basis kernel (a batched solve uses the same).
 template <typename TV>
-int spmv_grid(int ntiles, int kw);
+int spmv_grid(int ntiles, int kw, bool seg);
 template <typename TV>
 int update_grid(int kind, int n, int nc, int s, size_t* smem);
 int combine_grid(int n);

@@ -219,11 +219,13 @@ class Matrix:
                                                                                 WHITEN))
         return (x, st) if stats else x
 
-    def set_tiling(self, rows_max: int = 256, nnz_cap: int = 2048, staged: bool = True):
-        _check(lib.fab_set_tiling(self._h, int(rows_max), int(nnz_cap), 1 if staged else 0), "fab_set_tiling")
+    def set_tiling(self, rows_max: int = 256, nnz_cap: int = 2048, staged: int = 1):
+        """staged: 0 direct loads, 1 (or True) staged tiles with a row per lane group,
+        2 staged tiles processed by nonzeros when they have many rows."""
+        _check(lib.fab_set_tiling(self._h, int(rows_max), int(nnz_cap), int(staged)), "fab_set_tiling")
 
     def set_fusion(self, on: bool = True):
-        """Allow (default) or forbid the one-pass basis steps of the FP32 basis."""
+        """Allow or forbid (the default) the one-pass basis steps of the FP32 basis."""
         _check(lib.fab_set_fusion(self._h, 1 if on else 0), "fab_set_fusion")
 
     def tune(self, precision: int = FP64, k: int = 2, stream=None):

@@ -105,6 +105,22 @@ def test_largest_krylov_dimension(fab, torch, method, N):
     assert _rel(x, ref.x) <= TOL
 
 
+@pytest.mark.parametrize("f,m", [(matfun.SQRT, 40), (matfun.SQRT, 200), (matfun.INVSQRT, 200), (matfun.EXP, 300)])
+def test_small_stage_past_the_staged_lu(fab, torch, f, m):
+    """The LU solves of Denman-Beavers and of the Pade approximant stage the factors in
+    shared memory for m <= 160 and read them from global memory above; one process runs
+    both sizes (m = 40 first), so a launch attribute set for the smaller must not
+    constrain the larger. Alg. 5, k = 2, on the 3D Laplacian 12^3."""
+    A = W.laplacian3d(12)
+    b = W.random_vector(A.n, 8)
+    k, t = 2, -0.05
+    ref = krylov.run(krylov.NOPROJ, W.to_scipy(A), b, m, k, f, None, t)
+    fe = {matfun.SQRT: fab.SQRT, matfun.INVSQRT: fab.INVSQRT, matfun.EXP: fab.EXP}[f]
+    x, st = _run(fab, torch, A, b, f=fe, t=t, m=m, k=k, method=krylov.NOPROJ)
+    assert st.m_used == m
+    assert _rel(x, ref.x) <= TOL
+
+
 @pytest.mark.parametrize("kind", [osk.SPARSE_SIGN, osk.SRHT])
 def test_largest_sketch_of_vectors(fab, torch, kind):
     """s = 4096, the largest sketch, on vectors with a wide dynamic range (n = 12345,

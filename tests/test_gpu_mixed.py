@@ -102,8 +102,9 @@ def test_mixed_precision_vs_fp64_oracle(fab, name, build, f, t, m, k, sk, s, met
     assert err <= tol
 
 
+@pytest.mark.parametrize("staged", [1, 2])
 @pytest.mark.parametrize("name,build,f,t,m,k,sk,s", [c for c in CASES if c[6] == osk.GAUSSIAN])
-def test_mixed_gaussian_stages(fab, name, build, f, t, m, k, sk, s):
+def test_mixed_gaussian_stages(fab, name, build, f, t, m, k, sk, s, staged):
     """Stage by stage on the GPU's own quantities, sketched_fast with the BF16 Gaussian
     sketch: (1) the FP32 basis satisfies the Arnoldi-like relation (eq. arnoldilike)
     within the componentwise rounding bound gamma (|A||V_m| + |V_{m+1}||H|) with
@@ -111,13 +112,15 @@ def test_mixed_gaussian_stages(fab, name, build, f, t, m, k, sk, s):
     (u_bf16^2 + 2 n u_32) |G| |V| entry by entry (the two-term BF16 split of each basis
     entry, FP32 accumulation of exact products over at most 2n terms); (3) the FP64 small stage
     (Remark after eq. sFOM: QR, y, f(Hhat) e_1) on the GPU's H and Theta V equals the
-    oracle's to 1e-12."""
+    oracle's to 1e-12. Both SpMV tile forms (a row per lane group; by nonzeros) are held
+    to the same componentwise bound."""
     import torch
 
     A = build()
     As = W.to_scipy(A)
     b = W.random_vector(A.n, 0)
     M = fab.Matrix.from_csr(A)
+    M.set_tiling(256, 2048, staged)
     p = fab.params(f=f, t=t, m=m, k=k, s=s, sketch=sk, seed=3, method=krylov.SKETCHED_FAST, precision=fab.MIXED)
     M.apply(torch.from_numpy(b).cuda(), p)
     ls, V = M.last_state(), M.last_basis()
@@ -134,3 +137,87 @@ def test_mixed_gaussian_stages(fab, name, build, f, t, m, k, sk, s):
     y, _, c, _ = krylov.sketch_solve_stage(ls.H, ls.SV, f, t)
     assert _rel(ls.y, y) <= 1e-12
     assert _rel(ls.coeffs, c) <= 1e-12
+
+
+def _golden_c3():
+    """The oracle's C3 solves and the rounding model's RMS at full size, as stored by
+    tests/golden/make_c3_reference.py."""
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c3_gauss.txt")
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        if parts[0] == "nnz":
+            out["nnz"] = int(parts[1])
+            continue
+        d = out.setdefault(parts[0], {"x": {}})
+        if parts[1] == "x":
+            d["x"][int(parts[2])] = float(parts[3])
+        elif parts[1] == "coeffs":
+            d["coeffs"] = np.array([float(v) for v in parts[2:]])
+        else:
+            d[parts[1]] = float(parts[2])
+    return out
+
+
+@pytest.fixture(scope="module")
+def c3_matrix():
+    return W.chung_lu_laplacian(4_000_000, seed=2)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("fname", ["invsqrt", "sqrt"])
+def test_c3_full_size_against_the_oracle(fab, c3_matrix, fname):
+    """The power-law graph workload at full size (n = 4M, nnz = 44M): m = 150, k = 2,
+    Gaussian sketch s = 600 on the tensor cores (two BF16 terms), FP32 basis, FP64 small
+    stage, sketched_fast. Against the FP64 oracle's f_m at the same m and sketch (stored:
+    1024 sampled rows of x and the coefficients), at 4 x the rounding model's RMS at this
+    size (stored with it); and stage by stage on the GPU's own quantities: the
+    Arnoldi-like relation on sampled rows, the sketch on sampled sketch rows, the FP64
+    small stage."""
+    import torch
+
+    A = c3_matrix
+    gold = _golden_c3()
+    assert gold["nnz"] == A.nnz
+    g = gold[fname]
+    f = matfun.INVSQRT if fname == "invsqrt" else matfun.SQRT
+    m, k, s = 150, 2, 600
+    b = W.random_vector(A.n, 0)
+    M = fab.Matrix.from_csr(A)
+    p = fab.params(f=f, t=1.0, m=m, k=k, s=s, sketch=fab.GAUSSIAN, seed=1, method=krylov.SKETCHED_FAST,
+                   precision=fab.MIXED)
+    x = M.apply(torch.from_numpy(b).cuda(), p).cpu().numpy()
+    ls = M.last_state()
+    idx = np.array(sorted(g["x"]))
+    xs = np.array([g["x"][i] for i in idx])
+    e_x, e_c = _rel(x[idx], xs), _rel(ls.coeffs, g["coeffs"])
+    bar = TAIL * g["model_rms"]
+    print(f"\nC3 {fname}: rel err vs FP64 oracle f_m {e_x:.3e} (sampled rows), {e_c:.3e} (coefficients); bar {bar:.3e}")
+    assert e_x <= bar and e_c <= bar
+    # stage by stage: the FP64 small stage on the GPU's H and sketch
+    y, _, c, _ = krylov.sketch_solve_stage(ls.H, ls.SV, f, 1.0)
+    assert _rel(ls.coeffs, c) <= 1e-10
+    # the relation A V_m = V_{m+1} H on sampled rows, within the FP32 componentwise bound
+    V = torch.empty((m + 1, A.n), dtype=torch.float64, device="cuda")
+    assert fab.lib.fab_last_basis(M._h, V.data_ptr(), 1) == 0
+    As = W.to_scipy(A)
+    rows = np.random.default_rng(1).choice(A.n, 64, replace=False)
+    gam_rows = (np.diff(As.indptr)[rows] + k + 2) * U32
+    A32 = As[rows].astype(np.float32).astype(np.float64)
+    cols = np.unique(A32.indices)
+    Vc = V[:, torch.from_numpy(cols).cuda()].cpu().numpy().T  # referenced rows of V
+    Vr = V[:, torch.from_numpy(rows).cuda()].cpu().numpy().T
+    A32c = A32[:, cols]
+    F = np.abs(A32c @ Vc[:, :m] - Vr @ ls.H)
+    B = gam_rows[:, None] * (abs(A32c) @ np.abs(Vc[:, :m]) + np.abs(Vr) @ np.abs(ls.H))
+    assert np.all(F <= B + 1e-300)
+    # the sketch on sampled sketch rows: within the two-term split and FP32 accumulation
+    qs = np.array([0, 1, 257, 599])
+    Gq = osk.gaussian_entries(s, A.n, 1, rows=qs, bf16=True)
+    Vh = V.cpu().numpy().T  # n x (m+1)
+    D = np.abs(ls.SV[qs] - Gq @ Vh)
+    assert np.all(D <= (U_BF16**2 + 2 * A.n * U32) * (np.abs(Gq) @ np.abs(Vh)))

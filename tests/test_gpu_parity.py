@@ -295,10 +295,13 @@ def test_c2_full_size_against_the_oracle(fab, torch):
 
 
 # ------------------------------------------------------- SpMV tilings
-@pytest.mark.parametrize("tiling", [(256, 2048, 1), (256, 2048, 0), (64, 512, 1), (16, 128, 1), (1, 2048, 1)])
+@pytest.mark.parametrize("tiling", [(256, 2048, 1), (256, 2048, 0), (64, 512, 1), (16, 128, 1), (1, 2048, 1),
+                                    (256, 2048, 2), (200, 1500, 2), (16, 128, 2)])
 def test_spmv_tilings_power_law_graph(fab, torch, tiling):
     """Every tiling (rows per tile, nonzeros per tile, staging) gives the oracle's result:
-    (1, ., .) puts the whole block on each row, (16, 128) mixes 16..256 lanes per row."""
+    (1, ., .) puts the whole block on each row, (16, 128) mixes 16..256 lanes per row;
+    staging 2 processes tiles of at least 32 rows by nonzeros (200 rows: tiles cut by the
+    nonzero cap keep any row count), and tiles of fewer rows by lanes."""
     A = W.chung_lu_laplacian(20000, seed=2)
     b = W.random_vector(A.n, 0)
     m, k, s = 30, 2, 120
@@ -307,6 +310,47 @@ def test_spmv_tilings_power_law_graph(fab, torch, tiling):
     M = fab.Matrix.from_csr(A)
     M.set_tiling(*tiling)
     x = M.apply(b, fab.params(f=fab.INVSQRT, m=m, k=k, s=s, sketch=fab.SRHT, seed=1))
+    assert _rel(x, ref.x) <= TOL
+
+
+def _uneven_rows(n, seed):
+    """Rows of 0..60 nonzeros (one in eight empty, a few of 300) at random columns,
+    with a dominant diagonal on the non-empty rows; CSR with sorted columns."""
+    rng = np.random.default_rng(seed)
+    lens = rng.integers(1, 61, n)
+    lens[rng.random(n) < 0.125] = 0
+    lens[rng.choice(n, 5, replace=False)] = 300
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=rowptr[1:])
+    cols, vals = [], []
+    for i, L in enumerate(lens):
+        if L == 0:
+            continue
+        c = np.sort(rng.choice(n, L, replace=False))
+        v = rng.standard_normal(L) / np.sqrt(L)
+        if i not in c:
+            c[0] = i
+            c = np.sort(c)
+        v[np.searchsorted(c, i)] = 3.0
+        cols.append(c)
+        vals.append(v)
+    return W.CSR(n=n, rowptr=rowptr, colind=np.concatenate(cols).astype(np.int32), vals=np.concatenate(vals))
+
+
+@pytest.mark.parametrize("tiling", [(256, 2048, 2), (97, 700, 2), (256, 2048, 1)])
+@pytest.mark.parametrize("k", [1, 3])
+def test_nonzero_parallel_tiles_empty_and_long_rows(fab, torch, tiling, k):
+    """Tiles processed by nonzeros with empty rows (their sums are 0), rows spread over
+    many threads (a row of 300 nonzeros in a staged tile) and rows cut at thread and tile
+    boundaries: sketched_fast against the oracle at 1e-10."""
+    A = _uneven_rows(6000, 12)
+    b = W.random_vector(A.n, 3)
+    m, s = 25, 100
+    th = osk.make(osk.SPARSE_SIGN, A.n, s, 2, 8)
+    ref = krylov.run(krylov.SKETCHED_FAST, W.to_scipy(A), b, m, k, matfun.EXP, th, -0.2)
+    M = fab.Matrix.from_csr(A)
+    M.set_tiling(*tiling)
+    x = M.apply(b, fab.params(f=fab.EXP, t=-0.2, m=m, k=k, s=s, sketch=fab.SPARSE_SIGN, zeta=8, seed=2))
     assert _rel(x, ref.x) <= TOL
 
 
@@ -329,7 +373,7 @@ def test_dense_rows_and_autotune(fab, torch):
     x = M.apply(b, fab.params(f=fab.EXP, t=-0.05, m=m, k=k, method=fab.NOPROJ))
     assert _rel(x, ref.x) <= TOL
     choice = M.tune(fab.FP64, k=k)
-    assert choice[0] in (256, 128, 64) and choice[1] in (2048, 1024, 512) and choice[2] in (0, 1)
+    assert choice[0] in (256, 128, 64) and choice[1] in (2048, 1024, 512) and choice[2] in (0, 1, 2)
     x2 = M.apply(b, fab.params(f=fab.EXP, t=-0.05, m=m, k=k, method=fab.NOPROJ))
     assert _rel(x2, ref.x) <= TOL
     with pytest.raises(fab.FabError) as e:
@@ -441,3 +485,31 @@ def test_skew_convdiff_exp_all_methods(fab, torch, method):
     _, x, _ = _run_gpu(fab, torch, A, b, f=fab.EXP, t=t, m=m, k=k, s=s, sketch=fab.SRHT, seed=1, method=method,
                        lsqr_tol=1e-14)
     assert _rel(x, ref.x) <= TOL
+
+
+# ------------------------------------------- exp(t H) e_1: Pade [13/13] scaling
+@pytest.mark.parametrize("method", [krylov.NOPROJ, krylov.SKETCHED_FAST])
+@pytest.mark.parametrize("t", [-1e-4, -3e-3, -2e-2])
+def test_exp_pade_scaling_across_norms(fab, torch, method, t):
+    """exp(t Hhat) e_1 by scaling and squaring with the [13/13] Pade approximant: for
+    ||t Hhat||_1 from 0.9 (no squaring) to 238 (6 squarings), the solve matches
+    the oracle (scipy's expm, a different scaling-and-squaring scheme) at 1e-10, and the
+    number of squarings is the smallest sq with ||t Hhat||_1 / 2^sq <= theta_13 (Higham
+    2005), computed from the oracle's Hhat."""
+    A = W.convdiff(2, 30)
+    b = W.random_vector(A.n, 4)
+    m, k, s = 30, 4, 120
+    th = osk.make(osk.SRHT, A.n, s, 2, 8) if method == krylov.SKETCHED_FAST else None
+    ref = krylov.run(method, W.to_scipy(A), b, m, k, matfun.EXP, th, t)
+    M = fab.Matrix.from_csr(A)
+    meth = fab.NOPROJ if method == krylov.NOPROJ else fab.SKETCHED_FAST
+    x, st = M.apply(torch.from_numpy(b).cuda(), fab.params(f=fab.EXP, t=t, m=m, k=k, s=s, sketch=fab.SRHT, seed=2,
+                                                        method=meth), stats=True)
+    assert _rel(x.cpu().numpy(), ref.x) <= TOL
+    theta13 = 5.371920351148152
+    nrm = float(np.abs(t * ref.Hhat).sum(axis=0).max())
+    ratio = math.log2(nrm / theta13) if nrm > theta13 else 0.0
+    if abs(ratio - round(ratio)) > 1e-6:  # away from a power-of-two boundary
+        assert st.fh_iters == max(0, math.ceil(ratio))
+    if t == -2e-2:
+        assert st.fh_iters >= 4
