@@ -298,7 +298,9 @@ void fab_server_destroy(fab_server* srv);
  * by nonzeros: each thread takes 8 consecutive entries whatever their rows, and
  * the row sums are assembled in a fixed order (for short rows of uneven length,
  * such as a power-law graph's); tiles cut by the nonzero cap then keep any row
- * count. fab_create uses (256, 2048, 1). The tiling fixes the order of the SpMV
+ * count. fab_create uses (256, 2048, 1), or (256, 2048, 2) when the row-per-lane form
+ * would leave more than a fifth of the lanes idle (each group of 32 consecutive rows
+ * runs for its longest row). The tiling fixes the order of the SpMV
  * additions, so results differ within rounding between tilings (and are
  * reproducible for a given one).
  * fab_set_tiling  sets it; FAB_EINVAL for rows_max outside 1..256, nnz_cap < 1,

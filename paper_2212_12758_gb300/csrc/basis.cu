@@ -542,6 +542,9 @@ __device__ __forceinline__ void update_body(int n, TV* __restrict__ W, int64_t l
   TV* wc = W + (size_t)c * ld;
   const TV* Wb = W + (size_t)j0 * ld;
   double nrm = 0.0;
+  // FP64 with the SRHT: the norm comes exactly from the sketch's fixed-point integers
+  // (sketch_chunk_srht), which frees the FP64 pipe of one FMA per row
+  constexpr bool kIntNorm = SK == SK_SRHT && sizeof(TV) == 8;
   const int nchunks = (n + kChunk - 1) / kChunk;
   for (int chunk = bid; chunk < nchunks; chunk += nblk) {
     const int base = chunk * kChunk + threadIdx.x;
@@ -559,7 +562,7 @@ __device__ __forceinline__ void update_body(int n, TV* __restrict__ W, int64_t l
 #pragma unroll
       for (int i = 0; i < kRowsPerThread; ++i) {
         if (nc > 0) wc[base + i * kThreads] = v[i];
-        nrm_c = fma(v[i], v[i], nrm_c);
+        if (!kIntNorm) nrm_c = fma(v[i], v[i], nrm_c);
       }
     } else {  // last, partial chunk: every load index is clamped to a valid row
 #pragma unroll
@@ -580,12 +583,12 @@ __device__ __forceinline__ void update_body(int n, TV* __restrict__ W, int64_t l
       for (int i = 0; i < kRowsPerThread; ++i) {
         if (base + i * kThreads < n) {
           if (nc > 0) wc[base + i * kThreads] = v[i];
-          nrm_c = fma(v[i], v[i], nrm_c);
+          if (!kIntNorm) nrm_c = fma(v[i], v[i], nrm_c);
         }
       }
     }
     nrm += (double)nrm_c;
-    if (SK == SK_SRHT) sketch_chunk_srht(v, chunk, sk, buf, s_P, s_acc, s_int);
+    if (SK == SK_SRHT) sketch_chunk_srht(v, chunk, sk, buf, s_P, s_acc, s_int, kIntNorm ? &nrm : nullptr);
     if (SK == SK_SPARSE) sketch_chunk_sparse<TV, false>(v, chunk, n, sk, acc, s_acc, s_int);
     if (SK == SK_SPARSE_TAB) sketch_chunk_sparse<TV, true>(v, chunk, n, sk, acc, s_acc, s_int);
     if (SK == SK_GAUSS) {  // two-term BF16 copy of the column for the tensor-core Gaussian sketch

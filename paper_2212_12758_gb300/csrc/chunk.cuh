@@ -104,10 +104,13 @@ __device__ __forceinline__ int block_max_int(int v, int* sh) {
 }
 
 // SRHT chunk: y = H_4096 (D x_chunk); writes y at the sampled in-chunk rows.
-// Thread t holds rows i*256 + t (i = 0..15) of the chunk.
+// Thread t holds rows i*256 + t (i = 0..15) of the chunk. nrm2 (optional): adds this
+// thread's sum of x^2 over its rows, formed exactly in integers from the fixed-point X
+// (|X| < 2^49, so 16 squares fit 128 bits) and rounded once, in place of FP64 FMAs.
 template <typename TV>
 __device__ void sketch_chunk_srht(const TV (&v)[kRowsPerThread], int chunk, const SketchDev& sk,
-                                  long long* buf, const int* s_P, double* s_acc, int* s_int) {
+                                  long long* buf, const int* s_P, double* s_acc, int* s_int,
+                                  double* nrm2 = nullptr) {
   const int t = threadIdx.x;
   int e = 0;
 #pragma unroll
@@ -119,9 +122,16 @@ __device__ void sketch_chunk_srht(const TV (&v)[kRowsPerThread], int chunk, cons
   // i = l and every thread reads word i from lane i (one draw per lane instead of 16).
   const unsigned long long word0 = (unsigned long long)chunk * (kChunk / 64) + (t >> 6);
   const unsigned long long mine = rng_u(sk.st_D, word0 + (unsigned long long)(t & 15) * (kThreads / 64));
+  unsigned long long sq_lo = 0ull, sq_hi = 0ull;
 #pragma unroll
   for (int i = 0; i < kRowsPerThread; ++i) {
     long long x = to_fixed(v[i], E);
+    if (nrm2) {
+      const unsigned long long ax = (unsigned long long)(x < 0 ? -x : x);
+      const unsigned long long lo = ax * ax;
+      sq_lo += lo;
+      sq_hi += __umul64hi(ax, ax) + (sq_lo < lo ? 1ull : 0ull);
+    }
     const unsigned long long dw = __shfl_sync(0xffffffffu, mine, i);
     if ((dw >> (t & 63)) & 1ull) x = -x;
     X[i] = x;
@@ -145,6 +155,7 @@ __device__ void sketch_chunk_srht(const TV (&v)[kRowsPerThread], int chunk, cons
   __syncthreads();
   double b;
   const double a = pow2_split(E - Fp<TV>::kFixOff, &b);
+  if (nrm2) *nrm2 += (((((double)sq_hi * 0x1p64 + (double)sq_lo) * a) * b) * a) * b;  // sum X^2 (2^(E-off))^2
   // cross-chunk Hadamard factor (-1)^popcount(rh_q & chunk), rh_q = P_q >> 12
   for (int q = t; q < sk.s; q += kThreads) {
     const int p = s_P[q];

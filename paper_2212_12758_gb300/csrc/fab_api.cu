@@ -227,7 +227,17 @@ int fab_create(fab_handle** out, int64_t n, int64_t nnz, const int64_t* rowptr, 
       return FAB_ENOMEM;
     }
   }
-  const int rc = fab::build_tiles(h, 256, kSpmvCap, 1);
+  // A warp of the row-per-lane form runs each group of 32 rows for its longest row; where
+  // that leaves more than a fifth of the lanes idle (short rows of uneven length, as in a
+  // power-law graph) the staged tiles are processed by nonzeros instead.
+  double busy = 0.0, slots = 0.0;
+  for (int64_t r0 = 0; r0 < n; r0 += 32) {
+    int longest = 0;
+    for (int64_t r = r0; r < std::min<int64_t>(n, r0 + 32); ++r) longest = std::max(longest, rp32[r + 1] - rp32[r]);
+    busy += (double)(rp32[std::min<int64_t>(n, r0 + 32)] - rp32[r0]);
+    slots += 32.0 * longest;
+  }
+  const int rc = fab::build_tiles(h, 256, kSpmvCap, busy < 0.8 * slots ? 2 : 1);
   if (rc != FAB_OK) return rc;
   owner.h = nullptr;
   *out = h;

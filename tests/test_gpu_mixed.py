@@ -177,7 +177,10 @@ def test_c3_full_size_against_the_oracle(fab, c3_matrix, fname):
     1024 sampled rows of x and the coefficients), at 4 x the rounding model's RMS at this
     size (stored with it); and stage by stage on the GPU's own quantities: the
     Arnoldi-like relation on sampled rows, the sketch on sampled sketch rows, the FP64
-    small stage."""
+    small stage. The coefficient vector c (x = ||b|| V_m c) is printed, not held to the
+    bar: the basis is far from orthogonal (the condition estimate of its sketch is
+    printed), so rounding moves c by up to kappa times what it moves x, and the model's
+    RMS is of x."""
     import torch
 
     A = c3_matrix
@@ -190,14 +193,16 @@ def test_c3_full_size_against_the_oracle(fab, c3_matrix, fname):
     M = fab.Matrix.from_csr(A)
     p = fab.params(f=f, t=1.0, m=m, k=k, s=s, sketch=fab.GAUSSIAN, seed=1, method=krylov.SKETCHED_FAST,
                    precision=fab.MIXED)
-    x = M.apply(torch.from_numpy(b).cuda(), p).cpu().numpy()
+    x, st = M.apply(torch.from_numpy(b).cuda(), p, stats=True)
+    x = x.cpu().numpy()
     ls = M.last_state()
     idx = np.array(sorted(g["x"]))
     xs = np.array([g["x"][i] for i in idx])
     e_x, e_c = _rel(x[idx], xs), _rel(ls.coeffs, g["coeffs"])
     bar = TAIL * g["model_rms"]
-    print(f"\nC3 {fname}: rel err vs FP64 oracle f_m {e_x:.3e} (sampled rows), {e_c:.3e} (coefficients); bar {bar:.3e}")
-    assert e_x <= bar and e_c <= bar
+    print(f"\nC3 {fname}: rel err vs FP64 oracle f_m {e_x:.3e} (sampled rows), {e_c:.3e} (coefficients); bar {bar:.3e}; "
+          f"kappa estimate of the sketched basis {st.kappa_est:.3e}")
+    assert e_x <= bar
     # stage by stage: the FP64 small stage on the GPU's H and sketch
     y, _, c, _ = krylov.sketch_solve_stage(ls.H, ls.SV, f, 1.0)
     assert _rel(ls.coeffs, c) <= 1e-10
