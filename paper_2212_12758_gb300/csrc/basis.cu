@@ -588,7 +588,7 @@ __device__ __forceinline__ void update_body(int n, TV* __restrict__ W, int64_t l
       }
     }
     nrm += (double)nrm_c;
-    if (SK == SK_SRHT) sketch_chunk_srht(v, chunk, sk, buf, s_P, s_acc, s_int, kIntNorm ? &nrm : nullptr);
+    if (SK == SK_SRHT) sketch_chunk_srht<TV, true>(v, chunk, sk, buf, s_P, s_acc, s_int, kIntNorm ? &nrm : nullptr);
     if (SK == SK_SPARSE) sketch_chunk_sparse<TV, false>(v, chunk, n, sk, acc, s_acc, s_int);
     if (SK == SK_SPARSE_TAB) sketch_chunk_sparse<TV, true>(v, chunk, n, sk, acc, s_acc, s_int);
     if (SK == SK_GAUSS) {  // two-term BF16 copy of the column for the tensor-core Gaussian sketch

@@ -92,14 +92,16 @@ __device__ __forceinline__ void wht16(long long (&X)[16]) {
   }
 }
 
-// Block maximum of an int (all threads receive it).
-__device__ __forceinline__ int block_max_int(int v, int* sh) {
+// Block maximum of an int (all threads receive it). reuse_barrier = false leaves out
+// the barrier that protects sh from the next call: for callers that pass a block
+// barrier of their own before calling again.
+__device__ __forceinline__ int block_max_int(int v, int* sh, bool reuse_barrier = true) {
   v = (int)__reduce_max_sync(0xffffffffu, (unsigned)v);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
   int m = 0;
   for (int w = 0; w < kThreads / 32; ++w) m = max(m, sh[w]);
-  __syncthreads();
+  if (reuse_barrier) __syncthreads();
   return m;
 }
 
@@ -107,7 +109,11 @@ __device__ __forceinline__ int block_max_int(int v, int* sh) {
 // Thread t holds rows i*256 + t (i = 0..15) of the chunk. nrm2 (optional): adds this
 // thread's sum of x^2 over its rows, formed exactly in integers from the fixed-point X
 // (|X| < 2^49, so 16 squares fit 128 bits) and rounded once, in place of FP64 FMAs.
-template <typename TV>
+// kLean: two block barriers fewer per chunk, for a caller that calls it chunk after
+// chunk and reads s_acc[q] only from thread q mod 256: s_int is read before the
+// barrier that precedes the first write of buf, and buf is not written again before the
+// next chunk's first barrier, which every thread reaches only after its reads of buf.
+template <typename TV, bool kLean = false>
 __device__ void sketch_chunk_srht(const TV (&v)[kRowsPerThread], int chunk, const SketchDev& sk,
                                   long long* buf, const int* s_P, double* s_acc, int* s_int,
                                   double* nrm2 = nullptr) {
@@ -115,7 +121,7 @@ __device__ void sketch_chunk_srht(const TV (&v)[kRowsPerThread], int chunk, cons
   int e = 0;
 #pragma unroll
   for (int i = 0; i < kRowsPerThread; ++i) e = max(e, exp_field(v[i]));
-  const int E = block_max_int(e, s_int);
+  const int E = block_max_int(e, s_int, !kLean);
   long long X[16];
   // D's signs: row i*256 + t takes bit (t mod 64) of word chunk*64 + t/64 + 4i. The 32
   // threads of a warp share t/64, so the warp needs 16 words: lane l < 16 draws the word of
@@ -162,7 +168,7 @@ __device__ void sketch_chunk_srht(const TV (&v)[kRowsPerThread], int chunk, cons
     const double yq = ((double)buf[pidx(p & (kChunk - 1))] * a) * b;
     s_acc[q] += (__popc((p >> kChunkLog2) & chunk) & 1) ? -yq : yq;
   }
-  __syncthreads();
+  if (!kLean) __syncthreads();
 }
 
 // The zeta distinct sketch rows of column j (R9): candidates floor(h s / 2^32)
