@@ -341,17 +341,18 @@ int fab_tune(fab_handle* h, int precision, int k, int* choice, void* stream);
 
 /*
  * Batched solves: many f(A)b of uneven size (different matrices, n, m, k, s, f)
- * as one CUDA graph. Work items are (solve, basis step, tile): for each basis
- * step c the graph holds one launch per (window k, sketch kind) group covering
- * every solve still building its basis (SpMV + window dots, window update +
- * norm + fused sketch, sketch reduce: Alg. 2 with the sketch of §2.1.1). A
- * solve's SpMV tiles are grouped at least 8 to a block (a batched solve shares
- * the GPU), so its results equal fab_apply's up to the grouping of partial
- * sums (same kernels, same tiles, same sketch). When a solve's
- * basis is complete, its small stage (Householder QR of the sketch, the
- * sketch-and-solve projection of eq. sFOM, or none for Alg. 5; f(H)e_1 by
- * Pade scaling and squaring or Denman-Beavers) runs as one CTA on a second
- * branch of the graph, then its combine x = ||b|| V_m c.
+ * as one CUDA graph of three kernels. The basis build of every solve (Alg. 2 with
+ * the sketch of §2.1.1: per step the SpMV + window dots, then the window update +
+ * norm + fused sketch; the sketch's partials are reduced once per solve at the end)
+ * is one persistent launch: its blocks claim work items (one block's share of one
+ * phase of one solve) in plan order from a device counter and wait, with a bounded
+ * wait, only for their own solve's previous phase. A solve's SpMV tiles are grouped
+ * at least 32 to a block (a batched solve shares the GPU), so its results equal
+ * fab_apply's up to the grouping of partial sums (same bodies, same tiles, same
+ * sketch). Then one launch runs every solve's small stage as one CTA (Householder
+ * QR of the sketch, the sketch-and-solve projection of eq. sFOM, or none for Alg.
+ * 5; f(H)e_1 by Pade scaling and squaring or Denman-Beavers) and one the combines
+ * x = ||b|| V_m c. A solve whose phase wait expires reports FAB_ETIMEOUT.
  *
  * fab_batch_create  plans `count` solves (hs[i], ps[i]) and allocates every
  *                   workspace at once (one device allocation; FAB_ENOMEM if it

@@ -83,7 +83,16 @@ constexpr int kSegRows = 32;
 // The work of block `bid` of `nblk` (a launch of its own, or one solve's share
 // of a batched wave) is a function of (bid, nblk) only, so a solve gives the
 // same bits whichever way its blocks are launched.
-template <typename TV, int KW, bool SEG = false>
+// Loads of the basis columns: through the read-only path, or (kCoh) through L1 with
+// the coherence an acquire gives, for a kernel that reads columns its other blocks
+// wrote earlier in the same launch (the persistent batch kernel).
+template <bool kCoh, typename TV>
+__device__ __forceinline__ TV ld_col(const TV* p) {
+  if constexpr (kCoh) return *p;
+  else return __ldg(p);
+}
+
+template <typename TV, int KW, bool SEG = false, bool kCoh = false>
 __device__ __forceinline__ void spmv_dots_body(
     const Csr& A, TV* __restrict__ W, int64_t ld, int c, int j0, int kw, const ColScale& cs, double* __restrict__ H,
     int ldh, double* __restrict__ coef, double* __restrict__ part, unsigned* __restrict__ counter, DevState* st,
@@ -245,7 +254,7 @@ __device__ __forceinline__ void spmv_dots_body(
             for (int u = 0; u < 8; u += 2) *reinterpret_cast<double2*>(av + u) = *reinterpret_cast<const double2*>(sv + u);
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) g[u] = (a + u >= lo && a + u < hi) ? __ldg(vin + ci[u]) : (TV)0;
+          for (int u = 0; u < 8; ++u) g[u] = (a + u >= lo && a + u < hi) ? ld_col<kCoh>(vin + ci[u]) : (TV)0;
           // the row of the first entry in the tile: the last row starting at or before it
           const int first = a > lo ? a : lo;
           int row = 0, top = nr;
@@ -300,7 +309,7 @@ __device__ __forceinline__ void spmv_dots_body(
         for (; e + 7 * L < e1; e += 8 * L) {  // eight gathers in flight per thread
           TV g[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) g[u] = __ldg(vin + sc[e + u * L]);
+          for (int u = 0; u < 8; ++u) g[u] = ld_col<kCoh>(vin + sc[e + u * L]);
 #pragma unroll
           for (int u = 0; u < 8; ++u) y = fma(sv[e + u * L], g[u], y);
         }
@@ -308,7 +317,7 @@ __device__ __forceinline__ void spmv_dots_body(
           const int rem = (e1 - e + L - 1) >> lgL;
           TV g[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) g[u] = __ldg(vin + sc[min(e + u * L, e1 - 1)]);
+          for (int u = 0; u < 8; ++u) g[u] = ld_col<kCoh>(vin + sc[min(e + u * L, e1 - 1)]);
 #pragma unroll
           for (int u = 0; u < 8; ++u)
             if (u < rem) y = fma(sv[e + u * L], g[u], y);
@@ -323,11 +332,11 @@ __device__ __forceinline__ void spmv_dots_body(
             av[u] = __ldg(Avals + e + u * L);
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) g[u] = __ldg(vin + cidx[u]);
+          for (int u = 0; u < 8; ++u) g[u] = ld_col<kCoh>(vin + cidx[u]);
 #pragma unroll
           for (int u = 0; u < 8; ++u) y = fma(av[u], g[u], y);
         }
-        for (; e < e1; e += L) y = fma(__ldg(Avals + e), __ldg(vin + __ldg(A.colind + e)), y);
+        for (; e < e1; e += L) y = fma(__ldg(Avals + e), ld_col<kCoh>(vin + __ldg(A.colind + e)), y);
       }
     }
     if (L > 1) {  // block-uniform branch: combine the lanes of each row
@@ -1076,10 +1085,9 @@ cudaError_t launch_to_f32(int n, const double* x, float* y, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------- batched waves
-// Each wave kernel finds its solve by a binary search of the wave's block
-// prefix and runs that solve's body with the solve's own (bid, nblk), so every
-// solve of a batch computes exactly what its own launches would.
+// ---------------------------------------------------------- batched basis
+// A wave lists solves and their blocks: job ids[i] owns blocks pre[i] ..
+// pre[i+1]-1 (its own launch's grid). wave_slot finds the entry of block b.
 __device__ __forceinline__ int wave_slot(const Wave& w, int b) {
   int lo = 0, hi = w.count - 1;
   while (lo < hi) {
@@ -1091,10 +1099,7 @@ __device__ __forceinline__ int wave_slot(const Wave& w, int b) {
 
 // state reset, counters, H = 0, W_0 = b (FP64 -> TV)
 template <typename TV>
-__global__ void k_init_wave(const BasisJob<TV>* __restrict__ jobs, Wave w) {
-  const int i = wave_slot(w, blockIdx.x);
-  const BasisJob<TV>* J = jobs + w.ids[i];
-  const int bid = blockIdx.x - w.pre[i], nblk = w.pre[i + 1] - w.pre[i];
+__device__ __forceinline__ void init_body(const BasisJob<TV>* J, int bid, int nblk) {
   const int n = J->A.n, m = J->m;
   if (bid == 0 && threadIdx.x == 0) {
     DevState* st = J->st;
@@ -1113,36 +1118,188 @@ __global__ void k_init_wave(const BasisJob<TV>* __restrict__ jobs, Wave w) {
   for (int r = bid * blockDim.x + threadIdx.x; r < n; r += nblk * blockDim.x) J->W[r] = (TV)J->b[r];
 }
 
-template <typename TV, int KW>
-__global__ __launch_bounds__(kThreads) void k_spmv_wave(const BasisJob<TV>* __restrict__ jobs, Wave w, int c) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int i = wave_slot(w, blockIdx.x);
-  const BasisJob<TV>* J = jobs + w.ids[i];
-  const Csr A = J->A;
-  const ColScale cs = J->cs;
-  spmv_dots_body<TV, KW>(A, J->W, J->ld, c, c - KW, KW, cs, J->H, J->ldh, J->coef, J->part, J->counter,
-                         J->st, blockIdx.x - w.pre[i], w.pre[i + 1] - w.pre[i], smem_raw);
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <int SK, typename TV>
-__global__ __launch_bounds__(kThreads, SK == SK_SPARSE ? 2 : 3) void k_update_wave(
-    const BasisJob<TV>* __restrict__ jobs, Wave w, int c, int nc, int mode) {
-  extern __shared__ __align__(16) unsigned char smem_upd[];
-  const int i = wave_slot(w, blockIdx.x);
-  const BasisJob<TV>* J = jobs + w.ids[i];
+// The phase bodies of the persistent kernel are separate (not inlined) functions, so
+// that each keeps the register allocation of its own kernel instead of sharing one
+// allocation with every other phase.
+template <typename TV, int KW>
+__device__ __noinline__ void spmv_phase_kw(const BasisJob<TV>* J, int c, int bid, int nblk, unsigned char* smem) {
+  const Csr A = J->A;
   const ColScale cs = J->cs;
-  const SketchDev sk = J->sk;
-  update_body<SK, TV>(J->A.n, J->W, J->ld, c, c - nc, nc, J->coef, J->H, J->ldh, cs, mode, J->part,
-                      J->counter, sk, J->st, blockIdx.x - w.pre[i], w.pre[i + 1] - w.pre[i], smem_upd);
+  spmv_dots_body<TV, KW, false, true>(A, J->W, J->ld, c, c - KW, KW, cs, J->H, J->ldh, J->coef, J->part,
+                                      J->counter, J->st, bid, nblk, smem);
+}
+
+// The SpMV + window-dot body for the window width of the phase (kw <= KMAX).
+template <typename TV, int KW, int KMAX>
+__device__ __forceinline__ void spmv_phase(int kw, const BasisJob<TV>* J, int c, int bid, int nblk,
+                                           unsigned char* smem) {
+  if constexpr (KW <= KMAX) {
+    if (kw == KW) {
+      spmv_phase_kw<TV, KW>(J, c, bid, nblk, smem);
+      return;
+    }
+    spmv_phase<TV, KW + 1, KMAX>(kw, J, c, bid, nblk, smem);
+  }
 }
 
 template <typename TV>
-__global__ void k_sketch_reduce_wave(const BasisJob<TV>* __restrict__ jobs, Wave w, int c) {
-  const int i = wave_slot(w, blockIdx.x);
-  const BasisJob<TV>* J = jobs + w.ids[i];
-  const SketchDev sk = J->sk;
-  sketch_reduce_body(sk, w.aux[i], J->cs.sigma, c, J->sk_scale, J->SV + (size_t)c * sk.s, J->st,
-                     blockIdx.x - w.pre[i]);
+__device__ __noinline__ void init_phase(const BasisJob<TV>* J, int bid, int nblk) {
+  init_body<TV>(J, bid, nblk);
+}
+
+// Theta V of every column of a solve from its kept partials (a warp per entry; the
+// columns the basis reached: all below m_used, and m_used itself unless it broke down).
+template <typename TV>
+__device__ __noinline__ void reduce_phase(const BasisJob<TV>* J, int nparts, int bid, int nblk) {
+  const SketchDev& sk = J->sk;
+  const int lane = threadIdx.x & 31;
+  const DevState* st = J->st;
+  const int mu = st->m_used;
+  const long long nw = (long long)nblk * (blockDim.x >> 5), entries = (long long)(J->m + 1) * sk.s;
+  for (long long wid = ((long long)bid * blockDim.x + threadIdx.x) >> 5; wid < entries; wid += nw) {
+    const int col = (int)(wid / sk.s), q = (int)(wid % sk.s);
+    if (!(col < mu || (col == mu && !st->stop))) continue;  // warp-uniform
+    const double* part = sk.part + (size_t)col * J->sk_colstride;
+    double a = 0.0;
+    for (int b = lane; b < nparts; b += 32) a += part[(size_t)b * sk.s + q];
+    a = warp_sum(a);
+    if (lane == 0) J->SV[(size_t)col * sk.s + q] = a * J->sk_scale * J->cs.sigma[col];
+  }
+}
+
+template <int SK, typename TV>
+__device__ __noinline__ void update_phase(const BasisJob<TV>* J, int c, int nc, int mode, int bid, int nblk,
+                                          unsigned char* smem) {
+  const ColScale cs = J->cs;
+  SketchDev sk = J->sk;
+  sk.part += (size_t)c * J->sk_colstride;  // this column's partials are kept
+  update_body<SK, TV>(J->A.n, J->W, J->ld, c, c - nc, nc, J->coef, J->H, J->ldh, cs, mode, J->part, J->counter, sk,
+                      J->st, bid, nblk, smem);
+}
+
+// The whole basis build of a batch in one persistent launch. The plan lists the
+// phases of the former per-step launches in order (start, then for every step the
+// SpMV + window dots, the window update + norm + fused sketch, and the sketch
+// reduce; Alg. 2 with the sketch of §2.1.1); a work item is one block of one solve in
+// one phase, and items are numbered in plan order. Each block of this kernel claims
+// the next item number from a global ticket, waits (bounded) until its solve has
+// completed the phase before (a per-solve counter, released by the block that ends
+// that phase and acquired here), runs the phase's body with the solve's own (bid,
+// nblk), and counts itself done. An item waits only on items with smaller numbers,
+// which were all claimed before it by running blocks, so the launch completes
+// whether or not all its blocks are resident at once. Every solve computes exactly
+// what its own launches compute. Columns written by other blocks of this launch are
+// read through L1 after the acquire (ld_col<true>), not through the read-only path.
+template <typename TV, int KMAX>
+__global__ __launch_bounds__(kThreads, 4) void k_batch_basis(const BasisJob<TV>* __restrict__ jobs, BatchPlan P) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int s_item[7];  // phase, entry, solve, bid, nblk, seq, ok (phase -1: no items left)
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) {
+      const unsigned t = atomicAdd(P.ticket, 1u);
+      if (t >= P.total) {
+        s_item[0] = -1;
+      } else {
+        int lo = 0, hi = P.nph - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (P.ph[mid].start <= t) lo = mid; else hi = mid - 1;
+        }
+        const PhaseWave& ph = P.ph[lo];
+        const int b = (int)(t - ph.start);
+        const int i = wave_slot(ph.w, b);
+        const int j = __ldg(ph.w.ids + i);
+        const unsigned seq = (unsigned)__ldg(ph.seq + i);
+        int polls = 0;
+        while (ld_acquire_u32(P.done + j) < seq && ++polls < P.poll_limit) __nanosleep(64);
+        const bool ok = ld_acquire_u32(P.done + j) >= seq;
+        if (!ok) {  // the phase before never completed: this solve stops, the launch goes on
+          jobs[j].st->status = FAB_ETIMEOUT;
+          jobs[j].st->stop = 1;
+        }
+        s_item[0] = lo;
+        s_item[1] = i;
+        s_item[2] = j;
+        s_item[3] = b - __ldg(ph.w.pre + i);
+        s_item[4] = __ldg(ph.w.pre + i + 1) - __ldg(ph.w.pre + i);
+        s_item[5] = (int)seq;
+        s_item[6] = ok ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    const int k = s_item[0];
+    if (k < 0) break;
+    const int i = s_item[1], j = s_item[2], bid = s_item[3], nblk = s_item[4], seq = s_item[5];
+    const bool ok = s_item[6] != 0;
+    const PhaseWave& ph = P.ph[k];
+    const BasisJob<TV>* J = jobs + j;
+    const int type = ph.type, c = ph.c;
+    if (ok) {
+      if (type == kPhInit) {
+        init_phase<TV>(J, bid, nblk);
+      } else if (type == kPhSpmv) {
+        spmv_phase<TV, 0, KMAX>(ph.arg, J, c, bid, nblk, smem_raw);
+      } else if (type == kPhUpdate) {
+        switch (ph.kind) {
+          case SK_SRHT: update_phase<SK_SRHT, TV>(J, c, ph.arg, ph.mode, bid, nblk, smem_raw); break;
+          case SK_SPARSE_TAB: update_phase<SK_SPARSE_TAB, TV>(J, c, ph.arg, ph.mode, bid, nblk, smem_raw); break;
+          default: update_phase<SK_NONE, TV>(J, c, ph.arg, ph.mode, bid, nblk, smem_raw); break;
+        }
+      } else {
+        reduce_phase<TV>(J, __ldg(ph.w.aux + i), bid, nblk);
+      }
+    }
+    __syncthreads();  // the body's writes precede the count; s_item may be refilled
+    if (tid == 0) {
+      __threadfence();
+      if (atomicAdd(P.blk + j, 1u) + 1u == (unsigned)nblk) {  // the last block of this phase
+        atomicExch(P.blk + j, 0u);
+        __threadfence();
+        st_release_u32(P.done + j, (unsigned)seq + 1u);
+      }
+    }
+  }
+}
+
+template <typename TV>
+const void* batch_basis_fn(int kmax) {
+  if (kmax <= 2) return (const void*)k_batch_basis<TV, 2>;
+  if (kmax <= 4) return (const void*)k_batch_basis<TV, 4>;
+  return (const void*)k_batch_basis<TV, 8>;
+}
+
+// Blocks of the persistent kernel (every resident slot once) after its
+// shared-memory limit is set; call before a graph capture.
+template <typename TV>
+cudaError_t batch_basis_prepare(int kmax, size_t smem, int* grid) {
+  const void* fn = batch_basis_fn<TV>(kmax);
+  cudaError_t e = ensure_smem_limit(fn, smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  *grid = sm_count() * (occ < 1 ? 1 : occ);
+  return cudaSuccess;
+}
+
+template <typename TV>
+cudaError_t launch_batch_basis(const BasisJob<TV>* jobs, const BatchPlan& plan, int kmax, int grid, size_t smem,
+                               cudaStream_t s) {
+  if (plan.total == 0) return cudaSuccess;
+  const BasisJob<TV>* jb = jobs;
+  BatchPlan p = plan;
+  void* args[] = {(void*)&jb, &p};
+  return cudaLaunchKernel(batch_basis_fn<TV>(kmax), dim3(grid), dim3(kThreads), args, smem, s);
 }
 
 // x = sum_{q < m_used} coef_q W_q, the arithmetic of k_combine with keep = 0
@@ -1163,55 +1320,6 @@ __global__ __launch_bounds__(kThreads) void k_combine_wave(const BasisJob<TV>* _
 }
 
 template <typename TV>
-cudaError_t launch_init_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, cudaStream_t s) {
-  if (nblocks <= 0) return cudaSuccess;
-  k_init_wave<TV><<<nblocks, kThreads, 0, s>>>(jobs, w);
-  return cudaGetLastError();
-}
-
-template <typename TV>
-cudaError_t launch_spmv_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, int kw, cudaStream_t s) {
-  static const void* fns[kMaxWindow + 1] = {
-      (const void*)k_spmv_wave<TV, 0>, (const void*)k_spmv_wave<TV, 1>, (const void*)k_spmv_wave<TV, 2>,
-      (const void*)k_spmv_wave<TV, 3>, (const void*)k_spmv_wave<TV, 4>, (const void*)k_spmv_wave<TV, 5>,
-      (const void*)k_spmv_wave<TV, 6>, (const void*)k_spmv_wave<TV, 7>, (const void*)k_spmv_wave<TV, 8>};
-  if (kw < 0 || kw > kMaxWindow) return cudaErrorInvalidValue;
-  if (nblocks <= 0) return cudaSuccess;
-  const size_t smem = (size_t)kSpmvStages * kSpmvCap * (sizeof(TV) + sizeof(int));
-  cudaError_t e = ensure_smem_limit(fns[kw], smem);
-  if (e != cudaSuccess) return e;
-  Wave wv = w;
-  void* args[] = {(void*)&jobs, &wv, &c};
-  return cudaLaunchKernel(fns[kw], dim3(nblocks), dim3(kThreads), args, smem, s);
-}
-
-template <typename TV>
-cudaError_t launch_update_wave(int kind, const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, int nc, int mode,
-                               size_t smem, cudaStream_t s) {
-  if (nblocks <= 0) return cudaSuccess;
-  const void* fn = nullptr;
-  switch (kind) {
-    case SK_SRHT: fn = (const void*)k_update_wave<SK_SRHT, TV>; break;
-    case SK_SPARSE: fn = (const void*)k_update_wave<SK_SPARSE, TV>; break;
-    case SK_SPARSE_TAB: fn = (const void*)k_update_wave<SK_SPARSE_TAB, TV>; break;
-    case SK_NONE: fn = (const void*)k_update_wave<SK_NONE, TV>; break;
-    default: return cudaErrorInvalidValue;  // the Gaussian sketch is not batched
-  }
-  cudaError_t e = ensure_smem_limit(fn, smem);
-  if (e != cudaSuccess) return e;
-  Wave wv = w;
-  void* args[] = {(void*)&jobs, &wv, &c, &nc, &mode};
-  return cudaLaunchKernel(fn, dim3(nblocks), dim3(kThreads), args, smem, s);
-}
-
-template <typename TV>
-cudaError_t launch_sketch_reduce_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, cudaStream_t s) {
-  if (nblocks <= 0) return cudaSuccess;
-  k_sketch_reduce_wave<TV><<<nblocks, 256, 0, s>>>(jobs, w, c);
-  return cudaGetLastError();
-}
-
-template <typename TV>
 cudaError_t launch_combine_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int mmax, cudaStream_t s) {
   if (nblocks <= 0) return cudaSuccess;
   const size_t smem = (size_t)(mmax + 1) * sizeof(double);
@@ -1221,40 +1329,14 @@ cudaError_t launch_combine_wave(const BasisJob<TV>* jobs, const Wave& w, int nbl
   return cudaGetLastError();
 }
 
-// Shared-memory limits of every wave kernel, set before a graph capture so the
-// capture itself issues no attribute calls. upd_smem: largest update-wave size.
-template <typename TV>
-cudaError_t wave_prepare(size_t upd_smem, int mmax) {
-  const size_t spmv_smem = (size_t)kSpmvStages * kSpmvCap * (sizeof(TV) + sizeof(int));
-  const void* spmv[] = {(const void*)k_spmv_wave<TV, 0>, (const void*)k_spmv_wave<TV, 1>,
-                        (const void*)k_spmv_wave<TV, 2>, (const void*)k_spmv_wave<TV, 3>,
-                        (const void*)k_spmv_wave<TV, 4>, (const void*)k_spmv_wave<TV, 5>,
-                        (const void*)k_spmv_wave<TV, 6>, (const void*)k_spmv_wave<TV, 7>,
-                        (const void*)k_spmv_wave<TV, 8>};
-  for (const void* f : spmv) {
-    cudaError_t e = ensure_smem_limit(f, spmv_smem);
-    if (e != cudaSuccess) return e;
-  }
-  const void* upd[] = {(const void*)k_update_wave<SK_SRHT, TV>, (const void*)k_update_wave<SK_SPARSE, TV>,
-                       (const void*)k_update_wave<SK_SPARSE_TAB, TV>, (const void*)k_update_wave<SK_NONE, TV>};
-  for (const void* f : upd) {
-    cudaError_t e = ensure_smem_limit(f, upd_smem);
-    if (e != cudaSuccess) return e;
-  }
-  return ensure_smem_limit((const void*)k_combine_wave<TV>, (size_t)(mmax + 1) * sizeof(double));
-}
-
-#define FAB_WAVES(TV)                                                                                              \
-  template cudaError_t launch_init_wave<TV>(const BasisJob<TV>*, const Wave&, int, cudaStream_t);                  \
-  template cudaError_t launch_spmv_wave<TV>(const BasisJob<TV>*, const Wave&, int, int, int, cudaStream_t);         \
-  template cudaError_t launch_update_wave<TV>(int, const BasisJob<TV>*, const Wave&, int, int, int, int, size_t,    \
-                                              cudaStream_t);                                                       \
-  template cudaError_t launch_sketch_reduce_wave<TV>(const BasisJob<TV>*, const Wave&, int, int, cudaStream_t);     \
-  template cudaError_t launch_combine_wave<TV>(const BasisJob<TV>*, const Wave&, int, int, cudaStream_t);        \
-  template cudaError_t wave_prepare<TV>(size_t, int);
-FAB_WAVES(double)
-FAB_WAVES(float)
-#undef FAB_WAVES
+#define FAB_BATCH(TV)                                                                                           \
+  template cudaError_t batch_basis_prepare<TV>(int, size_t, int*);                                              \
+  template cudaError_t launch_batch_basis<TV>(const BasisJob<TV>*, const BatchPlan&, int, int, size_t,          \
+                                              cudaStream_t);                                                    \
+  template cudaError_t launch_combine_wave<TV>(const BasisJob<TV>*, const Wave&, int, int, cudaStream_t);
+FAB_BATCH(double)
+FAB_BATCH(float)
+#undef FAB_BATCH
 
 // ------------------------------------------------------------- grid sizes
 static int g_sms = 0;

@@ -1,18 +1,17 @@
 // Batched solves of libfab: many f(A)b solves of uneven size (different
 // matrices, n, m, window k, sketch and f) captured into one CUDA graph.
 //
-// Work items are (solve, basis step, tile): for every basis step c the graph
-// holds one launch per (window, sketch kind) group that covers the tiles of
-// every solve still building its basis (SpMV + window dots, then the window
-// update + norm + fused sketch, then the sketch reduce; Alg. 2 with the sketch
-// of §2.1.1). A solve's blocks inside such a wave run the bodies of its own
+// The plan lists phases: for every basis step c, per (window, sketch kind) group,
+// the SpMV + window dots, then the window update + norm + fused sketch, then the
+// sketch reduce (Alg. 2 with the sketch of §2.1.1), each over every solve still
+// building its basis. A solve's blocks in a phase run the bodies of its own
 // launches on the same tiles and chunks (with at least kMinTiles SpMV tiles per
-// block), so its results equal fab_apply's up to the grouping of partial sums.
-// As soon as a solve's basis is complete its small stage (QR of the
-// sketch, the sketch-and-solve projection of eq. sFOM or none for Alg. 5,
-// f(H)e_1) runs as one CTA on a second branch of the graph, followed by its
-// combine x = ||b|| V_m c, so the FP64-bound small stages of early finishers
-// overlap the HBM-bound basis steps of the others.
+// block), so its results equal fab_apply's up to the grouping of partial sums. The
+// whole basis build is one persistent launch (k_batch_basis: blocks claim the
+// plan's work items in order and wait only for their own solve's previous phase),
+// then one launch runs every solve's small stage as one CTA (QR of the sketch, the
+// sketch-and-solve projection of eq. sFOM or none for Alg. 5, f(H)e_1) and one
+// the combines x = ||b|| V_m c. The graph holds these three kernels.
 #include <math.h>
 #include <string.h>
 
@@ -27,7 +26,7 @@ namespace {
 
 using namespace fab;
 
-constexpr int kSkReduceWarps = 8;  // warps per block of the sketch reduce (one sketch row per warp)
+constexpr int kReduceEntries = 8 * 32;  // sketch entries per block of the reduce phase (a warp per entry, 32 rounds)
 
 // Bump allocator over one device allocation (sizing pass when base is NULL).
 struct Arena {
@@ -49,7 +48,7 @@ struct HostWave {
   int c = 0, arg = 0, mode = 0, kind = SK_NONE;  // arg: window / update column count
   size_t smem = 0;
   int nblocks = 0;
-  size_t pre = 0, ids = 0, aux = 0;  // offsets into the table
+  size_t pre = 0, ids = 0, aux = 0, seq = 0;  // offsets into the table
   int count = 0;
   int mmax = 0;
 };
@@ -65,6 +64,9 @@ int sk_kind_of(const fab_params& p) {
 // its partial-sum reduction).
 constexpr int kMinTiles = 32;
 constexpr int kMinChunks = 4;
+// Polls (each a 64 ns sleep and an L2 round trip) of a solve's phase counter before
+// the waiting block gives up: seconds, far beyond any phase's duration.
+constexpr int kPhasePolls = 1 << 22;
 
 }  // namespace
 
@@ -106,12 +108,12 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
     }
     group_of[j] = (int)(it - groups.begin());
   }
-  std::vector<int> tab;  // wave tables (prefix, ids, aux), uploaded once
-  std::vector<HostWave> waves;
-  auto add_wave = [&](HostWave w, const std::vector<int>& ids, const std::vector<int>& nblk,
-                      const std::vector<int>& aux) {
+  std::vector<int> tab;  // wave tables (prefix, ids, aux, phase numbers), uploaded once
+  std::vector<HostWave> waves;  // the basis phases, in plan order
+  std::vector<int> phases(count, 0);  // per solve: phases planned so far
+  auto add_table = [&](HostWave& w, const std::vector<int>& ids, const std::vector<int>& nblk,
+                       const std::vector<int>& aux) {
     w.count = (int)ids.size();
-    if (w.count == 0) return;
     w.pre = tab.size();
     int acc = 0;
     tab.push_back(0);
@@ -122,6 +124,13 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
     w.aux = tab.size();
     if (aux.empty()) tab.insert(tab.end(), ids.size(), 0);
     else tab.insert(tab.end(), aux.begin(), aux.end());
+    w.seq = tab.size();
+    for (int j : ids) tab.push_back(phases[j]++);
+  };
+  auto add_wave = [&](HostWave w, const std::vector<int>& ids, const std::vector<int>& nblk,
+                      const std::vector<int>& aux) {
+    if (ids.empty()) return;
+    add_table(w, ids, nblk, aux);
     waves.push_back(w);
   };
   {  // start: state, counters, H = 0, W_0 = b
@@ -132,7 +141,8 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
     }
     add_wave(HostWave{W_INIT}, ids, nb, {});
   }
-  std::vector<size_t> skpart_need(count, 1), part_need(count, 1);  // per-solve partial buffer sizes
+  std::vector<size_t> part_need(count, 1);  // per-solve partial counts
+  std::vector<int> upd_blocks(count, 1);     // per solve: the largest update grid (sketch partials per column)
   for (int c = 0; c <= mmax; ++c) {
     for (int g = 0; g < (int)groups.size(); ++g) {
       const int k = groups[g].first, kd = groups[g].second;
@@ -163,7 +173,7 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
         nb.push_back(grid);
         smem = std::max(smem, sm);
         part_need[j] = std::max(part_need[j], (size_t)grid);
-        skpart_need[j] = std::max(skpart_need[j], (size_t)grid * (size_t)std::max(s, 1));
+        upd_blocks[j] = std::max(upd_blocks[j], grid);
       }
       HostWave w{W_UPDATE};
       w.c = c;
@@ -172,37 +182,36 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       w.kind = kd;
       w.smem = smem;
       add_wave(w, ids, nb, {});
-      if (kd != SK_NONE) {
-        std::vector<int> nr;
-        for (int j : ids) nr.push_back((ps[j].s + kSkReduceWarps - 1) / kSkReduceWarps);
-        HostWave r{W_REDUCE};
-        r.c = c;
-        add_wave(r, ids, nr, nb);  // aux: the update's block count = partials to sum
-      }
-    }
-    if (c >= 1) {  // solves whose basis is complete: small stage, then combine (second branch)
-      std::vector<int> ids, nb;
-      int mm = 1;
-      for (int j = 0; j < count; ++j)
-        if (ps[j].m == c) {
-          ids.push_back(j);
-          nb.push_back(1);
-          mm = std::max(mm, ps[j].m);
-        }
-      if (!ids.empty()) {
-        HostWave w{W_SMALL};
-        w.c = c;
-        w.mmax = mm;
-        add_wave(w, ids, nb, {});
-        std::vector<int> nc;
-        for (int j : ids) nc.push_back(combine_grid(bt->n[j]));
-        HostWave cw{W_COMBINE};
-        cw.c = c;
-        cw.mmax = mm;
-        add_wave(cw, ids, nc, {});
-      }
     }
   }
+  // The sketch partials of every column stay (column c at c * colstride), so one
+  // reduce phase per sketched solve, after its basis, forms all of Theta V (a warp
+  // per sketch entry) instead of a reduce phase per step.
+  {
+    std::vector<int> ids, nr, np;
+    for (int j = 0; j < count; ++j)
+      if (kind[j] != SK_NONE) {
+        ids.push_back(j);
+        nr.push_back((int)(((size_t)(ps[j].m + 1) * ps[j].s + kReduceEntries - 1) / kReduceEntries));
+        np.push_back(upd_blocks[j]);  // partials per column: the largest update grid
+      }
+    HostWave r{W_REDUCE};
+    add_wave(r, ids, nr, np);
+  }
+  // after the basis: every solve's small stage (one CTA each), then every combine
+  std::vector<int> all(count), ones(count, 1), ncomb(count);
+  for (int j = 0; j < count; ++j) {
+    all[j] = j;
+    ncomb[j] = combine_grid(bt->n[j]);
+  }
+  HostWave small_w{W_SMALL};
+  small_w.mmax = mmax;
+  add_table(small_w, all, ones, {});
+  HostWave comb_w{W_COMBINE};
+  comb_w.mmax = mmax;
+  add_table(comb_w, all, ncomb, {});
+  int kmax = 1;
+  for (int j = 0; j < count; ++j) kmax = std::max(kmax, ps[j].k);
 
   // ------------------------------------------------------------ layout
   std::vector<BasisJob<TV>> jobs(count);
@@ -212,6 +221,8 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
     SmallJob* small_dev = ar.take<SmallJob>(count);
     int* tab_dev = ar.take<int>(tab.size());
     DevState* states = ar.take<DevState>(count);
+    PhaseWave* ph_dev = ar.take<PhaseWave>(waves.size());
+    unsigned* ctr_dev = ar.take<unsigned>(1 + 2 * (size_t)count);  // ticket, done[count], blk[count]
     for (int j = 0; j < count; ++j) {
       fab_handle* h = hs[j];
       const fab_params& p = ps[j];
@@ -250,7 +261,8 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       sk.st_signs = rng_state(p.seed, 2);
       sk.st_D = rng_state(p.seed, 3);
       sk.P = ar.take<int>(s);
-      sk.part = ar.take<double>(skpart_need[j]);
+      J.sk_colstride = (size_t)upd_blocks[j] * (size_t)std::max(s, 1);
+      sk.part = ar.take<double>((size_t)(m + 1) * J.sk_colstride);
       sk.pat = kind[j] == SK_SPARSE_TAB ? ar.take<unsigned short>(sparse_table_bytes(n, p.s, p.zeta) / 2) : nullptr;
       J.sk_scale = kind[j] == SK_SRHT ? 1.0 / sqrt((double)p.s) : (kind[j] == SK_SPARSE_TAB ? 1.0 / sqrt((double)p.zeta) : 1.0);
       double* bst = ar.take<double>(n);
@@ -282,7 +294,7 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       S.scal = ar.take<double>(16);
       S.coef = J.coef;
     }
-    return std::make_tuple(jobs_dev, small_dev, tab_dev, states);
+    return std::make_tuple(jobs_dev, small_dev, tab_dev, states, ph_dev, ctr_dev);
   };
   Arena sizing;
   layout(sizing);
@@ -304,19 +316,39 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
   BasisJob<TV>* jobs_dev;
   SmallJob* small_dev;
   int* tab_dev;
-  std::tie(jobs_dev, small_dev, tab_dev, bt->states) = layout(ar);
+  PhaseWave* ph_dev;
+  unsigned* ctr_dev;
+  std::tie(jobs_dev, small_dev, tab_dev, bt->states, ph_dev, ctr_dev) = layout(ar);
+  // the plan: phases with the device addresses of their tables
+  std::vector<PhaseWave> ph(waves.size());
+  unsigned total = 0;
+  size_t upd_smem = 0;
+  for (size_t q = 0; q < waves.size(); ++q) {
+    const HostWave& w = waves[q];
+    PhaseWave& P = ph[q];
+    P.type = w.type == W_INIT ? kPhInit : w.type == W_SPMV ? kPhSpmv : w.type == W_UPDATE ? kPhUpdate : kPhReduce;
+    P.c = w.c;
+    P.arg = w.arg;
+    P.mode = w.mode;
+    P.kind = w.kind;
+    P.start = total;
+    P.w = Wave{tab_dev + w.pre, tab_dev + w.ids, tab_dev + w.aux, w.count};
+    P.seq = tab_dev + w.seq;
+    total += (unsigned)w.nblocks;
+    if (w.type == W_UPDATE) upd_smem = std::max(upd_smem, w.smem);
+  }
+  BatchPlan plan;
+  plan.ph = ph_dev;
+  plan.nph = (int)ph.size();
+  plan.total = total;
+  plan.ticket = ctr_dev;
+  plan.done = ctr_dev + 1;
+  plan.blk = ctr_dev + 1 + count;
+  plan.poll_limit = kPhasePolls;
+  const size_t basis_smem = std::max(upd_smem, (size_t)kSpmvStages * kSpmvCap * (sizeof(TV) + sizeof(int)));
 
-  // Small stages of different completion steps go to separate graph branches
-  // (streams of a pool), so a group never waits for the previous group's CTAs.
-  constexpr int kBranches = 16;
   cudaStream_t cap = nullptr;
-  cudaStream_t side[kBranches] = {};
-  cudaEvent_t fork = nullptr, join = nullptr;
   auto cleanup = [&]() {
-    if (fork) cudaEventDestroy(fork);
-    if (join) cudaEventDestroy(join);
-    for (cudaStream_t& q : side)
-      if (q) cudaStreamDestroy(q);
     if (cap) cudaStreamDestroy(cap);
   };
 #define BK(call)              \
@@ -328,12 +360,10 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
     }                         \
   } while (0)
   BK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  for (cudaStream_t& q : side) BK(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
-  BK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-  BK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
   BK(cudaMemcpyAsync(jobs_dev, jobs.data(), sizeof(BasisJob<TV>) * count, cudaMemcpyHostToDevice, cap));
   BK(cudaMemcpyAsync(small_dev, small.data(), sizeof(SmallJob) * count, cudaMemcpyHostToDevice, cap));
   BK(cudaMemcpyAsync(tab_dev, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, cap));
+  BK(cudaMemcpyAsync(ph_dev, ph.data(), sizeof(PhaseWave) * ph.size(), cudaMemcpyHostToDevice, cap));
   for (int j = 0; j < count; ++j) {  // SRHT samples and sparse sign patterns are fixed: drawn once here
     if (kind[j] == SK_SRHT) {
       int64_t npad = 1;
@@ -343,50 +373,28 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
     if (kind[j] == SK_SPARSE_TAB)
       BK(launch_sparse_pattern(bt->n[j], jobs[j].sk, const_cast<unsigned short*>(jobs[j].sk.pat), cap));
   }
+  for (int j = 0; j < count; ++j)  // partial slots a column's update grid leaves unwritten read as zero
+    if (kind[j] != SK_NONE)
+      BK(cudaMemsetAsync(jobs[j].sk.part, 0, (size_t)(ps[j].m + 1) * jobs[j].sk_colstride * sizeof(double), cap));
   BK(cudaStreamSynchronize(cap));
   PadeCoef pd;
   memcpy(pd.b, pade13_b(), sizeof(pd.b));
   pd.theta = pade13_theta();
-  // every wave kernel gets its shared-memory limit before the capture
+  // every kernel gets its shared-memory limit before the capture
   BK(small_fused_prepare(mmax));
-  {
-    size_t upd = 0;
-    for (const HostWave& w : waves)
-      if (w.type == W_UPDATE) upd = std::max(upd, w.smem);
-    BK(wave_prepare<TV>(upd, mmax));
-  }
+  int basis_grid = 0;
+  BK(batch_basis_prepare<TV>(kmax, basis_smem, &basis_grid));
 
   // ------------------------------------------------------------ capture
   BK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-  int kernels = 0, branch = -1;
-  bool side_used[kBranches] = {};
-  cudaError_t e = cudaSuccess;
-  for (const HostWave& w : waves) {
-    const Wave wv{tab_dev + w.pre, tab_dev + w.ids, tab_dev + w.aux, w.count};
-    switch (w.type) {
-      case W_INIT: e = launch_init_wave<TV>(jobs_dev, wv, w.nblocks, cap); break;
-      case W_SPMV: e = launch_spmv_wave<TV>(jobs_dev, wv, w.nblocks, w.c, w.arg, cap); break;
-      case W_UPDATE:
-        e = launch_update_wave<TV>(w.kind, jobs_dev, wv, w.nblocks, w.c, w.arg, w.mode, w.smem, cap);
-        break;
-      case W_REDUCE: e = launch_sketch_reduce_wave<TV>(jobs_dev, wv, w.nblocks, w.c, cap); break;
-      case W_SMALL:
-        branch = (branch + 1) % kBranches;
-        if ((e = cudaEventRecord(fork, cap)) != cudaSuccess) break;
-        if ((e = cudaStreamWaitEvent(side[branch], fork, 0)) != cudaSuccess) break;
-        side_used[branch] = true;
-        e = launch_small_fused(small_dev, tab_dev + w.ids, w.count, w.mmax, pd, side[branch]);
-        break;
-      case W_COMBINE: e = launch_combine_wave<TV>(jobs_dev, wv, w.nblocks, w.mmax, side[branch]); break;
-    }
-    if (e != cudaSuccess) break;
-    ++kernels;
+  cudaError_t e = cudaMemsetAsync(ctr_dev, 0, (1 + 2 * (size_t)count) * sizeof(unsigned), cap);
+  if (e == cudaSuccess) e = launch_batch_basis<TV>(jobs_dev, plan, kmax, basis_grid, basis_smem, cap);
+  if (e == cudaSuccess) e = launch_small_fused(small_dev, tab_dev + small_w.ids, count, mmax, pd, cap);
+  if (e == cudaSuccess) {
+    const Wave cw{tab_dev + comb_w.pre, tab_dev + comb_w.ids, tab_dev + comb_w.aux, comb_w.count};
+    e = launch_combine_wave<TV>(jobs_dev, cw, comb_w.nblocks, mmax, cap);
   }
-  for (int q = 0; q < kBranches && e == cudaSuccess; ++q)
-    if (side_used[q]) {
-      e = cudaEventRecord(join, side[q]);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, join, 0);
-    }
+  const int kernels = 3;
   cudaGraph_t graph = nullptr;
   const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
   if (e != cudaSuccess || e2 != cudaSuccess) {

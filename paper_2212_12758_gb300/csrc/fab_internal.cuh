@@ -456,19 +456,41 @@ struct BasisJob {
   unsigned* counter;
   DevState* st;
   SketchDev sk;  // sk.kind SK_NONE for Alg. 5 without a sketch
+  size_t sk_colstride;  // sketch partials of column c at sk.part + c * sk_colstride
   double sk_scale;
   double* SV;       // s x (m+1)
   const double* b;  // start vector (FP64, device)
   double* x;        // result (FP64, device)
 };
-// A wave is one launch over several solves: job ids[i] owns blocks pre[i] ..
+// A wave lists solves and their blocks: job ids[i] owns blocks pre[i] ..
 // pre[i+1]-1 (its own launch's grid); aux[i] is a per-job extra (the sketch
-// partial count of the update wave before a reduce wave).
+// partial count of the update phase before a reduce phase).
 struct Wave {
   const int* pre;
   const int* ids;
   const int* aux;
   int count;
+};
+// Phases of a batch's basis build, in plan order, run by one persistent launch.
+enum PhaseType { kPhInit = 0, kPhSpmv = 1, kPhUpdate = 2, kPhReduce = 3 };
+struct PhaseWave {
+  int type;        // PhaseType
+  int c;           // basis step (column)
+  int arg;         // SpMV: window width; update: window columns updated
+  int mode;        // update mode bits
+  int kind;        // sketch kind of the update
+  unsigned start;  // number of the phase's first work item
+  Wave w;          // its solves and their blocks
+  const int* seq;  // per entry: the solve's phase number (phases of one solve run in order)
+};
+struct BatchPlan {
+  const PhaseWave* ph;
+  int nph;
+  unsigned total;   // work items
+  unsigned* ticket; // next item to claim
+  unsigned* done;   // per solve: phases completed
+  unsigned* blk;    // per solve: blocks done in the current phase
+  int poll_limit;   // polls of a solve's counter before its solve gives up (FAB_ETIMEOUT)
 };
 // Grid of the single-solve launch of each basis kernel (a batched solve uses the same).
 template <typename TV>
@@ -476,19 +498,15 @@ int spmv_grid(int ntiles, int kw, bool seg);
 template <typename TV>
 int update_grid(int kind, int n, int nc, int s, size_t* smem);
 int combine_grid(int n);
+// The persistent basis kernel of a batch (window widths up to kmax): its grid, once its
+// shared-memory limit (smem bytes) is set, then its launch.
 template <typename TV>
-cudaError_t launch_init_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, cudaStream_t s);
+cudaError_t batch_basis_prepare(int kmax, size_t smem, int* grid);
 template <typename TV>
-cudaError_t launch_spmv_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, int kw, cudaStream_t s);
-template <typename TV>
-cudaError_t launch_update_wave(int kind, const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, int nc, int mode,
-                               size_t smem, cudaStream_t s);
-template <typename TV>
-cudaError_t launch_sketch_reduce_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int c, cudaStream_t s);
+cudaError_t launch_batch_basis(const BasisJob<TV>* jobs, const BatchPlan& plan, int kmax, int grid, size_t smem,
+                               cudaStream_t s);
 template <typename TV>
 cudaError_t launch_combine_wave(const BasisJob<TV>* jobs, const Wave& w, int nblocks, int mmax, cudaStream_t s);
-template <typename TV>
-cudaError_t wave_prepare(size_t upd_smem, int mmax);
 cudaError_t launch_srht_sample(int64_t npad, int s, uint64_t stP, int* P, cudaStream_t st);
 template <typename TV, typename TX>
 cudaError_t launch_gemv_t(int n, const TV* W, int64_t ld, int j0, int nc, const TX* x, double* part,
