@@ -1202,7 +1202,7 @@ __device__ __noinline__ void update_phase(const BasisJob<TV>* J, int c, int nc, 
 template <typename TV, int KMAX>
 __global__ __launch_bounds__(kThreads, 4) void k_batch_basis(const BasisJob<TV>* __restrict__ jobs, BatchPlan P) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ int s_item[7];  // phase, entry, solve, bid, nblk, seq, ok (phase -1: no items left)
+  __shared__ int s_item[5];  // item code (-1: no items left), solve, bid | nblk, seq | c, ok
   const int tid = threadIdx.x;
   for (;;) {
     if (tid == 0) {
@@ -1210,16 +1210,9 @@ __global__ __launch_bounds__(kThreads, 4) void k_batch_basis(const BasisJob<TV>*
       if (t >= P.total) {
         s_item[0] = -1;
       } else {
-        int lo = 0, hi = P.nph - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (P.ph[mid].start <= t) lo = mid; else hi = mid - 1;
-        }
-        const PhaseWave& ph = P.ph[lo];
-        const int b = (int)(t - ph.start);
-        const int i = wave_slot(ph.w, b);
-        const int j = __ldg(ph.w.ids + i);
-        const unsigned seq = (unsigned)__ldg(ph.seq + i);
+        const int4 r = __ldg(P.items + t);  // one load: the acquire below empties L1 every item
+        const int j = r.x;
+        const unsigned seq = (unsigned)r.z & 0xffffu;
         int polls = 0;
         while (ld_acquire_u32(P.done + j) < seq && ++polls < P.poll_limit) __nanosleep(64);
         const bool ok = ld_acquire_u32(P.done + j) >= seq;
@@ -1227,36 +1220,34 @@ __global__ __launch_bounds__(kThreads, 4) void k_batch_basis(const BasisJob<TV>*
           jobs[j].st->status = FAB_ETIMEOUT;
           jobs[j].st->stop = 1;
         }
-        s_item[0] = lo;
-        s_item[1] = i;
-        s_item[2] = j;
-        s_item[3] = b - __ldg(ph.w.pre + i);
-        s_item[4] = __ldg(ph.w.pre + i + 1) - __ldg(ph.w.pre + i);
-        s_item[5] = (int)seq;
-        s_item[6] = ok ? 1 : 0;
+        s_item[0] = r.w;
+        s_item[1] = j;
+        s_item[2] = r.y;
+        s_item[3] = r.z;
+        s_item[4] = ok ? 1 : 0;
       }
     }
     __syncthreads();
-    const int k = s_item[0];
-    if (k < 0) break;
-    const int i = s_item[1], j = s_item[2], bid = s_item[3], nblk = s_item[4], seq = s_item[5];
-    const bool ok = s_item[6] != 0;
-    const PhaseWave& ph = P.ph[k];
+    const int code = s_item[0];
+    if (code < 0) break;
+    const int j = s_item[1], bid = s_item[2] & 0xffff, nblk = (int)((unsigned)s_item[2] >> 16);
+    const int seq = s_item[3] & 0xffff, c = (int)((unsigned)s_item[3] >> 16);
+    const bool ok = s_item[4] != 0;
+    const int type = code & 3, mode = (code >> 2) & 3, kind = ((code >> 4) & 7) - 1, arg = code >> 8;
     const BasisJob<TV>* J = jobs + j;
-    const int type = ph.type, c = ph.c;
     if (ok) {
       if (type == kPhInit) {
         init_phase<TV>(J, bid, nblk);
       } else if (type == kPhSpmv) {
-        spmv_phase<TV, 0, KMAX>(ph.arg, J, c, bid, nblk, smem_raw);
+        spmv_phase<TV, 0, KMAX>(arg, J, c, bid, nblk, smem_raw);
       } else if (type == kPhUpdate) {
-        switch (ph.kind) {
-          case SK_SRHT: update_phase<SK_SRHT, TV>(J, c, ph.arg, ph.mode, bid, nblk, smem_raw); break;
-          case SK_SPARSE_TAB: update_phase<SK_SPARSE_TAB, TV>(J, c, ph.arg, ph.mode, bid, nblk, smem_raw); break;
-          default: update_phase<SK_NONE, TV>(J, c, ph.arg, ph.mode, bid, nblk, smem_raw); break;
+        switch (kind) {
+          case SK_SRHT: update_phase<SK_SRHT, TV>(J, c, arg, mode, bid, nblk, smem_raw); break;
+          case SK_SPARSE_TAB: update_phase<SK_SPARSE_TAB, TV>(J, c, arg, mode, bid, nblk, smem_raw); break;
+          default: update_phase<SK_NONE, TV>(J, c, arg, mode, bid, nblk, smem_raw); break;
         }
       } else {
-        reduce_phase<TV>(J, __ldg(ph.w.aux + i), bid, nblk);
+        reduce_phase<TV>(J, arg, bid, nblk);
       }
     }
     __syncthreads();  // the body's writes precede the count; s_item may be refilled

@@ -213,6 +213,23 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
   int kmax = 1;
   for (int j = 0; j < count; ++j) kmax = std::max(kmax, ps[j].k);
 
+  // ------------------------------------------------------------ work items
+  // every block of every phase, in plan order, decoded once here (see BatchPlan)
+  std::vector<int4> items;
+  size_t upd_smem = 0;
+  for (const HostWave& w : waves) {
+    const int type = w.type == W_INIT ? kPhInit : w.type == W_SPMV ? kPhSpmv : w.type == W_UPDATE ? kPhUpdate : kPhReduce;
+    if (w.type == W_UPDATE) upd_smem = std::max(upd_smem, w.smem);
+    for (int i = 0; i < w.count; ++i) {
+      const int j = tab[w.ids + i], nb = tab[w.pre + i + 1] - tab[w.pre + i], seq = tab[w.seq + i];
+      const int arg = type == kPhReduce ? tab[w.aux + i] : w.arg;
+      if (nb >= 65536 || seq >= 65536 || w.c >= 65536 || arg >= (1 << 23) || w.kind + 1 > 7) return FAB_EINVAL;
+      const int code = type | (w.mode << 2) | ((w.kind + 1) << 4) | (arg << 8);
+      for (int b = 0; b < nb; ++b) items.push_back(make_int4(j, b | (nb << 16), seq | (w.c << 16), code));
+    }
+  }
+  const size_t n_items = items.size();
+
   // ------------------------------------------------------------ layout
   std::vector<BasisJob<TV>> jobs(count);
   std::vector<SmallJob> small(count);
@@ -221,7 +238,7 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
     SmallJob* small_dev = ar.take<SmallJob>(count);
     int* tab_dev = ar.take<int>(tab.size());
     DevState* states = ar.take<DevState>(count);
-    PhaseWave* ph_dev = ar.take<PhaseWave>(waves.size());
+    int4* items_dev = ar.take<int4>(n_items);
     unsigned* ctr_dev = ar.take<unsigned>(1 + 2 * (size_t)count);  // ticket, done[count], blk[count]
     for (int j = 0; j < count; ++j) {
       fab_handle* h = hs[j];
@@ -294,7 +311,7 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
       S.scal = ar.take<double>(16);
       S.coef = J.coef;
     }
-    return std::make_tuple(jobs_dev, small_dev, tab_dev, states, ph_dev, ctr_dev);
+    return std::make_tuple(jobs_dev, small_dev, tab_dev, states, items_dev, ctr_dev);
   };
   Arena sizing;
   layout(sizing);
@@ -316,31 +333,12 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
   BasisJob<TV>* jobs_dev;
   SmallJob* small_dev;
   int* tab_dev;
-  PhaseWave* ph_dev;
+  int4* items_dev;
   unsigned* ctr_dev;
-  std::tie(jobs_dev, small_dev, tab_dev, bt->states, ph_dev, ctr_dev) = layout(ar);
-  // the plan: phases with the device addresses of their tables
-  std::vector<PhaseWave> ph(waves.size());
-  unsigned total = 0;
-  size_t upd_smem = 0;
-  for (size_t q = 0; q < waves.size(); ++q) {
-    const HostWave& w = waves[q];
-    PhaseWave& P = ph[q];
-    P.type = w.type == W_INIT ? kPhInit : w.type == W_SPMV ? kPhSpmv : w.type == W_UPDATE ? kPhUpdate : kPhReduce;
-    P.c = w.c;
-    P.arg = w.arg;
-    P.mode = w.mode;
-    P.kind = w.kind;
-    P.start = total;
-    P.w = Wave{tab_dev + w.pre, tab_dev + w.ids, tab_dev + w.aux, w.count};
-    P.seq = tab_dev + w.seq;
-    total += (unsigned)w.nblocks;
-    if (w.type == W_UPDATE) upd_smem = std::max(upd_smem, w.smem);
-  }
+  std::tie(jobs_dev, small_dev, tab_dev, bt->states, items_dev, ctr_dev) = layout(ar);
   BatchPlan plan;
-  plan.ph = ph_dev;
-  plan.nph = (int)ph.size();
-  plan.total = total;
+  plan.items = items_dev;
+  plan.total = (unsigned)items.size();
   plan.ticket = ctr_dev;
   plan.done = ctr_dev + 1;
   plan.blk = ctr_dev + 1 + count;
@@ -363,7 +361,7 @@ int build(fab_batch* bt, fab_handle* const* hs, const fab_params* ps, cudaStream
   BK(cudaMemcpyAsync(jobs_dev, jobs.data(), sizeof(BasisJob<TV>) * count, cudaMemcpyHostToDevice, cap));
   BK(cudaMemcpyAsync(small_dev, small.data(), sizeof(SmallJob) * count, cudaMemcpyHostToDevice, cap));
   BK(cudaMemcpyAsync(tab_dev, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, cap));
-  BK(cudaMemcpyAsync(ph_dev, ph.data(), sizeof(PhaseWave) * ph.size(), cudaMemcpyHostToDevice, cap));
+  BK(cudaMemcpyAsync(items_dev, items.data(), sizeof(int4) * n_items, cudaMemcpyHostToDevice, cap));
   for (int j = 0; j < count; ++j) {  // SRHT samples and sparse sign patterns are fixed: drawn once here
     if (kind[j] == SK_SRHT) {
       int64_t npad = 1;

@@ -471,21 +471,14 @@ struct Wave {
   const int* aux;
   int count;
 };
-// Phases of a batch's basis build, in plan order, run by one persistent launch.
+// Phases of a batch's basis build, run in plan order by one persistent launch.
 enum PhaseType { kPhInit = 0, kPhSpmv = 1, kPhUpdate = 2, kPhReduce = 3 };
-struct PhaseWave {
-  int type;        // PhaseType
-  int c;           // basis step (column)
-  int arg;         // SpMV: window width; update: window columns updated
-  int mode;        // update mode bits
-  int kind;        // sketch kind of the update
-  unsigned start;  // number of the phase's first work item
-  Wave w;          // its solves and their blocks
-  const int* seq;  // per entry: the solve's phase number (phases of one solve run in order)
-};
+// One work item of the persistent batch launch, decoded on the host:
+//   x = solve, y = bid | nblk << 16, z = phase number of the solve | c << 16,
+//   w = type | update mode << 2 | (sketch kind + 1) << 4 | arg << 8
+// (arg: SpMV window width, update column count, or the reduce's partials per column).
 struct BatchPlan {
-  const PhaseWave* ph;
-  int nph;
+  const int4* items;
   unsigned total;   // work items
   unsigned* ticket; // next item to claim
   unsigned* done;   // per solve: phases completed
