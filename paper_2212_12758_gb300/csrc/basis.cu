@@ -1186,11 +1186,12 @@ __device__ __noinline__ void update_phase(const BasisJob<TV>* J, int c, int nc, 
                       J->st, bid, nblk, smem);
 }
 
-// The whole basis build of a batch in one persistent launch. The plan lists the
-// phases of the former per-step launches in order (start, then for every step the
-// SpMV + window dots, the window update + norm + fused sketch, and the sketch
-// reduce; Alg. 2 with the sketch of §2.1.1); a work item is one block of one solve in
-// one phase, and items are numbered in plan order. Each block of this kernel claims
+// The whole basis build of a batch in one persistent launch. The plan lists phases in
+// order (the start of every solve; then for every step the SpMV + window dots and the
+// window update + norm + fused sketch, Alg. 2 with the sketch of §2.1.1; then per
+// solve one reduce of its kept sketch partials); a work item is one block of one solve
+// in one phase, items are numbered in plan order, and each has a 16-byte record
+// (BatchPlan). Each block of this kernel claims
 // the next item number from a global ticket, waits (bounded) until its solve has
 // completed the phase before (a per-solve counter, released by the block that ends
 // that phase and acquired here), runs the phase's body with the solve's own (bid,
