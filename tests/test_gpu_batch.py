@@ -187,3 +187,35 @@ def test_batch_fp64_many_blocks_per_wave(fab):
         assert _rel(xs[i], refs[i]) <= TOL, i
         alone = mats[i].apply(bs[i], ps[i])
         assert _rel(xs[i], alone) <= 1e-11, i
+
+
+def test_batch_many_small_solves_in_one_launch(fab):
+    """240 small solves (2D convection-diffusion, n from 100 to 3600; m from 4 to 30;
+    windows 1, 2 and 3; SRHT, sparse sign and Alg. 5), FP64: every phase of every solve
+    runs as work items of the one persistent launch, claimed in plan order with many
+    solves in each phase. Each result equals the solve run alone to 1e-11, twice in a
+    row (the phase counters and the ticket start from zero in every replay)."""
+    rng = np.random.default_rng(21)
+    grids = [10, 17, 23, 31, 44, 60]
+    A = {N: W.convdiff(2, N) for N in grids}
+    M = {N: fab.Matrix.from_csr(a) for N, a in A.items()}
+    mats, ps, bs = [], [], []
+    for i in range(240):
+        N = grids[int(rng.integers(len(grids)))]
+        m = int(rng.integers(4, 31))
+        k = int(rng.integers(1, 4))
+        kind = i % 3
+        sk = fab.SRHT if kind == 0 else fab.SPARSE_SIGN
+        method = fab.NOPROJ if kind == 2 else fab.SKETCHED_FAST
+        mats.append(M[N])
+        ps.append(fab.params(f=fab.EXP, t=-0.05 / N, m=m, k=k, s=4 * m, zeta=4, sketch=sk, seed=1 + i % 5,
+                             method=method))
+        bs.append(W.random_vector(A[N].n, 300 + i))
+    bt = fab.Batch(mats, ps)
+    for _ in range(2):
+        xs, sts = bt.run(bs, stats=True)
+        for i, (b, x, st) in enumerate(zip(bs, xs, sts)):
+            assert st.m_used == ps[i].m, i
+            alone = mats[i].apply(b, ps[i])
+            assert _rel(x, alone) <= 1e-11, (i, _rel(x, alone))
+    bt.close()
