@@ -858,7 +858,8 @@ def main():
     try:
         fp64_peak, fp64_peak_ms = fab.fma_peak(fab.FP64, stream=sp)
         fp32_peak, _ = fab.fma_peak(fab.MIXED, stream=sp)
-        fp64_src = "measured (fab_fma_peak: independent FP64 FMA chains on every SM, CUDA events)"
+        fp64_src = ("measured (fab_fma_peak: independent FP64 FMA chains on every SM in three operand "
+                    "patterns, the fastest kept; CUDA events)")
     except Exception:
         fp64_peak, fp64_peak_ms, fp32_peak = FP64_PEAK_GFLOPS_NOMINAL, 0.0, None
         fp64_src = "nominal (measurement failed)"

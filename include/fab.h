@@ -411,11 +411,13 @@ int fab_batch_run(fab_handle* const* hs, const fab_params* ps, const double* con
 /*
  * fab_fma_peak - measured fused multiply-add throughput of this GPU (measurement
  * support: the arithmetic bound of the FP64 basis kernels, which do about one FP64
- * FMA per 4 to 8 bytes they move). Runs independent chains of FMAs on every SM and
- * times them with CUDA events at the clocks the GPU runs now (it changes no clock).
+ * FMA per 4 to 8 bytes they move). Runs independent chains of FMAs on every SM, in
+ * three operand patterns (the rate depends on how operands fall on the register
+ * banks), times each with CUDA events at the clocks the GPU runs now (it changes no
+ * clock) and reports the fastest.
  *   precision  FAB_FP64 (FP64 FMAs) or FAB_MIXED (FP32 FMAs)
  *   gflops     2 x FMAs / second / 1e9 (one FMA counts two flops)
- *   ms         nullable: duration of the timed launch (at least about 50 ms)
+ *   ms         nullable: duration of the fastest timed launch (at least about 50 ms)
  *   stream     cudaStream_t or NULL; the call synchronizes it
  * FAB_EINVAL for another precision or a NULL gflops.
  */

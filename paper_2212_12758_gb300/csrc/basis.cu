@@ -955,16 +955,29 @@ cudaError_t launch_reduce_cols(const double* part, int ntiles, int nc, const dou
 // bounded (x tends to b / (1 - a)); the sum is stored only if it equals an impossible
 // value, which the compiler cannot prove false.
 __device__ double g_fma_sink;
-template <typename T>
-__global__ __launch_bounds__(kThreads) void k_fma_peak(int iters, T a, T b) {
-  T x[8];
+// The FMA pipe's rate depends on how the operands of an FMA fall on the register
+// banks, so the kernel comes in three operand patterns and the caller keeps the
+// fastest: P0 the same multiplier and addend for every chain, P1 and P2 four and two
+// different ones (on GB300 P1 and P2 run 13 % faster in FP64 than P0).
+template <typename T, int P>
+__global__ __launch_bounds__(kThreads) void k_fma_peak(int iters, T a0, T b0) {
+  T x[8], a[4], b[4];
 #pragma unroll
   for (int q = 0; q < 8; ++q) x[q] = (T)(threadIdx.x * 8 + q) * (T)1e-3;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    a[q] = a0 - (T)q * (T)1e-6;
+    b[q] = b0 + (T)q * (T)1e-9;
+  }
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) x[q] = fma(x[q], a, b);
+      for (int q = 0; q < 8; ++q) {
+        if (P == 0) x[q] = fma(x[q], a0, b0);
+        else if (P == 1) x[q] = fma(x[q], a[q & 3], b[(q >> 2) & 3]);
+        else x[q] = fma(x[q], a[(q >> 1) & 3], b[q & 1]);
+      }
     }
   }
   T t = (T)0;
@@ -974,14 +987,17 @@ __global__ __launch_bounds__(kThreads) void k_fma_peak(int iters, T a, T b) {
 }
 
 template <typename T>
-cudaError_t launch_fma_peak(int blocks_per_sm, int iters, cudaStream_t s, double* fmas) {
+cudaError_t launch_fma_peak(int pattern, int blocks_per_sm, int iters, cudaStream_t s, double* fmas) {
   const int grid = sm_count() * blocks_per_sm;
-  k_fma_peak<T><<<grid, kThreads, 0, s>>>(iters, (T)0.999999, (T)1e-7);
+  const T a = (T)0.999999, b = (T)1e-7;
+  if (pattern == 0) k_fma_peak<T, 0><<<grid, kThreads, 0, s>>>(iters, a, b);
+  else if (pattern == 1) k_fma_peak<T, 1><<<grid, kThreads, 0, s>>>(iters, a, b);
+  else k_fma_peak<T, 2><<<grid, kThreads, 0, s>>>(iters, a, b);
   if (fmas) *fmas = (double)grid * kThreads * (double)iters * 16.0 * 8.0;
   return cudaGetLastError();
 }
-template cudaError_t launch_fma_peak<double>(int, int, cudaStream_t, double*);
-template cudaError_t launch_fma_peak<float>(int, int, cudaStream_t, double*);
+template cudaError_t launch_fma_peak<double>(int, int, int, cudaStream_t, double*);
+template cudaError_t launch_fma_peak<float>(int, int, int, cudaStream_t, double*);
 
 // -------------------------------------------------------------- combine
 // out[r] = keep * out[r] + sum_q coef[q] W_q[r]   (keep = 0 overwrites out)

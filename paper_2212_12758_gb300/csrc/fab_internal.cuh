@@ -523,10 +523,10 @@ cudaError_t launch_to_f32(int n, const double* x, float* y, cudaStream_t s);
 cudaError_t launch_csr_spmv(int n, const int* rowptr, const int* colind, const double* vals, const double* x,
                             double* y, cudaStream_t s);
 
-// FMA throughput probe (T = double or float): blocks_per_sm x sm_count() blocks of
-// kThreads threads, each thread 128 iters FMAs; *fmas receives the total.
+// FMA throughput probe (T = double or float; operand pattern 0..2): blocks_per_sm x
+// sm_count() blocks of kThreads threads, each thread 128 iters FMAs; *fmas receives the total.
 template <typename T>
-cudaError_t launch_fma_peak(int blocks_per_sm, int iters, cudaStream_t s, double* fmas);
+cudaError_t launch_fma_peak(int pattern, int blocks_per_sm, int iters, cudaStream_t s, double* fmas);
 int sm_count();              // multiprocessors of the current device
 int grid_rows(int n);        // grid for the thread-per-row kernels
 // Raises (never lowers) kernel fn's dynamic shared-memory limit to at least `bytes`; thread-safe.

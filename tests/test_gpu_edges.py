@@ -214,3 +214,16 @@ def test_kappa_estimate_of_the_sketched_basis(fab, torch, method):
     assert st.kappa_est <= sv[0] / sv[-1] * (1 + 1e-6)
     _, st0 = _run(fab, torch, A, b, f=fab.EXP, t=-0.005, m=m, k=2, method=fab.NOPROJ)
     assert st0.kappa_est == 0.0
+
+
+def test_fma_peak_is_plausible(fab, torch):
+    """fab_fma_peak: the fastest of its operand patterns lies between half and all of
+    the device's nominal FP64 rate (2 FMAs per clock per SM at GB300's 2.07 GHz
+    maximum clock, 5 % slack) and FP32 runs at least 20 times faster than FP64."""
+    p = torch.cuda.get_device_properties(0)
+    f64, ms64 = fab.fma_peak(fab.FP64)
+    f32, _ = fab.fma_peak(fab.MIXED)
+    nominal64 = p.multi_processor_count * 2 * 2 * 2.07
+    assert 0.5 * nominal64 <= f64 <= 1.05 * nominal64, (f64, nominal64)
+    assert ms64 >= 40.0
+    assert f32 >= 20 * f64, (f32, f64)
