@@ -219,3 +219,25 @@ def test_batch_many_small_solves_in_one_launch(fab):
             alone = mats[i].apply(b, ps[i])
             assert _rel(x, alone) <= 1e-11, (i, _rel(x, alone))
     bt.close()
+
+
+def test_batch_wide_windows(fab):
+    """Windows of 5 to 8 columns (the persistent kernel's widest instantiation), FP64,
+    against each solve run alone at 1e-11 and against the oracle at 1e-10."""
+    A = {"cd3": W.convdiff(3, 19), "cd2": W.convdiff(2, 50)}
+    M = {k: fab.Matrix.from_csr(v) for k, v in A.items()}
+    specs = [("cd3", 5, 30, krylov.SKETCHED_FAST, osk.SRHT), ("cd2", 8, 40, krylov.SKETCHED_FAST, osk.SPARSE_SIGN),
+             ("cd3", 6, 25, krylov.NOPROJ, osk.SRHT), ("cd2", 7, 33, krylov.SKETCHED_FAST, osk.SRHT)]
+    mats, ps, bs, refs = [], [], [], []
+    for i, (name, k, m, method, sk) in enumerate(specs):
+        kw = dict(f=matfun.EXP, t=-0.003, m=m, k=k, s=4 * m, zeta=8, sketch=sk, method=method, seed=2 + i)
+        mats.append(M[name])
+        ps.append(fab.params(**kw))
+        bs.append(W.random_vector(A[name].n, 40 + i))
+        refs.append((name, kw))
+    bt = fab.Batch(mats, ps)
+    xs = bt.run(bs)
+    for i, ((name, kw), b, x) in enumerate(zip(refs, bs, xs)):
+        assert _rel(x, mats[i].apply(b, ps[i])) <= 1e-11, i
+        assert _rel(x, _oracle(A, name, kw, b)) <= TOL, i
+    bt.close()
